@@ -1,0 +1,415 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a property
+that a plausible mistake (dropped term, wrong sign, wrong weight, transposed
+index) would break -- closed forms, brute-force minimisers, library
+optimisers, invariants of the method, or values the paper prints.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.optimize as so
+import scipy.sparse as sp
+
+import oracle as O
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _dist_to_slab_bruteforce_2d(a, l, u, x, half=3.0, n=1201):
+    """Nearest point of the slab to x by dense grid search in 2-D."""
+    g = np.linspace(-half, half, n)
+    Y = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2) + x
+    r = Y @ a
+    ins = (r >= l) & (r <= u)
+    d = np.linalg.norm(Y[ins] - x, axis=1)
+    k = np.argmin(d)
+    return Y[ins][k], d[k]
+
+
+# ------------------------------------------------------ single projection --
+
+@pytest.mark.parametrize("seed", range(6))
+def test_hyperslab_projection_is_nearest_point(seed):
+    """Eq. (2), two-sided (Q1): P x lies in the slab, P x - x is parallel to a,
+    P is idempotent, and P x is the slab's nearest point (SLSQP)."""
+    rng = np.random.default_rng(seed)
+    n = 5
+    a = rng.standard_normal(n)
+    l, u = sorted(rng.uniform(-2, 2, size=2))
+    for x in [rng.standard_normal(n) * 3 for _ in range(4)]:
+        p = O.hyperslab_project(a, l, u, x)
+        r = a @ p
+        assert l - 1e-12 <= r <= u + 1e-12
+        d = p - x
+        # parallel to a: the component orthogonal to a vanishes
+        perp = d - (d @ a) / (a @ a) * a
+        assert np.linalg.norm(perp) <= 1e-12 * (1 + np.linalg.norm(d))
+        np.testing.assert_allclose(O.hyperslab_project(a, l, u, p), p, atol=1e-12)
+        cons = [{"type": "ineq", "fun": lambda y: a @ y - l},
+                {"type": "ineq", "fun": lambda y: u - a @ y}]
+        res = so.minimize(lambda y: np.sum((y - x) ** 2), x, constraints=cons,
+                          method="SLSQP", options={"ftol": 1e-14, "maxiter": 500})
+        np.testing.assert_allclose(p, res.x, atol=1e-6)
+
+
+def test_hyperslab_projection_bruteforce_2d():
+    """In 2-D the distance to the slab found by dense grid search matches."""
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        a = rng.standard_normal(2)
+        l, u = sorted(rng.uniform(-1, 1, size=2))
+        x = rng.standard_normal(2) * 2
+        p = O.hyperslab_project(a, l, u, x)
+        _, dbf = _dist_to_slab_bruteforce_2d(a, l, u, x)
+        assert abs(np.linalg.norm(p - x) - dbf) < 2 * 6.0 / 1200
+
+
+def test_halfspace_case_matches_eq2():
+    """With l = -inf the slab projection is the halfspace projection of Eq. (2):
+    moved by (<a,x> - b)/||a||^2 along -a when <a,x> > b, unchanged otherwise."""
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal(4)
+    b = 0.3
+    x_out = rng.standard_normal(4)
+    x_out += (b + 1.0 - a @ x_out) / (a @ a) * a          # <a,x> = b + 1 > b
+    x_in = x_out - 2.0 / (a @ a) * a                       # <a,x> = b - 1 < b
+    p = O.hyperslab_project(a, -np.inf, b, x_out)
+    np.testing.assert_allclose(p, x_out - 1.0 / (a @ a) * a, atol=1e-13)
+    np.testing.assert_array_equal(O.hyperslab_project(a, -np.inf, b, x_in), x_in)
+
+
+def test_relaxation_endpoints():
+    """Eq. (3): lambda = 0 keeps x, lambda = 1 is the projection, lambda = 2 the
+    reflection through the slab face."""
+    a = np.array([1.0, 2.0])
+    x = np.array([3.0, 3.0])
+    p = O.hyperslab_project(a, -1.0, 1.0, x)
+    np.testing.assert_allclose(O.relaxed(x, p, 0.0), x)
+    np.testing.assert_allclose(O.relaxed(x, p, 1.0), p)
+    refl = O.relaxed(x, p, 2.0)
+    assert abs((a @ refl) - (2 * 1.0 - a @ x)) < 1e-12
+
+
+# -------------------------------------------------------------- proximity --
+
+def test_single_constraint_proximity_is_half_squared_distance():
+    """Eq. (WeightedProximity) with one constraint (w = 1) is 1/2 dist^2; the
+    distance comes from a brute-force grid search, so a dropped 1/2 or a
+    missing ||a||^2 fails here."""
+    a = np.array([0.6, -1.7])
+    l, u = -0.4, 0.5
+    x = np.array([1.3, -0.9])
+    A = sp.csr_matrix(a[None, :])
+    S = O.setup(A, np.array([l]), np.array([u]))
+    _, dbf = _dist_to_slab_bruteforce_2d(a, l, u, x, n=2401)
+    assert abs(O.proximity(S, np.array([l]), np.array([u]), x) - 0.5 * dbf ** 2) < 5e-3 * dbf
+
+
+def test_proximity_zero_at_feasible_point():
+    rng = np.random.default_rng(5)
+    A = sp.random(30, 12, density=0.4, random_state=5, format="csr")
+    x = rng.uniform(size=12)
+    b = A @ x
+    S = O.setup(A, b - 0.1, b + 0.1)
+    assert O.proximity(S, b - 0.1, b + 0.1, x) == 0.0
+
+
+def test_zero_rows_dropped_or_rejected():
+    """Q11: an empty row whose slab contains 0 is dropped (weights use m'),
+    one whose slab excludes 0 is rejected."""
+    A = sp.csr_matrix(np.array([[1.0, 0.0], [0.0, 0.0], [0.0, 2.0]]))
+    S = O.setup(A, np.array([0.0, -1.0, 0.0]), np.array([1.0, 1.0, 1.0]))
+    np.testing.assert_allclose(S.w_sweep, [0.5, 0.0, 0.5])
+    with pytest.raises(ValueError):
+        O.setup(A, np.array([0.0, 0.5, 0.0]), np.array([1.0, 1.0, 1.0]))
+
+
+# ----------------------------------------------------------------- sweeps --
+
+def test_single_row_sweep_lands_on_slab():
+    """m = 1, lambda = 1, w = 1: one simultaneous step is the exact projection,
+    so the point lands on the violated face."""
+    rng = np.random.default_rng(2)
+    a = rng.uniform(0.1, 1.0, size=6)
+    A = sp.csr_matrix(a[None, :])
+    x = rng.uniform(size=6) * 10
+    l, u = np.array([1.0]), np.array([2.0])
+    S = O.setup(A, l, u)
+    x1, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, -np.inf, np.inf, x)
+    assert abs(a @ x1 - 2.0) < 1e-14 * 10
+
+
+def _tiny(seed, m=12, n=6, consistent=True):
+    rng = np.random.default_rng(seed)
+    A = sp.csr_matrix(rng.uniform(0, 1, size=(m, n)) * (rng.uniform(size=(m, n)) < 0.7))
+    A = A[np.asarray(A.multiply(A).sum(1)).ravel() > 0]
+    xt = rng.uniform(0, 1, size=n)
+    b = A @ xt
+    if not consistent:
+        b = b * (1 + 0.5 * rng.standard_normal(b.shape))
+    l, u = np.minimum(b * 0.97, b * 1.03), np.maximum(b * 0.97, b * 1.03)
+    return A, l, u
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 1.5, 1.9])
+@pytest.mark.parametrize("consistent", [True, False])
+def test_cimmino_proximity_nonincreasing(lam, consistent):
+    """The box-projected simultaneous step is a projected gradient step on
+    F = 1/2 sum w_i d_i^2 with Lipschitz constant sum w_i = 1, so F never
+    increases for lambda in (0, 2) -- on consistent and inconsistent systems."""
+    A, l, u = _tiny(7 + int(consistent), consistent=consistent)
+    S = O.setup(A, l, u)
+    x = np.full(A.shape[1], 0.9)
+    prev = O.proximity(S, l, u, x)
+    for _ in range(200):
+        x, p_in = O.sweep(S, O.CIMMINO, l, u, lam, 0.0, 1.0, x)
+        assert abs(p_in - prev) <= 1e-15 + 1e-12 * prev    # monitor = F at the input
+        cur = O.proximity(S, l, u, x)
+        assert cur <= prev * (1 + 1e-12) + 1e-300
+        prev = cur
+
+
+def test_cimmino_consistent_converges_to_feasible():
+    A, l, u = _tiny(21, consistent=True)
+    S = O.setup(A, l, u)
+    x = np.zeros(A.shape[1])
+    for _ in range(5000):
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, 0.0, 1.0, x)
+    assert O.proximity(S, l, u, x) < 1e-10
+
+
+def test_cimmino_limit_is_bruteforce_least_violation_point_3x3():
+    """3 inconsistent slabs in 3 unknowns with a box: the simultaneous method's
+    limit minimises the equal-weight proximity over the box.  The minimiser is
+    found independently by a dense grid and refined by L-BFGS-B; wrong weights
+    or a wrong step would converge elsewhere."""
+    A = np.array([[1.0, 0.5, 0.0], [0.2, 1.0, 0.7], [0.9, 0.0, 1.2]])
+    l = np.array([1.4, 0.1, 1.9])
+    u = np.array([1.6, 0.3, 2.0])
+    # a 4th slab conflicting with the first makes the system inconsistent
+    A = np.vstack([A, [1.0, 0.5, 0.0]])
+    l = np.append(l, 0.2)
+    u = np.append(u, 0.3)
+    S = O.setup(sp.csr_matrix(A), l, u)
+    x = np.full(3, 0.5)
+    for _ in range(20000):
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, 0.0, 1.0, x)
+
+    def F(y):   # 1/2 mean of squared distances, written from the geometry
+        r = A @ y
+        viol = np.maximum(l - r, 0) + np.maximum(r - u, 0)
+        return 0.5 * np.mean(viol ** 2 / np.sum(A * A, axis=1))
+
+    g = np.linspace(0, 1, 61)
+    G = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    R = G @ A.T
+    V = np.maximum(l - R, 0) + np.maximum(R - u, 0)
+    Fg = 0.5 * np.mean(V ** 2 / np.sum(A * A, axis=1), axis=1)
+    y0 = G[np.argmin(Fg)]
+    res = so.minimize(F, y0, method="L-BFGS-B", bounds=[(0, 1)] * 3,
+                      options={"ftol": 1e-16, "gtol": 1e-12, "maxiter": 10000})
+    assert F(x) <= Fg.min() + 1e-12
+    assert abs(F(x) - res.fun) < 1e-10
+    np.testing.assert_allclose(x, res.x, atol=2e-4)
+
+
+def test_bip_single_block_is_cimmino_bitwise():
+    A, l, u = _tiny(31, m=20, n=8, consistent=False)
+    S1 = O.setup(A, l, u)
+    S2 = O.setup(A, l, u, O.BIP, np.zeros(A.shape[0], dtype=np.int32))
+    x1 = x2 = np.full(A.shape[1], 0.3)
+    for _ in range(20):
+        x1, p1 = O.sweep(S1, O.CIMMINO, l, u, 1.0, 0.0, 1.0, x1)
+        x2, p2 = O.sweep(S2, O.BIP, l, u, 1.0, 0.0, 1.0, x2)
+        np.testing.assert_array_equal(x1, x2)
+        assert p1 == p2
+
+
+def test_bip_block_step_does_not_increase_block_proximity():
+    A, l, u = _tiny(41, m=24, n=8, consistent=False)
+    blocks = np.arange(A.shape[0]) % 3
+    S = O.setup(A, l, u, O.BIP, blocks.astype(np.int32))
+    x = np.full(A.shape[1], 0.7)
+    for _ in range(30):
+        for rows, At in zip(S.blocks, S.sub):
+            St = O.setup(At, l[rows], u[rows])
+            before = O.proximity(St, l[rows], u[rows], x)
+            x, _ = O.simultaneous_step(At, S.rho[rows], S.keep[rows], S.w_sweep[rows],
+                                       S.w_prox[rows], l[rows], u[rows], 1.0, 0.0, 1.0, x)
+            assert O.proximity(St, l[rows], u[rows], x) <= before * (1 + 1e-12) + 1e-300
+
+
+def test_bip_weights_are_per_block():
+    A = sp.csr_matrix(np.eye(5))
+    S = O.setup(A, np.zeros(5), np.ones(5), O.BIP, np.array([0, 0, 1, 1, 1], np.int32))
+    np.testing.assert_allclose(S.w_sweep, [0.5, 0.5, 1 / 3, 1 / 3, 1 / 3])
+    np.testing.assert_allclose(S.w_prox, np.full(5, 0.2))
+
+
+# ------------------------------------------------------------- objectives --
+
+def test_tv_constant_image_is_zero():
+    assert O.tv_iso(np.full(12, 0.37), 3, 4) == 0.0
+    assert O.tv_aniso(np.full(12, 0.37), 3, 4) == 0.0
+    assert not np.any(O.tv_iso_subgrad(np.full(12, 0.37), 3, 4))
+
+
+@pytest.mark.parametrize("H,W,c", [(5, 7, 3), (8, 4, 2)])
+def test_tv_vertical_step_edge(H, W, c):
+    """A vertical edge of height h between columns c-1 and c crosses H-1 terms
+    of Eq. (TV) with value h each (non-square H x W catches a transposition)."""
+    h = 0.8
+    X = np.zeros((H, W))
+    X[:, c:] = h
+    assert abs(O.tv_iso(X.ravel(), H, W) - (H - 1) * h) < 1e-14
+    assert abs(O.tv_aniso(X.ravel(), H, W) - H * h) < 1e-14
+    Xt = np.zeros((H, W))
+    Xt[c:, :] = h     # horizontal edge: W-1 terms
+    assert abs(O.tv_iso(Xt.ravel(), H, W) - (W - 1) * h) < 1e-14
+
+
+def test_tv_checkerboard_closed_forms():
+    H, W, h = 6, 9, 0.5
+    X = h * ((np.arange(H)[:, None] + np.arange(W)[None, :]) % 2).astype(float)
+    assert abs(O.tv_iso(X.ravel(), H, W) - (H - 1) * (W - 1) * h * np.sqrt(2)) < 1e-12
+    assert abs(O.tv_aniso(X.ravel(), H, W) - h * ((H - 1) * W + H * (W - 1))) < 1e-12
+
+
+@pytest.mark.parametrize("kind", [O.OBJ_TV_ISO, O.OBJ_TV_ANISO])
+def test_tv_subgradient_matches_central_differences(kind):
+    """Away from kinks TV is differentiable and its subgradient is the
+    gradient: compare with central finite differences."""
+    H, W = 7, 5
+    rng = np.random.default_rng(9)
+    x = rng.uniform(size=H * W)    # distinct values: no kink
+    ob = O.Objective(kind, (H, W))
+    g = ob.g(x)
+    eps = 1e-6
+    fd = np.array([(ob.f(x + eps * e) - ob.f(x - eps * e)) / (2 * eps) for e in np.eye(H * W)])
+    np.testing.assert_allclose(g, fd, atol=1e-6)
+
+
+def test_tv_subgradient_inequality_at_kinks():
+    """At a kink (flat regions) the returned vector is a subgradient:
+    f(y) >= f(x) + g.(y - x) for all y (checked on random y)."""
+    H, W = 6, 6
+    x = np.zeros(H * W)
+    x[7] = 1.0
+    x[20:24] = 0.5
+    rng = np.random.default_rng(4)
+    for kind in (O.OBJ_TV_ISO, O.OBJ_TV_ANISO):
+        ob = O.Objective(kind, (H, W))
+        g, fx = ob.g(x), ob.f(x)
+        for _ in range(200):
+            y = x + rng.standard_normal(H * W) * rng.uniform(0.001, 1.0)
+            assert ob.f(y) >= fx + g @ (y - x) - 1e-12
+
+
+def test_mean_dose_vector_hand_example():
+    """f_Mean over a 2-voxel structure with doses d = A x: c = A^T 1 / N."""
+    body = sp.csr_matrix(np.array([[1.0, 2.0], [3.0, 4.0]]))
+    np.testing.assert_allclose(O.mean_dose_vector(body), [2.0, 3.0])
+
+
+# ---------------------------------------------------------- perturbations --
+
+def test_linear_objective_step_decreases_by_beta_norm():
+    """For f = c.x and v = -c/||c||: f(z) = f(y) - beta ||c|| (Sec. 2.1.2, Q3)."""
+    c = np.array([0.2, 1.5, 0.7])
+    ob = O.Objective(O.OBJ_LINEAR, c=c)
+    st = O.PertState()
+    P = O.Params(gamma=0.8, alpha=0.9, n_red=1)
+    y = np.array([1.0, 2.0, 3.0])
+    z, acc, tr = O.perturbation_phase(ob, y.copy(), st, P)
+    assert acc == 1 and tr == 1 and st.ell == 1
+    assert abs(ob.f(z) - (ob.f(y) - 0.8 * np.linalg.norm(c))) < 1e-14
+
+
+def test_perturbation_is_nonascending_and_counts_trials():
+    """Accepted steps never increase f (Algorithm 1); the exponent advances at
+    every trial (Q4) and the step sizes stay below gamma / (1 - alpha)."""
+    H, W = 16, 16
+    rng = np.random.default_rng(8)
+    x = rng.uniform(size=H * W)
+    ob = O.Objective(O.OBJ_TV_ISO, (H, W))
+    P = O.Params(gamma=2.0, alpha=0.7, n_red=4, max_trials=50)
+    st = O.PertState()
+    total_beta = 0.0
+    f0 = ob.f(x)
+    for k in range(30):
+        ell0 = st.ell
+        x, acc, tr = O.perturbation_phase(ob, x, st, P)
+        assert st.ell - ell0 == tr
+        total_beta += sum(P.gamma * P.alpha ** e for e in range(ell0, st.ell))
+        f1 = ob.f(x)
+        assert f1 <= f0 + 1e-12
+        f0 = f1
+    assert total_beta <= P.gamma / (1 - P.alpha) + 1e-12
+
+
+def test_unperturbed_run_equals_plain_sweeps():
+    """obj = NONE (or gamma = 0) gives exactly the feasibility-seeking iterates."""
+    A, l, u = _tiny(51, m=30, n=16, consistent=False)
+    S = O.setup(A, l, u)
+    P = O.Params(gamma=0.0, max_sweeps=15)
+    ob = O.Objective(O.OBJ_TV_ISO, (4, 4))
+    r0 = O.run(S, O.CIMMINO, l, u, 0.0, 1.0, O.Objective(O.OBJ_NONE), P)
+    r1 = O.run(S, O.CIMMINO, l, u, 0.0, 1.0, ob, P, x0=np.zeros(16))
+    x = np.zeros(16)
+    for _ in range(15):
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, 0.0, 1.0, x)
+    np.testing.assert_array_equal(r0.x, x)
+    np.testing.assert_array_equal(r1.x, x)
+
+
+def test_restart_resets_exponent():
+    """Sec. 2.1.2: after the r-th restart the exponent becomes r (Q7)."""
+    P = O.Params(restart_every=10)
+    st = O.PertState(ell=37)
+    O.maybe_restart(st, 9, P)
+    assert st.ell == 37
+    O.maybe_restart(st, 10, P)
+    assert st.ell == 1 and st.restarts == 1
+    O.maybe_restart(st, 10, P)      # idempotent within one iteration
+    assert st.ell == 1
+    st.ell = 50
+    O.maybe_restart(st, 20, P)
+    assert st.ell == 2
+
+
+def test_zero_subgradient_skips_phase():
+    """x0 = 0 has TV subgradient 0: the phase accepts nothing and leaves l (Q6, Q18)."""
+    ob = O.Objective(O.OBJ_TV_ISO, (4, 4))
+    st = O.PertState()
+    y, acc, tr = O.perturbation_phase(ob, np.zeros(16), st, O.Params())
+    assert acc == 0 and tr == 0 and st.ell == 0 and not y.any()
+
+
+# --------------------------------------------------------------- stopping --
+
+def test_stopping_defaults_are_the_papers():
+    with open(os.path.join(GOLD, "paper_defaults.json")) as fh:
+        gold = json.load(fh)["stopping"]
+    P = O.Params()
+    assert P.prox_abs == gold["prox_abs"] and P.prox_rel == gold["prox_rel"]
+    assert P.patience == gold["patience"] and P.max_sweeps == gold["max_sweeps"]
+    assert P.obj_rel == gold["obj_rel"]
+
+
+def test_stopping_rule_sequences():
+    P = O.Params(prox_abs=1e-6, prox_rel=1e-3, patience=3, obj_rel=0.0)
+    ss = O.StopState()
+    seq = [1.0, 0.5, 0.4999, 0.49985, 0.4998, 0.49979, 0.3]
+    hits = [O.stop_check(ss, p, None, P) for p in seq]
+    assert hits == [False, False, False, False, True, True, False]
+    ss = O.StopState()
+    assert O.stop_check(ss, 1e-7, None, P)          # below P*
+    # objective criterion must also hold when enabled
+    P2 = O.Params(prox_abs=1e-6, obj_rel=1e-6)
+    ss = O.StopState()
+    assert not O.stop_check(ss, 1e-7, 10.0, P2)
+    assert O.stop_check(ss, 1e-7, 10.0 + 1e-7, P2)
+    assert not O.stop_check(ss, 1e-7, 11.0, P2)
