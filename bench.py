@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the superiorized hyperslab-projection path on GB300.
+
+A step is one superiorized iteration (Algorithm 1): the TV perturbation phase
+followed by one fused Cimmino sweep over the CT 512x512 system (360 angles x
+725 bins, Siddon CSR, FP32 values, int32 indices) with the fused proximity.
+The headline value is nnz * sweeps / s with A resident in HBM; the e2e value
+is the same metric through the C ABI with host buffers (new bounds in, x and
+statistics out, copies inside the timed region).  Extra variants (block-
+iterative, BF16 values, batched seismic, radiotherapy, tiny CT) are reported
+under "variants".
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "nnz·sweeps/s"
+UNIT = "nnz*sweeps/s"
+CT512 = dict(N=512, nang=360, nbin=725, I0=5e3, delta=0.02, seed_phantom=201, seed_noise=202)
+SUP = dict(gamma=0.5, alpha=0.99, n_red=1)
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def ct512():
+    import synth
+    return synth.ct_problem(**CT512)
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100",
+                                          "-i", self.gpu], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def gpu_id_for(dev: int) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        return ids[dev] if dev < len(ids) else str(dev)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU baseline --
+
+def cpu_baseline(prob, seconds: float, warm: int = 0):
+    """The FP64 oracle as it stands, timed on this host on a bounded sample:
+    superiorized Cimmino iterations of the same workload until `seconds`."""
+    import oracle as O
+    S, l, u, lo, hi = O.from_problem(prob)
+    ob = O.Objective(O.OBJ_TV_ISO, prob.shape)
+    P = O.Params(**SUP)
+    st = O.PertState()
+    x = np.zeros(prob.A.n)
+    for _ in range(warm):
+        x, _, _ = O.perturbation_phase(ob, x, st, P)
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+    it = 0
+    t0 = time.perf_counter()
+    while True:
+        x, _, _ = O.perturbation_phase(ob, x, st, P)
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+        it += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return it, el
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    prob = ct512()
+    nnz = prob.A.nnz
+    import oracle as O
+    S, l, u, lo, hi = O.from_problem(prob)
+    ob = O.Objective(O.OBJ_TV_ISO, prob.shape)
+    P = O.Params(**SUP)
+    st = O.PertState()
+    x = np.zeros(prob.A.n)
+
+    def step(x):
+        x, _, _ = O.perturbation_phase(ob, x, st, P)
+        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+        return x
+
+    for _ in range(args.warmup):
+        x = step(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = step(x)
+    el = time.perf_counter() - t0
+    v = nnz * args.steps / el
+    sample = (f"{args.steps} superiorized Cimmino iterations (TV perturbation + sweep) of the "
+              f"CT 512x512 workload, FP64 numpy/scipy oracle, single thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": config_of(prob),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def config_of(prob):
+    return {"workload": "ct512_cimmino_tv_f32", "image": "512x512", "angles": 360, "bins": 725,
+            "m": prob.A.m, "n": prob.A.n, "nnz": prob.A.nnz, "I0": 5e3, "slab_delta": 0.02,
+            "perturbation": "TV, beta=0.5*0.99^l, n_red=1", "relaxation": 1.0,
+            "l2": "inputs larger than L2 (A values+indices ~0.96 GB > 126 MB L2)"}
+
+
+# ------------------------------------------------------------------ ours ----
+
+def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
+    """Run W untimed iterations, then K timed ones in one suppy_run call;
+    returns (elapsed ms, sweep-kernel ms, sweep-kernel launches, launches)."""
+    import torch
+    s = torch.cuda.current_stream()
+    if W:
+        ctx.suppy_run(pk.suppy_params_default(max_sweeps=W, **params_kw))
+    torch.cuda.synchronize()
+    if with_timing:
+        ctx.suppy_timing_enable(True)
+    l0 = ctx.suppy_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    ctx.suppy_run(pk.suppy_params_default(max_sweeps=K, **params_kw))
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nl = ctx.suppy_launch_count() - l0
+    kms, kn = ctx.suppy_kernel_time() if with_timing else (0.0, 0)
+    if with_timing:
+        ctx.suppy_timing_enable(False)
+    return ms, kms, kn, nl
+
+
+def sweep_alg_bytes(m, n, nnz, vbytes, B=1):
+    """Algorithmic bytes of one sweep launch: A values and column indices once,
+    per-row offset/l/u/weight (l, u per right-hand side), x read and delta
+    written once per right-hand side."""
+    return nnz * (vbytes + 4) + m * (8 + 8 * B) + n * 8 * B
+
+
+def variants(pk, K, W):
+    """Secondary workloads (outside the headline timed region)."""
+    import torch
+    import synth
+    out = {}
+
+    def run_one(name, prob, metric_units, **kw):
+        obj = kw.pop("obj")
+        dtype = kw.pop("dtype", pk.SUPPY_F32)
+        mode = kw.pop("mode", pk.SUPPY_CIMMINO)
+        pkw = kw.pop("params")
+        B = 1 if prob.l.ndim == 1 else prob.l.shape[1]
+        t0 = time.perf_counter()
+        ctx = pk.from_problem(prob, obj=obj, dtype=dtype, mode=mode)
+        t_create = time.perf_counter() - t0
+        ms, kms, kn, nl = time_iterations(ctx, pk, Kv, W, pkw)
+        info = ctx.suppy_info_get()
+        vb = 4 if dtype == pk.SUPPY_F32 else 2
+        nnz = prob.A.nnz
+        per_launch = kms / max(kn, 1)
+        nseg = info["nblocks"]
+        alg = sweep_alg_bytes(prob.A.m, prob.A.n, nnz, vb, B)
+        gbs = alg / nseg / (per_launch * 1e-3) / 1e9 if kn else None
+        out[name] = {"value": nnz * B * Kv / (ms * 1e-3), "unit": metric_units,
+                     "ms_per_step": ms / Kv, "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B,
+                     "sweep_kernel_ms": per_launch, "sweep_launches_per_step": nseg,
+                     "sweep_kernel_gbs_alg": gbs, "create_s": t_create,
+                     "lanes_per_row": info["lanes_per_row"], "grid": info["grid"]}
+        ctx.close()
+        torch.cuda.synchronize()
+
+    Kv = max(20, min(K, 200))
+    prob = ct512()
+    run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
+            params=SUP)
+    prob.blocks = synth.angle_blocks(360, 725, 36)
+    run_one("ct512_bip36_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP,
+            params=SUP)
+    del prob
+    seis = synth.seismic_problem(nrhs=16)
+    run_one("seismic_b16_atv_f32", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
+            params=SUP)
+    seis.l, seis.u = seis.l[:, 0].copy(), seis.u[:, 0].copy()
+    run_one("seismic_b1_atv_f32", seis, UNIT, obj=pk.SUPPY_OBJ_TV_ANISO, params=SUP)
+    del seis
+    rt = synth.rt_problem()
+    run_one("rt_bip3_meandose_f32", rt, UNIT, obj=pk.SUPPY_OBJ_LINEAR, mode=pk.SUPPY_BIP,
+            params=dict(gamma=1.0, alpha=0.99, n_red=1))
+    del rt
+    tiny = synth.ct_problem()
+    run_one("ct64_cimmino_tv_f32", tiny, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP)
+    return out
+
+
+def ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2606_27086_gb300 import build as pkbuild
+    pkbuild.build()
+    import paper_2606_27086_gb300 as pk
+
+    K, W = args.steps, args.warmup
+    prob = ct512()
+    A = prob.A
+    log(f"[bench] CT 512^2: m={A.m} n={A.n} nnz={A.nnz}")
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    info = ctx.suppy_info_get()
+    if W:
+        ctx.suppy_run(pk.suppy_params_default(max_sweeps=W, **SUP))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(gpu_id_for(local))
+    sampler.start()
+    time.sleep(0.3)
+    ms, kms, kn, nl = time_iterations(ctx, pk, K, 0, SUP)
+    clocks = sampler.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = A.nnz * K * world / (ms * 1e-3)
+    per_launch = kms / max(kn, 1)
+    alg = sweep_alg_bytes(A.m, A.n, A.nnz, 4)
+    peak, peak_kind = peaks()
+    achieved = alg / (per_launch * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "k_sweep (fused CSR sweep)",
+            "alg_bytes_per_launch": alg, "launch_ms": per_launch, "peak_source": peak_kind}
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(traffic_path):
+        try:
+            tr = json.load(open(traffic_path)).get("ct512_k_sweep")
+            if tr:
+                roof["traffic"] = tr
+        except Exception:
+            pass
+
+    # end to end through the C ABI with host buffers
+    Ke = max(5, min(K, 100))
+    l_pin = torch.from_numpy(np.ascontiguousarray(prob.l)).pin_memory()
+    u_pin = torch.from_numpy(np.ascontiguousarray(prob.u)).pin_memory()
+    x_pin = torch.empty(A.n, dtype=torch.float32).pin_memory()
+    p1 = pk.suppy_params_default(max_sweeps=1, **SUP)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        ctx.suppy_set_bounds(l_pin, u_pin)
+        st = ctx.suppy_run(p1)
+        ctx.suppy_get_x(x_pin)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e = {"value": A.nnz * Ke * world / te, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * A.m * 4, "d2h_bytes_per_step": A.n * 4 + 40,
+           "steps": Ke, "note": "set_bounds(host l,u) + one superiorized iteration + get_x(host)"}
+    del st
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(prob),
+           "roofline": roof, "e2e": e2e, "gpu_launches": int(nl), "clocks": clocks,
+           "launch_shape": {k: info[k] for k in ("lanes_per_row", "chunks_in_regs", "grid",
+                                                  "block", "perturb_cluster")}}
+    ctx.close()
+    if rank == 0 and not args.no_variants:
+        res["variants"] = variants(pk, K, min(W, 5))
+    if rank == 0 and not args.no_cpu:
+        it, el = cpu_baseline(prob, args.cpu_seconds)
+        res["cpu_baseline"] = {"value": A.nnz * it / el, "unit": UNIT, "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{it} superiorized Cimmino iterations of the CT "
+                                         f"512x512 workload ({el:.1f} s, FP64 numpy/scipy oracle, "
+                                         f"single thread)"}
+    if world > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        # each oracle step is about a second of CPU work: bound the sample
+        args.steps = min(args.steps, 20)
+        args.warmup = min(args.warmup, 3)
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

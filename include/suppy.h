@@ -1,0 +1,269 @@
+/*
+ * suppy.h -- C ABI of the GB300 (sm_103a) superiorized hyperslab-projection
+ * library (libsuppy_gb300.so).
+ *
+ * The library solves the feasibility problem  l <= A x <= u,  lo <= x <= hi
+ * (A sparse, CSR) with the simultaneous (Cimmino-type) or block-iterative
+ * projection method, superiorized by nonascending subgradient perturbations of
+ * an objective f (isotropic / anisotropic total variation, or a linear mean
+ * dose).  Paper: arXiv 2606.27086, "GPU-accelerated superiorization on
+ * constrained physical problems with SupPy".
+ *
+ *   hyperslab projection   Sec. 2.1.1, Eq. (2), taken two-sided:
+ *                          P_i x = x + ((clamp(<a_i,x>, l_i, u_i) - <a_i,x>) / ||a_i||^2) a_i
+ *   relaxation             Eq. (3): x + lambda (P x - x), lambda in (0, 2)
+ *   simultaneous step      Sec. 2.1.1: x <- box(x + lambda sum_i w_i (P_i x - x)),
+ *                          w_i = 1/m' over the m' nonzero rows
+ *   block-iterative step   Sec. 2.1.1: the same step inside block B_t with
+ *                          w_i = 1/|B_t|, blocks in order, box after each block
+ *   box projection         Sec. 2.3.3 (BoxProjection after each iteration)
+ *   proximity              Eq. (WeightedProximity): 1/2 sum_i w_i ||P_i x - x||^2, w_i = 1/m'
+ *   superiorization        Algorithm 1; beta = gamma * alpha^l (Sec. 2.1.2),
+ *                          v = -g_f / ||g_f||; trial accepted when f(z) <= f(y)
+ *   stopping               Sec. 2.2.1 (P <= P*, relative change of P below dP*
+ *                          for N consecutive iterations, N_max) and Sec. 2.2.3
+ *                          (relative change of f below df*)
+ *   objectives             Eq. (TV) with its Combettes/Penfold subgradient
+ *                          (Sec. 2.3.1); anisotropic TV; f_Mean of Sec. 2.3.3
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every call returns a suppy_status.  Nothing aborts, traps or prints.  On
+ *   failure suppy_last_error(ctx) (or suppy_last_error(NULL) when no context
+ *   exists) returns a message; it stays valid until the next call on the same
+ *   context / thread.
+ * - Pointers flagged "on_device" are CUDA device pointers of the current
+ *   device; otherwise they are host pointers (pageable or pinned).  Inputs are
+ *   always copied: the caller keeps ownership and may free them after the call
+ *   returns.  Library device memory is owned by the context until
+ *   suppy_destroy.
+ * - All GPU work is enqueued on the context's stream (suppy_create /
+ *   suppy_set_stream).  Calls that return host values (proximity, objective,
+ *   get_x to host, run statistics, state) synchronize that stream.  A context
+ *   is not thread-safe; separate contexts are independent.
+ * - B right-hand sides (1 <= B <= 32) share one matrix.  Vectors over the
+ *   unknowns are n x B row-major (element (j, b) at j*B + b); vectors over the
+ *   constraints (l, u) are m x B row-major (i*B + b).  Per-RHS outputs are
+ *   arrays of length B.
+ * - Matrix indices are int32; nnz after padding each row to a multiple of 4
+ *   must stay below 2^31 (SUPPY_EINVAL otherwise).
+ */
+#ifndef SUPPY_GB300_H
+#define SUPPY_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct suppy_ctx suppy_ctx;
+
+typedef enum {
+    SUPPY_OK = 0,
+    SUPPY_EINVAL = -1,   /* bad argument, malformed CSR, NaN, l > u, ...         */
+    SUPPY_ENOMEM = -2,   /* device or host allocation failed                     */
+    SUPPY_ECUDA = -3,    /* a CUDA runtime call failed (message has the details) */
+    SUPPY_ETIMEOUT = -4, /* a bounded device-side wait gave up                   */
+    SUPPY_ESTATE = -5    /* call not valid in the context's state                */
+} suppy_status;
+
+/* Storage type of A's values on the device.  BF16/FP16 are rounded to nearest
+ * even from the FP32 input; every accumulation stays FP32 (dot products,
+ * corrections) or FP64 (row norms, proximity, objective, acceptance). */
+typedef enum { SUPPY_F32 = 0, SUPPY_BF16 = 1, SUPPY_F16 = 2 } suppy_dtype;
+
+/* Feasibility-seeking operator T (Sec. 2.1.1). */
+typedef enum { SUPPY_CIMMINO = 0, SUPPY_BIP = 1 } suppy_mode;
+
+/* Objective of the perturbation phase. */
+typedef enum {
+    SUPPY_OBJ_NONE = 0,     /* feasibility-seeking only                              */
+    SUPPY_OBJ_TV_ISO = 1,   /* Eq. (TV) on an img_h x img_w row-major image          */
+    SUPPY_OBJ_TV_ANISO = 2, /* sum |x[i+1,j]-x[i,j]| + sum |x[i,j+1]-x[i,j]|         */
+    SUPPY_OBJ_LINEAR = 3    /* f = c.x, e.g. f_Mean = (1/N_S) sum_{i in S} (A_S x)_i */
+} suppy_obj;
+
+/* CSR matrix: row_ptr[m+1] (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz),
+ * col[nnz] in [0, n), val[nnz] finite.  Column order inside a row is free. */
+typedef struct {
+    int32_t m, n;
+    int64_t nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const float* val;
+    int32_t on_device; /* 1: the three arrays are device pointers */
+} suppy_csr;
+
+typedef struct {
+    suppy_dtype a_dtype;
+    suppy_mode mode;
+    /* SUPPY_BIP: host array of m block ids in [0, nblocks).  Blocks are swept
+     * in increasing id; rows keep their relative order inside a block. */
+    const int32_t* block_of_row;
+    int32_t nblocks;
+    suppy_obj obj;
+    int32_t img_h, img_w;     /* TV objectives: img_h * img_w == n */
+    /* SUPPY_OBJ_LINEAR: either c_lin (n floats, host) or obj_rows, an
+     * objective matrix S whose column means c = S^T 1 / rows(S) are computed
+     * on the device at create (f_Mean over the structure S). */
+    const float* c_lin;
+    const suppy_csr* obj_rows;
+    int32_t nrhs;             /* B, 1..32 (0 is read as 1) */
+    int64_t box_len;          /* 1: scalar box bounds; n: one bound per unknown */
+    int32_t tune;             /* 1: time candidate launch shapes at create */
+} suppy_opts;
+
+/* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
+ * fills the paper's stopping defaults (P* = 1e-6, dP* = 1e-8, N = 5,
+ * N_max = 500, df* = 1e-6), lambda = 1, gamma = 0.5, alpha = 0.99, n_red = 1. */
+typedef struct {
+    double lambda;          /* relaxation, (0, 2)                                  */
+    double gamma, alpha;    /* beta = gamma * alpha^l                              */
+    int32_t n_red;          /* accepted reduction steps per perturbation phase     */
+    int32_t max_trials;     /* trials per reduction step before the phase ends     */
+    int32_t restart_every;  /* 0: no restarts; else l <- r after the r-th restart  */
+    int32_t max_sweeps;     /* N_max                                               */
+    int32_t check_every;    /* host polls the stop flags every this many sweeps    */
+    double prox_abs;        /* P*                                                  */
+    double prox_rel;        /* dP*                                                 */
+    double obj_rel;         /* df*; <= 0 disables the objective criterion          */
+    int32_t patience;       /* N                                                   */
+    int32_t use_stopping;   /* 0: run exactly max_sweeps sweeps                    */
+    int32_t use_graphs;     /* 1: replay the sweep loop through CUDA graphs        */
+} suppy_params;
+
+typedef struct {
+    int32_t sweeps;     /* sweeps applied to this right-hand side            */
+    int32_t accepted;   /* accepted perturbation steps, total                */
+    int32_t trials;     /* perturbation trials, total                        */
+    int32_t stopped;    /* 1 when the stopping rule ended this RHS           */
+    int64_t ell;        /* current power-law exponent l                      */
+    double proximity;   /* monitored proximity of the last sweep             */
+    double objective;   /* f(x^k) at the start of the last perturbation      */
+} suppy_stats;
+
+typedef struct {
+    int32_t m, n, nrhs, m_kept;   /* m_kept = m' (rows with ||a_i|| > 0)     */
+    int64_t nnz, nnz_padded;
+    int32_t nblocks;
+    int32_t lanes_per_row;        /* launch shape chosen for the sweep       */
+    int32_t chunks_in_regs;
+    int32_t grid;                 /* CTAs of the sweep launch                */
+    int32_t block;                /* threads per CTA of the sweep launch     */
+    int32_t perturb_cluster;      /* CTAs per cluster of the perturbation    */
+    int64_t device_bytes;         /* device memory held by the context       */
+} suppy_info;
+
+/* Fill *p with the defaults listed above. */
+void suppy_params_default(suppy_params* p);
+
+/* Create a context: copy A, l, u and the box into library-owned device
+ * memory, validate them, and run the setup step -- FP64 row norms
+ * ||a_i||^2 (the denominator of Eq. (2)), weights w_i (1/m' or 1/|B_t|), the
+ * zero-row drop (a row with ||a_i|| = 0 needs l_i <= 0 <= u_i, else
+ * SUPPY_EINVAL), conversion of A's values to opts->a_dtype, the block
+ * permutation and the launch partition.
+ *   A        CSR of the constraint rows; A->on_device selects host/device for
+ *            A, l, u, box_lo, box_hi and opts->c_lin alike.
+ *   l, u     m x B, +-INFINITY allowed, no NaN, l <= u.
+ *   box_lo, box_hi  opts->box_len values each (1 or n); -INF/+INF allowed.
+ *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * The initial point is x = box(0) for every right-hand side.  On success
+ * *out receives the context; on failure *out is NULL and nothing is leaked. */
+suppy_status suppy_create(const suppy_csr* A, const float* l, const float* u,
+                          const float* box_lo, const float* box_hi, const suppy_opts* opts,
+                          void* stream, suppy_ctx** out);
+
+/* Release every resource of the context (NULL is a no-op).  Synchronizes the
+ * context's stream first. */
+void suppy_destroy(suppy_ctx* ctx);
+
+/* Enqueue later work on another stream. */
+suppy_status suppy_set_stream(suppy_ctx* ctx, void* stream);
+
+/* Replace the slab bounds (m x B each, same rules as at create) -- e.g. a new
+ * sinogram over the same geometry.  Resets iteration counters, exponents,
+ * histories and stop flags, keeps x. */
+suppy_status suppy_set_bounds(suppy_ctx* ctx, const float* l, const float* u, int32_t on_device);
+
+/* Set x (n x B) and project it onto the box.  Resets iteration counters,
+ * exponents, histories and stop flags. */
+suppy_status suppy_set_x(suppy_ctx* ctx, const float* x, int32_t on_device);
+
+/* Copy x (n x B) out.  A host copy synchronizes the stream. */
+suppy_status suppy_get_x(suppy_ctx* ctx, float* x, int32_t on_device);
+
+/* One perturbation phase of Algorithm 1 on every active right-hand side:
+ * up to n_red accepted steps z = y - beta g/||g||, beta = gamma alpha^l, l
+ * advanced at every trial, accepted when f(z) <= f(y) in FP64; the phase
+ * ends early when ||g|| = 0 or max_trials trials in a row are rejected.
+ * Restarts (Sec. 2.1.2) apply when the sweep count is a positive multiple
+ * of restart_every.  accepted (host, B entries) may be NULL; when given the
+ * call synchronizes and writes the accepted steps of this phase.
+ * SUPPY_ESTATE when the context has no objective. */
+suppy_status suppy_perturb(suppy_ctx* ctx, const suppy_params* p, int32_t* accepted);
+
+/* Apply the feasibility-seeking operator T nsweeps times (no perturbation):
+ * Cimmino -- one fused pass over A computing r = A x, the clamped corrections
+ * and their scatter, then x <- box(x + delta); BIP -- the same per block.  Each
+ * sweep records the monitored proximity (Cimmino: P at the sweep's input point;
+ * BIP: the sum of each block's terms at that block's input point) and advances
+ * the stopping rule when p->use_stopping is set.  Asynchronous. */
+suppy_status suppy_sweep(suppy_ctx* ctx, const suppy_params* p, int32_t nsweeps);
+
+/* Eq. (WeightedProximity) at the current x, w_i = 1/m', FP64, deterministic:
+ * out[b] for each right-hand side (host, B entries).  Synchronizes. */
+suppy_status suppy_proximity(suppy_ctx* ctx, double* out);
+
+/* f(x) at the current x, FP64, deterministic; out[b] (host, B entries).
+ * Synchronizes.  SUPPY_ESTATE when the context has no objective. */
+suppy_status suppy_objective(suppy_ctx* ctx, double* out);
+
+/* Algorithm 1: repeat [perturbation phase (when an objective is set), one
+ * sweep] until the stopping rule holds for every right-hand side or
+ * max_sweeps sweeps ran.  Sweeps of a stopped right-hand side are skipped
+ * on the device.  out (host, B entries) may be NULL.  Synchronizes at the
+ * end and every check_every sweeps when use_stopping is set. */
+suppy_status suppy_run(suppy_ctx* ctx, const suppy_params* p, suppy_stats* out);
+
+/* Copy the per-sweep history of right-hand side rhs: prox[k] (monitored
+ * proximity of sweep k) and obj[k] (f(x^k), NaN when no objective), up to cap
+ * entries each; *count receives the number of recorded sweeps (which may
+ * exceed cap).  Either array may be NULL.  Synchronizes. */
+suppy_status suppy_history(suppy_ctx* ctx, int32_t rhs, double* prox, double* obj, int32_t cap,
+                           int32_t* count);
+
+/* Checkpoint: serialise x and the per-RHS iteration state (exponent l,
+ * restart count, sweep count, stopping state) into buf.  With buf NULL, *len
+ * receives the size needed.  Synchronizes. */
+suppy_status suppy_get_state(suppy_ctx* ctx, void* buf, size_t* len);
+
+/* Restore a checkpoint written by suppy_get_state for the same shapes. */
+suppy_status suppy_set_state(suppy_ctx* ctx, const void* buf, size_t len);
+
+/* Sizes and launch shapes of the context. */
+suppy_status suppy_info_get(const suppy_ctx* ctx, suppy_info* out);
+
+/* Kernel timing for measurement: when enabled, every sweep-kernel launch is
+ * bracketed by CUDA events on the context's stream and graphs are not used.
+ * suppy_kernel_time returns the summed event time (ms) and the launch count of
+ * the sweep kernel since timing was enabled, and synchronizes. */
+suppy_status suppy_timing_enable(suppy_ctx* ctx, int32_t enable);
+suppy_status suppy_kernel_time(suppy_ctx* ctx, double* total_ms, int64_t* launches);
+
+/* Number of kernels the library launched on this context so far. */
+int64_t suppy_launch_count(const suppy_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx NULL: of this thread's last
+ * failed call that had no context). */
+const char* suppy_last_error(const suppy_ctx* ctx);
+
+/* Library version string. */
+const char* suppy_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUPPY_GB300_H */

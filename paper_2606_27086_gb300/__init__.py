@@ -1,0 +1,357 @@
+"""Python binding of the GB300 superiorized hyperslab-projection library.
+
+Thin ctypes marshalling over the C ABI of ``include/suppy.h`` (the function
+names are the same); every step of the method runs in the CUDA kernels of
+``libsuppy_gb300.so``.  There is no CPU fallback: importing a function that
+needs the library raises when the library has not been built.
+
+Arrays may be numpy arrays (host) or torch CUDA tensors (device); one create
+call takes all its arrays from one side.  PyTorch is used only for device
+memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsuppy_gb300.so")
+
+SUPPY_OK, SUPPY_EINVAL, SUPPY_ENOMEM, SUPPY_ECUDA, SUPPY_ETIMEOUT, SUPPY_ESTATE = 0, -1, -2, -3, -4, -5
+SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2
+SUPPY_CIMMINO, SUPPY_BIP = 0, 1
+SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
+
+EXPORTED = [
+    "suppy_params_default", "suppy_create", "suppy_destroy", "suppy_set_stream",
+    "suppy_set_bounds", "suppy_set_x", "suppy_get_x", "suppy_perturb", "suppy_sweep",
+    "suppy_proximity", "suppy_objective", "suppy_run", "suppy_history", "suppy_get_state",
+    "suppy_set_state", "suppy_info_get", "suppy_timing_enable", "suppy_kernel_time",
+    "suppy_launch_count", "suppy_last_error", "suppy_version",
+]
+
+
+class suppy_csr(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int32)]
+
+
+class suppy_opts(ctypes.Structure):
+    _fields_ = [("a_dtype", ctypes.c_int), ("mode", ctypes.c_int),
+                ("block_of_row", ctypes.c_void_p), ("nblocks", ctypes.c_int32),
+                ("obj", ctypes.c_int), ("img_h", ctypes.c_int32), ("img_w", ctypes.c_int32),
+                ("c_lin", ctypes.c_void_p), ("obj_rows", ctypes.POINTER(suppy_csr)),
+                ("nrhs", ctypes.c_int32), ("box_len", ctypes.c_int64), ("tune", ctypes.c_int32)]
+
+
+class suppy_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("n_red", ctypes.c_int32),
+                ("max_trials", ctypes.c_int32), ("restart_every", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("prox_abs", ctypes.c_double), ("prox_rel", ctypes.c_double),
+                ("obj_rel", ctypes.c_double), ("patience", ctypes.c_int32),
+                ("use_stopping", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+
+
+class suppy_stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("stopped", ctypes.c_int32),
+                ("ell", ctypes.c_int64), ("proximity", ctypes.c_double),
+                ("objective", ctypes.c_double)]
+
+
+class suppy_info(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nrhs", ctypes.c_int32),
+                ("m_kept", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("nnz_padded", ctypes.c_int64), ("nblocks", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("chunks_in_regs", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("perturb_cluster", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises when it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2606_27086_gb300.build.build()"
+                           " -- there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "suppy_params_default": (None, [ctypes.POINTER(suppy_params)]),
+        "suppy_create": (ctypes.c_int, [ctypes.POINTER(suppy_csr), P, P, P, P,
+                                        ctypes.POINTER(suppy_opts), P, ctypes.POINTER(P)]),
+        "suppy_destroy": (None, [P]),
+        "suppy_set_stream": (ctypes.c_int, [P, P]),
+        "suppy_set_bounds": (ctypes.c_int, [P, P, P, I32]),
+        "suppy_set_x": (ctypes.c_int, [P, P, I32]),
+        "suppy_get_x": (ctypes.c_int, [P, P, I32]),
+        "suppy_perturb": (ctypes.c_int, [P, ctypes.POINTER(suppy_params), P]),
+        "suppy_sweep": (ctypes.c_int, [P, ctypes.POINTER(suppy_params), I32]),
+        "suppy_proximity": (ctypes.c_int, [P, P]),
+        "suppy_objective": (ctypes.c_int, [P, P]),
+        "suppy_run": (ctypes.c_int, [P, ctypes.POINTER(suppy_params), P]),
+        "suppy_history": (ctypes.c_int, [P, I32, P, P, I32, ctypes.POINTER(I32)]),
+        "suppy_get_state": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "suppy_set_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+        "suppy_info_get": (ctypes.c_int, [P, ctypes.POINTER(suppy_info)]),
+        "suppy_timing_enable": (ctypes.c_int, [P, I32]),
+        "suppy_kernel_time": (ctypes.c_int, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "suppy_launch_count": (I64, [P]),
+        "suppy_last_error": (ctypes.c_char_p, [P]),
+        "suppy_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SuppyError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"suppy status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int, ctx) -> None:
+    if status != SUPPY_OK:
+        msg = load_library().suppy_last_error(ctx)
+        raise SuppyError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            a = a.contiguous()
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda), a
+    arr = np.ascontiguousarray(a)
+    return ctypes.c_void_p(arr.ctypes.data), 0, arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def suppy_params_default(**overrides) -> suppy_params:
+    p = suppy_params()
+    load_library().suppy_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+    return p
+
+
+def _csr(row_ptr, col, val, m, n, keep):
+    rp, d1, k1 = _ptr(row_ptr)
+    cp, d2, k2 = _ptr(col)
+    vp, d3, k3 = _ptr(val)
+    keep += [k1, k2, k3]
+    if not (d1 == d2 == d3):
+        raise ValueError("row_ptr, col and val must live on the same side")
+    nnz = int(val.shape[0]) if hasattr(val, "shape") else len(val)
+    return suppy_csr(int(m), int(n), nnz, rp, cp, vp, d1)
+
+
+class Context:
+    """Owns one ``suppy_ctx``; methods call the C ABI functions of the same name."""
+
+    def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
+                 mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
+                 c_lin=None, obj_rows=None, nrhs=1, tune=0, stream=None):
+        lib = load_library()
+        self._lib = lib
+        keep = []
+        A = _csr(row_ptr, col, val, m, n, keep)
+        lp, dl, kl = _ptr(l)
+        up, du, ku = _ptr(u)
+        lop, _, klo = _ptr(box_lo)
+        hip, _, khi = _ptr(box_hi)
+        keep += [kl, ku, klo, khi]
+        o = suppy_opts()
+        o.a_dtype = dtype
+        o.mode = mode
+        if block_of_row is not None:
+            bor = np.ascontiguousarray(np.asarray(block_of_row), dtype=np.int32)
+            keep.append(bor)
+            o.block_of_row = ctypes.c_void_p(bor.ctypes.data)
+            o.nblocks = int(bor.max()) + 1 if bor.size else 1
+        o.obj = obj
+        if shape is not None:
+            o.img_h, o.img_w = int(shape[0]), int(shape[1])
+        if c_lin is not None:
+            cp, _, kc = _ptr(c_lin)
+            keep.append(kc)
+            o.c_lin = cp
+        if obj_rows is not None:
+            S = _csr(*obj_rows, keep=keep) if isinstance(obj_rows, tuple) else obj_rows
+            keep.append(S)
+            o.obj_rows = ctypes.pointer(S)
+        o.nrhs = int(nrhs)
+        blen = box_lo.shape[0] if hasattr(box_lo, "shape") else len(box_lo)
+        o.box_len = int(blen)
+        o.tune = int(tune)
+        ctx = ctypes.c_void_p()
+        self._keep = keep
+        self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
+        st = lib.suppy_create(ctypes.byref(A), lp, up, lop, hip, ctypes.byref(o),
+                              _stream_handle(stream), ctypes.byref(ctx))
+        _check(st, None)
+        self.ctx = ctx
+        self._keep = None
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "ctx", None):
+            self._lib.suppy_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C ABI wrappers (same names)
+    def suppy_set_stream(self, stream):
+        _check(self._lib.suppy_set_stream(self.ctx, _stream_handle(stream)), self.ctx)
+
+    def suppy_set_bounds(self, l, u):
+        lp, dl, k1 = _ptr(l)
+        up, du, k2 = _ptr(u)
+        _check(self._lib.suppy_set_bounds(self.ctx, lp, up, dl), self.ctx)
+
+    def suppy_set_x(self, x):
+        xp, d, k = _ptr(x)
+        _check(self._lib.suppy_set_x(self.ctx, xp, d), self.ctx)
+
+    def suppy_get_x(self, out=None):
+        if out is None:
+            out = np.empty((self.n, self.nrhs) if self.nrhs > 1 else self.n, dtype=np.float32)
+        xp, d, k = _ptr(out)
+        _check(self._lib.suppy_get_x(self.ctx, xp, d), self.ctx)
+        return out
+
+    def suppy_perturb(self, params: suppy_params, want_accepted: bool = True):
+        acc = np.zeros(self.nrhs, dtype=np.int32) if want_accepted else None
+        ap = ctypes.c_void_p(acc.ctypes.data) if acc is not None else None
+        _check(self._lib.suppy_perturb(self.ctx, ctypes.byref(params), ap), self.ctx)
+        return acc
+
+    def suppy_sweep(self, params: suppy_params, nsweeps: int = 1):
+        _check(self._lib.suppy_sweep(self.ctx, ctypes.byref(params), int(nsweeps)), self.ctx)
+
+    def suppy_proximity(self):
+        out = np.zeros(self.nrhs, dtype=np.float64)
+        _check(self._lib.suppy_proximity(self.ctx, ctypes.c_void_p(out.ctypes.data)), self.ctx)
+        return out
+
+    def suppy_objective(self):
+        out = np.zeros(self.nrhs, dtype=np.float64)
+        _check(self._lib.suppy_objective(self.ctx, ctypes.c_void_p(out.ctypes.data)), self.ctx)
+        return out
+
+    def suppy_run(self, params: suppy_params):
+        st = (suppy_stats * self.nrhs)()
+        _check(self._lib.suppy_run(self.ctx, ctypes.byref(params), ctypes.cast(st, ctypes.c_void_p)),
+               self.ctx)
+        return [dict(sweeps=s.sweeps, accepted=s.accepted, trials=s.trials, stopped=s.stopped,
+                     ell=s.ell, proximity=s.proximity, objective=s.objective) for s in st]
+
+    def suppy_history(self, rhs: int = 0, cap: int = 1 << 16):
+        cnt = ctypes.c_int32()
+        _check(self._lib.suppy_history(self.ctx, int(rhs), None, None, 0, ctypes.byref(cnt)),
+               self.ctx)
+        k = min(cnt.value, cap)
+        prox = np.zeros(k, dtype=np.float64)
+        obj = np.zeros(k, dtype=np.float64)
+        _check(self._lib.suppy_history(self.ctx, int(rhs), ctypes.c_void_p(prox.ctypes.data),
+                                       ctypes.c_void_p(obj.ctypes.data), k, ctypes.byref(cnt)),
+               self.ctx)
+        return prox, obj
+
+    def suppy_get_state(self) -> bytes:
+        ln = ctypes.c_size_t()
+        _check(self._lib.suppy_get_state(self.ctx, None, ctypes.byref(ln)), self.ctx)
+        buf = ctypes.create_string_buffer(ln.value)
+        _check(self._lib.suppy_get_state(self.ctx, buf, ctypes.byref(ln)), self.ctx)
+        return buf.raw
+
+    def suppy_set_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.suppy_set_state(self.ctx, buf, len(blob)), self.ctx)
+
+    def suppy_info_get(self) -> dict:
+        inf = suppy_info()
+        _check(self._lib.suppy_info_get(self.ctx, ctypes.byref(inf)), self.ctx)
+        return {k: getattr(inf, k) for k, _ in suppy_info._fields_}
+
+    def suppy_timing_enable(self, enable: bool = True):
+        _check(self._lib.suppy_timing_enable(self.ctx, int(enable)), self.ctx)
+
+    def suppy_kernel_time(self):
+        ms = ctypes.c_double()
+        nl = ctypes.c_int64()
+        _check(self._lib.suppy_kernel_time(self.ctx, ctypes.byref(ms), ctypes.byref(nl)), self.ctx)
+        return ms.value, nl.value
+
+    def suppy_launch_count(self) -> int:
+        return int(self._lib.suppy_launch_count(self.ctx))
+
+
+def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
+                 stream=None, tune=0) -> Context:
+    """Create a context from a ``synth.Problem`` (host arrays, or copied to the
+    current CUDA device first when ``device`` is True)."""
+    A = prob.A
+    l, u = prob.l, prob.u
+    nrhs = 1 if l.ndim == 1 else l.shape[1]
+    arrs = [A.row_ptr, A.col, A.val, l, u, prob.box_lo, prob.box_hi]
+    if device:
+        import torch
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    rp, col, val, l, u, lo, hi = arrs
+    kw = {}
+    if obj in (SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO):
+        kw["shape"] = prob.shape
+    if obj == SUPPY_OBJ_LINEAR:
+        if prob.body is not None:
+            b = prob.body
+            kw["obj_rows"] = (b.row_ptr, b.col, b.val, b.m, b.n)
+        else:
+            kw["c_lin"] = prob.c_lin
+    blocks = prob.blocks if mode == SUPPY_BIP else None
+    return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
+                   block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune, **kw)
+
+
+def version() -> str:
+    return load_library().suppy_version().decode()

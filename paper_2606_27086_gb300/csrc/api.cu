@@ -1,0 +1,1038 @@
+// Host side of the C ABI declared in include/suppy.h: context lifetime, input
+// validation, setup orchestration (device layout, weights, launch partition),
+// the Algorithm 1 driver loop, checkpoints and measurement hooks.  All compute
+// runs in the kernels of sweep.cu, perturb.cu and setup.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace suppy;
+
+namespace {
+
+thread_local std::string g_err;
+
+}  // namespace
+
+struct suppy_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int m = 0, n = 0, B_user = 1, B = 1;
+    long long nnz = 0, nnz_pad = 0;
+    suppy_dtype dt = SUPPY_F32;
+    suppy_mode mode = SUPPY_CIMMINO;
+    suppy_obj obj = SUPPY_OBJ_NONE;
+    int H = 0, W = 0;
+    int box_len = 1;
+    int nseg = 1;
+    std::vector<int> seg_start;     // device-order row ranges of the segments (blocks)
+    std::vector<int> seg_kept;      // kept rows per segment
+    int m_kept = 0;
+
+    // device buffers
+    int2* d_rinfo = nullptr;
+    int* d_col = nullptr;
+    void* d_val = nullptr;
+    float* d_wr = nullptr;
+    double* d_rho = nullptr;
+    float* d_l = nullptr;
+    float* d_u = nullptr;
+    int* d_perm = nullptr;          // device row -> source row (null: identity)
+    float* d_x = nullptr;
+    float* d_delta = nullptr;
+    float* d_g = nullptr;
+    float* d_lo = nullptr;
+    float* d_hi = nullptr;
+    double* d_pp = nullptr;
+    RhsState* d_st = nullptr;
+    double* d_prox_hist = nullptr;
+    double* d_obj_hist = nullptr;
+    int hist_cap = 0;
+    double* d_c64 = nullptr;
+    float* d_c32 = nullptr;
+    double* d_out = nullptr;        // B doubles for proximity / objective results
+    double* d_objpart = nullptr;
+    int* d_part = nullptr;          // nseg x (groups + 1)
+    double* h_out = nullptr;        // pinned B doubles
+    int k_upper = 0;                // upper bound of the sweep counters (history sizing)
+    float* d_stage_l = nullptr;     // persistent staging of host bounds (set_bounds)
+    float* d_stage_u = nullptr;
+    int* d_flags = nullptr;         // validation flags
+
+    // launch shapes
+    int G = 32, maxch = 4;
+    int grid_sweep = 0, groups = 0;
+    int grid_fin = 0;
+    int grid_obj = 0;
+    int perturb_cluster = 1;
+
+    // measurement
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+    double timing_ms = 0.0;
+    long long timing_n = 0;
+    long long launches = 0;
+    size_t dev_bytes = 0;
+    std::vector<void*> allocs;
+
+    std::string err;
+};
+
+namespace {
+
+suppy_status fail(suppy_ctx* c, suppy_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, SUPPY_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+suppy_status dalloc(suppy_ctx* c, T** p, size_t count) {
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, e == cudaErrorMemoryAllocation ? SUPPY_ENOMEM : SUPPY_ECUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    c->dev_bytes += bytes;
+    *p = static_cast<T*>(q);
+    return SUPPY_OK;
+}
+
+void dfree(suppy_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+// Copy count elements from a host or device pointer into a new device buffer
+// (returns src itself when it already lives on the device and own == false).
+template <typename T>
+suppy_status stage(suppy_ctx* c, const T* src, size_t count, int on_device, T** out,
+                   std::vector<void*>& temps) {
+    if (on_device) {
+        *out = const_cast<T*>(src);
+        return SUPPY_OK;
+    }
+    T* d = nullptr;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, SUPPY_ENOMEM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
+    }
+    d = static_cast<T*>(q);
+    temps.push_back(q);
+    if (count) CK(cudaMemcpyAsync(d, src, count * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    *out = d;
+    return SUPPY_OK;
+}
+
+struct TempGuard {
+    std::vector<void*> v;
+    cudaStream_t s = nullptr;
+    ~TempGuard() {
+        if (s) cudaStreamSynchronize(s);
+        for (void* p : v) cudaFree(p);
+    }
+};
+
+void note_launch(suppy_ctx* c, int k = 1) { c->launches += k; }
+
+// nnz-balanced contiguous partition of rows [r0, r1) into ng groups; the work
+// of a row is its padded length plus a fixed per-row cost.
+void partition(const std::vector<long long>& pref, int r0, int r1, int ng, int* out) {
+    const long long kRowCost = 16;
+    auto work = [&](int r) { return pref[r] + kRowCost * r; };
+    const long long w0 = work(r0), w1 = work(r1);
+    out[0] = r0;
+    int lo = r0;
+    for (int g = 1; g < ng; ++g) {
+        const long long target = w0 + (w1 - w0) * g / ng;
+        int a = lo, b = r1;
+        while (a < b) {
+            const int mid = a + (b - a) / 2;
+            if (work(mid) < target) a = mid + 1;
+            else b = mid;
+        }
+        out[g] = a;
+        lo = a;
+    }
+    out[ng] = r1;
+}
+
+void reset_state_host(suppy_ctx* c, std::vector<RhsState>& st) {
+    st.assign(c->B, RhsState{});
+    for (int b = 0; b < c->B; ++b) {
+        st[b].last_restart_k = -1;
+        st[b].stopped = (b >= c->B_user) ? 1 : 0;
+    }
+}
+
+suppy_status reset_state(suppy_ctx* c) {
+    c->k_upper = 0;
+    std::vector<RhsState> st;
+    reset_state_host(c, st);
+    CK(cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status ensure_hist(suppy_ctx* c, int need) {
+    if (need <= c->hist_cap) return SUPPY_OK;
+    int cap = std::max(need, std::max(1024, 2 * c->hist_cap));
+    double *p = nullptr, *o = nullptr;
+    suppy_status s;
+    if ((s = dalloc(c, &p, (size_t)cap * c->B)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &o, (size_t)cap * c->B)) != SUPPY_OK) return s;
+    if (c->hist_cap > 0) {
+        CK(cudaMemcpy2DAsync(p, cap * sizeof(double), c->d_prox_hist, c->hist_cap * sizeof(double),
+                             c->hist_cap * sizeof(double), c->B, cudaMemcpyDeviceToDevice,
+                             c->stream));
+        CK(cudaMemcpy2DAsync(o, cap * sizeof(double), c->d_obj_hist, c->hist_cap * sizeof(double),
+                             c->hist_cap * sizeof(double), c->B, cudaMemcpyDeviceToDevice,
+                             c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        dfree(c, c->d_prox_hist);
+        dfree(c, c->d_obj_hist);
+    }
+    c->d_prox_hist = p;
+    c->d_obj_hist = o;
+    c->hist_cap = cap;
+    return SUPPY_OK;
+}
+
+suppy_status flush_timing(suppy_ctx* c) {
+    if (c->evs.empty()) return SUPPY_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& pr : c->evs) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        c->timing_ms += ms;
+        c->timing_n += 1;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    c->evs.clear();
+    return SUPPY_OK;
+}
+
+// One application of T: every segment's fused sweep and its finalize.
+suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
+    StopParams sp;
+    sp.prox_abs = p->prox_abs;
+    sp.prox_rel = p->prox_rel;
+    sp.obj_rel = p->obj_rel;
+    sp.patience = p->patience;
+    sp.use_stopping = p->use_stopping;
+    sp.has_obj = c->obj != SUPPY_OBJ_NONE;
+    for (int t = 0; t < c->nseg; ++t) {
+        SweepArgs a;
+        a.rinfo = c->d_rinfo;
+        a.col = c->d_col;
+        a.val = c->d_val;
+        a.l = c->d_l;
+        a.u = c->d_u;
+        a.wr = c->d_wr;
+        a.x = c->d_x;
+        a.delta = c->d_delta;
+        a.part = c->d_part + (size_t)t * (c->groups + 1);
+        a.pp = c->d_pp;
+        a.st = c->d_st;
+        a.lam = (float)p->lambda;
+        a.B = c->B;
+        a.scatter = 1;
+        a.check_stop = 1;
+        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+        if (c->timing) {
+            CK(cudaEventCreate(&ev.first));
+            CK(cudaEventCreate(&ev.second));
+            CK(cudaEventRecord(ev.first, c->stream));
+        }
+        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxch, c->grid_sweep, c->stream));
+        else CK(launch_sweep_batched(a, c->dt, 32, c->grid_sweep, c->stream));
+        if (c->timing) {
+            CK(cudaEventRecord(ev.second, c->stream));
+            c->evs.push_back(ev);
+        }
+        FinalizeArgs f;
+        f.x = c->d_x;
+        f.delta = c->d_delta;
+        f.lo = c->d_lo;
+        f.hi = c->d_hi;
+        f.nB = (long long)c->n * c->B;
+        f.B = c->B;
+        f.box_len = c->box_len;
+        f.pp = c->d_pp;
+        f.npp = c->grid_sweep;
+        f.scale = 0.5 * (c->m_kept > 0 ? (double)c->seg_kept[t] / c->m_kept : 0.0);
+        if (c->nseg == 1) f.scale = 0.5;
+        f.st = c->d_st;
+        f.prox_hist = c->d_prox_hist;
+        f.obj_hist = c->d_obj_hist;
+        f.hist_cap = c->hist_cap;
+        f.first_seg = (t == 0);
+        f.last_seg = (t == c->nseg - 1);
+        f.sp = sp;
+        CK(launch_finalize(f, c->grid_fin, c->stream));
+        note_launch(c, 2);
+    }
+    c->k_upper += 1;
+    if (c->evs.size() > 8192) return flush_timing(c);
+    return SUPPY_OK;
+}
+
+suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_only) {
+    PerturbArgs a;
+    a.x = c->d_x;
+    a.g = c->d_g;
+    a.c32 = c->d_c32;
+    a.c64 = c->d_c64;
+    a.n = c->n;
+    a.B = c->B;
+    a.H = c->H;
+    a.W = c->W;
+    a.obj = (int)c->obj;
+    a.gamma = p ? p->gamma : 0.0;
+    a.alpha = p ? p->alpha : 0.0;
+    a.n_red = p ? p->n_red : 0;
+    a.max_trials = p ? p->max_trials : 0;
+    a.restart_every = p ? p->restart_every : 0;
+    a.st = c->d_st;
+    a.record_only = record_only;
+    CK(launch_perturb(a, c->perturb_cluster, c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+suppy_status check_params(suppy_ctx* c, const suppy_params* p) {
+    if (!p) return fail(c, SUPPY_EINVAL, "params is NULL");
+    if (!(p->lambda > 0.0 && p->lambda < 2.0))
+        return fail(c, SUPPY_EINVAL, "lambda must lie in (0, 2)");
+    if (!(p->alpha > 0.0 && p->alpha <= 1.0) || !(p->gamma >= 0.0))
+        return fail(c, SUPPY_EINVAL, "need gamma >= 0 and 0 < alpha <= 1");
+    if (p->n_red < 0 || p->max_trials < 0 || p->max_sweeps < 0 || p->patience < 0 ||
+        p->restart_every < 0)
+        return fail(c, SUPPY_EINVAL, "negative count in params");
+    return SUPPY_OK;
+}
+
+suppy_status read_flags(suppy_ctx* c, int* d_flags, int* h_flags, int count) {
+    CK(cudaMemcpyAsync(h_flags, d_flags, sizeof(int) * count, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+// Choose rows-per-group and registers-held chunks from the row-length mix.
+void choose_shape(suppy_ctx* c, double mean_len, int max_len) {
+    if (c->B > 1) {
+        c->G = 32;
+        c->maxch = 0;
+        return;
+    }
+    if (mean_len >= 192) c->G = 32;
+    else if (mean_len >= 64) c->G = 16;
+    else if (mean_len >= 20) c->G = 8;
+    else c->G = 4;
+    const int per = 4 * c->G;
+    int need = (max_len + per - 1) / per;
+    if (c->G == 32) c->maxch = need <= 2 ? 2 : (need <= 4 ? 4 : 8);
+    else if (c->G == 4) c->maxch = 2;
+    else c->maxch = need <= 2 ? 2 : 4;
+}
+
+suppy_status build_partition(suppy_ctx* c, const std::vector<long long>& pref) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    int bps = sweep_blocks_per_sm(c->dt, c->G, c->maxch, c->B);
+    if (bps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the chosen sweep shape");
+    c->grid_sweep = sms * bps;
+    const int gpc = (c->B > 1) ? kSweepThreads / 32 : kSweepThreads / c->G;
+    c->groups = c->grid_sweep * gpc;
+    std::vector<int> part((size_t)c->nseg * (c->groups + 1));
+    for (int t = 0; t < c->nseg; ++t)
+        partition(pref, c->seg_start[t], c->seg_start[t + 1], c->groups,
+                  part.data() + (size_t)t * (c->groups + 1));
+    if (c->d_part) dfree(c, c->d_part);
+    c->d_part = nullptr;
+    suppy_status s = dalloc(c, &c->d_part, part.size());
+    if (s != SUPPY_OK) return s;
+    CK(cudaMemcpyAsync(c->d_part, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (c->d_pp) dfree(c, c->d_pp);
+    c->d_pp = nullptr;
+    s = dalloc(c, &c->d_pp, (size_t)c->grid_sweep * c->B);
+    if (s != SUPPY_OK) return s;
+    long long vec4 = ((long long)c->n * c->B + 3) / 4;
+    c->grid_fin = (int)std::min<long long>(std::max<long long>((vec4 + 255) / 256, 1), sms * 8LL);
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, const float* box_lo,
+                         const float* box_hi, const suppy_opts* o, void* stream, suppy_ctx* c) {
+    if (!A || !l || !u || !box_lo || !box_hi || !o)
+        return fail(c, SUPPY_EINVAL, "NULL argument to suppy_create");
+    if (A->m < 0 || A->n < 1 || A->nnz < 0 || !A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
+        return fail(c, SUPPY_EINVAL, "bad CSR shape or pointers");
+    if (A->nnz >= (1LL << 31)) return fail(c, SUPPY_EINVAL, "nnz must be below 2^31");
+    c->m = A->m;
+    c->n = A->n;
+    c->nnz = A->nnz;
+    c->dt = o->a_dtype;
+    if (c->dt != SUPPY_F32 && c->dt != SUPPY_BF16 && c->dt != SUPPY_F16)
+        return fail(c, SUPPY_EINVAL, "unknown a_dtype");
+    c->mode = o->mode;
+    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP) return fail(c, SUPPY_EINVAL, "unknown mode");
+    c->obj = o->obj;
+    if ((int)c->obj < 0 || (int)c->obj > 3) return fail(c, SUPPY_EINVAL, "unknown objective");
+    c->B_user = o->nrhs <= 0 ? 1 : o->nrhs;
+    if (c->B_user > kMaxRhs) return fail(c, SUPPY_EINVAL, "nrhs must be at most 32");
+    c->B = 1;
+    if (c->B_user > 1) {
+        c->B = 4;
+        while (c->B < c->B_user) c->B *= 2;
+    }
+    c->box_len = (int)o->box_len;
+    if (o->box_len != 1 && o->box_len != (int64_t)A->n)
+        return fail(c, SUPPY_EINVAL, "box_len must be 1 or n");
+    if (c->obj == SUPPY_OBJ_TV_ISO || c->obj == SUPPY_OBJ_TV_ANISO) {
+        if (o->img_h < 1 || o->img_w < 1 || (long long)o->img_h * o->img_w != A->n)
+            return fail(c, SUPPY_EINVAL, "TV objectives need img_h * img_w == n");
+        c->H = o->img_h;
+        c->W = o->img_w;
+    } else {
+        c->H = 1;
+        c->W = A->n;
+    }
+    if (c->obj == SUPPY_OBJ_LINEAR && !o->c_lin && !o->obj_rows)
+        return fail(c, SUPPY_EINVAL, "linear objective needs c_lin or obj_rows");
+    c->stream = static_cast<cudaStream_t>(stream);
+    CK(cudaGetDevice(&c->dev));
+    const int on_dev = A->on_device ? 1 : 0;
+    const int m = c->m, n = c->n;
+
+    // ---- host copy of row_ptr (partition, padding) and block structure
+    std::vector<int> rp(m + 1);
+    if (on_dev) {
+        CK(cudaMemcpyAsync(rp.data(), A->row_ptr, sizeof(int) * (m + 1), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(rp.data(), A->row_ptr, sizeof(int) * (m + 1));
+    }
+    if (rp[0] != 0 || (long long)rp[m] != A->nnz)
+        return fail(c, SUPPY_EINVAL, "row_ptr[0] must be 0 and row_ptr[m] must equal nnz");
+    for (int i = 0; i < m; ++i)
+        if (rp[i + 1] < rp[i]) return fail(c, SUPPY_EINVAL, "row_ptr must be nondecreasing");
+
+    std::vector<int> perm;   // device row -> source row
+    std::vector<int> seg_of_row;
+    if (c->mode == SUPPY_BIP) {
+        if (!o->block_of_row || o->nblocks < 1)
+            return fail(c, SUPPY_EINVAL, "block-iterative mode needs block_of_row and nblocks >= 1");
+        c->nseg = o->nblocks;
+        std::vector<int> cnt(c->nseg + 1, 0);
+        for (int i = 0; i < m; ++i) {
+            const int t = o->block_of_row[i];
+            if (t < 0 || t >= c->nseg) return fail(c, SUPPY_EINVAL, "block id out of range");
+            cnt[t + 1]++;
+        }
+        for (int t = 0; t < c->nseg; ++t) cnt[t + 1] += cnt[t];
+        c->seg_start.assign(cnt.begin(), cnt.end());
+        perm.resize(m);
+        seg_of_row.resize(m);
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        for (int i = 0; i < m; ++i) {
+            const int t = o->block_of_row[i];
+            perm[pos[t]] = i;
+            seg_of_row[pos[t]] = t;
+            pos[t]++;
+        }
+    } else {
+        c->nseg = 1;
+        c->seg_start = {0, m};
+    }
+
+    // padded row layout in device order
+    std::vector<int2> rinfo(m);
+    std::vector<long long> pref(m + 1, 0);
+    long long off = 0;
+    int max_len = 0;
+    for (int i = 0; i < m; ++i) {
+        const int src = perm.empty() ? i : perm[i];
+        const int len = rp[src + 1] - rp[src];
+        const int padded = (len + 3) & ~3;
+        rinfo[i] = make_int2((int)off, len);
+        off += padded;
+        pref[i + 1] = off;
+        max_len = std::max(max_len, len);
+    }
+    if (off >= (1LL << 31)) return fail(c, SUPPY_EINVAL, "padded nnz must be below 2^31");
+    c->nnz_pad = off;
+
+    TempGuard tg;
+    tg.s = c->stream;
+    int *s_rp = nullptr, *s_col = nullptr;
+    float *s_val = nullptr, *s_l = nullptr, *s_u = nullptr, *s_lo = nullptr, *s_hi = nullptr;
+    suppy_status s;
+    const size_t mB = (size_t)m * c->B_user;
+    if ((s = stage(c, A->row_ptr, (size_t)m + 1, on_dev, &s_rp, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, A->col, (size_t)A->nnz, on_dev, &s_col, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, A->val, (size_t)A->nnz, on_dev, &s_val, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, l, mB, on_dev, &s_l, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, u, mB, on_dev, &s_u, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, box_lo, (size_t)c->box_len, on_dev, &s_lo, tg.v)) != SUPPY_OK) return s;
+    if ((s = stage(c, box_hi, (size_t)c->box_len, on_dev, &s_hi, tg.v)) != SUPPY_OK) return s;
+
+    // ---- validation on the device
+    int* d_flags = nullptr;
+    if ((s = dalloc(c, &d_flags, 8)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(d_flags, 0, 8 * sizeof(int), c->stream));
+    CK(launch_validate_csr(s_rp, s_col, s_val, m, n, A->nnz, d_flags, c->stream));
+    CK(launch_validate_vec(s_l, (long long)mB, 1, d_flags + 1, 1, c->stream));
+    CK(launch_validate_vec(s_u, (long long)mB, 1, d_flags + 1, 2, c->stream));
+    CK(launch_validate_pair(s_l, s_u, (long long)mB, d_flags + 1, 4, c->stream));
+    CK(launch_validate_vec(s_lo, c->box_len, 1, d_flags + 2, 1, c->stream));
+    CK(launch_validate_vec(s_hi, c->box_len, 1, d_flags + 2, 2, c->stream));
+    CK(launch_validate_pair(s_lo, s_hi, c->box_len, d_flags + 2, 4, c->stream));
+    note_launch(c, 7);
+    int hf[8];
+    if ((s = read_flags(c, d_flags, hf, 3)) != SUPPY_OK) return s;
+    if (hf[0] & 1) return fail(c, SUPPY_EINVAL, "row_ptr is not a valid CSR row pointer");
+    if (hf[0] & 2) return fail(c, SUPPY_EINVAL, "column index outside [0, n)");
+    if (hf[0] & 4) return fail(c, SUPPY_EINVAL, "matrix value is NaN or infinite");
+    if (hf[1] & 3) return fail(c, SUPPY_EINVAL, "NaN in the slab bounds l or u");
+    if (hf[1] & 4) return fail(c, SUPPY_EINVAL, "slab bounds need l <= u");
+    if (hf[2] & 3) return fail(c, SUPPY_EINVAL, "NaN in the box bounds");
+    if (hf[2] & 4) return fail(c, SUPPY_EINVAL, "box bounds need lo <= hi");
+
+    // ---- packed matrix, row norms, weights
+    const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
+    if ((s = dalloc(c, &c->d_rinfo, (size_t)m)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz_pad + 16)) != SUPPY_OK) return s;
+    {
+        char* q = nullptr;
+        if ((s = dalloc(c, &q, ((size_t)c->nnz_pad + 16) * vsz)) != SUPPY_OK) return s;
+        c->d_val = q;
+    }
+    if ((s = dalloc(c, &c->d_rho, (size_t)m)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_wr, (size_t)m)) != SUPPY_OK) return s;
+    if (m) CK(cudaMemcpyAsync(c->d_rinfo, rinfo.data(), sizeof(int2) * m, cudaMemcpyHostToDevice,
+                              c->stream));
+    int* d_perm_tmp = nullptr;
+    int* d_seg = nullptr;
+    if (!perm.empty()) {
+        if ((s = dalloc(c, &c->d_perm, (size_t)m)) != SUPPY_OK) return s;
+        CK(cudaMemcpyAsync(c->d_perm, perm.data(), sizeof(int) * m, cudaMemcpyHostToDevice,
+                           c->stream));
+        if ((s = stage(c, seg_of_row.data(), (size_t)m, 0, &d_seg, tg.v)) != SUPPY_OK) return s;
+        d_perm_tmp = c->d_perm;
+    }
+    CK(launch_pack(s_rp, s_col, s_val, d_perm_tmp, c->d_rinfo, m, c->d_col, c->d_val, c->dt,
+                   c->d_rho, c->stream));
+    int* d_kept = nullptr;
+    std::vector<int> zeros(c->nseg, 0);
+    if ((s = stage(c, zeros.data(), zeros.size(), 0, &d_kept, tg.v)) != SUPPY_OK) return s;
+    CK(launch_count_kept(c->d_rho, d_seg, m, d_kept, c->stream));
+    c->seg_kept.assign(c->nseg, 0);
+    CK(cudaMemcpyAsync(c->seg_kept.data(), d_kept, sizeof(int) * c->nseg, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    note_launch(c, 2);
+    c->m_kept = 0;
+    for (int t = 0; t < c->nseg; ++t) c->m_kept += c->seg_kept[t];
+    std::vector<double> segw(c->nseg, 0.0);
+    for (int t = 0; t < c->nseg; ++t) {
+        const int k = (c->mode == SUPPY_BIP) ? c->seg_kept[t] : c->m_kept;
+        segw[t] = k > 0 ? 1.0 / k : 0.0;
+    }
+    double* d_segw = nullptr;
+    if ((s = stage(c, segw.data(), segw.size(), 0, &d_segw, tg.v)) != SUPPY_OK) return s;
+    CK(launch_weights(c->d_rho, d_seg, d_segw, m, c->d_wr, c->stream));
+
+    // ---- bounds (device order, padded right-hand sides) and box
+    if ((s = dalloc(c, &c->d_l, (size_t)m * c->B)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_u, (size_t)m * c->B)) != SUPPY_OK) return s;
+    CK(launch_permute_bounds(s_l, s_u, c->d_perm, m, c->B_user, c->B, c->d_l, c->d_u, c->stream));
+    CK(cudaMemsetAsync(d_flags + 3, 0, sizeof(int), c->stream));
+    CK(launch_zero_row_check(c->d_rho, c->d_l, c->d_u, m, c->B, d_flags + 3, c->stream));
+    note_launch(c, 3);
+    if ((s = read_flags(c, d_flags + 3, hf + 3, 1)) != SUPPY_OK) return s;
+    if (hf[3]) return fail(c, SUPPY_EINVAL, "a zero row needs l <= 0 <= u");
+    if ((s = dalloc(c, &c->d_lo, (size_t)c->box_len)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_hi, (size_t)c->box_len)) != SUPPY_OK) return s;
+    CK(cudaMemcpyAsync(c->d_lo, s_lo, sizeof(float) * c->box_len, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_hi, s_hi, sizeof(float) * c->box_len, cudaMemcpyDeviceToDevice, c->stream));
+
+    // ---- iterate, correction, scratch, state
+    const size_t nB = (size_t)n * c->B;
+    if ((s = dalloc(c, &c->d_x, nB)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_delta, nB)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_delta, 0, nB * sizeof(float), c->stream));
+    CK(launch_box_init(c->d_x, c->d_lo, c->d_hi, (long long)nB, c->B, c->box_len, nullptr, 0,
+                       c->stream));
+    note_launch(c);
+    if (c->obj != SUPPY_OBJ_NONE) {
+        if ((s = dalloc(c, &c->d_g, nB)) != SUPPY_OK) return s;
+    }
+    if ((s = dalloc(c, &c->d_st, (size_t)c->B)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_out, (size_t)c->B)) != SUPPY_OK) return s;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    c->grid_obj = std::max(1, std::min(sms * 4, (n + 255) / 256));
+    if ((s = dalloc(c, &c->d_objpart, (size_t)c->grid_obj * c->B)) != SUPPY_OK) return s;
+    CK(cudaMallocHost(&c->h_out, sizeof(double) * kMaxRhs));
+
+    // ---- linear objective vector
+    if (c->obj == SUPPY_OBJ_LINEAR) {
+        if ((s = dalloc(c, &c->d_c64, (size_t)n)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_c32, (size_t)n)) != SUPPY_OK) return s;
+        if (o->obj_rows) {
+            const suppy_csr* S = o->obj_rows;
+            if (S->n != n || S->m < 1 || S->nnz < 0 || !S->row_ptr)
+                return fail(c, SUPPY_EINVAL, "obj_rows must have n columns and at least one row");
+            int *q_rp = nullptr, *q_col = nullptr;
+            float* q_val = nullptr;
+            const int sd = S->on_device ? 1 : 0;
+            if ((s = stage(c, S->row_ptr, (size_t)S->m + 1, sd, &q_rp, tg.v)) != SUPPY_OK) return s;
+            if ((s = stage(c, S->col, (size_t)S->nnz, sd, &q_col, tg.v)) != SUPPY_OK) return s;
+            if ((s = stage(c, S->val, (size_t)S->nnz, sd, &q_val, tg.v)) != SUPPY_OK) return s;
+            CK(cudaMemsetAsync(d_flags + 4, 0, sizeof(int), c->stream));
+            CK(launch_validate_csr(q_rp, q_col, q_val, S->m, n, S->nnz, d_flags + 4, c->stream));
+            if ((s = read_flags(c, d_flags + 4, hf + 4, 1)) != SUPPY_OK) return s;
+            if (hf[4]) return fail(c, SUPPY_EINVAL, "obj_rows is not a valid CSR matrix");
+            const int slices = std::max(1, std::min(512, S->m / 64));
+            void* wq = nullptr;
+            CK(cudaMalloc(&wq, sizeof(double) * (size_t)slices * n));
+            tg.v.push_back(wq);
+            double* work = static_cast<double*>(wq);
+            CK(launch_colmean(q_rp, q_col, q_val, S->m, n, c->d_c64, c->d_c32, work, slices,
+                              c->stream));
+            note_launch(c, 3);
+        } else {
+            std::vector<float> hc(n);
+            if (on_dev) {
+                CK(cudaMemcpyAsync(hc.data(), o->c_lin, sizeof(float) * n, cudaMemcpyDeviceToHost,
+                                   c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+            } else {
+                std::memcpy(hc.data(), o->c_lin, sizeof(float) * n);
+            }
+            std::vector<double> hd(hc.begin(), hc.end());
+            for (double v : hd)
+                if (!std::isfinite(v)) return fail(c, SUPPY_EINVAL, "c_lin must be finite");
+            CK(cudaMemcpyAsync(c->d_c32, hc.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->d_c64, hd.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+        }
+    }
+
+    // ---- launch shape and partition
+    const double mean_len = m > 0 ? (double)A->nnz / m : 0.0;
+    choose_shape(c, mean_len, max_len);
+    if ((s = build_partition(c, pref)) != SUPPY_OK) return s;
+    c->perturb_cluster = fit_perturb_cluster(choose_perturb_cluster(n, c->B));
+    if ((s = ensure_hist(c, 1024)) != SUPPY_OK) return s;
+    if ((s = reset_state(c)) != SUPPY_OK) return s;
+    dfree(c, d_flags);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    return SUPPY_OK;
+}
+
+void destroy_impl(suppy_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& pr : c->evs) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_out) cudaFreeHost(c->h_out);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void suppy_params_default(suppy_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->lambda = 1.0;
+    p->gamma = 0.5;
+    p->alpha = 0.99;
+    p->n_red = 1;
+    p->max_trials = 100;
+    p->restart_every = 0;
+    p->max_sweeps = 500;
+    p->check_every = 10;
+    p->prox_abs = 1e-6;
+    p->prox_rel = 1e-8;
+    p->obj_rel = 1e-6;
+    p->patience = 5;
+    p->use_stopping = 0;
+    p->use_graphs = 0;
+}
+
+suppy_status suppy_create(const suppy_csr* A, const float* l, const float* u,
+                          const float* box_lo, const float* box_hi, const suppy_opts* opts,
+                          void* stream, suppy_ctx** out) {
+    if (!out) return fail(nullptr, SUPPY_EINVAL, "out is NULL");
+    *out = nullptr;
+    suppy_ctx* c = new (std::nothrow) suppy_ctx();
+    if (!c) return fail(nullptr, SUPPY_ENOMEM, "host allocation failed");
+    suppy_status s = create_impl(A, l, u, box_lo, box_hi, opts, stream, c);
+    if (s != SUPPY_OK) {
+        g_err = c->err;
+        destroy_impl(c);
+        return s;
+    }
+    *out = c;
+    return SUPPY_OK;
+}
+
+void suppy_destroy(suppy_ctx* c) { destroy_impl(c); }
+
+suppy_status suppy_set_stream(suppy_ctx* c, void* stream) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    c->stream = static_cast<cudaStream_t>(stream);
+    return SUPPY_OK;
+}
+
+suppy_status suppy_set_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!l || !u) return fail(c, SUPPY_EINVAL, "NULL bounds");
+    const size_t mB = (size_t)c->m * c->B_user;
+    suppy_status s;
+    const float *s_l = l, *s_u = u;
+    if (!on_device) {
+        if (!c->d_stage_l) {
+            if ((s = dalloc(c, &c->d_stage_l, mB)) != SUPPY_OK) return s;
+            if ((s = dalloc(c, &c->d_stage_u, mB)) != SUPPY_OK) return s;
+        }
+        CK(cudaMemcpyAsync(c->d_stage_l, l, mB * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->d_stage_u, u, mB * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        s_l = c->d_stage_l;
+        s_u = c->d_stage_u;
+    }
+    if (!c->d_flags && (s = dalloc(c, &c->d_flags, 4)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(int), c->stream));
+    CK(launch_validate_vec(s_l, (long long)mB, 1, c->d_flags, 1, c->stream));
+    CK(launch_validate_vec(s_u, (long long)mB, 1, c->d_flags, 2, c->stream));
+    CK(launch_validate_pair(s_l, s_u, (long long)mB, c->d_flags, 4, c->stream));
+    int hf[2] = {0, 0};
+    if ((s = read_flags(c, c->d_flags, hf, 1)) != SUPPY_OK) return s;
+    note_launch(c, 3);
+    if (hf[0]) return fail(c, SUPPY_EINVAL, "bounds need l <= u and no NaN");
+    CK(launch_permute_bounds(s_l, s_u, c->d_perm, c->m, c->B_user, c->B, c->d_l, c->d_u, c->stream));
+    CK(launch_zero_row_check(c->d_rho, c->d_l, c->d_u, c->m, c->B, c->d_flags + 1, c->stream));
+    note_launch(c, 2);
+    if ((s = read_flags(c, c->d_flags + 1, hf + 1, 1)) != SUPPY_OK) return s;
+    if (hf[1]) return fail(c, SUPPY_EINVAL, "a zero row needs l <= 0 <= u");
+    return reset_state(c);
+}
+
+suppy_status suppy_set_x(suppy_ctx* c, const float* x, int32_t on_device) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!x) return fail(c, SUPPY_EINVAL, "x is NULL");
+    TempGuard tg;
+    tg.s = c->stream;
+    float* s_x = nullptr;
+    suppy_status s;
+    if ((s = stage(c, x, (size_t)c->n * c->B_user, on_device, &s_x, tg.v)) != SUPPY_OK) return s;
+    CK(launch_box_init(c->d_x, c->d_lo, c->d_hi, (long long)c->n * c->B, c->B, c->box_len, s_x,
+                       c->B_user, c->stream));
+    note_launch(c);
+    return reset_state(c);
+}
+
+suppy_status suppy_get_x(suppy_ctx* c, float* x, int32_t on_device) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!x) return fail(c, SUPPY_EINVAL, "x is NULL");
+    const size_t cnt = (size_t)c->n * c->B_user;
+    if (c->B == c->B_user) {
+        CK(cudaMemcpyAsync(x, c->d_x, cnt * sizeof(float),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        TempGuard tg;
+        tg.s = c->stream;
+        float* tmp = x;
+        if (!on_device) {
+            void* q = nullptr;
+            CK(cudaMalloc(&q, cnt * sizeof(float)));
+            tg.v.push_back(q);
+            tmp = static_cast<float*>(q);
+        }
+        CK(launch_unpad_x(c->d_x, c->n, c->B, c->B_user, tmp, c->stream));
+        note_launch(c);
+        if (!on_device)
+            CK(cudaMemcpyAsync(x, tmp, cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status suppy_perturb(suppy_ctx* c, const suppy_params* p, int32_t* accepted) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (c->obj == SUPPY_OBJ_NONE) return fail(c, SUPPY_ESTATE, "the context has no objective");
+    suppy_status s = check_params(c, p);
+    if (s != SUPPY_OK) return s;
+    if ((s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
+    if (accepted) {
+        std::vector<RhsState> st(c->B);
+        CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int b = 0; b < c->B_user; ++b) accepted[b] = st[b].stopped ? 0 : st[b].accepted_last;
+    }
+    return SUPPY_OK;
+}
+
+suppy_status suppy_sweep(suppy_ctx* c, const suppy_params* p, int32_t nsweeps) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    suppy_status s = check_params(c, p);
+    if (s != SUPPY_OK) return s;
+    if (nsweeps < 0) return fail(c, SUPPY_EINVAL, "nsweeps < 0");
+    if ((s = ensure_hist(c, c->k_upper + nsweeps)) != SUPPY_OK) return s;
+    for (int k = 0; k < nsweeps; ++k)
+        if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
+    return SUPPY_OK;
+}
+
+suppy_status suppy_proximity(suppy_ctx* c, double* out) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
+    for (int t = 0; t < c->nseg; ++t) {
+        SweepArgs a;
+        a.rinfo = c->d_rinfo;
+        a.col = c->d_col;
+        a.val = c->d_val;
+        a.l = c->d_l;
+        a.u = c->d_u;
+        a.wr = c->d_wr;
+        a.x = c->d_x;
+        a.delta = c->d_delta;
+        a.part = c->d_part + (size_t)t * (c->groups + 1);
+        a.pp = c->d_pp;
+        a.st = c->d_st;
+        a.lam = 0.f;
+        a.B = c->B;
+        a.scatter = 0;
+        a.check_stop = 0;
+        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxch, c->grid_sweep, c->stream));
+        else CK(launch_sweep_batched(a, c->dt, 32, c->grid_sweep, c->stream));
+        double scale = 0.5;
+        if (c->nseg > 1) scale = c->m_kept > 0 ? 0.5 * (double)c->seg_kept[t] / c->m_kept : 0.0;
+        CK(launch_reduce_pp(c->d_pp, c->grid_sweep, c->B, scale, t > 0, c->d_out, c->stream));
+        note_launch(c, 2);
+    }
+    CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, c->h_out, sizeof(double) * c->B_user);
+    return SUPPY_OK;
+}
+
+suppy_status suppy_objective(suppy_ctx* c, double* out) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
+    if (c->obj == SUPPY_OBJ_NONE) return fail(c, SUPPY_ESTATE, "the context has no objective");
+    ObjArgs a;
+    a.x = c->d_x;
+    a.c64 = c->d_c64;
+    a.n = c->n;
+    a.B = c->B;
+    a.H = c->H;
+    a.W = c->W;
+    a.obj = (int)c->obj;
+    a.partial = c->d_objpart;
+    CK(launch_objective(a, c->grid_obj, c->d_out, c->stream));
+    note_launch(c, 2);
+    CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    std::memcpy(out, c->h_out, sizeof(double) * c->B_user);
+    return SUPPY_OK;
+}
+
+suppy_status suppy_run(suppy_ctx* c, const suppy_params* p, suppy_stats* out) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    suppy_status s = check_params(c, p);
+    if (s != SUPPY_OK) return s;
+    std::vector<RhsState> st(c->B);
+    if ((s = ensure_hist(c, c->k_upper + p->max_sweeps)) != SUPPY_OK) return s;
+    const int chunk = p->use_stopping ? std::max(1, p->check_every) : std::max(1, p->max_sweeps);
+    int done = 0;
+    while (done < p->max_sweeps) {
+        const int todo = std::min(chunk, p->max_sweeps - done);
+        for (int k = 0; k < todo; ++k) {
+            if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
+            if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
+        }
+        done += todo;
+        if (p->use_stopping && done < p->max_sweeps) {
+            CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            bool all = true;
+            for (int b = 0; b < c->B_user; ++b) all = all && st[b].stopped;
+            if (all) break;
+        }
+    }
+    if (out) {
+        CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int b = 0; b < c->B_user; ++b) {
+            out[b].sweeps = st[b].k;
+            out[b].accepted = st[b].accepted_total;
+            out[b].trials = st[b].trials_total;
+            out[b].stopped = st[b].stopped;
+            out[b].ell = st[b].ell;
+            out[b].proximity = st[b].last_prox;
+            out[b].objective = st[b].f_prev;
+        }
+    }
+    return SUPPY_OK;
+}
+
+suppy_status suppy_history(suppy_ctx* c, int32_t rhs, double* prox, double* obj, int32_t cap,
+                           int32_t* count) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (rhs < 0 || rhs >= c->B_user) return fail(c, SUPPY_EINVAL, "rhs out of range");
+    RhsState st;
+    CK(cudaMemcpyAsync(&st, c->d_st + rhs, sizeof(RhsState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int k = std::min(st.k, c->hist_cap);
+    const int cp = std::max(0, std::min(cap, k));
+    if (prox && cp)
+        CK(cudaMemcpyAsync(prox, c->d_prox_hist + (size_t)rhs * c->hist_cap, sizeof(double) * cp,
+                           cudaMemcpyDeviceToHost, c->stream));
+    if (obj && cp)
+        CK(cudaMemcpyAsync(obj, c->d_obj_hist + (size_t)rhs * c->hist_cap, sizeof(double) * cp,
+                           cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (count) *count = st.k;
+    return SUPPY_OK;
+}
+
+namespace {
+struct CkptHeader {
+    uint64_t magic;
+    int32_t version, n, m, B;
+};
+constexpr uint64_t kMagic = 0x5355505059434b31ULL;   // "SUPPYCK1"
+}  // namespace
+
+suppy_status suppy_get_state(suppy_ctx* c, void* buf, size_t* len) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!len) return fail(c, SUPPY_EINVAL, "len is NULL");
+    const size_t need = sizeof(CkptHeader) + sizeof(float) * (size_t)c->n * c->B +
+                        sizeof(RhsState) * c->B;
+    if (!buf) {
+        *len = need;
+        return SUPPY_OK;
+    }
+    if (*len < need) return fail(c, SUPPY_EINVAL, "checkpoint buffer too small");
+    char* q = static_cast<char*>(buf);
+    CkptHeader h{kMagic, 1, c->n, c->m, c->B};
+    std::memcpy(q, &h, sizeof(h));
+    CK(cudaMemcpyAsync(q + sizeof(h), c->d_x, sizeof(float) * (size_t)c->n * c->B,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(q + sizeof(h) + sizeof(float) * (size_t)c->n * c->B, c->d_st,
+                       sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *len = need;
+    return SUPPY_OK;
+}
+
+suppy_status suppy_set_state(suppy_ctx* c, const void* buf, size_t len) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!buf) return fail(c, SUPPY_EINVAL, "buf is NULL");
+    const size_t need = sizeof(CkptHeader) + sizeof(float) * (size_t)c->n * c->B +
+                        sizeof(RhsState) * c->B;
+    if (len < need) return fail(c, SUPPY_EINVAL, "checkpoint too short");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kMagic || h.version != 1 || h.n != c->n || h.m != c->m || h.B != c->B)
+        return fail(c, SUPPY_EINVAL, "checkpoint does not match this context");
+    const char* q = static_cast<const char*>(buf);
+    CK(cudaMemcpyAsync(c->d_x, q + sizeof(h), sizeof(float) * (size_t)c->n * c->B,
+                       cudaMemcpyHostToDevice, c->stream));
+    const RhsState* rs = reinterpret_cast<const RhsState*>(q + sizeof(h) + sizeof(float) * (size_t)c->n * c->B);
+    std::vector<RhsState> st(rs, rs + c->B);
+    c->k_upper = 0;
+    for (auto& r : st) c->k_upper = std::max(c->k_upper, r.k);
+    CK(cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
+    suppy_ctx* c = const_cast<suppy_ctx*>(cc);
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
+    out->m = c->m;
+    out->n = c->n;
+    out->nrhs = c->B_user;
+    out->m_kept = c->m_kept;
+    out->nnz = c->nnz;
+    out->nnz_padded = c->nnz_pad;
+    out->nblocks = c->nseg;
+    out->lanes_per_row = c->G;
+    out->chunks_in_regs = c->maxch;
+    out->grid = c->grid_sweep;
+    out->block = kSweepThreads;
+    out->perturb_cluster = c->perturb_cluster;
+    out->device_bytes = (int64_t)c->dev_bytes;
+    return SUPPY_OK;
+}
+
+suppy_status suppy_timing_enable(suppy_ctx* c, int32_t enable) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    suppy_status s = flush_timing(c);
+    if (s != SUPPY_OK) return s;
+    c->timing = enable != 0;
+    c->timing_ms = 0.0;
+    c->timing_n = 0;
+    return SUPPY_OK;
+}
+
+suppy_status suppy_kernel_time(suppy_ctx* c, double* total_ms, int64_t* launches) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    suppy_status s = flush_timing(c);
+    if (s != SUPPY_OK) return s;
+    if (total_ms) *total_ms = c->timing_ms;
+    if (launches) *launches = c->timing_n;
+    return SUPPY_OK;
+}
+
+int64_t suppy_launch_count(const suppy_ctx* c) { return c ? c->launches : 0; }
+
+const char* suppy_last_error(const suppy_ctx* c) {
+    return c ? c->err.c_str() : g_err.c_str();
+}
+
+const char* suppy_version(void) { return "suppy-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Shared declarations of the suppy GB300 library (device structs, launch
+// entry points between translation units, small device helpers).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "suppy.h"
+
+namespace suppy {
+
+constexpr int kSweepThreads = 256;     // threads per CTA of the sweep kernels
+constexpr int kFinalizeThreads = 256;
+constexpr int kPerturbThreads = 512;   // threads per CTA of the perturbation cluster
+constexpr int kMaxRhs = 32;
+
+// Per right-hand-side iteration state, resident on the device so that the
+// perturbation, sweep and stopping logic never wait for the host.
+struct RhsState {
+    long long ell;          // power-law exponent l of beta = gamma * alpha^l
+    int restarts;           // restarts applied so far
+    int last_restart_k;     // sweep index of the last restart (-1: none)
+    int k;                  // sweeps applied
+    int stopped;            // stopping rule fired (or padding RHS)
+    int calm;               // consecutive sweeps with small relative proximity change
+    int accepted_total, trials_total;
+    int accepted_last, trials_last;
+    int has_prev_p, has_prev_f, f_valid;
+    int pad0;
+    double p_prev, f_prev, f_cur;
+    double p_acc;           // running monitored proximity within a block-iterative sweep
+    double last_prox;
+};
+
+struct StopParams {
+    double prox_abs, prox_rel, obj_rel;
+    int patience;
+    int use_stopping;
+    int has_obj;
+};
+
+// One launch of the fused sweep over rows [part[0], part[ngroups]).
+struct SweepArgs {
+    const int2* rinfo;      // per row: {padded start, length}
+    const int* col;         // padded column indices
+    const void* val;        // padded values (float / bf16 / half)
+    const float* l;         // m x B bounds (device row order)
+    const float* u;
+    const float* wr;        // w_i / ||a_i||^2 (0 for dropped rows)
+    const float* x;         // n x B iterate (read only during the sweep)
+    float* delta;           // n x B correction accumulator (zero on entry)
+    const int* part;        // group boundaries (ngroups + 1 absolute row indices)
+    double* pp;             // proximity partials: pp[cta * B + b]
+    RhsState* st;
+    float lam;
+    int B;                  // right-hand sides in the device layout
+    int scatter;            // 0: proximity only (no correction)
+    int check_stop;         // 1: skip the launch when right-hand side 0 has stopped (B = 1)
+};
+
+struct FinalizeArgs {
+    float* x;
+    float* delta;
+    const float* lo;
+    const float* hi;
+    long long nB;           // n * B elements
+    int B;
+    int box_len;            // 1 or n
+    const double* pp;
+    int npp;                // CTAs that wrote partials
+    double scale;           // factor applied to the partial sums (1/2 and block weight ratio)
+    RhsState* st;
+    double* prox_hist;      // [B][hist_cap]
+    double* obj_hist;
+    int hist_cap;
+    int first_seg, last_seg;
+    StopParams sp;
+};
+
+struct PerturbArgs {
+    float* x;               // n x B
+    float* g;               // n x B scratch for the subgradient
+    const float* c32;       // linear objective (FP32) or null
+    const double* c64;      // linear objective (FP64) or null
+    int n, B, H, W, obj;
+    double gamma, alpha;
+    int n_red, max_trials, restart_every;
+    RhsState* st;
+    int record_only;        // 1: compute f(x) into st->f_cur only (no step)
+};
+
+struct ObjArgs {
+    const float* x;
+    const double* c64;
+    int n, B, H, W, obj;
+    double* partial;        // [cta][B]
+};
+
+// --- launchers (defined in sweep.cu / perturb.cu / setup.cu) ---------------
+cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxch, int grid,
+                         cudaStream_t s);
+cudaError_t launch_sweep_batched(const SweepArgs& a, suppy_dtype dt, int G, int grid,
+                                 cudaStream_t s);
+int sweep_blocks_per_sm(suppy_dtype dt, int G, int maxch, int batchedB);
+cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
+                             double* out, cudaStream_t s);
+cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s);
+int choose_perturb_cluster(int n, int B);
+int fit_perturb_cluster(int want);
+cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s);
+
+cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,
+                                int n, long long nnz, int* flags, cudaStream_t s);
+cudaError_t launch_validate_vec(const float* v, long long len, int allow_inf, int* flags,
+                                int bit, cudaStream_t s);
+cudaError_t launch_validate_pair(const float* lo, const float* hi, long long len, int* flags,
+                                 int bit, cudaStream_t s);
+cudaError_t launch_pack(const int* row_ptr, const int* col, const float* val, const int* perm,
+                        const int2* rinfo, int m, int* pcol, void* pval, suppy_dtype dt,
+                        double* rho, cudaStream_t s);
+cudaError_t launch_count_kept(const double* rho, const int* seg_of_row, int m, int* kept,
+                              cudaStream_t s);
+cudaError_t launch_weights(const double* rho, const int* seg_of_row, const double* seg_w, int m,
+                           float* wr, cudaStream_t s);
+cudaError_t launch_zero_row_check(const double* rho, const float* l, const float* u, int m,
+                                  int B, int* flags, cudaStream_t s);
+cudaError_t launch_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
+                                  int B_in, int B, float* l, float* u, cudaStream_t s);
+cudaError_t launch_box_init(float* x, const float* lo, const float* hi, long long nB, int B,
+                            int box_len, const float* x_in, int B_in, cudaStream_t s);
+cudaError_t launch_unpad_x(const float* x, long long n, int B, int B_out, float* out,
+                           cudaStream_t s);
+cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
+                           double* c64, float* c32, double* work, int work_ctas,
+                           cudaStream_t s);
+cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s);
+
+// --- device helpers ---------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) {
+    return fminf(fmaxf(v, lo), hi);
+}
+
+}  // namespace suppy

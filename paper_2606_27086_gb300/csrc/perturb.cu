@@ -1,0 +1,287 @@
+// Perturbation phase of Algorithm 1 (nonascending subgradient steps with the
+// power-law step size beta = gamma * alpha^l of Sec. 2.1.2) and the objective
+// evaluations it needs: isotropic TV (Eq. (TV)) with the Combettes/Penfold
+// subgradient, anisotropic TV, and the linear mean dose f = c.x (Sec. 2.3.3).
+//
+// One thread-block cluster owns one right-hand side.  Every trial needs a
+// global decision f(z) <= f(y); the cluster makes it without the host: each
+// CTA reduces its FP64 partial in a fixed order, the partials are exchanged
+// through distributed shared memory after a hardware cluster barrier, and
+// every CTA sums them in the same order -- so all CTAs take the same decision
+// and the run is bitwise reproducible.  The trial loop is bounded by
+// max_trials, so the kernel always ends.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace suppy {
+namespace {
+
+// Strided view of right-hand side b of an n x B row-major array.  Reads go
+// through L2 only (ld.global.cg): other CTAs of the cluster rewrite these
+// vectors between the passes of one launch, and L2 is the coherence point.
+struct Vec {
+    float* p;
+    int B;
+    __device__ __forceinline__ float operator()(int j) const { return __ldcg(p + (size_t)j * B); }
+};
+
+// z = y - s * g, the trial point, computed identically wherever it is used.
+__device__ __forceinline__ float trial(float y, float g, float s) { return __fmaf_rn(-s, g, y); }
+
+// Objective term owned by pixel p (FP64 result; TV terms are FP32 then widened).
+template <class Y>
+__device__ __forceinline__ double obj_term(int obj, int p, int H, int W, const double* c64,
+                                           const Y& y) {
+    if (obj == SUPPY_OBJ_LINEAR) return c64[p] * (double)y(p);
+    const int i = p / W, j = p - i * W;
+    const float y0 = y(p);
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        if (i < H - 1 && j < W - 1) {
+            const float dx = y(p + W) - y0, dy = y(p + 1) - y0;
+            return (double)sqrtf(dx * dx + dy * dy);
+        }
+        return 0.0;
+    }
+    float t = 0.f;   // anisotropic
+    if (i < H - 1) t += fabsf(y(p + W) - y0);
+    if (j < W - 1) t += fabsf(y(p + 1) - y0);
+    return (double)t;
+}
+
+__device__ __forceinline__ float sgnf(float v) { return (v > 0.f) ? 1.f : ((v < 0.f) ? -1.f : 0.f); }
+
+// Subgradient component at pixel p (gather form of the term-wise derivatives).
+template <class Y>
+__device__ __forceinline__ float subgrad(int obj, int p, int H, int W, const float* c32,
+                                         const Y& y) {
+    if (obj == SUPPY_OBJ_LINEAR) return c32[p];
+    const int i = p / W, j = p - i * W;
+    const float y0 = y(p);
+    float g = 0.f;
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        // term (i, j): d/dX[i,j] = -(dx + dy) / phi
+        if (i < H - 1 && j < W - 1) {
+            const float dx = y(p + W) - y0, dy = y(p + 1) - y0;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g -= (dx + dy) / phi;
+        }
+        // term (i-1, j): d/dX[i,j] = dx' / phi'  (X[i,j] is its X[i'+1,j])
+        if (i > 0 && j < W - 1) {
+            const float ym = y(p - W);
+            const float dx = y0 - ym, dy = y(p - W + 1) - ym;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g += dx / phi;
+        }
+        // term (i, j-1): d/dX[i,j] = dy'' / phi''  (X[i,j] is its X[i,j'+1])
+        if (j > 0 && i < H - 1) {
+            const float yl = y(p - 1);
+            const float dx = y(p + W - 1) - yl, dy = y0 - yl;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g += dy / phi;
+        }
+        return g;
+    }
+    if (i < H - 1) g -= sgnf(y(p + W) - y0);
+    if (i > 0) g += sgnf(y0 - y(p - W));
+    if (j < W - 1) g -= sgnf(y(p + 1) - y0);
+    if (j > 0) g += sgnf(y0 - y(p - 1));
+    return g;
+}
+
+// Deterministic cluster-wide sum of two FP64 values.
+__device__ double2 cluster_sum2(double a, double b, double2* sw, double2* scta,
+                                cg::cluster_group& cluster) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sw[wid] = make_double2(a, b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int w = 0; w < kPerturbThreads / 32; ++w) {
+            s.x += sw[w].x;
+            s.y += sw[w].y;
+        }
+        *scta = s;
+    }
+    cluster.sync();
+    double2 t = make_double2(0.0, 0.0);
+    const unsigned nr = cluster.num_blocks();
+    for (unsigned r = 0; r < nr; ++r) {
+        const double2 v = *cluster.map_shared_rank(scta, r);
+        t.x += v.x;
+        t.y += v.y;
+    }
+    cluster.sync();   // nobody overwrites scta before every CTA has read it
+    return t;
+}
+
+__global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a) {
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double2 sw[kPerturbThreads / 32];
+    __shared__ double2 scta;
+    const int ncl = (int)cluster.num_blocks();
+    const int b = blockIdx.x / ncl;             // right-hand side of this cluster
+    RhsState& st = a.st[b];
+    if (st.stopped) return;                     // uniform over the cluster
+    const int rank = (int)cluster.block_rank();
+    const int tid = rank * kPerturbThreads + threadIdx.x;
+    const int nthr = ncl * kPerturbThreads;
+    const int n = a.n, H = a.H, W = a.W, obj = a.obj;
+    Vec y{a.x + b, a.B};
+    Vec g{a.g + b, a.B};
+
+    long long ell = st.ell;
+    int restarts = st.restarts, last_restart_k = st.last_restart_k;
+    const int k = st.k;
+    if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
+        last_restart_k != k) {
+        restarts += 1;
+        ell = restarts;
+        last_restart_k = k;
+    }
+    int accepted = 0, trials = 0;
+    double f_start = 0.0;
+    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
+        // pass G: subgradient, ||g||^2 and f(y)
+        double gg = 0.0, fy = 0.0;
+        for (int p = tid; p < n; p += nthr) {
+            fy += obj_term(obj, p, H, W, a.c64, y);
+            if (!a.record_only) {
+                const float gp = subgrad(obj, p, H, W, a.c32, y);
+                __stcg(g.p + (size_t)p * a.B, gp);
+                gg += (double)gp * (double)gp;
+            }
+        }
+        const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
+        gg = r.x;
+        fy = r.y;
+        if (s == 0) f_start = fy;
+        if (a.record_only || gg == 0.0) break;
+        const double gnorm = sqrt(gg);
+        bool ok = false;
+        for (int j = 0; j < a.max_trials; ++j) {
+            const double beta = a.gamma * pow(a.alpha, (double)ell);
+            ell += 1;
+            trials += 1;
+            const float sc = (float)(beta / gnorm);
+            Vec yy = y;
+            Vec gv = g;
+            auto z = [yy, gv, sc](int q) { return trial(yy(q), gv(q), sc); };
+            double fz = 0.0;
+            for (int p = tid; p < n; p += nthr) fz += obj_term(obj, p, H, W, a.c64, z);
+            fz = cluster_sum2(fz, 0.0, sw, &scta, cluster).x;
+            if (fz <= fy) {
+                for (int p = tid; p < n; p += nthr) {
+                    const size_t o = (size_t)p * a.B;
+                    __stcg(y.p + o, trial(__ldcg(y.p + o), __ldcg(g.p + o), sc));
+                }
+                cluster.sync();
+                accepted += 1;
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) break;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        st.f_cur = f_start;
+        st.f_valid = 1;
+        if (!a.record_only) {
+            st.ell = ell;
+            st.restarts = restarts;
+            st.last_restart_k = last_restart_k;
+            st.accepted_last = accepted;
+            st.trials_last = trials;
+            st.accepted_total += accepted;
+            st.trials_total += trials;
+        }
+    }
+}
+
+// Objective partials: CTA c writes f-partials of every right-hand side.
+__global__ void __launch_bounds__(256) k_objective(const ObjArgs a) {
+    __shared__ double sw[8];
+    for (int b = 0; b < a.B; ++b) {
+        Vec y{const_cast<float*>(a.x) + b, a.B};
+        double f = 0.0;
+        for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += gridDim.x * blockDim.x)
+            f += obj_term(a.obj, p, a.H, a.W, a.c64, y);
+        f = warp_sum(f);
+        if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = f;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < 8; ++w) s += sw[w];
+            a.partial[(size_t)blockIdx.x * a.B + b] = s;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int choose_perturb_cluster(int n, int B) {
+    // enough CTAs that each thread owns a handful of pixels; at most 16 (one GPC)
+    int want = (n + kPerturbThreads * 8 - 1) / (kPerturbThreads * 8);
+    int cs = 1;
+    while (cs < want && cs < 16) cs <<= 1;
+    (void)B;
+    return cs;
+}
+
+int fit_perturb_cluster(int want) {
+    // largest power of two <= want for which a cluster can be resident
+    cudaFuncSetAttribute(k_perturb, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs = want; cs >= 1; cs >>= 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cs, 1, 1);
+        cfg.blockDim = dim3(kPerturbThreads, 1, 1);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k_perturb, &cfg) == cudaSuccess && nc > 0)
+            return cs;
+        cudaGetLastError();
+    }
+    return 1;
+}
+
+cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_perturb, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.B * cluster, 1, 1);
+    cfg.blockDim = dim3(kPerturbThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_perturb, a);
+}
+
+cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s) {
+    k_objective<<<grid, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce_pp(a.partial, grid, a.B, 1.0, 0, out, s);
+}
+
+}  // namespace suppy

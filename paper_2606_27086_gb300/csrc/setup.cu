@@ -1,0 +1,319 @@
+// Setup kernels: input validation, packing A into the padded device layout
+// (values converted to the storage dtype), FP64 row norms ||a_i||^2 (the
+// denominator of Eq. (2)), kept-row counts and the weights w_i / ||a_i||^2 of
+// the simultaneous or block-iterative step (Sec. 2.1.1), the zero-row check,
+// bound permutation, the box projection of the initial point and the column
+// means c = S^T 1 / rows(S) of the mean-dose objective (Sec. 2.3.3).
+#include "common.cuh"
+
+namespace suppy {
+namespace {
+
+// flags bits
+constexpr int kBadRowPtr = 1, kBadCol = 2, kBadVal = 4;
+
+__global__ void k_validate_csr(const int* rp, const int* col, const float* val, int m, int n,
+                               long long nnz, int* flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long i = t0; i < m; i += stride) {
+        const int a = rp[i], b = rp[i + 1];
+        if (a > b || a < 0 || (long long)b > nnz) atomicOr(flags, kBadRowPtr);
+    }
+    if (t0 == 0 && (rp[0] != 0 || (long long)rp[m] != nnz)) atomicOr(flags, kBadRowPtr);
+    for (long long e = t0; e < nnz; e += stride) {
+        const int c = col[e];
+        if (c < 0 || c >= n) atomicOr(flags, kBadCol);
+        if (!isfinite(val[e])) atomicOr(flags, kBadVal);
+    }
+}
+
+__global__ void k_validate_vec(const float* v, long long len, int allow_inf, int* flags,
+                               int bit) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float f = v[i];
+        if (isnan(f) || (!allow_inf && isinf(f))) atomicOr(flags, bit);
+    }
+}
+
+__global__ void k_validate_pair(const float* lo, const float* hi, long long len, int* flags,
+                                int bit) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!(lo[i] <= hi[i])) atomicOr(flags, bit);
+    }
+}
+
+template <typename VT>
+__device__ __forceinline__ VT to_store(float v);
+template <>
+__device__ __forceinline__ float to_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_store<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half to_store<__half>(float v) { return __float2half_rn(v); }
+
+template <typename VT>
+__device__ __forceinline__ float from_store(VT v);
+template <>
+__device__ __forceinline__ float from_store<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float from_store<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+template <>
+__device__ __forceinline__ float from_store<__half>(__half v) { return __half2float(v); }
+
+// One warp per device row i (source row perm[i]): copy columns, convert
+// values, pad to a multiple of 4 with (last column, 0), and accumulate the
+// FP64 squared norm of the stored values.
+template <typename VT>
+__global__ void k_pack(const int* rp, const int* col, const float* val, const int* perm,
+                       const int2* rinfo, int m, int* pcol, VT* pval, double* rho) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+        const int src = perm ? perm[i] : i;
+        const int a = rp[src], len = rp[src + 1] - a;
+        const int2 ri = rinfo[i];
+        const int padded = (len + 3) & ~3;
+        const int lastc = len > 0 ? col[a + len - 1] : 0;
+        double s = 0.0;
+        for (int e = lane; e < padded; e += 32) {
+            if (e < len) {
+                const VT v = to_store<VT>(val[a + e]);
+                pcol[ri.x + e] = col[a + e];
+                pval[ri.x + e] = v;
+                const double f = (double)from_store<VT>(v);
+                s += f * f;
+            } else {
+                pcol[ri.x + e] = lastc;
+                pval[ri.x + e] = to_store<VT>(0.f);
+            }
+        }
+        s = warp_sum(s);
+        if (lane == 0) rho[i] = s;
+    }
+}
+
+__global__ void k_count_kept(const double* rho, const int* seg, int m, int* kept) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        if (rho[i] > 0.0) atomicAdd(kept + (seg ? seg[i] : 0), 1);
+}
+
+__global__ void k_weights(const double* rho, const int* seg, const double* seg_w, int m,
+                          float* wr) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const double r = rho[i];
+        wr[i] = (r > 0.0) ? (float)(seg_w[seg ? seg[i] : 0] / r) : 0.f;
+    }
+}
+
+__global__ void k_zero_row_check(const double* rho, const float* l, const float* u, int m,
+                                 int B, int* flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (rho[i] > 0.0) continue;
+        for (int b = 0; b < B; ++b) {
+            const size_t o = (size_t)i * B + b;
+            if (!(l[o] <= 0.f && u[o] >= 0.f)) atomicOr(flags, 1);
+        }
+    }
+}
+
+// l[i*B + b] = l_in[perm[i]*B_in + b] for b < B_in; padding RHS get (-inf, inf).
+__global__ void k_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
+                                 int B_in, int B, float* l, float* u) {
+    const long long tot = (long long)m * B;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / B), b = (int)(t - (long long)i * B);
+        const int src = perm ? perm[i] : i;
+        if (b < B_in) {
+            l[t] = l_in[(size_t)src * B_in + b];
+            u[t] = u_in[(size_t)src * B_in + b];
+        } else {
+            l[t] = -INFINITY;
+            u[t] = INFINITY;
+        }
+    }
+}
+
+// x[j*B + b] = clamp(x_in[j*B_in + b] (or 0), lo, hi); padding RHS are 0-clamped.
+__global__ void k_box_init(float* x, const float* lo, const float* hi, long long nB, int B,
+                           int box_len, const float* x_in, int B_in) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nB;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long j = t / B;
+        const int b = (int)(t - j * B);
+        const float v = (x_in && b < B_in) ? x_in[j * B_in + b] : 0.f;
+        const long long bj = (box_len == 1) ? 0 : j;
+        x[t] = clampf(v, lo[bj], hi[bj]);
+    }
+}
+
+__global__ void k_unpad_x(const float* x, long long n, int B, int B_out, float* out) {
+    const long long tot = n * B_out;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long j = t / B_out;
+        const int b = (int)(t - j * B_out);
+        out[t] = x[j * B + b];
+    }
+}
+
+// Column sums of S for column tiles held in shared memory: CTA (tile, slice)
+// accumulates rows of its slice into a private FP64 tile, written to
+// work[slice][col]; a second kernel sums the slices in order.
+constexpr int kColTile = 4096;
+__global__ void k_colsum_partial(const int* rp, const int* col, const float* val, int m, int n,
+                                 int slices, double* work) {
+    __shared__ double acc[kColTile];
+    const int tile = blockIdx.x / slices, slice = blockIdx.x % slices;
+    const int c0 = tile * kColTile;
+    for (int t = threadIdx.x; t < kColTile; t += blockDim.x) acc[t] = 0.0;
+    __syncthreads();
+    const int r0 = (int)((long long)m * slice / slices);
+    const int r1 = (int)((long long)m * (slice + 1) / slices);
+    // one warp walks the slice's rows in order; the lanes of a row add
+    // distinct columns, so every acc[c] receives its terms in row order
+    if (threadIdx.x < 32) {
+        for (int i = r0; i < r1; ++i) {
+            for (int e = rp[i] + (int)threadIdx.x; e < rp[i + 1]; e += 32) {
+                const int c = col[e] - c0;
+                if (c >= 0 && c < kColTile) acc[c] += (double)val[e];
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kColTile; t += blockDim.x) {
+        const int c = c0 + t;
+        if (c < n) work[(size_t)slice * n + c] = acc[t];
+    }
+}
+
+__global__ void k_colsum_final(const double* work, int slices, int n, int m, double* c64,
+                               float* c32) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < slices; ++k) s += work[(size_t)k * n + c];
+        s /= (double)m;
+        c64[c] = s;
+        c32[c] = (float)s;
+    }
+}
+
+__global__ void k_sumsq(const double* v, int n, double* out) {
+    __shared__ double sw[8];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i] * v[i];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sw[w];
+        *out = t;
+    }
+}
+
+inline int grid_for(long long work, int threads = 256) {
+    long long g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 8) g = 152 * 8;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,
+                                int n, long long nnz, int* flags, cudaStream_t s) {
+    k_validate_csr<<<grid_for(nnz > m ? nnz : m), 256, 0, s>>>(row_ptr, col, val, m, n, nnz,
+                                                               flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_vec(const float* v, long long len, int allow_inf, int* flags,
+                                int bit, cudaStream_t s) {
+    k_validate_vec<<<grid_for(len), 256, 0, s>>>(v, len, allow_inf, flags, bit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_pair(const float* lo, const float* hi, long long len, int* flags,
+                                 int bit, cudaStream_t s) {
+    k_validate_pair<<<grid_for(len), 256, 0, s>>>(lo, hi, len, flags, bit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const int* row_ptr, const int* col, const float* val, const int* perm,
+                        const int2* rinfo, int m, int* pcol, void* pval, suppy_dtype dt,
+                        double* rho, cudaStream_t s) {
+    const int grid = grid_for((long long)m * 32);
+    if (dt == SUPPY_F32)
+        k_pack<float><<<grid, 256, 0, s>>>(row_ptr, col, val, perm, rinfo, m, pcol,
+                                           static_cast<float*>(pval), rho);
+    else if (dt == SUPPY_BF16)
+        k_pack<__nv_bfloat16><<<grid, 256, 0, s>>>(row_ptr, col, val, perm, rinfo, m, pcol,
+                                                   static_cast<__nv_bfloat16*>(pval), rho);
+    else
+        k_pack<__half><<<grid, 256, 0, s>>>(row_ptr, col, val, perm, rinfo, m, pcol,
+                                            static_cast<__half*>(pval), rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_kept(const double* rho, const int* seg, int m, int* kept,
+                              cudaStream_t s) {
+    k_count_kept<<<grid_for(m), 256, 0, s>>>(rho, seg, m, kept);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(const double* rho, const int* seg, const double* seg_w, int m,
+                           float* wr, cudaStream_t s) {
+    k_weights<<<grid_for(m), 256, 0, s>>>(rho, seg, seg_w, m, wr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_row_check(const double* rho, const float* l, const float* u, int m,
+                                  int B, int* flags, cudaStream_t s) {
+    k_zero_row_check<<<grid_for(m), 256, 0, s>>>(rho, l, u, m, B, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
+                                  int B_in, int B, float* l, float* u, cudaStream_t s) {
+    k_permute_bounds<<<grid_for((long long)m * B), 256, 0, s>>>(l_in, u_in, perm, m, B_in, B, l,
+                                                                u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_init(float* x, const float* lo, const float* hi, long long nB, int B,
+                            int box_len, const float* x_in, int B_in, cudaStream_t s) {
+    k_box_init<<<grid_for(nB), 256, 0, s>>>(x, lo, hi, nB, B, box_len, x_in, B_in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpad_x(const float* x, long long n, int B, int B_out, float* out,
+                           cudaStream_t s) {
+    k_unpad_x<<<grid_for(n * B_out), 256, 0, s>>>(x, n, B, B_out, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
+                           double* c64, float* c32, double* work, int slices, cudaStream_t s) {
+    const int tiles = (n + kColTile - 1) / kColTile;
+    k_colsum_partial<<<tiles * slices, 256, 0, s>>>(row_ptr, col, val, m, n, slices, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_colsum_final<<<grid_for(n), 256, 0, s>>>(work, slices, n, m, c64, c32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s) {
+    k_sumsq<<<1, 256, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace suppy

@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: one sweep from the same point <= 1e-5 relative L2 (FP32 A);
+a full superiorized run <= 1e-3; proximity and objective values <= 1e-3
+relative (much tighter in practice for single evaluations).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_27086_gb300 as pk
+import synth
+from tests.helpers import oracle_objective, random_x, rel, rel_l2, rounded_values, small_ct
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DT = {"f32": pk.SUPPY_F32, "bf16": pk.SUPPY_BF16, "f16": pk.SUPPY_F16}
+
+
+def _params(**kw):
+    return pk.suppy_params_default(**kw)
+
+
+def _oracle_sweep(prob, x, mode=O.CIMMINO, dtype="f32", lam=1.0, b=0):
+    vals = rounded_values(prob.A.val, dtype)
+    S, l, u, lo, hi = O.from_problem(prob, mode, values=vals)
+    return O.sweep(S, mode, O.rhs(l, b), O.rhs(u, b), lam, lo, hi, np.asarray(x, np.float64))
+
+
+# ------------------------------------------------------------ one sweep ----
+
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+def test_one_sweep_tiny_ct(mode):
+    prob = small_ct()
+    if mode == O.BIP:
+        prob.blocks = synth.angle_blocks(90, 91, 10)
+    ctx = pk.from_problem(prob, mode=mode)
+    x0 = random_x(prob.A.n, 1, seed=1)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 1)
+    xg = ctx.suppy_get_x()
+    xo, po = _oracle_sweep(prob, x0, mode)
+    assert rel_l2(xg, xo) <= 1e-5
+    ph, _ = ctx.suppy_history()
+    assert len(ph) == 1 and rel(ph[0], po) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_one_sweep_low_precision_values(dtype):
+    """BF16/FP16 storage: parity against the oracle run on the rounded values;
+    the error against the FP32-valued oracle is reported by the bench."""
+    prob = small_ct()
+    ctx = pk.from_problem(prob, dtype=DT[dtype])
+    x0 = random_x(prob.A.n, 1, seed=2)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 1)
+    xo, _ = _oracle_sweep(prob, x0, dtype=dtype)
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+
+
+@pytest.mark.parametrize("mean_len,long_len", [(3, 0), (30, 0), (100, 0), (300, 0), (40, 2100),
+                                               (250, 1500)])
+def test_one_sweep_row_length_mix(mean_len, long_len):
+    """Ragged rows covering every launch shape (4..32 lanes per row), empty
+    rows, rows longer than the register-held chunks, n not a multiple of 4."""
+    n = 3001
+    prob = synth.random_problem(700, n, seed=mean_len + long_len, feasible=False,
+                                mean_len=mean_len, empty_frac=0.05,
+                                long_rows=7 if long_len else 0, long_len=long_len)
+    ctx = pk.from_problem(prob)
+    x0 = random_x(n, 1, seed=3)
+    for lam in (1.0, 1.7):
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(lam=lam), 1)
+        xo, po = _oracle_sweep(prob, x0, lam=lam)
+        assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+        ph, _ = ctx.suppy_history()
+        assert rel(ph[0], po) <= 1e-5
+
+
+def test_vector_box_and_infinite_bounds():
+    n = 500
+    prob = synth.random_problem(300, n, seed=5, feasible=False, mean_len=25)
+    rng = np.random.default_rng(5)
+    prob.box_lo = rng.uniform(-0.2, 0.3, size=n).astype(np.float32)
+    prob.box_hi = (prob.box_lo + rng.uniform(0.1, 1.0, size=n)).astype(np.float32)
+    prob.l[::3] = -np.inf
+    prob.u[1::3] = np.inf
+    ctx = pk.from_problem(prob)
+    x0 = random_x(n, 1, seed=6, lo=-1, hi=2)
+    ctx.suppy_set_x(x0)
+    x0c = np.clip(x0, prob.box_lo, prob.box_hi)
+    np.testing.assert_array_equal(ctx.suppy_get_x(), x0c)
+    ctx.suppy_sweep(_params(), 1)
+    xo, _ = _oracle_sweep(prob, x0c)
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+
+
+# ------------------------------------------------- proximity / objective ----
+
+def test_proximity_matches_and_is_deterministic():
+    prob = small_ct()
+    ctx = pk.from_problem(prob)
+    x0 = random_x(prob.A.n, 1, seed=7)
+    ctx.suppy_set_x(x0)
+    p1 = ctx.suppy_proximity()[0]
+    p2 = ctx.suppy_proximity()[0]
+    assert p1 == p2
+    S, l, u, lo, hi = O.from_problem(prob)
+    assert rel(p1, O.proximity(S, l, u, x0.astype(np.float64))) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["tv", "atv"])
+def test_objective_matches(kind):
+    prob = small_ct()
+    obj = {"tv": pk.SUPPY_OBJ_TV_ISO, "atv": pk.SUPPY_OBJ_TV_ANISO}[kind]
+    ctx = pk.from_problem(prob, obj=obj)
+    x0 = random_x(prob.A.n, 1, seed=8)
+    ctx.suppy_set_x(x0)
+    f = ctx.suppy_objective()[0]
+    ob = oracle_objective(prob, {"tv": O.OBJ_TV_ISO, "atv": O.OBJ_TV_ANISO}[kind])
+    assert rel(f, ob.f(x0.astype(np.float64))) <= 1e-6
+
+
+# ----------------------------------------------------------- perturbation ----
+
+@pytest.mark.parametrize("kind", ["tv", "atv"])
+def test_perturbation_phase_matches(kind):
+    prob = small_ct()
+    obj = {"tv": pk.SUPPY_OBJ_TV_ISO, "atv": pk.SUPPY_OBJ_TV_ANISO}[kind]
+    okind = {"tv": O.OBJ_TV_ISO, "atv": O.OBJ_TV_ANISO}[kind]
+    ctx = pk.from_problem(prob, obj=obj)
+    x0 = random_x(prob.A.n, 1, seed=9)
+    ctx.suppy_set_x(x0)
+    P = dict(gamma=2.0, alpha=0.9, n_red=4, max_trials=50)
+    acc = ctx.suppy_perturb(_params(**P))
+    ob = oracle_objective(prob, okind)
+    st = O.PertState()
+    y, a, t = O.perturbation_phase(ob, x0.astype(np.float64), st, O.Params(**P))
+    assert acc[0] == a
+    blob = ctx.suppy_get_state()
+    assert rel_l2(ctx.suppy_get_x(), y) <= 1e-5
+    del blob
+
+
+# --------------------------------------------------------------- full runs ----
+
+def test_full_superiorized_run_tiny_ct():
+    """Configuration of the tiny CT workload: 100 superiorized Cimmino sweeps,
+    TV, beta = 0.5 * 0.99^l, lambda = 1."""
+    prob = small_ct()
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    P = dict(gamma=0.5, alpha=0.99, n_red=1, max_sweeps=100)
+    st = ctx.suppy_run(_params(**P))
+    S, l, u, lo, hi = O.from_problem(prob)
+    r = O.run(S, O.CIMMINO, l, u, lo, hi, oracle_objective(prob, O.OBJ_TV_ISO), O.Params(**P))
+    xg = ctx.suppy_get_x()
+    assert st[0]["sweeps"] == 100
+    assert rel_l2(xg, r.x) <= 1e-3
+    ph, oh = ctx.suppy_history()
+    assert rel(ph[-1], r.prox_hist[-1]) <= 1e-3
+    assert rel(oh[-1], r.obj_hist[-1]) <= 1e-3
+    assert st[0]["ell"] == r.ell
+
+
+def test_full_bip_run_linear_objective_rt_small():
+    """Radiotherapy shape (reduced): block-iterative sweeps over target / OAR
+    blocks, mean body dose objective computed from the body rows."""
+    prob = synth.rt_problem(nx=30, ny=20, nz=12, ns=9, nzb=7)
+    ctx = pk.from_problem(prob, mode=pk.SUPPY_BIP, obj=pk.SUPPY_OBJ_LINEAR)
+    P = dict(gamma=1.0, alpha=0.99, n_red=1, max_sweeps=40, lam=1.0)
+    ctx.suppy_run(_params(**P))
+    S, l, u, lo, hi = O.from_problem(prob, O.BIP)
+    ob = oracle_objective(prob, O.OBJ_LINEAR)
+    r = O.run(S, O.BIP, l, u, lo, hi, ob, O.Params(gamma=1.0, alpha=0.99, n_red=1,
+                                                      max_sweeps=40))
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3
+    f = ctx.suppy_objective()[0]
+    assert rel(f, ob.f(r.x)) <= 1e-3
+
+
+def test_stopping_rule_stops_at_the_oracles_sweep():
+    prob = synth.random_problem(400, 300, seed=11, feasible=True, mean_len=30)
+    ctx = pk.from_problem(prob)
+    P = dict(max_sweeps=300, prox_rel=1e-3, patience=3, use_stopping=1, check_every=7,
+             obj_rel=0.0)
+    st = ctx.suppy_run(_params(**P))
+    S, l, u, lo, hi = O.from_problem(prob)
+    r = O.run(S, O.CIMMINO, l, u, lo, hi, O.Objective(O.OBJ_NONE),
+              O.Params(max_sweeps=300, prox_rel=1e-3, patience=3, use_stopping=True, obj_rel=0.0))
+    assert st[0]["stopped"] == 1
+    assert st[0]["sweeps"] == r.sweeps
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-4
+
+
+def test_checkpoint_resume_is_exact_on_state():
+    prob = small_ct()
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    P = _params(gamma=0.5, alpha=0.99, max_sweeps=10)
+    ctx.suppy_run(P)
+    blob = ctx.suppy_get_state()
+    x_mid = ctx.suppy_get_x().copy()
+    ctx.suppy_run(P)
+    x_a = ctx.suppy_get_x().copy()
+    ctx.suppy_set_state(blob)
+    np.testing.assert_array_equal(ctx.suppy_get_x(), x_mid)
+    st = ctx.suppy_run(P)
+    assert st[0]["sweeps"] == 20
+    assert rel_l2(ctx.suppy_get_x(), x_a) <= 1e-5
+
+
+# ------------------------------------------------------------------ batched ----
+
+@pytest.mark.parametrize("nrhs", [3, 4, 16])
+def test_batched_sweep_matches_per_rhs_oracle(nrhs):
+    prob = synth.ct_problem(32, 30, 45, nrhs=nrhs)
+    ctx = pk.from_problem(prob)
+    x0 = random_x(prob.A.n, nrhs, seed=12)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 2)
+    xg = ctx.suppy_get_x()
+    for b in range(nrhs):
+        S, l, u, lo, hi = O.from_problem(prob)
+        x = x0[:, b].astype(np.float64)
+        for _ in range(2):
+            x, _ = O.sweep(S, O.CIMMINO, O.rhs(prob.l, b), O.rhs(prob.u, b), 1.0, lo, hi, x)
+        assert rel_l2(xg[:, b], x) <= 1e-5
+
+
+def test_batched_run_equals_single_runs():
+    """A right-hand side gives the same result alone and inside a batch."""
+    prob = synth.ct_problem(32, 30, 45, nrhs=4)
+    P = _params(gamma=0.5, alpha=0.99, max_sweeps=25)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    ctx.suppy_run(P)
+    xb = ctx.suppy_get_x()
+    for b in range(4):
+        p1 = synth.ct_problem(32, 30, 45, nrhs=4)
+        p1.l, p1.u = p1.l[:, b].copy(), p1.u[:, b].copy()
+        c1 = pk.from_problem(p1, obj=pk.SUPPY_OBJ_TV_ISO)
+        c1.suppy_run(P)
+        assert rel_l2(xb[:, b], c1.suppy_get_x()) <= 1e-4
+
+
+# --------------------------------------------------------------- validation ----
+
+def test_invalid_inputs_are_rejected():
+    prob = synth.random_problem(50, 40, seed=13, mean_len=5)
+    bad = synth.random_problem(50, 40, seed=13, mean_len=5)
+    bad.A.col = bad.A.col.copy()
+    bad.A.col[3] = 40
+    with pytest.raises(pk.SuppyError) as e:
+        pk.from_problem(bad)
+    assert e.value.status == pk.SUPPY_EINVAL
+    bad = synth.random_problem(50, 40, seed=13, mean_len=5)
+    bad.l = bad.l.copy()
+    bad.l[0] = bad.u[0] + 1
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(bad)
+    bad = synth.random_problem(50, 40, seed=13, mean_len=5)
+    bad.A.val = bad.A.val.copy()
+    bad.A.val[0] = np.nan
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(bad)
+    # a zero row whose slab excludes 0
+    bad = synth.random_problem(50, 40, seed=13, mean_len=5, empty_frac=0.3)
+    z = np.flatnonzero(np.diff(bad.A.row_ptr) == 0)[0]
+    bad.l = bad.l.copy()
+    bad.l[z], bad.u[z] = 1.0, 2.0
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(bad)
+    ctx = pk.from_problem(prob)
+    with pytest.raises(pk.SuppyError):
+        ctx.suppy_perturb(_params())          # no objective: ESTATE
+
+
+def test_device_inputs_equal_host_inputs():
+    prob = small_ct()
+    c_h = pk.from_problem(prob)
+    c_d = pk.from_problem(prob, device=True)
+    x0 = random_x(prob.A.n, 1, seed=14)
+    for c in (c_h, c_d):
+        c.suppy_set_x(x0)
+        c.suppy_sweep(_params(), 1)
+    assert rel_l2(c_h.suppy_get_x(), c_d.suppy_get_x()) <= 1e-6
