@@ -200,7 +200,7 @@ def config_of(prob):
 
 def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
     """Run W untimed iterations, then K timed ones in one suppy_run call;
-    returns (elapsed ms, sweep-kernel ms, sweep-kernel launches, launches)."""
+    returns (elapsed ms, {kind: (kernel ms, launches)}, library launches)."""
     import torch
     s = torch.cuda.current_stream()
     if W:
@@ -217,17 +217,55 @@ def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     nl = ctx.suppy_launch_count() - l0
-    kms, kn = ctx.suppy_kernel_time() if with_timing else (0.0, 0)
+    kt = {k: ctx.suppy_kernel_time(k) for k in (0, 1, 2)} if with_timing else {}
     if with_timing:
         ctx.suppy_timing_enable(False)
-    return ms, kms, kn, nl
+    return ms, kt, nl
+
+
+KIND = {0: "row pass", 1: "column pass / finalize", 2: "perturbation"}
+
+
+def kernel_alg_bytes(strategy, kind, m, n, nnz, vb, B=1):
+    """Algorithmic bytes of one sweep's kernel of the given kind (summed over
+    the blocks of a block-iterative sweep).  Row pass: A's values and column
+    indices once, per row its offset/length (8 B), weight (4 B) and l, u per
+    right-hand side, x read once; plus delta written once (one pass) or the
+    coefficients written once (two passes).  Column pass (two passes): the CSC
+    values and row indices once, per column offset/length, coefficients read
+    once, x read and written.  Finalize (one pass): x and delta read and
+    written.  Perturbation: not HBM-bound (x, g are L2-resident)."""
+    if kind == 0:
+        b = nnz * (vb + 4) + m * 12 + m * 8 * B + n * 4 * B
+        return b + (m * 4 * B if strategy == 2 else n * 4 * B)
+    if kind == 1:
+        if strategy == 2:
+            return nnz * (vb + 4) + n * 8 + m * 4 * B + n * 8 * B
+        return n * 16 * B
+    return n * 12 * B
 
 
 def sweep_alg_bytes(m, n, nnz, vbytes, B=1):
-    """Algorithmic bytes of one sweep launch: A values and column indices once,
-    per-row offset/l/u/weight (l, u per right-hand side), x read and delta
-    written once per right-hand side."""
-    return nnz * (vbytes + 4) + m * (8 + 8 * B) + n * 8 * B
+    """Algorithmic bytes of one application of T: A once, per-row data and the
+    iterate/correction vectors once."""
+    return nnz * (vbytes + 4) + m * (12 + 8 * B) + n * 16 * B
+
+
+def summarize(ctx, prob, K, ms, kt, vb, B=1):
+    info = ctx.suppy_info_get()
+    strat = info["strategy"]
+    A = prob.A
+    per = {}
+    for k, (tms, nl) in kt.items():
+        if nl == 0:
+            continue
+        sweeps_launches = max(nl // K, 1)
+        alg = kernel_alg_bytes(strat, k, A.m, A.n, A.nnz, vb, B)
+        per[KIND[k]] = {"ms_per_sweep": tms / K, "launches_per_sweep": sweeps_launches,
+                        "alg_bytes_per_sweep": alg,
+                        "gbs_alg": alg / (tms / K * 1e-3) / 1e9 if k != 2 else None}
+    t_sweep = sum(kt[k][0] for k in (0, 1) if k in kt) / K
+    return info, per, t_sweep
 
 
 def variants(pk, K, W):
@@ -235,6 +273,7 @@ def variants(pk, K, W):
     import torch
     import synth
     out = {}
+    Kv = max(20, min(K, 200))
 
     def run_one(name, prob, metric_units, **kw):
         obj = kw.pop("obj")
@@ -243,28 +282,31 @@ def variants(pk, K, W):
         pkw = kw.pop("params")
         B = 1 if prob.l.ndim == 1 else prob.l.shape[1]
         t0 = time.perf_counter()
-        ctx = pk.from_problem(prob, obj=obj, dtype=dtype, mode=mode)
+        ctx = pk.from_problem(prob, obj=obj, dtype=dtype, mode=mode, **kw)
         t_create = time.perf_counter() - t0
-        ms, kms, kn, nl = time_iterations(ctx, pk, Kv, W, pkw)
-        info = ctx.suppy_info_get()
+        ms, kt, nl = time_iterations(ctx, pk, Kv, W, pkw)
         vb = 4 if dtype == pk.SUPPY_F32 else 2
+        info, per, t_sweep = summarize(ctx, prob, Kv, ms, kt, vb, B)
         nnz = prob.A.nnz
-        per_launch = kms / max(kn, 1)
-        nseg = info["nblocks"]
         alg = sweep_alg_bytes(prob.A.m, prob.A.n, nnz, vb, B)
-        gbs = alg / nseg / (per_launch * 1e-3) / 1e9 if kn else None
         out[name] = {"value": nnz * B * Kv / (ms * 1e-3), "unit": metric_units,
-                     "ms_per_step": ms / Kv, "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B,
-                     "sweep_kernel_ms": per_launch, "sweep_launches_per_step": nseg,
-                     "sweep_kernel_gbs_alg": gbs, "create_s": t_create,
-                     "lanes_per_row": info["lanes_per_row"], "grid": info["grid"]}
+                     "ms_per_step": ms / Kv, "sweep_ms": t_sweep,
+                     "sweep_gbs_alg": alg / (t_sweep * 1e-3) / 1e9 if t_sweep else None,
+                     "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B, "kernels": per,
+                     "create_s": t_create, "strategy": info["strategy"],
+                     "scatter": info["scatter"], "lanes_per_row": info["lanes_per_row"],
+                     "col_lanes": info["col_lanes"], "nblocks": info["nblocks"],
+                     "launches_per_step": nl / Kv}
         ctx.close()
         torch.cuda.synchronize()
 
-    Kv = max(20, min(K, 200))
     prob = ct512()
+    run_one("ct512_cimmino_tv_f32_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
+            strategy=pk.STRATEGY_ONE_PASS)
     run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
             params=SUP)
+    run_one("ct512_cimmino_tv_bf16_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
+            dtype=pk.SUPPY_BF16, params=SUP, strategy=pk.STRATEGY_ONE_PASS)
     prob.blocks = synth.angle_blocks(360, 725, 36)
     run_one("ct512_bip36_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP,
             params=SUP)
@@ -272,6 +314,8 @@ def variants(pk, K, W):
     seis = synth.seismic_problem(nrhs=16)
     run_one("seismic_b16_atv_f32", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
             params=SUP)
+    run_one("seismic_b16_atv_f32_onepass", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
+            params=SUP, strategy=pk.STRATEGY_ONE_PASS)
     seis.l, seis.u = seis.l[:, 0].copy(), seis.u[:, 0].copy()
     run_one("seismic_b1_atv_f32", seis, UNIT, obj=pk.SUPPY_OBJ_TV_ANISO, params=SUP)
     del seis
@@ -300,7 +344,6 @@ def ours(args):
     A = prob.A
     log(f"[bench] CT 512^2: m={A.m} n={A.n} nnz={A.nnz}")
     ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
-    info = ctx.suppy_info_get()
     if W:
         ctx.suppy_run(pk.suppy_params_default(max_sweeps=W, **SUP))
     torch.cuda.synchronize()
@@ -309,7 +352,7 @@ def ours(args):
     sampler = ClockSampler(gpu_id_for(local))
     sampler.start()
     time.sleep(0.3)
-    ms, kms, kn, nl = time_iterations(ctx, pk, K, 0, SUP)
+    ms, kt, nl = time_iterations(ctx, pk, K, 0, SUP)
     clocks = sampler.stop()
     if world > 1:
         import torch.distributed as dist
@@ -317,17 +360,26 @@ def ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = A.nnz * K * world / (ms * 1e-3)
-    per_launch = kms / max(kn, 1)
-    alg = sweep_alg_bytes(A.m, A.n, A.nnz, 4)
+    info, per, t_sweep = summarize(ctx, prob, K, ms, kt, 4)
+    # dominant kernel of the step
+    dom = max((k for k in (0, 1, 2) if kt.get(k, (0, 0))[1]), key=lambda k: kt[k][0])
+    dms, dn = kt[dom]
+    per_launch = dms / dn
+    alg = kernel_alg_bytes(info["strategy"], dom, A.m, A.n, A.nnz, 4) / max(dn // K, 1)
     peak, peak_kind = peaks()
     achieved = alg / (per_launch * 1e-3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_sweep (fused CSR sweep)",
-            "alg_bytes_per_launch": alg, "launch_ms": per_launch, "peak_source": peak_kind}
+            "frac": achieved / peak, "traffic": None, "kernel": KIND[dom],
+            "alg_bytes_per_launch": alg, "launch_ms": per_launch,
+            "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
+    sweep_alg = sweep_alg_bytes(A.m, A.n, A.nnz, 4)
+    sweep_roof = {"alg_bytes": sweep_alg, "sweep_ms": t_sweep,
+                  "achieved": sweep_alg / (t_sweep * 1e-3) / 1e9,
+                  "frac": sweep_alg / (t_sweep * 1e-3) / 1e9 / peak}
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
         try:
-            tr = json.load(open(traffic_path)).get("ct512_k_sweep")
+            tr = json.load(open(traffic_path)).get(f"ct512_{info['strategy']}_{dom}")
             if tr:
                 roof["traffic"] = tr
         except Exception:
@@ -355,9 +407,11 @@ def ours(args):
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(prob),
-           "roofline": roof, "e2e": e2e, "gpu_launches": int(nl), "clocks": clocks,
-           "launch_shape": {k: info[k] for k in ("lanes_per_row", "chunks_in_regs", "grid",
-                                                  "block", "perturb_cluster")}}
+           "roofline": roof, "sweep_roofline": sweep_roof, "kernels": per, "e2e": e2e,
+           "gpu_launches": int(nl), "clocks": clocks,
+           "launch_shape": {k: info[k] for k in ("strategy", "scatter", "lanes_per_row",
+                                                  "elems_in_regs", "grid", "col_lanes",
+                                                  "col_grid", "perturb_cluster")}}
     ctx.close()
     if rank == 0 and not args.no_variants:
         res["variants"] = variants(pk, K, min(W, 5))
@@ -375,6 +429,25 @@ def ours(args):
     return 0
 
 
+def profile_case(strategy: int, steps: int) -> int:
+    """A short run for ncu: the inputs (A ~0.4 GB) exceed L2, the device holds
+    about 1 GB, and each kernel is launched `steps` times."""
+    import torch
+    import synth
+    from paper_2606_27086_gb300 import build as pkbuild
+    pkbuild.build()
+    import paper_2606_27086_gb300 as pk
+    prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201, seed_noise=202)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=strategy)
+    ctx.suppy_run(pk.suppy_params_default(max_sweeps=steps, **SUP))
+    torch.cuda.synchronize()
+    info = ctx.suppy_info_get()
+    log(f"[profile] strategy {strategy}: m={prob.A.m} n={prob.A.n} nnz={prob.A.nnz} "
+        f"shape={info}")
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +457,12 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2],
+                    help="run a short profiling case (CT 384x384, 270 angles x 545 bins) with "
+                         "sweep strategy 1 (one pass) or 2 (two passes) and exit")
     args = ap.parse_args()
+    if args.profile:
+        return profile_case(args.profile, args.steps if args.steps < 50 else 6)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -45,8 +45,8 @@
  *   unknowns are n x B row-major (element (j, b) at j*B + b); vectors over the
  *   constraints (l, u) are m x B row-major (i*B + b).  Per-RHS outputs are
  *   arrays of length B.
- * - Matrix indices are int32; nnz after padding each row to a multiple of 4
- *   must stay below 2^31 (SUPPY_EINVAL otherwise).
+ * - Matrix indices are int32 and nnz must stay below 2^31 (SUPPY_EINVAL
+ *   otherwise).  Column indices inside a row must be distinct.
  */
 #ifndef SUPPY_GB300_H
 #define SUPPY_GB300_H
@@ -112,7 +112,13 @@ typedef struct {
     const suppy_csr* obj_rows;
     int32_t nrhs;             /* B, 1..32 (0 is read as 1) */
     int64_t box_len;          /* 1: scalar box bounds; n: one bound per unknown */
-    int32_t tune;             /* 1: time candidate launch shapes at create */
+    int32_t tune;             /* 1: time candidate strategies / launch shapes at create */
+    /* Sweep strategy: 0 automatic; 1 one pass over A (row pass with the
+     * correction scattered by L2 reductions, or staged in shared memory when
+     * n*B*4 bytes fit); 2 two passes (row pass writing the coefficients, then a
+     * column pass over a CSC copy of A gathering them -- no atomics, bitwise
+     * reproducible, twice the matrix memory). */
+    int32_t strategy;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -146,14 +152,18 @@ typedef struct {
 
 typedef struct {
     int32_t m, n, nrhs, m_kept;   /* m_kept = m' (rows with ||a_i|| > 0)     */
-    int64_t nnz, nnz_padded;
+    int64_t nnz, nnz_csc;         /* nnz_csc: entries of the CSC copy (two passes) */
     int32_t nblocks;
     int32_t lanes_per_row;        /* launch shape chosen for the sweep       */
-    int32_t chunks_in_regs;
+    int32_t elems_in_regs;        /* row elements a lane holds between dot and scatter */
     int32_t grid;                 /* CTAs of the sweep launch                */
     int32_t block;                /* threads per CTA of the sweep launch     */
     int32_t perturb_cluster;      /* CTAs per cluster of the perturbation    */
     int64_t device_bytes;         /* device memory held by the context       */
+    int32_t strategy;             /* 1 one pass, 2 two passes                */
+    int32_t scatter;              /* one pass: 1 L2 reductions, 2 shared-memory staged */
+    int32_t col_lanes;            /* two passes: lanes per column            */
+    int32_t col_grid;             /* two passes: CTAs of the column pass     */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */
@@ -246,12 +256,15 @@ suppy_status suppy_set_state(suppy_ctx* ctx, const void* buf, size_t len);
 /* Sizes and launch shapes of the context. */
 suppy_status suppy_info_get(const suppy_ctx* ctx, suppy_info* out);
 
-/* Kernel timing for measurement: when enabled, every sweep-kernel launch is
- * bracketed by CUDA events on the context's stream and graphs are not used.
- * suppy_kernel_time returns the summed event time (ms) and the launch count of
- * the sweep kernel since timing was enabled, and synchronizes. */
+/* Kernel timing for measurement: when enabled, every launch of the kernels
+ * below is bracketed by CUDA events on the context's stream.
+ * suppy_kernel_time(kind) returns the summed event time (ms) and the launch
+ * count since timing was enabled, and synchronizes.  kind: 0 the row pass
+ * (the fused one-pass sweep, or the row pass of the two-pass sweep); 1 the
+ * box step (finalize kernel, or the column pass of the two-pass sweep); 2 the
+ * perturbation phase. */
 suppy_status suppy_timing_enable(suppy_ctx* ctx, int32_t enable);
-suppy_status suppy_kernel_time(suppy_ctx* ctx, double* total_ms, int64_t* launches);
+suppy_status suppy_kernel_time(suppy_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
 /* Number of kernels the library launched on this context so far. */
 int64_t suppy_launch_count(const suppy_ctx* ctx);

@@ -23,6 +23,7 @@ SUPPY_OK, SUPPY_EINVAL, SUPPY_ENOMEM, SUPPY_ECUDA, SUPPY_ETIMEOUT, SUPPY_ESTATE 
 SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2
 SUPPY_CIMMINO, SUPPY_BIP = 0, 1
 SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
+STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS = 0, 1, 2
 
 EXPORTED = [
     "suppy_params_default", "suppy_create", "suppy_destroy", "suppy_set_stream",
@@ -44,7 +45,8 @@ class suppy_opts(ctypes.Structure):
                 ("block_of_row", ctypes.c_void_p), ("nblocks", ctypes.c_int32),
                 ("obj", ctypes.c_int), ("img_h", ctypes.c_int32), ("img_w", ctypes.c_int32),
                 ("c_lin", ctypes.c_void_p), ("obj_rows", ctypes.POINTER(suppy_csr)),
-                ("nrhs", ctypes.c_int32), ("box_len", ctypes.c_int64), ("tune", ctypes.c_int32)]
+                ("nrhs", ctypes.c_int32), ("box_len", ctypes.c_int64), ("tune", ctypes.c_int32),
+                ("strategy", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -67,10 +69,12 @@ class suppy_stats(ctypes.Structure):
 class suppy_info(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("n", ctypes.c_int32), ("nrhs", ctypes.c_int32),
                 ("m_kept", ctypes.c_int32), ("nnz", ctypes.c_int64),
-                ("nnz_padded", ctypes.c_int64), ("nblocks", ctypes.c_int32),
-                ("lanes_per_row", ctypes.c_int32), ("chunks_in_regs", ctypes.c_int32),
+                ("nnz_csc", ctypes.c_int64), ("nblocks", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("elems_in_regs", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("perturb_cluster", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("perturb_cluster", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("strategy", ctypes.c_int32), ("scatter", ctypes.c_int32),
+                ("col_lanes", ctypes.c_int32), ("col_grid", ctypes.c_int32)]
 
 
 _lib = None
@@ -105,7 +109,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_set_state": (ctypes.c_int, [P, P, ctypes.c_size_t]),
         "suppy_info_get": (ctypes.c_int, [P, ctypes.POINTER(suppy_info)]),
         "suppy_timing_enable": (ctypes.c_int, [P, I32]),
-        "suppy_kernel_time": (ctypes.c_int, [P, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "suppy_kernel_time": (ctypes.c_int, [P, I32, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "suppy_launch_count": (I64, [P]),
         "suppy_last_error": (ctypes.c_char_p, [P]),
         "suppy_version": (ctypes.c_char_p, []),
@@ -180,7 +184,7 @@ class Context:
 
     def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
-                 c_lin=None, obj_rows=None, nrhs=1, tune=0, stream=None):
+                 c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, stream=None):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -213,6 +217,7 @@ class Context:
         blen = box_lo.shape[0] if hasattr(box_lo, "shape") else len(box_lo)
         o.box_len = int(blen)
         o.tune = int(tune)
+        o.strategy = int(strategy)
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
@@ -317,10 +322,12 @@ class Context:
     def suppy_timing_enable(self, enable: bool = True):
         _check(self._lib.suppy_timing_enable(self.ctx, int(enable)), self.ctx)
 
-    def suppy_kernel_time(self):
+    def suppy_kernel_time(self, kind: int = 0):
+        """(total ms, launches) of kernel kind 0 row pass, 1 box step, 2 perturbation."""
         ms = ctypes.c_double()
         nl = ctypes.c_int64()
-        _check(self._lib.suppy_kernel_time(self.ctx, ctypes.byref(ms), ctypes.byref(nl)), self.ctx)
+        _check(self._lib.suppy_kernel_time(self.ctx, int(kind), ctypes.byref(ms), ctypes.byref(nl)),
+               self.ctx)
         return ms.value, nl.value
 
     def suppy_launch_count(self) -> int:
@@ -328,7 +335,7 @@ class Context:
 
 
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
-                 stream=None, tune=0) -> Context:
+                 stream=None, tune=0, strategy=0) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -350,7 +357,8 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
             kw["c_lin"] = prob.c_lin
     blocks = prob.blocks if mode == SUPPY_BIP else None
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
-                   block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune, **kw)
+                   block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
+                   strategy=strategy, **kw)
 
 
 def version() -> str:

@@ -24,7 +24,7 @@ struct suppy_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     int m = 0, n = 0, B_user = 1, B = 1;
-    long long nnz = 0, nnz_pad = 0;
+    long long nnz = 0;
     suppy_dtype dt = SUPPY_F32;
     suppy_mode mode = SUPPY_CIMMINO;
     suppy_obj obj = SUPPY_OBJ_NONE;
@@ -65,18 +65,35 @@ struct suppy_ctx {
     float* d_stage_u = nullptr;
     int* d_flags = nullptr;         // validation flags
 
+    // two-pass layout: CSC copy of A per block, coefficients
+    int2* d_cinfo = nullptr;        // nseg x n
+    int* d_ridx = nullptr;
+    void* d_cval = nullptr;
+    float* d_coef = nullptr;        // m x B
+    int* d_cpart = nullptr;         // nseg x (cgroups + 1)
+    std::vector<long long> cpref;   // per segment column-work prefix (nseg x (n + 1))
+    long long nnz_csc = 0;
+
     // launch shapes
-    int G = 32, maxch = 4;
+    int strategy = 1;               // 1 one pass, 2 two passes
+    int scat = 1;                   // one pass: 1 L2 reductions, 2 shared-memory staged
+    int G = 32, maxe = 8;
     int grid_sweep = 0, groups = 0;
+    int Gc = 32, grid_col = 0, cgroups = 0;
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
+    std::vector<long long> rpref;   // row-work prefix (m + 1)
 
     // measurement
+    struct TimedLaunch {
+        int kind;
+        cudaEvent_t a, b;
+    };
     bool timing = false;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
-    double timing_ms = 0.0;
-    long long timing_n = 0;
+    std::vector<TimedLaunch> evs;
+    double timing_ms[3] = {0.0, 0.0, 0.0};
+    long long timing_n[3] = {0, 0, 0};
     long long launches = 0;
     size_t dev_bytes = 0;
     std::vector<void*> allocs;
@@ -223,20 +240,39 @@ suppy_status ensure_hist(suppy_ctx* c, int need) {
 suppy_status flush_timing(suppy_ctx* c) {
     if (c->evs.empty()) return SUPPY_OK;
     CK(cudaStreamSynchronize(c->stream));
-    for (auto& pr : c->evs) {
+    for (auto& t : c->evs) {
         float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, pr.first, pr.second));
-        c->timing_ms += ms;
-        c->timing_n += 1;
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+        CK(cudaEventElapsedTime(&ms, t.a, t.b));
+        c->timing_ms[t.kind] += ms;
+        c->timing_n[t.kind] += 1;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
     }
     c->evs.clear();
     return SUPPY_OK;
 }
 
-// One application of T: every segment's fused sweep and its finalize.
-suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
+// Bracket one launch with events when timing is enabled.
+struct Timed {
+    suppy_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t begin() {
+        if (!c->timing) return cudaSuccess;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        if (e == cudaSuccess) e = cudaEventRecord(a, c->stream);
+        return e;
+    }
+    cudaError_t end() {
+        if (!c->timing) return cudaSuccess;
+        cudaError_t e = cudaEventRecord(b, c->stream);
+        if (e == cudaSuccess) c->evs.push_back({kind, a, b});
+        return e;
+    }
+};
+
+StopParams stop_params(const suppy_ctx* c, const suppy_params* p) {
     StopParams sp;
     sp.prox_abs = p->prox_abs;
     sp.prox_rel = p->prox_rel;
@@ -244,56 +280,111 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     sp.patience = p->patience;
     sp.use_stopping = p->use_stopping;
     sp.has_obj = c->obj != SUPPY_OBJ_NONE;
+    return sp;
+}
+
+SweepArgs row_args(suppy_ctx* c, int t, float lam) {
+    SweepArgs a;
+    a.rinfo = c->d_rinfo;
+    a.col = c->d_col;
+    a.val = c->d_val;
+    a.l = c->d_l;
+    a.u = c->d_u;
+    a.wr = c->d_wr;
+    a.x = c->d_x;
+    a.delta = c->d_delta;
+    a.coef = nullptr;
+    a.part = c->d_part + (size_t)t * (c->groups + 1);
+    a.pp = c->d_pp;
+    a.st = c->d_st;
+    a.lam = lam;
+    a.B = c->B;
+    a.n = c->n;
+    a.check_stop = 1;
+    return a;
+}
+
+double seg_scale(const suppy_ctx* c, int t) {
+    if (c->nseg == 1) return 0.5;
+    return c->m_kept > 0 ? 0.5 * (double)c->seg_kept[t] / c->m_kept : 0.0;
+}
+
+EpiArgs epi_args(suppy_ctx* c, int t, const StopParams& sp) {
+    EpiArgs e;
+    e.pp = c->d_pp;
+    e.npp = c->grid_sweep;
+    e.B = c->B;
+    e.scale = seg_scale(c, t);
+    e.st = c->d_st;
+    e.prox_hist = c->d_prox_hist;
+    e.obj_hist = c->d_obj_hist;
+    e.hist_cap = c->hist_cap;
+    e.first_seg = (t == 0);
+    e.last_seg = (t == c->nseg - 1);
+    e.sp = sp;
+    return e;
+}
+
+// Row pass of block t: the fused one-pass sweep (scat 1/2) or the
+// coefficient-writing row pass (scat 0).
+suppy_status launch_rows(suppy_ctx* c, const SweepArgs& a, int scat) {
+    Timed tm{c, 0};
+    CK(tm.begin());
+    if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, scat, c->grid_sweep, c->stream));
+    else CK(launch_sweep_batched(a, c->dt, scat, c->grid_sweep, c->stream));
+    CK(tm.end());
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+// One application of T.
+suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
+    const StopParams sp = stop_params(c, p);
+    suppy_status s;
     for (int t = 0; t < c->nseg; ++t) {
-        SweepArgs a;
-        a.rinfo = c->d_rinfo;
-        a.col = c->d_col;
-        a.val = c->d_val;
-        a.l = c->d_l;
-        a.u = c->d_u;
-        a.wr = c->d_wr;
-        a.x = c->d_x;
-        a.delta = c->d_delta;
-        a.part = c->d_part + (size_t)t * (c->groups + 1);
-        a.pp = c->d_pp;
-        a.st = c->d_st;
-        a.lam = (float)p->lambda;
-        a.B = c->B;
-        a.scatter = 1;
-        a.check_stop = 1;
-        std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-        if (c->timing) {
-            CK(cudaEventCreate(&ev.first));
-            CK(cudaEventCreate(&ev.second));
-            CK(cudaEventRecord(ev.first, c->stream));
+        SweepArgs a = row_args(c, t, (float)p->lambda);
+        const EpiArgs epi = epi_args(c, t, sp);
+        if (c->strategy == 2) {
+            a.coef = c->d_coef;
+            if ((s = launch_rows(c, a, 0)) != SUPPY_OK) return s;
+            ColArgs ca;
+            ca.cinfo = c->d_cinfo + (size_t)t * c->n;
+            ca.ridx = c->d_ridx;
+            ca.cval = c->d_cval;
+            ca.coef = c->d_coef;
+            ca.x = c->d_x;
+            ca.lo = c->d_lo;
+            ca.hi = c->d_hi;
+            ca.box_len = c->box_len;
+            ca.B = c->B;
+            ca.cpart = c->d_cpart + (size_t)t * (c->cgroups + 1);
+            ca.epi = epi;
+            Timed tm{c, 1};
+            CK(tm.begin());
+            CK(launch_colpass(ca, c->dt, c->Gc, c->grid_col, c->stream));
+            CK(tm.end());
+            note_launch(c);
+            if (epi.last_seg) {
+                CK(launch_epilogue(epi, c->stream));
+                note_launch(c);
+            }
+        } else {
+            if ((s = launch_rows(c, a, c->scat)) != SUPPY_OK) return s;
+            FinalizeArgs f;
+            f.x = c->d_x;
+            f.delta = c->d_delta;
+            f.lo = c->d_lo;
+            f.hi = c->d_hi;
+            f.nB = (long long)c->n * c->B;
+            f.B = c->B;
+            f.box_len = c->box_len;
+            f.epi = epi;
+            Timed tm{c, 1};
+            CK(tm.begin());
+            CK(launch_finalize(f, c->grid_fin, c->stream));
+            CK(tm.end());
+            note_launch(c);
         }
-        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxch, c->grid_sweep, c->stream));
-        else CK(launch_sweep_batched(a, c->dt, 32, c->grid_sweep, c->stream));
-        if (c->timing) {
-            CK(cudaEventRecord(ev.second, c->stream));
-            c->evs.push_back(ev);
-        }
-        FinalizeArgs f;
-        f.x = c->d_x;
-        f.delta = c->d_delta;
-        f.lo = c->d_lo;
-        f.hi = c->d_hi;
-        f.nB = (long long)c->n * c->B;
-        f.B = c->B;
-        f.box_len = c->box_len;
-        f.pp = c->d_pp;
-        f.npp = c->grid_sweep;
-        f.scale = 0.5 * (c->m_kept > 0 ? (double)c->seg_kept[t] / c->m_kept : 0.0);
-        if (c->nseg == 1) f.scale = 0.5;
-        f.st = c->d_st;
-        f.prox_hist = c->d_prox_hist;
-        f.obj_hist = c->d_obj_hist;
-        f.hist_cap = c->hist_cap;
-        f.first_seg = (t == 0);
-        f.last_seg = (t == c->nseg - 1);
-        f.sp = sp;
-        CK(launch_finalize(f, c->grid_fin, c->stream));
-        note_launch(c, 2);
     }
     c->k_upper += 1;
     if (c->evs.size() > 8192) return flush_timing(c);
@@ -318,7 +409,10 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.restart_every = p ? p->restart_every : 0;
     a.st = c->d_st;
     a.record_only = record_only;
+    Timed tm{c, 2};
+    CK(tm.begin());
     CK(launch_perturb(a, c->perturb_cluster, c->stream));
+    CK(tm.end());
     note_launch(c);
     return SUPPY_OK;
 }
@@ -341,35 +435,40 @@ suppy_status read_flags(suppy_ctx* c, int* d_flags, int* h_flags, int count) {
     return SUPPY_OK;
 }
 
-// Choose rows-per-group and registers-held chunks from the row-length mix.
-void choose_shape(suppy_ctx* c, double mean_len, int max_len) {
-    if (c->B > 1) {
-        c->G = 32;
-        c->maxch = 0;
-        return;
-    }
+// Launch shape of the row pass from the row-length mix: lanes per row and the
+// row elements a lane keeps in registers between the dot product and the
+// scatter (rows longer than G*maxe stream their tail twice).
+void choose_row_shape(suppy_ctx* c, double mean_len, int max_len) {
     if (mean_len >= 192) c->G = 32;
     else if (mean_len >= 64) c->G = 16;
     else if (mean_len >= 20) c->G = 8;
     else c->G = 4;
-    const int per = 4 * c->G;
-    int need = (max_len + per - 1) / per;
-    if (c->G == 32) c->maxch = need <= 2 ? 2 : (need <= 4 ? 4 : 8);
-    else if (c->G == 4) c->maxch = 2;
-    else c->maxch = need <= 2 ? 2 : 4;
+    const int need = (max_len + c->G - 1) / c->G;
+    if (c->strategy == 2) c->maxe = 8;           // no scatter: registers only buffer loads
+    else if (c->G == 32) c->maxe = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
+    else if (c->G == 4) c->maxe = 8;
+    else c->maxe = need <= 8 ? 8 : 16;
 }
 
-suppy_status build_partition(suppy_ctx* c, const std::vector<long long>& pref) {
+void choose_col_shape(suppy_ctx* c, double mean_col) {
+    if (mean_col >= 128) c->Gc = 32;
+    else if (mean_col >= 48) c->Gc = 16;
+    else if (mean_col >= 12) c->Gc = 8;
+    else c->Gc = 4;
+}
+
+suppy_status build_row_partition(suppy_ctx* c) {
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-    int bps = sweep_blocks_per_sm(c->dt, c->G, c->maxch, c->B);
+    const int scat = (c->strategy == 2) ? 0 : c->scat;
+    int bps = sweep_blocks_per_sm(c->dt, c->G, c->maxe, scat, c->B, c->n);
     if (bps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the chosen sweep shape");
     c->grid_sweep = sms * bps;
     const int gpc = (c->B > 1) ? kSweepThreads / 32 : kSweepThreads / c->G;
     c->groups = c->grid_sweep * gpc;
     std::vector<int> part((size_t)c->nseg * (c->groups + 1));
     for (int t = 0; t < c->nseg; ++t)
-        partition(pref, c->seg_start[t], c->seg_start[t + 1], c->groups,
+        partition(c->rpref, c->seg_start[t], c->seg_start[t + 1], c->groups,
                   part.data() + (size_t)t * (c->groups + 1));
     if (c->d_part) dfree(c, c->d_part);
     c->d_part = nullptr;
@@ -384,6 +483,151 @@ suppy_status build_partition(suppy_ctx* c, const std::vector<long long>& pref) {
     long long vec4 = ((long long)c->n * c->B + 3) / 4;
     c->grid_fin = (int)std::min<long long>(std::max<long long>((vec4 + 255) / 256, 1), sms * 8LL);
     CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status build_col_partition(suppy_ctx* c) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    int bps = colpass_blocks_per_sm(c->dt, c->Gc, c->B);
+    if (bps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the column pass");
+    c->grid_col = sms * bps;
+    const int gpc = (c->B > 1) ? kSweepThreads / 32 : kSweepThreads / c->Gc;
+    c->cgroups = c->grid_col * gpc;
+    std::vector<int> part((size_t)c->nseg * (c->cgroups + 1));
+    std::vector<long long> pref(c->n + 1);
+    for (int t = 0; t < c->nseg; ++t) {
+        std::copy(c->cpref.begin() + (size_t)t * (c->n + 1),
+                  c->cpref.begin() + (size_t)(t + 1) * (c->n + 1), pref.begin());
+        partition(pref, 0, c->n, c->cgroups, part.data() + (size_t)t * (c->cgroups + 1));
+    }
+    if (c->d_cpart) dfree(c, c->d_cpart);
+    c->d_cpart = nullptr;
+    suppy_status s = dalloc(c, &c->d_cpart, part.size());
+    if (s != SUPPY_OK) return s;
+    CK(cudaMemcpyAsync(c->d_cpart, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+// CSC copy of the packed rows, one column range per block: a stable counting
+// sort by column on the host (rows stay in device order inside a column) gives
+// each CSR entry its CSC position; the device scatters rows and stored values.
+suppy_status build_csc(suppy_ctx* c, const std::vector<int>& rp, const int* hcol,
+                       const std::vector<int>& perm, const std::vector<int>& seg_of_row,
+                       const std::vector<int2>& rinfo) {
+    const int m = c->m, n = c->n, nseg = c->nseg;
+    const size_t cells = (size_t)nseg * n;
+    std::vector<long long> cnt(cells + 1, 0);
+    for (int i = 0; i < m; ++i) {
+        const int src = perm.empty() ? i : perm[i];
+        const size_t base = (size_t)(seg_of_row.empty() ? 0 : seg_of_row[i]) * n;
+        for (int e = rp[src]; e < rp[src + 1]; ++e) cnt[base + hcol[e]]++;
+    }
+    std::vector<int2> cinfo(cells);
+    c->cpref.assign((size_t)nseg * (n + 1), 0);
+    long long off = 0;
+    for (size_t k = 0; k < cells; ++k) {
+        cinfo[k] = make_int2((int)off, (int)cnt[k]);
+        const int t = (int)(k / n), j = (int)(k % n);
+        long long* pr = c->cpref.data() + (size_t)t * (n + 1);
+        pr[j + 1] = pr[j] + cnt[k] + 8;     // column work: entries plus a fixed cost
+        cnt[k] = off;                       // becomes the cursor
+        off += cinfo[k].y;
+    }
+    c->nnz_csc = off;
+    std::vector<int> pos((size_t)std::max<long long>(c->nnz, 1));
+    for (int i = 0; i < m; ++i) {
+        const int src = perm.empty() ? i : perm[i];
+        const size_t base = (size_t)(seg_of_row.empty() ? 0 : seg_of_row[i]) * n;
+        int d = rinfo[i].x;
+        for (int e = rp[src]; e < rp[src + 1]; ++e, ++d) pos[d] = (int)(cnt[base + hcol[e]]++);
+    }
+    const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
+    suppy_status s;
+    if ((s = dalloc(c, &c->d_cinfo, cells)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_ridx, (size_t)c->nnz)) != SUPPY_OK) return s;
+    {
+        char* q = nullptr;
+        if ((s = dalloc(c, &q, (size_t)std::max<long long>(c->nnz, 1) * vsz)) != SUPPY_OK) return s;
+        c->d_cval = q;
+    }
+    if ((s = dalloc(c, &c->d_coef, (size_t)std::max(m, 1) * c->B)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_coef, 0, sizeof(float) * (size_t)std::max(m, 1) * c->B, c->stream));
+    CK(cudaMemcpyAsync(c->d_cinfo, cinfo.data(), sizeof(int2) * cells, cudaMemcpyHostToDevice,
+                       c->stream));
+    int* d_pos = nullptr;
+    CK(cudaMalloc(&d_pos, sizeof(int) * pos.size()));
+    cudaError_t e = cudaMemcpyAsync(d_pos, pos.data(), sizeof(int) * pos.size(),
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_csc_fill(c->d_rinfo, m, c->d_val, c->dt, d_pos, c->d_ridx, c->d_cval, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_pos);
+    if (e != cudaSuccess)
+        return fail(c, SUPPY_ECUDA, std::string("building the CSC copy: ") + cudaGetErrorString(e));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+void free_csc(suppy_ctx* c) {
+    dfree(c, c->d_cinfo);
+    dfree(c, c->d_ridx);
+    dfree(c, c->d_cval);
+    dfree(c, c->d_coef);
+    dfree(c, c->d_cpart);
+    c->d_cinfo = nullptr;
+    c->d_ridx = nullptr;
+    c->d_cval = nullptr;
+    c->d_coef = nullptr;
+    c->d_cpart = nullptr;
+    c->nnz_csc = 0;
+    c->cpref.clear();
+    c->cpref.shrink_to_fit();
+}
+
+// Time a few sweeps of the current configuration on a scratch copy of the
+// iterate and state (restored afterwards).
+suppy_status time_config(suppy_ctx* c, float* ms_out) {
+    suppy_params p;
+    suppy_params_default(&p);
+    const size_t nB = (size_t)c->n * c->B;
+    float* xs = nullptr;
+    CK(cudaMalloc(&xs, sizeof(float) * nB));
+    std::vector<RhsState> st(c->B);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemcpyAsync(xs, c->d_x, sizeof(float) * nB, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    suppy_status s = SUPPY_OK;
+    const bool was_timing = c->timing;
+    c->timing = false;
+    const int k_up = c->k_upper;
+    if (e == cudaSuccess) s = enqueue_sweep(c, &p);
+    if (e == cudaSuccess && s == SUPPY_OK) e = cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < 3 && e == cudaSuccess && s == SUPPY_OK; ++k) s = enqueue_sweep(c, &p);
+    if (e == cudaSuccess && s == SUPPY_OK) e = cudaEventRecord(e1, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    float ms = 0.f;
+    if (e == cudaSuccess && s == SUPPY_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_x, xs, sizeof(float) * nB, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->d_delta)
+        e = cudaMemsetAsync(c->d_delta, 0, sizeof(float) * nB, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->timing = was_timing;
+    c->k_upper = k_up;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(xs);
+    if (s != SUPPY_OK) return s;
+    if (e != cudaSuccess) return fail(c, SUPPY_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
+    *ms_out = ms / 3.f;
     return SUPPY_OK;
 }
 
@@ -472,22 +716,19 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         c->seg_start = {0, m};
     }
 
-    // padded row layout in device order
+    // row layout in device order (rows of a block contiguous)
     std::vector<int2> rinfo(m);
-    std::vector<long long> pref(m + 1, 0);
+    c->rpref.assign(m + 1, 0);
     long long off = 0;
     int max_len = 0;
     for (int i = 0; i < m; ++i) {
         const int src = perm.empty() ? i : perm[i];
         const int len = rp[src + 1] - rp[src];
-        const int padded = (len + 3) & ~3;
         rinfo[i] = make_int2((int)off, len);
-        off += padded;
-        pref[i + 1] = off;
+        off += len;
+        c->rpref[i + 1] = off;
         max_len = std::max(max_len, len);
     }
-    if (off >= (1LL << 31)) return fail(c, SUPPY_EINVAL, "padded nnz must be below 2^31");
-    c->nnz_pad = off;
 
     TempGuard tg;
     tg.s = c->stream;
@@ -528,10 +769,10 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     // ---- packed matrix, row norms, weights
     const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
     if ((s = dalloc(c, &c->d_rinfo, (size_t)m)) != SUPPY_OK) return s;
-    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz_pad + 16)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz + 16)) != SUPPY_OK) return s;
     {
         char* q = nullptr;
-        if ((s = dalloc(c, &q, ((size_t)c->nnz_pad + 16) * vsz)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &q, ((size_t)c->nnz + 16) * vsz)) != SUPPY_OK) return s;
         c->d_val = q;
     }
     if ((s = dalloc(c, &c->d_rho, (size_t)m)) != SUPPY_OK) return s;
@@ -646,12 +887,60 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         }
     }
 
-    // ---- launch shape and partition
-    const double mean_len = m > 0 ? (double)A->nnz / m : 0.0;
-    choose_shape(c, mean_len, max_len);
-    if ((s = build_partition(c, pref)) != SUPPY_OK) return s;
+    // ---- sweep strategy, launch shapes, partitions (K9 autotuner when tune)
     c->perturb_cluster = fit_perturb_cluster(choose_perturb_cluster(n, c->B));
     if ((s = ensure_hist(c, 1024)) != SUPPY_OK) return s;
+    if ((s = reset_state(c)) != SUPPY_OK) return s;
+    const double mean_len = m > 0 ? (double)A->nnz / m : 0.0;
+    const double mean_col = (double)A->nnz / n / c->nseg;
+    const bool smem_ok = (c->B == 1) && (size_t)n * sizeof(float) <= 64 * 1024;
+    const int want = o->strategy;
+    if (want < 0 || want > 2) return fail(c, SUPPY_EINVAL, "unknown strategy");
+    const bool need_csc = (want == 2) || (want == 0 && (o->tune || !smem_ok));
+    if (need_csc) {
+        std::vector<int> hcol_buf;
+        const int* hcol = A->col;
+        if (on_dev) {
+            hcol_buf.resize((size_t)std::max<long long>(A->nnz, 1));
+            if (A->nnz)
+                CK(cudaMemcpyAsync(hcol_buf.data(), A->col, sizeof(int) * A->nnz,
+                                   cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            hcol = hcol_buf.data();
+        }
+        if ((s = build_csc(c, rp, hcol, perm, seg_of_row, rinfo)) != SUPPY_OK) return s;
+        choose_col_shape(c, mean_col);
+        if ((s = build_col_partition(c)) != SUPPY_OK) return s;
+    }
+    struct Cand {
+        int strategy, scat;
+    };
+    std::vector<Cand> cands;
+    if (want != 2) cands.push_back({1, smem_ok ? 2 : 1});
+    if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1});
+    if (need_csc) cands.push_back({2, 0});
+    Cand best = cands[0];
+    if (want == 0 && !o->tune) best = smem_ok ? Cand{1, 2} : Cand{2, 0};
+    if (o->tune && cands.size() > 1) {
+        float best_ms = 1e30f;
+        for (const Cand& cd : cands) {
+            c->strategy = cd.strategy;
+            c->scat = cd.scat;
+            choose_row_shape(c, mean_len, max_len);
+            if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+            float ms = 0.f;
+            if ((s = time_config(c, &ms)) != SUPPY_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cd;
+            }
+        }
+    }
+    c->strategy = best.strategy;
+    c->scat = best.scat;
+    choose_row_shape(c, mean_len, max_len);
+    if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+    if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
     CK(cudaStreamSynchronize(c->stream));
@@ -662,9 +951,9 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
 void destroy_impl(suppy_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
-    for (auto& pr : c->evs) {
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+    for (auto& t : c->evs) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
     }
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_out) cudaFreeHost(c->h_out);
@@ -824,27 +1113,11 @@ suppy_status suppy_proximity(suppy_ctx* c, double* out) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
     for (int t = 0; t < c->nseg; ++t) {
-        SweepArgs a;
-        a.rinfo = c->d_rinfo;
-        a.col = c->d_col;
-        a.val = c->d_val;
-        a.l = c->d_l;
-        a.u = c->d_u;
-        a.wr = c->d_wr;
-        a.x = c->d_x;
-        a.delta = c->d_delta;
-        a.part = c->d_part + (size_t)t * (c->groups + 1);
-        a.pp = c->d_pp;
-        a.st = c->d_st;
-        a.lam = 0.f;
-        a.B = c->B;
-        a.scatter = 0;
+        SweepArgs a = row_args(c, t, 0.f);
         a.check_stop = 0;
-        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxch, c->grid_sweep, c->stream));
-        else CK(launch_sweep_batched(a, c->dt, 32, c->grid_sweep, c->stream));
-        double scale = 0.5;
-        if (c->nseg > 1) scale = c->m_kept > 0 ? 0.5 * (double)c->seg_kept[t] / c->m_kept : 0.0;
-        CK(launch_reduce_pp(c->d_pp, c->grid_sweep, c->B, scale, t > 0, c->d_out, c->stream));
+        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, 0, c->grid_sweep, c->stream));
+        else CK(launch_sweep_batched(a, c->dt, 0, c->grid_sweep, c->stream));
+        CK(launch_reduce_pp(c->d_pp, c->grid_sweep, c->B, seg_scale(c, t), t > 0, c->d_out, c->stream));
         note_launch(c, 2);
     }
     CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
@@ -997,14 +1270,18 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->nrhs = c->B_user;
     out->m_kept = c->m_kept;
     out->nnz = c->nnz;
-    out->nnz_padded = c->nnz_pad;
+    out->nnz_csc = c->nnz_csc;
     out->nblocks = c->nseg;
     out->lanes_per_row = c->G;
-    out->chunks_in_regs = c->maxch;
+    out->elems_in_regs = c->maxe;
     out->grid = c->grid_sweep;
     out->block = kSweepThreads;
     out->perturb_cluster = c->perturb_cluster;
     out->device_bytes = (int64_t)c->dev_bytes;
+    out->strategy = c->strategy;
+    out->scatter = c->strategy == 1 ? c->scat : 0;
+    out->col_lanes = c->strategy == 2 ? c->Gc : 0;
+    out->col_grid = c->strategy == 2 ? c->grid_col : 0;
     return SUPPY_OK;
 }
 
@@ -1013,17 +1290,20 @@ suppy_status suppy_timing_enable(suppy_ctx* c, int32_t enable) {
     suppy_status s = flush_timing(c);
     if (s != SUPPY_OK) return s;
     c->timing = enable != 0;
-    c->timing_ms = 0.0;
-    c->timing_n = 0;
+    for (int k = 0; k < 3; ++k) {
+        c->timing_ms[k] = 0.0;
+        c->timing_n[k] = 0;
+    }
     return SUPPY_OK;
 }
 
-suppy_status suppy_kernel_time(suppy_ctx* c, double* total_ms, int64_t* launches) {
+suppy_status suppy_kernel_time(suppy_ctx* c, int32_t kind, double* total_ms, int64_t* launches) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (kind < 0 || kind > 2) return fail(c, SUPPY_EINVAL, "kernel kind must be 0, 1 or 2");
     suppy_status s = flush_timing(c);
     if (s != SUPPY_OK) return s;
-    if (total_ms) *total_ms = c->timing_ms;
-    if (launches) *launches = c->timing_n;
+    if (total_ms) *total_ms = c->timing_ms[kind];
+    if (launches) *launches = c->timing_n[kind];
     return SUPPY_OK;
 }
 

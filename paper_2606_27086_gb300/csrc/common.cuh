@@ -41,23 +41,39 @@ struct StopParams {
     int has_obj;
 };
 
-// One launch of the fused sweep over rows [part[0], part[ngroups]).
+// One launch of the row pass over rows [part[0], part[ngroups]).
 struct SweepArgs {
-    const int2* rinfo;      // per row: {padded start, length}
-    const int* col;         // padded column indices
-    const void* val;        // padded values (float / bf16 / half)
+    const int2* rinfo;      // per row: {start, length}
+    const int* col;         // column indices
+    const void* val;        // values (float / bf16 / half)
     const float* l;         // m x B bounds (device row order)
     const float* u;
     const float* wr;        // w_i / ||a_i||^2 (0 for dropped rows)
-    const float* x;         // n x B iterate (read only during the sweep)
-    float* delta;           // n x B correction accumulator (zero on entry)
+    const float* x;         // n x B iterate (read only during the pass)
+    float* delta;           // n x B correction accumulator (one-pass scatter)
+    float* coef;            // m x B correction coefficients (two-pass) or null
     const int* part;        // group boundaries (ngroups + 1 absolute row indices)
     double* pp;             // proximity partials: pp[cta * B + b]
     RhsState* st;
     float lam;
     int B;                  // right-hand sides in the device layout
-    int scatter;            // 0: proximity only (no correction)
+    int n;                  // unknowns (shared-memory staging size)
     int check_stop;         // 1: skip the launch when right-hand side 0 has stopped (B = 1)
+};
+
+// Epilogue of a sweep (CTA 0 of the finalize / column pass): fixed-order
+// reduction of the row-pass proximity partials, history, stopping rule.
+struct EpiArgs {
+    const double* pp;
+    int npp;                // CTAs that wrote partials
+    int B;
+    double scale;           // factor applied to the partial sums (1/2 and block weight ratio)
+    RhsState* st;
+    double* prox_hist;      // [B][hist_cap]
+    double* obj_hist;
+    int hist_cap;
+    int first_seg, last_seg;
+    StopParams sp;
 };
 
 struct FinalizeArgs {
@@ -68,15 +84,23 @@ struct FinalizeArgs {
     long long nB;           // n * B elements
     int B;
     int box_len;            // 1 or n
-    const double* pp;
-    int npp;                // CTAs that wrote partials
-    double scale;           // factor applied to the partial sums (1/2 and block weight ratio)
-    RhsState* st;
-    double* prox_hist;      // [B][hist_cap]
-    double* obj_hist;
-    int hist_cap;
-    int first_seg, last_seg;
-    StopParams sp;
+    EpiArgs epi;
+};
+
+// Column pass of the two-pass sweep: x_j <- box(x_j + sum_i a_ij coef_i)
+// over the columns [cpart[0], cpart[ngroups]) of one block's CSC.
+struct ColArgs {
+    const int2* cinfo;      // per column: {start, length}
+    const int* ridx;        // device row index of each entry
+    const void* cval;       // values (same storage type as the rows)
+    const float* coef;      // m x B
+    float* x;               // n x B
+    const float* lo;
+    const float* hi;
+    int box_len;
+    int B;
+    const int* cpart;
+    EpiArgs epi;
 };
 
 struct PerturbArgs {
@@ -99,11 +123,16 @@ struct ObjArgs {
 };
 
 // --- launchers (defined in sweep.cu / perturb.cu / setup.cu) ---------------
-cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxch, int grid,
+// scat: 0 no scatter (proximity / coefficient output), 1 global reductions,
+// 2 shared-memory staged reductions (n * 4 bytes of shared memory)
+cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,
                          cudaStream_t s);
-cudaError_t launch_sweep_batched(const SweepArgs& a, suppy_dtype dt, int G, int grid,
+cudaError_t launch_sweep_batched(const SweepArgs& a, suppy_dtype dt, int scat, int grid,
                                  cudaStream_t s);
-int sweep_blocks_per_sm(suppy_dtype dt, int G, int maxch, int batchedB);
+int sweep_blocks_per_sm(suppy_dtype dt, int G, int maxe, int scat, int batchedB, int n);
+cudaError_t launch_colpass(const ColArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s);
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
+int colpass_blocks_per_sm(suppy_dtype dt, int G, int B);
 cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                              double* out, cudaStream_t s);
@@ -121,6 +150,8 @@ cudaError_t launch_validate_pair(const float* lo, const float* hi, long long len
 cudaError_t launch_pack(const int* row_ptr, const int* col, const float* val, const int* perm,
                         const int2* rinfo, int m, int* pcol, void* pval, suppy_dtype dt,
                         double* rho, cudaStream_t s);
+cudaError_t launch_csc_fill(const int2* rinfo, int m, const void* pval, suppy_dtype dt,
+                            const int* pos, int* ridx, void* cval, cudaStream_t s);
 cudaError_t launch_count_kept(const double* rho, const int* seg_of_row, int m, int* kept,
                               cudaStream_t s);
 cudaError_t launch_weights(const double* rho, const int* seg_of_row, const double* seg_w, int m,

@@ -1,4 +1,4 @@
-// Setup kernels: input validation, packing A into the padded device layout
+// Setup kernels: input validation, packing A into the device layout
 // (values converted to the storage dtype), FP64 row norms ||a_i||^2 (the
 // denominator of Eq. (2)), kept-row counts and the weights w_i / ||a_i||^2 of
 // the simultaneous or block-iterative step (Sec. 2.1.1), the zero-row check,
@@ -68,8 +68,8 @@ template <>
 __device__ __forceinline__ float from_store<__half>(__half v) { return __half2float(v); }
 
 // One warp per device row i (source row perm[i]): copy columns, convert
-// values, pad to a multiple of 4 with (last column, 0), and accumulate the
-// FP64 squared norm of the stored values.
+// values to the storage type, and accumulate the FP64 squared norm of the
+// stored values.
 template <typename VT>
 __global__ void k_pack(const int* rp, const int* col, const float* val, const int* perm,
                        const int2* rinfo, int m, int* pcol, VT* pval, double* rho) {
@@ -79,23 +79,34 @@ __global__ void k_pack(const int* rp, const int* col, const float* val, const in
         const int src = perm ? perm[i] : i;
         const int a = rp[src], len = rp[src + 1] - a;
         const int2 ri = rinfo[i];
-        const int padded = (len + 3) & ~3;
-        const int lastc = len > 0 ? col[a + len - 1] : 0;
         double s = 0.0;
-        for (int e = lane; e < padded; e += 32) {
-            if (e < len) {
-                const VT v = to_store<VT>(val[a + e]);
-                pcol[ri.x + e] = col[a + e];
-                pval[ri.x + e] = v;
-                const double f = (double)from_store<VT>(v);
-                s += f * f;
-            } else {
-                pcol[ri.x + e] = lastc;
-                pval[ri.x + e] = to_store<VT>(0.f);
-            }
+        for (int e = lane; e < len; e += 32) {
+            const VT v = to_store<VT>(val[a + e]);
+            pcol[ri.x + e] = col[a + e];
+            pval[ri.x + e] = v;
+            const double f = (double)from_store<VT>(v);
+            s += f * f;
         }
         s = warp_sum(s);
         if (lane == 0) rho[i] = s;
+    }
+}
+
+// CSC copy of the packed rows: entry e of device row i goes to position
+// pos[e] (a stable counting sort by column computed on the host), carrying
+// its row index and its stored value.
+template <typename VT>
+__global__ void k_csc_fill(const int2* rinfo, int m, const VT* pval, const int* pos, int* ridx,
+                           VT* cval) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+        const int2 ri = rinfo[i];
+        for (int e = lane; e < ri.y; e += 32) {
+            const int p = pos[ri.x + e];
+            ridx[p] = i;
+            cval[p] = pval[ri.x + e];
+        }
     }
 }
 
@@ -261,6 +272,22 @@ cudaError_t launch_pack(const int* row_ptr, const int* col, const float* val, co
     else
         k_pack<__half><<<grid, 256, 0, s>>>(row_ptr, col, val, perm, rinfo, m, pcol,
                                             static_cast<__half*>(pval), rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csc_fill(const int2* rinfo, int m, const void* pval, suppy_dtype dt,
+                            const int* pos, int* ridx, void* cval, cudaStream_t s) {
+    const int grid = grid_for((long long)m * 32);
+    if (dt == SUPPY_F32)
+        k_csc_fill<float><<<grid, 256, 0, s>>>(rinfo, m, static_cast<const float*>(pval), pos, ridx,
+                                               static_cast<float*>(cval));
+    else if (dt == SUPPY_BF16)
+        k_csc_fill<__nv_bfloat16><<<grid, 256, 0, s>>>(
+            rinfo, m, static_cast<const __nv_bfloat16*>(pval), pos, ridx,
+            static_cast<__nv_bfloat16*>(cval));
+    else
+        k_csc_fill<__half><<<grid, 256, 0, s>>>(rinfo, m, static_cast<const __half*>(pval), pos,
+                                                ridx, static_cast<__half*>(cval));
     return cudaGetLastError();
 }
 

@@ -1,16 +1,18 @@
-// Fused one-pass CSR hyperslab sweep (the simultaneous projection step of
-// Sec. 2.1.1 with the relaxation of Eq. (3)), its finalize step (box of
-// Sec. 2.3.3) and the deterministic second-level proximity reduction
-// (Eq. (WeightedProximity)).
+// Simultaneous hyperslab projection sweep (Sec. 2.1.1 with the relaxation of
+// Eq. (3)) and its finalize step (box of Sec. 2.3.3), with the deterministic
+// FP64 proximity of Eq. (WeightedProximity) fused in.
 //
-// For every row i a group of G lanes streams a_i once from HBM with 128-bit
-// loads (L1 bypass, L2 evict-first), forms r_i = <a_i, x> with an in-group
-// shuffle reduction, computes d_i = clamp(r_i, l_i, u_i) - r_i and the
-// correction coefficient lambda * w_i / ||a_i||^2 * d_i, and scatter-adds
-// coef * a_i into delta with fire-and-forget L2 reductions -- reusing the row
-// held in registers, so A crosses HBM once per sweep.  The proximity term
-// w_i d_i^2 / ||a_i||^2 of the sweep's input point is accumulated in FP64 in a
-// fixed order (per group, per CTA, then across CTAs in the finalize kernel).
+// Two strategies share the row pass:
+//  * one-pass: a group of G lanes streams row a_i once from HBM (lane-strided,
+//    fully coalesced loads, L1 bypass, L2 evict-first), keeps it in registers,
+//    forms r_i = <a_i, x> with an in-group shuffle tree, computes
+//    coef_i = lambda w_i (clamp(r_i, l_i, u_i) - r_i) / ||a_i||^2 and
+//    scatter-adds coef_i * a_i into delta -- with global L2 reductions whose
+//    lanes hit consecutive columns (address-coalesced), or staged in shared
+//    memory when delta fits there -- then the finalize kernel applies the box;
+//  * two-pass: the row pass writes coef_i only; a column pass streams the CSC
+//    copy of A and computes x_j <- box(x_j + sum_i a_ij coef_i) with gathers
+//    of coef from L2, no atomics at all (bitwise deterministic).
 #include "common.cuh"
 
 namespace suppy {
@@ -22,66 +24,31 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     return p;
 }
 
-__device__ __forceinline__ int4 ld_stream_i4(const int* ptr, uint64_t pol) {
-    int4 v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.s32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-        : "l"(ptr), "l"(pol));
+__device__ __forceinline__ int ld_stream_i(const int* ptr, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
     return v;
 }
 
 template <typename VT>
-struct ValLoad;
-
+__device__ __forceinline__ float ld_stream_v(const VT* ptr, uint64_t pol);
 template <>
-struct ValLoad<float> {
-    static __device__ __forceinline__ float4 load4(const float* ptr, uint64_t pol) {
-        float4 v;
-        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-            : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-            : "l"(ptr), "l"(pol));
-        return v;
-    }
-};
-
-template <>
-struct ValLoad<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 load4(const __nv_bfloat16* ptr, uint64_t pol) {
-        uint32_t a, b;
-        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;"
-            : "=r"(a), "=r"(b)
-            : "l"(ptr), "l"(pol));
-        // bf16 -> fp32 is exact: the bf16 bits are the high half of the fp32
-        return make_float4(__uint_as_float(a << 16), __uint_as_float(a & 0xffff0000u),
-                           __uint_as_float(b << 16), __uint_as_float(b & 0xffff0000u));
-    }
-};
-
-template <>
-struct ValLoad<__half> {
-    static __device__ __forceinline__ float4 load4(const __half* ptr, uint64_t pol) {
-        uint32_t a, b;
-        asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b32 {%0,%1}, [%2], %3;"
-            : "=r"(a), "=r"(b)
-            : "l"(ptr), "l"(pol));
-        __half2 ha = *reinterpret_cast<__half2*>(&a), hb = *reinterpret_cast<__half2*>(&b);
-        float2 fa = __half22float2(ha), fb = __half22float2(hb);
-        return make_float4(fa.x, fa.y, fb.x, fb.y);
-    }
-};
-
-// Scalar value load through L1 (the batched kernel re-reads its row).
-template <typename VT>
-__device__ __forceinline__ float ld_val(const VT* p) {
-    return __ldg(p);
+__device__ __forceinline__ float ld_stream_v<float>(const float* ptr, uint64_t pol) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(ptr), "l"(pol));
+    return v;
 }
 template <>
-__device__ __forceinline__ float ld_val<__nv_bfloat16>(const __nv_bfloat16* p) {
-    return __bfloat162float(__ldg(p));
+__device__ __forceinline__ float ld_stream_v<__nv_bfloat16>(const __nv_bfloat16* ptr, uint64_t pol) {
+    unsigned short h;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(h) : "l"(ptr), "l"(pol));
+    return __uint_as_float(((uint32_t)h) << 16);   // exact widening
 }
 template <>
-__device__ __forceinline__ float ld_val<__half>(const __half* p) {
-    return __half2float(__ldg(p));
+__device__ __forceinline__ float ld_stream_v<__half>(const __half* ptr, uint64_t pol) {
+    unsigned short h;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(h) : "l"(ptr), "l"(pol));
+    return __half2float(__ushort_as_half(h));
 }
 
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
@@ -90,98 +57,15 @@ __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, 
                  : "memory");
 }
 
-// ---------------------------------------------------------------- B = 1 ----
-// G lanes per row (4..32), up to MAXCH chunks of 4*G elements held in
-// registers between the dot product and the scatter; longer rows stream their
-// remaining chunks twice (the second read hits L2).
-template <typename VT, int G, int MAXCH>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
-    if (a.check_stop && a.st[0].stopped) return;
-    const int lane = threadIdx.x & (G - 1);
-    const unsigned gmask =
-        (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
-    const int grp = (blockIdx.x * kSweepThreads + threadIdx.x) / G;
-    const int rb = a.part[grp], re = a.part[grp + 1];
-    const uint64_t pol = policy_evict_first();
-    const VT* __restrict__ val = static_cast<const VT*>(a.val);
-    const int* __restrict__ colp = a.col;
-    const float* __restrict__ x = a.x;
-    float* __restrict__ delta = a.delta;
-    double prox = 0.0;
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) return 0xffffffffu;
+    else return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+}
 
-    for (int i = rb; i < re; ++i) {
-        const int2 ri = a.rinfo[i];
-        const int len = ri.y;
-        if (len == 0) continue;
-        const VT* vrow = val + ri.x;
-        const int* crow = colp + ri.x;
-        const int nch = (len + 4 * G - 1) / (4 * G);
-        float4 v[MAXCH];
-        int4 c[MAXCH];
-#pragma unroll
-        for (int k = 0; k < MAXCH; ++k) {
-            const int e = k * 4 * G + 4 * lane;
-            if (k < nch && e < len) {
-                v[k] = ValLoad<VT>::load4(vrow + e, pol);
-                c[k] = ld_stream_i4(crow + e, pol);
-            } else {
-                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                c[k] = make_int4(0, 0, 0, 0);
-            }
-        }
-        float dot = 0.f;
-#pragma unroll
-        for (int k = 0; k < MAXCH; ++k) {
-            if (k < nch) {
-                dot = fmaf(v[k].x, __ldg(x + c[k].x), dot);
-                dot = fmaf(v[k].y, __ldg(x + c[k].y), dot);
-                dot = fmaf(v[k].z, __ldg(x + c[k].z), dot);
-                dot = fmaf(v[k].w, __ldg(x + c[k].w), dot);
-            }
-        }
-        for (int k = MAXCH; k < nch; ++k) {
-            const int e = k * 4 * G + 4 * lane;
-            if (e < len) {
-                const float4 vv = ValLoad<VT>::load4(vrow + e, pol);
-                const int4 cc = ld_stream_i4(crow + e, pol);
-                dot = fmaf(vv.x, __ldg(x + cc.x), dot);
-                dot = fmaf(vv.y, __ldg(x + cc.y), dot);
-                dot = fmaf(vv.z, __ldg(x + cc.z), dot);
-                dot = fmaf(vv.w, __ldg(x + cc.w), dot);
-            }
-        }
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gmask, dot, o);
-
-        const float d = clampf(dot, a.l[i], a.u[i]) - dot;
-        const float w = a.wr[i];
-        if (lane == 0) prox += (double)d * (double)d * (double)w;
-        const float coef = a.lam * w * d;
-        if (a.scatter && coef != 0.f) {
-#pragma unroll
-            for (int k = 0; k < MAXCH; ++k) {
-                const int e = k * 4 * G + 4 * lane;
-                if (k < nch && e < len) {
-                    atomicAdd(delta + c[k].x, coef * v[k].x);
-                    if (e + 1 < len) atomicAdd(delta + c[k].y, coef * v[k].y);
-                    if (e + 2 < len) atomicAdd(delta + c[k].z, coef * v[k].z);
-                    if (e + 3 < len) atomicAdd(delta + c[k].w, coef * v[k].w);
-                }
-            }
-            for (int k = MAXCH; k < nch; ++k) {
-                const int e = k * 4 * G + 4 * lane;
-                if (e < len) {
-                    const float4 vv = ValLoad<VT>::load4(vrow + e, pol);
-                    const int4 cc = ld_stream_i4(crow + e, pol);
-                    atomicAdd(delta + cc.x, coef * vv.x);
-                    if (e + 1 < len) atomicAdd(delta + cc.y, coef * vv.y);
-                    if (e + 2 < len) atomicAdd(delta + cc.z, coef * vv.z);
-                    if (e + 3 < len) atomicAdd(delta + cc.w, coef * vv.w);
-                }
-            }
-        }
-    }
-    // deterministic CTA partial: warp tree, then warps in order
+// Per-CTA proximity partial: lane 0 of each group holds its sum; warp tree,
+// then warps in order.
+__device__ __forceinline__ void cta_partial(double prox, double* out) {
     prox = warp_sum(prox);
     __shared__ double sw[kSweepThreads / 32];
     if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = prox;
@@ -190,17 +74,149 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < kSweepThreads / 32; ++w) s += sw[w];
-        a.pp[blockIdx.x] = s;
+        *out = s;
     }
 }
 
-// -------------------------------------------------------------- B = 4Q ----
+// Epilogue: CTA 0, warp w handles right-hand sides w, w+8, ...
+__device__ void sweep_epilogue(const EpiArgs& a) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = wid; b < a.B; b += blockDim.x / 32) {
+        double s = 0.0;
+        for (int c = lane; c < a.npp; c += 32) s += a.pp[(size_t)c * a.B + b];
+        s = warp_sum(s);
+        if (lane != 0) continue;
+        RhsState& st = a.st[b];
+        if (st.stopped) continue;
+        if (a.first_seg) st.p_acc = 0.0;
+        st.p_acc += a.scale * s;
+        if (!a.last_seg) continue;
+        const double p = st.p_acc;
+        const int k = st.k;
+        if (k < a.hist_cap) {
+            a.prox_hist[(size_t)b * a.hist_cap + k] = p;
+            a.obj_hist[(size_t)b * a.hist_cap + k] =
+                st.f_valid ? st.f_cur : __longlong_as_double(0x7ff8000000000000LL);
+        }
+        // stopping rule (Sec. 2.2.1 and 2.2.3)
+        if (st.has_prev_p && fabs(p - st.p_prev) / fmax(1.0, st.p_prev) < a.sp.prox_rel)
+            st.calm += 1;
+        else
+            st.calm = 0;
+        const bool feas = (p <= a.sp.prox_abs) || (st.calm >= a.sp.patience);
+        bool objok = true;
+        if (a.sp.has_obj && a.sp.obj_rel > 0.0 && st.f_valid) {
+            objok = st.has_prev_f &&
+                    fabs(st.f_cur - st.f_prev) / fmax(1.0, fabs(st.f_prev)) < a.sp.obj_rel;
+        }
+        st.p_prev = p;
+        st.has_prev_p = 1;
+        if (st.f_valid) {
+            st.f_prev = st.f_cur;
+            st.has_prev_f = 1;
+        }
+        st.f_valid = 0;
+        st.last_prox = p;
+        st.k = k + 1;
+        if (a.sp.use_stopping && feas && objok) st.stopped = 1;
+    }
+}
+
+// ------------------------------------------------------ row pass, B = 1 ----
+// Lane `lane` of a G-lane group owns elements lane, lane+G, lane+2G, ... of
+// the row; the first MAXE*G elements stay in registers for the scatter.
+// SCAT: 0 none (coefficients / proximity only), 1 global, 2 shared memory.
+template <typename VT, int G, int MAXE, int SCAT>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
+    extern __shared__ float s_delta[];
+    if (a.check_stop && a.st[0].stopped) return;
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    const int grp = (blockIdx.x * kSweepThreads + threadIdx.x) / G;
+    const int rb = a.part[grp], re = a.part[grp + 1];
+    const uint64_t pol = policy_evict_first();
+    const VT* __restrict__ val = static_cast<const VT*>(a.val);
+    const int* __restrict__ colp = a.col;
+    const float* __restrict__ x = a.x;
+    float* __restrict__ delta = (SCAT == 2) ? s_delta : a.delta;
+    if (SCAT == 2) {
+        for (int j = threadIdx.x; j < a.n; j += kSweepThreads) s_delta[j] = 0.f;
+        __syncthreads();
+    }
+    double prox = 0.0;
+
+    for (int i = rb; i < re; ++i) {
+        const int2 ri = a.rinfo[i];
+        const int len = ri.y;
+        if (len == 0) continue;
+        const VT* vrow = val + ri.x;
+        const int* crow = colp + ri.x;
+        const int nk = (len + G - 1) / G;
+        float v[MAXE];
+        int c[MAXE];
+#pragma unroll
+        for (int k = 0; k < MAXE; ++k) {
+            const int e = k * G + lane;
+            if (k < nk && e < len) {
+                v[k] = ld_stream_v<VT>(vrow + e, pol);
+                c[k] = ld_stream_i(crow + e, pol);
+            } else {
+                v[k] = 0.f;
+                c[k] = 0;
+            }
+        }
+        float dot = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXE; ++k)
+            if (k < nk) dot = fmaf(v[k], __ldg(x + c[k]), dot);
+        for (int k = MAXE; k < nk; ++k) {
+            const int e = k * G + lane;
+            if (e < len) dot = fmaf(ld_stream_v<VT>(vrow + e, pol), __ldg(x + ld_stream_i(crow + e, pol)), dot);
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gmask, dot, o);
+
+        const float d = clampf(dot, a.l[i], a.u[i]) - dot;
+        const float w = a.wr[i];
+        if (lane == 0) prox += (double)d * (double)d * (double)w;
+        const float coef = a.lam * w * d;
+        if (SCAT == 0) {
+            if (a.coef && lane == 0) a.coef[i] = coef;
+        } else if (coef != 0.f) {
+#pragma unroll
+            for (int k = 0; k < MAXE; ++k) {
+                const int e = k * G + lane;
+                if (k < nk && e < len) atomicAdd(delta + c[k], coef * v[k]);
+            }
+            for (int k = MAXE; k < nk; ++k) {
+                const int e = k * G + lane;
+                if (e < len)
+                    atomicAdd(delta + ld_stream_i(crow + e, pol), coef * ld_stream_v<VT>(vrow + e, pol));
+            }
+        }
+    }
+    if (SCAT == 2) {
+        // flush the CTA's staged corrections with 128-bit reductions, skipping zeros
+        __syncthreads();
+        const int n4 = a.n >> 2;
+        for (int q = threadIdx.x; q < n4; q += kSweepThreads) {
+            const float4 d4 = reinterpret_cast<const float4*>(s_delta)[q];
+            if (d4.x != 0.f || d4.y != 0.f || d4.z != 0.f || d4.w != 0.f)
+                red_add_v4(a.delta + 4 * q, d4.x, d4.y, d4.z, d4.w);
+        }
+        for (int j = 4 * n4 + threadIdx.x; j < a.n; j += kSweepThreads)
+            if (s_delta[j] != 0.f) atomicAdd(a.delta + j, s_delta[j]);
+    }
+    cta_partial(prox, a.pp + blockIdx.x);
+}
+
+// ------------------------------------------------------ row pass, B = 4Q ----
 // One warp per row; lane = e*Q + q handles element slot e (E = 32/Q slots per
-// pass) and right-hand sides 4q..4q+3, so the Q lanes of one element gather
-// the contiguous 4B floats X[col*B .. col*B+B) with 128-bit loads and scatter
-// them back with 128-bit vector reductions.  The row is streamed from HBM for
-// the dot products and re-read (L1/L2) for the scatter.
-template <typename VT, int Q>
+// pass) and right-hand sides 4q..4q+3: the Q lanes of one element gather the
+// contiguous floats X[col*B .. col*B+B) with 128-bit loads and (one-pass)
+// scatter them back with 128-bit vector reductions.  The row is streamed from
+// HBM for the dot products and re-read through L1 for the scatter.
+template <typename VT, int Q, int SCAT>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs a) {
     constexpr int E = 32 / Q;
     constexpr int B = 4 * Q;
@@ -226,7 +242,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         const int* crow = colp + ri.x;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int e = e0; e < len; e += E) {
-            const float v = ld_val<VT>(vrow + e);
+            const float v = (float)__ldg(vrow + e);
             const int c = __ldg(crow + e);
             const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)c * B) + q);
             acc.x = fmaf(v, xv.x, acc.x);
@@ -257,16 +273,18 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
             cf[t] = live[t] ? a.lam * w * d[t] : 0.f;
             any |= (cf[t] != 0.f);
         }
-        if (a.scatter && any) {
+        if (SCAT == 0) {
+            if (a.coef && e0 == 0)
+                reinterpret_cast<float4*>(a.coef + (size_t)i * B)[q] =
+                    make_float4(cf[0], cf[1], cf[2], cf[3]);
+        } else if (any) {
             for (int e = e0; e < len; e += E) {
-                const float v = ld_val<VT>(vrow + e);
+                const float v = (float)__ldg(vrow + e);
                 const int c = __ldg(crow + e);
-                red_add_v4(D + (size_t)c * B + 4 * q, cf[0] * v, cf[1] * v, cf[2] * v,
-                           cf[3] * v);
+                red_add_v4(D + (size_t)c * B + 4 * q, cf[0] * v, cf[1] * v, cf[2] * v, cf[3] * v);
             }
         }
     }
-    // per-CTA partial per right-hand side, fixed order
     __shared__ double sw[kSweepThreads / 32][B];
     const int wid = threadIdx.x >> 5;
     if (e0 == 0) {
@@ -282,12 +300,96 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
     }
 }
 
+// ---------------------------------------------------------- column pass ----
+// B = 1: a group of G lanes per column j streams its CSC entries and gathers
+// coef from L2; lane 0 applies x_j <- clamp(x_j + sum, lo_j, hi_j).
+template <typename VT, int G>
+__global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
+    // the row pass skipped a stopped system and left no coefficients; the flag
+    // cannot change during this launch (the stopping rule runs in k_epilogue)
+    if (a.epi.st[0].stopped) return;
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    const int grp = (blockIdx.x * kSweepThreads + threadIdx.x) / G;
+    const int jb = a.cpart[grp], je = a.cpart[grp + 1];
+    const uint64_t pol = policy_evict_first();
+    const VT* __restrict__ val = static_cast<const VT*>(a.cval);
+    const float* __restrict__ coef = a.coef;
+    for (int j = jb; j < je; ++j) {
+        const int2 ci = a.cinfo[j];
+        const VT* vcol = val + ci.x;
+        const int* rcol = a.ridx + ci.x;
+        float s = 0.f;
+        for (int e = lane; e < ci.y; e += G)
+            s = fmaf(ld_stream_v<VT>(vcol + e, pol), __ldg(coef + ld_stream_i(rcol + e, pol)), s);
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
+        if (lane == 0 && ci.y > 0) {
+            const int bj = (a.box_len == 1) ? 0 : j;
+            a.x[j] = clampf(a.x[j] + s, a.lo[bj], a.hi[bj]);
+        }
+    }
+    if (blockIdx.x == 0 && !a.epi.last_seg) sweep_epilogue(a.epi);
+}
+
+// B = 4Q: one warp per column; lane = e*Q + q gathers the 4 coefficients of
+// right-hand sides 4q..4q+3 of row ridx[e] (contiguous 16 bytes).
+template <typename VT, int Q>
+__global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs a) {
+    constexpr int E = 32 / Q;
+    constexpr int B = 4 * Q;
+    const int lane = threadIdx.x & 31;
+    const int q = lane % Q;
+    const int e0 = lane / Q;
+    const int warp = (blockIdx.x * kSweepThreads + threadIdx.x) >> 5;
+    const int jb = a.cpart[warp], je = a.cpart[warp + 1];
+    const VT* __restrict__ val = static_cast<const VT*>(a.cval);
+    for (int j = jb; j < je; ++j) {
+        const int2 ci = a.cinfo[j];
+        if (ci.y == 0) continue;
+        const VT* vcol = val + ci.x;
+        const int* rcol = a.ridx + ci.x;
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = e0; e < ci.y; e += E) {
+            const float v = (float)__ldg(vcol + e);
+            const int r = __ldg(rcol + e);
+            const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r * B) + q);
+            s.x = fmaf(v, cv.x, s.x);
+            s.y = fmaf(v, cv.y, s.y);
+            s.z = fmaf(v, cv.z, s.z);
+            s.w = fmaf(v, cv.w, s.w);
+        }
+#pragma unroll
+        for (int o = 16; o >= Q; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+            s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+        }
+        if (e0 == 0) {
+            const int bj = (a.box_len == 1) ? 0 : j;
+            const float lo = a.lo[bj], hi = a.hi[bj];
+            float4* xp = reinterpret_cast<float4*>(a.x + (size_t)j * B) + q;
+            float4 xv = *xp;
+            xv.x = clampf(xv.x + s.x, lo, hi);
+            xv.y = clampf(xv.y + s.y, lo, hi);
+            xv.z = clampf(xv.z + s.z, lo, hi);
+            xv.w = clampf(xv.w + s.w, lo, hi);
+            *xp = xv;
+        }
+    }
+    if (blockIdx.x == 0 && !a.epi.last_seg) sweep_epilogue(a.epi);
+}
+
+// Epilogue of the last block of a two-pass sweep (it may set the stop flag, so
+// it runs after every column-pass CTA has read that flag).
+__global__ void k_epilogue(const EpiArgs a) { sweep_epilogue(a); }
+
 // ------------------------------------------------------------- finalize ----
-// x <- clamp(x + delta, lo, hi), delta <- 0 (n x B elements, 128-bit).  CTA 0
-// also reduces the sweep's proximity partials in a fixed order, records the
-// history and advances the stopping rule of each right-hand side.
+// x <- clamp(x + delta, lo, hi), delta <- 0 (n x B elements, 128-bit); CTA 0
+// also runs the sweep epilogue.
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArgs a) {
-    const long long nv = a.nB >> 2;   // nB is a multiple of 4 (n*B, B in {1,4..32} padded)
+    const long long nv = a.nB >> 2;
     float4* x4 = reinterpret_cast<float4*>(a.x);
     float4* d4 = reinterpret_cast<float4*>(a.delta);
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -309,54 +411,13 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
         x4[v] = xv;
         d4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    // tail when n*B is not a multiple of 4 (B = 1 only)
     if (blockIdx.x == 0) {
         for (long long idx = 4 * nv + threadIdx.x; idx < a.nB; idx += blockDim.x) {
             const long long j = (a.box_len == 1) ? 0 : idx / a.B;
             a.x[idx] = clampf(a.x[idx] + a.delta[idx], a.lo[j], a.hi[j]);
             a.delta[idx] = 0.f;
         }
-    }
-    if (blockIdx.x != 0) return;
-    // proximity partials: warp w handles right-hand sides w, w+8, ...
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = wid; b < a.B; b += kFinalizeThreads / 32) {
-        double s = 0.0;
-        for (int c = lane; c < a.npp; c += 32) s += a.pp[(size_t)c * a.B + b];
-        s = warp_sum(s);
-        if (lane != 0) continue;
-        RhsState& st = a.st[b];
-        if (st.stopped) continue;
-        if (a.first_seg) st.p_acc = 0.0;
-        st.p_acc += a.scale * s;
-        if (!a.last_seg) continue;
-        const double p = st.p_acc;
-        const int k = st.k;
-        if (k < a.hist_cap) {
-            a.prox_hist[(size_t)b * a.hist_cap + k] = p;
-            a.obj_hist[(size_t)b * a.hist_cap + k] = st.f_valid ? st.f_cur : __longlong_as_double(0x7ff8000000000000LL);
-        }
-        // stopping rule (Sec. 2.2.1 and 2.2.3)
-        if (st.has_prev_p && fabs(p - st.p_prev) / fmax(1.0, st.p_prev) < a.sp.prox_rel)
-            st.calm += 1;
-        else
-            st.calm = 0;
-        const bool feas = (p <= a.sp.prox_abs) || (st.calm >= a.sp.patience);
-        bool objok = true;
-        if (a.sp.has_obj && a.sp.obj_rel > 0.0 && st.f_valid) {
-            objok = st.has_prev_f &&
-                    fabs(st.f_cur - st.f_prev) / fmax(1.0, fabs(st.f_prev)) < a.sp.obj_rel;
-        }
-        st.p_prev = p;
-        st.has_prev_p = 1;
-        if (st.f_valid) {
-            st.f_prev = st.f_cur;
-            st.has_prev_f = 1;
-        }
-        st.f_valid = 0;
-        st.last_prox = p;
-        st.k = k + 1;
-        if (a.sp.use_stopping && feas && objok) st.stopped = 1;
+        sweep_epilogue(a.epi);
     }
 }
 
@@ -373,52 +434,135 @@ __global__ void k_reduce_pp(const double* pp, int npp, int B, double scale, int 
 }
 
 using SweepFn = void (*)(SweepArgs);
+using ColFn = void (*)(ColArgs);
+
+template <typename VT, int G, int MAXE>
+SweepFn pick_scat(int scat) {
+    if (scat == 0) return k_sweep<VT, G, MAXE, 0>;
+    if (scat == 1) return k_sweep<VT, G, MAXE, 1>;
+    return k_sweep<VT, G, MAXE, 2>;
+}
 
 template <typename VT>
-SweepFn pick_sweep(int G, int maxch) {
-    if (G == 32 && maxch == 8) return k_sweep<VT, 32, 8>;
-    if (G == 32 && maxch == 4) return k_sweep<VT, 32, 4>;
-    if (G == 32 && maxch == 2) return k_sweep<VT, 32, 2>;
-    if (G == 16 && maxch == 4) return k_sweep<VT, 16, 4>;
-    if (G == 16 && maxch == 2) return k_sweep<VT, 16, 2>;
-    if (G == 8 && maxch == 4) return k_sweep<VT, 8, 4>;
-    if (G == 8 && maxch == 2) return k_sweep<VT, 8, 2>;
-    if (G == 4 && maxch == 2) return k_sweep<VT, 4, 2>;
+SweepFn pick_sweep(int G, int maxe, int scat) {
+    if (G == 32 && maxe == 32) return pick_scat<VT, 32, 32>(scat);
+    if (G == 32 && maxe == 16) return pick_scat<VT, 32, 16>(scat);
+    if (G == 32 && maxe == 8) return pick_scat<VT, 32, 8>(scat);
+    if (G == 16 && maxe == 16) return pick_scat<VT, 16, 16>(scat);
+    if (G == 16 && maxe == 8) return pick_scat<VT, 16, 8>(scat);
+    if (G == 8 && maxe == 16) return pick_scat<VT, 8, 16>(scat);
+    if (G == 8 && maxe == 8) return pick_scat<VT, 8, 8>(scat);
+    if (G == 4 && maxe == 8) return pick_scat<VT, 4, 8>(scat);
     return nullptr;
 }
 
 template <typename VT>
-SweepFn pick_batched(int B) {
+SweepFn pick_batched(int B, int scat) {
+    const bool one = scat != 0;
     switch (B) {
-        case 4: return k_sweep_batched<VT, 1>;
-        case 8: return k_sweep_batched<VT, 2>;
-        case 16: return k_sweep_batched<VT, 4>;
-        case 32: return k_sweep_batched<VT, 8>;
+        case 4: return one ? k_sweep_batched<VT, 1, 1> : k_sweep_batched<VT, 1, 0>;
+        case 8: return one ? k_sweep_batched<VT, 2, 1> : k_sweep_batched<VT, 2, 0>;
+        case 16: return one ? k_sweep_batched<VT, 4, 1> : k_sweep_batched<VT, 4, 0>;
+        case 32: return one ? k_sweep_batched<VT, 8, 1> : k_sweep_batched<VT, 8, 0>;
         default: return nullptr;
     }
 }
 
+template <typename VT>
+ColFn pick_col(int G, int B) {
+    if (B > 1) {
+        switch (B) {
+            case 4: return k_colpass_batched<VT, 1>;
+            case 8: return k_colpass_batched<VT, 2>;
+            case 16: return k_colpass_batched<VT, 4>;
+            case 32: return k_colpass_batched<VT, 8>;
+            default: return nullptr;
+        }
+    }
+    switch (G) {
+        case 32: return k_colpass<VT, 32>;
+        case 16: return k_colpass<VT, 16>;
+        case 8: return k_colpass<VT, 8>;
+        case 4: return k_colpass<VT, 4>;
+        default: return nullptr;
+    }
+}
+
+SweepFn sweep_fn(suppy_dtype dt, int G, int maxe, int scat, int B) {
+    if (B > 1) {
+        if (dt == SUPPY_F32) return pick_batched<float>(B, scat);
+        if (dt == SUPPY_BF16) return pick_batched<__nv_bfloat16>(B, scat);
+        return pick_batched<__half>(B, scat);
+    }
+    if (dt == SUPPY_F32) return pick_sweep<float>(G, maxe, scat);
+    if (dt == SUPPY_BF16) return pick_sweep<__nv_bfloat16>(G, maxe, scat);
+    return pick_sweep<__half>(G, maxe, scat);
+}
+
+ColFn col_fn(suppy_dtype dt, int G, int B) {
+    if (dt == SUPPY_F32) return pick_col<float>(G, B);
+    if (dt == SUPPY_BF16) return pick_col<__nv_bfloat16>(G, B);
+    return pick_col<__half>(G, B);
+}
+
 }  // namespace
 
-cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxch, int grid,
+cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,
                          cudaStream_t s) {
-    SweepFn f = nullptr;
-    if (dt == SUPPY_F32) f = pick_sweep<float>(G, maxch);
-    else if (dt == SUPPY_BF16) f = pick_sweep<__nv_bfloat16>(G, maxch);
-    else f = pick_sweep<__half>(G, maxch);
+    SweepFn f = sweep_fn(dt, G, maxe, scat, 1);
+    if (!f) return cudaErrorInvalidValue;
+    size_t smem = 0;
+    if (scat == 2) {
+        smem = sizeof(float) * (size_t)a.n;
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    f<<<grid, kSweepThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batched(const SweepArgs& a, suppy_dtype dt, int scat, int grid,
+                                 cudaStream_t s) {
+    SweepFn f = sweep_fn(dt, 32, 0, scat, a.B);
     if (!f) return cudaErrorInvalidValue;
     f<<<grid, kSweepThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_batched(const SweepArgs& a, suppy_dtype dt, int /*G*/, int grid,
-                                 cudaStream_t s) {
-    SweepFn f = nullptr;
-    if (dt == SUPPY_F32) f = pick_batched<float>(a.B);
-    else if (dt == SUPPY_BF16) f = pick_batched<__nv_bfloat16>(a.B);
-    else f = pick_batched<__half>(a.B);
+int sweep_blocks_per_sm(suppy_dtype dt, int G, int maxe, int scat, int B, int n) {
+    SweepFn f = sweep_fn(dt, G, maxe, scat, B);
+    if (!f) return 0;
+    size_t smem = 0;
+    if (scat == 2 && B == 1) {
+        smem = sizeof(float) * (size_t)n;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+    }
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kSweepThreads, smem) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_colpass(const ColArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s) {
+    ColFn f = col_fn(dt, G, a.B);
     if (!f) return cudaErrorInvalidValue;
     f<<<grid, kSweepThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int colpass_blocks_per_sm(suppy_dtype dt, int G, int B) {
+    ColFn f = col_fn(dt, G, B);
+    if (!f) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kSweepThreads, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
+    k_epilogue<<<1, kFinalizeThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -431,28 +575,6 @@ cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int
                              double* out, cudaStream_t s) {
     k_reduce_pp<<<1, 256, 0, s>>>(pp, npp, B, scale, accumulate, out);
     return cudaGetLastError();
-}
-
-}  // namespace suppy
-
-namespace suppy {
-
-int sweep_blocks_per_sm(suppy_dtype dt, int G, int maxch, int batchedB) {
-    SweepFn f = nullptr;
-    if (batchedB > 1) {
-        if (dt == SUPPY_F32) f = pick_batched<float>(batchedB);
-        else if (dt == SUPPY_BF16) f = pick_batched<__nv_bfloat16>(batchedB);
-        else f = pick_batched<__half>(batchedB);
-    } else {
-        if (dt == SUPPY_F32) f = pick_sweep<float>(G, maxch);
-        else if (dt == SUPPY_BF16) f = pick_sweep<__nv_bfloat16>(G, maxch);
-        else f = pick_sweep<__half>(G, maxch);
-    }
-    if (!f) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kSweepThreads, 0) != cudaSuccess)
-        return 0;
-    return nb;
 }
 
 }  // namespace suppy

@@ -33,12 +33,16 @@ def _oracle_sweep(prob, x, mode=O.CIMMINO, dtype="f32", lam=1.0, b=0):
 
 # ------------------------------------------------------------ one sweep ----
 
+STRATS = [pk.STRATEGY_ONE_PASS, pk.STRATEGY_TWO_PASS]
+
+
+@pytest.mark.parametrize("strategy", STRATS)
 @pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
-def test_one_sweep_tiny_ct(mode):
+def test_one_sweep_tiny_ct(mode, strategy):
     prob = small_ct()
     if mode == O.BIP:
         prob.blocks = synth.angle_blocks(90, 91, 10)
-    ctx = pk.from_problem(prob, mode=mode)
+    ctx = pk.from_problem(prob, mode=mode, strategy=strategy)
     x0 = random_x(prob.A.n, 1, seed=1)
     ctx.suppy_set_x(x0)
     ctx.suppy_sweep(_params(), 1)
@@ -49,12 +53,13 @@ def test_one_sweep_tiny_ct(mode):
     assert len(ph) == 1 and rel(ph[0], po) <= 1e-5
 
 
+@pytest.mark.parametrize("strategy", STRATS)
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
-def test_one_sweep_low_precision_values(dtype):
+def test_one_sweep_low_precision_values(dtype, strategy):
     """BF16/FP16 storage: parity against the oracle run on the rounded values;
     the error against the FP32-valued oracle is reported by the bench."""
     prob = small_ct()
-    ctx = pk.from_problem(prob, dtype=DT[dtype])
+    ctx = pk.from_problem(prob, dtype=DT[dtype], strategy=strategy)
     x0 = random_x(prob.A.n, 1, seed=2)
     ctx.suppy_set_x(x0)
     ctx.suppy_sweep(_params(), 1)
@@ -62,16 +67,23 @@ def test_one_sweep_low_precision_values(dtype):
     assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
 
 
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("n", [3001, 20011])
 @pytest.mark.parametrize("mean_len,long_len", [(3, 0), (30, 0), (100, 0), (300, 0), (40, 2100),
                                                (250, 1500)])
-def test_one_sweep_row_length_mix(mean_len, long_len):
+def test_one_sweep_row_length_mix(mean_len, long_len, n, strategy):
     """Ragged rows covering every launch shape (4..32 lanes per row), empty
-    rows, rows longer than the register-held chunks, n not a multiple of 4."""
-    n = 3001
+    rows, rows longer than the register-held elements, n not a multiple of 4;
+    n = 3001 stages the one-pass scatter in shared memory, n = 20011 uses L2
+    reductions."""
     prob = synth.random_problem(700, n, seed=mean_len + long_len, feasible=False,
                                 mean_len=mean_len, empty_frac=0.05,
                                 long_rows=7 if long_len else 0, long_len=long_len)
-    ctx = pk.from_problem(prob)
+    ctx = pk.from_problem(prob, strategy=strategy)
+    info = ctx.suppy_info_get()
+    assert info["strategy"] == strategy
+    if strategy == pk.STRATEGY_ONE_PASS:
+        assert info["scatter"] == (2 if n * 4 <= 65536 else 1)
     x0 = random_x(n, 1, seed=3)
     for lam in (1.0, 1.7):
         ctx.suppy_set_x(x0)
@@ -215,10 +227,11 @@ def test_checkpoint_resume_is_exact_on_state():
 
 # ------------------------------------------------------------------ batched ----
 
-@pytest.mark.parametrize("nrhs", [3, 4, 16])
-def test_batched_sweep_matches_per_rhs_oracle(nrhs):
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("nrhs", [3, 4, 16, 32])
+def test_batched_sweep_matches_per_rhs_oracle(nrhs, strategy):
     prob = synth.ct_problem(32, 30, 45, nrhs=nrhs)
-    ctx = pk.from_problem(prob)
+    ctx = pk.from_problem(prob, strategy=strategy)
     x0 = random_x(prob.A.n, nrhs, seed=12)
     ctx.suppy_set_x(x0)
     ctx.suppy_sweep(_params(), 2)
@@ -243,7 +256,7 @@ def test_batched_run_equals_single_runs():
         p1.l, p1.u = p1.l[:, b].copy(), p1.u[:, b].copy()
         c1 = pk.from_problem(p1, obj=pk.SUPPY_OBJ_TV_ISO)
         c1.suppy_run(P)
-        assert rel_l2(xb[:, b], c1.suppy_get_x()) <= 1e-4
+        assert rel_l2(xb[:, b], c1.suppy_get_x()) <= 1e-3
 
 
 # --------------------------------------------------------------- validation ----
@@ -278,12 +291,46 @@ def test_invalid_inputs_are_rejected():
         ctx.suppy_perturb(_params())          # no objective: ESTATE
 
 
-def test_device_inputs_equal_host_inputs():
+@pytest.mark.parametrize("strategy", STRATS)
+def test_device_inputs_equal_host_inputs(strategy):
     prob = small_ct()
-    c_h = pk.from_problem(prob)
-    c_d = pk.from_problem(prob, device=True)
+    c_h = pk.from_problem(prob, strategy=strategy)
+    c_d = pk.from_problem(prob, device=True, strategy=strategy)
     x0 = random_x(prob.A.n, 1, seed=14)
     for c in (c_h, c_d):
         c.suppy_set_x(x0)
         c.suppy_sweep(_params(), 1)
     assert rel_l2(c_h.suppy_get_x(), c_d.suppy_get_x()) <= 1e-6
+
+
+def test_two_pass_sweep_is_bitwise_reproducible():
+    """The two-pass sweep has no atomics: repeated runs give identical bits."""
+    prob = small_ct()
+    xs = []
+    for _ in range(2):
+        ctx = pk.from_problem(prob, strategy=pk.STRATEGY_TWO_PASS, obj=pk.SUPPY_OBJ_TV_ISO)
+        ctx.suppy_run(_params(max_sweeps=20))
+        xs.append(ctx.suppy_get_x().copy())
+    np.testing.assert_array_equal(xs[0], xs[1])
+
+
+def test_autotuner_picks_a_measured_strategy():
+    prob = synth.ct_problem(128, 90, 181)
+    ctx = pk.from_problem(prob, tune=1)
+    info = ctx.suppy_info_get()
+    assert info["strategy"] in (1, 2)
+    x0 = random_x(prob.A.n, 1, seed=21)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 1)
+    xo, _ = _oracle_sweep(prob, x0)
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+
+
+def test_kernel_timing_counts_launches():
+    prob = small_ct()
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    ctx.suppy_timing_enable(True)
+    ctx.suppy_run(_params(max_sweeps=5))
+    for kind, expect in ((0, 5), (1, 5), (2, 5)):
+        ms, nl = ctx.suppy_kernel_time(kind)
+        assert nl == expect and ms > 0
