@@ -123,7 +123,8 @@ typedef struct {
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
  * fills the paper's stopping defaults (P* = 1e-6, dP* = 1e-8, N = 5,
- * N_max = 500, df* = 1e-6), lambda = 1, gamma = 0.5, alpha = 0.99, n_red = 1. */
+ * N_max = 500, df* = 1e-6), lambda = 1, gamma = 0.5, alpha = 0.99, n_red = 1,
+ * max_trials = 100, check_every = 10, use_graphs = 1. */
 typedef struct {
     double lambda;          /* relaxation, (0, 2)                                  */
     double gamma, alpha;    /* beta = gamma * alpha^l                              */
@@ -137,7 +138,7 @@ typedef struct {
     double obj_rel;         /* df*; <= 0 disables the objective criterion          */
     int32_t patience;       /* N                                                   */
     int32_t use_stopping;   /* 0: run exactly max_sweeps sweeps                    */
-    int32_t use_graphs;     /* 1: replay the sweep loop through CUDA graphs        */
+    int32_t use_graphs;     /* 1: suppy_run replays one captured iteration (CUDA graph) */
 } suppy_params;
 
 typedef struct {

@@ -78,8 +78,10 @@ struct suppy_ctx {
     int strategy = 1;               // 1 one pass, 2 two passes
     int scat = 1;                   // one pass: 1 L2 reductions, 2 shared-memory staged
     int G = 32, maxe = 8;
-    int grid_sweep = 0, groups = 0;
-    int Gc = 32, grid_col = 0, cgroups = 0;
+    int grid_sweep = 0, groups = 0;             // largest row-pass launch
+    int Gc = 32, grid_col = 0, cgroups = 0;     // largest column-pass launch
+    std::vector<int> seg_grid, seg_cgrid;       // per block launch sizes
+    std::vector<size_t> seg_part_off, seg_cpart_off;
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
@@ -97,6 +99,11 @@ struct suppy_ctx {
     long long launches = 0;
     size_t dev_bytes = 0;
     std::vector<void*> allocs;
+
+    // CUDA graph of one superiorized iteration (perturbation + sweep)
+    cudaGraphExec_t graph = nullptr;
+    std::vector<char> graph_key;
+    long long graph_launches = 0;
 
     std::string err;
 };
@@ -294,7 +301,7 @@ SweepArgs row_args(suppy_ctx* c, int t, float lam) {
     a.x = c->d_x;
     a.delta = c->d_delta;
     a.coef = nullptr;
-    a.part = c->d_part + (size_t)t * (c->groups + 1);
+    a.part = c->d_part + c->seg_part_off[t];
     a.pp = c->d_pp;
     a.st = c->d_st;
     a.lam = lam;
@@ -312,7 +319,7 @@ double seg_scale(const suppy_ctx* c, int t) {
 EpiArgs epi_args(suppy_ctx* c, int t, const StopParams& sp) {
     EpiArgs e;
     e.pp = c->d_pp;
-    e.npp = c->grid_sweep;
+    e.npp = c->seg_grid[t];
     e.B = c->B;
     e.scale = seg_scale(c, t);
     e.st = c->d_st;
@@ -327,11 +334,12 @@ EpiArgs epi_args(suppy_ctx* c, int t, const StopParams& sp) {
 
 // Row pass of block t: the fused one-pass sweep (scat 1/2) or the
 // coefficient-writing row pass (scat 0).
-suppy_status launch_rows(suppy_ctx* c, const SweepArgs& a, int scat) {
+suppy_status launch_rows(suppy_ctx* c, const SweepArgs& a, int scat, int t) {
     Timed tm{c, 0};
     CK(tm.begin());
-    if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, scat, c->grid_sweep, c->stream));
-    else CK(launch_sweep_batched(a, c->dt, scat, c->grid_sweep, c->stream));
+    const int grid = c->seg_grid[t];
+    if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, scat, grid, c->stream));
+    else CK(launch_sweep_batched(a, c->dt, scat, grid, c->stream));
     CK(tm.end());
     note_launch(c);
     return SUPPY_OK;
@@ -346,7 +354,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
         const EpiArgs epi = epi_args(c, t, sp);
         if (c->strategy == 2) {
             a.coef = c->d_coef;
-            if ((s = launch_rows(c, a, 0)) != SUPPY_OK) return s;
+            if ((s = launch_rows(c, a, 0, t)) != SUPPY_OK) return s;
             ColArgs ca;
             ca.cinfo = c->d_cinfo + (size_t)t * c->n;
             ca.ridx = c->d_ridx;
@@ -357,11 +365,11 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.hi = c->d_hi;
             ca.box_len = c->box_len;
             ca.B = c->B;
-            ca.cpart = c->d_cpart + (size_t)t * (c->cgroups + 1);
+            ca.cpart = c->d_cpart + c->seg_cpart_off[t];
             ca.epi = epi;
             Timed tm{c, 1};
             CK(tm.begin());
-            CK(launch_colpass(ca, c->dt, c->Gc, c->grid_col, c->stream));
+            CK(launch_colpass(ca, c->dt, c->Gc, c->seg_cgrid[t], c->stream));
             CK(tm.end());
             note_launch(c);
             if (epi.last_seg) {
@@ -369,7 +377,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 note_launch(c);
             }
         } else {
-            if ((s = launch_rows(c, a, c->scat)) != SUPPY_OK) return s;
+            if ((s = launch_rows(c, a, c->scat, t)) != SUPPY_OK) return s;
             FinalizeArgs f;
             f.x = c->d_x;
             f.delta = c->d_delta;
@@ -444,9 +452,7 @@ void choose_row_shape(suppy_ctx* c, double mean_len, int max_len) {
     else if (mean_len >= 20) c->G = 8;
     else c->G = 4;
     const int need = (max_len + c->G - 1) / c->G;
-    if (c->strategy == 2) c->maxe = 8;           // no scatter: registers only buffer loads
-    else if (c->G == 32) c->maxe = need <= 8 ? 8 : (need <= 16 ? 16 : 32);
-    else if (c->G == 4) c->maxe = 8;
+    if (c->strategy == 2 || c->G == 4) c->maxe = 8;   // no scatter: registers only buffer loads
     else c->maxe = need <= 8 ? 8 : 16;
 }
 
@@ -457,6 +463,10 @@ void choose_col_shape(suppy_ctx* c, double mean_col) {
     else c->Gc = 4;
 }
 
+// Work per group the launch aims for: enough rows (or columns) per group to
+// amortize the group's start-up, capped by the resident grid.
+constexpr long long kWorkPerGroup = 1024;
+
 suppy_status build_row_partition(suppy_ctx* c) {
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
@@ -466,10 +476,21 @@ suppy_status build_row_partition(suppy_ctx* c) {
     c->grid_sweep = sms * bps;
     const int gpc = (c->B > 1) ? kSweepThreads / 32 : kSweepThreads / c->G;
     c->groups = c->grid_sweep * gpc;
-    std::vector<int> part((size_t)c->nseg * (c->groups + 1));
+    c->seg_grid.assign(c->nseg, 0);
+    c->seg_part_off.assign(c->nseg + 1, 0);
+    for (int t = 0; t < c->nseg; ++t) {
+        const long long work = c->rpref[c->seg_start[t + 1]] - c->rpref[c->seg_start[t]] +
+                               16LL * (c->seg_start[t + 1] - c->seg_start[t]);
+        long long g = (work + gpc * kWorkPerGroup - 1) / (gpc * kWorkPerGroup);
+        // a shared-memory staged scatter flushes n values per CTA: fewer CTAs
+        if (scat == 2) g = std::min<long long>(g, sms);
+        c->seg_grid[t] = (int)std::max<long long>(1, std::min<long long>(g, c->grid_sweep));
+        c->seg_part_off[t + 1] = c->seg_part_off[t] + (size_t)c->seg_grid[t] * gpc + 1;
+    }
+    std::vector<int> part(c->seg_part_off[c->nseg]);
     for (int t = 0; t < c->nseg; ++t)
-        partition(c->rpref, c->seg_start[t], c->seg_start[t + 1], c->groups,
-                  part.data() + (size_t)t * (c->groups + 1));
+        partition(c->rpref, c->seg_start[t], c->seg_start[t + 1], c->seg_grid[t] * gpc,
+                  part.data() + c->seg_part_off[t]);
     if (c->d_part) dfree(c, c->d_part);
     c->d_part = nullptr;
     suppy_status s = dalloc(c, &c->d_part, part.size());
@@ -494,12 +515,20 @@ suppy_status build_col_partition(suppy_ctx* c) {
     c->grid_col = sms * bps;
     const int gpc = (c->B > 1) ? kSweepThreads / 32 : kSweepThreads / c->Gc;
     c->cgroups = c->grid_col * gpc;
-    std::vector<int> part((size_t)c->nseg * (c->cgroups + 1));
+    c->seg_cgrid.assign(c->nseg, 0);
+    c->seg_cpart_off.assign(c->nseg + 1, 0);
+    for (int t = 0; t < c->nseg; ++t) {
+        const long long work = c->cpref[(size_t)t * (c->n + 1) + c->n];
+        long long g = (work + gpc * kWorkPerGroup - 1) / (gpc * kWorkPerGroup);
+        c->seg_cgrid[t] = (int)std::max<long long>(1, std::min<long long>(g, c->grid_col));
+        c->seg_cpart_off[t + 1] = c->seg_cpart_off[t] + (size_t)c->seg_cgrid[t] * gpc + 1;
+    }
+    std::vector<int> part(c->seg_cpart_off[c->nseg]);
     std::vector<long long> pref(c->n + 1);
     for (int t = 0; t < c->nseg; ++t) {
         std::copy(c->cpref.begin() + (size_t)t * (c->n + 1),
                   c->cpref.begin() + (size_t)(t + 1) * (c->n + 1), pref.begin());
-        partition(pref, 0, c->n, c->cgroups, part.data() + (size_t)t * (c->cgroups + 1));
+        partition(pref, 0, c->n, c->seg_cgrid[t] * gpc, part.data() + c->seg_cpart_off[t]);
     }
     if (c->d_cpart) dfree(c, c->d_cpart);
     c->d_cpart = nullptr;
@@ -888,7 +917,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     }
 
     // ---- sweep strategy, launch shapes, partitions (K9 autotuner when tune)
-    c->perturb_cluster = fit_perturb_cluster(choose_perturb_cluster(n, c->B));
+    c->perturb_cluster = fit_perturb_cluster(choose_perturb_cluster(n, c->B), (int)c->obj, n, c->H, c->W);
     if ((s = ensure_hist(c, 1024)) != SUPPY_OK) return s;
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     const double mean_len = m > 0 ? (double)A->nnz / m : 0.0;
@@ -948,6 +977,63 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     return SUPPY_OK;
 }
 
+// Enqueue `iters` superiorized iterations.  With graphs, one iteration is
+// captured once (per parameter set and buffer layout) and replayed; the
+// captured kernels read every evolving quantity (iterate, state, counters)
+// from device memory, so replays are exact.
+suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) {
+    suppy_status s;
+    const bool use_graph = p->use_graphs && !c->timing;
+    if (!use_graph) {
+        for (int k = 0; k < iters; ++k) {
+            if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
+            if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
+        }
+        return SUPPY_OK;
+    }
+    std::vector<char> key(sizeof(suppy_params) + sizeof(void*) + sizeof(int) * 2);
+    std::memcpy(key.data(), p, sizeof(suppy_params));
+    std::memcpy(key.data() + sizeof(suppy_params), &c->d_prox_hist, sizeof(void*));
+    std::memcpy(key.data() + sizeof(suppy_params) + sizeof(void*), &c->hist_cap, sizeof(int));
+    std::memcpy(key.data() + sizeof(suppy_params) + sizeof(void*) + sizeof(int), &c->strategy,
+                sizeof(int));
+    if (!c->graph || key != c->graph_key) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        const long long launches = c->launches;
+        const int k_up = c->k_upper;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        s = SUPPY_OK;
+        if (c->obj != SUPPY_OBJ_NONE) s = enqueue_perturb(c, p, 0);
+        if (s == SUPPY_OK) s = enqueue_sweep(c, p);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (s != SUPPY_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(c, SUPPY_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&c->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->graph = nullptr;
+            return fail(c, SUPPY_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        c->graph_launches = c->launches - launches;
+        c->launches = launches;
+        c->k_upper = k_up;
+        c->graph_key = key;
+    }
+    for (int k = 0; k < iters; ++k) {
+        CK(cudaGraphLaunch(c->graph, c->stream));
+        c->launches += c->graph_launches;
+        c->k_upper += 1;
+    }
+    return SUPPY_OK;
+}
+
 void destroy_impl(suppy_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
@@ -955,6 +1041,7 @@ void destroy_impl(suppy_ctx* c) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_out) cudaFreeHost(c->h_out);
     delete c;
@@ -980,7 +1067,7 @@ void suppy_params_default(suppy_params* p) {
     p->obj_rel = 1e-6;
     p->patience = 5;
     p->use_stopping = 0;
-    p->use_graphs = 0;
+    p->use_graphs = 1;
 }
 
 suppy_status suppy_create(const suppy_csr* A, const float* l, const float* u,
@@ -1115,9 +1202,9 @@ suppy_status suppy_proximity(suppy_ctx* c, double* out) {
     for (int t = 0; t < c->nseg; ++t) {
         SweepArgs a = row_args(c, t, 0.f);
         a.check_stop = 0;
-        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, 0, c->grid_sweep, c->stream));
-        else CK(launch_sweep_batched(a, c->dt, 0, c->grid_sweep, c->stream));
-        CK(launch_reduce_pp(c->d_pp, c->grid_sweep, c->B, seg_scale(c, t), t > 0, c->d_out, c->stream));
+        if (c->B == 1) CK(launch_sweep(a, c->dt, c->G, c->maxe, 0, c->seg_grid[t], c->stream));
+        else CK(launch_sweep_batched(a, c->dt, 0, c->seg_grid[t], c->stream));
+        CK(launch_reduce_pp(c->d_pp, c->seg_grid[t], c->B, seg_scale(c, t), t > 0, c->d_out, c->stream));
         note_launch(c, 2);
     }
     CK(cudaMemcpyAsync(c->h_out, c->d_out, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
@@ -1157,10 +1244,7 @@ suppy_status suppy_run(suppy_ctx* c, const suppy_params* p, suppy_stats* out) {
     int done = 0;
     while (done < p->max_sweeps) {
         const int todo = std::min(chunk, p->max_sweeps - done);
-        for (int k = 0; k < todo; ++k) {
-            if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
-            if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
-        }
+        if ((s = enqueue_iterations(c, p, todo)) != SUPPY_OK) return s;
         done += todo;
         if (p->use_stopping && done < p->max_sweeps) {
             CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
@@ -1274,14 +1358,14 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->nblocks = c->nseg;
     out->lanes_per_row = c->G;
     out->elems_in_regs = c->maxe;
-    out->grid = c->grid_sweep;
+    out->grid = c->seg_grid.empty() ? 0 : c->seg_grid[0];
     out->block = kSweepThreads;
     out->perturb_cluster = c->perturb_cluster;
     out->device_bytes = (int64_t)c->dev_bytes;
     out->strategy = c->strategy;
     out->scatter = c->strategy == 1 ? c->scat : 0;
     out->col_lanes = c->strategy == 2 ? c->Gc : 0;
-    out->col_grid = c->strategy == 2 ? c->grid_col : 0;
+    out->col_grid = (c->strategy == 2 && !c->seg_cgrid.empty()) ? c->seg_cgrid[0] : 0;
     return SUPPY_OK;
 }
 

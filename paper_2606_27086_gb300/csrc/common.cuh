@@ -138,7 +138,7 @@ cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int
                              double* out, cudaStream_t s);
 cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s);
 int choose_perturb_cluster(int n, int B);
-int fit_perturb_cluster(int want);
+int fit_perturb_cluster(int want, int obj, int n, int H, int W);
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s);
 
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,

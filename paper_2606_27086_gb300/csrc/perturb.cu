@@ -202,6 +202,195 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
     }
 }
 
+// ------------------------------------------- shared-memory resident phase ----
+// Same algorithm as k_perturb, with the right-hand side's iterate and
+// subgradient held in the shared memory of the cluster for the whole phase:
+// CTA r owns image rows [R_r, R_{r+1}) (TV) or elements [P_r, P_{r+1})
+// (linear); the one halo row above and below a band is read from the
+// neighbouring CTA's shared memory (distributed shared memory).  HBM / L2
+// see one read and one write of x per phase.
+struct Band {
+    const float* own;
+    const float* up;     // previous rank's band (DSMEM) or null
+    const float* down;   // next rank's band (DSMEM) or null
+    int r0, r1, up_r0, W;
+    __device__ __forceinline__ float operator()(int i, int j) const {
+        if (i >= r0 && i < r1) return own[(i - r0) * W + j];
+        if (i < r0) return up[(i - up_r0) * W + j];
+        return down[j];
+    }
+};
+
+__device__ __forceinline__ int band_start(int r, int H, int cs) { return (int)((long long)H * r / cs); }
+
+template <class Y>
+__device__ __forceinline__ float tv_term(int obj, int i, int j, int H, int W, const Y& y) {
+    const float y0 = y(i, j);
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        if (i < H - 1 && j < W - 1) {
+            const float dx = y(i + 1, j) - y0, dy = y(i, j + 1) - y0;
+            return sqrtf(dx * dx + dy * dy);
+        }
+        return 0.f;
+    }
+    float t = 0.f;
+    if (i < H - 1) t += fabsf(y(i + 1, j) - y0);
+    if (j < W - 1) t += fabsf(y(i, j + 1) - y0);
+    return t;
+}
+
+template <class Y>
+__device__ __forceinline__ float tv_subgrad(int obj, int i, int j, int H, int W, const Y& y) {
+    const float y0 = y(i, j);
+    float g = 0.f;
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        if (i < H - 1 && j < W - 1) {
+            const float dx = y(i + 1, j) - y0, dy = y(i, j + 1) - y0;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g -= (dx + dy) / phi;
+        }
+        if (i > 0 && j < W - 1) {
+            const float ym = y(i - 1, j);
+            const float dx = y0 - ym, dy = y(i - 1, j + 1) - ym;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g += dx / phi;
+        }
+        if (j > 0 && i < H - 1) {
+            const float yl = y(i, j - 1);
+            const float dx = y(i + 1, j - 1) - yl, dy = y0 - yl;
+            const float phi = sqrtf(dx * dx + dy * dy);
+            if (phi > 0.f) g += dy / phi;
+        }
+        return g;
+    }
+    if (i < H - 1) g -= sgnf(y(i + 1, j) - y0);
+    if (i > 0) g += sgnf(y0 - y(i - 1, j));
+    if (j < W - 1) g -= sgnf(y(i, j + 1) - y0);
+    if (j > 0) g += sgnf(y0 - y(i, j - 1));
+    return g;
+}
+
+__global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbArgs a) {
+    extern __shared__ float smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double2 sw[kPerturbThreads / 32];
+    __shared__ double2 scta;
+    const int cs = (int)cluster.num_blocks();
+    const int b = blockIdx.x / cs;
+    RhsState& st = a.st[b];
+    if (st.stopped) return;
+    const int rank = (int)cluster.block_rank();
+    const bool lin = (a.obj == SUPPY_OBJ_LINEAR);
+    const int H = lin ? a.n : a.H, W = lin ? 1 : a.W;   // linear: a column of n "rows"
+    const int r0 = band_start(rank, H, cs), r1 = band_start(rank + 1, H, cs);
+    const int band = (r1 - r0) * W;
+    const int maxband = ((H + cs - 1) / cs) * W;
+    float* ys = smem;
+    float* gs = smem + maxband;
+    float* X = a.x + b;
+    const int B = a.B;
+    const int p0 = r0 * W;
+    for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
+        ys[q] = X[(size_t)(p0 + q) * B];
+        if (lin) gs[q] = a.c32[p0 + q];
+    }
+    cluster.sync();
+    Band yb{ys, nullptr, nullptr, r0, r1, 0, W};
+    Band gb{gs, nullptr, nullptr, r0, r1, 0, W};
+    if (!lin) {
+        if (rank > 0) {
+            yb.up = cluster.map_shared_rank(ys, rank - 1);
+            gb.up = cluster.map_shared_rank(gs, rank - 1);
+            yb.up_r0 = gb.up_r0 = band_start(rank - 1, H, cs);
+        }
+        if (rank < cs - 1) {
+            yb.down = cluster.map_shared_rank(ys, rank + 1);
+            gb.down = cluster.map_shared_rank(gs, rank + 1);
+        }
+    }
+
+    long long ell = st.ell;
+    int restarts = st.restarts, last_restart_k = st.last_restart_k;
+    const int k = st.k;
+    if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
+        last_restart_k != k) {
+        restarts += 1;
+        ell = restarts;
+        last_restart_k = k;
+    }
+    int accepted = 0, trials = 0;
+    double f_start = 0.0;
+    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
+        double gg = 0.0, fy = 0.0;
+        for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
+            if (lin) {
+                const int p = p0 + q;
+                fy += a.c64[p] * (double)ys[q];
+                const float gp = gs[q];
+                gg += (double)gp * (double)gp;
+            } else {
+                const int i = r0 + q / W, j = q % W;
+                fy += (double)tv_term(a.obj, i, j, H, W, yb);
+                if (!a.record_only) {
+                    const float gp = tv_subgrad(a.obj, i, j, H, W, yb);
+                    gs[q] = gp;
+                    gg += (double)gp * (double)gp;
+                }
+            }
+        }
+        const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
+        gg = r.x;
+        fy = r.y;
+        if (s == 0) f_start = fy;
+        if (a.record_only || gg == 0.0) break;
+        const double gnorm = sqrt(gg);
+        bool ok = false;
+        for (int jt = 0; jt < a.max_trials; ++jt) {
+            const double beta = a.gamma * pow(a.alpha, (double)ell);
+            ell += 1;
+            trials += 1;
+            const float sc = (float)(beta / gnorm);
+            double fz = 0.0;
+            if (lin) {
+                for (int q = threadIdx.x; q < band; q += kPerturbThreads)
+                    fz += a.c64[p0 + q] * (double)trial(ys[q], gs[q], sc);
+            } else {
+                auto z = [&yb, &gb, sc](int i, int j) { return trial(yb(i, j), gb(i, j), sc); };
+                for (int q = threadIdx.x; q < band; q += kPerturbThreads)
+                    fz += (double)tv_term(a.obj, r0 + q / W, q % W, H, W, z);
+            }
+            fz = cluster_sum2(fz, 0.0, sw, &scta, cluster).x;
+            if (fz <= fy) {
+                for (int q = threadIdx.x; q < band; q += kPerturbThreads)
+                    ys[q] = trial(ys[q], gs[q], sc);
+                cluster.sync();
+                accepted += 1;
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) break;
+    }
+    if (!a.record_only) {
+        for (int q = threadIdx.x; q < band; q += kPerturbThreads) X[(size_t)(p0 + q) * B] = ys[q];
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        st.f_cur = f_start;
+        st.f_valid = 1;
+        if (!a.record_only) {
+            st.ell = ell;
+            st.restarts = restarts;
+            st.last_restart_k = last_restart_k;
+            st.accepted_last = accepted;
+            st.trials_last = trials;
+            st.accepted_total += accepted;
+            st.trials_total += trials;
+        }
+    }
+    // no CTA may leave while a neighbour can still read its shared memory
+    cluster.sync();
+}
+
 // Objective partials: CTA c writes f-partials of every right-hand side.
 __global__ void __launch_bounds__(256) k_objective(const ObjArgs a) {
     __shared__ double sw[8];
@@ -224,6 +413,8 @@ __global__ void __launch_bounds__(256) k_objective(const ObjArgs a) {
 
 }  // namespace
 
+size_t perturb_smem_bytes(int obj, int n, int H, int W, int cs);
+
 int choose_perturb_cluster(int n, int B) {
     // enough CTAs that each thread owns a handful of pixels; at most 16 (one GPC)
     int want = (n + kPerturbThreads * 8 - 1) / (kPerturbThreads * 8);
@@ -233,13 +424,17 @@ int choose_perturb_cluster(int n, int B) {
     return cs;
 }
 
-int fit_perturb_cluster(int want) {
+int fit_perturb_cluster(int want, int obj, int n, int H, int W) {
     // largest power of two <= want for which a cluster can be resident
-    cudaFuncSetAttribute(k_perturb, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     for (int cs = want; cs >= 1; cs >>= 1) {
+        const size_t smem = perturb_smem_bytes(obj, n, H, W, cs);
+        auto kern = smem ? k_perturb_smem : k_perturb;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (smem) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cs, 1, 1);
         cfg.blockDim = dim3(kPerturbThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
         attr[0].val.clusterDim.x = cs;
@@ -248,24 +443,34 @@ int fit_perturb_cluster(int want) {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, k_perturb, &cfg) == cudaSuccess && nc > 0)
-            return cs;
+        if (cudaOccupancyMaxActiveClusters(&nc, kern, &cfg) == cudaSuccess && nc > 0) return cs;
         cudaGetLastError();
     }
     return 1;
 }
 
+size_t perturb_smem_bytes(int obj, int n, int H, int W, int cs) {
+    const bool lin = (obj == SUPPY_OBJ_LINEAR);
+    const long long rows = lin ? n : H, w = lin ? 1 : W;
+    if (!lin && cs > H) return 0;
+    const long long maxband = ((rows + cs - 1) / cs) * w;
+    const size_t bytes = (size_t)(2 * maxband) * sizeof(float);
+    return bytes <= 200 * 1024 ? bytes : 0;
+}
+
 cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_perturb, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    const size_t smem = perturb_smem_bytes(a.obj, a.n, a.H, a.W, cluster);
+    auto kern = smem ? k_perturb_smem : k_perturb;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+    if (smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(a.B * cluster, 1, 1);
     cfg.blockDim = dim3(kPerturbThreads, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -274,7 +479,7 @@ cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_perturb, a);
+    return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s) {

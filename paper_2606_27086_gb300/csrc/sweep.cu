@@ -124,10 +124,53 @@ __device__ void sweep_epilogue(const EpiArgs& a) {
 
 // ------------------------------------------------------ row pass, B = 1 ----
 // Lane `lane` of a G-lane group owns elements lane, lane+G, lane+2G, ... of
-// the row; the first MAXE*G elements stay in registers for the scatter.
+// the row.  Loads are issued in batches (all values and indices of a batch
+// first, then all gathers of x) so that each lane keeps many independent
+// loads in flight.  The first MAXE*G elements stay in registers for the
+// scatter; longer rows stream their tail in batches of 8 per lane, twice.
 // SCAT: 0 none (coefficients / proximity only), 1 global, 2 shared memory.
+template <typename VT, int G, int U>
+__device__ __forceinline__ float dot_batch(const VT* vrow, const int* crow, int base, int len,
+                                           int lane, const float* __restrict__ x, uint64_t pol) {
+    float v[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = base + u * G + lane;
+        if (e < len) {
+            v[u] = ld_stream_v<VT>(vrow + e, pol);
+            c[u] = ld_stream_i(crow + e, pol);
+        } else {
+            v[u] = 0.f;
+            c[u] = 0;
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) s = fmaf(v[u], __ldg(x + c[u]), s);
+    return s;
+}
+
+template <typename VT, int G, int U>
+__device__ __forceinline__ void scatter_batch(const VT* vrow, const int* crow, int base, int len,
+                                              int lane, float coef, float* delta, uint64_t pol) {
+    float v[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int e = base + u * G + lane;
+        if (e < len) {
+            v[u] = ld_stream_v<VT>(vrow + e, pol);
+            c[u] = ld_stream_i(crow + e, pol);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+        if (base + u * G + lane < len) atomicAdd(delta + c[u], coef * v[u]);
+}
+
 template <typename VT, int G, int MAXE, int SCAT>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(const SweepArgs a) {
     extern __shared__ float s_delta[];
     if (a.check_stop && a.st[0].stopped) return;
     const int lane = threadIdx.x & (G - 1);
@@ -144,6 +187,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         __syncthreads();
     }
     double prox = 0.0;
+    constexpr int HOLD = (SCAT == 0) ? 0 : MAXE;   // elements per lane kept for the scatter
+    constexpr int TB = (SCAT == 0) ? 8 : 4;        // tail batch per lane
 
     for (int i = rb; i < re; ++i) {
         const int2 ri = a.rinfo[i];
@@ -151,28 +196,26 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         if (len == 0) continue;
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
-        const int nk = (len + G - 1) / G;
-        float v[MAXE];
-        int c[MAXE];
-#pragma unroll
-        for (int k = 0; k < MAXE; ++k) {
-            const int e = k * G + lane;
-            if (k < nk && e < len) {
-                v[k] = ld_stream_v<VT>(vrow + e, pol);
-                c[k] = ld_stream_i(crow + e, pol);
-            } else {
-                v[k] = 0.f;
-                c[k] = 0;
-            }
-        }
+        float v[HOLD > 0 ? HOLD : 1];
+        int c[HOLD > 0 ? HOLD : 1];
         float dot = 0.f;
+        if constexpr (HOLD > 0) {
 #pragma unroll
-        for (int k = 0; k < MAXE; ++k)
-            if (k < nk) dot = fmaf(v[k], __ldg(x + c[k]), dot);
-        for (int k = MAXE; k < nk; ++k) {
-            const int e = k * G + lane;
-            if (e < len) dot = fmaf(ld_stream_v<VT>(vrow + e, pol), __ldg(x + ld_stream_i(crow + e, pol)), dot);
+            for (int k = 0; k < HOLD; ++k) {
+                const int e = k * G + lane;
+                if (e < len) {
+                    v[k] = ld_stream_v<VT>(vrow + e, pol);
+                    c[k] = ld_stream_i(crow + e, pol);
+                } else {
+                    v[k] = 0.f;
+                    c[k] = 0;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < HOLD; ++k) dot = fmaf(v[k], __ldg(x + c[k]), dot);
         }
+        for (int base = HOLD * G; base < len; base += TB * G)
+            dot += dot_batch<VT, G, TB>(vrow, crow, base, len, lane, x, pol);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gmask, dot, o);
 
@@ -180,18 +223,15 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const SweepArgs a) {
         const float w = a.wr[i];
         if (lane == 0) prox += (double)d * (double)d * (double)w;
         const float coef = a.lam * w * d;
-        if (SCAT == 0) {
+        if constexpr (SCAT == 0) {
             if (a.coef && lane == 0) a.coef[i] = coef;
-        } else if (coef != 0.f) {
+        } else {
+            if (coef != 0.f) {
 #pragma unroll
-            for (int k = 0; k < MAXE; ++k) {
-                const int e = k * G + lane;
-                if (k < nk && e < len) atomicAdd(delta + c[k], coef * v[k]);
-            }
-            for (int k = MAXE; k < nk; ++k) {
-                const int e = k * G + lane;
-                if (e < len)
-                    atomicAdd(delta + ld_stream_i(crow + e, pol), coef * ld_stream_v<VT>(vrow + e, pol));
+                for (int k = 0; k < HOLD; ++k)
+                    if (k * G + lane < len) atomicAdd(delta + c[k], coef * v[k]);
+                for (int base = HOLD * G; base < len; base += TB * G)
+                    scatter_batch<VT, G, TB>(vrow, crow, base, len, lane, coef, delta, pol);
             }
         }
     }
@@ -241,14 +281,24 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = e0; e < len; e += E) {
-            const float v = (float)__ldg(vrow + e);
-            const int c = __ldg(crow + e);
-            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)c * B) + q);
-            acc.x = fmaf(v, xv.x, acc.x);
-            acc.y = fmaf(v, xv.y, acc.y);
-            acc.z = fmaf(v, xv.z, acc.z);
-            acc.w = fmaf(v, xv.w, acc.w);
+        constexpr int UB = 4;
+        for (int base = e0; base < len; base += UB * E) {
+            float vv[UB];
+            int cc[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int e = base + u * E;
+                vv[u] = (e < len) ? (float)__ldg(vrow + e) : 0.f;
+                cc[u] = (e < len) ? __ldg(crow + e) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)cc[u] * B) + q);
+                acc.x = fmaf(vv[u], xv.x, acc.x);
+                acc.y = fmaf(vv[u], xv.y, acc.y);
+                acc.z = fmaf(vv[u], xv.z, acc.z);
+                acc.w = fmaf(vv[u], xv.w, acc.w);
+            }
         }
 #pragma unroll
         for (int o = 16; o >= Q; o >>= 1) {
@@ -320,8 +370,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float s = 0.f;
-        for (int e = lane; e < ci.y; e += G)
-            s = fmaf(ld_stream_v<VT>(vcol + e, pol), __ldg(coef + ld_stream_i(rcol + e, pol)), s);
+        for (int base = 0; base < ci.y; base += 8 * G)
+            s += dot_batch<VT, G, 8>(vcol, rcol, base, ci.y, lane, coef, pol);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (lane == 0 && ci.y > 0) {
@@ -350,14 +400,24 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = e0; e < ci.y; e += E) {
-            const float v = (float)__ldg(vcol + e);
-            const int r = __ldg(rcol + e);
-            const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r * B) + q);
-            s.x = fmaf(v, cv.x, s.x);
-            s.y = fmaf(v, cv.y, s.y);
-            s.z = fmaf(v, cv.z, s.z);
-            s.w = fmaf(v, cv.w, s.w);
+        constexpr int UB = 4;
+        for (int base = e0; base < ci.y; base += UB * E) {
+            float vv[UB];
+            int rr[UB];
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const int e = base + u * E;
+                vv[u] = (e < ci.y) ? (float)__ldg(vcol + e) : 0.f;
+                rr[u] = (e < ci.y) ? __ldg(rcol + e) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < UB; ++u) {
+                const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)rr[u] * B) + q);
+                s.x = fmaf(vv[u], cv.x, s.x);
+                s.y = fmaf(vv[u], cv.y, s.y);
+                s.z = fmaf(vv[u], cv.z, s.z);
+                s.w = fmaf(vv[u], cv.w, s.w);
+            }
         }
 #pragma unroll
         for (int o = 16; o >= Q; o >>= 1) {
@@ -445,7 +505,6 @@ SweepFn pick_scat(int scat) {
 
 template <typename VT>
 SweepFn pick_sweep(int G, int maxe, int scat) {
-    if (G == 32 && maxe == 32) return pick_scat<VT, 32, 32>(scat);
     if (G == 32 && maxe == 16) return pick_scat<VT, 32, 16>(scat);
     if (G == 32 && maxe == 8) return pick_scat<VT, 32, 8>(scat);
     if (G == 16 && maxe == 16) return pick_scat<VT, 16, 16>(scat);

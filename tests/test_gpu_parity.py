@@ -334,3 +334,39 @@ def test_kernel_timing_counts_launches():
     for kind, expect in ((0, 5), (1, 5), (2, 5)):
         ms, nl = ctx.suppy_kernel_time(kind)
         assert nl == expect and ms > 0
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+def test_graph_replay_equals_direct_launches(strategy, mode):
+    """suppy_run through a captured CUDA graph gives the iterates of direct
+    launches (bitwise for the atomic-free two-pass sweep)."""
+    prob = small_ct()
+    if mode == O.BIP:
+        prob.blocks = synth.angle_blocks(90, 91, 10)
+    xs = []
+    for graphs in (0, 1):
+        ctx = pk.from_problem(prob, mode=mode, strategy=strategy, obj=pk.SUPPY_OBJ_TV_ISO)
+        st = ctx.suppy_run(_params(max_sweeps=15, use_graphs=graphs))
+        assert st[0]["sweeps"] == 15
+        xs.append(ctx.suppy_get_x().copy())
+    if strategy == pk.STRATEGY_TWO_PASS:
+        np.testing.assert_array_equal(xs[0], xs[1])
+    else:
+        assert rel_l2(xs[1], xs[0]) <= 1e-5
+
+
+def test_perturbation_resident_kernel_on_large_image():
+    """Images split across a 16-CTA cluster with halo rows read from the
+    neighbouring CTA's shared memory (CT 256x256)."""
+    prob = synth.ct_problem(256, 30, 363)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    assert ctx.suppy_info_get()["perturb_cluster"] > 1
+    x0 = random_x(prob.A.n, 1, seed=31)
+    ctx.suppy_set_x(x0)
+    P = dict(gamma=2.0, alpha=0.9, n_red=3, max_trials=40)
+    acc = ctx.suppy_perturb(_params(**P))
+    ob = oracle_objective(prob, O.OBJ_TV_ISO)
+    y, a, _ = O.perturbation_phase(ob, x0.astype(np.float64), O.PertState(), O.Params(**P))
+    assert acc[0] == a
+    assert rel_l2(ctx.suppy_get_x(), y) <= 1e-5
