@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsuppy_gb300.so")
+# SUPPY_LIBRARY selects another build (e.g. libsuppy_gb300_checked.so)
+LIB_PATH = os.environ.get("SUPPY_LIBRARY") or os.path.join(_HERE, "libsuppy_gb300.so")
 
 SUPPY_OK, SUPPY_EINVAL, SUPPY_ENOMEM, SUPPY_ECUDA, SUPPY_ETIMEOUT, SUPPY_ESTATE = 0, -1, -2, -3, -4, -5
 SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2

@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsuppy_gb300.so")
+LIB_CHECKED = os.path.join(HERE, "libsuppy_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,15 +40,22 @@ def _stale(out: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Build the library; ``checked`` builds libsuppy_gb300_checked.so, whose
+    kernels verify indices and vector alignment and report the first violation
+    instead of accessing memory."""
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "suppy.h")]
-    if not force and not _stale(LIB, srcs + headers + [__file__]):
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib, srcs + headers + [__file__]):
+        return lib
+    objdir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(objdir, exist_ok=True)
     nv = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if checked:
+        extra = extra + ["-DSUPPY_CHECKED"]
 
     def compile_one(src):
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
@@ -63,17 +71,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, err in results:
             if err.strip():
                 print(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cudalib = os.path.join(os.path.dirname(os.path.dirname(nv)), "lib64")
     cmd = [nv, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart",
            "-Xlinker", f"-rpath,{cudalib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -104,6 +104,7 @@ struct suppy_ctx {
     cudaGraphExec_t graph = nullptr;
     std::vector<char> graph_key;
     long long graph_launches = 0;
+    cudaStream_t cap_stream = nullptr;   // private stream used only while capturing
 
     std::string err;
 };
@@ -116,11 +117,15 @@ suppy_status fail(suppy_ctx* c, suppy_status s, const std::string& msg) {
     return s;
 }
 
+// On failure the runtime's last-error slot is cleared so that a later,
+// unrelated launch check does not report this error again.
 #define CK(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
+        if (e_ != cudaSuccess) {                                                          \
+            cudaGetLastError();                                                           \
             return fail(c, SUPPY_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                 \
     } while (0)
 
 template <typename T>
@@ -308,6 +313,8 @@ SweepArgs row_args(suppy_ctx* c, int t, float lam) {
     a.B = c->B;
     a.n = c->n;
     a.check_stop = 1;
+    a.m = c->m;
+    a.nnz = c->nnz;
     return a;
 }
 
@@ -366,6 +373,9 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.box_len = c->box_len;
             ca.B = c->B;
             ca.cpart = c->d_cpart + c->seg_cpart_off[t];
+            ca.n = c->n;
+            ca.m = c->m;
+            ca.nnz = c->nnz_csc;
             ca.epi = epi;
             Timed tm{c, 1};
             CK(tm.begin());
@@ -395,6 +405,19 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
         }
     }
     c->k_upper += 1;
+#ifdef SUPPY_CHECKED
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c->stream, &capst));
+    if (capst == cudaStreamCaptureStatusNone) {
+        CK(cudaStreamSynchronize(c->stream));
+        int w[3];
+        CK(read_check_word(w));
+        if (w[0])
+            return fail(c, SUPPY_EINVAL, "checked build: kernel check " + std::to_string(w[0]) +
+                                             " failed at index " +
+                                             std::to_string(((long long)w[2] << 32) | (unsigned)w[1]));
+    }
+#endif
     if (c->evs.size() > 8192) return flush_timing(c);
     return SUPPY_OK;
 }
@@ -422,6 +445,18 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     CK(launch_perturb(a, c->perturb_cluster, c->stream));
     CK(tm.end());
     note_launch(c);
+#ifdef SUPPY_CHECKED
+    cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(c->stream, &capst));
+    if (capst == cudaStreamCaptureStatusNone) {
+        CK(cudaStreamSynchronize(c->stream));
+        int w[3];
+        CK(read_check_word_perturb(w));
+        if (w[0])
+            return fail(c, SUPPY_EINVAL, "checked build: perturbation check " + std::to_string(w[0]) +
+                                             " failed at " + std::to_string(w[1]));
+    }
+#endif
     return SUPPY_OK;
 }
 
@@ -1004,17 +1039,33 @@ suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) 
         }
         const long long launches = c->launches;
         const int k_up = c->k_upper;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        // capture on a private stream (the caller's stream may be the legacy
+        // default stream, which cannot be captured); the graph is then
+        // launched on the caller's stream
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamSynchronize(c->stream));
+        cudaStream_t user = c->stream;
+        c->stream = c->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            c->stream = user;
+            cudaGetLastError();
+            return fail(c, SUPPY_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
         s = SUPPY_OK;
         if (c->obj != SUPPY_OBJ_NONE) s = enqueue_perturb(c, p, 0);
         if (s == SUPPY_OK) s = enqueue_sweep(c, p);
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        e = cudaStreamEndCapture(c->stream, &g);
+        c->stream = user;
         if (s != SUPPY_OK) {
             if (g) cudaGraphDestroy(g);
             return s;
         }
-        if (e != cudaSuccess) return fail(c, SUPPY_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, SUPPY_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        }
         e = cudaGraphInstantiate(&c->graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -1042,6 +1093,7 @@ void destroy_impl(suppy_ctx* c) {
         cudaEventDestroy(t.b);
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_out) cudaFreeHost(c->h_out);
     delete c;

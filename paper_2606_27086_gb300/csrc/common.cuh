@@ -59,6 +59,8 @@ struct SweepArgs {
     int B;                  // right-hand sides in the device layout
     int n;                  // unknowns (shared-memory staging size)
     int check_stop;         // 1: skip the launch when right-hand side 0 has stopped (B = 1)
+    int m;                  // rows (bounds checks of the checked build)
+    long long nnz;          // entries (bounds checks of the checked build)
 };
 
 // Epilogue of a sweep (CTA 0 of the finalize / column pass): fixed-order
@@ -100,6 +102,8 @@ struct ColArgs {
     int box_len;
     int B;
     const int* cpart;
+    int n, m;               // columns / rows (checked build)
+    long long nnz;
     EpiArgs epi;
 };
 
@@ -168,6 +172,12 @@ cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val,
                            double* c64, float* c32, double* work, int work_ctas,
                            cudaStream_t s);
 cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s);
+
+// Checked build (-DSUPPY_CHECKED): kernels verify indices and the alignment of
+// vector accesses before issuing them; the first violation is recorded in a
+// device word (kernel tag, index) and the access is skipped.
+cudaError_t read_check_word(int* out3);   // {tag, index low, index high}; resets the word
+cudaError_t read_check_word_perturb(int* out3);
 
 // --- device helpers ---------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

@@ -17,6 +17,33 @@
 namespace cg = cooperative_groups;
 
 namespace suppy {
+
+#ifdef SUPPY_CHECKED
+__device__ int g_check_p[3];
+__device__ __noinline__ bool check_fail_p(int tag, long long idx) {
+    if (atomicCAS(&g_check_p[0], 0, tag) == 0) {
+        g_check_p[1] = (int)(idx & 0xffffffffLL);
+        g_check_p[2] = (int)(idx >> 32);
+    }
+    return false;
+}
+#define PCHECKED(cond, tag, idx) ((cond) ? true : check_fail_p((tag), (long long)(idx)))
+#else
+#define PCHECKED(cond, tag, idx) true
+#endif
+
+cudaError_t read_check_word_perturb(int* out3) {
+#ifdef SUPPY_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(out3, g_check_p, sizeof(int) * 3);
+    if (e != cudaSuccess) return e;
+    int z[3] = {0, 0, 0};
+    return cudaMemcpyToSymbol(g_check_p, z, sizeof(int) * 3);
+#else
+    out3[0] = out3[1] = out3[2] = 0;
+    return cudaSuccess;
+#endif
+}
+
 namespace {
 
 // Strided view of right-hand side b of an n x B row-major array.  Reads go
@@ -283,8 +310,9 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     const bool lin = (a.obj == SUPPY_OBJ_LINEAR);
     const int H = lin ? a.n : a.H, W = lin ? 1 : a.W;   // linear: a column of n "rows"
     const int r0 = band_start(rank, H, cs), r1 = band_start(rank + 1, H, cs);
-    const int band = (r1 - r0) * W;
+    int band = (r1 - r0) * W;
     const int maxband = ((H + cs - 1) / cs) * W;
+    if (!PCHECKED(band >= 0 && band <= maxband && (lin || cs <= H), 401, rank)) band = 0;
     float* ys = smem;
     float* gs = smem + maxband;
     float* X = a.x + b;

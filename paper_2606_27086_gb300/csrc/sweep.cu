@@ -16,6 +16,35 @@
 #include "common.cuh"
 
 namespace suppy {
+
+#ifdef SUPPY_CHECKED
+__device__ int g_check[3];
+__device__ __noinline__ bool check_fail(int tag, long long idx) {
+    if (atomicCAS(&g_check[0], 0, tag) == 0) {
+        g_check[1] = (int)(idx & 0xffffffffLL);
+        g_check[2] = (int)(idx >> 32);
+    }
+    return false;
+}
+#define CHECKED(cond, tag, idx) ((cond) ? true : check_fail((tag), (long long)(idx)))
+#define ALIGNED16(p) ((((uintptr_t)(p)) & 15u) == 0)
+#else
+#define CHECKED(cond, tag, idx) true
+#define ALIGNED16(p) true
+#endif
+
+cudaError_t read_check_word(int* out3) {
+#ifdef SUPPY_CHECKED
+    cudaError_t e = cudaMemcpyFromSymbol(out3, g_check, sizeof(int) * 3);
+    if (e != cudaSuccess) return e;
+    int z[3] = {0, 0, 0};
+    return cudaMemcpyToSymbol(g_check, z, sizeof(int) * 3);
+#else
+    out3[0] = out3[1] = out3[2] = 0;
+    return cudaSuccess;
+#endif
+}
+
 namespace {
 
 __device__ __forceinline__ uint64_t policy_evict_first() {
@@ -176,7 +205,8 @@ __global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(cons
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
     const int grp = (blockIdx.x * kSweepThreads + threadIdx.x) / G;
-    const int rb = a.part[grp], re = a.part[grp + 1];
+    int rb = a.part[grp], re = a.part[grp + 1];
+    if (!CHECKED(rb >= 0 && rb <= re && re <= a.m, 1, grp)) re = rb;
     const uint64_t pol = policy_evict_first();
     const VT* __restrict__ val = static_cast<const VT*>(a.val);
     const int* __restrict__ colp = a.col;
@@ -194,6 +224,7 @@ __global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(cons
         const int2 ri = a.rinfo[i];
         const int len = ri.y;
         if (len == 0) continue;
+        if (!CHECKED(ri.x >= 0 && (long long)ri.x + len <= a.nnz, 2, i)) continue;
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
         float v[HOLD > 0 ? HOLD : 1];
@@ -264,7 +295,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
     const int q = lane % Q;
     const int e0 = lane / Q;
     const int warp = (blockIdx.x * kSweepThreads + threadIdx.x) >> 5;
-    const int rb = a.part[warp], re = a.part[warp + 1];
+    int rb = a.part[warp], re = a.part[warp + 1];
+    if (!CHECKED(rb >= 0 && rb <= re && re <= a.m, 101, warp)) re = rb;
     const VT* __restrict__ val = static_cast<const VT*>(a.val);
     const int* __restrict__ colp = a.col;
     const float* __restrict__ X = a.x;
@@ -278,6 +310,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         const int2 ri = a.rinfo[i];
         const int len = ri.y;
         if (len == 0) continue;
+        if (!CHECKED(ri.x >= 0 && (long long)ri.x + len <= a.nnz, 102, i)) continue;
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -293,6 +326,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
             }
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
+                if (!CHECKED(cc[u] >= 0 && cc[u] < a.n && ALIGNED16(X + (size_t)cc[u] * B + 4 * q), 103,
+                             (long long)i * 64 + u))
+                    cc[u] = 0;
                 const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)cc[u] * B) + q);
                 acc.x = fmaf(vv[u], xv.x, acc.x);
                 acc.y = fmaf(vv[u], xv.y, acc.y);
@@ -307,6 +343,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
             acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
             acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
         }
+        if (!CHECKED(ALIGNED16(a.l + (size_t)i * B + 4 * q) && ALIGNED16(a.u + (size_t)i * B + 4 * q),
+                     104, i))
+            continue;
         const float4 lv = __ldg(reinterpret_cast<const float4*>(a.l + (size_t)i * B) + q);
         const float4 uv = __ldg(reinterpret_cast<const float4*>(a.u + (size_t)i * B) + q);
         const float w = a.wr[i];
@@ -331,6 +370,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
             for (int e = e0; e < len; e += E) {
                 const float v = (float)__ldg(vrow + e);
                 const int c = __ldg(crow + e);
+                if (!CHECKED(c >= 0 && c < a.n && ALIGNED16(D + (size_t)c * B + 4 * q), 105,
+                             (long long)i * 64 + e))
+                    continue;
                 red_add_v4(D + (size_t)c * B + 4 * q, cf[0] * v, cf[1] * v, cf[2] * v, cf[3] * v);
             }
         }
@@ -361,12 +403,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
     const int lane = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
     const int grp = (blockIdx.x * kSweepThreads + threadIdx.x) / G;
-    const int jb = a.cpart[grp], je = a.cpart[grp + 1];
+    int jb = a.cpart[grp], je = a.cpart[grp + 1];
+    if (!CHECKED(jb >= 0 && jb <= je && je <= a.n, 301, grp)) je = jb;
     const uint64_t pol = policy_evict_first();
     const VT* __restrict__ val = static_cast<const VT*>(a.cval);
     const float* __restrict__ coef = a.coef;
     for (int j = jb; j < je; ++j) {
         const int2 ci = a.cinfo[j];
+        if (!CHECKED(ci.x >= 0 && (long long)ci.x + ci.y <= a.nnz, 302, j)) continue;
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float s = 0.f;
@@ -392,11 +436,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
     const int q = lane % Q;
     const int e0 = lane / Q;
     const int warp = (blockIdx.x * kSweepThreads + threadIdx.x) >> 5;
-    const int jb = a.cpart[warp], je = a.cpart[warp + 1];
+    int jb = a.cpart[warp], je = a.cpart[warp + 1];
+    if (!CHECKED(jb >= 0 && jb <= je && je <= a.n, 311, warp)) je = jb;
     const VT* __restrict__ val = static_cast<const VT*>(a.cval);
     for (int j = jb; j < je; ++j) {
         const int2 ci = a.cinfo[j];
         if (ci.y == 0) continue;
+        if (!CHECKED(ci.x >= 0 && (long long)ci.x + ci.y <= a.nnz, 312, j)) continue;
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -412,6 +458,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
             }
 #pragma unroll
             for (int u = 0; u < UB; ++u) {
+                if (!CHECKED(rr[u] >= 0 && rr[u] < a.m && ALIGNED16(a.coef + (size_t)rr[u] * B + 4 * q),
+                             313, (long long)j * 64 + u))
+                    rr[u] = 0;
                 const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)rr[u] * B) + q);
                 s.x = fmaf(vv[u], cv.x, s.x);
                 s.y = fmaf(vv[u], cv.y, s.y);
@@ -426,7 +475,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
             s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
             s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
         }
-        if (e0 == 0) {
+        if (e0 == 0 && CHECKED(ALIGNED16(a.x + (size_t)j * B + 4 * q), 314, j)) {
             const int bj = (a.box_len == 1) ? 0 : j;
             const float lo = a.lo[bj], hi = a.hi[bj];
             float4* xp = reinterpret_cast<float4*>(a.x + (size_t)j * B) + q;
@@ -449,7 +498,8 @@ __global__ void k_epilogue(const EpiArgs a) { sweep_epilogue(a); }
 // x <- clamp(x + delta, lo, hi), delta <- 0 (n x B elements, 128-bit); CTA 0
 // also runs the sweep epilogue.
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArgs a) {
-    const long long nv = a.nB >> 2;
+    long long nv = a.nB >> 2;
+    if (!CHECKED(ALIGNED16(a.x) && ALIGNED16(a.delta), 201, 0)) nv = 0;
     float4* x4 = reinterpret_cast<float4*>(a.x);
     float4* d4 = reinterpret_cast<float4*>(a.delta);
     const long long stride = (long long)gridDim.x * blockDim.x;
