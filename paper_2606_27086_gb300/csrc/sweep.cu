@@ -314,27 +314,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        constexpr int UB = 4;
-        for (int base = e0; base < len; base += UB * E) {
-            float vv[UB];
-            int cc[UB];
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                const int e = base + u * E;
-                vv[u] = (e < len) ? (float)__ldg(vrow + e) : 0.f;
-                cc[u] = (e < len) ? __ldg(crow + e) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                if (!CHECKED(cc[u] >= 0 && cc[u] < a.n && ALIGNED16(X + (size_t)cc[u] * B + 4 * q), 103,
-                             (long long)i * 64 + u))
-                    cc[u] = 0;
-                const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)cc[u] * B) + q);
-                acc.x = fmaf(vv[u], xv.x, acc.x);
-                acc.y = fmaf(vv[u], xv.y, acc.y);
-                acc.z = fmaf(vv[u], xv.z, acc.z);
-                acc.w = fmaf(vv[u], xv.w, acc.w);
-            }
+        for (int e = e0; e < len; e += E) {
+            const float v = (float)__ldg(vrow + e);
+            int c = __ldg(crow + e);
+            if (!CHECKED(c >= 0 && c < a.n && ALIGNED16(X + (size_t)c * B + 4 * q), 103,
+                         (long long)i * 64 + e))
+                c = 0;
+            const float4 xv = __ldg(reinterpret_cast<const float4*>(X + (size_t)c * B) + q);
+            acc.x = fmaf(v, xv.x, acc.x);
+            acc.y = fmaf(v, xv.y, acc.y);
+            acc.z = fmaf(v, xv.z, acc.z);
+            acc.w = fmaf(v, xv.w, acc.w);
         }
 #pragma unroll
         for (int o = 16; o >= Q; o >>= 1) {
@@ -446,27 +436,17 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        constexpr int UB = 4;
-        for (int base = e0; base < ci.y; base += UB * E) {
-            float vv[UB];
-            int rr[UB];
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                const int e = base + u * E;
-                vv[u] = (e < ci.y) ? (float)__ldg(vcol + e) : 0.f;
-                rr[u] = (e < ci.y) ? __ldg(rcol + e) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < UB; ++u) {
-                if (!CHECKED(rr[u] >= 0 && rr[u] < a.m && ALIGNED16(a.coef + (size_t)rr[u] * B + 4 * q),
-                             313, (long long)j * 64 + u))
-                    rr[u] = 0;
-                const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)rr[u] * B) + q);
-                s.x = fmaf(vv[u], cv.x, s.x);
-                s.y = fmaf(vv[u], cv.y, s.y);
-                s.z = fmaf(vv[u], cv.z, s.z);
-                s.w = fmaf(vv[u], cv.w, s.w);
-            }
+        for (int e = e0; e < ci.y; e += E) {
+            const float v = (float)__ldg(vcol + e);
+            int r = __ldg(rcol + e);
+            if (!CHECKED(r >= 0 && r < a.m && ALIGNED16(a.coef + (size_t)r * B + 4 * q), 313,
+                         (long long)j * 64 + e))
+                r = 0;
+            const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r * B) + q);
+            s.x = fmaf(v, cv.x, s.x);
+            s.y = fmaf(v, cv.y, s.y);
+            s.z = fmaf(v, cv.z, s.z);
+            s.w = fmaf(v, cv.w, s.w);
         }
 #pragma unroll
         for (int o = 16; o >= Q; o >>= 1) {
