@@ -296,6 +296,7 @@ def variants(pk, K, W):
                      "create_s": t_create, "strategy": info["strategy"],
                      "scatter": info["scatter"], "lanes_per_row": info["lanes_per_row"],
                      "col_lanes": info["col_lanes"], "nblocks": info["nblocks"],
+                     "tma": info["tma"],
                      "launches_per_step": nl / Kv}
         ctx.close()
         torch.cuda.synchronize()
@@ -303,6 +304,10 @@ def variants(pk, K, W):
     prob = ct512()
     run_one("ct512_cimmino_tv_f32_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
             strategy=pk.STRATEGY_ONE_PASS)
+    run_one("ct512_cimmino_tv_f32_twopass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
+            strategy=pk.STRATEGY_TWO_PASS, tma=-1)
+    run_one("ct512_cimmino_tv_f32_onepass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
+            params=SUP, strategy=pk.STRATEGY_ONE_PASS, tma=-1)
     run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
             params=SUP)
     run_one("ct512_cimmino_tv_bf16_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
@@ -409,7 +414,7 @@ def ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(prob),
            "roofline": roof, "sweep_roofline": sweep_roof, "kernels": per, "e2e": e2e,
            "gpu_launches": int(nl), "clocks": clocks,
-           "launch_shape": {k: info[k] for k in ("strategy", "scatter", "lanes_per_row",
+           "launch_shape": {k: info[k] for k in ("strategy", "scatter", "tma", "lanes_per_row",
                                                   "elems_in_regs", "grid", "col_lanes",
                                                   "col_grid", "perturb_cluster")}}
     ctx.close()

@@ -119,6 +119,9 @@ typedef struct {
      * column pass over a CSC copy of A gathering them -- no atomics, bitwise
      * reproducible, twice the matrix memory). */
     int32_t strategy;
+    /* Streaming of A through shared memory by bulk asynchronous copies (TMA)
+     * for one right-hand side: 0 automatic (used when eligible), -1 off. */
+    int32_t tma;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -165,6 +168,7 @@ typedef struct {
     int32_t scatter;              /* one pass: 1 L2 reductions, 2 shared-memory staged */
     int32_t col_lanes;            /* two passes: lanes per column            */
     int32_t col_grid;             /* two passes: CTAs of the column pass     */
+    int32_t tma;                  /* 1: the sweep streams A by bulk copies   */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

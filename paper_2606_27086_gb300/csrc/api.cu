@@ -82,6 +82,15 @@ struct suppy_ctx {
     int Gc = 32, grid_col = 0, cgroups = 0;     // largest column-pass launch
     std::vector<int> seg_grid, seg_cgrid;       // per block launch sizes
     std::vector<size_t> seg_part_off, seg_cpart_off;
+    // TMA-fed streaming passes (B = 1): CTA item ranges per block
+    bool use_tma = false;
+    int tile = 4096;
+    int max_row = 0, max_col = 0;
+    std::vector<int> seg_tgrid, seg_ctgrid;
+    std::vector<size_t> seg_tpart_off, seg_ctpart_off;
+    int* d_tpart = nullptr;
+    int* d_ctpart = nullptr;
+    int* d_err = nullptr;           // set by a kernel whose bounded wait gave up
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
@@ -359,7 +368,75 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     for (int t = 0; t < c->nseg; ++t) {
         SweepArgs a = row_args(c, t, (float)p->lambda);
         const EpiArgs epi = epi_args(c, t, sp);
-        if (c->strategy == 2) {
+        if (c->use_tma) {
+            StreamArgs sa;
+            std::memset(&sa, 0, sizeof(sa));
+            sa.info = c->d_rinfo;
+            sa.idx = c->d_col;
+            sa.val = c->d_val;
+            sa.cta_items = c->d_tpart + c->seg_tpart_off[t];
+            sa.tile = c->tile;
+            sa.err = c->d_err;
+            sa.l = c->d_l;
+            sa.u = c->d_u;
+            sa.wr = c->d_wr;
+            sa.x = c->d_x;
+            sa.delta = c->d_delta;
+            sa.coef = (c->strategy == 2) ? c->d_coef : nullptr;
+            sa.pp = c->d_pp;
+            sa.st = c->d_st;
+            sa.lam = (float)p->lambda;
+            sa.check_stop = 1;
+            EpiArgs e2 = epi;
+            e2.npp = c->seg_tgrid[t];
+            {
+                Timed tm{c, 0};
+                CK(tm.begin());
+                CK(launch_rows_tma(sa, c->dt, c->strategy == 2 ? 0 : 1, c->seg_tgrid[t], c->stream));
+                CK(tm.end());
+                note_launch(c);
+            }
+            if (c->strategy == 2) {
+                StreamArgs ca;
+                std::memset(&ca, 0, sizeof(ca));
+                ca.info = c->d_cinfo + (size_t)t * c->n;
+                ca.idx = c->d_ridx;
+                ca.val = c->d_cval;
+                ca.cta_items = c->d_ctpart + c->seg_ctpart_off[t];
+                ca.tile = c->tile;
+                ca.err = c->d_err;
+                ca.coef_in = c->d_coef;
+                ca.xw = c->d_x;
+                ca.lo = c->d_lo;
+                ca.hi = c->d_hi;
+                ca.box_len = c->box_len;
+                ca.epi = e2;
+                Timed tm{c, 1};
+                CK(tm.begin());
+                CK(launch_cols_tma(ca, c->dt, c->seg_ctgrid[t], c->stream));
+                CK(tm.end());
+                note_launch(c);
+                if (e2.last_seg) {
+                    CK(launch_epilogue(e2, c->stream));
+                    note_launch(c);
+                }
+            } else {
+                FinalizeArgs f;
+                f.x = c->d_x;
+                f.delta = c->d_delta;
+                f.lo = c->d_lo;
+                f.hi = c->d_hi;
+                f.nB = (long long)c->n * c->B;
+                f.B = c->B;
+                f.box_len = c->box_len;
+                f.epi = e2;
+                Timed tm{c, 1};
+                CK(tm.begin());
+                CK(launch_finalize(f, c->grid_fin, c->stream));
+                CK(tm.end());
+                note_launch(c);
+            }
+        } else if (c->strategy == 2) {
             a.coef = c->d_coef;
             if ((s = launch_rows(c, a, 0, t)) != SUPPY_OK) return s;
             ColArgs ca;
@@ -457,6 +534,20 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
                                              " failed at " + std::to_string(w[1]));
     }
 #endif
+    return SUPPY_OK;
+}
+
+// A streaming kernel whose bounded wait gave up leaves a nonzero error word;
+// report (and clear) it at the next synchronizing call.
+suppy_status check_device_error(suppy_ctx* c) {
+    if (!c->d_err) return SUPPY_OK;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
+    }
     return SUPPY_OK;
 }
 
@@ -575,6 +666,90 @@ suppy_status build_col_partition(suppy_ctx* c) {
     return SUPPY_OK;
 }
 
+// Item ranges of the TMA-fed passes: per block, contiguous nnz-balanced item
+// ranges, one per CTA, at least a few ring stages each.
+void tma_partition(const std::vector<long long>& pref, int i0, int i1, int grid, int* out) {
+    const long long w0 = pref[i0], w1 = pref[i1];
+    out[0] = i0;
+    int lo = i0;
+    for (int g = 1; g < grid; ++g) {
+        const long long target = w0 + (w1 - w0) * g / grid;
+        int a = lo, b = i1;
+        while (a < b) {
+            const int mid = a + (b - a) / 2;
+            if (pref[mid] < target) a = mid + 1;
+            else b = mid;
+        }
+        out[g] = a;
+        lo = a;
+    }
+    out[grid] = i1;
+}
+
+suppy_status build_tma_partitions(suppy_ctx* c) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const int bps = stream_blocks_per_sm(c->dt, c->tile);
+    if (bps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the streaming passes");
+    const long long per_cta_min = 4LL * c->tile;
+    c->seg_tgrid.assign(c->nseg, 0);
+    c->seg_tpart_off.assign(c->nseg + 1, 0);
+    for (int t = 0; t < c->nseg; ++t) {
+        const long long nz = c->rpref[c->seg_start[t + 1]] - c->rpref[c->seg_start[t]];
+        const long long g = std::min<long long>((long long)sms * bps, (nz + per_cta_min - 1) / per_cta_min);
+        c->seg_tgrid[t] = (int)std::max<long long>(1, g);
+        c->seg_tpart_off[t + 1] = c->seg_tpart_off[t] + c->seg_tgrid[t] + 1;
+    }
+    std::vector<int> part(c->seg_tpart_off[c->nseg]);
+    for (int t = 0; t < c->nseg; ++t)
+        tma_partition(c->rpref, c->seg_start[t], c->seg_start[t + 1], c->seg_tgrid[t],
+                      part.data() + c->seg_tpart_off[t]);
+    if (c->d_tpart) dfree(c, c->d_tpart);
+    c->d_tpart = nullptr;
+    suppy_status s = dalloc(c, &c->d_tpart, part.size());
+    if (s != SUPPY_OK) return s;
+    CK(cudaMemcpyAsync(c->d_tpart, part.data(), part.size() * sizeof(int), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (c->strategy == 2) {
+        // columns: element prefix per block is the CSC offset (blocks are contiguous)
+        c->seg_ctgrid.assign(c->nseg, 0);
+        c->seg_ctpart_off.assign(c->nseg + 1, 0);
+        std::vector<int2> cinfo((size_t)c->nseg * c->n);
+        CK(cudaMemcpyAsync(cinfo.data(), c->d_cinfo, sizeof(int2) * cinfo.size(),
+                           cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::vector<long long> pref(c->n + 1);
+        std::vector<int> cpart;
+        for (int t = 0; t < c->nseg; ++t) {
+            const int2* ci = cinfo.data() + (size_t)t * c->n;
+            for (int j = 0; j < c->n; ++j) pref[j + 1] = pref[j] + ci[j].y;
+            const long long nz = pref[c->n];
+            const long long g = std::min<long long>((long long)sms * bps, (nz + per_cta_min - 1) / per_cta_min);
+            c->seg_ctgrid[t] = (int)std::max<long long>(1, g);
+            c->seg_ctpart_off[t + 1] = c->seg_ctpart_off[t] + c->seg_ctgrid[t] + 1;
+            const size_t base = cpart.size();
+            cpart.resize(base + c->seg_ctgrid[t] + 1);
+            tma_partition(pref, 0, c->n, c->seg_ctgrid[t], cpart.data() + base);
+        }
+        if (c->d_ctpart) dfree(c, c->d_ctpart);
+        c->d_ctpart = nullptr;
+        s = dalloc(c, &c->d_ctpart, cpart.size());
+        if (s != SUPPY_OK) return s;
+        CK(cudaMemcpyAsync(c->d_ctpart, cpart.data(), cpart.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, c->stream));
+    }
+    const int gmax = *std::max_element(c->seg_tgrid.begin(), c->seg_tgrid.end());
+    if (gmax > c->grid_sweep) {
+        if (c->d_pp) dfree(c, c->d_pp);
+        c->d_pp = nullptr;
+        c->grid_sweep = gmax;
+        s = dalloc(c, &c->d_pp, (size_t)gmax * c->B);
+        if (s != SUPPY_OK) return s;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
 // CSC copy of the packed rows, one column range per block: a stable counting
 // sort by column on the host (rows stay in device order inside a column) gives
 // each CSR entry its CSC position; the device scatters rows and stored values.
@@ -601,6 +776,8 @@ suppy_status build_csc(suppy_ctx* c, const std::vector<int>& rp, const int* hcol
         off += cinfo[k].y;
     }
     c->nnz_csc = off;
+    c->max_col = 0;
+    for (size_t k = 0; k < cells; ++k) c->max_col = std::max(c->max_col, cinfo[k].y);
     std::vector<int> pos((size_t)std::max<long long>(c->nnz, 1));
     for (int i = 0; i < m; ++i) {
         const int src = perm.empty() ? i : perm[i];
@@ -611,12 +788,13 @@ suppy_status build_csc(suppy_ctx* c, const std::vector<int>& rp, const int* hcol
     const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
     suppy_status s;
     if ((s = dalloc(c, &c->d_cinfo, cells)) != SUPPY_OK) return s;
-    if ((s = dalloc(c, &c->d_ridx, (size_t)c->nnz)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_ridx, (size_t)c->nnz + c->tile + 16)) != SUPPY_OK) return s;
     {
         char* q = nullptr;
-        if ((s = dalloc(c, &q, (size_t)std::max<long long>(c->nnz, 1) * vsz)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &q, ((size_t)c->nnz + c->tile + 16) * vsz)) != SUPPY_OK) return s;
         c->d_cval = q;
     }
+    CK(cudaMemsetAsync(c->d_ridx, 0, sizeof(int) * ((size_t)c->nnz + c->tile + 16), c->stream));
     if ((s = dalloc(c, &c->d_coef, (size_t)std::max(m, 1) * c->B)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_coef, 0, sizeof(float) * (size_t)std::max(m, 1) * c->B, c->stream));
     CK(cudaMemcpyAsync(c->d_cinfo, cinfo.data(), sizeof(int2) * cells, cudaMemcpyHostToDevice,
@@ -693,6 +871,17 @@ suppy_status time_config(suppy_ctx* c, float* ms_out) {
     if (e != cudaSuccess) return fail(c, SUPPY_ECUDA, std::string("tuning: ") + cudaGetErrorString(e));
     *ms_out = ms / 3.f;
     return SUPPY_OK;
+}
+
+// The TMA-fed passes serve one right-hand side with the L2-reduction scatter
+// or the two-pass sweep, when every item fits in the ring's window.
+bool tma_eligible(const suppy_ctx* c, int want) {
+    if (want < 0) return false;                 // disabled by the caller
+    if (c->B != 1) return false;
+    if (c->strategy == 1 && c->scat != 1) return false;
+    if (c->max_row > stream_max_item(c->tile)) return false;
+    if (c->strategy == 2 && c->max_col > stream_max_item(c->tile)) return false;
+    return true;
 }
 
 suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, const float* box_lo,
@@ -833,12 +1022,14 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     // ---- packed matrix, row norms, weights
     const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
     if ((s = dalloc(c, &c->d_rinfo, (size_t)m)) != SUPPY_OK) return s;
-    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz + 16)) != SUPPY_OK) return s;
+    // slack of one ring stage: the streaming passes read whole stages
+    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz + c->tile + 16)) != SUPPY_OK) return s;
     {
         char* q = nullptr;
-        if ((s = dalloc(c, &q, ((size_t)c->nnz + 16) * vsz)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &q, ((size_t)c->nnz + c->tile + 16) * vsz)) != SUPPY_OK) return s;
         c->d_val = q;
     }
+    CK(cudaMemsetAsync(c->d_col, 0, sizeof(int) * ((size_t)c->nnz + c->tile + 16), c->stream));
     if ((s = dalloc(c, &c->d_rho, (size_t)m)) != SUPPY_OK) return s;
     if ((s = dalloc(c, &c->d_wr, (size_t)m)) != SUPPY_OK) return s;
     if (m) CK(cudaMemcpyAsync(c->d_rinfo, rinfo.data(), sizeof(int2) * m, cudaMemcpyHostToDevice,
@@ -957,6 +1148,9 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     const double mean_len = m > 0 ? (double)A->nnz / m : 0.0;
     const double mean_col = (double)A->nnz / n / c->nseg;
+    c->max_row = max_len;
+    if ((s = dalloc(c, &c->d_err, 1)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     const bool smem_ok = (c->B == 1) && (size_t)n * sizeof(float) <= 64 * 1024;
     const int want = o->strategy;
     if (want < 0 || want > 2) return fail(c, SUPPY_EINVAL, "unknown strategy");
@@ -992,6 +1186,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             c->scat = cd.scat;
             choose_row_shape(c, mean_len, max_len);
             if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+            c->use_tma = tma_eligible(c, o->tma);
+            if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
             float ms = 0.f;
             if ((s = time_config(c, &ms)) != SUPPY_OK) return s;
             if (ms < best_ms) {
@@ -1004,6 +1200,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     c->scat = best.scat;
     choose_row_shape(c, mean_len, max_len);
     if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+    c->use_tma = tma_eligible(c, o->tma);
+    if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
@@ -1218,7 +1416,7 @@ suppy_status suppy_get_x(suppy_ctx* c, float* x, int32_t on_device) {
             CK(cudaMemcpyAsync(x, tmp, cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     }
     if (!on_device) CK(cudaStreamSynchronize(c->stream));
-    return SUPPY_OK;
+    return on_device ? SUPPY_OK : check_device_error(c);
 }
 
 suppy_status suppy_perturb(suppy_ctx* c, const suppy_params* p, int32_t* accepted) {
@@ -1307,6 +1505,7 @@ suppy_status suppy_run(suppy_ctx* c, const suppy_params* p, suppy_stats* out) {
             if (all) break;
         }
     }
+    if ((s = check_device_error(c)) != SUPPY_OK) return s;
     if (out) {
         CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
                            c->stream));
@@ -1418,6 +1617,12 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->scatter = c->strategy == 1 ? c->scat : 0;
     out->col_lanes = c->strategy == 2 ? c->Gc : 0;
     out->col_grid = (c->strategy == 2 && !c->seg_cgrid.empty()) ? c->seg_cgrid[0] : 0;
+    out->tma = c->use_tma ? 1 : 0;
+    if (c->use_tma) {
+        out->grid = c->seg_tgrid[0];
+        out->block = kStreamThreads;
+        if (c->strategy == 2) out->col_grid = c->seg_ctgrid[0];
+    }
     return SUPPY_OK;
 }
 

@@ -126,7 +126,43 @@ struct ObjArgs {
     double* partial;        // [cta][B]
 };
 
-// --- launchers (defined in sweep.cu / perturb.cu / setup.cu) ---------------
+// One launch of a TMA-fed streaming pass (stream.cu) over the items
+// [cta_items[0], cta_items[grid]) of one block: rows of the CSR copy (row pass)
+// or columns of the CSC copy (column pass), B = 1.
+constexpr int kStreamThreads = 512;
+struct StreamArgs {
+    const int2* info;       // per item {start, length}
+    const int* idx;         // column (row pass) or row (column pass) indices
+    const void* val;
+    const int* cta_items;   // grid + 1 item boundaries
+    int tile;               // ring stage length in elements (power of two)
+    int* err;               // set to 1 when a bounded wait gives up
+    // row pass
+    const float* l;
+    const float* u;
+    const float* wr;
+    const float* x;
+    float* delta;
+    float* coef;            // coefficients out (two-pass) or null
+    double* pp;
+    RhsState* st;
+    float lam;
+    int check_stop;
+    // column pass
+    const float* coef_in;
+    float* xw;
+    const float* lo;
+    const float* hi;
+    int box_len;
+    EpiArgs epi;
+};
+
+// --- launchers (defined in sweep.cu / stream.cu / perturb.cu / setup.cu) ----
+size_t stream_smem_bytes(suppy_dtype dt, int tile);
+int stream_max_item(int tile);
+int stream_blocks_per_sm(suppy_dtype dt, int tile);
+cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int scat, int grid, cudaStream_t s);
+cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int grid, cudaStream_t s);
 // scat: 0 no scatter (proximity / coefficient output), 1 global reductions,
 // 2 shared-memory staged reductions (n * 4 bytes of shared memory)
 cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,

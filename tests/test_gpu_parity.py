@@ -370,3 +370,55 @@ def test_perturbation_resident_kernel_on_large_image():
     y, a, _ = O.perturbation_phase(ob, x0.astype(np.float64), O.PertState(), O.Params(**P))
     assert acc[0] == a
     assert rel_l2(ctx.suppy_get_x(), y) <= 1e-5
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_tma_streaming_matches_oracle_and_plain_kernels(strategy, dtype):
+    """The bulk-copy (TMA) fed passes give the oracle's sweep, and the same
+    iterates as the register-fed kernels (bitwise for the two-pass sweep)."""
+    prob = synth.ct_problem(160, 60, 227)          # n = 25600: L2-reduction scatter
+    x0 = random_x(prob.A.n, 1, seed=41)
+    out = []
+    for tma in (0, -1):
+        ctx = pk.from_problem(prob, strategy=strategy, dtype=DT[dtype], tma=tma)
+        assert ctx.suppy_info_get()["tma"] == (1 if tma == 0 else 0)
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(), 3)
+        out.append(ctx.suppy_get_x().copy())
+        ph, _ = ctx.suppy_history()
+    vals = rounded_values(prob.A.val, dtype)
+    S, l, u, lo, hi = O.from_problem(prob, values=vals)
+    x = x0.astype(np.float64)
+    for _ in range(3):
+        x, p_last = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+    assert rel_l2(out[0], x) <= 1e-5
+    assert rel(ph[-1], p_last) <= 1e-5
+    if strategy == pk.STRATEGY_TWO_PASS:
+        np.testing.assert_array_equal(out[0], out[1])
+    else:
+        assert rel_l2(out[0], out[1]) <= 1e-5
+
+
+def test_tma_block_iterative_and_long_rows():
+    """Block-iterative sweep through the streaming passes (one launch pair per
+    block), and rows longer than the ring window falling back to the
+    register-fed kernels."""
+    prob = synth.ct_problem(160, 60, 227)
+    prob.blocks = synth.angle_blocks(60, 227, 6)
+    for strategy in STRATS:
+        ctx = pk.from_problem(prob, mode=pk.SUPPY_BIP, strategy=strategy)
+        assert ctx.suppy_info_get()["tma"] == 1
+        x0 = random_x(prob.A.n, 1, seed=42)
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(), 1)
+        xo, _ = _oracle_sweep(prob, x0, O.BIP)
+        assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+    longp = synth.random_problem(300, 30000, seed=43, mean_len=60, long_rows=3, long_len=13000)
+    ctx = pk.from_problem(longp, strategy=pk.STRATEGY_TWO_PASS)
+    assert ctx.suppy_info_get()["tma"] == 0
+    x0 = random_x(30000, 1, seed=44)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 1)
+    xo, _ = _oracle_sweep(longp, x0)
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
