@@ -85,6 +85,7 @@ struct suppy_ctx {
     // TMA-fed streaming passes (B = 1): CTA item ranges per block
     bool use_tma = false;
     int tile = 4096;
+    int tG = 32, tGc = 32;          // lanes per item of the streaming row / column passes
     int max_row = 0, max_col = 0;
     std::vector<int> seg_tgrid, seg_ctgrid;
     std::vector<size_t> seg_tpart_off, seg_ctpart_off;
@@ -392,7 +393,8 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             {
                 Timed tm{c, 0};
                 CK(tm.begin());
-                CK(launch_rows_tma(sa, c->dt, c->strategy == 2 ? 0 : 1, c->seg_tgrid[t], c->stream));
+                CK(launch_rows_tma(sa, c->dt, c->tG, c->strategy == 2 ? 0 : 1, c->seg_tgrid[t],
+                                   c->stream));
                 CK(tm.end());
                 note_launch(c);
             }
@@ -413,7 +415,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.epi = e2;
                 Timed tm{c, 1};
                 CK(tm.begin());
-                CK(launch_cols_tma(ca, c->dt, c->seg_ctgrid[t], c->stream));
+                CK(launch_cols_tma(ca, c->dt, c->tGc, c->seg_ctgrid[t], c->stream));
                 CK(tm.end());
                 note_launch(c);
                 if (e2.last_seg) {
@@ -686,7 +688,18 @@ void tma_partition(const std::vector<long long>& pref, int i0, int i1, int grid,
     out[grid] = i1;
 }
 
+// Lanes per item of a streaming pass: wide groups for long items, narrow ones
+// (several items per warp) for short items, as long as the items a warp takes
+// in one round fit the ring's window.
+int stream_group(double mean_len, int max_item, int tile) {
+    int g = mean_len >= 128 ? 32 : (mean_len >= 48 ? 16 : (mean_len >= 16 ? 8 : 4));
+    while (g < 32 && (long long)(32 / g) * max_item > stream_max_item(tile)) g *= 2;
+    return g;
+}
+
 suppy_status build_tma_partitions(suppy_ctx* c) {
+    c->tG = stream_group(c->m > 0 ? (double)c->nnz / c->m : 0.0, c->max_row, c->tile);
+    if (c->strategy == 2) c->tGc = stream_group((double)c->nnz / c->n / c->nseg, c->max_col, c->tile);
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     const int bps = stream_blocks_per_sm(c->dt, c->tile);
@@ -1621,7 +1634,11 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     if (c->use_tma) {
         out->grid = c->seg_tgrid[0];
         out->block = kStreamThreads;
-        if (c->strategy == 2) out->col_grid = c->seg_ctgrid[0];
+        out->lanes_per_row = c->tG;
+        if (c->strategy == 2) {
+            out->col_grid = c->seg_ctgrid[0];
+            out->col_lanes = c->tGc;
+        }
     }
     return SUPPY_OK;
 }

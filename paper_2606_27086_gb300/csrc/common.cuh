@@ -129,7 +129,7 @@ struct ObjArgs {
 // One launch of a TMA-fed streaming pass (stream.cu) over the items
 // [cta_items[0], cta_items[grid]) of one block: rows of the CSR copy (row pass)
 // or columns of the CSC copy (column pass), B = 1.
-constexpr int kStreamThreads = 512;
+constexpr int kStreamThreads = 768;
 struct StreamArgs {
     const int2* info;       // per item {start, length}
     const int* idx;         // column (row pass) or row (column pass) indices
@@ -161,8 +161,9 @@ struct StreamArgs {
 size_t stream_smem_bytes(suppy_dtype dt, int tile);
 int stream_max_item(int tile);
 int stream_blocks_per_sm(suppy_dtype dt, int tile);
-cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int scat, int grid, cudaStream_t s);
-cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int grid, cudaStream_t s);
+cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
+                            cudaStream_t s);
+cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s);
 // scat: 0 no scatter (proximity / coefficient output), 1 global reductions,
 // 2 shared-memory staged reductions (n * 4 bytes of shared memory)
 cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,

@@ -5,11 +5,13 @@
 // copy, or columns of the CSC copy of A), hence one contiguous slice of the
 // index and value arrays.  One producer lane streams that slice into a
 // four-stage shared-memory ring with 1-D bulk copies (cp.async.bulk, L2
-// evict-first) tracked by mbarriers; fifteen consumer warps take the items
-// round-robin and read them from the ring, so HBM streaming runs ahead of the
-// gathers of x (or of the coefficients) from L2 instead of waiting behind
-// them.  A consumer releases a stage once every item it owns there is done;
-// the producer refills a stage when all consumers released it.
+// evict-first) tracked by mbarriers; twenty-three consumer warps, split into
+// groups of G lanes (one group per item, G chosen from the item lengths), take
+// the items round-robin and read them from the ring four elements per 16-byte
+// access, so HBM streaming runs ahead of the gathers of x (or of the
+// coefficients) instead of waiting behind them.  A consumer warp releases a
+// stage once its items there are done; the producer refills a stage when all
+// consumer warps released it.
 //
 //  * row pass: r_i = <a_i, x>, d_i = clamp(r_i, l_i, u_i) - r_i, the FP64
 //    proximity term, and either coef_i = lambda w_i d_i / ||a_i||^2 written
@@ -89,19 +91,93 @@ template <typename VT>
 __device__ __forceinline__ float to_f(VT v) { return (float)v; }
 
 // Ring of the CTA's slice: element g of the slice (counted from the aligned
-// start Ea) lives at ring position g & mask.
+// start Ea) lives at ring position g & mask; groups of four elements starting
+// at a multiple of four are contiguous and 16-byte aligned in the ring.
 template <typename VT>
 struct Ring {
     const VT* val;
     const int* idx;
-    long long ea;   // aligned slice start (global element index)
     int mask;
 };
 
-// Producer / consumer skeleton.  work(item, ring, lane) runs in a consumer
-// warp for each of its items; returns the FP64 proximity contribution of the
-// item (lane 0), zero elsewhere.
-template <typename VT, class Work>
+template <typename VT>
+struct Quad;
+template <>
+struct Quad<float> {
+    static __device__ __forceinline__ float4 load(const float* p) {
+        return *reinterpret_cast<const float4*>(p);
+    }
+};
+template <>
+struct Quad<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 load(const __nv_bfloat16* p) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                           __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    }
+};
+template <>
+struct Quad<__half> {
+    static __device__ __forceinline__ float4 load(const __half* p) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
+template <int G>
+__device__ __forceinline__ unsigned gmask_of(int lane) {
+    if constexpr (G == 32) return 0xffffffffu;
+    else return ((1u << G) - 1u) << (lane & ~(G - 1));
+}
+
+// sum_e a_e * vec[idx_e] over the item's elements held in the ring, by the
+// G lanes of one group reading four elements per 16-byte ring access.
+template <typename VT, int G>
+__device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, int gl,
+                                          const float* __restrict__ vec) {
+    constexpr int U = 4;
+    const int q0 = g0 >> 2, q1 = (g0 + len + 3) >> 2;
+    const int e_hi = g0 + len;
+    float acc = 0.f;
+    for (int qb = q0 + gl; qb < q1; qb += G * U) {
+        float4 v[U];
+        int4 c[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = qb + u * G;
+            const int e = q << 2;
+            if (q < q1) {
+                const int pos = e & r.mask;
+                v[u] = Quad<VT>::load(r.val + pos);
+                c[u] = *reinterpret_cast<const int4*>(r.idx + pos);
+                // mask the neighbours' elements that share the first / last quad
+                if (e < g0 || e >= e_hi) { v[u].x = 0.f; c[u].x = 0; }
+                if (e + 1 < g0 || e + 1 >= e_hi) { v[u].y = 0.f; c[u].y = 0; }
+                if (e + 2 < g0 || e + 2 >= e_hi) { v[u].z = 0.f; c[u].z = 0; }
+                if (e + 3 >= e_hi) { v[u].w = 0.f; c[u].w = 0; }
+            } else {
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                c[u] = make_int4(0, 0, 0, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            acc = fmaf(v[u].x, __ldg(vec + c[u].x), acc);
+            acc = fmaf(v[u].y, __ldg(vec + c[u].y), acc);
+            acc = fmaf(v[u].z, __ldg(vec + c[u].z), acc);
+            acc = fmaf(v[u].w, __ldg(vec + c[u].w), acc);
+        }
+    }
+    return acc;
+}
+
+// Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes;
+// in each round the groups of a warp take consecutive items, so a warp's
+// items cover a contiguous element range.  work(item, len, g0, ring, gl)
+// returns the FP64 proximity contribution of the item (one lane), else 0.
+template <typename VT, int G, class Work>
 __device__ double stream_items(const StreamArgs& a, Work work) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
@@ -113,6 +189,7 @@ __device__ double stream_items(const StreamArgs& a, Work work) {
     uint64_t* empty = full + kStages;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = kStreamThreads / 32 - 1;
+    constexpr int GPW = 32 / G;
     const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
     double acc = 0.0;
     if (I0 >= I1) return 0.0;   // uniform over the CTA
@@ -155,10 +232,13 @@ __device__ double stream_items(const StreamArgs& a, Work work) {
             }
         }
     } else {
-        const Ring<VT> ring{sval, sidx, Ea, RING - 1};
+        const Ring<VT> ring{sval, sidx, RING - 1};
+        const int gw = lane / G, gl = lane % G;
         int next_rel = 0;
         bool ok = true;
-        auto wait_tile = [&](int k) { return mbar_wait(&full[k % kStages], (k / kStages) & 1, &abort_flag); };
+        auto wait_tile = [&](int k) {
+            return mbar_wait(&full[k % kStages], (k / kStages) & 1, &abort_flag);
+        };
         auto release_upto = [&](int kend) {
             for (; ok && next_rel < kend; ++next_rel) {
                 if (!__all_sync(0xffffffffu, wait_tile(next_rel))) {
@@ -169,17 +249,25 @@ __device__ double stream_items(const StreamArgs& a, Work work) {
                 if (lane == 0) mbar_arrive(&empty[next_rel % kStages]);
             }
         };
-        for (int i = I0 + (warp - 1); ok && i < I1; i += NW) {
-            const int2 inf = a.info[i];
-            if (inf.y == 0) continue;   // an empty item needs no data (and contributes nothing)
-            const long long g0 = (long long)inf.x - Ea;
-            const int k0 = (int)(g0 / T);
-            const int k1 = (int)((g0 + (inf.y > 0 ? inf.y - 1 : 0)) / T);
-            release_upto(k0);
-            for (int k = max(k0, next_rel); ok && k <= k1; ++k)
+        constexpr int BIG = 0x7fffffff;
+        for (int base = I0 + (warp - 1) * GPW; ok && base < I1; base += NW * GPW) {
+            const int i = base + gw;
+            int2 inf = make_int2(0, 0);
+            if (i < I1) inf = a.info[i];
+            const int g0 = (int)((long long)inf.x - Ea);
+            int kb = BIG, ke = -1;
+            if (inf.y > 0) {
+                kb = (int)(g0 / T);
+                ke = (int)((g0 + inf.y - 1) / T);
+            }
+            kb = __reduce_min_sync(0xffffffffu, kb);
+            ke = __reduce_max_sync(0xffffffffu, ke);
+            if (ke < 0) continue;   // no data needed by this warp in this round
+            release_upto(kb);
+            for (int k = max(kb, next_rel); ok && k <= ke; ++k)
                 ok = __all_sync(0xffffffffu, wait_tile(k));
             if (!ok) break;
-            acc += work(i, inf.y, g0, ring, lane);
+            if (i < I1 && inf.y > 0) acc += work(i, inf.y, g0, ring, gl);
         }
         if (ok) release_upto(K);
         if (!ok) {
@@ -204,79 +292,55 @@ __device__ __forceinline__ void cta_sum_to(double v, double* out) {
 }
 
 // Row pass.  SCAT 0: coefficients written to a.coef (when set); 1: scatter.
-template <typename VT, int SCAT>
+template <typename VT, int G, int SCAT>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs a) {
     if (a.check_stop && a.st[0].stopped) return;
     const float* __restrict__ x = a.x;
-    auto work = [&](int i, int len, long long g0, const Ring<VT>& r, int lane) -> double {
-        constexpr int U = 8;
-        float dot = 0.f;
-        for (int t0 = lane; t0 < len; t0 += 32 * U) {
-            float v[U];
-            int c[U];
+    auto work = [&](int i, int len, int g0, const Ring<VT>& r, int gl) -> double {
+        const unsigned gm = gmask_of<G>(threadIdx.x & 31);
+        float dot = ring_dot<VT, G>(r, g0, len, gl, x);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + 32 * u;
-                const int p = (int)((g0 + t) & r.mask);
-                v[u] = (t < len) ? to_f(r.val[p]) : 0.f;
-                c[u] = (t < len) ? r.idx[p] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) dot = fmaf(v[u], __ldg(x + c[u]), dot);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, a.l[i], a.u[i]) - dot;
         const float w = a.wr[i];
         const float coef = a.lam * w * d;
         if (SCAT == 0) {
-            if (a.coef && lane == 0) a.coef[i] = coef;
+            if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
-            for (int t = lane; t < len; t += 32) {
-                const int p = (int)((g0 + t) & r.mask);
+            // lane-strided over the elements: consecutive lanes, consecutive columns
+            for (int t = gl; t < len; t += G) {
+                const int p = (g0 + t) & r.mask;
                 atomicAdd(a.delta + r.idx[p], coef * to_f(r.val[p]));
             }
         }
-        return lane == 0 ? (double)d * (double)d * (double)w : 0.0;
+        return gl == 0 ? (double)d * (double)d * (double)w : 0.0;
     };
-    const double prox = stream_items<VT>(a, work);
+    const double prox = stream_items<VT, G>(a, work);
     cta_sum_to(prox, a.pp + blockIdx.x);
 }
 
 // Column pass of the two-pass sweep (B = 1).
-template <typename VT>
+template <typename VT, int G>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs a) {
     if (a.epi.st[0].stopped) return;   // the row pass left no coefficients
     const float* __restrict__ coef = a.coef_in;
-    auto work = [&](int j, int len, long long g0, const Ring<VT>& r, int lane) -> double {
-        constexpr int U = 8;
-        float s = 0.f;
-        for (int t0 = lane; t0 < len; t0 += 32 * U) {
-            float v[U];
-            int c[U];
+    auto work = [&](int j, int len, int g0, const Ring<VT>& r, int gl) -> double {
+        const unsigned gm = gmask_of<G>(threadIdx.x & 31);
+        float s = ring_dot<VT, G>(r, g0, len, gl, coef);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = t0 + 32 * u;
-                const int p = (int)((g0 + t) & r.mask);
-                v[u] = (t < len) ? to_f(r.val[p]) : 0.f;
-                c[u] = (t < len) ? r.idx[p] : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) s = fmaf(v[u], __ldg(coef + c[u]), s);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0 && len > 0) {
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
+        if (gl == 0) {
             const int bj = (a.box_len == 1) ? 0 : j;
             a.xw[j] = clampf(a.xw[j] + s, a.lo[bj], a.hi[bj]);
         }
         return 0.0;
     };
-    stream_items<VT>(a, work);
+    stream_items<VT, G>(a, work);
     __syncthreads();
     if (blockIdx.x == 0 && !a.epi.last_seg) {
-        // CTA 0 also reduces the row pass's proximity partials (never the
-        // last block: the stop flag is set by a separate launch)
+        // CTA 0 also accumulates the row pass's proximity partials of this
+        // block (never for the last block: the stop flag is set by a
+        // separate launch)
         const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int b = wid; b < a.epi.B; b += kStreamThreads / 32) {
             double s = 0.0;
@@ -293,20 +357,35 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs
 using StreamFn = void (*)(StreamArgs);
 
 template <typename VT>
-StreamFn pick_rows(int scat) {
-    return scat ? k_rows_tma<VT, 1> : k_rows_tma<VT, 0>;
+StreamFn pick_rows(int G, int scat) {
+    switch (G) {
+        case 4: return scat ? k_rows_tma<VT, 4, 1> : k_rows_tma<VT, 4, 0>;
+        case 8: return scat ? k_rows_tma<VT, 8, 1> : k_rows_tma<VT, 8, 0>;
+        case 16: return scat ? k_rows_tma<VT, 16, 1> : k_rows_tma<VT, 16, 0>;
+        default: return scat ? k_rows_tma<VT, 32, 1> : k_rows_tma<VT, 32, 0>;
+    }
 }
 
-StreamFn rows_fn(suppy_dtype dt, int scat) {
-    if (dt == SUPPY_F32) return pick_rows<float>(scat);
-    if (dt == SUPPY_BF16) return pick_rows<__nv_bfloat16>(scat);
-    return pick_rows<__half>(scat);
+template <typename VT>
+StreamFn pick_cols(int G) {
+    switch (G) {
+        case 4: return k_cols_tma<VT, 4>;
+        case 8: return k_cols_tma<VT, 8>;
+        case 16: return k_cols_tma<VT, 16>;
+        default: return k_cols_tma<VT, 32>;
+    }
 }
 
-StreamFn cols_fn(suppy_dtype dt) {
-    if (dt == SUPPY_F32) return k_cols_tma<float>;
-    if (dt == SUPPY_BF16) return k_cols_tma<__nv_bfloat16>;
-    return k_cols_tma<__half>;
+StreamFn rows_fn(suppy_dtype dt, int G, int scat) {
+    if (dt == SUPPY_F32) return pick_rows<float>(G, scat);
+    if (dt == SUPPY_BF16) return pick_rows<__nv_bfloat16>(G, scat);
+    return pick_rows<__half>(G, scat);
+}
+
+StreamFn cols_fn(suppy_dtype dt, int G) {
+    if (dt == SUPPY_F32) return pick_cols<float>(G);
+    if (dt == SUPPY_BF16) return pick_cols<__nv_bfloat16>(G);
+    return pick_cols<__half>(G);
 }
 
 }  // namespace
@@ -327,18 +406,18 @@ static cudaError_t launch_stream(StreamFn f, const StreamArgs& a, suppy_dtype dt
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int scat, int grid,
+cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
                             cudaStream_t s) {
-    return launch_stream(rows_fn(dt, scat), a, dt, grid, s);
+    return launch_stream(rows_fn(dt, G, scat), a, dt, grid, s);
 }
 
-cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int grid, cudaStream_t s) {
-    return launch_stream(cols_fn(dt), a, dt, grid, s);
+cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s) {
+    return launch_stream(cols_fn(dt, G), a, dt, grid, s);
 }
 
 int stream_blocks_per_sm(suppy_dtype dt, int tile) {
     const size_t smem = stream_smem_bytes(dt, tile);
-    StreamFn f = rows_fn(dt, 1);
+    StreamFn f = rows_fn(dt, 32, 1);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
