@@ -13,7 +13,7 @@ namespace suppy {
 
 constexpr int kSweepThreads = 256;     // threads per CTA of the sweep kernels
 constexpr int kFinalizeThreads = 256;
-constexpr int kPerturbThreads = 512;   // threads per CTA of the perturbation cluster
+constexpr int kPerturbThreads = 1024;  // threads per CTA of the perturbation cluster
 constexpr int kMaxRhs = 32;
 
 // Per right-hand-side iteration state, resident on the device so that the
@@ -159,7 +159,7 @@ struct StreamArgs {
 
 // --- launchers (defined in sweep.cu / stream.cu / perturb.cu / setup.cu) ----
 size_t stream_smem_bytes(suppy_dtype dt, int tile);
-int stream_max_item(int tile);
+int stream_max_item(int tile);   // longest item a ring window holds
 int stream_blocks_per_sm(suppy_dtype dt, int tile);
 cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
                             cudaStream_t s);

@@ -27,8 +27,9 @@
 namespace suppy {
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr long long kWaitCycles = 4000000000LL;
+constexpr uint32_t kSuspendNs = 2000;   // a waiting thread sleeps up to this long per try
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -53,10 +54,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -91,13 +92,18 @@ template <typename VT>
 __device__ __forceinline__ float to_f(VT v) { return (float)v; }
 
 // Ring of the CTA's slice: element g of the slice (counted from the aligned
-// start Ea) lives at ring position g & mask; groups of four elements starting
-// at a multiple of four are contiguous and 16-byte aligned in the ring.
+// start Ea) lies in tile g / T, held by stage (g / T) % kStages at offset
+// g % T; groups of four elements starting at a multiple of four never straddle
+// a tile and are 16-byte aligned in the ring.
 template <typename VT>
 struct Ring {
     const VT* val;
     const int* idx;
-    int mask;
+    int tshift;   // log2(T)
+    __device__ __forceinline__ int pos(int g) const {
+        const int k = g >> tshift;
+        return ((k % kStages) << tshift) | (g & ((1 << tshift) - 1));
+    }
 };
 
 template <typename VT>
@@ -149,7 +155,7 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
             const int q = qb + u * G;
             const int e = q << 2;
             if (q < q1) {
-                const int pos = e & r.mask;
+                const int pos = r.pos(e);
                 v[u] = Quad<VT>::load(r.val + pos);
                 c[u] = *reinterpret_cast<const int4*>(r.idx + pos);
                 // mask the neighbours' elements that share the first / last quad
@@ -232,7 +238,7 @@ __device__ double stream_items(const StreamArgs& a, Work work) {
             }
         }
     } else {
-        const Ring<VT> ring{sval, sidx, RING - 1};
+        const Ring<VT> ring{sval, sidx, 31 - __clz(T)};
         const int gw = lane / G, gl = lane % G;
         int next_rel = 0;
         bool ok = true;
@@ -298,18 +304,19 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs
     const float* __restrict__ x = a.x;
     auto work = [&](int i, int len, int g0, const Ring<VT>& r, int gl) -> double {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
+        // issue the row's bound and weight loads before the gathers
+        const float li = __ldg(a.l + i), ui = __ldg(a.u + i), w = __ldg(a.wr + i);
         float dot = ring_dot<VT, G>(r, g0, len, gl, x);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
-        const float d = clampf(dot, a.l[i], a.u[i]) - dot;
-        const float w = a.wr[i];
+        const float d = clampf(dot, li, ui) - dot;
         const float coef = a.lam * w * d;
         if (SCAT == 0) {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
             // lane-strided over the elements: consecutive lanes, consecutive columns
             for (int t = gl; t < len; t += G) {
-                const int p = (g0 + t) & r.mask;
+                const int p = r.pos(g0 + t);
                 atomicAdd(a.delta + r.idx[p], coef * to_f(r.val[p]));
             }
         }
@@ -326,13 +333,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs
     const float* __restrict__ coef = a.coef_in;
     auto work = [&](int j, int len, int g0, const Ring<VT>& r, int gl) -> double {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
+        const int bj = (a.box_len == 1) ? 0 : j;
+        const float xj = a.xw[j], lo = __ldg(a.lo + bj), hi = __ldg(a.hi + bj);   // before the gathers
         float s = ring_dot<VT, G>(r, g0, len, gl, coef);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
-        if (gl == 0) {
-            const int bj = (a.box_len == 1) ? 0 : j;
-            a.xw[j] = clampf(a.xw[j] + s, a.lo[bj], a.hi[bj]);
-        }
+        if (gl == 0) a.xw[j] = clampf(xj + s, lo, hi);
         return 0.0;
     };
     stream_items<VT, G>(a, work);

@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(cons
         if (!CHECKED(ri.x >= 0 && (long long)ri.x + len <= a.nnz, 2, i)) continue;
         const VT* vrow = val + ri.x;
         const int* crow = colp + ri.x;
+        const float li = __ldg(a.l + i), ui = __ldg(a.u + i), w = __ldg(a.wr + i);
         float v[HOLD > 0 ? HOLD : 1];
         int c[HOLD > 0 ? HOLD : 1];
         float dot = 0.f;
@@ -250,8 +251,7 @@ __global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(cons
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gmask, dot, o);
 
-        const float d = clampf(dot, a.l[i], a.u[i]) - dot;
-        const float w = a.wr[i];
+        const float d = clampf(dot, li, ui) - dot;
         if (lane == 0) prox += (double)d * (double)d * (double)w;
         const float coef = a.lam * w * d;
         if constexpr (SCAT == 0) {
