@@ -411,7 +411,7 @@ def test_tma_block_iterative_and_long_rows():
         ctx.suppy_sweep(_params(), 1)
         xo, _ = _oracle_sweep(prob, x0, O.BIP)
         assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
-    longp = synth.random_problem(300, 30000, seed=43, mean_len=60, long_rows=3, long_len=13000)
+    longp = synth.random_problem(300, 30000, seed=43, mean_len=60, long_rows=3, long_len=25000)
     ctx = pk.from_problem(longp, strategy=pk.STRATEGY_TWO_PASS)
     assert ctx.suppy_info_get()["tma"] == 0
     x0 = random_x(30000, 1, seed=44)
