@@ -692,7 +692,8 @@ void tma_partition(const std::vector<long long>& pref, int i0, int i1, int grid,
 // (several items per warp) for short items, as long as the items a warp takes
 // in one round fit the ring's window.
 int stream_group(double mean_len, int max_item, int tile) {
-    int g = mean_len >= 128 ? 32 : (mean_len >= 48 ? 16 : (mean_len >= 16 ? 8 : 4));
+    // about 1.5K elements per warp and round
+    int g = mean_len >= 768 ? 32 : (mean_len >= 384 ? 16 : (mean_len >= 96 ? 8 : 4));
     while (g < 32 && (long long)(32 / g) * max_item > stream_max_item(tile)) g *= 2;
     return g;
 }

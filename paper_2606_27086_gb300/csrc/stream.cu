@@ -182,9 +182,11 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
 // Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes;
 // in each round the groups of a warp take consecutive items, so a warp's
 // items cover a contiguous element range.  work(item, len, g0, ring, gl)
-// returns the FP64 proximity contribution of the item (one lane), else 0.
+// returns the FP64 proximity contribution of the item (one lane), else 0;
+// work.prefetch(next item or -1) loads the next round's per-item operands and
+// work.advance() makes them current.
 template <typename VT, int G, class Work>
-__device__ double stream_items(const StreamArgs& a, Work work) {
+__device__ double stream_items(const StreamArgs& a, Work& work) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
     const int T = a.tile;
@@ -256,24 +258,34 @@ __device__ double stream_items(const StreamArgs& a, Work work) {
             }
         };
         constexpr int BIG = 0x7fffffff;
-        for (int base = I0 + (warp - 1) * GPW; ok && base < I1; base += NW * GPW) {
+        // the next round's item descriptor is loaded while this round runs
+        int base = I0 + (warp - 1) * GPW;
+        int2 nxt = make_int2(0, 0);
+        if (base + gw < I1) nxt = a.info[base + gw];
+        for (; ok && base < I1; base += NW * GPW) {
             const int i = base + gw;
-            int2 inf = make_int2(0, 0);
-            if (i < I1) inf = a.info[i];
+            const int2 inf = nxt;
+            const int inext = i + NW * GPW;
+            nxt = (inext < I1) ? a.info[inext] : make_int2(0, 0);
+            work.prefetch(inext < I1 ? inext : -1);
             const int g0 = (int)((long long)inf.x - Ea);
             int kb = BIG, ke = -1;
             if (inf.y > 0) {
-                kb = (int)(g0 / T);
-                ke = (int)((g0 + inf.y - 1) / T);
+                kb = g0 / T;
+                ke = (g0 + inf.y - 1) / T;
             }
             kb = __reduce_min_sync(0xffffffffu, kb);
             ke = __reduce_max_sync(0xffffffffu, ke);
-            if (ke < 0) continue;   // no data needed by this warp in this round
+            if (ke < 0) {
+                work.advance();
+                continue;   // no data needed by this warp in this round
+            }
             release_upto(kb);
             for (int k = max(kb, next_rel); ok && k <= ke; ++k)
                 ok = __all_sync(0xffffffffu, wait_tile(k));
             if (!ok) break;
             if (i < I1 && inf.y > 0) acc += work(i, inf.y, g0, ring, gl);
+            work.advance();
         }
         if (ok) release_upto(K);
         if (!ok) {
@@ -299,14 +311,25 @@ __device__ __forceinline__ void cta_sum_to(double v, double* out) {
 
 // Row pass.  SCAT 0: coefficients written to a.coef (when set); 1: scatter.
 template <typename VT, int G, int SCAT>
-__global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs a) {
-    if (a.check_stop && a.st[0].stopped) return;
-    const float* __restrict__ x = a.x;
-    auto work = [&](int i, int len, int g0, const Ring<VT>& r, int gl) -> double {
+struct RowWork {
+    const StreamArgs& a;
+    float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
+    float nl = 0.f, nu = 0.f, nw = 0.f;     // next round's
+    __device__ void prefetch(int i) {
+        if (i >= 0) {
+            nl = __ldg(a.l + i);
+            nu = __ldg(a.u + i);
+            nw = __ldg(a.wr + i);
+        }
+    }
+    __device__ void advance() {
+        li = nl;
+        ui = nu;
+        w = nw;
+    }
+    __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        // issue the row's bound and weight loads before the gathers
-        const float li = __ldg(a.l + i), ui = __ldg(a.u + i), w = __ldg(a.wr + i);
-        float dot = ring_dot<VT, G>(r, g0, len, gl, x);
+        float dot = ring_dot<VT, G>(r, g0, len, gl, a.x);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;
@@ -321,26 +344,65 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs
             }
         }
         return gl == 0 ? (double)d * (double)d * (double)w : 0.0;
-    };
+    }
+};
+
+template <typename VT, int G, int SCAT>
+__global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs a) {
+    if (a.check_stop && a.st[0].stopped) return;
+    RowWork<VT, G, SCAT> work{a};
+    // the first round's operands
+    {
+        const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int i = I0 + (warp - 1) * (32 / G) + lane / G;
+        work.prefetch(warp > 0 && i < I1 ? i : -1);
+        work.advance();
+    }
     const double prox = stream_items<VT, G>(a, work);
     cta_sum_to(prox, a.pp + blockIdx.x);
 }
 
 // Column pass of the two-pass sweep (B = 1).
 template <typename VT, int G>
-__global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs a) {
-    if (a.epi.st[0].stopped) return;   // the row pass left no coefficients
-    const float* __restrict__ coef = a.coef_in;
-    auto work = [&](int j, int len, int g0, const Ring<VT>& r, int gl) -> double {
+struct ColWork {
+    const StreamArgs& a;
+    float xj = 0.f, lo = 0.f, hi = 0.f;
+    float nx = 0.f, nlo = 0.f, nhi = 0.f;
+    __device__ void prefetch(int j) {
+        if (j >= 0) {
+            const int bj = (a.box_len == 1) ? 0 : j;
+            nx = a.xw[j];   // owned by this group alone during the pass
+            nlo = __ldg(a.lo + bj);
+            nhi = __ldg(a.hi + bj);
+        }
+    }
+    __device__ void advance() {
+        xj = nx;
+        lo = nlo;
+        hi = nhi;
+    }
+    __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        const int bj = (a.box_len == 1) ? 0 : j;
-        const float xj = a.xw[j], lo = __ldg(a.lo + bj), hi = __ldg(a.hi + bj);   // before the gathers
-        float s = ring_dot<VT, G>(r, g0, len, gl, coef);
+        float s = ring_dot<VT, G>(r, g0, len, gl, a.coef_in);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
         if (gl == 0) a.xw[j] = clampf(xj + s, lo, hi);
         return 0.0;
-    };
+    }
+};
+
+template <typename VT, int G>
+__global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs a) {
+    if (a.epi.st[0].stopped) return;   // the row pass left no coefficients
+    ColWork<VT, G> work{a};
+    {
+        const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int j = I0 + (warp - 1) * (32 / G) + lane / G;
+        work.prefetch(warp > 0 && j < I1 ? j : -1);
+        work.advance();
+    }
     stream_items<VT, G>(a, work);
     __syncthreads();
     if (blockIdx.x == 0 && !a.epi.last_seg) {
