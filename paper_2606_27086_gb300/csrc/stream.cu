@@ -13,8 +13,9 @@
 // stage once its items there are done; the producer refills a stage when all
 // consumer warps released it.
 //
-//  * row pass: r_i = <a_i, x>, d_i = clamp(r_i, l_i, u_i) - r_i, the FP64
-//    proximity term, and either coef_i = lambda w_i d_i / ||a_i||^2 written
+//  * row pass: r_i = <a_i, x>, d_i = clamp(r_i, l_i, u_i) - r_i, the
+//    proximity term (compensated FP32 per thread, FP64 across threads and
+//    CTAs), and either coef_i = lambda w_i d_i / ||a_i||^2 written
 //    out (two-pass) or coef_i * a_i scatter-added into delta by address-
 //    coalesced L2 reductions (one-pass);
 //  * column pass: x_j <- clamp(x_j + sum_i a_ij coef_i, lo_j, hi_j).
@@ -315,6 +316,18 @@ struct RowWork {
     const StreamArgs& a;
     float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
     float nl = 0.f, nu = 0.f, nw = 0.f;     // next round's
+    // The group leader's proximity terms are summed in FP32 with Kahan
+    // compensation (error independent of the term count) and widened to FP64
+    // for the CTA and grid reductions: FP64 arithmetic is scarce on GB300 and
+    // a warp-wide FP64 add per row would cost more than the row's gathers.
+    float ps = 0.f, pc = 0.f;
+    __device__ void kahan_add(float v) {
+        const float y = v - pc;
+        const float t = ps + y;
+        pc = (t - ps) - y;
+        ps = t;
+    }
+    __device__ double total() const { return (double)ps - (double)pc; }
     __device__ void prefetch(int i) {
         if (i >= 0) {
             nl = __ldg(a.l + i);
@@ -343,7 +356,8 @@ struct RowWork {
                 atomicAdd(a.delta + r.idx[p], coef * to_f(r.val[p]));
             }
         }
-        return gl == 0 ? (double)d * (double)d * (double)w : 0.0;
+        if (gl == 0) kahan_add(d * d * w);
+        return 0.0;
     }
 };
 
@@ -359,8 +373,8 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs
         work.prefetch(warp > 0 && i < I1 ? i : -1);
         work.advance();
     }
-    const double prox = stream_items<VT, G>(a, work);
-    cta_sum_to(prox, a.pp + blockIdx.x);
+    stream_items<VT, G>(a, work);
+    cta_sum_to(work.total(), a.pp + blockIdx.x);
 }
 
 // Column pass of the two-pass sweep (B = 1).
