@@ -271,6 +271,32 @@ suppy_status suppy_info_get(const suppy_ctx* ctx, suppy_info* out);
 suppy_status suppy_timing_enable(suppy_ctx* ctx, int32_t enable);
 suppy_status suppy_kernel_time(suppy_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 
+/* One simultaneous sweep on caller-provided device buffers, allocating
+ * nothing.  The paper has no counterpart: this is an integration entry point
+ * for callers that cannot allocate device memory where they need a sweep
+ * (an allocator that forbids cudaMalloc after start-up, a fixed memory pool
+ * they own, or a loop that must not take the implicit synchronization of
+ * cudaMalloc/cudaFree).  It computes, for the rows with ||a_i|| > 0,
+ *   x <- clamp(x + lambda * weight * sum_i ((clamp(r_i, l_i, u_i) - r_i) / ||a_i||^2) a_i, lo, hi)
+ * with r = A x, and writes 1/2 weight sum_i d_i^2 / ||a_i||^2 at the input
+ * point to *proximity (a device double; NULL to skip).  weight = 1/m' gives
+ * the equal-weight step of suppy_sweep.
+ *   A            CSR with on_device = 1; l, u (m), box_lo, box_hi (box_len =
+ *                1 or n) and x (n, updated in place) are device pointers.
+ *   stream       cudaStream_t the kernels are enqueued on; asynchronous.
+ * Its scratch (correction accumulator and per-CTA partials) is a static
+ * device array of 4 MiB + 16 KiB that every GPU loading the library holds
+ * until exit; n above 1048576 is rejected with SUPPY_EINVAL.  Every call on a
+ * device shares that array (each call clears what must start at zero), so
+ * calls that can overlap on the GPU race.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress): make that first
+ * call before any stream capture.  Errors: SUPPY_EINVAL for bad arguments,
+ * SUPPY_ECUDA for a failed lookup or launch; messages via
+ * suppy_last_error(NULL). */
+suppy_status suppy_sweep_static(const suppy_csr* A, const float* l, const float* u, float weight,
+                                float lambda, const float* box_lo, const float* box_hi,
+                                int64_t box_len, float* x, double* proximity, void* stream);
+
 /* Number of kernels the library launched on this context so far. */
 int64_t suppy_launch_count(const suppy_ctx* ctx);
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "suppy_set_bounds", "suppy_set_x", "suppy_get_x", "suppy_perturb", "suppy_sweep",
     "suppy_proximity", "suppy_objective", "suppy_run", "suppy_history", "suppy_get_state",
     "suppy_set_state", "suppy_info_get", "suppy_timing_enable", "suppy_kernel_time",
-    "suppy_launch_count", "suppy_last_error", "suppy_version",
+    "suppy_launch_count", "suppy_last_error", "suppy_version", "suppy_sweep_static",
 ]
 
 
@@ -115,6 +115,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_launch_count": (I64, [P]),
         "suppy_last_error": (ctypes.c_char_p, [P]),
         "suppy_version": (ctypes.c_char_p, []),
+        "suppy_sweep_static": (ctypes.c_int, [ctypes.POINTER(suppy_csr), P, P, ctypes.c_float,
+                                              ctypes.c_float, P, P, I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -362,6 +364,22 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
                    block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
                    strategy=strategy, tma=tma, **kw)
+
+
+def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,
+                       proximity=None, stream=None):
+    """One allocation-free sweep on device tensors (see include/suppy.h);
+    x is updated in place, proximity (a one-element float64 device tensor)
+    receives the proximity of the input point."""
+    lib = load_library()
+    keep = []
+    A = _csr(row_ptr, col, val, m, n, keep)
+    args = [_ptr(t)[0] for t in (l, u, box_lo, box_hi, x)]
+    bl = box_lo.shape[0] if hasattr(box_lo, "shape") else len(box_lo)
+    pp = _ptr(proximity)[0] if proximity is not None else None
+    st = lib.suppy_sweep_static(ctypes.byref(A), args[0], args[1], float(weight), float(lam),
+                                args[2], args[3], int(bl), args[4], pp, _stream_handle(stream))
+    _check(st, None)
 
 
 def version() -> str:

@@ -20,6 +20,10 @@ thread_local std::string g_err;
 
 }  // namespace
 
+namespace suppy {
+void set_thread_error(const std::string& msg) { g_err = msg; }
+}  // namespace suppy
+
 struct suppy_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "suppy.h"
 
 namespace suppy {
@@ -215,6 +217,9 @@ cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s);
 // device word (kernel tag, index) and the access is skipped.
 cudaError_t read_check_word(int* out3);   // {tag, index low, index high}; resets the word
 cudaError_t read_check_word_perturb(int* out3);
+
+// Set the message suppy_last_error(NULL) returns on this thread (api.cu).
+void set_thread_error(const std::string& msg);
 
 // --- device helpers ---------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
