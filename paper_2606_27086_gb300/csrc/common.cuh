@@ -15,7 +15,7 @@ namespace suppy {
 
 constexpr int kSweepThreads = 256;     // threads per CTA of the sweep kernels
 constexpr int kFinalizeThreads = 256;
-constexpr int kPerturbThreads = 1024;  // threads per CTA of the perturbation cluster
+constexpr int kPerturbThreads = 512;   // threads per CTA of the perturbation cluster
 constexpr int kMaxRhs = 32;
 
 // Per right-hand-side iteration state, resident on the device so that the

@@ -250,6 +250,20 @@ struct Band {
 
 __device__ __forceinline__ int band_start(int r, int H, int cs) { return (int)((long long)H * r / cs); }
 
+// Per-thread compensated FP32 sum (Kahan); widened to FP64 for the cluster
+// reduction.  FP64 arithmetic is scarce on GB300: one FP64 add per pixel and
+// pass would cost more than the stencil itself.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <class Y>
 __device__ __forceinline__ float tv_term(int obj, int i, int j, int H, int W, const Y& y) {
     const float y0 = y(i, j);
@@ -271,22 +285,23 @@ __device__ __forceinline__ float tv_subgrad(int obj, int i, int j, int H, int W,
     const float y0 = y(i, j);
     float g = 0.f;
     if (obj == SUPPY_OBJ_TV_ISO) {
+        // each term contributes (its partial derivative) * 1/phi, phi = 0 -> 0
         if (i < H - 1 && j < W - 1) {
             const float dx = y(i + 1, j) - y0, dy = y(i, j + 1) - y0;
-            const float phi = sqrtf(dx * dx + dy * dy);
-            if (phi > 0.f) g -= (dx + dy) / phi;
+            const float q = dx * dx + dy * dy;
+            if (q > 0.f) g -= (dx + dy) * rsqrtf(q);
         }
         if (i > 0 && j < W - 1) {
             const float ym = y(i - 1, j);
             const float dx = y0 - ym, dy = y(i - 1, j + 1) - ym;
-            const float phi = sqrtf(dx * dx + dy * dy);
-            if (phi > 0.f) g += dx / phi;
+            const float q = dx * dx + dy * dy;
+            if (q > 0.f) g += dx * rsqrtf(q);
         }
         if (j > 0 && i < H - 1) {
             const float yl = y(i, j - 1);
             const float dx = y(i + 1, j - 1) - yl, dy = y0 - yl;
-            const float phi = sqrtf(dx * dx + dy * dy);
-            if (phi > 0.f) g += dy / phi;
+            const float q = dx * dx + dy * dy;
+            if (q > 0.f) g += dy * rsqrtf(q);
         }
         return g;
     }
@@ -350,22 +365,25 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     double f_start = 0.0;
     for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
         double gg = 0.0, fy = 0.0;
+        KSum kg, kf;
         for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
             if (lin) {
                 const int p = p0 + q;
                 fy += a.c64[p] * (double)ys[q];
                 const float gp = gs[q];
-                gg += (double)gp * (double)gp;
+                kg.add(gp * gp);
             } else {
                 const int i = r0 + q / W, j = q % W;
-                fy += (double)tv_term(a.obj, i, j, H, W, yb);
+                kf.add(tv_term(a.obj, i, j, H, W, yb));
                 if (!a.record_only) {
                     const float gp = tv_subgrad(a.obj, i, j, H, W, yb);
                     gs[q] = gp;
-                    gg += (double)gp * (double)gp;
+                    kg.add(gp * gp);
                 }
             }
         }
+        gg += kg.value();
+        fy += kf.value();
         const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
         gg = r.x;
         fy = r.y;
@@ -384,8 +402,10 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
                     fz += a.c64[p0 + q] * (double)trial(ys[q], gs[q], sc);
             } else {
                 auto z = [&yb, &gb, sc](int i, int j) { return trial(yb(i, j), gb(i, j), sc); };
+                KSum kz;
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
-                    fz += (double)tv_term(a.obj, r0 + q / W, q % W, H, W, z);
+                    kz.add(tv_term(a.obj, r0 + q / W, q % W, H, W, z));
+                fz = kz.value();
             }
             fz = cluster_sum2(fz, 0.0, sw, &scta, cluster).x;
             if (fz <= fy) {
