@@ -122,6 +122,12 @@ typedef struct {
     /* Streaming of A through shared memory by bulk asynchronous copies (TMA)
      * for one right-hand side: 0 automatic (used when eligible), -1 off. */
     int32_t tma;
+    /* Launch shape of the streaming passes, 0 = automatic (or measured when
+     * tune is set): ring tile length in elements (a power of two, 256..4096),
+     * ring stages (2..32, within the shared-memory budget) and lanes per item
+     * (4, 8, 16 or 32).  Values outside these ranges give SUPPY_EINVAL; a shape
+     * whose ring window cannot hold a warp's items leaves streaming off. */
+    int32_t stream_tile, stream_stages, stream_lanes;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -169,6 +175,8 @@ typedef struct {
     int32_t col_lanes;            /* two passes: lanes per column            */
     int32_t col_grid;             /* two passes: CTAs of the column pass     */
     int32_t tma;                  /* 1: the sweep streams A by bulk copies   */
+    int32_t tile, stages;         /* streaming row pass: ring tile length (elements), stages */
+    int32_t col_tile, col_stages; /* streaming column pass: the same       */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

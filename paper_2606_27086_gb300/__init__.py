@@ -47,7 +47,9 @@ class suppy_opts(ctypes.Structure):
                 ("obj", ctypes.c_int), ("img_h", ctypes.c_int32), ("img_w", ctypes.c_int32),
                 ("c_lin", ctypes.c_void_p), ("obj_rows", ctypes.POINTER(suppy_csr)),
                 ("nrhs", ctypes.c_int32), ("box_len", ctypes.c_int64), ("tune", ctypes.c_int32),
-                ("strategy", ctypes.c_int32), ("tma", ctypes.c_int32)]
+                ("strategy", ctypes.c_int32), ("tma", ctypes.c_int32),
+                ("stream_tile", ctypes.c_int32), ("stream_stages", ctypes.c_int32),
+                ("stream_lanes", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -76,7 +78,9 @@ class suppy_info(ctypes.Structure):
                 ("perturb_cluster", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("strategy", ctypes.c_int32), ("scatter", ctypes.c_int32),
                 ("col_lanes", ctypes.c_int32), ("col_grid", ctypes.c_int32),
-                ("tma", ctypes.c_int32)]
+                ("tma", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("stages", ctypes.c_int32), ("col_tile", ctypes.c_int32),
+                ("col_stages", ctypes.c_int32)]
 
 
 _lib = None
@@ -188,7 +192,8 @@ class Context:
 
     def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
-                 c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None):
+                 c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None,
+                 stream_shape=(0, 0, 0)):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -223,6 +228,7 @@ class Context:
         o.tune = int(tune)
         o.strategy = int(strategy)
         o.tma = int(tma)
+        o.stream_tile, o.stream_stages, o.stream_lanes = (int(v) for v in stream_shape)
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
@@ -340,7 +346,7 @@ class Context:
 
 
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
-                 stream=None, tune=0, strategy=0, tma=0) -> Context:
+                 stream=None, tune=0, strategy=0, tma=0, stream_shape=(0, 0, 0)) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -363,7 +369,7 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
     blocks = prob.blocks if mode == SUPPY_BIP else None
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
                    block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
-                   strategy=strategy, tma=tma, **kw)
+                   strategy=strategy, tma=tma, stream_shape=stream_shape, **kw)
 
 
 def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,

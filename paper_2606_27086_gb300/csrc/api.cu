@@ -18,6 +18,14 @@ namespace {
 
 thread_local std::string g_err;
 
+// Longest ring tile of the streaming passes; the packed copies of A carry
+// this much zeroed slack after the last item, since a pass reads whole tiles.
+constexpr int kMaxTile = 4096;
+
+// Stored length of an item: rows and columns start at multiples of four
+// elements and are zero-padded to a multiple of four.
+inline long long pad4(long long len) { return (len + 3) & ~3LL; }
+
 }  // namespace
 
 namespace suppy {
@@ -29,6 +37,7 @@ struct suppy_ctx {
     cudaStream_t stream = nullptr;
     int m = 0, n = 0, B_user = 1, B = 1;
     long long nnz = 0;
+    long long nnz_pad = 0;          // storage length of the row copy (rows padded to 4)
     suppy_dtype dt = SUPPY_F32;
     suppy_mode mode = SUPPY_CIMMINO;
     suppy_obj obj = SUPPY_OBJ_NONE;
@@ -77,6 +86,7 @@ struct suppy_ctx {
     int* d_cpart = nullptr;         // nseg x (cgroups + 1)
     std::vector<long long> cpref;   // per segment column-work prefix (nseg x (n + 1))
     long long nnz_csc = 0;
+    long long csc_len = 0;          // storage length of the CSC copy (columns padded to 4)
 
     // launch shapes
     int strategy = 1;               // 1 one pass, 2 two passes
@@ -88,7 +98,8 @@ struct suppy_ctx {
     std::vector<size_t> seg_part_off, seg_cpart_off;
     // TMA-fed streaming passes (B = 1): CTA item ranges per block
     bool use_tma = false;
-    int tile = 4096;
+    int tile = 4096, stages = 6;    // row pass ring: tile length, stages
+    int ctile = 4096, cstages = 6;  // column pass ring
     int tG = 32, tGc = 32;          // lanes per item of the streaming row / column passes
     int max_row = 0, max_col = 0;
     std::vector<int> seg_tgrid, seg_ctgrid;
@@ -328,7 +339,7 @@ SweepArgs row_args(suppy_ctx* c, int t, float lam) {
     a.n = c->n;
     a.check_stop = 1;
     a.m = c->m;
-    a.nnz = c->nnz;
+    a.nnz = c->nnz_pad;
     return a;
 }
 
@@ -381,6 +392,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             sa.val = c->d_val;
             sa.cta_items = c->d_tpart + c->seg_tpart_off[t];
             sa.tile = c->tile;
+            sa.stages = c->stages;
             sa.err = c->d_err;
             sa.l = c->d_l;
             sa.u = c->d_u;
@@ -409,7 +421,8 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.idx = c->d_ridx;
                 ca.val = c->d_cval;
                 ca.cta_items = c->d_ctpart + c->seg_ctpart_off[t];
-                ca.tile = c->tile;
+                ca.tile = c->ctile;
+                ca.stages = c->cstages;
                 ca.err = c->d_err;
                 ca.coef_in = c->d_coef;
                 ca.xw = c->d_x;
@@ -458,7 +471,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.cpart = c->d_cpart + c->seg_cpart_off[t];
             ca.n = c->n;
             ca.m = c->m;
-            ca.nnz = c->nnz_csc;
+            ca.nnz = c->csc_len;
             ca.epi = epi;
             Timed tm{c, 1};
             CK(tm.begin());
@@ -692,22 +705,90 @@ void tma_partition(const std::vector<long long>& pref, int i0, int i1, int grid,
     out[grid] = i1;
 }
 
-// Lanes per item of a streaming pass: wide groups for long items, narrow ones
-// (several items per warp) for short items, as long as the items a warp takes
-// in one round fit the ring's window.
-int stream_group(double mean_len, int max_item, int tile) {
-    // about 1.5K elements per warp and round
-    int g = mean_len >= 768 ? 32 : (mean_len >= 384 ? 16 : (mean_len >= 96 ? 8 : 4));
-    while (g < 32 && (long long)(32 / g) * max_item > stream_max_item(tile)) g *= 2;
+// The items one warp takes in a round (32/G of them) must fit the ring's
+// window of S - 1 tiles.
+bool group_fits(int G, int max_item, int tile, int stages) {
+    return (long long)(32 / G) * max_item <= stream_max_item(tile, stages);
+}
+
+// Lanes per item of a streaming pass.  The items all consumer warps hold in
+// one round must fill well under half of the ring, so that the rest streams
+// ahead of them; within that, narrow groups (several items per warp) keep
+// more gathers in flight per lane.
+int stream_group(double mean_len, int max_item, int tile, int stages) {
+    const double budget = 0.45 * (double)stages * tile / (kStreamThreads / 32 - 1);
+    int g = 4;
+    while (g < 32 && ((32 / g) * mean_len > budget || !group_fits(g, max_item, tile, stages))) g *= 2;
     return g;
 }
 
+// Default ring and group shapes of the streaming passes: 4096-element tiles,
+// as many stages as the shared-memory budget holds (6 for FP32 values, 9 for
+// 16-bit values).
+void default_tma_shape(suppy_ctx* c) {
+    c->tile = c->ctile = kMaxTile;
+    c->stages = c->cstages = stream_stages_for(c->dt, kMaxTile);
+    c->tG = stream_group(c->m > 0 ? (double)c->nnz / c->m : 0.0, c->max_row, c->tile, c->stages);
+    if (c->strategy == 2)
+        c->tGc = stream_group((double)c->nnz / c->n / c->nseg, c->max_col, c->ctile, c->cstages);
+}
+
+// Caller-fixed shape (opts->stream_*), the same for both passes; zero fields
+// keep the defaults.
+void apply_stream_shape(suppy_ctx* c, int tile, int stages, int lanes) {
+    if (tile) c->tile = c->ctile = tile;
+    c->stages = c->cstages = stages ? stages : stream_stages_for(c->dt, c->tile);
+    c->tG = lanes ? lanes
+                  : stream_group(c->m > 0 ? (double)c->nnz / c->m : 0.0, c->max_row, c->tile, c->stages);
+    if (c->strategy == 2)
+        c->tGc = lanes ? lanes
+                       : stream_group((double)c->nnz / c->n / c->nseg, c->max_col, c->ctile, c->cstages);
+}
+
+// Device row order inside each block: chunks of 32 consecutive rows are dealt
+// out in a low-discrepancy order (chunk k takes source chunk k*S mod Q, S
+// coprime to Q near Q/phi).  A simultaneous step does not depend on the row
+// order, but the per-row cost of a pass does (how scattered the gathers of a
+// row are): neighbouring rows of the input usually cost alike, so contiguous
+// nnz-balanced CTA ranges of the input order can differ in time, while
+// interleaved chunks give every CTA the same mix.  Rows inside a chunk keep
+// their order, and with it the locality of their gathers.
+void interleave_row_chunks(const std::vector<int>& seg_start, int m, std::vector<int>& perm,
+                           std::vector<int>& seg_of_row) {
+    constexpr int kChunk = 32, kMinChunks = 512;
+    bool any = false;
+    for (size_t t = 0; t + 1 < seg_start.size(); ++t)
+        any |= (seg_start[t + 1] - seg_start[t]) >= kChunk * kMinChunks;
+    if (!any) return;
+    if (perm.empty()) {
+        perm.resize(m);
+        std::iota(perm.begin(), perm.end(), 0);
+        seg_of_row.assign(m, 0);
+    }
+    std::vector<int> out(perm.size());
+    for (size_t t = 0; t + 1 < seg_start.size(); ++t) {
+        const int r0 = seg_start[t], r1 = seg_start[t + 1], len = r1 - r0;
+        if (len < kChunk * kMinChunks) {
+            std::copy(perm.begin() + r0, perm.begin() + r1, out.begin() + r0);
+            continue;
+        }
+        const long long Q = (len + kChunk - 1) / kChunk;
+        long long S = (long long)std::llround((double)Q * 0.6180339887498949);
+        while (std::gcd(S, Q) != 1) ++S;
+        int d = r0;
+        for (long long k = 0; k < Q; ++k) {
+            const long long q = (k * S) % Q;
+            const int a = r0 + (int)(q * kChunk), b = std::min(r1, a + kChunk);
+            for (int i = a; i < b; ++i) out[d++] = perm[i];
+        }
+    }
+    perm.swap(out);
+}
+
 suppy_status build_tma_partitions(suppy_ctx* c) {
-    c->tG = stream_group(c->m > 0 ? (double)c->nnz / c->m : 0.0, c->max_row, c->tile);
-    if (c->strategy == 2) c->tGc = stream_group((double)c->nnz / c->n / c->nseg, c->max_col, c->tile);
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-    const int bps = stream_blocks_per_sm(c->dt, c->tile);
+    const int bps = stream_blocks_per_sm(c->dt, c->tile, c->stages);
     if (bps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the streaming passes");
     const long long per_cta_min = 4LL * c->tile;
     c->seg_tgrid.assign(c->nseg, 0);
@@ -738,11 +819,14 @@ suppy_status build_tma_partitions(suppy_ctx* c) {
         CK(cudaStreamSynchronize(c->stream));
         std::vector<long long> pref(c->n + 1);
         std::vector<int> cpart;
+        const int cbps = stream_blocks_per_sm(c->dt, c->ctile, c->cstages);
+        if (cbps <= 0) return fail(c, SUPPY_ECUDA, "no resident CTA for the streaming column pass");
+        const long long cper_cta_min = 4LL * c->ctile;
         for (int t = 0; t < c->nseg; ++t) {
             const int2* ci = cinfo.data() + (size_t)t * c->n;
-            for (int j = 0; j < c->n; ++j) pref[j + 1] = pref[j] + ci[j].y;
+            for (int j = 0; j < c->n; ++j) pref[j + 1] = pref[j] + pad4(ci[j].y);
             const long long nz = pref[c->n];
-            const long long g = std::min<long long>((long long)sms * bps, (nz + per_cta_min - 1) / per_cta_min);
+            const long long g = std::min<long long>((long long)sms * cbps, (nz + cper_cta_min - 1) / cper_cta_min);
             c->seg_ctgrid[t] = (int)std::max<long long>(1, g);
             c->seg_ctpart_off[t + 1] = c->seg_ctpart_off[t] + c->seg_ctgrid[t] + 1;
             const size_t base = cpart.size();
@@ -785,18 +869,23 @@ suppy_status build_csc(suppy_ctx* c, const std::vector<int>& rp, const int* hcol
     std::vector<int2> cinfo(cells);
     c->cpref.assign((size_t)nseg * (n + 1), 0);
     long long off = 0;
+    long long real = 0;
     for (size_t k = 0; k < cells; ++k) {
         cinfo[k] = make_int2((int)off, (int)cnt[k]);
         const int t = (int)(k / n), j = (int)(k % n);
         long long* pr = c->cpref.data() + (size_t)t * (n + 1);
         pr[j + 1] = pr[j] + cnt[k] + 8;     // column work: entries plus a fixed cost
+        real += cinfo[k].y;
         cnt[k] = off;                       // becomes the cursor
-        off += cinfo[k].y;
+        off += pad4(cinfo[k].y);
     }
-    c->nnz_csc = off;
+    if (off >= (1LL << 31) - kMaxTile - 16)
+        return fail(c, SUPPY_EINVAL, "nnz (padded to four per column) must stay below 2^31");
+    c->nnz_csc = real;
+    c->csc_len = off;
     c->max_col = 0;
     for (size_t k = 0; k < cells; ++k) c->max_col = std::max(c->max_col, cinfo[k].y);
-    std::vector<int> pos((size_t)std::max<long long>(c->nnz, 1));
+    std::vector<int> pos((size_t)std::max<long long>(c->nnz_pad, 1));
     for (int i = 0; i < m; ++i) {
         const int src = perm.empty() ? i : perm[i];
         const size_t base = (size_t)(seg_of_row.empty() ? 0 : seg_of_row[i]) * n;
@@ -806,13 +895,16 @@ suppy_status build_csc(suppy_ctx* c, const std::vector<int>& rp, const int* hcol
     const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
     suppy_status s;
     if ((s = dalloc(c, &c->d_cinfo, cells)) != SUPPY_OK) return s;
-    if ((s = dalloc(c, &c->d_ridx, (size_t)c->nnz + c->tile + 16)) != SUPPY_OK) return s;
+    const size_t clen = (size_t)c->csc_len + kMaxTile + 16;
+    if ((s = dalloc(c, &c->d_ridx, clen)) != SUPPY_OK) return s;
     {
         char* q = nullptr;
-        if ((s = dalloc(c, &q, ((size_t)c->nnz + c->tile + 16) * vsz)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &q, clen * vsz)) != SUPPY_OK) return s;
         c->d_cval = q;
     }
-    CK(cudaMemsetAsync(c->d_ridx, 0, sizeof(int) * ((size_t)c->nnz + c->tile + 16), c->stream));
+    // padding entries: index 0, value 0
+    CK(cudaMemsetAsync(c->d_ridx, 0, sizeof(int) * clen, c->stream));
+    CK(cudaMemsetAsync(c->d_cval, 0, vsz * clen, c->stream));
     if ((s = dalloc(c, &c->d_coef, (size_t)std::max(m, 1) * c->B)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_coef, 0, sizeof(float) * (size_t)std::max(m, 1) * c->B, c->stream));
     CK(cudaMemcpyAsync(c->d_cinfo, cinfo.data(), sizeof(int2) * cells, cudaMemcpyHostToDevice,
@@ -843,6 +935,7 @@ void free_csc(suppy_ctx* c) {
     c->d_coef = nullptr;
     c->d_cpart = nullptr;
     c->nnz_csc = 0;
+    c->csc_len = 0;
     c->cpref.clear();
     c->cpref.shrink_to_fit();
 }
@@ -897,9 +990,67 @@ bool tma_eligible(const suppy_ctx* c, int want) {
     if (want < 0) return false;                 // disabled by the caller
     if (c->B != 1) return false;
     if (c->strategy == 1 && c->scat != 1) return false;
-    if (c->max_row > stream_max_item(c->tile)) return false;
-    if (c->strategy == 2 && c->max_col > stream_max_item(c->tile)) return false;
+    if (c->max_row > stream_max_item(c->tile, c->stages)) return false;
+    if (c->strategy == 2 && c->max_col > stream_max_item(c->ctile, c->cstages)) return false;
     return true;
+}
+
+// Measured choice of the streaming passes' shapes: every ring (tile length
+// 1024 / 2048 / 4096 elements, the full shared-memory budget of stages or
+// half of it) and group width (4 .. 32 lanes per item) whose window holds a
+// warp's round is timed on this matrix, first for the row pass, then for the
+// column pass; the fastest stays.
+suppy_status tune_tma(suppy_ctx* c) {
+    struct Shape {
+        int G, tile, stages;
+    };
+    auto cands = [&](int max_item) {
+        std::vector<Shape> v;
+        for (int tile : {1024, 2048, 4096}) {
+            const int full = stream_stages_for(c->dt, tile);
+            for (int st : {full, full / 2}) {
+                if (st < 3 || stream_max_item(tile, st) < max_item) continue;
+                for (int G : {4, 8, 16, 32})
+                    if (group_fits(G, max_item, tile, st)) v.push_back({G, tile, st});
+            }
+        }
+        return v;
+    };
+    suppy_status s;
+    for (int pass = 0; pass < (c->strategy == 2 ? 2 : 1); ++pass) {
+        const std::vector<Shape> v = cands(pass == 0 ? c->max_row : c->max_col);
+        Shape best{pass == 0 ? c->tG : c->tGc, pass == 0 ? c->tile : c->ctile,
+                   pass == 0 ? c->stages : c->cstages};
+        float best_ms = 1e30f;
+        for (const Shape& sh : v) {
+            if (pass == 0) {
+                c->tG = sh.G;
+                c->tile = sh.tile;
+                c->stages = sh.stages;
+            } else {
+                c->tGc = sh.G;
+                c->ctile = sh.tile;
+                c->cstages = sh.stages;
+            }
+            if ((s = build_tma_partitions(c)) != SUPPY_OK) return s;
+            float ms = 0.f;
+            if ((s = time_config(c, &ms)) != SUPPY_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+        if (pass == 0) {
+            c->tG = best.G;
+            c->tile = best.tile;
+            c->stages = best.stages;
+        } else {
+            c->tGc = best.G;
+            c->ctile = best.tile;
+            c->cstages = best.stages;
+        }
+    }
+    return build_tma_partitions(c);
 }
 
 suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, const float* box_lo,
@@ -921,6 +1072,15 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if ((int)c->obj < 0 || (int)c->obj > 3) return fail(c, SUPPY_EINVAL, "unknown objective");
     c->B_user = o->nrhs <= 0 ? 1 : o->nrhs;
     if (c->B_user > kMaxRhs) return fail(c, SUPPY_EINVAL, "nrhs must be at most 32");
+    {
+        const int t = o->stream_tile, st = o->stream_stages, g = o->stream_lanes;
+        if (t != 0 && (t < 256 || t > kMaxTile || (t & (t - 1))))
+            return fail(c, SUPPY_EINVAL, "stream_tile must be 0 or a power of two in [256, 4096]");
+        if (g != 0 && g != 4 && g != 8 && g != 16 && g != 32)
+            return fail(c, SUPPY_EINVAL, "stream_lanes must be 0, 4, 8, 16 or 32");
+        if (st != 0 && (st < 2 || st > stream_stages_for(o->a_dtype, t ? t : kMaxTile)))
+            return fail(c, SUPPY_EINVAL, "stream_stages must be 0 or 2.. the shared-memory budget");
+    }
     c->B = 1;
     if (c->B_user > 1) {
         c->B = 4;
@@ -986,6 +1146,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         c->nseg = 1;
         c->seg_start = {0, m};
     }
+    interleave_row_chunks(c->seg_start, m, perm, seg_of_row);
 
     // row layout in device order (rows of a block contiguous)
     std::vector<int2> rinfo(m);
@@ -996,10 +1157,13 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         const int src = perm.empty() ? i : perm[i];
         const int len = rp[src + 1] - rp[src];
         rinfo[i] = make_int2((int)off, len);
-        off += len;
+        off += pad4(len);
         c->rpref[i + 1] = off;
         max_len = std::max(max_len, len);
     }
+    if (off >= (1LL << 31) - kMaxTile - 16)
+        return fail(c, SUPPY_EINVAL, "nnz (padded to four per row) must stay below 2^31");
+    c->nnz_pad = off;
 
     TempGuard tg;
     tg.s = c->stream;
@@ -1041,13 +1205,16 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     const size_t vsz = (c->dt == SUPPY_F32) ? 4 : 2;
     if ((s = dalloc(c, &c->d_rinfo, (size_t)m)) != SUPPY_OK) return s;
     // slack of one ring stage: the streaming passes read whole stages
-    if ((s = dalloc(c, &c->d_col, (size_t)c->nnz + c->tile + 16)) != SUPPY_OK) return s;
+    const size_t rlen = (size_t)c->nnz_pad + kMaxTile + 16;
+    if ((s = dalloc(c, &c->d_col, rlen)) != SUPPY_OK) return s;
     {
         char* q = nullptr;
-        if ((s = dalloc(c, &q, ((size_t)c->nnz + c->tile + 16) * vsz)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &q, rlen * vsz)) != SUPPY_OK) return s;
         c->d_val = q;
     }
-    CK(cudaMemsetAsync(c->d_col, 0, sizeof(int) * ((size_t)c->nnz + c->tile + 16), c->stream));
+    // padding entries: index 0, value 0
+    CK(cudaMemsetAsync(c->d_col, 0, sizeof(int) * rlen, c->stream));
+    CK(cudaMemsetAsync(c->d_val, 0, vsz * rlen, c->stream));
     if ((s = dalloc(c, &c->d_rho, (size_t)m)) != SUPPY_OK) return s;
     if ((s = dalloc(c, &c->d_wr, (size_t)m)) != SUPPY_OK) return s;
     if (m) CK(cudaMemcpyAsync(c->d_rinfo, rinfo.data(), sizeof(int2) * m, cudaMemcpyHostToDevice,
@@ -1204,6 +1371,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             c->scat = cd.scat;
             choose_row_shape(c, mean_len, max_len);
             if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+            default_tma_shape(c);
             c->use_tma = tma_eligible(c, o->tma);
             if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
             float ms = 0.f;
@@ -1218,8 +1386,18 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     c->scat = best.scat;
     choose_row_shape(c, mean_len, max_len);
     if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+    default_tma_shape(c);
+    const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
+    if (fixed_shape) apply_stream_shape(c, o->stream_tile, o->stream_stages, o->stream_lanes);
     c->use_tma = tma_eligible(c, o->tma);
-    if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
+    if (fixed_shape && c->use_tma && (!group_fits(c->tG, c->max_row, c->tile, c->stages) ||
+                                      (c->strategy == 2 &&
+                                       !group_fits(c->tGc, c->max_col, c->ctile, c->cstages))))
+        c->use_tma = false;
+    if (c->use_tma) {
+        if ((s = build_tma_partitions(c)) != SUPPY_OK) return s;
+        if (o->tune && !fixed_shape && (s = tune_tma(c)) != SUPPY_OK) return s;
+    }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
@@ -1636,6 +1814,10 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->col_lanes = c->strategy == 2 ? c->Gc : 0;
     out->col_grid = (c->strategy == 2 && !c->seg_cgrid.empty()) ? c->seg_cgrid[0] : 0;
     out->tma = c->use_tma ? 1 : 0;
+    out->tile = c->use_tma ? c->tile : 0;
+    out->stages = c->use_tma ? c->stages : 0;
+    out->col_tile = (c->use_tma && c->strategy == 2) ? c->ctile : 0;
+    out->col_stages = (c->use_tma && c->strategy == 2) ? c->cstages : 0;
     if (c->use_tma) {
         out->grid = c->seg_tgrid[0];
         out->block = kStreamThreads;

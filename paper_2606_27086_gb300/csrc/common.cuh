@@ -130,7 +130,8 @@ struct ObjArgs {
 
 // One launch of a TMA-fed streaming pass (stream.cu) over the items
 // [cta_items[0], cta_items[grid]) of one block: rows of the CSR copy (row pass)
-// or columns of the CSC copy (column pass), B = 1.
+// or columns of the CSC copy (column pass), B = 1.  Items start at multiples
+// of four elements and are zero-padded to a multiple of four.
 constexpr int kStreamThreads = 768;
 struct StreamArgs {
     const int2* info;       // per item {start, length}
@@ -138,6 +139,7 @@ struct StreamArgs {
     const void* val;
     const int* cta_items;   // grid + 1 item boundaries
     int tile;               // ring stage length in elements (power of two)
+    int stages;             // ring stages (2..32)
     int* err;               // set to 1 when a bounded wait gives up
     // row pass
     const float* l;
@@ -160,9 +162,10 @@ struct StreamArgs {
 };
 
 // --- launchers (defined in sweep.cu / stream.cu / perturb.cu / setup.cu) ----
-size_t stream_smem_bytes(suppy_dtype dt, int tile);
-int stream_max_item(int tile);   // longest item a ring window holds
-int stream_blocks_per_sm(suppy_dtype dt, int tile);
+size_t stream_smem_bytes(suppy_dtype dt, int tile, int stages);
+int stream_stages_for(suppy_dtype dt, int tile);   // stages filling the shared-memory budget
+int stream_max_item(int tile, int stages);          // longest item a ring window holds
+int stream_blocks_per_sm(suppy_dtype dt, int tile, int stages);
 cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
                             cudaStream_t s);
 cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s);

@@ -3,15 +3,20 @@
 //
 // Each CTA owns a contiguous, nnz-balanced range of items (rows of the CSR
 // copy, or columns of the CSC copy of A), hence one contiguous slice of the
-// index and value arrays.  One producer lane streams that slice into a
-// four-stage shared-memory ring with 1-D bulk copies (cp.async.bulk, L2
-// evict-first) tracked by mbarriers; twenty-three consumer warps, split into
-// groups of G lanes (one group per item, G chosen from the item lengths), take
-// the items round-robin and read them from the ring four elements per 16-byte
-// access, so HBM streaming runs ahead of the gathers of x (or of the
-// coefficients) instead of waiting behind them.  A consumer warp releases a
-// stage once its items there are done; the producer refills a stage when all
-// consumer warps released it.
+// index and value arrays.  One producer lane streams that slice into an
+// S-stage shared-memory ring of T-element tiles with 1-D bulk copies
+// (cp.async.bulk, L2 evict-first) tracked by mbarriers; twenty-three consumer
+// warps, split into groups of G lanes (one group per item), take the items
+// round-robin and read them from the ring four elements per 16-byte access,
+// so HBM streaming runs ahead of the gathers of x (or of the coefficients)
+// instead of waiting behind them.  A consumer warp releases a stage once its
+// items there are done; the producer refills a stage when all consumer warps
+// released it.  G, T and S are launch parameters (chosen per matrix, by
+// measurement when the context is tuned).
+//
+// Items start at multiples of four elements and are zero-padded to a
+// multiple of four (value 0, index 0), so a 16-byte ring access never holds
+// two items' elements and the consumers need no per-element masking.
 //
 //  * row pass: r_i = <a_i, x>, d_i = clamp(r_i, l_i, u_i) - r_i, the
 //    proximity term (compensated FP32 per thread, FP64 across threads and
@@ -23,12 +28,27 @@
 // Every mbarrier wait is bounded (about two seconds of SM clock); on timeout
 // the CTA records an error word, stops, lets its copies in flight land and
 // returns.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace suppy {
+
+#ifdef SUPPY_STREAM_STATS
+// Measurement build only: cycle counters of the streaming skeleton (consumer
+// waits for full tiles, releases, item work, rounds; producer waits for empty
+// stages), summed over warps; slots 0-7 row pass, 8-15 column pass.
+__device__ unsigned long long g_stream_stats[16];
+#define SSTAT_CLOCK() clock64()
+#define SSTAT_ADD(k, v) atomicAdd(&g_stream_stats[(k) + (a.coef_in ? 8 : 0)], (unsigned long long)(v))
+#else
+#define SSTAT_CLOCK() 0LL
+#define SSTAT_ADD(k, v) ((void)0)
+#endif
+
 namespace {
 
-constexpr int kStages = 6;
+constexpr int kMaxStages = 32;
 constexpr long long kWaitCycles = 4000000000LL;
 constexpr uint32_t kSuspendNs = 2000;   // a waiting thread sleeps up to this long per try
 
@@ -93,17 +113,19 @@ template <typename VT>
 __device__ __forceinline__ float to_f(VT v) { return (float)v; }
 
 // Ring of the CTA's slice: element g of the slice (counted from the aligned
-// start Ea) lies in tile g / T, held by stage (g / T) % kStages at offset
-// g % T; groups of four elements starting at a multiple of four never straddle
-// a tile and are 16-byte aligned in the ring.
+// start Ea) lies in tile g / T, held by stage (g / T) % S at offset g % T;
+// the stages are contiguous, so that position is g % (S T).  Groups of four
+// elements starting at a multiple of four never straddle a tile and are
+// 16-byte aligned in the ring.
 template <typename VT>
 struct Ring {
     const VT* val;
     const int* idx;
-    int tshift;   // log2(T)
-    __device__ __forceinline__ int pos(int g) const {
-        const int k = g >> tshift;
-        return ((k % kStages) << tshift) | (g & ((1 << tshift) - 1));
+    int size;     // S * T elements
+    __device__ __forceinline__ int pos(int g) const { return g % size; }
+    __device__ __forceinline__ void step(int& p, int d) const {
+        p += d;
+        if (p >= size) p -= size;
     }
 };
 
@@ -140,44 +162,57 @@ __device__ __forceinline__ unsigned gmask_of(int lane) {
 }
 
 // sum_e a_e * vec[idx_e] over the item's elements held in the ring, by the
-// G lanes of one group reading four elements per 16-byte ring access.
+// G lanes of one group reading four elements per 16-byte ring access.  Lane
+// gl takes the quads gl, gl + G, gl + 2G, ...: four at a time (sixteen gathers
+// in flight), then the remaining two and one.  (A single predicated batch of
+// up to eight quads measured slower on GB300: the extra outstanding gathers
+// only lengthen the queue at L1.)
 template <typename VT, int G>
 __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, int gl,
                                           const float* __restrict__ vec) {
-    constexpr int U = 4;
-    const int q0 = g0 >> 2, q1 = (g0 + len + 3) >> 2;
-    const int e_hi = g0 + len;
-    float acc = 0.f;
-    for (int qb = q0 + gl; qb < q1; qb += G * U) {
-        float4 v[U];
-        int4 c[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int q = qb + u * G;
-            const int e = q << 2;
-            if (q < q1) {
-                const int pos = r.pos(e);
-                v[u] = Quad<VT>::load(r.val + pos);
-                c[u] = *reinterpret_cast<const int4*>(r.idx + pos);
-                // mask the neighbours' elements that share the first / last quad
-                if (e < g0 || e >= e_hi) { v[u].x = 0.f; c[u].x = 0; }
-                if (e + 1 < g0 || e + 1 >= e_hi) { v[u].y = 0.f; c[u].y = 0; }
-                if (e + 2 < g0 || e + 2 >= e_hi) { v[u].z = 0.f; c[u].z = 0; }
-                if (e + 3 >= e_hi) { v[u].w = 0.f; c[u].w = 0; }
-            } else {
-                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                c[u] = make_int4(0, 0, 0, 0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            acc = fmaf(v[u].x, __ldg(vec + c[u].x), acc);
-            acc = fmaf(v[u].y, __ldg(vec + c[u].y), acc);
-            acc = fmaf(v[u].z, __ldg(vec + c[u].z), acc);
-            acc = fmaf(v[u].w, __ldg(vec + c[u].w), acc);
-        }
+    const int nq = (len + 3) >> 2;
+    int q = gl;
+    int p = r.pos(g0 + 4 * gl);
+    float acc0 = 0.f, acc1 = 0.f;
+    auto quad = [&](float4& v, int4& c) {
+        v = Quad<VT>::load(r.val + p);
+        c = *reinterpret_cast<const int4*>(r.idx + p);
+        r.step(p, 4 * G);
+    };
+    auto fma4 = [&](const float4& v, const int4& c) {
+        acc0 = fmaf(v.x, __ldg(vec + c.x), acc0);
+        acc1 = fmaf(v.y, __ldg(vec + c.y), acc1);
+        acc0 = fmaf(v.z, __ldg(vec + c.z), acc0);
+        acc1 = fmaf(v.w, __ldg(vec + c.w), acc1);
+    };
+    for (; q + 3 * G < nq; q += 4 * G) {
+        float4 v0, v1, v2, v3;
+        int4 c0, c1, c2, c3;
+        quad(v0, c0);
+        quad(v1, c1);
+        quad(v2, c2);
+        quad(v3, c3);
+        fma4(v0, c0);
+        fma4(v1, c1);
+        fma4(v2, c2);
+        fma4(v3, c3);
     }
-    return acc;
+    if (q + G < nq) {
+        float4 v0, v1;
+        int4 c0, c1;
+        quad(v0, c0);
+        quad(v1, c1);
+        fma4(v0, c0);
+        fma4(v1, c1);
+        q += 2 * G;
+    }
+    if (q < nq) {
+        float4 v0;
+        int4 c0;
+        quad(v0, c0);
+        fma4(v0, c0);
+    }
+    return acc0 + acc1;
 }
 
 // Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes;
@@ -191,11 +226,13 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
     const int T = a.tile;
-    const int RING = kStages * T;
+    const int S = a.stages;
+    const int RING = S * T;
+    const int ts = 31 - __clz(T);
     VT* sval = reinterpret_cast<VT*>(smraw);
     int* sidx = reinterpret_cast<int*>(smraw + (size_t)RING * sizeof(VT));
     uint64_t* full = reinterpret_cast<uint64_t*>(sidx + RING);
-    uint64_t* empty = full + kStages;
+    uint64_t* empty = full + S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int NW = kStreamThreads / 32 - 1;
     constexpr int GPW = 32 / G;
@@ -207,7 +244,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
     const long long Ea = E0 & ~7LL;
     const int K = (int)((E1 - Ea + T - 1) / T);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], NW);
         }
@@ -221,32 +258,40 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             const uint64_t pol = policy_evict_first();
             const uint32_t bytes_v = (uint32_t)(T * sizeof(VT)), bytes_i = (uint32_t)(T * 4);
             int issued = 0;
-            for (int k = 0; k < K; ++k) {
-                const int s = k % kStages;
-                if (k >= kStages && !mbar_wait(&empty[s], ((k / kStages) - 1) & 1, &abort_flag)) {
+            long long st_t0 = SSTAT_CLOCK(), st_wait = 0;
+            for (int k = 0, s = 0, ph = 0; k < K; ++k) {
+                const long long tw = SSTAT_CLOCK();
+                if (k >= S && !mbar_wait(&empty[s], (ph - 1) & 1, &abort_flag)) {
                     abort_flag = 1;
                     atomicExch(a.err, 1);
                     break;
                 }
+                st_wait += SSTAT_CLOCK() - tw;
                 mbar_arrive_expect_tx(&full[s], bytes_v + bytes_i);
                 bulk_g2s(sval + (size_t)s * T, gval + Ea + (long long)k * T, bytes_v, &full[s], pol);
                 bulk_g2s(sidx + (size_t)s * T, a.idx + Ea + (long long)k * T, bytes_i, &full[s], pol);
                 issued = k + 1;
+                if (++s == S) {
+                    s = 0;
+                    ++ph;
+                }
             }
+            SSTAT_ADD(6, st_wait);
+            SSTAT_ADD(7, SSTAT_CLOCK() - st_t0);
             if (abort_flag) {
                 // let the copies in flight land before the CTA leaves
                 volatile int never = 0;
-                for (int k = (issued > kStages ? issued - kStages : 0); k < issued; ++k)
-                    mbar_wait(&full[k % kStages], (k / kStages) & 1, &never);
+                for (int k = (issued > S ? issued - S : 0); k < issued; ++k)
+                    mbar_wait(&full[k % S], (k / S) & 1, &never);
             }
         }
     } else {
-        const Ring<VT> ring{sval, sidx, 31 - __clz(T)};
+        const Ring<VT> ring{sval, sidx, RING};
         const int gw = lane / G, gl = lane % G;
         int next_rel = 0;
         bool ok = true;
         auto wait_tile = [&](int k) {
-            return mbar_wait(&full[k % kStages], (k / kStages) & 1, &abort_flag);
+            return mbar_wait(&full[k % S], (k / S) & 1, &abort_flag);
         };
         auto release_upto = [&](int kend) {
             for (; ok && next_rel < kend; ++next_rel) {
@@ -255,10 +300,11 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
                     break;
                 }
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[next_rel % kStages]);
+                if (lane == 0) mbar_arrive(&empty[next_rel % S]);
             }
         };
         constexpr int BIG = 0x7fffffff;
+        long long st_t0 = SSTAT_CLOCK(), st_full = 0, st_rel = 0, st_work = 0, st_rounds = 0;
         // the next round's item descriptor is loaded while this round runs
         int base = I0 + (warp - 1) * GPW;
         int2 nxt = make_int2(0, 0);
@@ -272,8 +318,8 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             const int g0 = (int)((long long)inf.x - Ea);
             int kb = BIG, ke = -1;
             if (inf.y > 0) {
-                kb = g0 / T;
-                ke = (g0 + inf.y - 1) / T;
+                kb = g0 >> ts;
+                ke = (g0 + inf.y - 1) >> ts;
             }
             kb = __reduce_min_sync(0xffffffffu, kb);
             ke = __reduce_max_sync(0xffffffffu, ke);
@@ -281,14 +327,30 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
                 work.advance();
                 continue;   // no data needed by this warp in this round
             }
+            long long t1 = SSTAT_CLOCK();
             release_upto(kb);
+            long long t2 = SSTAT_CLOCK();
             for (int k = max(kb, next_rel); ok && k <= ke; ++k)
                 ok = __all_sync(0xffffffffu, wait_tile(k));
+            long long t3 = SSTAT_CLOCK();
             if (!ok) break;
             if (i < I1 && inf.y > 0) acc += work(i, inf.y, g0, ring, gl);
             work.advance();
+            __syncwarp();
+            st_rel += t2 - t1;
+            st_full += t3 - t2;
+            st_work += SSTAT_CLOCK() - t3;
+            st_rounds += 1;
         }
         if (ok) release_upto(K);
+        if (lane == 0) {
+            SSTAT_ADD(0, 1);
+            SSTAT_ADD(1, st_full);
+            SSTAT_ADD(2, st_rel);
+            SSTAT_ADD(3, st_work);
+            SSTAT_ADD(4, st_rounds);
+            SSTAT_ADD(5, SSTAT_CLOCK() - st_t0);
+        }
         if (!ok) {
             abort_flag = 1;
             if (lane == 0) atomicExch(a.err, 1);
@@ -351,9 +413,10 @@ struct RowWork {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
             // lane-strided over the elements: consecutive lanes, consecutive columns
+            int p = r.pos(g0 + gl);
             for (int t = gl; t < len; t += G) {
-                const int p = r.pos(g0 + t);
                 atomicAdd(a.delta + r.idx[p], coef * to_f(r.val[p]));
+                r.step(p, G);
             }
         }
         if (gl == 0) kahan_add(d * d * w);
@@ -472,16 +535,35 @@ StreamFn cols_fn(suppy_dtype dt, int G) {
 
 }  // namespace
 
-size_t stream_smem_bytes(suppy_dtype dt, int tile) {
+size_t stream_smem_bytes(suppy_dtype dt, int tile, int stages) {
     const size_t vsz = (dt == SUPPY_F32) ? 4 : 2;
-    return (size_t)kStages * tile * (vsz + 4) + 2 * kStages * sizeof(uint64_t);
+    return (size_t)stages * tile * (vsz + 4) + 2 * (size_t)stages * sizeof(uint64_t);
 }
 
-int stream_max_item(int tile) { return (kStages - 1) * tile; }
+// Most stages of T elements that fit the dynamic shared-memory budget.
+int stream_stages_for(suppy_dtype dt, int tile) {
+    constexpr size_t kBudget = 220 * 1024;
+    const size_t vsz = (dt == SUPPY_F32) ? 4 : 2;
+    const size_t per = (size_t)tile * (vsz + 4) + 2 * sizeof(uint64_t);
+    return (int)std::min<size_t>(kMaxStages, kBudget / per);
+}
+
+int stream_max_item(int tile, int stages) { return (stages - 1) * tile; }
+
+#ifdef SUPPY_STREAM_STATS
+cudaError_t stream_stats_read(unsigned long long* out16, int reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out16, g_stream_stats, sizeof(unsigned long long) * 16);
+    if (e != cudaSuccess || !reset) return e;
+    unsigned long long z[16] = {};
+    return cudaMemcpyToSymbol(g_stream_stats, z, sizeof(z));
+}
+#endif
 
 static cudaError_t launch_stream(StreamFn f, const StreamArgs& a, suppy_dtype dt, int grid,
                                  cudaStream_t s) {
-    const size_t smem = stream_smem_bytes(dt, a.tile);
+    if (a.stages < 2 || a.stages > kMaxStages || a.tile < 64 || (a.tile & (a.tile - 1)))
+        return cudaErrorInvalidValue;
+    const size_t smem = stream_smem_bytes(dt, a.tile, a.stages);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     f<<<grid, kStreamThreads, smem, s>>>(a);
@@ -497,8 +579,8 @@ cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid
     return launch_stream(cols_fn(dt, G), a, dt, grid, s);
 }
 
-int stream_blocks_per_sm(suppy_dtype dt, int tile) {
-    const size_t smem = stream_smem_bytes(dt, tile);
+int stream_blocks_per_sm(suppy_dtype dt, int tile, int stages) {
+    const size_t smem = stream_smem_bytes(dt, tile, stages);
     StreamFn f = rows_fn(dt, 32, 1);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
@@ -509,3 +591,9 @@ int stream_blocks_per_sm(suppy_dtype dt, int tile) {
 }
 
 }  // namespace suppy
+
+#ifdef SUPPY_STREAM_STATS
+extern "C" int suppy_stream_stats(unsigned long long* out16, int reset) {
+    return (int)suppy::stream_stats_read(out16, reset);
+}
+#endif

@@ -65,3 +65,30 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.suppy_proximity(None, None) == pk.SUPPY_EINVAL
     assert lib.suppy_launch_count(None) == 0
     lib.suppy_destroy(None)
+
+
+def test_ctypes_structs_match_the_c_layout(tmp_path):
+    """The binding's ctypes structures have the sizes and field offsets the C
+    compiler gives the header's structs (compiled here with gcc)."""
+    import subprocess
+    import paper_2606_27086_gb300 as pk
+    structs = {"suppy_csr": pk.suppy_csr, "suppy_opts": pk.suppy_opts,
+               "suppy_params": pk.suppy_params, "suppy_stats": pk.suppy_stats,
+               "suppy_info": pk.suppy_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "suppy.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            cname = "lambda" if fname == "lambda_" else fname
+            lines.append(f'printf("{name}.{fname} %zu\\n", offsetof({name}, {cname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src),
+                           "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got[f"{name}.{fname}"]) == getattr(cls, fname).offset, (name, fname)

@@ -419,3 +419,84 @@ def test_tma_block_iterative_and_long_rows():
     ctx.suppy_sweep(_params(), 1)
     xo, _ = _oracle_sweep(longp, x0)
     assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("shape", [(256, 8, 4), (512, 32, 8), (1024, 4, 16), (2048, 12, 32),
+                                   (4096, 2, 32)])
+def test_tma_stream_shapes_match_oracle(shape, strategy):
+    """Every ring shape the tuner may pick (tile length, stages, lanes per
+    item) gives the oracle's sweep on ragged items: row and column lengths
+    that are not multiples of four, empty rows, several tiles per CTA."""
+    prob = synth.random_problem(4000, 30011, seed=45, feasible=False, mean_len=37,
+                                empty_frac=0.05, long_rows=5, long_len=190)
+    ctx = pk.from_problem(prob, strategy=strategy, stream_shape=shape)
+    info = ctx.suppy_info_get()
+    assert info["tma"] == 1
+    assert (info["tile"], info["stages"], info["lanes_per_row"]) == shape
+    if strategy == pk.STRATEGY_TWO_PASS:
+        assert (info["col_tile"], info["col_stages"], info["col_lanes"]) == shape
+    x0 = random_x(prob.A.n, 1, seed=46)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(lam=1.3), 2)
+    vals = rounded_values(prob.A.val, "f32")
+    S, l, u, lo, hi = O.from_problem(prob, values=vals)
+    x = x0.astype(np.float64)
+    for _ in range(2):
+        x, p_last = O.sweep(S, O.CIMMINO, l, u, 1.3, lo, hi, x)
+    assert rel_l2(ctx.suppy_get_x(), x) <= 1e-5
+    ph, _ = ctx.suppy_history()
+    assert rel(ph[-1], p_last) <= 1e-5
+
+
+def test_tuned_stream_shapes_match_oracle():
+    """tune = 1 times the ring and group shapes of both streaming passes on
+    the matrix and keeps a valid one."""
+    prob = synth.ct_problem(128, 90, 181)
+    ctx = pk.from_problem(prob, tune=1, strategy=pk.STRATEGY_TWO_PASS)
+    info = ctx.suppy_info_get()
+    assert info["tma"] == 1
+    assert info["tile"] in (1024, 2048, 4096) and info["col_tile"] in (1024, 2048, 4096)
+    assert 3 <= info["stages"] <= 32 and 3 <= info["col_stages"] <= 32
+    assert info["lanes_per_row"] in (4, 8, 16, 32) and info["col_lanes"] in (4, 8, 16, 32)
+    x0 = random_x(prob.A.n, 1, seed=47)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(_params(), 1)
+    xo, _ = _oracle_sweep(prob, x0)
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(300, 0, 0), (8192, 0, 0), (0, 1, 0), (0, 40, 0), (0, 0, 5)])
+def test_invalid_stream_shapes_are_rejected(shape):
+    prob = small_ct()
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(prob, stream_shape=shape)
+
+
+@pytest.mark.parametrize("tma", [0, -1])
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+def test_interleaved_row_order_matches_oracle(mode, strategy, tma):
+    """Blocks of at least 16384 rows are stored in a chunk-interleaved device
+    order; sweeps, the monitored proximity and set_bounds still follow the
+    source row order's problem exactly (up to FP32 summation order)."""
+    prob = synth.random_problem(40000, 20011, seed=48, feasible=False, mean_len=18,
+                                empty_frac=0.03, long_rows=4, long_len=300)
+    if mode == O.BIP:
+        prob.blocks = (np.arange(prob.A.m) * 2 // prob.A.m).astype(np.int32)
+    ctx = pk.from_problem(prob, mode=mode, strategy=strategy, tma=tma)
+    x0 = random_x(prob.A.n, 1, seed=49)
+    for rnd in range(2):
+        if rnd == 1:
+            # new bounds through set_bounds (device-order permutation of l, u)
+            l2, u2 = prob.l * np.float32(0.9), prob.u * np.float32(1.1)
+            prob.l, prob.u = np.minimum(l2, u2), np.maximum(l2, u2)
+            ctx.suppy_set_bounds(prob.l, prob.u)
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(lam=1.5), 1)
+        xo, po = _oracle_sweep(prob, x0, mode, lam=1.5)
+        assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+        ph, _ = ctx.suppy_history()
+        assert rel(ph[0], po) <= 1e-5
+        S, l, u, _, _ = O.from_problem(prob, mode)
+        assert rel(ctx.suppy_proximity()[0], O.proximity(S, l, u, xo)) <= 1e-3
