@@ -303,19 +303,21 @@ def variants(pk, K, W):
         torch.cuda.synchronize()
 
     prob = ct512()
+    run_one("ct512_cimmino_tv_f32_twopass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
+            strategy=pk.STRATEGY_TWO_PASS, tune=1)
     run_one("ct512_cimmino_tv_f32_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
-            strategy=pk.STRATEGY_ONE_PASS)
+            strategy=pk.STRATEGY_ONE_PASS, tune=1)
     run_one("ct512_cimmino_tv_f32_twopass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
             strategy=pk.STRATEGY_TWO_PASS, tma=-1)
     run_one("ct512_cimmino_tv_f32_onepass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
             params=SUP, strategy=pk.STRATEGY_ONE_PASS, tma=-1)
     run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
-            params=SUP)
+            params=SUP, tune=1)
     run_one("ct512_cimmino_tv_bf16_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
-            dtype=pk.SUPPY_BF16, params=SUP, strategy=pk.STRATEGY_ONE_PASS)
+            dtype=pk.SUPPY_BF16, params=SUP, strategy=pk.STRATEGY_ONE_PASS, tune=1)
     prob.blocks = synth.angle_blocks(360, 725, 36)
     run_one("ct512_bip36_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP,
-            params=SUP)
+            params=SUP, tune=1)
     del prob
     seis = synth.seismic_problem(nrhs=16)
     run_one("seismic_b16_atv_f32", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
@@ -323,7 +325,7 @@ def variants(pk, K, W):
     run_one("seismic_b16_atv_f32_onepass", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
             params=SUP, strategy=pk.STRATEGY_ONE_PASS)
     seis.l, seis.u = seis.l[:, 0].copy(), seis.u[:, 0].copy()
-    run_one("seismic_b1_atv_f32", seis, UNIT, obj=pk.SUPPY_OBJ_TV_ANISO, params=SUP)
+    run_one("seismic_b1_atv_f32", seis, UNIT, obj=pk.SUPPY_OBJ_TV_ANISO, params=SUP, tune=1)
     del seis
     rt = synth.rt_problem()
     run_one("rt_bip3_meandose_f32", rt, UNIT, obj=pk.SUPPY_OBJ_LINEAR, mode=pk.SUPPY_BIP,

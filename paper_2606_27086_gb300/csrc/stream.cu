@@ -6,13 +6,12 @@
 // index and value arrays.  One producer lane streams that slice into an
 // S-stage shared-memory ring of T-element tiles with 1-D bulk copies
 // (cp.async.bulk, L2 evict-first) tracked by mbarriers; twenty-three consumer
-// warps, split into groups of G lanes (one group per item), take the items
-// round-robin and read them from the ring four elements per 16-byte access,
-// so HBM streaming runs ahead of the gathers of x (or of the coefficients)
-// instead of waiting behind them.  A consumer warp releases a stage once its
-// items there are done; the producer refills a stage when all consumer warps
-// released it.  G, T and S are launch parameters (chosen per matrix, by
-// measurement when the context is tuned).
+// warps, split into groups of G lanes (one group per item), take batches of
+// consecutive items in order from a shared counter and read them from the
+// ring four elements per 16-byte access, so HBM streaming runs ahead of the
+// gathers of x (or of the coefficients) instead of waiting behind them.  A
+// stage is refilled once every item element of its tile is done.  G, T and S are launch parameters (chosen per matrix,
+// by measurement when the context is tuned).
 //
 // Items start at multiples of four elements and are zero-padded to a
 // multiple of four (value 0, index 0), so a 16-byte ring access never holds
@@ -164,9 +163,10 @@ __device__ __forceinline__ unsigned gmask_of(int lane) {
 // sum_e a_e * vec[idx_e] over the item's elements held in the ring, by the
 // G lanes of one group reading four elements per 16-byte ring access.  Lane
 // gl takes the quads gl, gl + G, gl + 2G, ...: four at a time (sixteen gathers
-// in flight), then the remaining two and one.  (A single predicated batch of
-// up to eight quads measured slower on GB300: the extra outstanding gathers
-// only lengthen the queue at L1.)
+// in flight), and the last one to three together, so that an item of up to
+// 16 G entries costs a single gather latency.  (One predicated batch of up
+// to eight quads measured slower on GB300: the extra outstanding gathers only
+// lengthen the queue at L1.)
 template <typename VT, int G>
 __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, int gl,
                                           const float* __restrict__ vec) {
@@ -179,11 +179,14 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
         c = *reinterpret_cast<const int4*>(r.idx + p);
         r.step(p, 4 * G);
     };
-    auto fma4 = [&](const float4& v, const int4& c) {
-        acc0 = fmaf(v.x, __ldg(vec + c.x), acc0);
-        acc1 = fmaf(v.y, __ldg(vec + c.y), acc1);
-        acc0 = fmaf(v.z, __ldg(vec + c.z), acc0);
-        acc1 = fmaf(v.w, __ldg(vec + c.w), acc1);
+    auto gather = [&](const int4& c) {
+        return make_float4(__ldg(vec + c.x), __ldg(vec + c.y), __ldg(vec + c.z), __ldg(vec + c.w));
+    };
+    auto fma4 = [&](const float4& v, const float4& x) {
+        acc0 = fmaf(v.x, x.x, acc0);
+        acc1 = fmaf(v.y, x.y, acc1);
+        acc0 = fmaf(v.z, x.z, acc0);
+        acc1 = fmaf(v.w, x.w, acc1);
     };
     for (; q + 3 * G < nq; q += 4 * G) {
         float4 v0, v1, v2, v3;
@@ -192,39 +195,49 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
         quad(v1, c1);
         quad(v2, c2);
         quad(v3, c3);
-        fma4(v0, c0);
-        fma4(v1, c1);
-        fma4(v2, c2);
-        fma4(v3, c3);
-    }
-    if (q + G < nq) {
-        float4 v0, v1;
-        int4 c0, c1;
-        quad(v0, c0);
-        quad(v1, c1);
-        fma4(v0, c0);
-        fma4(v1, c1);
-        q += 2 * G;
+        const float4 x0 = gather(c0), x1 = gather(c1), x2 = gather(c2), x3 = gather(c3);
+        fma4(v0, x0);
+        fma4(v1, x1);
+        fma4(v2, x2);
+        fma4(v3, x3);
     }
     if (q < nq) {
-        float4 v0;
-        int4 c0;
+        // one to three quads left: one batch; a missing quad gathers vec[0]
+        // with value 0
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int4 zi = make_int4(0, 0, 0, 0);
+        float4 v0, v1 = z, v2 = z;
+        int4 c0, c1 = zi, c2 = zi;
         quad(v0, c0);
-        fma4(v0, c0);
+        if (q + G < nq) quad(v1, c1);
+        if (q + 2 * G < nq) quad(v2, c2);
+        const float4 x0 = gather(c0), x1 = gather(c1), x2 = gather(c2);
+        fma4(v0, x0);
+        fma4(v1, x1);
+        fma4(v2, x2);
     }
     return acc0 + acc1;
 }
 
-// Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes;
-// in each round the groups of a warp take consecutive items, so a warp's
-// items cover a contiguous element range.  work(item, len, g0, ring, gl)
+// Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes.
+// A warp takes the next 32/G consecutive items of the CTA's range from a
+// shared counter (one group per item), so all warps move through the slice
+// together and the ring holds only the items in work plus the prefetched
+// tiles, however the item costs vary.  A stage is released when the padded
+// elements of its tile that belong to finished items add up to all of the
+// tile's item elements: the group that completes the count resets it and
+// arrives on the stage's empty barrier.  work(item, len, g0, ring, gl)
 // returns the FP64 proximity contribution of the item (one lane), else 0;
-// work.prefetch(next item or -1) loads the next round's per-item operands and
-// work.advance() makes them current.
+// work.prefetch(next item or -1) loads the next batch's per-item operands
+// and work.advance() makes them current.  A warp takes its next batch before
+// working on the current one, so those loads overlap the work.
 template <typename VT, int G, class Work>
 __device__ double stream_items(const StreamArgs& a, Work& work) {
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
+    __shared__ int next_grab;                         // items handed out (from I0)
+    __shared__ volatile int stage_tile[kMaxStages];   // tile issued into each stage
+    __shared__ int tile_done[kMaxStages];             // finished item elements of it
     const int T = a.tile;
     const int S = a.stages;
     const int RING = S * T;
@@ -234,20 +247,25 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
     uint64_t* full = reinterpret_cast<uint64_t*>(sidx + RING);
     uint64_t* empty = full + S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int NW = kStreamThreads / 32 - 1;
     constexpr int GPW = 32 / G;
     const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
     double acc = 0.0;
     if (I0 >= I1) return 0.0;   // uniform over the CTA
     const long long E0 = a.info[I0].x;
-    const long long E1 = (long long)a.info[I1 - 1].x + a.info[I1 - 1].y;
+    const int2 last = a.info[I1 - 1];
     const long long Ea = E0 & ~7LL;
-    const int K = (int)((E1 - Ea + T - 1) / T);
+    // the items' padded elements cover [lo_r, hi_r) of the slice, contiguously
+    const int lo_r = (int)(E0 - Ea);
+    const int hi_r = (int)((long long)last.x + ((last.y + 3) & ~3) - Ea);
+    const int K = (hi_r + T - 1) >> ts;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NW);
+            mbar_init(&empty[s], 1);
+            stage_tile[s] = -1;
+            tile_done[s] = 0;
         }
+        next_grab = 0;
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -267,6 +285,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
                     break;
                 }
                 st_wait += SSTAT_CLOCK() - tw;
+                stage_tile[s] = k;
                 mbar_arrive_expect_tx(&full[s], bytes_v + bytes_i);
                 bulk_g2s(sval + (size_t)s * T, gval + Ea + (long long)k * T, bytes_v, &full[s], pol);
                 bulk_g2s(sidx + (size_t)s * T, a.idx + Ea + (long long)k * T, bytes_i, &full[s], pol);
@@ -288,61 +307,76 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
     } else {
         const Ring<VT> ring{sval, sidx, RING};
         const int gw = lane / G, gl = lane % G;
-        int next_rel = 0;
+        const int nitems = I1 - I0;
         bool ok = true;
+        // tile k is in the ring once its stage holds it and the stage's
+        // barrier completed the phase of that fill
         auto wait_tile = [&](int k) {
-            return mbar_wait(&full[k % S], (k / S) & 1, &abort_flag);
-        };
-        auto release_upto = [&](int kend) {
-            for (; ok && next_rel < kend; ++next_rel) {
-                if (!__all_sync(0xffffffffu, wait_tile(next_rel))) {
-                    ok = false;
-                    break;
+            const int s = k % S;
+            if (stage_tile[s] != k) {
+                const long long t0 = clock64();
+                while (stage_tile[s] != k) {
+                    if (abort_flag || clock64() - t0 > kWaitCycles) return false;
+                    __nanosleep(64);
                 }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[next_rel % S]);
             }
+            return mbar_wait(&full[s], (k / S) & 1, &abort_flag);
+        };
+        auto target = [&](int k) {
+            return min((k + 1) << ts, hi_r) - max(k << ts, lo_r);
+        };
+        auto grab = [&]() {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(&next_grab, GPW);
+            return __shfl_sync(0xffffffffu, b, 0);
         };
         constexpr int BIG = 0x7fffffff;
         long long st_t0 = SSTAT_CLOCK(), st_full = 0, st_rel = 0, st_work = 0, st_rounds = 0;
-        // the next round's item descriptor is loaded while this round runs
-        int base = I0 + (warp - 1) * GPW;
-        int2 nxt = make_int2(0, 0);
-        if (base + gw < I1) nxt = a.info[base + gw];
-        for (; ok && base < I1; base += NW * GPW) {
-            const int i = base + gw;
+        int nb = grab();
+        int2 nxt = (nb + gw < nitems) ? a.info[I0 + nb + gw] : make_int2(0, 0);
+        work.prefetch(nb + gw < nitems ? I0 + nb + gw : -1);
+        while (ok && nb < nitems) {
+            const bool valid = nb + gw < nitems;
+            const int i = I0 + nb + gw;
             const int2 inf = nxt;
-            const int inext = i + NW * GPW;
-            nxt = (inext < I1) ? a.info[inext] : make_int2(0, 0);
-            work.prefetch(inext < I1 ? inext : -1);
+            work.advance();
+            nb = grab();
+            nxt = (nb + gw < nitems) ? a.info[I0 + nb + gw] : make_int2(0, 0);
+            work.prefetch(nb + gw < nitems ? I0 + nb + gw : -1);
+            const bool has = valid && inf.y > 0;
             const int g0 = (int)((long long)inf.x - Ea);
             int kb = BIG, ke = -1;
-            if (inf.y > 0) {
+            if (has) {
                 kb = g0 >> ts;
                 ke = (g0 + inf.y - 1) >> ts;
             }
             kb = __reduce_min_sync(0xffffffffu, kb);
             ke = __reduce_max_sync(0xffffffffu, ke);
-            if (ke < 0) {
-                work.advance();
-                continue;   // no data needed by this warp in this round
-            }
-            long long t1 = SSTAT_CLOCK();
-            release_upto(kb);
-            long long t2 = SSTAT_CLOCK();
-            for (int k = max(kb, next_rel); ok && k <= ke; ++k)
-                ok = __all_sync(0xffffffffu, wait_tile(k));
-            long long t3 = SSTAT_CLOCK();
+            if (ke < 0) continue;   // only empty items in this batch
+            const long long t2 = SSTAT_CLOCK();
+            for (int k = kb; ok && k <= ke; ++k) ok = __all_sync(0xffffffffu, wait_tile(k));
+            const long long t3 = SSTAT_CLOCK();
             if (!ok) break;
-            if (i < I1 && inf.y > 0) acc += work(i, inf.y, g0, ring, gl);
-            work.advance();
+            if (has) acc += work(i, inf.y, g0, ring, gl);
             __syncwarp();
-            st_rel += t2 - t1;
+            const long long t4 = SSTAT_CLOCK();
+            // hand the group's padded elements back, tile by tile
+            if (has && gl == 0) {
+                const int e1 = g0 + ((inf.y + 3) & ~3);
+                for (int k = g0 >> ts; k <= (e1 - 1) >> ts; ++k) {
+                    const int ov = min(e1, (k + 1) << ts) - max(g0, k << ts);
+                    const int s = k % S;
+                    if (atomicAdd(&tile_done[s], ov) + ov == target(k)) {
+                        tile_done[s] = 0;
+                        mbar_arrive(&empty[s]);
+                    }
+                }
+            }
             st_full += t3 - t2;
-            st_work += SSTAT_CLOCK() - t3;
+            st_work += t4 - t3;
+            st_rel += SSTAT_CLOCK() - t4;
             st_rounds += 1;
         }
-        if (ok) release_upto(K);
         if (lane == 0) {
             SSTAT_ADD(0, 1);
             SSTAT_ADD(1, st_full);
@@ -428,14 +462,6 @@ template <typename VT, int G, int SCAT>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs a) {
     if (a.check_stop && a.st[0].stopped) return;
     RowWork<VT, G, SCAT> work{a};
-    // the first round's operands
-    {
-        const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int i = I0 + (warp - 1) * (32 / G) + lane / G;
-        work.prefetch(warp > 0 && i < I1 ? i : -1);
-        work.advance();
-    }
     stream_items<VT, G>(a, work);
     cta_sum_to(work.total(), a.pp + blockIdx.x);
 }
@@ -473,13 +499,6 @@ template <typename VT, int G>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs a) {
     if (a.epi.st[0].stopped) return;   // the row pass left no coefficients
     ColWork<VT, G> work{a};
-    {
-        const int I0 = a.cta_items[blockIdx.x], I1 = a.cta_items[blockIdx.x + 1];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int j = I0 + (warp - 1) * (32 / G) + lane / G;
-        work.prefetch(warp > 0 && j < I1 ? j : -1);
-        work.advance();
-    }
     stream_items<VT, G>(a, work);
     __syncthreads();
     if (blockIdx.x == 0 && !a.epi.last_seg) {
