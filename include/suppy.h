@@ -128,6 +128,13 @@ typedef struct {
      * (4, 8, 16 or 32).  Values outside these ranges give SUPPY_EINVAL; a shape
      * whose ring window cannot hold a warp's items leaves streaming off. */
     int32_t stream_tile, stream_stages, stream_lanes;
+    /* Perturbation phase: 2 -- the first reduction step on the whole GPU
+     * (subgradient pass, eight trial step sizes evaluated in one pass, the
+     * first accepted one applied: the same choice as the sequential trial
+     * loop), the rest of the phase, when there is one, by one thread-block
+     * cluster per right-hand side; 1 -- the cluster kernel alone; 0 --
+     * automatic: 2 when n * nrhs >= 65536, else 1. */
+    int32_t perturb_path;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default

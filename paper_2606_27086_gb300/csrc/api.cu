@@ -110,6 +110,12 @@ struct suppy_ctx {
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
+    // whole-GPU first step of the perturbation phase
+    bool wide = false;
+    int wide_grid = 0;
+    WideState* d_ws = nullptr;
+    double* d_wpart = nullptr;
+    unsigned* d_ticket = nullptr;
     std::vector<long long> rpref;   // row-work prefix (m + 1)
 
     // measurement
@@ -531,16 +537,26 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.obj = (int)c->obj;
     a.gamma = p ? p->gamma : 0.0;
     a.alpha = p ? p->alpha : 0.0;
+    a.log2_alpha = (p && p->alpha > 0.0) ? std::log2(p->alpha) : 0.0;
     a.n_red = p ? p->n_red : 0;
     a.max_trials = p ? p->max_trials : 0;
     a.restart_every = p ? p->restart_every : 0;
     a.st = c->d_st;
     a.record_only = record_only;
+    a.ws = c->d_ws;
+    a.resume = 0;
+    a.part = c->d_wpart;
+    a.ticket = c->d_ticket;
     Timed tm{c, 2};
     CK(tm.begin());
-    CK(launch_perturb(a, c->perturb_cluster, c->stream));
+    if (c->wide && !record_only) {
+        CK(launch_perturb_wide(a, c->wide_grid, c->perturb_cluster, c->stream));
+        note_launch(c, 4);
+    } else {
+        CK(launch_perturb(a, c->perturb_cluster, c->stream));
+        note_launch(c);
+    }
     CK(tm.end());
-    note_launch(c);
 #ifdef SUPPY_CHECKED
     cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(c->stream, &capst));
@@ -1072,6 +1088,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if ((int)c->obj < 0 || (int)c->obj > 3) return fail(c, SUPPY_EINVAL, "unknown objective");
     c->B_user = o->nrhs <= 0 ? 1 : o->nrhs;
     if (c->B_user > kMaxRhs) return fail(c, SUPPY_EINVAL, "nrhs must be at most 32");
+    if (o->perturb_path < 0 || o->perturb_path > 2)
+        return fail(c, SUPPY_EINVAL, "perturb_path must be 0, 1 or 2");
     {
         const int t = o->stream_tile, st = o->stream_stages, g = o->stream_lanes;
         if (t != 0 && (t < 256 || t > kMaxTile || (t & (t - 1))))
@@ -1272,13 +1290,27 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     CK(launch_box_init(c->d_x, c->d_lo, c->d_hi, (long long)nB, c->B, c->box_len, nullptr, 0,
                        c->stream));
     note_launch(c);
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     if (c->obj != SUPPY_OBJ_NONE) {
         if ((s = dalloc(c, &c->d_g, nB)) != SUPPY_OK) return s;
+        // the whole-GPU first step pays off for large images (a few fixed
+        // microseconds of launches and reductions against the cluster's
+        // per-pixel work); 2 forces it, 1 disables it
+        if (o->perturb_path == 2 || (o->perturb_path == 0 && (long long)nB >= 65536)) {
+            c->wide = true;
+            c->wide_grid = (int)std::max<long long>(
+                1, std::min<long long>(2LL * sms, ((long long)nB + kWideThreads - 1) / kWideThreads));
+            if ((s = dalloc(c, &c->d_ws, (size_t)c->B)) != SUPPY_OK) return s;
+            if ((s = dalloc(c, &c->d_wpart, wide_part_doubles(c->wide_grid, c->B))) != SUPPY_OK)
+                return s;
+            if ((s = dalloc(c, &c->d_ticket, 1)) != SUPPY_OK) return s;
+            CK(cudaMemsetAsync(c->d_ws, 0, sizeof(WideState) * c->B, c->stream));
+            CK(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream));
+        }
     }
     if ((s = dalloc(c, &c->d_st, (size_t)c->B)) != SUPPY_OK) return s;
     if ((s = dalloc(c, &c->d_out, (size_t)c->B)) != SUPPY_OK) return s;
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     c->grid_obj = std::max(1, std::min(sms * 4, (n + 255) / 256));
     if ((s = dalloc(c, &c->d_objpart, (size_t)c->grid_obj * c->B)) != SUPPY_OK) return s;
     CK(cudaMallocHost(&c->h_out, sizeof(double) * kMaxRhs));

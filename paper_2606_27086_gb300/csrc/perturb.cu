@@ -58,6 +58,20 @@ struct Vec {
 // z = y - s * g, the trial point, computed identically wherever it is used.
 __device__ __forceinline__ float trial(float y, float g, float s) { return __fmaf_rn(-s, g, y); }
 
+// Trial step beta / ||g|| with beta = gamma alpha^l (Sec. 2.1.2).  The
+// exponent is split in FP64, alpha^l = 2^(l log2 alpha) = 2^k 2^f with k an
+// integer and f in [0, 1), and the rest is FP32, so the relative error stays
+// at a few FP32 ulps for any l.  (FP64 on GB300 costs tens of cycles per
+// dependent operation; an FP64 pow() takes microseconds, on the critical
+// path of every trial.)
+__device__ __forceinline__ float trial_scale(double gamma, double log2_alpha, long long ell,
+                                             float inv_gnorm) {
+    const double e = (double)ell * log2_alpha;
+    const double k = floor(e);
+    const float f = (float)(e - k);
+    return (float)gamma * ldexpf(exp2f(f), (int)k) * inv_gnorm;
+}
+
 // Objective term owned by pixel p (FP64 result; TV terms are FP32 then widened).
 template <class Y>
 __device__ __forceinline__ double obj_term(int obj, int p, int H, int W, const double* c64,
@@ -146,6 +160,68 @@ __device__ double2 cluster_sum2(double a, double b, double2* sw, double2* scta,
     return t;
 }
 
+// Where a perturbation phase starts: a fresh phase applies the restart rule
+// (Sec. 2.1.2: l <- r at the r-th restart); in resume mode the whole-GPU
+// kernels already took the first reduction step (or its first trials) and
+// the phase continues from their state.
+struct PhaseStart {
+    long long ell;
+    int restarts, last_restart_k;
+    int accepted, trials;
+    int s0;        // first reduction step to take
+    int jt0;       // trials already spent in step s0
+    double f_start;
+    bool have_f;
+    bool skip;     // nothing left to do
+};
+
+__device__ __forceinline__ PhaseStart phase_start(const PerturbArgs& a, int b) {
+    const RhsState& st = a.st[b];
+    PhaseStart ps;
+    ps.ell = st.ell;
+    ps.restarts = st.restarts;
+    ps.last_restart_k = st.last_restart_k;
+    ps.accepted = ps.trials = ps.s0 = ps.jt0 = 0;
+    ps.f_start = 0.0;
+    ps.have_f = false;
+    ps.skip = false;
+    if (a.resume && !a.record_only) {
+        const WideState& w = a.ws[b];
+        ps.skip = w.done != 0;
+        ps.accepted = w.acc;
+        ps.trials = w.trials;
+        ps.s0 = w.acc;
+        ps.jt0 = (w.acc == 0) ? w.trials : 0;
+        ps.f_start = w.fy;
+        ps.have_f = true;
+        return ps;
+    }
+    const int k = st.k;
+    if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
+        ps.last_restart_k != k) {
+        ps.restarts += 1;
+        ps.ell = ps.restarts;
+        ps.last_restart_k = k;
+    }
+    return ps;
+}
+
+// Bookkeeping at the end of a phase: f at its start, exponent, restart
+// state, counts of this phase and in total.
+__device__ __forceinline__ void phase_end(const PerturbArgs& a, RhsState& st, const PhaseStart& ps,
+                                          long long ell, int accepted, int trials, double f_start) {
+    st.f_cur = f_start;
+    st.f_valid = 1;
+    if (a.record_only) return;
+    st.ell = ell;
+    st.restarts = ps.restarts;
+    st.last_restart_k = ps.last_restart_k;
+    st.accepted_last = accepted;
+    st.trials_last = trials;
+    st.accepted_total += accepted;
+    st.trials_total += trials;
+}
+
 __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
     __shared__ double2 sw[kPerturbThreads / 32];
@@ -161,18 +237,13 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
     Vec y{a.x + b, a.B};
     Vec g{a.g + b, a.B};
 
-    long long ell = st.ell;
-    int restarts = st.restarts, last_restart_k = st.last_restart_k;
-    const int k = st.k;
-    if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
-        last_restart_k != k) {
-        restarts += 1;
-        ell = restarts;
-        last_restart_k = k;
-    }
-    int accepted = 0, trials = 0;
-    double f_start = 0.0;
-    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
+    PhaseStart ps = phase_start(a, b);
+    if (ps.skip) return;                        // uniform over the cluster
+    long long ell = ps.ell;
+    int accepted = ps.accepted, trials = ps.trials;
+    double f_start = ps.f_start;
+    bool have_f = ps.have_f;
+    for (int s = ps.s0; s < (a.record_only ? 1 : a.n_red); ++s) {
         // pass G: subgradient, ||g||^2 and f(y)
         double gg = 0.0, fy = 0.0;
         for (int p = tid; p < n; p += nthr) {
@@ -186,15 +257,17 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
         const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
         gg = r.x;
         fy = r.y;
-        if (s == 0) f_start = fy;
+        if (!have_f) {
+            f_start = fy;
+            have_f = true;
+        }
         if (a.record_only || gg == 0.0) break;
-        const double gnorm = sqrt(gg);
+        const float inv_gnorm = 1.0f / sqrtf((float)gg);
         bool ok = false;
-        for (int j = 0; j < a.max_trials; ++j) {
-            const double beta = a.gamma * pow(a.alpha, (double)ell);
+        for (int j = (s == ps.s0 ? ps.jt0 : 0); j < a.max_trials; ++j) {
+            const float sc = trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
             ell += 1;
             trials += 1;
-            const float sc = (float)(beta / gnorm);
             Vec yy = y;
             Vec gv = g;
             auto z = [yy, gv, sc](int q) { return trial(yy(q), gv(q), sc); };
@@ -214,19 +287,7 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
         }
         if (!ok) break;
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        st.f_cur = f_start;
-        st.f_valid = 1;
-        if (!a.record_only) {
-            st.ell = ell;
-            st.restarts = restarts;
-            st.last_restart_k = last_restart_k;
-            st.accepted_last = accepted;
-            st.trials_last = trials;
-            st.accepted_total += accepted;
-            st.trials_total += trials;
-        }
-    }
+    if (rank == 0 && threadIdx.x == 0) phase_end(a, st, ps, ell, accepted, trials, f_start);
 }
 
 // ------------------------------------------- shared-memory resident phase ----
@@ -249,6 +310,15 @@ struct Band {
 };
 
 __device__ __forceinline__ int band_start(int r, int H, int cs) { return (int)((long long)H * r / cs); }
+
+// Image of one right-hand side in global memory (read-only during a launch).
+struct GlobalImage {
+    const float* y;   // element 0 of the right-hand side
+    int B, W;
+    __device__ __forceinline__ float operator()(int i, int j) const {
+        return __ldg(y + ((size_t)i * W + j) * B);
+    }
+};
 
 // Per-thread compensated FP32 sum (Kahan); widened to FP64 for the cluster
 // reduction.  FP64 arithmetic is scarce on GB300: one FP64 add per pixel and
@@ -321,6 +391,8 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     const int b = blockIdx.x / cs;
     RhsState& st = a.st[b];
     if (st.stopped) return;
+    const PhaseStart ps = phase_start(a, b);
+    if (ps.skip) return;                        // uniform over the cluster
     const int rank = (int)cluster.block_rank();
     const bool lin = (a.obj == SUPPY_OBJ_LINEAR);
     const int H = lin ? a.n : a.H, W = lin ? 1 : a.W;   // linear: a column of n "rows"
@@ -352,18 +424,11 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
         }
     }
 
-    long long ell = st.ell;
-    int restarts = st.restarts, last_restart_k = st.last_restart_k;
-    const int k = st.k;
-    if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
-        last_restart_k != k) {
-        restarts += 1;
-        ell = restarts;
-        last_restart_k = k;
-    }
-    int accepted = 0, trials = 0;
-    double f_start = 0.0;
-    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
+    long long ell = ps.ell;
+    int accepted = ps.accepted, trials = ps.trials;
+    double f_start = ps.f_start;
+    bool have_f = ps.have_f;
+    for (int s = ps.s0; s < (a.record_only ? 1 : a.n_red); ++s) {
         double gg = 0.0, fy = 0.0;
         KSum kg, kf;
         for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
@@ -387,15 +452,17 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
         const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
         gg = r.x;
         fy = r.y;
-        if (s == 0) f_start = fy;
+        if (!have_f) {
+            f_start = fy;
+            have_f = true;
+        }
         if (a.record_only || gg == 0.0) break;
-        const double gnorm = sqrt(gg);
+        const float inv_gnorm = 1.0f / sqrtf((float)gg);
         bool ok = false;
-        for (int jt = 0; jt < a.max_trials; ++jt) {
-            const double beta = a.gamma * pow(a.alpha, (double)ell);
+        for (int jt = (s == ps.s0 ? ps.jt0 : 0); jt < a.max_trials; ++jt) {
+            const float sc = trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
             ell += 1;
             trials += 1;
-            const float sc = (float)(beta / gnorm);
             double fz = 0.0;
             if (lin) {
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
@@ -422,21 +489,312 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     if (!a.record_only) {
         for (int q = threadIdx.x; q < band; q += kPerturbThreads) X[(size_t)(p0 + q) * B] = ys[q];
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        st.f_cur = f_start;
-        st.f_valid = 1;
-        if (!a.record_only) {
-            st.ell = ell;
-            st.restarts = restarts;
-            st.last_restart_k = last_restart_k;
-            st.accepted_last = accepted;
-            st.trials_last = trials;
-            st.accepted_total += accepted;
-            st.trials_total += trials;
-        }
-    }
+    if (rank == 0 && threadIdx.x == 0) phase_end(a, st, ps, ell, accepted, trials, f_start);
     // no CTA may leave while a neighbour can still read its shared memory
     cluster.sync();
+}
+
+// ------------------------------------------------ whole-GPU first step ----
+// The first reduction step of a phase on the whole GPU, in three launches:
+//  k_wide_grad    g = subgradient at y, ||g||^2 and f(y) (restart rule and
+//                 f(x^k) recorded by the last CTA);
+//  k_wide_trials  f(y - beta_j g/||g||) for kWideTrials consecutive trial
+//                 exponents at once; the last CTA takes the first j with
+//                 f(z_j) <= f(y), exactly the trial the sequential loop of
+//                 Algorithm 1 would accept, and advances l by j + 1;
+//  k_wide_update  y <- z_j.
+// Element e of the n x B array is pixel e / B of right-hand side e % B; every
+// thread keeps one right-hand side (the grid stride is a multiple of B).
+// CTA partials are summed by the last CTA to finish in a fixed order, so the
+// decisions are deterministic.  What this step leaves undone (more reduction
+// steps, or more trials) the cluster kernel finishes in resume mode.
+
+__device__ __forceinline__ void wide_bookkeeping(RhsState& st, int acc, int trials) {
+    st.accepted_last = acc;
+    st.trials_last = trials;
+    st.accepted_total += acc;
+    st.trials_total += trials;
+}
+
+// TV term of pixel p of z = y - s g (the trial point of every term computed
+// as in the cluster kernels); y, g point at right-hand side b's element 0.
+__device__ __forceinline__ float wide_tv_term(int obj, int i, int j, int H, int W, const float* y,
+                                              const float* g, int B, float s) {
+    const size_t p = (size_t)i * W + j;
+    const float z0 = trial(__ldg(y + p * B), __ldg(g + p * B), s);
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        if (i < H - 1 && j < W - 1) {
+            const size_t pd = p + W, pr = p + 1;
+            const float dx = trial(__ldg(y + pd * B), __ldg(g + pd * B), s) - z0;
+            const float dy = trial(__ldg(y + pr * B), __ldg(g + pr * B), s) - z0;
+            return sqrtf(dx * dx + dy * dy);
+        }
+        return 0.f;
+    }
+    float t = 0.f;
+    if (i < H - 1) t += fabsf(trial(__ldg(y + (p + W) * B), __ldg(g + (p + W) * B), s) - z0);
+    if (j < W - 1) t += fabsf(trial(__ldg(y + (p + 1) * B), __ldg(g + (p + 1) * B), s) - z0);
+    return t;
+}
+
+// Float-float value hi + lo (about 44 significant bits): CTA-level sums of the
+// per-thread compensated FP32 sums stay in FP32 arithmetic, and FP64 is used
+// only for the grid-level sum of the CTA partials.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    const float hi = s + e;
+    return FF{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ FF ff_of(const KSum& k) { return FF{k.s, -k.c}; }
+
+// An FP64 value as float-float (used for the FP64 per-element sums of the
+// linear objective).
+__device__ __forceinline__ FF ff_of(double v) {
+    const float hi = (float)v;
+    return FF{hi, (float)(v - (double)hi)};
+}
+
+// Last-CTA election: every CTA's partials are visible to the CTA that draws
+// the last ticket; it resets the ticket for the next launch.
+__device__ __forceinline__ bool last_cta(unsigned* ticket) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// Fixed-order sum of part[c * stride + off] over the grid's CTAs by one warp.
+__device__ __forceinline__ double warp_sum_parts(const double* part, int ncta, int stride,
+                                                 int off) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int c = lane; c < ncta; c += 32) s += __ldcg(part + (size_t)c * stride + off);
+    return warp_sum(s);
+}
+
+// Per-CTA sums of NV values per right-hand side, written as FP64 to
+// part[(cta * B + b) * NV + v]: float-float sums over the lanes of each
+// right-hand side, then over the warps in order.  sw holds 8 * NV * 32 values.
+template <int NV>
+__device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double* part) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+        for (int o = 16; o >= B && o > 0; o >>= 1) {
+            const FF w{__shfl_xor_sync(0xffffffffu, v[j].hi, o),
+                       __shfl_xor_sync(0xffffffffu, v[j].lo, o)};
+            v[j] = ff_add(v[j], w);
+        }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < B)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) sw[(wid * NV + j) * 32 + lane] = v[j];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NV * B; t += kWideThreads) {
+        const int b = t / NV, j = t - b * NV;
+        FF acc{0.f, 0.f};
+        for (int w = 0; w < kWideThreads / 32; ++w) acc = ff_add(acc, sw[(w * NV + j) * 32 + b]);
+        part[((size_t)blockIdx.x * B + b) * NV + j] = (double)acc.hi + (double)acc.lo;
+    }
+}
+
+// In the last CTA: the grid sums of the NV * B values, one warp per value,
+// into res[b * NV + v] (shared memory).
+template <int NV>
+__device__ __forceinline__ void grid_sums(const double* part, int B, double* res) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = wid; t < NV * B; t += kWideThreads / 32) {
+        const double v = warp_sum_parts(part, gridDim.x, NV * B, t);
+        if (lane == 0) res[t] = v;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_wide_grad(const PerturbArgs a) {
+    __shared__ FF sw[(kWideThreads / 32) * 2 * 32];
+    __shared__ double res[2 * kMaxRhs];
+    __shared__ long long ell_s[kMaxRhs];
+    __shared__ float inv_s[kMaxRhs];
+    const int B = a.B, H = a.H, W = a.W, obj = a.obj;
+    const long long nB = (long long)a.n * B;
+    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
+    const long long stride = (long long)gridDim.x * kWideThreads;
+    const int b = (int)(tid & (B - 1));
+    const bool act = !a.st[b].stopped;
+    const bool lin = (obj == SUPPY_OBJ_LINEAR);
+    KSum kg, kf;
+    double fl = 0.0;
+    if (act) {
+        const float* yb = a.x + b;
+        for (long long e = tid; e < nB; e += stride) {
+            const int p = (int)(e / B);
+            float gp;
+            if (lin) {
+                gp = a.c32[p];
+                fl += a.c64[p] * (double)a.x[e];
+            } else {
+                const int i = p / W, j = p - i * W;
+                GlobalImage yi{yb, B, W};
+                kf.add(tv_term(obj, i, j, H, W, yi));
+                gp = tv_subgrad(obj, i, j, H, W, yi);
+            }
+            a.g[e] = gp;
+            kg.add(gp * gp);
+        }
+    }
+    FF v[2] = {ff_of(kg), lin ? ff_of(fl) : ff_of(kf)};
+    cta_partials<2>(v, B, sw, a.part);
+    if (!last_cta(a.ticket)) return;
+    grid_sums<2>(a.part, B, res);
+    if (threadIdx.x < B) {
+        const int r = threadIdx.x;
+        const double G2 = res[2 * r], F = res[2 * r + 1];
+        RhsState& st = a.st[r];
+        WideState& w = a.ws[r];
+        ell_s[r] = -1;
+        if (st.stopped) {
+            w.done = 1;
+        } else {
+            // restart rule at the phase start (Sec. 2.1.2)
+            const int k = st.k;
+            long long ell = st.ell;
+            if (a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
+                st.last_restart_k != k) {
+                st.restarts += 1;
+                ell = st.restarts;
+                st.ell = ell;
+                st.last_restart_k = k;
+            }
+            st.f_cur = F;
+            st.f_valid = 1;
+            w.fy = F;
+            w.acc = 0;
+            w.trials = 0;
+            w.pending = 0;
+            w.done = 0;
+            if (G2 == 0.0 || a.n_red <= 0) {
+                w.done = 1;
+                wide_bookkeeping(st, 0, 0);
+            } else {
+                ell_s[r] = ell;
+                inv_s[r] = 1.0f / sqrtf((float)G2);
+            }
+        }
+    }
+    __syncthreads();
+    // the trial step sizes of the next launch, one thread each
+    if (threadIdx.x < B * kWideTrials) {
+        const int r = threadIdx.x / kWideTrials, jj = threadIdx.x - r * kWideTrials;
+        if (ell_s[r] >= 0)
+            a.ws[r].step[jj] = trial_scale(a.gamma, a.log2_alpha, ell_s[r] + jj, inv_s[r]);
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_wide_trials(const PerturbArgs a) {
+    __shared__ FF sw[(kWideThreads / 32) * kWideTrials * 32];
+    __shared__ double res[kWideTrials * kMaxRhs];
+    const int B = a.B, H = a.H, W = a.W, obj = a.obj;
+    const long long nB = (long long)a.n * B;
+    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
+    const long long stride = (long long)gridDim.x * kWideThreads;
+    const int b = (int)(tid & (B - 1));
+    const bool act = !a.st[b].stopped && !a.ws[b].done;
+    const bool lin = (obj == SUPPY_OBJ_LINEAR);
+    float sj[kWideTrials];
+    KSum kz[kWideTrials];
+    double fl[kWideTrials];
+#pragma unroll
+    for (int jj = 0; jj < kWideTrials; ++jj) {
+        sj[jj] = act ? a.ws[b].step[jj] : 0.f;
+        fl[jj] = 0.0;
+    }
+    if (act) {
+        const float* yb = a.x + b;
+        const float* gb = a.g + b;
+        for (long long e = tid; e < nB; e += stride) {
+            const int p = (int)(e / B);
+            if (lin) {
+                const float y0 = a.x[e], g0 = a.g[e];
+                const double c = a.c64[p];
+#pragma unroll
+                for (int jj = 0; jj < kWideTrials; ++jj) fl[jj] += c * (double)trial(y0, g0, sj[jj]);
+            } else {
+                const int i = p / W, j = p - i * W;
+#pragma unroll
+                for (int jj = 0; jj < kWideTrials; ++jj)
+                    kz[jj].add(wide_tv_term(obj, i, j, H, W, yb, gb, B, sj[jj]));
+            }
+        }
+    }
+    FF v[kWideTrials];
+#pragma unroll
+    for (int jj = 0; jj < kWideTrials; ++jj) v[jj] = lin ? ff_of(fl[jj]) : ff_of(kz[jj]);
+    cta_partials<kWideTrials>(v, B, sw, a.part);
+    if (!last_cta(a.ticket)) return;
+    grid_sums<kWideTrials>(a.part, B, res);
+    if (threadIdx.x < B) {
+        const int r = threadIdx.x;
+        RhsState& st = a.st[r];
+        WideState& w = a.ws[r];
+        if (!st.stopped && !w.done) {
+            const int jmax = min(kWideTrials, a.max_trials);
+            int hit = -1;
+            for (int jj = 0; jj < jmax; ++jj)
+                if (res[r * kWideTrials + jj] <= w.fy) {
+                    hit = jj;
+                    break;
+                }
+            if (hit >= 0) {
+                w.sc = w.step[hit];
+                w.pending = 1;
+                w.acc = 1;
+                w.trials = hit + 1;
+                st.ell += hit + 1;
+            } else {
+                w.trials = jmax;
+                st.ell += jmax;
+                if (jmax >= a.max_trials) {
+                    // the step ran out of trials: the phase ends
+                    w.done = 1;
+                    wide_bookkeeping(st, 0, jmax);
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_wide_update(const PerturbArgs a) {
+    const int B = a.B;
+    const long long nB = (long long)a.n * B;
+    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
+    const long long stride = (long long)gridDim.x * kWideThreads;
+    const int b = (int)(tid & (B - 1));
+    if (!a.st[b].stopped && a.ws[b].pending) {
+        const float sc = a.ws[b].sc;
+        for (long long e = tid; e < nB; e += stride) a.x[e] = trial(a.x[e], a.g[e], sc);
+    }
+    if (!last_cta(a.ticket)) return;
+    for (int r = threadIdx.x; r < B; r += kWideThreads) {
+        WideState& w = a.ws[r];
+        if (!w.pending) continue;
+        w.pending = 0;
+        if (w.acc >= a.n_red) {
+            w.done = 1;
+            wide_bookkeeping(a.st[r], w.acc, w.trials);
+        }
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
 // Objective partials: CTA c writes f-partials of every right-hand side.
@@ -528,6 +886,20 @@ cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+size_t wide_part_doubles(int grid, int B) { return (size_t)grid * B * kWideTrials; }
+
+cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, int cluster, cudaStream_t s) {
+    if (a.B != 1 && (a.B & (a.B - 1))) return cudaErrorInvalidValue;
+    k_wide_grad<<<grid, kWideThreads, 0, s>>>(a);
+    k_wide_trials<<<grid, kWideThreads, 0, s>>>(a);
+    k_wide_update<<<grid, kWideThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    PerturbArgs r = a;
+    r.resume = 1;
+    return launch_perturb(r, cluster, s);
 }
 
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s) {

@@ -500,3 +500,72 @@ def test_interleaved_row_order_matches_oracle(mode, strategy, tma):
         assert rel(ph[0], po) <= 1e-5
         S, l, u, _, _ = O.from_problem(prob, mode)
         assert rel(ctx.suppy_proximity()[0], O.proximity(S, l, u, xo)) <= 1e-3
+
+
+# ------------------------------------------- whole-GPU perturbation step ----
+
+PERT_CASES = [
+    # (gamma, alpha, n_red, max_trials): first trial accepted; later trials only
+    # (the first eight rejected, the cluster kernel resumes); several reduction
+    # steps; fewer trials than one whole-GPU launch evaluates
+    (0.05, 0.99, 1, 100),
+    (40.0, 0.7, 1, 100),
+    (2.0, 0.9, 3, 50),
+    (40.0, 0.7, 1, 3),
+]
+
+
+@pytest.mark.parametrize("case", PERT_CASES)
+@pytest.mark.parametrize("kind", ["tv", "atv"])
+def test_whole_gpu_perturbation_matches_oracle_and_cluster_path(kind, case):
+    """The whole-GPU first step (eight trials per pass, first acceptance kept)
+    followed by the cluster kernel's resume gives the oracle's phase: the same
+    accepted steps, trial count and exponent, and the same point."""
+    gamma, alpha, n_red, max_trials = case
+    prob = synth.ct_problem(128, 60, 181)
+    obj = {"tv": pk.SUPPY_OBJ_TV_ISO, "atv": pk.SUPPY_OBJ_TV_ANISO}[kind]
+    okind = {"tv": O.OBJ_TV_ISO, "atv": O.OBJ_TV_ANISO}[kind]
+    x0 = random_x(prob.A.n, 1, seed=51)
+    P = dict(gamma=gamma, alpha=alpha, n_red=n_red, max_trials=max_trials)
+    ob = oracle_objective(prob, okind)
+    ost = O.PertState()
+    y, a, t = O.perturbation_phase(ob, x0.astype(np.float64), ost, O.Params(**P))
+    xs = []
+    for path in (2, 1):
+        ctx = pk.from_problem(prob, obj=obj, perturb_path=path)
+        ctx.suppy_set_x(x0)
+        acc = ctx.suppy_perturb(_params(**P))
+        st = ctx.suppy_run(_params(max_sweeps=0))[0]
+        assert acc[0] == a
+        assert st["trials"] == t and st["ell"] == ost.ell
+        xs.append(ctx.suppy_get_x().copy())
+        assert rel_l2(xs[-1], y) <= 1e-5
+    assert rel_l2(xs[0], xs[1]) <= 1e-6
+
+
+def test_whole_gpu_perturbation_batched_and_linear():
+    """Several right-hand sides in one whole-GPU launch (each its own
+    exponent and decisions), and the linear mean-dose objective."""
+    prob = synth.ct_problem(96, 40, 137, nrhs=5)
+    x0 = random_x(prob.A.n, 5, seed=52)
+    P = dict(gamma=3.0, alpha=0.8, n_red=2, max_trials=40)
+    ob = oracle_objective(prob, O.OBJ_TV_ISO)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, perturb_path=2)
+    ctx.suppy_set_x(x0)
+    acc = ctx.suppy_perturb(_params(**P))
+    xg = ctx.suppy_get_x()
+    for b in range(5):
+        y, a, _ = O.perturbation_phase(ob, x0[:, b].astype(np.float64), O.PertState(),
+                                       O.Params(**P))
+        assert acc[b] == a
+        assert rel_l2(xg[:, b], y) <= 1e-5
+    rt = synth.rt_problem(nx=30, ny=20, nz=12, ns=9, nzb=7)
+    obl = oracle_objective(rt, O.OBJ_LINEAR)
+    xr = random_x(rt.A.n, 1, seed=53)
+    ctx = pk.from_problem(rt, mode=pk.SUPPY_BIP, obj=pk.SUPPY_OBJ_LINEAR, perturb_path=2)
+    ctx.suppy_set_x(xr)
+    P = dict(gamma=1.0, alpha=0.99, n_red=2, max_trials=10)
+    acc = ctx.suppy_perturb(_params(**P))
+    y, a, _ = O.perturbation_phase(obl, xr.astype(np.float64), O.PertState(), O.Params(**P))
+    assert acc[0] == a
+    assert rel_l2(ctx.suppy_get_x(), y) <= 1e-5
