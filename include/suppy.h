@@ -312,6 +312,79 @@ suppy_status suppy_sweep_static(const suppy_csr* A, const float* l, const float*
                                 float lambda, const float* box_lo, const float* box_hi,
                                 int64_t box_len, float* x, double* proximity, void* stream);
 
+/* ---- Serving: continuous batching of many solves on one GPU --------------
+ *
+ * The paper runs one solve at a time; this runtime has no counterpart there.
+ * A server holds registered matrices (CT geometries, seismic geometries,
+ * radiotherapy plans) and serves requests -- one set of slab bounds l, u for
+ * a registered matrix each -- through batched contexts: every context holds
+ * one matrix resident and up to `slots` right-hand sides, each a request with
+ * its own iterate, bounds, exponent l and stopping state on the device.  A
+ * request waiting for its matrix takes a free slot as soon as one exists, or
+ * a new context when the device-memory budget allows one; a finished request
+ * leaves its slot at the next poll.  Contexts run on their own CUDA streams,
+ * so the work of different matrices overlaps on the device.  Each request
+ * runs Algorithm 1 with the matrix's parameters until the stopping rule holds
+ * for it (p->use_stopping) or p->max_sweeps sweeps ran.  The result of a
+ * request does not depend on the other requests in its context (every
+ * right-hand side is computed independently).  Not thread-safe: one host
+ * thread drives a server. */
+typedef struct suppy_server suppy_server;
+
+typedef struct {
+    int64_t hbm_budget;      /* device bytes all contexts may hold; 0: 80% of the free memory */
+    int32_t slots;           /* right-hand sides per context, 1..32 (0: 32)                   */
+    int32_t check_every;     /* iterations enqueued per context between polls (0: 8)          */
+} suppy_server_opts;
+
+typedef struct {
+    int32_t state;           /* 0 waiting, 1 running, 2 done                                   */
+    int32_t sweeps, accepted, trials;
+    double proximity;        /* monitored proximity of the last sweep                          */
+    double objective;        /* f at the start of the last perturbation phase                  */
+    double t_submit, t_start, t_done;   /* seconds on the server clock (suppy_server_clock)    */
+} suppy_request_info;
+
+/* Create a server.  Errors: SUPPY_EINVAL (bad options), SUPPY_ECUDA. */
+suppy_status suppy_server_create(const suppy_server_opts* o, suppy_server** out);
+
+/* Release every context and buffer of the server (NULL is a no-op). */
+void suppy_server_destroy(suppy_server* srv);
+
+/* Register a matrix with its box (o->box_len values each), context options
+ * (value type, mode, blocks, objective; nrhs is the server's slot count) and
+ * Algorithm 1 parameters.  Host arrays only (A->on_device = 0); they are
+ * copied.  Nothing is put on the device until a request needs it. */
+suppy_status suppy_server_add_matrix(suppy_server* srv, const suppy_csr* A, const float* box_lo,
+                                     const float* box_hi, const suppy_opts* o,
+                                     const suppy_params* p, int32_t* matrix_id);
+
+/* Queue a request: slab bounds l, u (host, m values each, the matrix's row
+ * order; same rules as suppy_create), copied.  *request_id identifies it. */
+suppy_status suppy_server_submit(suppy_server* srv, int32_t matrix_id, const float* l,
+                                 const float* u, int64_t* request_id);
+
+/* One scheduling round, without blocking on the device: retire requests
+ * whose contexts finished their last chunk (copying their x out), admit
+ * waiting requests into free slots or new contexts, and enqueue the next
+ * chunk of iterations on every idle context with running requests.
+ * running / waiting (may be NULL) receive the counts after the round. */
+suppy_status suppy_server_step(suppy_server* srv, int32_t* running, int32_t* waiting);
+
+/* State of a request; x (host, n values, may be NULL) receives the solution
+ * once the request is done.  SUPPY_EINVAL for an unknown id. */
+suppy_status suppy_server_query(suppy_server* srv, int64_t request_id, suppy_request_info* info,
+                                float* x);
+
+/* Seconds since the server was created (monotonic clock). */
+double suppy_server_clock(const suppy_server* srv);
+
+/* Device bytes the server's contexts and buffers hold now. */
+int64_t suppy_server_device_bytes(const suppy_server* srv);
+
+/* Message of the last failed server call. */
+const char* suppy_server_last_error(const suppy_server* srv);
+
 /* Number of kernels the library launched on this context so far. */
 int64_t suppy_launch_count(const suppy_ctx* ctx);
 

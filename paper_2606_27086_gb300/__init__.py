@@ -32,6 +32,9 @@ EXPORTED = [
     "suppy_proximity", "suppy_objective", "suppy_run", "suppy_history", "suppy_get_state",
     "suppy_set_state", "suppy_info_get", "suppy_timing_enable", "suppy_kernel_time",
     "suppy_launch_count", "suppy_last_error", "suppy_version", "suppy_sweep_static",
+    "suppy_server_create", "suppy_server_destroy", "suppy_server_add_matrix",
+    "suppy_server_submit", "suppy_server_step", "suppy_server_query", "suppy_server_clock",
+    "suppy_server_device_bytes", "suppy_server_last_error",
 ]
 
 
@@ -67,6 +70,19 @@ class suppy_stats(ctypes.Structure):
                 ("trials", ctypes.c_int32), ("stopped", ctypes.c_int32),
                 ("ell", ctypes.c_int64), ("proximity", ctypes.c_double),
                 ("objective", ctypes.c_double)]
+
+
+class suppy_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("check_every", ctypes.c_int32)]
+
+
+class suppy_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("accepted", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("proximity", ctypes.c_double), ("objective", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 class suppy_info(ctypes.Structure):
@@ -121,6 +137,17 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_version": (ctypes.c_char_p, []),
         "suppy_sweep_static": (ctypes.c_int, [ctypes.POINTER(suppy_csr), P, P, ctypes.c_float,
                                               ctypes.c_float, P, P, I64, P, P, P]),
+        "suppy_server_create": (ctypes.c_int, [ctypes.POINTER(suppy_server_opts), P]),
+        "suppy_server_destroy": (None, [P]),
+        "suppy_server_add_matrix": (ctypes.c_int, [P, ctypes.POINTER(suppy_csr), P, P,
+                                                   ctypes.POINTER(suppy_opts),
+                                                   ctypes.POINTER(suppy_params), P]),
+        "suppy_server_submit": (ctypes.c_int, [P, I32, P, P, P]),
+        "suppy_server_step": (ctypes.c_int, [P, P, P]),
+        "suppy_server_query": (ctypes.c_int, [P, I64, ctypes.POINTER(suppy_request_info), P]),
+        "suppy_server_clock": (D, [P]),
+        "suppy_server_device_bytes": (I64, [P]),
+        "suppy_server_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -393,3 +420,102 @@ def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_h
 
 def version() -> str:
     return load_library().suppy_version().decode()
+
+
+class Server:
+    """Owns one ``suppy_server`` (continuous batching of many solves); methods
+    call the C ABI functions of the same name."""
+
+    def __init__(self, hbm_budget: int = 0, slots: int = 32, check_every: int = 8):
+        self._lib = load_library()
+        o = suppy_server_opts(int(hbm_budget), int(slots), int(check_every))
+        h = ctypes.c_void_p()
+        st = self._lib.suppy_server_create(ctypes.byref(o), ctypes.byref(h))
+        _check(st, None)
+        self.srv = h
+        self.matrices = []
+
+    def _check(self, st):
+        if st != SUPPY_OK:
+            msg = self._lib.suppy_server_last_error(self.srv)
+            raise SuppyError(st, msg.decode() if msg else "")
+
+    def suppy_server_add_matrix(self, prob, params: suppy_params, *, dtype=SUPPY_F32,
+                                mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, strategy=0) -> int:
+        """Register the matrix, box and objective of a ``synth.Problem``."""
+        A = prob.A
+        keep = []
+        csr = _csr(A.row_ptr, A.col, A.val, A.m, A.n, keep)
+        lop, _, k1 = _ptr(np.ascontiguousarray(prob.box_lo, np.float32))
+        hip, _, k2 = _ptr(np.ascontiguousarray(prob.box_hi, np.float32))
+        keep += [k1, k2]
+        o = suppy_opts()
+        o.a_dtype = dtype
+        o.mode = mode
+        if mode == SUPPY_BIP and prob.blocks is not None:
+            bor = np.ascontiguousarray(prob.blocks, dtype=np.int32)
+            keep.append(bor)
+            o.block_of_row = ctypes.c_void_p(bor.ctypes.data)
+            o.nblocks = int(bor.max()) + 1
+        o.obj = obj
+        if obj in (SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO):
+            o.img_h, o.img_w = int(prob.shape[0]), int(prob.shape[1])
+        if obj == SUPPY_OBJ_LINEAR:
+            if prob.body is not None:
+                b = prob.body
+                S = _csr(b.row_ptr, b.col, b.val, b.m, b.n, keep)
+                keep.append(S)
+                o.obj_rows = ctypes.pointer(S)
+            else:
+                cp, _, kc = _ptr(np.ascontiguousarray(prob.c_lin, np.float32))
+                keep.append(kc)
+                o.c_lin = cp
+        o.box_len = int(np.asarray(prob.box_lo).shape[0])
+        o.strategy = int(strategy)
+        mid = ctypes.c_int32()
+        self._check(self._lib.suppy_server_add_matrix(self.srv, ctypes.byref(csr), lop, hip,
+                                                      ctypes.byref(o), ctypes.byref(params),
+                                                      ctypes.byref(mid)))
+        self.matrices.append((A.m, A.n))
+        return mid.value
+
+    def suppy_server_submit(self, matrix_id: int, l, u) -> int:
+        l = np.ascontiguousarray(l, np.float32)
+        u = np.ascontiguousarray(u, np.float32)
+        rid = ctypes.c_int64()
+        self._check(self._lib.suppy_server_submit(self.srv, int(matrix_id),
+                                                  ctypes.c_void_p(l.ctypes.data),
+                                                  ctypes.c_void_p(u.ctypes.data),
+                                                  ctypes.byref(rid)))
+        return rid.value
+
+    def suppy_server_step(self):
+        r, w = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.suppy_server_step(self.srv, ctypes.byref(r), ctypes.byref(w)))
+        return r.value, w.value
+
+    def suppy_server_query(self, request_id: int, n: int | None = None):
+        info = suppy_request_info()
+        x = np.zeros(n, np.float32) if n else None
+        xp = ctypes.c_void_p(x.ctypes.data) if x is not None else None
+        self._check(self._lib.suppy_server_query(self.srv, int(request_id), ctypes.byref(info),
+                                                 xp))
+        d = {k: getattr(info, k) for k, _ in suppy_request_info._fields_}
+        return d, (x if d["state"] == 2 else None)
+
+    def suppy_server_clock(self) -> float:
+        return self._lib.suppy_server_clock(self.srv)
+
+    def suppy_server_device_bytes(self) -> int:
+        return self._lib.suppy_server_device_bytes(self.srv)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            self._lib.suppy_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

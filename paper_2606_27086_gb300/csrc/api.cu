@@ -110,6 +110,11 @@ struct suppy_ctx {
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
+    // serving: per right-hand side sweep budget and one-slot staging
+    int slot_max_sweeps = 0;
+    float* d_slot_l = nullptr;
+    float* d_slot_u = nullptr;
+    std::vector<unsigned char> zero_row;   // source order: ||a_i|| = 0
     // whole-GPU first step of the perturbation phase
     bool wide = false;
     int wide_grid = 0;
@@ -323,6 +328,7 @@ StopParams stop_params(const suppy_ctx* c, const suppy_params* p) {
     sp.patience = p->patience;
     sp.use_stopping = p->use_stopping;
     sp.has_obj = c->obj != SUPPY_OBJ_NONE;
+    sp.max_sweeps = c->slot_max_sweeps;
     return sp;
 }
 
@@ -1510,6 +1516,95 @@ suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) 
     }
     return SUPPY_OK;
 }
+
+}  // namespace
+
+// ---- internal interface of the serving runtime (serve.cu) -----------------
+namespace suppy {
+
+int ctx_slots(const suppy_ctx* c) { return c->B_user; }
+int ctx_n(const suppy_ctx* c) { return c->n; }
+int ctx_m(const suppy_ctx* c) { return c->m; }
+cudaStream_t ctx_stream(const suppy_ctx* c) { return c->stream; }
+size_t ctx_device_bytes(const suppy_ctx* c) { return c->dev_bytes; }
+const char* ctx_error(const suppy_ctx* c) { return c->err.c_str(); }
+void ctx_set_sweep_budget(suppy_ctx* c, int max_sweeps) { c->slot_max_sweeps = max_sweeps; }
+
+// Load right-hand side b: bounds l, u (host, m values in the caller's row
+// order) checked on the host, x[:, b] <- box(0), a fresh state.  Enqueued on
+// the context's stream; nothing is synchronized.
+suppy_status ctx_slot_load(suppy_ctx* c, int b, const float* l, const float* u) {
+    if (b < 0 || b >= c->B_user) return fail(c, SUPPY_EINVAL, "slot out of range");
+    const int m = c->m;
+    suppy_status s;
+    if (c->zero_row.empty() && m > 0) {
+        std::vector<double> rho(m);
+        std::vector<int> perm(m);
+        CK(cudaMemcpyAsync(rho.data(), c->d_rho, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                           c->stream));
+        if (c->d_perm)
+            CK(cudaMemcpyAsync(perm.data(), c->d_perm, sizeof(int) * m, cudaMemcpyDeviceToHost,
+                               c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->zero_row.assign(m, 0);
+        for (int i = 0; i < m; ++i) c->zero_row[c->d_perm ? perm[i] : i] = rho[i] == 0.0;
+    }
+    for (int i = 0; i < m; ++i) {
+        if (std::isnan(l[i]) || std::isnan(u[i]) || !(l[i] <= u[i]))
+            return fail(c, SUPPY_EINVAL, "bounds need l <= u and no NaN");
+        if (c->zero_row[i] && !(l[i] <= 0.f && 0.f <= u[i]))
+            return fail(c, SUPPY_EINVAL, "a zero row needs l <= 0 <= u");
+    }
+    if (!c->d_slot_l) {
+        if ((s = dalloc(c, &c->d_slot_l, (size_t)std::max(m, 1))) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_slot_u, (size_t)std::max(m, 1))) != SUPPY_OK) return s;
+    }
+    CK(cudaMemcpyAsync(c->d_slot_l, l, sizeof(float) * m, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_slot_u, u, sizeof(float) * m, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_load_column(c->d_slot_l, c->d_slot_u, c->d_perm, m, c->B, b, c->d_l, c->d_u,
+                          c->stream));
+    CK(launch_reset_column(c->d_x, c->d_lo, c->d_hi, c->n, c->B, b, c->box_len, c->d_st,
+                           c->stream));
+    note_launch(c, 2);
+    return SUPPY_OK;
+}
+
+// Mark right-hand side b stopped (a free slot): every kernel skips it.
+suppy_status ctx_slot_stop(suppy_ctx* c, int b) {
+    if (b < 0 || b >= c->B) return fail(c, SUPPY_EINVAL, "slot out of range");
+    CK(launch_set_stopped(c->d_st, b, c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+// Enqueue a copy of the per-RHS states (B_user entries) into host memory.
+suppy_status ctx_states_async(suppy_ctx* c, RhsState* host) {
+    CK(cudaMemcpyAsync(host, c->d_st, sizeof(RhsState) * c->B_user, cudaMemcpyDeviceToHost,
+                       c->stream));
+    return SUPPY_OK;
+}
+
+// Enqueue x[:, b] -> out (device, n floats).
+suppy_status ctx_slot_extract(suppy_ctx* c, int b, float* out) {
+    CK(launch_extract_column(c->d_x, c->n, c->B, b, out, c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+// Enqueue `iters` superiorized iterations of every active right-hand side.
+suppy_status ctx_iterate(suppy_ctx* c, const suppy_params* p, int iters) {
+    suppy_status s = check_params(c, p);
+    if (s != SUPPY_OK) return s;
+    // a served right-hand side never runs more than its sweep budget, so the
+    // history stays that long however many requests pass through the slot
+    const int need = c->slot_max_sweeps > 0 ? c->slot_max_sweeps : c->k_upper + iters;
+    if ((s = ensure_hist(c, need)) != SUPPY_OK) return s;
+    return enqueue_iterations(c, p, iters);
+}
+
+}  // namespace suppy
+
+namespace {
 
 void destroy_impl(suppy_ctx* c) {
     if (!c) return;

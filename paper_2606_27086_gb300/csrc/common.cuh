@@ -41,6 +41,7 @@ struct StopParams {
     int patience;
     int use_stopping;
     int has_obj;
+    int max_sweeps;         // > 0: a right-hand side also stops after this many sweeps
 };
 
 // One launch of the row pass over rows [part[0], part[ngroups]).
@@ -239,6 +240,13 @@ cudaError_t launch_box_init(float* x, const float* lo, const float* hi, long lon
                             int box_len, const float* x_in, int B_in, cudaStream_t s);
 cudaError_t launch_unpad_x(const float* x, long long n, int B, int B_out, float* out,
                            cudaStream_t s);
+cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
+                               int b, float* l, float* u, cudaStream_t s);
+cudaError_t launch_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
+                                int b, int box_len, RhsState* st, cudaStream_t s);
+cudaError_t launch_set_stopped(RhsState* st, int b, cudaStream_t s);
+cudaError_t launch_extract_column(const float* x, long long n, int B, int b, float* out,
+                                  cudaStream_t s);
 cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
                            double* c64, float* c32, double* work, int work_ctas,
                            cudaStream_t s);
@@ -252,6 +260,20 @@ cudaError_t read_check_word_perturb(int* out3);
 
 // Set the message suppy_last_error(NULL) returns on this thread (api.cu).
 void set_thread_error(const std::string& msg);
+
+// Internal interface of a context for the serving runtime (api.cu, serve.cu).
+int ctx_slots(const suppy_ctx* c);
+int ctx_n(const suppy_ctx* c);
+int ctx_m(const suppy_ctx* c);
+cudaStream_t ctx_stream(const suppy_ctx* c);
+size_t ctx_device_bytes(const suppy_ctx* c);
+const char* ctx_error(const suppy_ctx* c);
+void ctx_set_sweep_budget(suppy_ctx* c, int max_sweeps);
+suppy_status ctx_slot_load(suppy_ctx* c, int b, const float* l, const float* u);
+suppy_status ctx_slot_stop(suppy_ctx* c, int b);
+suppy_status ctx_states_async(suppy_ctx* c, RhsState* host);
+suppy_status ctx_slot_extract(suppy_ctx* c, int b, float* out);
+suppy_status ctx_iterate(suppy_ctx* c, const suppy_params* p, int iters);
 
 // --- device helpers ---------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

@@ -328,6 +328,64 @@ cudaError_t launch_unpad_x(const float* x, long long n, int B, int B_out, float*
     return cudaGetLastError();
 }
 
+// ---- one right-hand side (slot) of a batched context -------------------
+// Column b of the device-order bounds from source-order l_in, u_in (m each).
+__global__ void k_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
+                              int b, float* l, float* u) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int src = perm ? perm[i] : i;
+        l[(size_t)i * B + b] = l_in[src];
+        u[(size_t)i * B + b] = u_in[src];
+    }
+}
+
+// x[:, b] <- box(0), and a fresh iteration state for right-hand side b.
+__global__ void k_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
+                               int b, int box_len, RhsState* st) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const long long bj = (box_len == 1) ? 0 : j;
+        x[j * B + b] = clampf(0.f, lo[bj], hi[bj]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        RhsState r = {};
+        r.last_restart_k = -1;
+        st[b] = r;
+    }
+}
+
+__global__ void k_set_stopped(RhsState* st, int b) { st[b].stopped = 1; }
+
+// out[j] = x[j * B + b]
+__global__ void k_extract_column(const float* x, long long n, int B, int b, float* out) {
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        out[j] = x[j * B + b];
+}
+
+cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
+                               int b, float* l, float* u, cudaStream_t s) {
+    k_load_column<<<grid_for(m), 256, 0, s>>>(l_in, u_in, perm, m, B, b, l, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
+                                int b, int box_len, RhsState* st, cudaStream_t s) {
+    k_reset_column<<<grid_for(n), 256, 0, s>>>(x, lo, hi, n, B, b, box_len, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_stopped(RhsState* st, int b, cudaStream_t s) {
+    k_set_stopped<<<1, 1, 0, s>>>(st, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract_column(const float* x, long long n, int B, int b, float* out,
+                                  cudaStream_t s) {
+    k_extract_column<<<grid_for(n), 256, 0, s>>>(x, n, B, b, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
                            double* c64, float* c32, double* work, int slices, cudaStream_t s) {
     const int tiles = (n + kColTile - 1) / kColTile;

@@ -147,7 +147,8 @@ __device__ void sweep_epilogue(const EpiArgs& a) {
         st.f_valid = 0;
         st.last_prox = p;
         st.k = k + 1;
-        if (a.sp.use_stopping && feas && objok) st.stopped = 1;
+        if ((a.sp.use_stopping && feas && objok) || (a.sp.max_sweeps > 0 && k + 1 >= a.sp.max_sweeps))
+            st.stopped = 1;
     }
 }
 

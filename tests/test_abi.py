@@ -74,7 +74,8 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
     import paper_2606_27086_gb300 as pk
     structs = {"suppy_csr": pk.suppy_csr, "suppy_opts": pk.suppy_opts,
                "suppy_params": pk.suppy_params, "suppy_stats": pk.suppy_stats,
-               "suppy_info": pk.suppy_info}
+               "suppy_info": pk.suppy_info, "suppy_server_opts": pk.suppy_server_opts,
+               "suppy_request_info": pk.suppy_request_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "suppy.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
