@@ -337,6 +337,151 @@ def variants(pk, K, W):
     return out
 
 
+# ----------------------------------------------------------------- serving --
+
+SERVE_STOP = dict(use_stopping=1, prox_rel=1e-4, patience=5, prox_abs=1e-6, obj_rel=0.0,
+                  max_sweeps=500)
+
+
+def serving_workload(pk, nreq: int, seed: int = 501):
+    """The serving mix: Poisson arrivals at 200 requests/s (seed 501); 60% CT
+    slices (128^2 / 256^2 / 512^2 with 90x183 / 180x363 / 360x725 geometries),
+    25% seismic (128x256 / 256x512), 15% radiotherapy plans (three plan sizes
+    on the 50k-300k voxel x 1k-6k beamlet grid, seed 502, OAR caps varied per
+    request).  Every request is one set of slab bounds for a registered
+    matrix; CT and seismic requests are independent noise realisations."""
+    import synth
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / 200.0, size=nreq))
+    kind = rng.choice(3, size=nreq, p=[0.60, 0.25, 0.15])
+    ct_geo = [(128, 90, 183), (256, 180, 363), (512, 360, 725)]
+    se_geo = [(128, 256, 64, 256), (256, 512, 128, 512)]
+    rt_geo = [dict(nx=50, ny=40, nz=25, ns=12, nzb=9), dict(nx=80, ny=50, nz=38, ns=20, nzb=17),
+              dict()]
+    sub = np.where(kind == 0, rng.integers(0, 3, nreq),
+                   np.where(kind == 1, rng.integers(0, 2, nreq), rng.integers(0, 3, nreq)))
+    rng_rt = np.random.default_rng(502)
+    mats, reqs = [], []
+    for k in range(3):
+        for g in range(3 if k != 1 else 2):
+            idx = np.where((kind == k) & (sub == g))[0]
+            if len(idx) == 0:
+                continue
+            R = len(idx)
+            if k == 0:
+                N, na, nb = ct_geo[g]
+                prob = synth.ct_problem(N, na, nb, I0=5e3, delta=0.02, seed_phantom=201 + g,
+                                        seed_noise=1000 * (g + 1), nrhs=max(R, 2))
+                spec = dict(obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_CIMMINO,
+                            sup=dict(gamma=0.5, alpha=0.99, n_red=1), name=f"ct{N}")
+                cols = [(prob.l[:, j], prob.u[:, j]) for j in range(R)]
+            elif k == 1:
+                H, W, ns, nr = se_geo[g]
+                prob = synth.seismic_problem(H, W, ns, nr, nrhs=max(R, 2),
+                                             seed_noise=2000 * (g + 1))
+                spec = dict(obj=pk.SUPPY_OBJ_TV_ANISO, mode=pk.SUPPY_CIMMINO,
+                            sup=dict(gamma=0.5, alpha=0.99, n_red=1), name=f"seismic{H}x{W}")
+                cols = [(prob.l[:, j], prob.u[:, j]) for j in range(R)]
+            else:
+                prob = synth.rt_problem(**rt_geo[g])
+                spec = dict(obj=pk.SUPPY_OBJ_LINEAR, mode=pk.SUPPY_BIP,
+                            sup=dict(gamma=1.0, alpha=0.99, n_red=1),
+                            name=f"rt{prob.meta['n_body']}x{prob.meta['beamlets']}")
+                nt, n1 = prob.meta["n_target"], prob.meta["n_oar1"]
+                cols = []
+                for _ in range(R):
+                    u = prob.u.copy()
+                    u[nt:nt + n1] = rng_rt.uniform(15.0, 25.0)
+                    u[nt + n1:] = rng_rt.uniform(25.0, 35.0)
+                    cols.append((prob.l, u))
+            mats.append((prob, spec))
+            for j, i in enumerate(idx):
+                reqs.append((float(t[i]), len(mats) - 1, cols[j][0], cols[j][1]))
+    reqs.sort(key=lambda r: r[0])
+    return mats, reqs
+
+
+def serving(pk, nreq: int):
+    """Batched BF16 continuous-batching server against one-at-a-time FP32
+    solves of the same requests (arrival times kept, queueing included)."""
+    import torch
+    mats, reqs = serving_workload(pk, nreq)
+    # batched, mixed precision
+    srv = pk.Server(slots=32, check_every=8)
+    mids = []
+    for prob, spec in mats:
+        P = pk.suppy_params_default(**spec["sup"], **SERVE_STOP)
+        mids.append(srv.suppy_server_add_matrix(prob, P, dtype=pk.SUPPY_BF16, mode=spec["mode"],
+                                                obj=spec["obj"]))
+    ids = [None] * len(reqs)
+    t0 = srv.suppy_server_clock()
+    nxt = 0
+    while True:
+        now = srv.suppy_server_clock() - t0
+        while nxt < len(reqs) and reqs[nxt][0] <= now:
+            ids[nxt] = srv.suppy_server_submit(mids[reqs[nxt][1]], reqs[nxt][2], reqs[nxt][3])
+            nxt += 1
+        r, w = srv.suppy_server_step()
+        if nxt == len(reqs) and r == 0 and w == 0:
+            break
+    lat, fin, prox_b, obj_b, sweeps_b = [], [], [], [], []
+    for k, rid in enumerate(ids):
+        info, _ = srv.suppy_server_query(rid)
+        lat.append(info["t_done"] - t0 - reqs[k][0])
+        fin.append(info["t_done"] - t0)
+        prox_b.append(info["proximity"])
+        obj_b.append(info["objective"])
+        sweeps_b.append(info["sweeps"])
+    peak_bytes = srv.suppy_server_device_bytes()
+    srv.close()
+    torch.cuda.synchronize()
+    batched = {"solves_per_s": len(reqs) / max(fin), "p50_s": float(np.percentile(lat, 50)),
+               "p99_s": float(np.percentile(lat, 99)), "makespan_s": max(fin),
+               "mean_sweeps": float(np.mean(sweeps_b)), "dtype": "bf16 A, f32 x, f64 acceptance",
+               "device_bytes_end": int(peak_bytes)}
+    # one at a time, FP32, per-matrix context resident after first use
+    ctxs = {}
+    lat1, fin1, prox_1, obj_1 = [], [], [], []
+    t1 = time.perf_counter()
+    for k, (ta, mi, l, u) in enumerate(reqs):
+        while time.perf_counter() - t1 < ta:
+            time.sleep(1e-4)
+        prob, spec = mats[mi]
+        if mi not in ctxs:
+            q = _with_bounds(prob, l, u)
+            ctxs[mi] = pk.from_problem(q, obj=spec["obj"], mode=spec["mode"])
+        ctx = ctxs[mi]
+        ctx.suppy_set_bounds(np.ascontiguousarray(l, np.float32), np.ascontiguousarray(u, np.float32))
+        ctx.suppy_set_x(np.zeros(prob.A.n, np.float32))
+        st = ctx.suppy_run(pk.suppy_params_default(**spec["sup"], **SERVE_STOP))[0]
+        d = time.perf_counter() - t1
+        lat1.append(d - ta)
+        fin1.append(d)
+        prox_1.append(st["proximity"])
+        obj_1.append(st["objective"])
+    for c in ctxs.values():
+        c.close()
+    torch.cuda.synchronize()
+    plain = {"solves_per_s": len(reqs) / max(fin1), "p50_s": float(np.percentile(lat1, 50)),
+             "p99_s": float(np.percentile(lat1, 99)), "makespan_s": max(fin1), "dtype": "f32"}
+    rp = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(prox_b, prox_1)]
+    ro = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(obj_b, obj_1)]
+    return {"requests": len(reqs), "arrival_rate_per_s": 200.0,
+            "mix": {spec["name"]: sum(1 for r in reqs if r[1] == i)
+                    for i, (_, spec) in enumerate(mats)},
+            "batched": batched, "one_at_a_time": plain,
+            "final_proximity_rel_diff": {"median": float(np.median(rp)), "max": float(np.max(rp))},
+            "final_objective_rel_diff": {"median": float(np.median(ro)), "max": float(np.max(ro))},
+            "stopping": "proximity change < 1e-4 relative for 5 sweeps, P <= 1e-6, or 500 sweeps"}
+
+
+def _with_bounds(prob, l, u):
+    import copy
+    q = copy.copy(prob)
+    q.l, q.u = np.ascontiguousarray(l, np.float32), np.ascontiguousarray(u, np.float32)
+    return q
+
+
 def ours(args):
     import torch
     rank, world, local = dist_env()
@@ -438,6 +583,8 @@ def ours(args):
     ctx.close()
     if rank == 0 and not args.no_variants:
         res["variants"] = variants(pk, K, min(W, 5))
+    if rank == 0 and args.serve_requests > 0:
+        res["serving"] = serving(pk, args.serve_requests)
     if rank == 0 and not args.no_cpu:
         it, el = cpu_baseline(prob, args.cpu_seconds)
         res["cpu_baseline"] = {"value": A.nnz * it / el, "unit": UNIT, "cores": 1,
@@ -494,6 +641,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=128,
+                    help="also run the serving mix with this many requests (512: the full "
+                         "trace) and report it under 'serving'")
     ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or 3: the "
