@@ -337,6 +337,19 @@ def variants(pk, K, W):
     return out
 
 
+def aggregate_over_ranks(ms: float, units: float, world: int):
+    """Whole-job figures of N independent replicas: the elapsed time is the
+    maximum over ranks, and the throughput is the units all ranks processed
+    (each rank `units`) divided by that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units * world / (ms * 1e-3)
+
+
 # ----------------------------------------------------------------- serving --
 
 SERVE_STOP = dict(use_stopping=1, prox_rel=1e-4, patience=5, prox_abs=1e-6, obj_rel=0.0,
@@ -520,12 +533,7 @@ def ours(args):
     # around every launch (no graphs)
     Kt = min(K, 500)
     _, kt, _ = time_iterations(ctx, pk, Kt, 0, SUP, with_timing=True)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = A.nnz * K * world / (ms * 1e-3)
+    ms, value = aggregate_over_ranks(ms, A.nnz * K, world)
     info, per, t_sweep = summarize(ctx, prob, Kt, ms, kt, 4)
     # dominant kernel of the step
     dom = max((k for k in (0, 1, 2) if kt.get(k, (0, 0))[1]), key=lambda k: kt[k][0])
