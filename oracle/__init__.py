@@ -16,6 +16,10 @@ constrained physical problems with SupPy"):
 * relaxation -- Eq. (3), x + lambda (P x - x);
 * simultaneous (Cimmino-type) projection -- Sec. 2.1.1, the relaxed weighted
   average x + lambda sum_i w_i (P_i x - x) with w_i > 0, sum w_i = 1;
+* DROP (diagonally relaxed orthogonal projections) -- appendix Table of used
+  methods, x <- x - Z A^T M (A x - b) with Z = diag(1/nnz(A_{:,j})), taken in
+  slab form with the step of Censor et al. (Q22): x <- box(x + lambda Z sum_i
+  (P_i x - x)), unit row weights;
 * block-iterative projection (BIP) -- Sec. 2.1.1: the simultaneous step inside
   one block, blocks visited in order;
 * box projection after each step -- Sec. 2.3.3 (BoxProjection onto x >= 0);
@@ -36,7 +40,11 @@ reduction step, phase ends when none is accepted or ||g|| = 0; Q7 l <- r after
 the r-th restart; Q8 proximity with the 1/2 of Eq. (WeightedProximity);
 Q10 box after each sweep (Cimmino) or each block (BIP); Q11 zero rows dropped
 (w_i = 0) when 0 lies in their slab; Q13/Q14 TV layout and subgradient; Q16
-stopping.  Parity of the whole superiorized run against printed values is
+stopping; Q22 DROP in slab form: the appendix prints M = diag(w_i) with
+sum w_i = 1 and no 1/||a_i||^2, which would scale the step by 1/m'; the step
+taken is the one of the cited DROP method (unit weights, each row's residual
+divided by ||a_i||^2, Z = diag(1/s_j) with s_j the nonzeros of column j over
+the kept rows), whose fixed points are those of the Cimmino step.  Parity of the whole superiorized run against printed values is
 unpinned: the paper prints no iterates for this path.
 """
 from __future__ import annotations
@@ -47,7 +55,7 @@ import numpy as np
 import scipy.sparse as sp
 
 OBJ_NONE, OBJ_TV_ISO, OBJ_TV_ANISO, OBJ_LINEAR = 0, 1, 2, 3
-CIMMINO, BIP = 0, 1
+CIMMINO, BIP, DROP = 0, 1, 2
 
 
 # ------------------------------------------------------------ projections --
@@ -94,6 +102,7 @@ class Setup:
     w_prox: np.ndarray
     blocks: list = field(default_factory=list)     # list of row-index arrays (BIP)
     sub: list = field(default_factory=list)        # A restricted to each block
+    z: np.ndarray | None = None                    # DROP: 1 / nonzeros per column
 
 
 def setup(A: sp.csr_matrix, l: np.ndarray, u: np.ndarray, mode: int = CIMMINO,
@@ -109,6 +118,11 @@ def setup(A: sp.csr_matrix, l: np.ndarray, u: np.ndarray, mode: int = CIMMINO,
     mk = int(keep.sum())
     w_prox = np.where(keep, 1.0 / max(mk, 1), 0.0)
     S = Setup(A, rho, keep, w_prox.copy(), w_prox)
+    if mode == DROP:
+        # Q22: unit row weights, column scaling 1/s_j over the kept rows
+        S.w_sweep = keep.astype(np.float64)
+        s = np.asarray((A[keep] != 0).sum(axis=0)).ravel().astype(np.float64)
+        S.z = np.where(s > 0, 1.0 / np.maximum(s, 1.0), 0.0)
     if mode == BIP:
         if block_of_row is None:
             raise ValueError("block-iterative mode needs a block id per row")
@@ -157,6 +171,20 @@ def simultaneous_step(A: sp.csr_matrix, rho: np.ndarray, keep: np.ndarray, w: np
     return box_project(x + A.T @ coef, lo, hi), p_in
 
 
+def drop_step(S: Setup, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
+              x: np.ndarray) -> tuple[np.ndarray, float]:
+    """One DROP step in slab form (appendix Table of used methods; Q22):
+    x <- box(x + lambda Z sum_i (P_i x - x)), Z = diag(1/s_j).  Returns the new
+    point and the proximity (weights 1/m') of the step's input point."""
+    r = S.A @ x
+    d = np.clip(r, l, u) - r
+    k = S.keep
+    coef = np.zeros_like(r)
+    coef[k] = d[k] / S.rho[k]
+    p_in = 0.5 * float(np.sum(S.w_prox[k] * d[k] ** 2 / S.rho[k]))
+    return box_project(x + lam * S.z * (S.A.T @ coef), lo, hi), p_in
+
+
 def sweep(S: Setup, mode: int, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
           x: np.ndarray) -> tuple[np.ndarray, float]:
     """One application of the feasibility-seeking operator T.
@@ -169,6 +197,8 @@ def sweep(S: Setup, mode: int, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
     """
     if mode == CIMMINO:
         return simultaneous_step(S.A, S.rho, S.keep, S.w_sweep, S.w_prox, l, u, lam, lo, hi, x)
+    if mode == DROP:
+        return drop_step(S, l, u, lam, lo, hi, x)
     p_tot = 0.0
     for rows, At in zip(S.blocks, S.sub):
         x, p = simultaneous_step(At, S.rho[rows], S.keep[rows], S.w_sweep[rows],

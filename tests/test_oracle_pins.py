@@ -413,3 +413,105 @@ def test_stopping_rule_sequences():
     assert not O.stop_check(ss, 1e-7, 10.0, P2)
     assert O.stop_check(ss, 1e-7, 10.0 + 1e-7, P2)
     assert not O.stop_check(ss, 1e-7, 11.0, P2)
+
+
+# ---------------------------------------------------------------- DROP ----
+
+def test_drop_column_scaling_for_disjoint_rows_is_exact_projection():
+    """Rows with disjoint supports: every column has one nonzero, Z = I, and a
+    DROP step with lambda = 1 projects onto every slab at once -- the exact
+    projection onto their intersection (each slab constrains its own
+    coordinates), landing on the feasible set in one step."""
+    rng = np.random.default_rng(41)
+    blocks = [np.arange(0, 3), np.arange(3, 7), np.arange(7, 9)]
+    A = np.zeros((3, 9))
+    for i, cols in enumerate(blocks):
+        A[i, cols] = rng.uniform(0.5, 2.0, size=len(cols))
+    l = np.array([1.0, -0.5, 2.0])
+    u = np.array([1.5, 0.5, 2.2])
+    S = O.setup(sp.csr_matrix(A), l, u, O.DROP)
+    np.testing.assert_array_equal(S.z, np.ones(9))
+    x = rng.uniform(-2, 2, size=9)
+    y, _ = O.sweep(S, O.DROP, l, u, 1.0, -np.inf, np.inf, x)
+    r = A @ y
+    assert np.all(r >= l - 1e-12) and np.all(r <= u + 1e-12)
+    # and it is the nearest feasible point: each block moved along its row
+    for i, cols in enumerate(blocks):
+        ri = A[i] @ x
+        want = x[cols] + (np.clip(ri, l[i], u[i]) - ri) / (A[i] @ A[i]) * A[i, cols]
+        np.testing.assert_allclose(y[cols], want, atol=1e-12)
+
+
+def test_drop_with_constant_column_counts_is_the_scaled_simultaneous_step():
+    """Every column with exactly two nonzeros: Z = I/2, so DROP equals the
+    simultaneous step with unit weights halved (w_i = 1/2, not 1/m')."""
+    rng = np.random.default_rng(43)
+    n = 8
+    A = np.zeros((n, n))
+    for j in range(n):          # column j lives in rows j and j+1 (cyclic)
+        A[j, j] = rng.uniform(0.5, 1.5)
+        A[(j + 1) % n, j] = rng.uniform(0.5, 1.5)
+    b = A @ rng.uniform(0, 1, n)
+    l, u = b * 0.9, b * 1.1
+    S = O.setup(sp.csr_matrix(A), l, u, O.DROP)
+    np.testing.assert_allclose(S.z, np.full(n, 0.5))
+    x = rng.uniform(-1, 2, n)
+    y, _ = O.sweep(S, O.DROP, l, u, 1.3, 0.0, 1.0, x)
+    # the same step written out row by row
+    acc = np.zeros(n)
+    for i in range(n):
+        r = A[i] @ x
+        acc += (np.clip(r, l[i], u[i]) - r) / (A[i] @ A[i]) * A[i]
+    np.testing.assert_allclose(y, np.clip(x + 1.3 * 0.5 * acc, 0.0, 1.0), atol=1e-13)
+
+
+@pytest.mark.parametrize("lam", [0.5, 1.0, 1.9])
+def test_drop_unit_weight_proximity_nonincreasing(lam):
+    """With unit weights and Z = diag(1/s_j), sum_i a_i a_i^T/||a_i||^2 has norm
+    at most 1 in the Z^{-1} metric, so the box-projected DROP step does not
+    increase F = 1/2 sum_i d_i^2/||a_i||^2 for lambda in (0, 2)."""
+    A, l, u = _tiny(45, consistent=False)
+    S = O.setup(A, l, u, O.DROP)
+    Ad = A.toarray()
+
+    def F(y):
+        r = Ad @ y
+        d = np.clip(r, l, u) - r
+        return 0.5 * np.sum(d ** 2 / np.sum(Ad * Ad, axis=1))
+
+    x = np.full(A.shape[1], 0.9)
+    prev = F(x)
+    for _ in range(200):
+        x, _ = O.sweep(S, O.DROP, l, u, lam, 0.0, 1.0, x)
+        cur = F(x)
+        assert cur <= prev * (1 + 1e-12) + 1e-300
+        prev = cur
+
+
+def test_drop_limit_is_the_least_violation_point_3x3():
+    """The fixed points of box(x + lambda Z g) are those of box(x + lambda g)
+    for a positive diagonal Z, so DROP converges to the same brute-force
+    least-violation point as the simultaneous method (unit weights)."""
+    A = np.array([[1.0, 0.5, 0.0], [0.2, 1.0, 0.7], [0.9, 0.0, 1.2], [1.0, 0.5, 0.0]])
+    l = np.array([1.4, 0.1, 1.9, 0.2])
+    u = np.array([1.6, 0.3, 2.0, 0.3])
+    S = O.setup(sp.csr_matrix(A), l, u, O.DROP)
+    np.testing.assert_allclose(S.z, [1 / 4, 1 / 3, 1 / 2])   # column nonzeros 4, 3, 2
+    x = np.full(3, 0.5)
+    for _ in range(40000):
+        x, _ = O.sweep(S, O.DROP, l, u, 1.0, 0.0, 1.0, x)
+
+    def F(y):
+        r = A @ y
+        viol = np.maximum(l - r, 0) + np.maximum(r - u, 0)
+        return 0.5 * np.sum(viol ** 2 / np.sum(A * A, axis=1))
+
+    g = np.linspace(0, 1, 61)
+    G = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    R = G @ A.T
+    V = np.maximum(l - R, 0) + np.maximum(R - u, 0)
+    Fg = 0.5 * np.sum(V ** 2 / np.sum(A * A, axis=1), axis=1)
+    res = so.minimize(F, G[np.argmin(Fg)], method="L-BFGS-B", bounds=[(0, 1)] * 3,
+                      options={"ftol": 1e-16, "gtol": 1e-12, "maxiter": 10000})
+    assert abs(F(x) - res.fun) < 1e-10
+    np.testing.assert_allclose(x, res.x, atol=2e-4)
