@@ -325,6 +325,8 @@ def variants(pk, K, W):
             params=SUP)
     run_one("seismic_b16_atv_f32_onepass", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
             params=SUP, strategy=pk.STRATEGY_ONE_PASS)
+    run_one("seismic_b16_atv_drop_f32", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
+            mode=pk.SUPPY_DROP, params=SUP)
     seis.l, seis.u = seis.l[:, 0].copy(), seis.u[:, 0].copy()
     run_one("seismic_b1_atv_f32", seis, UNIT, obj=pk.SUPPY_OBJ_TV_ANISO, params=SUP, tune=1)
     del seis

@@ -75,7 +75,14 @@ typedef enum {
 typedef enum { SUPPY_F32 = 0, SUPPY_BF16 = 1, SUPPY_F16 = 2 } suppy_dtype;
 
 /* Feasibility-seeking operator T (Sec. 2.1.1). */
-typedef enum { SUPPY_CIMMINO = 0, SUPPY_BIP = 1 } suppy_mode;
+/* SUPPY_CIMMINO: simultaneous projections, w_i = 1/m' (Sec. 2.1.1).
+ * SUPPY_BIP: block-iterative, w_i = 1/|B_t| inside block t, box after each block.
+ * SUPPY_DROP: diagonally relaxed orthogonal projections (appendix Table of used
+ *   methods, in slab form): x <- box(x + lambda Z sum_i (P_i x - x)) with unit
+ *   row weights and Z = diag(1/s_j), s_j the stored nonzeros of column j in the
+ *   rows with ||a_i|| > 0 (0 for an empty column).  The monitored proximity
+ *   keeps the weights 1/m'. */
+typedef enum { SUPPY_CIMMINO = 0, SUPPY_BIP = 1, SUPPY_DROP = 2 } suppy_mode;
 
 /* Objective of the perturbation phase. */
 typedef enum {

@@ -62,6 +62,7 @@ struct suppy_ctx {
     float* d_g = nullptr;
     float* d_lo = nullptr;
     float* d_hi = nullptr;
+    float* d_zc = nullptr;          // DROP column scaling (null otherwise)
     double* d_pp = nullptr;
     RhsState* d_st = nullptr;
     double* d_prox_hist = nullptr;
@@ -356,6 +357,8 @@ SweepArgs row_args(suppy_ctx* c, int t, float lam) {
 }
 
 double seg_scale(const suppy_ctx* c, int t) {
+    // DROP sweeps with unit row weights; the monitored proximity keeps 1/m'
+    if (c->mode == SUPPY_DROP) return c->m_kept > 0 ? 0.5 / c->m_kept : 0.0;
     if (c->nseg == 1) return 0.5;
     return c->m_kept > 0 ? 0.5 * (double)c->seg_kept[t] / c->m_kept : 0.0;
 }
@@ -440,6 +443,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.xw = c->d_x;
                 ca.lo = c->d_lo;
                 ca.hi = c->d_hi;
+                ca.zc = c->d_zc;
                 ca.box_len = c->box_len;
                 ca.epi = e2;
                 Timed tm{c, 1};
@@ -455,6 +459,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 FinalizeArgs f;
                 f.x = c->d_x;
                 f.delta = c->d_delta;
+                f.zc = c->d_zc;
                 f.lo = c->d_lo;
                 f.hi = c->d_hi;
                 f.nB = (long long)c->n * c->B;
@@ -478,6 +483,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.x = c->d_x;
             ca.lo = c->d_lo;
             ca.hi = c->d_hi;
+            ca.zc = c->d_zc;
             ca.box_len = c->box_len;
             ca.B = c->B;
             ca.cpart = c->d_cpart + c->seg_cpart_off[t];
@@ -499,6 +505,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             FinalizeArgs f;
             f.x = c->d_x;
             f.delta = c->d_delta;
+            f.zc = c->d_zc;
             f.lo = c->d_lo;
             f.hi = c->d_hi;
             f.nB = (long long)c->n * c->B;
@@ -1089,7 +1096,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (c->dt != SUPPY_F32 && c->dt != SUPPY_BF16 && c->dt != SUPPY_F16)
         return fail(c, SUPPY_EINVAL, "unknown a_dtype");
     c->mode = o->mode;
-    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP) return fail(c, SUPPY_EINVAL, "unknown mode");
+    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP)
+        return fail(c, SUPPY_EINVAL, "unknown mode");
     c->obj = o->obj;
     if ((int)c->obj < 0 || (int)c->obj > 3) return fail(c, SUPPY_EINVAL, "unknown objective");
     c->B_user = o->nrhs <= 0 ? 1 : o->nrhs;
@@ -1268,7 +1276,17 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     std::vector<double> segw(c->nseg, 0.0);
     for (int t = 0; t < c->nseg; ++t) {
         const int k = (c->mode == SUPPY_BIP) ? c->seg_kept[t] : c->m_kept;
-        segw[t] = k > 0 ? 1.0 / k : 0.0;
+        segw[t] = (c->mode == SUPPY_DROP) ? 1.0 : (k > 0 ? 1.0 / k : 0.0);
+    }
+    if (c->mode == SUPPY_DROP) {
+        int* d_cnt = nullptr;
+        if ((s = dalloc(c, &c->d_zc, (size_t)n)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &d_cnt, (size_t)n)) != SUPPY_OK) return s;
+        CK(launch_column_scaling(c->d_rinfo, c->d_col, c->d_val, c->dt, c->d_rho, m, n, d_cnt,
+                                 c->d_zc, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        dfree(c, d_cnt);
+        note_launch(c, 2);
     }
     double* d_segw = nullptr;
     if ((s = stage(c, segw.data(), segw.size(), 0, &d_segw, tg.v)) != SUPPY_OK) return s;

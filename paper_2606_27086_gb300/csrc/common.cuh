@@ -84,6 +84,7 @@ struct EpiArgs {
 struct FinalizeArgs {
     float* x;
     float* delta;
+    const float* zc;        // DROP column scaling 1/s_j (n) or null (1)
     const float* lo;
     const float* hi;
     long long nB;           // n * B elements
@@ -102,6 +103,7 @@ struct ColArgs {
     float* x;               // n x B
     const float* lo;
     const float* hi;
+    const float* zc;        // DROP column scaling 1/s_j (n) or null (1)
     int box_len;
     int B;
     const int* cpart;
@@ -182,6 +184,7 @@ struct StreamArgs {
     float* xw;
     const float* lo;
     const float* hi;
+    const float* zc;        // DROP column scaling 1/s_j (n) or null (1)
     int box_len;
     EpiArgs epi;
 };
@@ -247,6 +250,10 @@ cudaError_t launch_reset_column(float* x, const float* lo, const float* hi, long
 cudaError_t launch_set_stopped(RhsState* st, int b, cudaStream_t s);
 cudaError_t launch_extract_column(const float* x, long long n, int B, int b, float* out,
                                   cudaStream_t s);
+// DROP: zc[j] = 1 / (stored nonzeros of column j in rows with ||a_i|| > 0), 0 if none.
+cudaError_t launch_column_scaling(const int2* rinfo, const int* col, const void* val,
+                                  suppy_dtype dt, const double* rho, int m, int n, int* counts,
+                                  float* zc, cudaStream_t s);
 cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
                            double* c64, float* c32, double* work, int work_ctas,
                            cudaStream_t s);

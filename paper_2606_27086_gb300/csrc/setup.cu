@@ -363,6 +363,45 @@ __global__ void k_extract_column(const float* x, long long n, int B, int b, floa
         out[j] = x[j * B + b];
 }
 
+// DROP column counts: one warp per device row with ||a_i|| > 0 adds 1 to the
+// count of every column it stores a nonzero in; zc = 1 / count.
+template <typename VT>
+__global__ void k_col_counts(const int2* rinfo, const int* col, const VT* val, const double* rho,
+                             int m, int* counts) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+        if (!(rho[i] > 0.0)) continue;
+        const int2 ri = rinfo[i];
+        for (int e = lane; e < ri.y; e += 32)
+            if ((float)val[ri.x + e] != 0.f) atomicAdd(counts + col[ri.x + e], 1);
+    }
+}
+
+__global__ void k_inv_counts(const int* counts, int n, float* zc) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        zc[j] = counts[j] > 0 ? 1.0f / (float)counts[j] : 0.f;
+}
+
+cudaError_t launch_column_scaling(const int2* rinfo, const int* col, const void* val,
+                                  suppy_dtype dt, const double* rho, int m, int n, int* counts,
+                                  float* zc, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((long long)m * 32);
+    if (dt == SUPPY_F32)
+        k_col_counts<float><<<grid, 256, 0, s>>>(rinfo, col, static_cast<const float*>(val), rho, m,
+                                                 counts);
+    else if (dt == SUPPY_BF16)
+        k_col_counts<__nv_bfloat16><<<grid, 256, 0, s>>>(
+            rinfo, col, static_cast<const __nv_bfloat16*>(val), rho, m, counts);
+    else
+        k_col_counts<__half><<<grid, 256, 0, s>>>(rinfo, col, static_cast<const __half*>(val), rho,
+                                                  m, counts);
+    k_inv_counts<<<grid_for(n), 256, 0, s>>>(counts, n, zc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
                                int b, float* l, float* u, cudaStream_t s) {
     k_load_column<<<grid_for(m), 256, 0, s>>>(l_in, u_in, perm, m, B, b, l, u);

@@ -470,26 +470,29 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs
 template <typename VT, int G>
 struct ColWork {
     const StreamArgs& a;
-    float xj = 0.f, lo = 0.f, hi = 0.f;
-    float nx = 0.f, nlo = 0.f, nhi = 0.f;
+    float xj = 0.f, lo = 0.f, hi = 0.f, z = 1.f;
+    float nx = 0.f, nlo = 0.f, nhi = 0.f, nz = 1.f;
     __device__ void prefetch(int j) {
         if (j >= 0) {
             const int bj = (a.box_len == 1) ? 0 : j;
             nx = a.xw[j];   // owned by this group alone during the pass
             nlo = __ldg(a.lo + bj);
             nhi = __ldg(a.hi + bj);
+            if (a.zc) nz = __ldg(a.zc + j);
         }
     }
     __device__ void advance() {
         xj = nx;
         lo = nlo;
         hi = nhi;
+        z = nz;
     }
     __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
         float s = ring_dot<VT, G>(r, g0, len, gl, a.coef_in);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
+        if (a.zc) s *= z;
         if (gl == 0) a.xw[j] = clampf(xj + s, lo, hi);
         return 0.0;
     }

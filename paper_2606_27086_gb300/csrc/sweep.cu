@@ -411,6 +411,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
         if (lane == 0 && ci.y > 0) {
             const int bj = (a.box_len == 1) ? 0 : j;
+            if (a.zc) s *= a.zc[j];
             a.x[j] = clampf(a.x[j] + s, a.lo[bj], a.hi[bj]);
         }
     }
@@ -459,6 +460,13 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
         if (e0 == 0 && CHECKED(ALIGNED16(a.x + (size_t)j * B + 4 * q), 314, j)) {
             const int bj = (a.box_len == 1) ? 0 : j;
             const float lo = a.lo[bj], hi = a.hi[bj];
+            if (a.zc) {
+                const float z = a.zc[j];
+                s.x *= z;
+                s.y *= z;
+                s.z *= z;
+                s.w *= z;
+            }
             float4* xp = reinterpret_cast<float4*>(a.x + (size_t)j * B) + q;
             float4 xv = *xp;
             xv.x = clampf(xv.x + s.x, lo, hi);
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
         float4 xv = x4[v];
-        const float4 dv = d4[v];
+        float4 dv = d4[v];
         float lo[4], hi[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
@@ -494,6 +502,12 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
             const long long j = (a.box_len == 1) ? 0 : idx / a.B;
             lo[t] = a.lo[j];
             hi[t] = a.hi[j];
+        }
+        if (a.zc) {
+            dv.x *= a.zc[(4 * v) / a.B];
+            dv.y *= a.zc[(4 * v + 1) / a.B];
+            dv.z *= a.zc[(4 * v + 2) / a.B];
+            dv.w *= a.zc[(4 * v + 3) / a.B];
         }
         xv.x = clampf(xv.x + dv.x, lo[0], hi[0]);
         xv.y = clampf(xv.y + dv.y, lo[1], hi[1]);
@@ -505,7 +519,8 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
     if (blockIdx.x == 0) {
         for (long long idx = 4 * nv + threadIdx.x; idx < a.nB; idx += blockDim.x) {
             const long long j = (a.box_len == 1) ? 0 : idx / a.B;
-            a.x[idx] = clampf(a.x[idx] + a.delta[idx], a.lo[j], a.hi[j]);
+            const float d = a.zc ? a.delta[idx] * a.zc[idx / a.B] : a.delta[idx];
+            a.x[idx] = clampf(a.x[idx] + d, a.lo[j], a.hi[j]);
             a.delta[idx] = 0.f;
         }
         sweep_epilogue(a.epi);
