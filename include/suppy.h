@@ -89,7 +89,10 @@ typedef enum {
     SUPPY_OBJ_NONE = 0,     /* feasibility-seeking only                              */
     SUPPY_OBJ_TV_ISO = 1,   /* Eq. (TV) on an img_h x img_w row-major image          */
     SUPPY_OBJ_TV_ANISO = 2, /* sum |x[i+1,j]-x[i,j]| + sum |x[i,j+1]-x[i,j]|         */
-    SUPPY_OBJ_LINEAR = 3    /* f = c.x, e.g. f_Mean = (1/N_S) sum_{i in S} (A_S x)_i */
+    SUPPY_OBJ_LINEAR = 3,   /* f = c.x, e.g. f_Mean = (1/N_S) sum_{i in S} (A_S x)_i */
+    SUPPY_OBJ_L1 = 4,       /* f = ||x||_1, subgradient sign(x) (0 at 0)             */
+    SUPPY_OBJ_L2 = 5        /* f = ||x||_2^2, gradient 2x (L1 / L2 perturbations of the
+                             * seismic study, Sec. 2.3.1)                             */
 } suppy_obj;
 
 /* CSR matrix: row_ptr[m+1] (row_ptr[0] = 0, nondecreasing, row_ptr[m] = nnz),

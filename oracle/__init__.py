@@ -29,8 +29,10 @@ constrained physical problems with SupPy"):
 * stopping -- Sec. 2.2.1 (P <= P*, relative proximity change below dP* for N
   consecutive iterations, N_max) and Sec. 2.2.3 (relative objective change);
 * objectives -- isotropic TV, Eq. (TV) with the subgradient of the Combettes /
-  Penfold method (Sec. 2.3.1), anisotropic TV, and the mean dose of Sec. 2.3.3
-  (f_Mean, appendix Table of dose objectives).
+  Penfold method (Sec. 2.3.1), anisotropic TV, the mean dose of Sec. 2.3.3
+  (f_Mean, appendix Table of dose objectives), and the L1 / L2 perturbations
+  of the seismic study (Sec. 2.3.1): ||x||_1 with subgradient sign(x), and
+  ||x||_2^2 with gradient 2x (Q23).
 
 Readings where the paper is silent or garbled (numbered as in the design notes):
 Q1 two-sided slab; Q2 w_i = 1/m' (Cimmino) and 1/|B_t| (BIP); Q3 descent
@@ -40,7 +42,8 @@ reduction step, phase ends when none is accepted or ||g|| = 0; Q7 l <- r after
 the r-th restart; Q8 proximity with the 1/2 of Eq. (WeightedProximity);
 Q10 box after each sweep (Cimmino) or each block (BIP); Q11 zero rows dropped
 (w_i = 0) when 0 lies in their slab; Q13/Q14 TV layout and subgradient; Q16
-stopping; Q22 DROP in slab form: the appendix prints M = diag(w_i) with
+stopping; Q23 L2 perturbation objective f = ||x||_2^2 (the acceptance test and
+the normalised direction are the same for ||x||_2); Q22 DROP in slab form: the appendix prints M = diag(w_i) with
 sum w_i = 1 and no 1/||a_i||^2, which would scale the step by 1/m'; the step
 taken is the one of the cited DROP method (unit weights, each row's residual
 divided by ||a_i||^2, Z = diag(1/s_j) with s_j the nonzeros of column j over
@@ -54,7 +57,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.sparse as sp
 
-OBJ_NONE, OBJ_TV_ISO, OBJ_TV_ANISO, OBJ_LINEAR = 0, 1, 2, 3
+OBJ_NONE, OBJ_TV_ISO, OBJ_TV_ANISO, OBJ_LINEAR, OBJ_L1, OBJ_L2 = 0, 1, 2, 3, 4, 5
 CIMMINO, BIP, DROP = 0, 1, 2
 
 
@@ -281,6 +284,10 @@ class Objective:
             return tv_aniso(x, *self.shape)
         if self.kind == OBJ_LINEAR:
             return float(self.c @ x)
+        if self.kind == OBJ_L1:
+            return float(np.sum(np.abs(x)))
+        if self.kind == OBJ_L2:
+            return float(x @ x)
         return 0.0
 
     def g(self, x: np.ndarray) -> np.ndarray:
@@ -290,6 +297,10 @@ class Objective:
             return tv_aniso_subgrad(x, *self.shape)
         if self.kind == OBJ_LINEAR:
             return self.c.copy()
+        if self.kind == OBJ_L1:
+            return np.sign(x)
+        if self.kind == OBJ_L2:
+            return 2.0 * x
         return np.zeros_like(x)
 
 
@@ -314,6 +325,7 @@ class Params:
     patience: int = 5
     obj_rel: float = 1e-6
     use_stopping: bool = False      # False: run exactly max_sweeps sweeps
+    variance_tol: float = 0.0       # > 0: the variance stopping rule (Sec. 3.2, CT study)
 
 
 @dataclass
@@ -404,6 +416,14 @@ class RunResult:
     ell: int
 
 
+def variance_of_changes(omega: list) -> float:
+    """Variance stopping measure of the CT study (Sec. 3.2): the sample
+    variance 1/(k-1) sum_i (omega_i - mean)^2 of the relative changes
+    omega_i = ||x^i - x^(i-1)|| / ||x^i|| of all iterates so far."""
+    w = np.asarray(omega, np.float64)
+    return float(np.sum((w - w.mean()) ** 2) / (len(w) - 1))
+
+
 def run(S: Setup, mode: int, l, u, lo, hi, obj: Objective, P: Params,
         x0: np.ndarray | None = None, n_sweeps: int | None = None) -> RunResult:
     """Algorithm 1: perturbation phase, then one application of T, repeated.
@@ -418,9 +438,11 @@ def run(S: Setup, mode: int, l, u, lo, hi, obj: Objective, P: Params,
     st = PertState()
     ss = StopState()
     ph, oh, acc, tri = [], [], [], []
+    omega = []
     K = P.max_sweeps if n_sweeps is None else n_sweeps
     k = 0
     while k < K:
+        x_prev = x
         f_k = None
         if obj.kind != OBJ_NONE:
             maybe_restart(st, k, P)
@@ -434,6 +456,11 @@ def run(S: Setup, mode: int, l, u, lo, hi, obj: Objective, P: Params,
         k += 1
         if P.use_stopping and stop_check(ss, p, f_k, P):
             break
+        if P.variance_tol > 0:
+            nx = float(np.linalg.norm(x))
+            omega.append(float(np.linalg.norm(x - x_prev)) / nx if nx > 0 else 0.0)
+            if len(omega) >= 2 and variance_of_changes(omega) < P.variance_tol:
+                break
     return RunResult(x, k, ph, oh, acc, tri, st.ell)
 
 

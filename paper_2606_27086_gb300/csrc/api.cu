@@ -1099,7 +1099,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP)
         return fail(c, SUPPY_EINVAL, "unknown mode");
     c->obj = o->obj;
-    if ((int)c->obj < 0 || (int)c->obj > 3) return fail(c, SUPPY_EINVAL, "unknown objective");
+    if ((int)c->obj < 0 || (int)c->obj > 5) return fail(c, SUPPY_EINVAL, "unknown objective");
     c->B_user = o->nrhs <= 0 ? 1 : o->nrhs;
     if (c->B_user > kMaxRhs) return fail(c, SUPPY_EINVAL, "nrhs must be at most 32");
     if (o->perturb_path < 0 || o->perturb_path > 2)

@@ -72,11 +72,27 @@ __device__ __forceinline__ float trial_scale(double gamma, double log2_alpha, lo
     return (float)gamma * ldexpf(exp2f(f), (int)k) * inv_gnorm;
 }
 
+// Objectives whose value is a sum of per-element terms (no stencil): the
+// linear mean dose c.x, ||x||_1 and ||x||_2^2.
+__device__ __forceinline__ bool elementwise(int obj) {
+    return obj == SUPPY_OBJ_LINEAR || obj == SUPPY_OBJ_L1 || obj == SUPPY_OBJ_L2;
+}
+
+// Term and (sub)gradient of ||x||_1 (sign, 0 at 0) and ||x||_2^2 (2x).
+__device__ __forceinline__ float norm_term(int obj, float v) {
+    return obj == SUPPY_OBJ_L1 ? fabsf(v) : v * v;
+}
+__device__ __forceinline__ float norm_grad(int obj, float v) {
+    if (obj == SUPPY_OBJ_L1) return (v > 0.f) ? 1.f : ((v < 0.f) ? -1.f : 0.f);
+    return 2.f * v;
+}
+
 // Objective term owned by pixel p (FP64 result; TV terms are FP32 then widened).
 template <class Y>
 __device__ __forceinline__ double obj_term(int obj, int p, int H, int W, const double* c64,
                                            const Y& y) {
     if (obj == SUPPY_OBJ_LINEAR) return c64[p] * (double)y(p);
+    if (obj == SUPPY_OBJ_L1 || obj == SUPPY_OBJ_L2) return (double)norm_term(obj, y(p));
     const int i = p / W, j = p - i * W;
     const float y0 = y(p);
     if (obj == SUPPY_OBJ_TV_ISO) {
@@ -99,6 +115,7 @@ template <class Y>
 __device__ __forceinline__ float subgrad(int obj, int p, int H, int W, const float* c32,
                                          const Y& y) {
     if (obj == SUPPY_OBJ_LINEAR) return c32[p];
+    if (obj == SUPPY_OBJ_L1 || obj == SUPPY_OBJ_L2) return norm_grad(obj, y(p));
     const int i = p / W, j = p - i * W;
     const float y0 = y(p);
     float g = 0.f;
@@ -395,11 +412,12 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     if (ps.skip) return;                        // uniform over the cluster
     const int rank = (int)cluster.block_rank();
     const bool lin = (a.obj == SUPPY_OBJ_LINEAR);
-    const int H = lin ? a.n : a.H, W = lin ? 1 : a.W;   // linear: a column of n "rows"
+    const bool elem = elementwise(a.obj);
+    const int H = elem ? a.n : a.H, W = elem ? 1 : a.W;   // element-wise: a column of n "rows"
     const int r0 = band_start(rank, H, cs), r1 = band_start(rank + 1, H, cs);
     int band = (r1 - r0) * W;
     const int maxband = ((H + cs - 1) / cs) * W;
-    if (!PCHECKED(band >= 0 && band <= maxband && (lin || cs <= H), 401, rank)) band = 0;
+    if (!PCHECKED(band >= 0 && band <= maxband && (elem || cs <= H), 401, rank)) band = 0;
     float* ys = smem;
     float* gs = smem + maxband;
     float* X = a.x + b;
@@ -412,7 +430,7 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     cluster.sync();
     Band yb{ys, nullptr, nullptr, r0, r1, 0, W};
     Band gb{gs, nullptr, nullptr, r0, r1, 0, W};
-    if (!lin) {
+    if (!elem) {
         if (rank > 0) {
             yb.up = cluster.map_shared_rank(ys, rank - 1);
             gb.up = cluster.map_shared_rank(gs, rank - 1);
@@ -437,6 +455,13 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
                 fy += a.c64[p] * (double)ys[q];
                 const float gp = gs[q];
                 kg.add(gp * gp);
+            } else if (elem) {
+                kf.add(norm_term(a.obj, ys[q]));
+                if (!a.record_only) {
+                    const float gp = norm_grad(a.obj, ys[q]);
+                    gs[q] = gp;
+                    kg.add(gp * gp);
+                }
             } else {
                 const int i = r0 + q / W, j = q % W;
                 kf.add(tv_term(a.obj, i, j, H, W, yb));
@@ -467,6 +492,11 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
             if (lin) {
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
                     fz += a.c64[p0 + q] * (double)trial(ys[q], gs[q], sc);
+            } else if (elem) {
+                KSum kz;
+                for (int q = threadIdx.x; q < band; q += kPerturbThreads)
+                    kz.add(norm_term(a.obj, trial(ys[q], gs[q], sc)));
+                fz = kz.value();
             } else {
                 auto z = [&yb, &gb, sc](int i, int j) { return trial(yb(i, j), gb(i, j), sc); };
                 KSum kz;
@@ -641,6 +671,10 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_grad(const PerturbArgs a)
             if (lin) {
                 gp = a.c32[p];
                 fl += a.c64[p] * (double)a.x[e];
+            } else if (elementwise(obj)) {
+                const float y0 = a.x[e];
+                kf.add(norm_term(obj, y0));
+                gp = norm_grad(obj, y0);
             } else {
                 const int i = p / W, j = p - i * W;
                 GlobalImage yi{yb, B, W};
@@ -728,6 +762,11 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_trials(const PerturbArgs 
                 const double c = a.c64[p];
 #pragma unroll
                 for (int jj = 0; jj < kWideTrials; ++jj) fl[jj] += c * (double)trial(y0, g0, sj[jj]);
+            } else if (elementwise(obj)) {
+                const float y0 = a.x[e], g0 = a.g[e];
+#pragma unroll
+                for (int jj = 0; jj < kWideTrials; ++jj)
+                    kz[jj].add(norm_term(obj, trial(y0, g0, sj[jj])));
             } else {
                 const int i = p / W, j = p - i * W;
 #pragma unroll
@@ -856,9 +895,9 @@ int fit_perturb_cluster(int want, int obj, int n, int H, int W) {
 }
 
 size_t perturb_smem_bytes(int obj, int n, int H, int W, int cs) {
-    const bool lin = (obj == SUPPY_OBJ_LINEAR);
-    const long long rows = lin ? n : H, w = lin ? 1 : W;
-    if (!lin && cs > H) return 0;
+    const bool elem = (obj == SUPPY_OBJ_LINEAR || obj == SUPPY_OBJ_L1 || obj == SUPPY_OBJ_L2);
+    const long long rows = elem ? n : H, w = elem ? 1 : W;
+    if (!elem && cs > H) return 0;
     const long long maxband = ((rows + cs - 1) / cs) * w;
     const size_t bytes = (size_t)(2 * maxband) * sizeof(float);
     return bytes <= 200 * 1024 ? bytes : 0;

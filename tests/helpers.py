@@ -7,7 +7,8 @@ import numpy as np
 import oracle as O
 import synth
 
-OBJ_OF = {"none": O.OBJ_NONE, "tv": O.OBJ_TV_ISO, "atv": O.OBJ_TV_ANISO, "lin": O.OBJ_LINEAR}
+OBJ_OF = {"none": O.OBJ_NONE, "tv": O.OBJ_TV_ISO, "atv": O.OBJ_TV_ANISO, "lin": O.OBJ_LINEAR,
+          "l1": O.OBJ_L1, "l2": O.OBJ_L2}
 
 
 def rel_l2(a, b) -> float:
@@ -36,6 +37,8 @@ def oracle_objective(prob, kind: int) -> O.Objective:
     if kind == O.OBJ_LINEAR:
         c = O.mean_dose_vector(prob.body.to_scipy()) if prob.body is not None else prob.c_lin
         return O.Objective(kind, c=c)
+    if kind in (O.OBJ_L1, O.OBJ_L2):
+        return O.Objective(kind)
     return O.Objective(kind, prob.shape)
 
 

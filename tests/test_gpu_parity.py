@@ -609,3 +609,33 @@ def test_drop_batched_and_superiorized_seismic_run():
         r = O.run(S, O.DROP, O.rhs(l, b), O.rhs(u, b), lo, hi, ob, O.Params(**P))
         assert st[b]["ell"] == r.ell
         assert rel_l2(xg[:, b], r.x) <= 1e-3
+
+
+# ------------------------------------------------------- L1 / L2 perturbations ----
+
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("kind", ["l1", "l2"])
+def test_norm_perturbations_match_oracle(kind, path):
+    """The L1 / L2 perturbations of the seismic study through the cluster
+    kernel and the whole-GPU step: one phase (several reduction steps), the
+    objective value, and a short superiorized DROP run."""
+    prob = synth.seismic_problem(32, 64, 16, 64, nrhs=1)
+    obj = {"l1": pk.SUPPY_OBJ_L1, "l2": pk.SUPPY_OBJ_L2}[kind]
+    okind = {"l1": O.OBJ_L1, "l2": O.OBJ_L2}[kind]
+    ob = oracle_objective(prob, okind)
+    x0 = random_x(prob.A.n, 1, seed=57, lo=-0.2, hi=0.5)
+    ctx = pk.from_problem(prob, obj=obj, mode=pk.SUPPY_DROP, perturb_path=path)
+    ctx.suppy_set_x(x0)
+    xb = np.clip(x0.astype(np.float64), prob.box_lo[0], prob.box_hi[0])
+    assert rel(ctx.suppy_objective()[0], ob.f(xb)) <= 1e-6
+    P = dict(gamma=0.2, alpha=0.9, n_red=3, max_trials=30)
+    acc = ctx.suppy_perturb(_params(**P))
+    y, a, _ = O.perturbation_phase(ob, xb, O.PertState(), O.Params(**P))
+    assert acc[0] == a
+    assert rel_l2(ctx.suppy_get_x(), y) <= 1e-5
+    ctx = pk.from_problem(prob, obj=obj, mode=pk.SUPPY_DROP, perturb_path=path)
+    R = dict(gamma=0.5, alpha=0.99, n_red=1, max_sweeps=25)
+    ctx.suppy_run(_params(**R))
+    S, l, u, lo, hi = O.from_problem(prob, O.DROP)
+    r = O.run(S, O.DROP, l, u, lo, hi, ob, O.Params(**R))
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3

@@ -515,3 +515,69 @@ def test_drop_limit_is_the_least_violation_point_3x3():
                       options={"ftol": 1e-16, "gtol": 1e-12, "maxiter": 10000})
     assert abs(F(x) - res.fun) < 1e-10
     np.testing.assert_allclose(x, res.x, atol=2e-4)
+
+
+# ------------------------------------------------------ L1 / L2 objectives ----
+
+def test_l1_objective_value_and_subgradient_inequality():
+    """f = ||x||_1: the value is the sum of magnitudes and sign(x) (0 at 0) is
+    a subgradient: f(y) >= f(x) + g.(y - x) for every y."""
+    rng = np.random.default_rng(61)
+    x = rng.normal(size=50)
+    x[[3, 17]] = 0.0
+    ob = O.Objective(O.OBJ_L1)
+    assert ob.f(x) == pytest.approx(sum(abs(v) for v in x), rel=1e-15)
+    g = ob.g(x)
+    assert g[3] == 0.0 and g[17] == 0.0
+    for _ in range(200):
+        y = rng.normal(size=50)
+        assert ob.f(y) >= ob.f(x) + g @ (y - x) - 1e-12
+
+
+def test_l2_objective_gradient_by_central_differences():
+    rng = np.random.default_rng(62)
+    x = rng.normal(size=20)
+    ob = O.Objective(O.OBJ_L2)
+    assert ob.f(x) == pytest.approx(float(np.dot(x, x)), rel=1e-15)
+    h = 1e-6
+    fd = np.array([(ob.f(x + h * e) - ob.f(x - h * e)) / (2 * h) for e in np.eye(20)])
+    np.testing.assert_allclose(ob.g(x), fd, atol=1e-6)
+
+
+def test_l2_perturbation_step_shrinks_towards_the_origin():
+    """With f = ||x||^2 the normalised direction is -x/||x||, so an accepted
+    step of size beta < ||x|| scales x by (1 - beta/||x||) exactly."""
+    x = np.array([3.0, -4.0, 0.0, 12.0])          # ||x|| = 13
+    P = O.Params(gamma=2.6, alpha=0.5, n_red=1, max_trials=5)
+    st = O.PertState()
+    y, a, t = O.perturbation_phase(O.Objective(O.OBJ_L2), x, st, P)
+    assert (a, t, st.ell) == (1, 1, 1)
+    np.testing.assert_allclose(y, x * (1 - 2.6 / 13.0), atol=1e-14)
+
+
+# ------------------------------------------------- variance stopping rule ----
+
+def test_variance_of_changes_is_the_sample_variance():
+    w = [1.0, 0.2, 0.1, 0.05]
+    m = sum(w) / 4
+    assert O.variance_of_changes(w) == pytest.approx(sum((v - m) ** 2 for v in w) / 3,
+                                                     rel=1e-15)
+
+
+def test_variance_rule_stops_at_the_first_iterate_below_the_threshold():
+    """Replaying the run by hand: the rule stops after the first iteration k
+    >= 2 whose variance of relative changes falls below the threshold."""
+    A, l, u = _tiny(71, m=30, n=10, consistent=False)
+    S = O.setup(A, l, u)
+    P = O.Params(max_sweeps=400, variance_tol=1e-2)     # the paper's threshold
+    r = O.run(S, O.CIMMINO, l, u, 0.0, 1.0, O.Objective(O.OBJ_NONE), P)
+    x = np.zeros(A.shape[1])
+    omega = []
+    for k in range(1, 401):
+        y, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, 0.0, 1.0, x)
+        omega.append(np.linalg.norm(y - x) / np.linalg.norm(y))
+        x = y
+        if k >= 2 and np.var(omega, ddof=1) < 1e-2:
+            break
+    assert r.sweeps == k < 400
+    np.testing.assert_array_equal(r.x, x)
