@@ -165,6 +165,12 @@ typedef struct {
     int32_t patience;       /* N                                                   */
     int32_t use_stopping;   /* 0: run exactly max_sweeps sweeps                    */
     int32_t use_graphs;     /* 1: suppy_run replays one captured iteration (CUDA graph) */
+    /* > 0: the variance stopping rule of the CT study (Sec. 3.2): a right-hand
+     * side stops after iteration k >= 2 once the sample variance of the
+     * relative changes ||x^i - x^(i-1)|| / ||x^i||, i = 1..k, of its iterates
+     * (since the last set_x / set_bounds / reset) is below variance_tol.  Applies
+     * in suppy_run, whatever use_stopping says; 0 disables it. */
+    double variance_tol;
 } suppy_params;
 
 typedef struct {

@@ -63,7 +63,8 @@ class suppy_params(ctypes.Structure):
                 ("max_sweeps", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("prox_abs", ctypes.c_double), ("prox_rel", ctypes.c_double),
                 ("obj_rel", ctypes.c_double), ("patience", ctypes.c_int32),
-                ("use_stopping", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("use_stopping", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("variance_tol", ctypes.c_double)]
 
 
 class suppy_stats(ctypes.Structure):

@@ -63,6 +63,12 @@ struct suppy_ctx {
     float* d_lo = nullptr;
     float* d_hi = nullptr;
     float* d_zc = nullptr;          // DROP column scaling (null otherwise)
+    // variance stopping rule: previous iterate, partials, ticket
+    float* d_xprev = nullptr;
+    bool xprev_stale = true;
+    double* d_vpart = nullptr;
+    unsigned* d_vticket = nullptr;
+    int vgrid = 0;
     double* d_pp = nullptr;
     RhsState* d_st = nullptr;
     double* d_prox_hist = nullptr;
@@ -254,6 +260,7 @@ void reset_state_host(suppy_ctx* c, std::vector<RhsState>& st) {
 
 suppy_status reset_state(suppy_ctx* c) {
     c->k_upper = 0;
+    c->xprev_stale = true;
     std::vector<RhsState> st;
     reset_state_host(c, st);
     CK(cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice,
@@ -1462,6 +1469,38 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     return SUPPY_OK;
 }
 
+// Variance stopping rule: buffers on first use; the previous iterate starts
+// as the current x whenever the state was reset.
+suppy_status ensure_variance(suppy_ctx* c) {
+    suppy_status s;
+    const size_t nB = (size_t)c->n * c->B;
+    if (!c->d_xprev) {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+        c->vgrid = (int)std::max<long long>(
+            1, std::min<long long>(2LL * sms, ((long long)nB + kWideThreads - 1) / kWideThreads));
+        if ((s = dalloc(c, &c->d_xprev, nB)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_vpart, (size_t)c->vgrid * c->B * 2)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_vticket, 1)) != SUPPY_OK) return s;
+        CK(cudaMemsetAsync(c->d_vticket, 0, sizeof(unsigned), c->stream));
+        c->xprev_stale = true;
+    }
+    if (c->xprev_stale) {
+        CK(cudaMemcpyAsync(c->d_xprev, c->d_x, sizeof(float) * nB, cudaMemcpyDeviceToDevice,
+                           c->stream));
+        c->xprev_stale = false;
+    }
+    return SUPPY_OK;
+}
+
+suppy_status enqueue_variance(suppy_ctx* c, const suppy_params* p) {
+    if (!(p->variance_tol > 0.0)) return SUPPY_OK;
+    CK(launch_variance(c->d_x, c->d_xprev, c->n, c->B, c->d_st, c->d_vpart, c->d_vticket,
+                       p->variance_tol, c->vgrid, c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
 // Enqueue `iters` superiorized iterations.  With graphs, one iteration is
 // captured once (per parameter set and buffer layout) and replayed; the
 // captured kernels read every evolving quantity (iterate, state, counters)
@@ -1469,10 +1508,12 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
 suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) {
     suppy_status s;
     const bool use_graph = p->use_graphs && !c->timing;
+    if (p->variance_tol > 0.0 && (s = ensure_variance(c)) != SUPPY_OK) return s;
     if (!use_graph) {
         for (int k = 0; k < iters; ++k) {
             if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
             if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
+            if ((s = enqueue_variance(c, p)) != SUPPY_OK) return s;
         }
         return SUPPY_OK;
     }
@@ -1505,6 +1546,7 @@ suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) 
         s = SUPPY_OK;
         if (c->obj != SUPPY_OBJ_NONE) s = enqueue_perturb(c, p, 0);
         if (s == SUPPY_OK) s = enqueue_sweep(c, p);
+        if (s == SUPPY_OK) s = enqueue_variance(c, p);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(c->stream, &g);
         c->stream = user;
@@ -1582,7 +1624,7 @@ suppy_status ctx_slot_load(suppy_ctx* c, int b, const float* l, const float* u) 
     CK(launch_load_column(c->d_slot_l, c->d_slot_u, c->d_perm, m, c->B, b, c->d_l, c->d_u,
                           c->stream));
     CK(launch_reset_column(c->d_x, c->d_lo, c->d_hi, c->n, c->B, b, c->box_len, c->d_st,
-                           c->stream));
+                           c->d_xprev, c->stream));
     note_launch(c, 2);
     return SUPPY_OK;
 }
@@ -1903,7 +1945,7 @@ suppy_status suppy_get_state(suppy_ctx* c, void* buf, size_t* len) {
     }
     if (*len < need) return fail(c, SUPPY_EINVAL, "checkpoint buffer too small");
     char* q = static_cast<char*>(buf);
-    CkptHeader h{kMagic, 1, c->n, c->m, c->B};
+    CkptHeader h{kMagic, 2, c->n, c->m, c->B};
     std::memcpy(q, &h, sizeof(h));
     CK(cudaMemcpyAsync(q + sizeof(h), c->d_x, sizeof(float) * (size_t)c->n * c->B,
                        cudaMemcpyDeviceToHost, c->stream));
@@ -1922,7 +1964,7 @@ suppy_status suppy_set_state(suppy_ctx* c, const void* buf, size_t len) {
     if (len < need) return fail(c, SUPPY_EINVAL, "checkpoint too short");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (h.magic != kMagic || h.version != 1 || h.n != c->n || h.m != c->m || h.B != c->B)
+    if (h.magic != kMagic || h.version != 2 || h.n != c->n || h.m != c->m || h.B != c->B)
         return fail(c, SUPPY_EINVAL, "checkpoint does not match this context");
     const char* q = static_cast<const char*>(buf);
     CK(cudaMemcpyAsync(c->d_x, q + sizeof(h), sizeof(float) * (size_t)c->n * c->B,
@@ -1930,6 +1972,7 @@ suppy_status suppy_set_state(suppy_ctx* c, const void* buf, size_t len) {
     const RhsState* rs = reinterpret_cast<const RhsState*>(q + sizeof(h) + sizeof(float) * (size_t)c->n * c->B);
     std::vector<RhsState> st(rs, rs + c->B);
     c->k_upper = 0;
+    c->xprev_stale = true;   // the variance rule continues from the restored iterate
     for (auto& r : st) c->k_upper = std::max(c->k_upper, r.k);
     CK(cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice,
                        c->stream));

@@ -34,6 +34,9 @@ struct RhsState {
     double p_prev, f_prev, f_cur;
     double p_acc;           // running monitored proximity within a block-iterative sweep
     double last_prox;
+    double w_s1, w_s2;      // variance rule: sums of the relative changes and their squares
+    int w_n;                // relative changes recorded
+    int pad1;
 };
 
 struct StopParams {
@@ -219,6 +222,11 @@ size_t wide_part_doubles(int grid, int B);   // partials the whole-GPU kernels n
 int choose_perturb_cluster(int n, int B);
 int fit_perturb_cluster(int want, int obj, int n, int H, int W);
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s);
+// Variance stopping rule after an iteration: relative change of every active
+// right-hand side against xprev (then xprev <- x), running sums in the state,
+// stop when the sample variance of the changes falls below tol.
+cudaError_t launch_variance(float* x, float* xprev, long long n, int B, RhsState* st,
+                            double* part, unsigned* ticket, double tol, int grid, cudaStream_t s);
 
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,
                                 int n, long long nnz, int* flags, cudaStream_t s);
@@ -246,7 +254,7 @@ cudaError_t launch_unpad_x(const float* x, long long n, int B, int B_out, float*
 cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
                                int b, float* l, float* u, cudaStream_t s);
 cudaError_t launch_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
-                                int b, int box_len, RhsState* st, cudaStream_t s);
+                                int b, int box_len, RhsState* st, float* xprev, cudaStream_t s);
 cudaError_t launch_set_stopped(RhsState* st, int b, cudaStream_t s);
 cudaError_t launch_extract_column(const float* x, long long n, int B, int b, float* out,
                                   cudaStream_t s);

@@ -836,6 +836,51 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_update(const PerturbArgs 
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
+// ------------------------------------------------ variance stopping rule ----
+// After an iteration: ||x - xprev||^2 and ||x||^2 per right-hand side
+// (compensated FP32 per thread, float-float per CTA, FP64 over the grid),
+// xprev <- x; the last CTA adds omega = ||x - xprev|| / ||x|| to the running
+// sums of the state and stops a right-hand side once the sample variance of
+// its omegas (k >= 2 of them) is below tol.
+__global__ void __launch_bounds__(kWideThreads) k_variance(float* x, float* xprev, long long n,
+                                                           int B, RhsState* st, double* part,
+                                                           unsigned* ticket, double tol) {
+    __shared__ FF sw[(kWideThreads / 32) * 2 * 32];
+    __shared__ double res[2 * kMaxRhs];
+    const long long nB = n * B;
+    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
+    const long long stride = (long long)gridDim.x * kWideThreads;
+    const int b = (int)(tid & (B - 1));
+    KSum kd, kx;
+    if (!st[b].stopped)
+        for (long long e = tid; e < nB; e += stride) {
+            const float v = x[e], d = v - xprev[e];
+            kd.add(d * d);
+            kx.add(v * v);
+            xprev[e] = v;
+        }
+    FF v[2] = {ff_of(kd), ff_of(kx)};
+    cta_partials<2>(v, B, sw, part);
+    if (!last_cta(ticket)) return;
+    grid_sums<2>(part, B, res);
+    if (threadIdx.x < B) {
+        RhsState& s = st[threadIdx.x];
+        if (!s.stopped) {
+            const double D = res[2 * threadIdx.x], X = res[2 * threadIdx.x + 1];
+            const double w = X > 0.0 ? sqrt(D / X) : 0.0;
+            s.w_n += 1;
+            s.w_s1 += w;
+            s.w_s2 += w * w;
+            if (s.w_n >= 2) {
+                const double nn = (double)s.w_n;
+                const double var = (s.w_s2 - s.w_s1 * s.w_s1 / nn) / (nn - 1.0);
+                if (var < tol) s.stopped = 1;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // Objective partials: CTA c writes f-partials of every right-hand side.
 __global__ void __launch_bounds__(256) k_objective(const ObjArgs a) {
     __shared__ double sw[8];
@@ -928,6 +973,12 @@ cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
 }
 
 size_t wide_part_doubles(int grid, int B) { return (size_t)grid * B * kWideTrials; }
+
+cudaError_t launch_variance(float* x, float* xprev, long long n, int B, RhsState* st,
+                            double* part, unsigned* ticket, double tol, int grid, cudaStream_t s) {
+    k_variance<<<grid, kWideThreads, 0, s>>>(x, xprev, n, B, st, part, ticket, tol);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, int cluster, cudaStream_t s) {
     if (a.B != 1 && (a.B & (a.B - 1))) return cudaErrorInvalidValue;

@@ -341,11 +341,13 @@ __global__ void k_load_column(const float* l_in, const float* u_in, const int* p
 
 // x[:, b] <- box(0), and a fresh iteration state for right-hand side b.
 __global__ void k_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
-                               int b, int box_len, RhsState* st) {
+                               int b, int box_len, RhsState* st, float* xprev) {
     for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
         const long long bj = (box_len == 1) ? 0 : j;
-        x[j * B + b] = clampf(0.f, lo[bj], hi[bj]);
+        const float v = clampf(0.f, lo[bj], hi[bj]);
+        x[j * B + b] = v;
+        if (xprev) xprev[j * B + b] = v;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         RhsState r = {};
@@ -409,8 +411,8 @@ cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* 
 }
 
 cudaError_t launch_reset_column(float* x, const float* lo, const float* hi, long long n, int B,
-                                int b, int box_len, RhsState* st, cudaStream_t s) {
-    k_reset_column<<<grid_for(n), 256, 0, s>>>(x, lo, hi, n, B, b, box_len, st);
+                                int b, int box_len, RhsState* st, float* xprev, cudaStream_t s) {
+    k_reset_column<<<grid_for(n), 256, 0, s>>>(x, lo, hi, n, B, b, box_len, st, xprev);
     return cudaGetLastError();
 }
 

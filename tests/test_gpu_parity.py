@@ -639,3 +639,27 @@ def test_norm_perturbations_match_oracle(kind, path):
     S, l, u, lo, hi = O.from_problem(prob, O.DROP)
     r = O.run(S, O.DROP, l, u, lo, hi, ob, O.Params(**R))
     assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3
+
+
+# ------------------------------------------------ variance stopping rule ----
+
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_variance_stopping_rule_stops_with_the_oracle(graphs):
+    """The variance rule of the CT study (threshold 0.01) on the tiny CT
+    workload with TV: the run stops at the oracle's iteration (within one,
+    for FP32 norms near the threshold) for every right-hand side."""
+    prob = small_ct(nrhs=2)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO)
+    P = dict(gamma=0.5, alpha=0.99, n_red=1, max_sweeps=400)
+    st = ctx.suppy_run(_params(variance_tol=1e-2, check_every=7, use_graphs=graphs, **P))
+    S, l, u, lo, hi = O.from_problem(prob)
+    ob = oracle_objective(prob, O.OBJ_TV_ISO)
+    xg = ctx.suppy_get_x()
+    for b in range(2):
+        r = O.run(S, O.CIMMINO, O.rhs(l, b), O.rhs(u, b), lo, hi, ob,
+                  O.Params(variance_tol=1e-2, **P))
+        assert r.sweeps < 400
+        assert st[b]["stopped"] == 1
+        assert abs(st[b]["sweeps"] - r.sweeps) <= 1
+        if st[b]["sweeps"] == r.sweeps:
+            assert rel_l2(xg[:, b], r.x) <= 1e-3
