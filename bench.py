@@ -615,18 +615,19 @@ def profile_case(case: int, steps: int) -> int:
     """A short run for ncu.  Cases 1 / 2: CT 384x384 (A ~0.4 GB, above L2; the
     device holds about 1 GB) with the one- / two-pass sweep.  Case 3: the CT
     512x512 workload with the sweep and launch shapes bench.py uses (two
-    passes, shapes tuned at create); the profiled iterations run inside the
-    NVTX range "profile", so that
+    passes, shapes tuned at create); case 4: the same with the one-pass sweep.
+    The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches."""
     import torch
     import synth
     from paper_2606_27086_gb300 import build as pkbuild
     pkbuild.build()
     import paper_2606_27086_gb300 as pk
-    if case == 3:
+    if case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
-                              strategy=pk.STRATEGY_TWO_PASS)
+                              strategy=pk.STRATEGY_TWO_PASS if case == 3 else
+                              pk.STRATEGY_ONE_PASS)
     else:
         prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
                                 seed_noise=202)
@@ -658,10 +659,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
-                         "bins) with sweep strategy 1 (one pass) or 2 (two passes), or 3: the "
-                         "CT 512x512 workload with the tuned launch shapes")
+                         "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
+                         "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
+                         "pass")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6)
