@@ -234,6 +234,12 @@ suppy_status suppy_set_stream(suppy_ctx* ctx, void* stream);
  * histories and stop flags, keeps x. */
 suppy_status suppy_set_bounds(suppy_ctx* ctx, const float* l, const float* u, int32_t on_device);
 
+/* Replace the slab bounds like suppy_set_bounds, but keep x and the iteration
+ * state (exponent l, counters, histories, stop flags): Algorithm 1 continues
+ * warm on the new bounds -- e.g. successive measurements of a slowly changing
+ * object.  A rejected call (SUPPY_EINVAL) leaves the old bounds. */
+suppy_status suppy_update_bounds(suppy_ctx* ctx, const float* l, const float* u, int32_t on_device);
+
 /* Set x (n x B) and project it onto the box.  Resets iteration counters,
  * exponents, histories and stop flags. */
 suppy_status suppy_set_x(suppy_ctx* ctx, const float* x, int32_t on_device);

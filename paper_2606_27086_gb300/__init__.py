@@ -29,7 +29,8 @@ STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS = 0, 1, 2
 
 EXPORTED = [
     "suppy_params_default", "suppy_create", "suppy_destroy", "suppy_set_stream",
-    "suppy_set_bounds", "suppy_set_x", "suppy_get_x", "suppy_perturb", "suppy_sweep",
+    "suppy_set_bounds", "suppy_update_bounds", "suppy_set_x", "suppy_get_x", "suppy_perturb",
+    "suppy_sweep",
     "suppy_proximity", "suppy_objective", "suppy_run", "suppy_history", "suppy_get_state",
     "suppy_set_state", "suppy_info_get", "suppy_timing_enable", "suppy_kernel_time",
     "suppy_launch_count", "suppy_last_error", "suppy_version", "suppy_sweep_static",
@@ -121,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_destroy": (None, [P]),
         "suppy_set_stream": (ctypes.c_int, [P, P]),
         "suppy_set_bounds": (ctypes.c_int, [P, P, P, I32]),
+        "suppy_update_bounds": (ctypes.c_int, [P, P, P, I32]),
         "suppy_set_x": (ctypes.c_int, [P, P, I32]),
         "suppy_get_x": (ctypes.c_int, [P, P, I32]),
         "suppy_perturb": (ctypes.c_int, [P, ctypes.POINTER(suppy_params), P]),
@@ -294,6 +296,11 @@ class Context:
         lp, dl, k1 = _ptr(l)
         up, du, k2 = _ptr(u)
         _check(self._lib.suppy_set_bounds(self.ctx, lp, up, dl), self.ctx)
+
+    def suppy_update_bounds(self, l, u):
+        lp, dl, k1 = _ptr(l)
+        up, du, k2 = _ptr(u)
+        _check(self._lib.suppy_update_bounds(self.ctx, lp, up, dl), self.ctx)
 
     def suppy_set_x(self, x):
         xp, d, k = _ptr(x)

@@ -250,22 +250,13 @@ void partition(const std::vector<long long>& pref, int r0, int r1, int ng, int* 
     out[ng] = r1;
 }
 
-void reset_state_host(suppy_ctx* c, std::vector<RhsState>& st) {
-    st.assign(c->B, RhsState{});
-    for (int b = 0; b < c->B; ++b) {
-        st[b].last_restart_k = -1;
-        st[b].stopped = (b >= c->B_user) ? 1 : 0;
-    }
-}
-
+// Fresh iteration state of every right-hand side (padding ones stopped),
+// enqueued on the context's stream.
 suppy_status reset_state(suppy_ctx* c) {
     c->k_upper = 0;
     c->xprev_stale = true;
-    std::vector<RhsState> st;
-    reset_state_host(c, st);
-    CK(cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(launch_reset_states(c->d_st, c->B, c->B_user, c->stream));
+    note_launch(c);
     return SUPPY_OK;
 }
 
@@ -1729,7 +1720,12 @@ suppy_status suppy_set_stream(suppy_ctx* c, void* stream) {
     return SUPPY_OK;
 }
 
-suppy_status suppy_set_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
+}  // extern "C"
+
+namespace {
+
+// New slab bounds, validated; the old ones stay when the call is rejected.
+suppy_status load_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!l || !u) return fail(c, SUPPY_EINVAL, "NULL bounds");
     const size_t mB = (size_t)c->m * c->B_user;
@@ -1745,21 +1741,39 @@ suppy_status suppy_set_bounds(suppy_ctx* c, const float* l, const float* u, int3
         s_l = c->d_stage_l;
         s_u = c->d_stage_u;
     }
+    // validation and the zero-row check read the new bounds in the caller's
+    // row order; the permutation into the device layout is skipped on the
+    // device when either failed, so a rejected call leaves the old bounds;
+    // one synchronization reads both results
     if (!c->d_flags && (s = dalloc(c, &c->d_flags, 4)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(int), c->stream));
     CK(launch_validate_vec(s_l, (long long)mB, 1, c->d_flags, 1, c->stream));
     CK(launch_validate_vec(s_u, (long long)mB, 1, c->d_flags, 2, c->stream));
     CK(launch_validate_pair(s_l, s_u, (long long)mB, c->d_flags, 4, c->stream));
+    CK(launch_zero_row_check_src(c->d_rho, s_l, s_u, c->d_perm, c->m, c->B_user, c->d_flags + 1,
+                                 c->stream));
+    CK(launch_permute_bounds(s_l, s_u, c->d_perm, c->m, c->B_user, c->B, c->d_l, c->d_u, c->stream,
+                             c->d_flags, 2));
+    note_launch(c, 5);
     int hf[2] = {0, 0};
-    if ((s = read_flags(c, c->d_flags, hf, 1)) != SUPPY_OK) return s;
-    note_launch(c, 3);
+    if ((s = read_flags(c, c->d_flags, hf, 2)) != SUPPY_OK) return s;
     if (hf[0]) return fail(c, SUPPY_EINVAL, "bounds need l <= u and no NaN");
-    CK(launch_permute_bounds(s_l, s_u, c->d_perm, c->m, c->B_user, c->B, c->d_l, c->d_u, c->stream));
-    CK(launch_zero_row_check(c->d_rho, c->d_l, c->d_u, c->m, c->B, c->d_flags + 1, c->stream));
-    note_launch(c, 2);
-    if ((s = read_flags(c, c->d_flags + 1, hf + 1, 1)) != SUPPY_OK) return s;
     if (hf[1]) return fail(c, SUPPY_EINVAL, "a zero row needs l <= 0 <= u");
+    return SUPPY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+suppy_status suppy_set_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
+    suppy_status s = load_bounds(c, l, u, on_device);
+    if (s != SUPPY_OK) return s;
     return reset_state(c);
+}
+
+suppy_status suppy_update_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
+    return load_bounds(c, l, u, on_device);
 }
 
 suppy_status suppy_set_x(suppy_ctx* c, const float* x, int32_t on_device) {
@@ -1888,11 +1902,20 @@ suppy_status suppy_run(suppy_ctx* c, const suppy_params* p, suppy_stats* out) {
             if (all) break;
         }
     }
-    if ((s = check_device_error(c)) != SUPPY_OK) return s;
-    if (out) {
+    // the error word of the streaming passes and the statistics in one
+    // synchronization
+    int herr = 0;
+    if (c->d_err)
+        CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    if (out)
         CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
                            c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (herr) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
+    }
+    if (out) {
         for (int b = 0; b < c->B_user; ++b) {
             out[b].sweeps = st[b].k;
             out[b].accepted = st[b].accepted_total;

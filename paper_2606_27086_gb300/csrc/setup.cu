@@ -134,9 +134,38 @@ __global__ void k_zero_row_check(const double* rho, const float* l, const float*
     }
 }
 
+// Zero rows (||a_i|| = 0, device row i) against source-order bounds: the
+// slab must contain 0.
+__global__ void k_zero_row_check_src(const double* rho, const float* l_in, const float* u_in,
+                                     const int* perm, int m, int B_in, int* flags) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        if (rho[i] > 0.0) continue;
+        const int src = perm ? perm[i] : i;
+        for (int b = 0; b < B_in; ++b) {
+            const size_t o = (size_t)src * B_in + b;
+            if (!(l_in[o] <= 0.f && u_in[o] >= 0.f)) atomicOr(flags, 1);
+        }
+    }
+}
+
+__global__ void k_reset_states(RhsState* st, int B, int B_user) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) {
+        RhsState r = {};
+        r.last_restart_k = -1;
+        r.stopped = (b >= B_user) ? 1 : 0;
+        st[b] = r;
+    }
+}
+
 // l[i*B + b] = l_in[perm[i]*B_in + b] for b < B_in; padding RHS get (-inf, inf).
+// With `skip` set, nothing is written when any of skip[0..nskip) is nonzero
+// (the bounds failed validation earlier on the same stream).
 __global__ void k_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
-                                 int B_in, int B, float* l, float* u) {
+                                 int B_in, int B, float* l, float* u, const int* skip,
+                                 int nskip) {
+    for (int k = 0; skip && k < nskip; ++k)
+        if (skip[k]) return;
     const long long tot = (long long)m * B;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x) {
@@ -310,9 +339,22 @@ cudaError_t launch_zero_row_check(const double* rho, const float* l, const float
 }
 
 cudaError_t launch_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
-                                  int B_in, int B, float* l, float* u, cudaStream_t s) {
+                                  int B_in, int B, float* l, float* u, cudaStream_t s,
+                                  const int* skip, int nskip) {
     k_permute_bounds<<<grid_for((long long)m * B), 256, 0, s>>>(l_in, u_in, perm, m, B_in, B, l,
-                                                                u);
+                                                                u, skip, nskip);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_row_check_src(const double* rho, const float* l_in, const float* u_in,
+                                      const int* perm, int m, int B_in, int* flags,
+                                      cudaStream_t s) {
+    k_zero_row_check_src<<<grid_for(m), 256, 0, s>>>(rho, l_in, u_in, perm, m, B_in, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_states(RhsState* st, int B, int B_user, cudaStream_t s) {
+    k_reset_states<<<1, 64, 0, s>>>(st, B, B_user);
     return cudaGetLastError();
 }
 

@@ -663,3 +663,36 @@ def test_variance_stopping_rule_stops_with_the_oracle(graphs):
         assert abs(st[b]["sweeps"] - r.sweeps) <= 1
         if st[b]["sweeps"] == r.sweeps:
             assert rel_l2(xg[:, b], r.x) <= 1e-3
+
+
+def test_update_bounds_keeps_the_iteration_state():
+    """suppy_update_bounds swaps the slabs and Algorithm 1 continues (same
+    exponent l, counters and history) -- the oracle's loop with the bounds
+    replaced between iterations; suppy_set_bounds resets the state."""
+    prob = small_ct(nrhs=2)
+    l0, u0 = O.rhs(prob.l, 0), O.rhs(prob.u, 0)
+    l1, u1 = O.rhs(prob.l, 1), O.rhs(prob.u, 1)
+    single = synth.ct_problem()
+    ctx = pk.from_problem(single, obj=pk.SUPPY_OBJ_TV_ISO)
+    ctx.suppy_set_bounds(l0.astype(np.float32), u0.astype(np.float32))
+    P = dict(gamma=0.5, alpha=0.99, n_red=1)
+    ctx.suppy_run(_params(max_sweeps=12, **P))
+    ctx.suppy_update_bounds(l1.astype(np.float32), u1.astype(np.float32))
+    st = ctx.suppy_run(_params(max_sweeps=8, **P))[0]
+    assert st["sweeps"] == 20
+    S, _, _, lo, hi = O.from_problem(single)
+    ob = oracle_objective(single, O.OBJ_TV_ISO)
+    op = O.Params(**P)
+    ps = O.PertState()
+    x = np.zeros(single.A.n)
+    for k in range(20):
+        l, u = (l0, u0) if k < 12 else (l1, u1)
+        x, _, _ = O.perturbation_phase(ob, x, ps, op)
+        x, p = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+    assert st["ell"] == ps.ell
+    assert rel_l2(ctx.suppy_get_x(), x) <= 1e-3
+    ph, _ = ctx.suppy_history()
+    assert len(ph) == 20 and rel(ph[-1], p) <= 1e-3
+    ctx.suppy_set_bounds(l1.astype(np.float32), u1.astype(np.float32))
+    st = ctx.suppy_run(_params(max_sweeps=0, **P))[0]
+    assert st["sweeps"] == 0 and st["ell"] == 0
