@@ -16,6 +16,8 @@ constrained physical problems with SupPy"):
 * relaxation -- Eq. (3), x + lambda (P x - x);
 * simultaneous (Cimmino-type) projection -- Sec. 2.1.1, the relaxed weighted
   average x + lambda sum_i w_i (P_i x - x) with w_i > 0, sum w_i = 1;
+* extrapolated Landweber (EL) and Landweber with error-minimising relaxation
+  (EMR) -- appendix Table of used methods, in slab form (Q25);
 * DROP (diagonally relaxed orthogonal projections) -- appendix Table of used
   methods, x <- x - Z A^T M (A x - b) with Z = diag(1/nnz(A_{:,j})), taken in
   slab form with the step of Censor et al. (Q22): x <- box(x + lambda Z sum_i
@@ -47,8 +49,13 @@ the normalised direction are the same for ||x||_2); Q22 DROP in slab form: the a
 sum w_i = 1 and no 1/||a_i||^2, which would scale the step by 1/m'; the step
 taken is the one of the cited DROP method (unit weights, each row's residual
 divided by ||a_i||^2, Z = diag(1/s_j) with s_j the nonzeros of column j over
-the kept rows), whose fixed points are those of the Cimmino step.  Parity of the whole superiorized run against printed values is
-unpinned: the paper prints no iterates for this path.
+the kept rows), whose fixed points are those of the Cimmino step; Q25 EL / EMR
+in slab form: the residual A x - b becomes A x - clamp(A x, l, u), weights
+w_i = 1/m' (D = diag(w_i/||a_i||^2), M = diag(w_i)), the step is followed by
+the box and scaled by the relaxation lambda; a zero correction leaves x.
+
+Parity of the whole superiorized run against printed values is unpinned: the
+paper prints no iterates for this path.
 """
 from __future__ import annotations
 
@@ -58,7 +65,7 @@ import numpy as np
 import scipy.sparse as sp
 
 OBJ_NONE, OBJ_TV_ISO, OBJ_TV_ANISO, OBJ_LINEAR, OBJ_L1, OBJ_L2 = 0, 1, 2, 3, 4, 5
-CIMMINO, BIP, DROP = 0, 1, 2
+CIMMINO, BIP, DROP, EL, EMR = 0, 1, 2, 3, 4
 
 
 # ------------------------------------------------------------ projections --
@@ -188,6 +195,45 @@ def drop_step(S: Setup, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
     return box_project(x + lam * S.z * (S.A.T @ coef), lo, hi), p_in
 
 
+def el_step(S: Setup, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
+            x: np.ndarray) -> tuple[np.ndarray, float]:
+    """Extrapolated Landweber (appendix Table of used methods; Q25):
+    x <- box(x - lambda t A^T D r), r = A x - clamp(A x, l, u),
+    D = diag(w_i/||a_i||^2), t = r^T D r / ||A^T D r||^2."""
+    r = S.A @ x
+    res = r - np.clip(r, l, u)
+    k = S.keep
+    Dr = np.zeros_like(r)
+    Dr[k] = S.w_prox[k] * res[k] / S.rho[k]
+    g = S.A.T @ Dr
+    p_in = 0.5 * float(np.sum(S.w_prox[k] * res[k] ** 2 / S.rho[k]))
+    gg = float(g @ g)
+    if gg == 0.0:
+        return box_project(x, lo, hi), p_in
+    t = float(res @ Dr) / gg
+    return box_project(x - lam * t * g, lo, hi), p_in
+
+
+def emr_step(S: Setup, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
+             x: np.ndarray) -> tuple[np.ndarray, float]:
+    """Landweber with error-minimising relaxation (appendix Table of used
+    methods; Q25): x <- box(x - lambda t A^T M r), M = diag(w_i),
+    t = ||A^T M r||^2 / ||M^(1/2) A A^T M r||^2."""
+    r = S.A @ x
+    res = r - np.clip(r, l, u)
+    k = S.keep
+    Mr = np.zeros_like(r)
+    Mr[k] = S.w_prox[k] * res[k]
+    g = S.A.T @ Mr
+    p_in = 0.5 * float(np.sum(S.w_prox[k] * res[k] ** 2 / S.rho[k]))
+    q = S.A @ g
+    den = float(np.sum(S.w_prox[k] * q[k] ** 2))
+    if den == 0.0:
+        return box_project(x, lo, hi), p_in
+    t = float(g @ g) / den
+    return box_project(x - lam * t * g, lo, hi), p_in
+
+
 def sweep(S: Setup, mode: int, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
           x: np.ndarray) -> tuple[np.ndarray, float]:
     """One application of the feasibility-seeking operator T.
@@ -202,6 +248,10 @@ def sweep(S: Setup, mode: int, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
         return simultaneous_step(S.A, S.rho, S.keep, S.w_sweep, S.w_prox, l, u, lam, lo, hi, x)
     if mode == DROP:
         return drop_step(S, l, u, lam, lo, hi, x)
+    if mode == EL:
+        return el_step(S, l, u, lam, lo, hi, x)
+    if mode == EMR:
+        return emr_step(S, l, u, lam, lo, hi, x)
     p_tot = 0.0
     for rows, At in zip(S.blocks, S.sub):
         x, p = simultaneous_step(At, S.rho[rows], S.keep[rows], S.w_sweep[rows],

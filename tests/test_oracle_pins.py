@@ -581,3 +581,108 @@ def test_variance_rule_stops_at_the_first_iterate_below_the_threshold():
             break
     assert r.sweeps == k < 400
     np.testing.assert_array_equal(r.x, x)
+
+
+# ------------------------------------------------------------ EL / EMR ----
+
+def _orthogonal_rows(seed, m=4, n=9, norm=1.7):
+    """Rows with disjoint supports scaled to one norm: pairwise orthogonal."""
+    rng = np.random.default_rng(seed)
+    A = np.zeros((m, n))
+    cols = np.array_split(rng.permutation(n), m)
+    for i, c in enumerate(cols):
+        v = rng.uniform(0.5, 2.0, size=len(c))
+        A[i, c] = norm * v / np.linalg.norm(v)
+    return A
+
+
+@pytest.mark.parametrize("mode", [O.EL, O.EMR])
+def test_extrapolated_steps_project_exactly_on_orthogonal_equal_norm_rows(mode):
+    """Orthogonal rows of equal norm: the simultaneous direction is the sum of
+    the single projections scaled by w, and both EL's t (1/w) and EMR's exact
+    line search undo that scaling -- one step lands on the intersection of
+    the slabs, the nearest feasible point (the Cimmino step moves 1/m of the
+    way)."""
+    A = _orthogonal_rows(81)
+    rng = np.random.default_rng(82)
+    x = rng.uniform(-1, 1, size=A.shape[1])
+    l = A @ x + rng.uniform(0.3, 1.0, size=4) * rng.choice([-1, 1], size=4)
+    u = l + 0.2
+    S = O.setup(sp.csr_matrix(A), l, u)
+    y, _ = O.sweep(S, mode, l, u, 1.0, -np.inf, np.inf, x)
+    want = x.copy()
+    for i in range(4):
+        r = A[i] @ x
+        want += (np.clip(r, l[i], u[i]) - r) / (A[i] @ A[i]) * A[i]
+    np.testing.assert_allclose(y, want, atol=1e-12)
+    c, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, -np.inf, np.inf, x)
+    np.testing.assert_allclose(c, x + (want - x) / 4, atol=1e-12)
+
+
+def test_emr_step_is_the_exact_line_search_of_the_weighted_residual():
+    """EMR's t minimises phi(t) = sum_i w_i (r_i + t q_i)^2 along the step for an
+    equality system (l = u): checked against a dense scan of t."""
+    rng = np.random.default_rng(83)
+    A = rng.uniform(0, 1, size=(15, 6)) * (rng.uniform(size=(15, 6)) < 0.8)
+    A = A[np.sum(A * A, axis=1) > 0]
+    b = A @ rng.uniform(0, 1, 6) + 0.1 * rng.standard_normal(A.shape[0])
+    S = O.setup(sp.csr_matrix(A), b, b)
+    x = rng.uniform(0, 1, 6)
+    y, _ = O.sweep(S, O.EMR, b, b, 1.0, -np.inf, np.inf, x)
+    w = 1.0 / A.shape[0]
+    g = A.T @ (w * (A @ x - b))
+    phi = lambda t: np.sum(w * (A @ (x - t * g) - b) ** 2)
+    ts = np.linspace(0, 50, 200001)
+    vals = np.array([phi(t) for t in ts[::100]])
+    t_best = ts[::100][np.argmin(vals)]
+    t_emr = np.linalg.norm(x - y) / np.linalg.norm(g)
+    assert abs(t_emr - t_best) <= 0.03 * t_best
+    assert phi(t_emr) <= vals.min() + 1e-12
+
+
+def _consistent_slabs(seed, m=14, n=8):
+    rng = np.random.default_rng(seed)
+    A = rng.uniform(0, 1, size=(m, n)) * (rng.uniform(size=(m, n)) < 0.7)
+    A = A[np.sum(A * A, axis=1) > 0]
+    xt = rng.uniform(0, 1, size=n)
+    b = A @ xt
+    return sp.csr_matrix(A), b * 0.97, b * 1.03, xt
+
+
+def test_el_is_fejer_monotone_for_consistent_slabs():
+    """EL extrapolates a firmly nonexpansive simultaneous step (t >= 1 is the
+    extrapolation of Cegielski's method), so on a consistent system every
+    feasible point z gets no farther away: ||x^(k+1) - z|| <= ||x^k - z||."""
+    A, l, u, xt = _consistent_slabs(85)
+    S = O.setup(A, l, u)
+    x = np.full(A.shape[1], 2.0)
+    prev = np.linalg.norm(x - xt)
+    for _ in range(300):
+        x, _ = O.sweep(S, O.EL, l, u, 1.0, -np.inf, np.inf, x)
+        cur = np.linalg.norm(x - xt)
+        assert cur <= prev * (1 + 1e-12) + 1e-15
+        prev = cur
+    assert O.proximity(S, l, u, x) < 1e-8
+
+
+def test_emr_weighted_residual_never_increases_on_consistent_slabs():
+    """EMR's t is the exact minimiser of the weighted residual along its
+    direction, so sum_i w_i d_i^2 never increases (up to rounding) and the
+    iterates become feasible."""
+    A, l, u, _ = _consistent_slabs(86)
+    S = O.setup(A, l, u)
+    Ad = A.toarray()
+
+    def F(y):
+        r = Ad @ y
+        d = np.clip(r, l, u) - r
+        return np.sum(d ** 2)
+
+    x = np.full(A.shape[1], 2.0)
+    prev = F(x)
+    for _ in range(300):
+        x, _ = O.sweep(S, O.EMR, l, u, 1.0, -np.inf, np.inf, x)
+        cur = F(x)
+        assert cur <= prev * (1 + 1e-9) + 1e-24
+        prev = cur
+    assert O.proximity(S, l, u, x) < 1e-8
