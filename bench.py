@@ -312,6 +312,10 @@ def variants(pk, K, W):
             strategy=pk.STRATEGY_TWO_PASS, tma=-1)
     run_one("ct512_cimmino_tv_f32_onepass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
             params=SUP, strategy=pk.STRATEGY_ONE_PASS, tma=-1)
+    run_one("ct512_emr_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EMR,
+            params=SUP, tune=1)
+    run_one("ct512_el_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EL,
+            params=SUP, tune=1)
     run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
             params=SUP, tune=1)
     run_one("ct512_cimmino_tv_bf16_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,

@@ -82,7 +82,20 @@ typedef enum { SUPPY_F32 = 0, SUPPY_BF16 = 1, SUPPY_F16 = 2 } suppy_dtype;
  *   row weights and Z = diag(1/s_j), s_j the stored nonzeros of column j in the
  *   rows with ||a_i|| > 0 (0 for an empty column).  The monitored proximity
  *   keeps the weights 1/m'. */
-typedef enum { SUPPY_CIMMINO = 0, SUPPY_BIP = 1, SUPPY_DROP = 2 } suppy_mode;
+/* SUPPY_EL: extrapolated Landweber (appendix table of used methods), in slab
+ *   form: x <- box(x + lambda t A^T D d), d_i = clamp(r_i, l_i, u_i) - r_i,
+ *   D = diag(w_i/||a_i||^2), w_i = 1/m', t = d^T D d / ||A^T D d||^2.
+ * SUPPY_EMR: Landweber with error-minimising relaxation (same table), slab
+ *   form: x <- box(x + lambda t A^T M d), M = diag(w_i),
+ *   t = ||A^T M d||^2 / ||M^(1/2) A A^T M d||^2 (one more pass over A).
+ *   Both take the two-pass sweep; a zero correction leaves x unchanged. */
+typedef enum {
+    SUPPY_CIMMINO = 0,
+    SUPPY_BIP = 1,
+    SUPPY_DROP = 2,
+    SUPPY_EL = 3,
+    SUPPY_EMR = 4
+} suppy_mode;
 
 /* Objective of the perturbation phase. */
 typedef enum {

@@ -22,7 +22,7 @@ LIB_PATH = os.environ.get("SUPPY_LIBRARY") or os.path.join(_HERE, "libsuppy_gb30
 
 SUPPY_OK, SUPPY_EINVAL, SUPPY_ENOMEM, SUPPY_ECUDA, SUPPY_ETIMEOUT, SUPPY_ESTATE = 0, -1, -2, -3, -4, -5
 SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2
-SUPPY_CIMMINO, SUPPY_BIP, SUPPY_DROP = 0, 1, 2
+SUPPY_CIMMINO, SUPPY_BIP, SUPPY_DROP, SUPPY_EL, SUPPY_EMR = 0, 1, 2, 3, 4
 SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
 SUPPY_OBJ_L1, SUPPY_OBJ_L2 = 4, 5
 STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS = 0, 1, 2

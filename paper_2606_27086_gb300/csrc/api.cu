@@ -63,6 +63,15 @@ struct suppy_ctx {
     float* d_lo = nullptr;
     float* d_hi = nullptr;
     float* d_zc = nullptr;          // DROP column scaling (null otherwise)
+    // EL / EMR: ||a_i||^2 as FP32, zero bounds, q-pass partials, step sizes
+    float* d_rhof = nullptr;
+    float* d_zero = nullptr;
+    double* d_qq = nullptr;
+    double* d_xpart = nullptr;
+    unsigned* d_xticket = nullptr;
+    double* d_tstep = nullptr;
+    int xgrid = 0;
+    int qq_cap = 0;                 // CTAs the q-pass partials hold
     // variance stopping rule: previous iterate, partials, ticket
     float* d_xprev = nullptr;
     bool xprev_stale = true;
@@ -342,6 +351,8 @@ SweepArgs row_args(suppy_ctx* c, int t, float lam) {
     a.x = c->d_x;
     a.delta = c->d_delta;
     a.coef = nullptr;
+    a.coef_mul = nullptr;
+    a.prox_mul = nullptr;
     a.part = c->d_part + c->seg_part_off[t];
     a.pp = c->d_pp;
     a.st = c->d_st;
@@ -390,12 +401,118 @@ suppy_status launch_rows(suppy_ctx* c, const SweepArgs& a, int scat, int t) {
     return SUPPY_OK;
 }
 
+// Buffers of the EL / EMR step: ||a_i||^2 as FP32 and zero bounds (EMR's
+// q-pass), the q-pass partials, the step's partials, ticket and step sizes.
+suppy_status prepare_ext(suppy_ctx* c) {
+    suppy_status s;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const long long nB = (long long)c->n * c->B;
+    c->xgrid = (int)std::max<long long>(1, std::min<long long>(2LL * sms, (nB + 255) / 256));
+    if ((s = dalloc(c, &c->d_xpart, (size_t)c->xgrid * c->B)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_xticket, 1)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_tstep, (size_t)c->B)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_xticket, 0, sizeof(unsigned), c->stream));
+    if (c->mode == SUPPY_EMR) {
+        // q-pass partials: one per CTA of any row-pass launch (at most 16 per SM)
+        const int g = 16 * sms;
+        c->qq_cap = g;
+        if ((s = dalloc(c, &c->d_rhof, (size_t)std::max(c->m, 1))) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_zero, (size_t)std::max(c->m, 1) * c->B)) != SUPPY_OK) return s;
+        if ((s = dalloc(c, &c->d_qq, (size_t)g * c->B)) != SUPPY_OK) return s;
+        CK(cudaMemsetAsync(c->d_zero, 0, sizeof(float) * (size_t)std::max(c->m, 1) * c->B,
+                           c->stream));
+        if (c->m) CK(launch_to_float(c->d_rho, c->m, c->d_rhof, c->stream));
+        note_launch(c);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+// EL / EMR after the column pass of block t (delta holds A^T(W d)): for EMR
+// the row pass over q = A delta (zero bounds, so d = -q; the proximity
+// machinery sums w_i q_i^2 with the multiplier ||a_i||^2), then the step.
+suppy_status enqueue_ext_step(suppy_ctx* c, const suppy_params* p, int t, int npp) {
+    int nqq = 0;
+    if (c->mode == SUPPY_EMR) {
+        // the launch writes one partial per CTA: check the buffer first
+        nqq = c->use_tma ? c->seg_tgrid[t] : c->seg_grid[t];
+        if (nqq > c->qq_cap) return fail(c, SUPPY_ECUDA, "q-pass launch exceeds its partials");
+        if (c->use_tma) {
+            StreamArgs q;
+            std::memset(&q, 0, sizeof(q));
+            q.info = c->d_rinfo;
+            q.idx = c->d_col;
+            q.val = c->d_val;
+            q.cta_items = c->d_tpart + c->seg_tpart_off[t];
+            q.tile = c->tile;
+            q.stages = c->stages;
+            q.err = c->d_err;
+            q.l = c->d_zero;
+            q.u = c->d_zero;
+            q.wr = c->d_wr;
+            q.x = c->d_delta;
+            q.prox_mul = c->d_rhof;
+            q.pp = c->d_qq;
+            q.st = c->d_st;
+            q.lam = 0.f;
+            q.check_stop = 1;
+            Timed tm{c, 0};
+            CK(tm.begin());
+            CK(launch_rows_tma(q, c->dt, c->tG, 0, c->seg_tgrid[t], c->stream));
+            CK(tm.end());
+        } else {
+            SweepArgs q = row_args(c, t, 0.f);
+            q.l = c->d_zero;
+            q.u = c->d_zero;
+            q.x = c->d_delta;
+            q.prox_mul = c->d_rhof;
+            q.pp = c->d_qq;
+            Timed tm{c, 0};
+            CK(tm.begin());
+            if (c->B == 1) CK(launch_sweep(q, c->dt, c->G, c->maxe, 0, c->seg_grid[t], c->stream));
+            else CK(launch_sweep_batched(q, c->dt, 0, c->seg_grid[t], c->stream));
+            CK(tm.end());
+        }
+        note_launch(c);
+    }
+    ExtArgs e;
+    e.x = c->d_x;
+    e.delta = c->d_delta;
+    e.lo = c->d_lo;
+    e.hi = c->d_hi;
+    e.box_len = c->box_len;
+    e.n = c->n;
+    e.B = c->B;
+    e.st = c->d_st;
+    e.method = (int)c->mode;
+    e.pp = c->d_pp;
+    e.npp = npp;
+    e.qq = c->d_qq;
+    e.nqq = nqq;
+    e.part = c->d_xpart;
+    e.ticket = c->d_xticket;
+    e.tstep = c->d_tstep;
+    e.lam = (float)p->lambda;
+    Timed tm{c, 1};
+    CK(tm.begin());
+    CK(launch_ext_step(e, c->xgrid, c->stream));
+    CK(tm.end());
+    note_launch(c, 2);
+    return SUPPY_OK;
+}
+
 // One application of T.
 suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     const StopParams sp = stop_params(c, p);
     suppy_status s;
+    // EL / EMR: the row pass writes unrelaxed coefficients, the column pass
+    // accumulates A^T(.) into delta, and the extrapolated step applies it
+    const bool ext = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
+    const float lam_row = ext ? 1.f : (float)p->lambda;
     for (int t = 0; t < c->nseg; ++t) {
-        SweepArgs a = row_args(c, t, (float)p->lambda);
+        SweepArgs a = row_args(c, t, lam_row);
+        if (c->mode == SUPPY_EMR) a.coef_mul = c->d_rhof;
         const EpiArgs epi = epi_args(c, t, sp);
         if (c->use_tma) {
             StreamArgs sa;
@@ -415,7 +532,8 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             sa.coef = (c->strategy == 2) ? c->d_coef : nullptr;
             sa.pp = c->d_pp;
             sa.st = c->d_st;
-            sa.lam = (float)p->lambda;
+            sa.lam = lam_row;
+            sa.coef_mul = (c->mode == SUPPY_EMR) ? c->d_rhof : nullptr;
             sa.check_stop = 1;
             EpiArgs e2 = epi;
             e2.npp = c->seg_tgrid[t];
@@ -442,13 +560,17 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.lo = c->d_lo;
                 ca.hi = c->d_hi;
                 ca.zc = c->d_zc;
+                ca.delta_out = ext ? c->d_delta : nullptr;
                 ca.box_len = c->box_len;
                 ca.epi = e2;
-                Timed tm{c, 1};
-                CK(tm.begin());
-                CK(launch_cols_tma(ca, c->dt, c->tGc, c->seg_ctgrid[t], c->stream));
-                CK(tm.end());
-                note_launch(c);
+                {
+                    Timed tm{c, 1};
+                    CK(tm.begin());
+                    CK(launch_cols_tma(ca, c->dt, c->tGc, c->seg_ctgrid[t], c->stream));
+                    CK(tm.end());
+                    note_launch(c);
+                }
+                if (ext && (s = enqueue_ext_step(c, p, t, e2.npp)) != SUPPY_OK) return s;
                 if (e2.last_seg) {
                     CK(launch_epilogue(e2, c->stream));
                     note_launch(c);
@@ -482,6 +604,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.lo = c->d_lo;
             ca.hi = c->d_hi;
             ca.zc = c->d_zc;
+            ca.delta_out = ext ? c->d_delta : nullptr;
             ca.box_len = c->box_len;
             ca.B = c->B;
             ca.cpart = c->d_cpart + c->seg_cpart_off[t];
@@ -489,11 +612,14 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             ca.m = c->m;
             ca.nnz = c->csc_len;
             ca.epi = epi;
-            Timed tm{c, 1};
-            CK(tm.begin());
-            CK(launch_colpass(ca, c->dt, c->Gc, c->seg_cgrid[t], c->stream));
-            CK(tm.end());
-            note_launch(c);
+            {
+                Timed tm{c, 1};
+                CK(tm.begin());
+                CK(launch_colpass(ca, c->dt, c->Gc, c->seg_cgrid[t], c->stream));
+                CK(tm.end());
+                note_launch(c);
+            }
+            if (ext && (s = enqueue_ext_step(c, p, t, epi.npp)) != SUPPY_OK) return s;
             if (epi.last_seg) {
                 CK(launch_epilogue(epi, c->stream));
                 note_launch(c);
@@ -1094,7 +1220,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (c->dt != SUPPY_F32 && c->dt != SUPPY_BF16 && c->dt != SUPPY_F16)
         return fail(c, SUPPY_EINVAL, "unknown a_dtype");
     c->mode = o->mode;
-    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP)
+    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP &&
+        c->mode != SUPPY_EL && c->mode != SUPPY_EMR)
         return fail(c, SUPPY_EINVAL, "unknown mode");
     c->obj = o->obj;
     if ((int)c->obj < 0 || (int)c->obj > 5) return fail(c, SUPPY_EINVAL, "unknown objective");
@@ -1391,7 +1518,11 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if ((s = dalloc(c, &c->d_err, 1)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     const bool smem_ok = (c->B == 1) && (size_t)n * sizeof(float) <= 64 * 1024;
-    const int want = o->strategy;
+    // EL / EMR take the two-pass sweep (the column pass accumulates A^T(.));
+    // their buffers exist before any timed candidate sweep
+    const bool ext_mode = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
+    if (ext_mode && (s = prepare_ext(c)) != SUPPY_OK) return s;
+    const int want = ext_mode ? 2 : o->strategy;
     if (want < 0 || want > 2) return fail(c, SUPPY_EINVAL, "unknown strategy");
     const bool need_csc = (want == 2) || (want == 0 && (o->tune || !smem_ok));
     if (need_csc) {

@@ -58,6 +58,8 @@ struct SweepArgs {
     const float* x;         // n x B iterate (read only during the pass)
     float* delta;           // n x B correction accumulator (one-pass scatter)
     float* coef;            // m x B correction coefficients (two-pass) or null
+    const float* coef_mul;  // per row multiplier of the coefficient (EMR) or null
+    const float* prox_mul;  // per row multiplier of the proximity term or null
     const int* part;        // group boundaries (ngroups + 1 absolute row indices)
     double* pp;             // proximity partials: pp[cta * B + b]
     RhsState* st;
@@ -107,6 +109,7 @@ struct ColArgs {
     const float* lo;
     const float* hi;
     const float* zc;        // DROP column scaling 1/s_j (n) or null (1)
+    float* delta_out;       // EL / EMR: the column sums go here (n x B), x untouched
     int box_len;
     int B;
     const int* cpart;
@@ -178,6 +181,8 @@ struct StreamArgs {
     const float* x;
     float* delta;
     float* coef;            // coefficients out (two-pass) or null
+    const float* coef_mul;  // per row multiplier of the coefficient (EMR) or null
+    const float* prox_mul;  // per row multiplier of the proximity term or null
     double* pp;
     RhsState* st;
     float lam;
@@ -188,8 +193,31 @@ struct StreamArgs {
     const float* lo;
     const float* hi;
     const float* zc;        // DROP column scaling 1/s_j (n) or null (1)
+    float* delta_out;       // EL / EMR: the column sums go here, x untouched
     int box_len;
     EpiArgs epi;
+};
+
+// Extrapolated step of EL / EMR (sweep.cu): t_b from the sweep's reductions,
+// then x <- box(x + lambda t_b delta), delta <- 0.
+struct ExtArgs {
+    float* x;
+    float* delta;           // n x B column sums A^T (W d)
+    const float* lo;
+    const float* hi;
+    int box_len;
+    long long n;
+    int B;
+    RhsState* st;
+    int method;             // SUPPY_EL or SUPPY_EMR
+    const double* pp;       // row pass partials (sum w d^2 / ||a||^2), npp CTAs x B
+    int npp;
+    const double* qq;       // EMR: partials of sum w q^2 (q = A delta), nqq CTAs x B
+    int nqq;
+    double* part;           // grid x B x 1 partials of ||delta||^2
+    unsigned* ticket;
+    double* tstep;          // B step sizes
+    float lam;
 };
 
 // --- launchers (defined in sweep.cu / stream.cu / perturb.cu / setup.cu) ----
@@ -267,6 +295,8 @@ cudaError_t launch_extract_column(const float* x, long long n, int B, int b, flo
 cudaError_t launch_column_scaling(const int2* rinfo, const int* col, const void* val,
                                   suppy_dtype dt, const double* rho, int m, int n, int* counts,
                                   float* zc, cudaStream_t s);
+cudaError_t launch_ext_step(const ExtArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_to_float(const double* v, int n, float* out, cudaStream_t s);
 cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val, int m, int n,
                            double* c64, float* c32, double* work, int work_ctas,
                            cudaStream_t s);

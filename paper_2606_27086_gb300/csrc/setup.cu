@@ -446,6 +446,16 @@ cudaError_t launch_column_scaling(const int2* rinfo, const int* col, const void*
     return cudaGetLastError();
 }
 
+__global__ void k_to_float(const double* v, int n, float* out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (float)v[i];
+}
+
+cudaError_t launch_to_float(const double* v, int n, float* out, cudaStream_t s) {
+    k_to_float<<<grid_for(n), 256, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_load_column(const float* l_in, const float* u_in, const int* perm, int m, int B,
                                int b, float* l, float* u, cudaStream_t s) {
     k_load_column<<<grid_for(m), 256, 0, s>>>(l_in, u_in, perm, m, B, b, l, u);

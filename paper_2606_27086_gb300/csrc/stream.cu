@@ -412,6 +412,7 @@ struct RowWork {
     const StreamArgs& a;
     float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
     float nl = 0.f, nu = 0.f, nw = 0.f;     // next round's
+    float cm = 1.f, pm = 1.f, ncm = 1.f, npm = 1.f;   // coefficient / proximity multipliers
     // The group leader's proximity terms are summed in FP32 with Kahan
     // compensation (error independent of the term count) and widened to FP64
     // for the CTA and grid reductions: FP64 arithmetic is scarce on GB300 and
@@ -429,12 +430,16 @@ struct RowWork {
             nl = __ldg(a.l + i);
             nu = __ldg(a.u + i);
             nw = __ldg(a.wr + i);
+            if (a.coef_mul) ncm = __ldg(a.coef_mul + i);
+            if (a.prox_mul) npm = __ldg(a.prox_mul + i);
         }
     }
     __device__ void advance() {
         li = nl;
         ui = nu;
         w = nw;
+        cm = ncm;
+        pm = npm;
     }
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
@@ -442,7 +447,7 @@ struct RowWork {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;
-        const float coef = a.lam * w * d;
+        const float coef = a.lam * w * d * cm;
         if (SCAT == 0) {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
@@ -453,7 +458,7 @@ struct RowWork {
                 r.step(p, G);
             }
         }
-        if (gl == 0) kahan_add(d * d * w);
+        if (gl == 0) kahan_add(d * d * w * pm);
         return 0.0;
     }
 };
@@ -493,7 +498,10 @@ struct ColWork {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
         if (a.zc) s *= z;
-        if (gl == 0) a.xw[j] = clampf(xj + s, lo, hi);
+        if (gl == 0) {
+            if (a.delta_out) a.delta_out[j] = s;
+            else a.xw[j] = clampf(xj + s, lo, hi);
+        }
         return 0.0;
     }
 };

@@ -253,8 +253,9 @@ __global__ void __launch_bounds__(kSweepThreads, SCAT == 0 ? 6 : 2) k_sweep(cons
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gmask, dot, o);
 
         const float d = clampf(dot, li, ui) - dot;
-        if (lane == 0) prox += (double)d * (double)d * (double)w;
-        const float coef = a.lam * w * d;
+        const float wp = a.prox_mul ? w * __ldg(a.prox_mul + i) : w;
+        if (lane == 0) prox += (double)d * (double)d * (double)wp;
+        const float coef = a.lam * w * d * (a.coef_mul ? __ldg(a.coef_mul + i) : 1.f);
         if constexpr (SCAT == 0) {
             if (a.coef && lane == 0) a.coef[i] = coef;
         } else {
@@ -340,6 +341,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         const float4 lv = __ldg(reinterpret_cast<const float4*>(a.l + (size_t)i * B) + q);
         const float4 uv = __ldg(reinterpret_cast<const float4*>(a.u + (size_t)i * B) + q);
         const float w = a.wr[i];
+        const float wp = a.prox_mul ? w * a.prox_mul[i] : w;
+        const float wc = a.coef_mul ? w * a.coef_mul[i] : w;
         float d[4];
         d[0] = clampf(acc.x, lv.x, uv.x) - acc.x;
         d[1] = clampf(acc.y, lv.y, uv.y) - acc.y;
@@ -349,8 +352,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batched(const SweepArgs
         bool any = false;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            if (e0 == 0) prox[t] += (double)d[t] * (double)d[t] * (double)w;
-            cf[t] = live[t] ? a.lam * w * d[t] : 0.f;
+            if (e0 == 0) prox[t] += (double)d[t] * (double)d[t] * (double)wp;
+            cf[t] = live[t] ? a.lam * wc * d[t] : 0.f;
             any |= (cf[t] != 0.f);
         }
         if (SCAT == 0) {
@@ -412,7 +415,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
         if (lane == 0 && ci.y > 0) {
             const int bj = (a.box_len == 1) ? 0 : j;
             if (a.zc) s *= a.zc[j];
-            a.x[j] = clampf(a.x[j] + s, a.lo[bj], a.hi[bj]);
+            if (a.delta_out) a.delta_out[j] = s;
+            else a.x[j] = clampf(a.x[j] + s, a.lo[bj], a.hi[bj]);
         }
     }
     if (blockIdx.x == 0 && !a.epi.last_seg) sweep_epilogue(a.epi);
@@ -466,6 +470,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
                 s.y *= z;
                 s.z *= z;
                 s.w *= z;
+            }
+            if (a.delta_out) {
+                reinterpret_cast<float4*>(a.delta_out + (size_t)j * B)[q] = s;
+                continue;
             }
             float4* xp = reinterpret_cast<float4*>(a.x + (size_t)j * B) + q;
             float4 xv = *xp;
@@ -610,6 +618,75 @@ ColFn col_fn(suppy_dtype dt, int G, int B) {
     return pick_col<__half>(G, B);
 }
 
+// ------------------------------------------------ EL / EMR extrapolation ----
+// k_ext_norm: ||delta_b||^2 per right-hand side (FP64 per thread, fixed-order
+// sums over lanes, warps and CTAs); the last CTA to finish turns the sweep's
+// reductions into the step t_b:
+//   EL  t = sum_i w_i d_i^2 / ||a_i||^2 / ||delta||^2   (delta = A^T D d)
+//   EMR t = ||delta||^2 / sum_i w_i q_i^2                (delta = A^T M d, q = A delta)
+// and 0 when a denominator vanishes or the right-hand side has stopped.
+__global__ void __launch_bounds__(256) k_ext_norm(const ExtArgs a) {
+    __shared__ double sw[8][32];
+    __shared__ bool is_last;
+    const long long nB = a.n * a.B;
+    const long long tid = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long stride = (long long)gridDim.x * 256;
+    const int B = a.B;
+    double s = 0.0;
+    for (long long e = tid; e < nB; e += stride) {
+        const double d = (double)a.delta[e];
+        s += d * d;
+    }
+    for (int o = 16; o >= B && o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane < B) sw[wid][lane] = s;
+    __syncthreads();
+    if (threadIdx.x < B) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += sw[w][threadIdx.x];
+        a.part[(size_t)blockIdx.x * B + threadIdx.x] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(a.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int b = wid; b < B; b += 8) {
+        double d2 = 0.0, num = 0.0;
+        for (int c = lane; c < (int)gridDim.x; c += 32) d2 += __ldcg(a.part + (size_t)c * B + b);
+        const double* src = (a.method == SUPPY_EL) ? a.pp : a.qq;
+        const int ns = (a.method == SUPPY_EL) ? a.npp : a.nqq;
+        for (int c = lane; c < ns; c += 32) num += __ldcg(src + (size_t)c * B + b);
+        d2 = warp_sum(d2);
+        num = warp_sum(num);
+        if (lane == 0) {
+            double t = 0.0;
+            if (!a.st[b].stopped) {
+                if (a.method == SUPPY_EL && d2 > 0.0) t = num / d2;
+                if (a.method == SUPPY_EMR && num > 0.0) t = d2 / num;
+            }
+            a.tstep[b] = t;
+        }
+    }
+    if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+// x <- box(x + lambda t_b delta), delta <- 0.
+__global__ void __launch_bounds__(256) k_ext_apply(const ExtArgs a) {
+    const long long nB = a.n * a.B;
+    for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < nB;
+         e += (long long)gridDim.x * 256) {
+        const int b = (int)(e % a.B);
+        const long long j = e / a.B;
+        const float t = a.lam * (float)a.tstep[b];
+        const long long bj = (a.box_len == 1) ? 0 : j;
+        const float d = a.delta[e];
+        if (t != 0.f) a.x[e] = clampf(a.x[e] + t * d, a.lo[bj], a.hi[bj]);
+        a.delta[e] = 0.f;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,
@@ -679,6 +756,12 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
 cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                              double* out, cudaStream_t s) {
     k_reduce_pp<<<1, 256, 0, s>>>(pp, npp, B, scale, accumulate, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ext_step(const ExtArgs& a, int grid, cudaStream_t s) {
+    k_ext_norm<<<grid, 256, 0, s>>>(a);
+    k_ext_apply<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

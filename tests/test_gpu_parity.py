@@ -696,3 +696,50 @@ def test_update_bounds_keeps_the_iteration_state():
     ctx.suppy_set_bounds(l1.astype(np.float32), u1.astype(np.float32))
     st = ctx.suppy_run(_params(max_sweeps=0, **P))[0]
     assert st["sweeps"] == 0 and st["ell"] == 0
+
+
+# ------------------------------------------------------------- EL / EMR ----
+
+@pytest.mark.parametrize("tma", [0, -1])
+@pytest.mark.parametrize("mode", [pk.SUPPY_EL, pk.SUPPY_EMR])
+def test_extrapolated_sweeps_match_oracle(mode, tma):
+    """EL and EMR (the column pass accumulates, the step size comes from
+    grid-wide FP64 reductions, EMR adds a pass over q = A delta), streamed
+    and register-fed, with lambda 1 and 0.8, over three sweeps."""
+    prob = synth.random_problem(3000, 20011, seed=58, feasible=False, mean_len=24,
+                                empty_frac=0.04, long_rows=3, long_len=400)
+    om = {pk.SUPPY_EL: O.EL, pk.SUPPY_EMR: O.EMR}[mode]
+    for lam in (1.0, 0.8):
+        ctx = pk.from_problem(prob, mode=mode, tma=tma)
+        assert ctx.suppy_info_get()["strategy"] == 2
+        x0 = random_x(prob.A.n, 1, seed=59)
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(lam=lam), 3)
+        S, l, u, lo, hi = O.from_problem(prob)
+        x = x0.astype(np.float64)
+        for _ in range(3):
+            x, p_last = O.sweep(S, om, l, u, lam, lo, hi, x)
+        assert rel_l2(ctx.suppy_get_x(), x) <= 1e-5
+        ph, _ = ctx.suppy_history()
+        assert rel(ph[-1], p_last) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [pk.SUPPY_EL, pk.SUPPY_EMR])
+def test_superiorized_extrapolated_runs_batched(mode):
+    """The CT study's setting: EMR / EL feasibility-seeking with TV
+    perturbations, several sinograms at once, against the oracle per
+    right-hand side.  EL's extrapolated steps (t up to ~m on this
+    inconsistent system) amplify the FP32 / FP64 difference -- the paper
+    reports EL fluctuating on inconsistent CT data -- so its run is shorter."""
+    prob = small_ct(nrhs=3)
+    om = {pk.SUPPY_EL: O.EL, pk.SUPPY_EMR: O.EMR}[mode]
+    ctx = pk.from_problem(prob, mode=mode, obj=pk.SUPPY_OBJ_TV_ISO)
+    P = dict(gamma=0.5, alpha=0.99, n_red=1, max_sweeps=12 if mode == pk.SUPPY_EL else 30)
+    st = ctx.suppy_run(_params(**P))
+    xg = ctx.suppy_get_x()
+    S, l, u, lo, hi = O.from_problem(prob)
+    ob = oracle_objective(prob, O.OBJ_TV_ISO)
+    for b in range(3):
+        r = O.run(S, om, O.rhs(l, b), O.rhs(u, b), lo, hi, ob, O.Params(**P))
+        assert st[b]["ell"] == r.ell
+        assert rel_l2(xg[:, b], r.x) <= 1e-3
