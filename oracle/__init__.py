@@ -26,6 +26,10 @@ constrained physical problems with SupPy"):
   one block, blocks visited in order;
 * box projection after each step -- Sec. 2.3.3 (BoxProjection onto x >= 0);
 * weighted proximity -- Eq. (WeightedProximity), 1/2 sum_i w_i ||P_i x - x||^2;
+* split feasibility -- Eq. (Split) and the CQ iteration printed after it,
+  for the dose-volume constraints of Sec. 2.3.3 (and its table of the
+  horseshoe plan's constraints), x <- x + gamma sum_j w_j A_j^T (P_Qj(A_j x) -
+  A_j x);
 * superiorization -- Algorithm 1 with the power-law step beta = gamma alpha^l
   and the normalised subgradient direction of Sec. 2.1.2;
 * stopping -- Sec. 2.2.1 (P <= P*, relative proximity change below dP* for N
@@ -53,6 +57,14 @@ the kept rows), whose fixed points are those of the Cimmino step; Q25 EL / EMR
 in slab form: the residual A x - b becomes A x - clamp(A x, l, u), weights
 w_i = 1/m' (D = diag(w_i/||a_i||^2), M = diag(w_i)), the step is followed by
 the box and scaled by the relaxation lambda; a zero correction leaves x.
+Q26 dose-volume sets: an upper DVC lets at most floor(V N) of the structure's N
+voxels exceed d_ref, a lower DVC demands at least ceil(V N) at or above d_ref;
+the projection keeps (upper) or raises (lower) the K highest doses, equal doses
+ranked by voxel index.  Q27 split iteration: the CQ step with weights
+w_j = 1/t over the t DVCs and gamma = relax / sum_j w_j ||A_j||_F^2, then the
+feasibility sweep over the slabs (P_C), then the box.  Q28 with a split problem
+the stopping rule and the recorded proximity use the target-space proximity
+1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 (Sec. 2.2.1).
 
 Parity of the whole superiorized run against printed values is unpinned: the
 paper prints no iterates for this path.
@@ -258,6 +270,113 @@ def sweep(S: Setup, mode: int, l: np.ndarray, u: np.ndarray, lam: float, lo, hi,
                                  S.w_prox[rows], l[rows], u[rows], lam, lo, hi, x)
         p_tot += p
     return x, p_tot
+
+
+# ------------------------------------------------- split feasibility (DVC) --
+
+DVC_UPPER, DVC_LOWER = 0, 1
+
+
+@dataclass
+class DVC:
+    """One dose-volume constraint on a structure (Sec. 2.3.3, radiotherapy):
+    DVC_UPPER is D_V <= d_ref (not more than the fraction V of the structure's
+    voxels above d_ref), DVC_LOWER is D_V >= d_ref (at least the fraction V at
+    or above d_ref).  ``structure`` indexes the row ranges of the split
+    matrix."""
+    kind: int
+    structure: int
+    volume: float
+    d_ref: float
+
+
+def dvc_count(kind: int, volume: float, N: int) -> int:
+    """Q26: the voxel count a DVC allows (upper: floor(V N) voxels may exceed
+    d_ref) or demands (lower: ceil(V N) voxels must reach d_ref); V N is one
+    double multiplication."""
+    v = float(volume) * float(N)
+    return int(np.floor(v)) if kind == DVC_UPPER else int(np.ceil(v))
+
+
+def dvc_project(d: np.ndarray, kind: int, volume: float, d_ref: float) -> np.ndarray:
+    """Euclidean projection of one structure's dose vector onto its DVC set
+    (Q26).
+
+    Upper: the set is the union, over voxel subsets S with |S| = K, of
+    {p : p_i <= d_ref for i not in S}; the nearest point leaves the K highest
+    doses as they are and lowers every other dose above d_ref to d_ref.
+    Lower: the union over |S| = K of {p : p_i >= d_ref for i in S}; the nearest
+    point raises those of the K highest doses that are below d_ref to d_ref.
+    Equal doses are ranked by the lower voxel index first.
+    """
+    d = np.asarray(d, np.float64)
+    N = len(d)
+    K = min(max(dvc_count(kind, volume, N), 0), N)
+    order = np.lexsort((np.arange(N), -d))      # descending dose, then index
+    top = np.zeros(N, dtype=bool)
+    top[order[:K]] = True
+    p = d.copy()
+    if kind == DVC_UPPER:
+        sel = (~top) & (d > d_ref)
+    else:
+        sel = top & (d < d_ref)
+    p[sel] = d_ref
+    return p
+
+
+@dataclass
+class SplitSetup:
+    """The target-space part of a split-feasibility problem (Eq. (Split)):
+    rows of ``Aq`` (dose rows of the DVC structures) grouped by structure,
+    ``sptr[s]:sptr[s+1]`` the rows of structure s; weights w_j = 1/t over the t
+    DVCs and the CQ step gamma = relax / L*, L* = sum_j w_j ||A_j||_F^2 (Q27)."""
+    Aq: sp.csr_matrix
+    sptr: np.ndarray
+    dvcs: list
+    w: np.ndarray
+    gamma: float
+
+
+def split_setup(Aq: sp.csr_matrix, sptr, dvcs: list, relax: float = 1.0) -> SplitSetup:
+    Aq = sp.csr_matrix(Aq, dtype=np.float64)
+    sptr = np.asarray(sptr, np.int64)
+    t = len(dvcs)
+    w = np.full(t, 1.0 / t) if t else np.zeros(0)
+    rows2 = np.asarray(Aq.multiply(Aq).sum(axis=1)).ravel()
+    L = 0.0
+    for j, q in enumerate(dvcs):
+        L += w[j] * float(np.sum(rows2[sptr[q.structure]:sptr[q.structure + 1]]))
+    return SplitSetup(Aq, sptr, list(dvcs), w, relax / L if L > 0 else 0.0)
+
+
+def dvc_corrections(SS: SplitSetup, d: np.ndarray) -> tuple[np.ndarray, float]:
+    """Given the doses d = Aq x: c = sum_j w_j (P_Qj(d_j) - d_j) (placed on the
+    rows of each DVC's structure) and the target-space proximity
+    1/2 sum_j w_j ||P_Qj(d_j) - d_j||^2 (Eq. (WeightedProximity) over the Q_j;
+    Q28)."""
+    d = np.asarray(d, np.float64)
+    c = np.zeros_like(d)
+    prox = 0.0
+    for j, q in enumerate(SS.dvcs):
+        r0, r1 = int(SS.sptr[q.structure]), int(SS.sptr[q.structure + 1])
+        dj = d[r0:r1]
+        e = dvc_project(dj, q.kind, q.volume, q.d_ref) - dj
+        c[r0:r1] += SS.w[j] * e
+        prox += 0.5 * SS.w[j] * float(e @ e)
+    return c, prox
+
+
+def dvc_proximity(SS: SplitSetup, x: np.ndarray) -> float:
+    return dvc_corrections(SS, SS.Aq @ x)[1]
+
+
+def cq_step(SS: SplitSetup, x: np.ndarray) -> tuple[np.ndarray, float]:
+    """The CQ step of Sec. 2.1.1 (after Eq. (Split)) for the several sets Q_j:
+    x <- x + gamma sum_j w_j A_j^T (P_Qj(A_j x) - A_j x).  P_C is applied by
+    the feasibility sweep that follows (Q27).  Returns the new point and the
+    target-space proximity of the input point."""
+    c, prox = dvc_corrections(SS, SS.Aq @ x)
+    return x + SS.gamma * (SS.Aq.T @ c), prox
 
 
 # -------------------------------------------------------------- objectives --
@@ -475,8 +594,13 @@ def variance_of_changes(omega: list) -> float:
 
 
 def run(S: Setup, mode: int, l, u, lo, hi, obj: Objective, P: Params,
-        x0: np.ndarray | None = None, n_sweeps: int | None = None) -> RunResult:
+        x0: np.ndarray | None = None, n_sweeps: int | None = None,
+        split: SplitSetup | None = None) -> RunResult:
     """Algorithm 1: perturbation phase, then one application of T, repeated.
+
+    With ``split`` (a split-feasibility problem, Eq. (Split)) each iteration
+    runs the CQ step over the dose-volume sets before T (Q27), and the monitored
+    proximity is the target-space one at the CQ step's input point (Q28).
 
     x0 defaults to box(0) (Q18).  With ``use_stopping`` False the run is exactly
     ``max_sweeps`` sweeps; otherwise it ends at the first sweep after which
@@ -501,7 +625,11 @@ def run(S: Setup, mode: int, l, u, lo, hi, obj: Objective, P: Params,
             acc.append(a)
             tri.append(t)
             oh.append(f_k)
+        if split is not None:
+            x, p_target = cq_step(split, x)
         x, p = sweep(S, mode, l, u, P.lam, lo, hi, x)
+        if split is not None:
+            p = p_target
         ph.append(p)
         k += 1
         if P.use_stopping and stop_check(ss, p, f_k, P):

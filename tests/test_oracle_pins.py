@@ -686,3 +686,172 @@ def test_emr_weighted_residual_never_increases_on_consistent_slabs():
         assert cur <= prev * (1 + 1e-9) + 1e-24
         prev = cur
     assert O.proximity(S, l, u, x) < 1e-8
+
+
+# ------------------------------------------------- split feasibility (DVC) --
+
+def _dvc_bruteforce(d, kind, K, d_ref):
+    """Nearest point of the dose-volume set by enumerating its convex pieces:
+    every voxel subset S of size K (upper: S may exceed d_ref; lower: S must
+    reach it).  Returns the smallest distance."""
+    from itertools import combinations
+    best = np.inf
+    for S in combinations(range(len(d)), K):
+        S = list(S)
+        p = d.copy()
+        mask = np.zeros(len(d), bool)
+        mask[S] = True
+        if kind == O.DVC_UPPER:
+            p[~mask] = np.minimum(d[~mask], d_ref)
+        else:
+            p[mask] = np.maximum(d[mask], d_ref)
+        best = min(best, float(np.linalg.norm(p - d)))
+    return best
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_dvc_projection_is_the_nearest_point_of_the_union(seed):
+    """Q26: the projection onto {at most / at least K voxels beyond d_ref} is
+    the nearest point over all K-subsets (brute force), and it lies in the set
+    as the paper words it: not more than V N voxels above d_ref (upper), at
+    least V N voxels at or above d_ref (lower)."""
+    rng = np.random.default_rng(900 + seed)
+    for N in range(1, 8):
+        for trial in range(6):
+            d = rng.standard_normal(N) * 2 + 3
+            if trial % 2:
+                d = np.round(d)             # ties
+            d_ref = float(np.median(d) + rng.uniform(-1, 1))
+            for V in (0.0, 0.1, 0.3, 0.5, 0.75, 1.0):
+                for kind in (O.DVC_UPPER, O.DVC_LOWER):
+                    p = O.dvc_project(d, kind, V, d_ref)
+                    K = O.dvc_count(kind, V, N)
+                    ref = _dvc_bruteforce(d, kind, K, d_ref)
+                    assert abs(np.linalg.norm(p - d) - ref) <= 1e-12
+                    if kind == O.DVC_UPPER:
+                        assert np.count_nonzero(p > d_ref) <= V * N
+                    else:
+                        assert np.count_nonzero(p >= d_ref) >= V * N - 1e-12
+                    # only voxels on the wrong side move, and only to d_ref
+                    moved = p != d
+                    assert np.all(p[moved] == d_ref)
+
+
+def test_dvc_counts_round_towards_the_constraint():
+    """'Not more than V%' allows floor(V N) voxels, 'at least V%' demands
+    ceil(V N): 5% of 30 voxels is 1.5."""
+    assert O.dvc_count(O.DVC_UPPER, 0.05, 30) == 1
+    assert O.dvc_count(O.DVC_LOWER, 0.05, 30) == 2
+    assert O.dvc_count(O.DVC_UPPER, 0.95, 20) == 19
+    assert O.dvc_count(O.DVC_LOWER, 0.95, 20) == 19
+    assert O.dvc_count(O.DVC_LOWER, 1.0, 7) == 7
+    assert O.dvc_count(O.DVC_UPPER, 0.0, 7) == 0
+
+
+def test_dvc_equal_doses_rank_lower_index_first():
+    p = O.dvc_project(np.array([5.0, 5.0, 5.0, 1.0]), O.DVC_UPPER, 0.25, 2.0)
+    assert p.tolist() == [5.0, 2.0, 2.0, 1.0]
+    p = O.dvc_project(np.array([1.0, 1.0, 1.0, 9.0]), O.DVC_LOWER, 0.75, 4.0)
+    assert p.tolist() == [4.0, 4.0, 1.0, 9.0]
+
+
+def test_dvc_extreme_volumes_are_the_plain_clamps():
+    """V = 0 upper is {d <= d_ref} voxel-wise, V = 1 lower is {d >= d_ref}."""
+    rng = np.random.default_rng(77)
+    d = rng.standard_normal(50)
+    assert np.array_equal(O.dvc_project(d, O.DVC_UPPER, 0.0, 0.1), np.minimum(d, 0.1))
+    assert np.array_equal(O.dvc_project(d, O.DVC_LOWER, 1.0, -0.2), np.maximum(d, -0.2))
+    assert np.array_equal(O.dvc_project(d, O.DVC_UPPER, 1.0, 0.1), d)
+    assert np.array_equal(O.dvc_project(d, O.DVC_LOWER, 0.0, 0.1), d)
+
+
+def _equal_norm_rows(m, n, seed, norm=1.3):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, n)) * (rng.uniform(size=(m, n)) < 0.6)
+    A[:, 0] += 0.5                      # no zero rows
+    A *= norm / np.linalg.norm(A, axis=1, keepdims=True)
+    return A
+
+
+@pytest.mark.parametrize("relax", [0.8, 1.6])
+def test_cq_step_with_halfspace_dvcs_is_the_cimmino_step(relax):
+    """With V = 0 every upper DVC is the halfspace family a_i x <= d_ref; on
+    rows of equal norm rho the CQ step x + gamma sum_j w_j A_j^T (P - d),
+    gamma = relax / sum_j w_j ||A_j||_F^2, is the simultaneous projection step
+    x + lambda sum_i (1/m) (clamp(r_i) - r_i)/rho a_i with lambda = relax."""
+    m1, m2, n = 7, 5, 6
+    A = _equal_norm_rows(m1 + m2, n, 31)
+    rng = np.random.default_rng(32)
+    x = rng.standard_normal(n)
+    u = np.concatenate([np.full(m1, 0.2), np.full(m2, -0.1)])
+    dv = [O.DVC(O.DVC_UPPER, 0, 0.0, 0.2), O.DVC(O.DVC_UPPER, 1, 0.0, -0.1)]
+    SS = O.split_setup(sp.csr_matrix(A), [0, m1, m1 + m2], dv, relax)
+    xq, pq = O.cq_step(SS, x)
+    S = O.setup(sp.csr_matrix(A), np.full(m1 + m2, -np.inf), u)
+    xc, pc = O.simultaneous_step(S.A, S.rho, S.keep, S.w_sweep, S.w_prox, np.full(m1 + m2, -np.inf),
+                                 u, relax, -np.inf, np.inf, x)
+    assert np.allclose(xq, xc, rtol=1e-13, atol=1e-14)
+    # proximities: target space weights 1/2 per DVC vs 1/m per row with 1/rho
+    r = A @ x
+    e = np.minimum(r, u) - r
+    assert np.isclose(pq, 0.5 * (0.5 * e[:m1] @ e[:m1] + 0.5 * e[m1:] @ e[m1:]), rtol=1e-13)
+    assert np.isclose(pc, 0.5 * np.sum(e ** 2) / (m1 + m2) / 1.3 ** 2, rtol=1e-13)
+
+
+def _split_case(seed):
+    rng = np.random.default_rng(seed)
+    m1, m2, n = 12, 9, 8
+    A = np.abs(rng.standard_normal((m1 + m2, n))) * (rng.uniform(size=(m1 + m2, n)) < 0.7)
+    dv = [O.DVC(O.DVC_LOWER, 0, 0.75, 3.0), O.DVC(O.DVC_UPPER, 0, 0.25, 4.0),
+          O.DVC(O.DVC_UPPER, 1, 0.2, 1.5)]
+    return A, [0, m1, m1 + m2], dv, rng
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_cq_direction_is_minus_the_gradient_of_the_target_proximity(seed):
+    """Away from ties and from d_ref the selected voxels stay fixed nearby, so
+    p(x) = 1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 is smooth there and the CQ
+    step is x - gamma grad p (central differences)."""
+    A, sptr, dv, rng = _split_case(seed)
+    SS = O.split_setup(sp.csr_matrix(A), sptr, dv, 1.0)
+    x = np.abs(rng.standard_normal(A.shape[1])) * 0.7
+    d = A @ x
+    for q in dv:       # margins: no dose near d_ref, no near-equal doses
+        dj = d[sptr[q.structure]:sptr[q.structure + 1]]
+        assert np.min(np.abs(dj - q.d_ref)) > 1e-4
+        assert np.min(np.diff(np.sort(dj))) > 1e-4
+    xn, p0 = O.cq_step(SS, x)
+    assert p0 > 0
+    h = 1e-6
+    grad = np.array([(O.dvc_proximity(SS, x + h * e) - O.dvc_proximity(SS, x - h * e)) / (2 * h)
+                     for e in np.eye(len(x))])
+    assert np.allclose((xn - x) / SS.gamma, -grad, rtol=1e-6, atol=1e-8)
+    # gamma is relax / sum_j w_j ||A_j||_F^2
+    F = [np.sum(A[sptr[s]:sptr[s + 1]] ** 2) for s in range(2)]
+    assert np.isclose(SS.gamma, 1.0 / ((F[0] + F[0] + F[1]) / 3.0), rtol=1e-14)
+
+
+@pytest.mark.parametrize("relax", [1.0, 1.9])
+def test_cq_iteration_never_increases_the_target_proximity(relax):
+    """gamma < 2/L makes the CQ step a descent step of the quadratic built on
+    the current projections, and re-projecting can only shorten the distances:
+    the target-space proximity never increases, even for these nonconvex sets."""
+    A, sptr, dv, rng = _split_case(11)
+    SS = O.split_setup(sp.csr_matrix(A), sptr, dv, relax)
+    x = np.abs(rng.standard_normal(A.shape[1])) * 2.0
+    prev = np.inf
+    for _ in range(60):
+        x, p = O.cq_step(SS, x)
+        assert p <= prev * (1 + 1e-12) + 1e-15
+        prev = p
+
+
+def test_cq_step_is_the_identity_when_every_dvc_holds():
+    A, sptr, _, rng = _split_case(12)
+    x = np.abs(rng.standard_normal(A.shape[1]))
+    d = A @ x
+    dv = [O.DVC(O.DVC_UPPER, 0, 0.1, float(d.max()) + 1.0),
+          O.DVC(O.DVC_LOWER, 1, 0.9, float(d.min()) - 1.0)]
+    SS = O.split_setup(sp.csr_matrix(A), sptr, dv, 1.0)
+    xn, p = O.cq_step(SS, x)
+    assert p == 0.0 and np.array_equal(xn, x)
