@@ -217,13 +217,13 @@ def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     nl = ctx.suppy_launch_count() - l0
-    kt = {k: ctx.suppy_kernel_time(k) for k in (0, 1, 2)} if with_timing else {}
+    kt = {k: ctx.suppy_kernel_time(k) for k in (0, 1, 2, 3)} if with_timing else {}
     if with_timing:
         ctx.suppy_timing_enable(False)
     return ms, kt, nl
 
 
-KIND = {0: "row pass", 1: "column pass / finalize", 2: "perturbation"}
+KIND = {0: "row pass", 1: "column pass / finalize", 2: "perturbation", 3: "split (CQ) step"}
 
 
 def kernel_alg_bytes(strategy, kind, m, n, nnz, vb, B=1):
@@ -260,7 +260,14 @@ def summarize(ctx, prob, K, ms, kt, vb, B=1):
         if nl == 0:
             continue
         sweeps_launches = max(nl // K, 1)
-        alg = kernel_alg_bytes(strat, k, A.m, A.n, A.nnz, vb, B)
+        if k == 3:
+            # CQ step: A_q read as CSR (doses) and as CSC (correction), 8 B an
+            # entry each time, row and column offsets, doses written, x read
+            # and written
+            Aq = prob.meta["split"]["Aq"]
+            alg = 2 * Aq.nnz * 8 + (Aq.m + A.n) * 8 + Aq.m * 4 + A.n * 8
+        else:
+            alg = kernel_alg_bytes(strat, k, A.m, A.n, A.nnz, vb, B)
         per[KIND[k]] = {"ms_per_sweep": tms / K, "launches_per_sweep": sweeps_launches,
                         "alg_bytes_per_sweep": alg,
                         "gbs_alg": alg / (tms / K * 1e-3) / 1e9 if k != 2 else None}
@@ -280,9 +287,16 @@ def variants(pk, K, W):
         dtype = kw.pop("dtype", pk.SUPPY_F32)
         mode = kw.pop("mode", pk.SUPPY_CIMMINO)
         pkw = kw.pop("params")
+        split = kw.pop("split", False)
         B = 1 if prob.l.ndim == 1 else prob.l.shape[1]
         t0 = time.perf_counter()
         ctx = pk.from_problem(prob, obj=obj, dtype=dtype, mode=mode, **kw)
+        nnz_q = 0
+        if split:
+            sp = prob.meta["split"]
+            Aq = sp["Aq"]
+            ctx.suppy_set_dvc(Aq.row_ptr, Aq.col, Aq.val, Aq.m, sp["sptr"], sp["dvcs"], 1.0)
+            nnz_q = Aq.nnz
         t_create = time.perf_counter() - t0
         ms, _, nl = time_iterations(ctx, pk, Kv, W, pkw, with_timing=False)
         _, kt, _ = time_iterations(ctx, pk, Kv, 0, pkw, with_timing=True)
@@ -290,7 +304,8 @@ def variants(pk, K, W):
         info, per, t_sweep = summarize(ctx, prob, Kv, ms, kt, vb, B)
         nnz = prob.A.nnz
         alg = sweep_alg_bytes(prob.A.m, prob.A.n, nnz, vb, B)
-        out[name] = {"value": nnz * B * Kv / (ms * 1e-3), "unit": metric_units,
+        # a split iteration also passes over the dose rows A_q: their entries count
+        out[name] = {"value": (nnz + nnz_q) * B * Kv / (ms * 1e-3), "unit": metric_units,
                      "ms_per_step": ms / Kv, "sweep_ms": t_sweep,
                      "sweep_gbs_alg": alg / (t_sweep * 1e-3) / 1e9 if t_sweep else None,
                      "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B, "kernels": per,
@@ -300,6 +315,8 @@ def variants(pk, K, W):
                      "tma": info["tma"], "tile": info["tile"], "stages": info["stages"],
                      "col_tile": info["col_tile"], "col_stages": info["col_stages"],
                      "launches_per_step": nl / Kv}
+        if split:
+            out[name]["nnz_split"] = nnz_q
         ctx.close()
         torch.cuda.synchronize()
 
@@ -338,6 +355,13 @@ def variants(pk, K, W):
     run_one("rt_bip3_meandose_f32", rt, UNIT, obj=pk.SUPPY_OBJ_LINEAR, mode=pk.SUPPY_BIP,
             params=dict(gamma=1.0, alpha=0.99, n_red=1))
     del rt
+    # the horseshoe plan as a split problem: DVCs by the CQ step, slabs by EMR
+    # (the paper's choice for the linear constraints), restarts every 500
+    rts = synth.rt_split_problem()
+    run_one("rt_split_dvc_emr_meandose_f32", rts, UNIT, obj=pk.SUPPY_OBJ_LINEAR,
+            mode=pk.SUPPY_EMR, params=dict(gamma=1.0, alpha=0.7, n_red=1, restart_every=500),
+            split=True)
+    del rts
     tiny = synth.ct_problem()
     run_one("ct64_cimmino_tv_f32", tiny, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP)
     return out

@@ -311,13 +311,66 @@ suppy_status suppy_set_state(suppy_ctx* ctx, const void* buf, size_t len);
 /* Sizes and launch shapes of the context. */
 suppy_status suppy_info_get(const suppy_ctx* ctx, suppy_info* out);
 
+/* ---------------------------------------------------------------------------
+ * Split feasibility with dose-volume constraints (Eq. (Split) and the CQ
+ * iteration printed after it, Sec. 2.1.1; dose-volume constraints of
+ * Sec. 2.3.3).  The hyperslabs of the context are the input-space sets C_k;
+ * the dose-volume sets Q_j live in the dose space of the rows A_q. */
+typedef enum { SUPPY_DVC_UPPER = 0, SUPPY_DVC_LOWER = 1 } suppy_dvc_kind;
+
+typedef struct {
+    int32_t kind;       /* SUPPY_DVC_UPPER: D_V <= d_ref, at most K = floor(V N) of
+                           the structure's N voxels above d_ref; SUPPY_DVC_LOWER:
+                           D_V >= d_ref, at least K = ceil(V N) voxels at or above
+                           d_ref (V N is one double multiplication)              */
+    int32_t structure;  /* index of the structure (row range of A_q)             */
+    double volume;      /* V, the volume fraction, in [0, 1]                     */
+    double d_ref;       /* reference dose, finite                                */
+} suppy_dvc;
+
+/* Attach the dose-volume sets of a split-feasibility problem.
+ *
+ * Aq: the dose rows (m_q x n, n the context's n) of the structures that carry
+ * DVCs, grouped by structure: rows structure_ptr[s] .. structure_ptr[s+1]-1
+ * (host array of nstruct + 1 entries, structure_ptr[0] = 0, nondecreasing,
+ * structure_ptr[nstruct] = m_q) are structure s.  Values are kept in FP32
+ * whatever the context's a_dtype.  dvc: ndvc constraints (host).  relax in
+ * (0, 2) sets gamma = relax / L*, L* = sum_j w_j ||A_j||_F^2 with w_j = 1/ndvc
+ * and A_j the rows of DVC j's structure (the Frobenius bound of the paper's
+ * step-size rule).
+ *
+ * Afterwards every sweep (suppy_sweep, suppy_run, captured graphs) starts with
+ * the CQ step x <- x + gamma sum_j w_j A_j^T (P_Qj(A_j x) - A_j x), where
+ * P_Qj keeps (upper) or raises to d_ref (lower) the K highest doses of the
+ * structure and lowers (upper) the other doses above d_ref to d_ref, equal
+ * doses ranked by row; the feasibility sweep over the hyperslabs (P_C) and
+ * the box follow.  The monitored proximity (history, stopping rule, stats)
+ * becomes the target-space proximity 1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2
+ * at the CQ step's input point (Sec. 2.2.1: stopping on the target space).
+ *
+ * Needs nrhs = 1.  Copies its inputs (device inputs when Aq->on_device);
+ * synchronizes; replaces an earlier set; ndvc = 0 removes the sets.
+ * SUPPY_EINVAL for nrhs > 1, a malformed matrix (row_ptr, col range, NaN or
+ * infinite values), bad structure ranges, kinds, structures, volumes or d_ref,
+ * relax outside (0, 2), or zero rows in every constrained structure. */
+suppy_status suppy_set_dvc(suppy_ctx* ctx, const suppy_csr* Aq, const int32_t* structure_ptr,
+                           int32_t nstruct, const suppy_dvc* dvc, int32_t ndvc, double relax);
+
+/* Doses d = A_q x at the current x (m_q floats, FP32 accumulation) into host
+ * or device memory.  A host copy synchronizes.  SUPPY_ESTATE without DVCs. */
+suppy_status suppy_dvc_dose(suppy_ctx* ctx, float* dose, int32_t on_device);
+
+/* Target-space proximity 1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 at the current
+ * x (FP64, host).  Synchronizes.  SUPPY_ESTATE without DVCs. */
+suppy_status suppy_dvc_proximity(suppy_ctx* ctx, double* out);
+
 /* Kernel timing for measurement: when enabled, every launch of the kernels
  * below is bracketed by CUDA events on the context's stream.
  * suppy_kernel_time(kind) returns the summed event time (ms) and the launch
  * count since timing was enabled, and synchronizes.  kind: 0 the row pass
  * (the fused one-pass sweep, or the row pass of the two-pass sweep); 1 the
  * box step (finalize kernel, or the column pass of the two-pass sweep); 2 the
- * perturbation phase. */
+ * perturbation phase; 3 the CQ step of a split problem (all its launches). */
 suppy_status suppy_timing_enable(suppy_ctx* ctx, int32_t enable);
 suppy_status suppy_kernel_time(suppy_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
 

@@ -26,6 +26,7 @@ SUPPY_CIMMINO, SUPPY_BIP, SUPPY_DROP, SUPPY_EL, SUPPY_EMR = 0, 1, 2, 3, 4
 SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
 SUPPY_OBJ_L1, SUPPY_OBJ_L2 = 4, 5
 STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS = 0, 1, 2
+SUPPY_DVC_UPPER, SUPPY_DVC_LOWER = 0, 1
 
 EXPORTED = [
     "suppy_params_default", "suppy_create", "suppy_destroy", "suppy_set_stream",
@@ -36,7 +37,8 @@ EXPORTED = [
     "suppy_launch_count", "suppy_last_error", "suppy_version", "suppy_sweep_static",
     "suppy_server_create", "suppy_server_destroy", "suppy_server_add_matrix",
     "suppy_server_submit", "suppy_server_step", "suppy_server_query", "suppy_server_clock",
-    "suppy_server_device_bytes", "suppy_server_last_error",
+    "suppy_server_device_bytes", "suppy_server_last_error", "suppy_set_dvc", "suppy_dvc_dose",
+    "suppy_dvc_proximity",
 ]
 
 
@@ -73,6 +75,11 @@ class suppy_stats(ctypes.Structure):
                 ("trials", ctypes.c_int32), ("stopped", ctypes.c_int32),
                 ("ell", ctypes.c_int64), ("proximity", ctypes.c_double),
                 ("objective", ctypes.c_double)]
+
+
+class suppy_dvc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("structure", ctypes.c_int32),
+                ("volume", ctypes.c_double), ("d_ref", ctypes.c_double)]
 
 
 class suppy_server_opts(ctypes.Structure):
@@ -152,6 +159,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_server_clock": (D, [P]),
         "suppy_server_device_bytes": (I64, [P]),
         "suppy_server_last_error": (ctypes.c_char_p, [P]),
+        "suppy_set_dvc": (ctypes.c_int, [P, ctypes.POINTER(suppy_csr), P, I32,
+                                         ctypes.POINTER(suppy_dvc), I32, D]),
+        "suppy_dvc_dose": (ctypes.c_int, [P, P, I32]),
+        "suppy_dvc_proximity": (ctypes.c_int, [P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +275,7 @@ class Context:
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
+        self.mq = 0                 # rows of the dose-volume matrix (suppy_set_dvc)
         st = lib.suppy_create(ctypes.byref(A), lp, up, lop, hip, ctypes.byref(o),
                               _stream_handle(stream), ctypes.byref(ctx))
         _check(st, None)
@@ -326,6 +338,35 @@ class Context:
         out = np.zeros(self.nrhs, dtype=np.float64)
         _check(self._lib.suppy_proximity(self.ctx, ctypes.c_void_p(out.ctypes.data)), self.ctx)
         return out
+
+    def suppy_set_dvc(self, row_ptr, col, val, m, structure_ptr, dvcs, relax: float = 1.0):
+        """dvcs: sequence of (kind, structure, volume, d_ref); empty removes the sets."""
+        if not len(dvcs):
+            _check(self._lib.suppy_set_dvc(self.ctx, None, None, 0, None, 0, float(relax)),
+                   self.ctx)
+            self.mq = 0
+            return
+        keep = []
+        A = _csr(row_ptr, col, val, m, self.n, keep)
+        sp = np.ascontiguousarray(structure_ptr, dtype=np.int32)
+        arr = (suppy_dvc * max(len(dvcs), 1))()
+        for j, (kind, st, vol, dref) in enumerate(dvcs):
+            arr[j] = suppy_dvc(int(kind), int(st), float(vol), float(dref))
+        _check(self._lib.suppy_set_dvc(self.ctx, ctypes.byref(A), ctypes.c_void_p(sp.ctypes.data),
+                                       len(sp) - 1, arr, len(dvcs), float(relax)), self.ctx)
+        self.mq = int(m) if len(dvcs) else 0
+
+    def suppy_dvc_dose(self, out=None):
+        if out is None:
+            out = np.empty(self.mq, dtype=np.float32)
+        op, d, k = _ptr(out)
+        _check(self._lib.suppy_dvc_dose(self.ctx, op, d), self.ctx)
+        return out
+
+    def suppy_dvc_proximity(self) -> float:
+        v = ctypes.c_double(0.0)
+        _check(self._lib.suppy_dvc_proximity(self.ctx, ctypes.byref(v)), self.ctx)
+        return v.value
 
     def suppy_objective(self):
         out = np.zeros(self.nrhs, dtype=np.float64)

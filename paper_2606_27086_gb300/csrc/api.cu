@@ -138,6 +138,23 @@ struct suppy_ctx {
     double* d_wpart = nullptr;
     unsigned* d_ticket = nullptr;
     std::vector<long long> rpref;   // row-work prefix (m + 1)
+    // split feasibility: dose rows A_q (CSR and CSC), structures, DVCs
+    bool dvc_on = false;
+    int mq = 0, nstruct = 0, ndvc = 0;
+    float dvc_gamma = 0.f;
+    int* d_qrp = nullptr;
+    int* d_qcol = nullptr;
+    float* d_qval = nullptr;
+    int* d_qcp = nullptr;
+    int* d_qrow = nullptr;
+    float* d_qcval = nullptr;
+    int* d_qsptr = nullptr;
+    int* d_qsdvc = nullptr;
+    DvcDesc* d_qdvc = nullptr;
+    float* d_dose = nullptr;
+    float* d_qcorr = nullptr;
+    double* d_qpd = nullptr;
+    double* d_target = nullptr;
 
     // measurement
     struct TimedLaunch {
@@ -146,8 +163,8 @@ struct suppy_ctx {
     };
     bool timing = false;
     std::vector<TimedLaunch> evs;
-    double timing_ms[3] = {0.0, 0.0, 0.0};
-    long long timing_n[3] = {0, 0, 0};
+    double timing_ms[4] = {0.0, 0.0, 0.0, 0.0};
+    long long timing_n[4] = {0, 0, 0, 0};
     long long launches = 0;
     size_t dev_bytes = 0;
     std::vector<void*> allocs;
@@ -385,6 +402,7 @@ EpiArgs epi_args(suppy_ctx* c, int t, const StopParams& sp) {
     e.first_seg = (t == 0);
     e.last_seg = (t == c->nseg - 1);
     e.sp = sp;
+    e.p_target = c->dvc_on ? c->d_target : nullptr;
     return e;
 }
 
@@ -503,9 +521,50 @@ suppy_status enqueue_ext_step(suppy_ctx* c, const suppy_params* p, int t, int np
 }
 
 // One application of T.
+DvcArgs dvc_args(suppy_ctx* c, bool check_stop) {
+    DvcArgs a;
+    a.rp = c->d_qrp;
+    a.col = c->d_qcol;
+    a.val = c->d_qval;
+    a.cp = c->d_qcp;
+    a.crow = c->d_qrow;
+    a.cval = c->d_qcval;
+    a.sptr = c->d_qsptr;
+    a.sdvc = c->d_qsdvc;
+    a.dvc = c->d_qdvc;
+    a.x = c->d_x;
+    a.xw = c->d_x;
+    a.dose = c->d_dose;
+    a.corr = c->d_qcorr;
+    a.pd = c->d_qpd;
+    a.target = c->d_target;
+    a.st = check_stop ? c->d_st : nullptr;
+    a.gamma = c->dvc_gamma;
+    a.mq = c->mq;
+    a.n = c->n;
+    a.nstruct = c->nstruct;
+    a.ndvc = c->ndvc;
+    return a;
+}
+
+// The CQ step of a split problem: doses, projections onto the DVC sets and
+// the target-space proximity, the correction x += gamma A_q^T corr.
+suppy_status enqueue_cq_step(suppy_ctx* c) {
+    const DvcArgs a = dvc_args(c, true);
+    Timed tm{c, 3};
+    CK(tm.begin());
+    CK(launch_dvc_dose(a, c->stream));
+    CK(launch_dvc_project(a, c->stream));
+    CK(launch_dvc_apply(a, c->stream));
+    CK(tm.end());
+    note_launch(c, 4);
+    return SUPPY_OK;
+}
+
 suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     const StopParams sp = stop_params(c, p);
     suppy_status s;
+    if (c->dvc_on && (s = enqueue_cq_step(c)) != SUPPY_OK) return s;
     // EL / EMR: the row pass writes unrelaxed coefficients, the column pass
     // accumulates A^T(.) into delta, and the extrapolated step applies it
     const bool ext = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
@@ -1907,6 +1966,207 @@ suppy_status suppy_update_bounds(suppy_ctx* c, const float* l, const float* u, i
     return load_bounds(c, l, u, on_device);
 }
 
+}  // extern "C"
+
+namespace {
+
+void free_dvc(suppy_ctx* c) {
+    void* bufs[] = {c->d_qrp,   c->d_qcol,  c->d_qval, c->d_qcp,  c->d_qrow,
+                    c->d_qcval, c->d_qsptr, c->d_qsdvc, c->d_qdvc, c->d_dose,
+                    c->d_qcorr, c->d_qpd,   c->d_target};
+    for (void* q : bufs) dfree(c, q);
+    c->d_qrp = c->d_qcol = c->d_qcp = c->d_qrow = c->d_qsptr = c->d_qsdvc = nullptr;
+    c->d_qval = c->d_qcval = c->d_dose = c->d_qcorr = nullptr;
+    c->d_qdvc = nullptr;
+    c->d_qpd = c->d_target = nullptr;
+    c->dvc_on = false;
+    c->mq = c->nstruct = c->ndvc = 0;
+    c->dvc_gamma = 0.f;
+}
+
+template <typename T>
+suppy_status to_host(suppy_ctx* c, const T* src, size_t count, int on_device, std::vector<T>& out) {
+    out.resize(count);
+    if (!count) return SUPPY_OK;
+    if (!src) return fail(c, SUPPY_EINVAL, "a DVC matrix array is NULL");
+    if (on_device) CK(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
+    else std::memcpy(out.data(), src, count * sizeof(T));
+    return SUPPY_OK;
+}
+
+template <typename T>
+suppy_status upload(suppy_ctx* c, const std::vector<T>& v, T** out) {
+    suppy_status s = dalloc(c, out, v.size());
+    if (s != SUPPY_OK) return s;
+    if (!v.empty())
+        CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr, int32_t nstruct,
+                          const suppy_dvc* dvc, int32_t ndvc, double relax) {
+    if (ndvc < 0) return fail(c, SUPPY_EINVAL, "ndvc must be >= 0");
+    if (ndvc > 0) {
+        if (c->B_user != 1 || c->B != 1)
+            return fail(c, SUPPY_EINVAL, "split feasibility needs a context with one right-hand side");
+        if (!A || !sptr || !dvc) return fail(c, SUPPY_EINVAL, "Aq, structure_ptr and dvc must be given");
+        if (A->n != c->n) return fail(c, SUPPY_EINVAL, "Aq must have the context's n columns");
+        if (A->m < 1 || A->nnz < 0 || A->nnz >= (1LL << 31))
+            return fail(c, SUPPY_EINVAL, "Aq needs m >= 1 rows and 0 <= nnz < 2^31");
+        if (nstruct < 1) return fail(c, SUPPY_EINVAL, "nstruct must be >= 1");
+        if (!(relax > 0.0 && relax < 2.0)) return fail(c, SUPPY_EINVAL, "relax must lie in (0, 2)");
+    }
+    const int mq = ndvc > 0 ? A->m : 0, n = c->n;
+    std::vector<int> rp, col, st(nstruct > 0 && ndvc > 0 ? nstruct + 1 : 0);
+    std::vector<float> val;
+    std::vector<DvcDesc> desc;
+    std::vector<int> sdvc;
+    suppy_status s;
+    if (ndvc > 0) {
+        for (int k = 0; k <= nstruct; ++k) st[k] = sptr[k];
+        if (st[0] != 0 || st[nstruct] != mq)
+            return fail(c, SUPPY_EINVAL, "structure_ptr must start at 0 and end at m_q");
+        for (int k = 0; k < nstruct; ++k)
+            if (st[k + 1] < st[k]) return fail(c, SUPPY_EINVAL, "structure_ptr must be nondecreasing");
+        if ((s = to_host(c, A->row_ptr, (size_t)mq + 1, A->on_device, rp)) != SUPPY_OK) return s;
+        if (rp[0] != 0 || rp[mq] != A->nnz)
+            return fail(c, SUPPY_EINVAL, "Aq row_ptr must start at 0 and end at nnz");
+        for (int i = 0; i < mq; ++i)
+            if (rp[i + 1] < rp[i]) return fail(c, SUPPY_EINVAL, "Aq row_ptr must be nondecreasing");
+        if ((s = to_host(c, A->col, (size_t)A->nnz, A->on_device, col)) != SUPPY_OK) return s;
+        if ((s = to_host(c, A->val, (size_t)A->nnz, A->on_device, val)) != SUPPY_OK) return s;
+        for (long long e = 0; e < A->nnz; ++e) {
+            if (col[e] < 0 || col[e] >= n) return fail(c, SUPPY_EINVAL, "Aq column index out of range");
+            if (!std::isfinite(val[e])) return fail(c, SUPPY_EINVAL, "Aq values must be finite");
+        }
+        // DVCs grouped by structure, caller order kept inside a structure
+        std::vector<int> order(ndvc);
+        for (int j = 0; j < ndvc; ++j) {
+            const suppy_dvc& q = dvc[j];
+            if (q.kind != SUPPY_DVC_UPPER && q.kind != SUPPY_DVC_LOWER)
+                return fail(c, SUPPY_EINVAL, "dvc kind must be SUPPY_DVC_UPPER or SUPPY_DVC_LOWER");
+            if (q.structure < 0 || q.structure >= nstruct)
+                return fail(c, SUPPY_EINVAL, "dvc structure out of range");
+            if (!(q.volume >= 0.0 && q.volume <= 1.0))
+                return fail(c, SUPPY_EINVAL, "dvc volume must lie in [0, 1]");
+            if (!std::isfinite(q.d_ref)) return fail(c, SUPPY_EINVAL, "dvc d_ref must be finite");
+            order[j] = j;
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return dvc[a].structure < dvc[b].structure; });
+        sdvc.assign(nstruct + 1, 0);
+        for (int j = 0; j < ndvc; ++j) sdvc[dvc[j].structure + 1]++;
+        for (int k = 0; k < nstruct; ++k) sdvc[k + 1] += sdvc[k];
+        for (int j : order) {
+            const suppy_dvc& q = dvc[j];
+            const double N = (double)(st[q.structure + 1] - st[q.structure]);
+            const double vN = q.volume * N;
+            DvcDesc d;
+            d.kind = q.kind;
+            d.K = (int)(q.kind == SUPPY_DVC_UPPER ? std::floor(vN) : std::ceil(vN));
+            d.orig = j;
+            d.pad = 0;
+            d.w = 1.0 / (double)ndvc;
+            d.d_ref = q.d_ref;
+            desc.push_back(d);
+        }
+    }
+    // the old sets (if any) go; graphs captured with them too
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_key.clear();
+    }
+    free_dvc(c);
+    if (ndvc == 0) return SUPPY_OK;
+
+    // CSC copy (rows ascending inside a column)
+    std::vector<int> cp(n + 1, 0), crow(A->nnz);
+    std::vector<float> cval(A->nnz);
+    for (long long e = 0; e < A->nnz; ++e) cp[col[e] + 1]++;
+    for (int j = 0; j < n; ++j) cp[j + 1] += cp[j];
+    {
+        std::vector<int> cur(cp.begin(), cp.end() - 1);
+        for (int i = 0; i < mq; ++i)
+            for (int e = rp[i]; e < rp[i + 1]; ++e) {
+                const int k = cur[col[e]]++;
+                crow[k] = i;
+                cval[k] = val[e];
+            }
+    }
+    if ((s = upload(c, rp, &c->d_qrp)) != SUPPY_OK || (s = upload(c, col, &c->d_qcol)) != SUPPY_OK ||
+        (s = upload(c, val, &c->d_qval)) != SUPPY_OK || (s = upload(c, cp, &c->d_qcp)) != SUPPY_OK ||
+        (s = upload(c, crow, &c->d_qrow)) != SUPPY_OK || (s = upload(c, cval, &c->d_qcval)) != SUPPY_OK ||
+        (s = upload(c, st, &c->d_qsptr)) != SUPPY_OK || (s = upload(c, sdvc, &c->d_qsdvc)) != SUPPY_OK ||
+        (s = upload(c, desc, &c->d_qdvc)) != SUPPY_OK) {
+        free_dvc(c);
+        return s;
+    }
+    if ((s = dalloc(c, &c->d_dose, (size_t)mq)) != SUPPY_OK || (s = dalloc(c, &c->d_qcorr, (size_t)mq)) != SUPPY_OK ||
+        (s = dalloc(c, &c->d_qpd, (size_t)ndvc + (size_t)nstruct)) != SUPPY_OK ||
+        (s = dalloc(c, &c->d_target, 1)) != SUPPY_OK) {
+        free_dvc(c);
+        return s;
+    }
+    // step size: gamma = relax / sum_j w_j ||A_j||_F^2 (per-structure norms on the device)
+    double* d_frob = c->d_qpd + ndvc;
+    CK(launch_dvc_frob(c->d_qrp, c->d_qval, c->d_qsptr, nstruct, d_frob, c->stream));
+    note_launch(c);
+    std::vector<double> frob(nstruct);
+    CK(cudaMemcpyAsync(frob.data(), d_frob, sizeof(double) * nstruct, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemsetAsync(c->d_target, 0, sizeof(double), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    double L = 0.0;
+    for (int j = 0; j < ndvc; ++j) L += (1.0 / (double)ndvc) * frob[dvc[j].structure];
+    if (!(L > 0.0)) {
+        free_dvc(c);
+        return fail(c, SUPPY_EINVAL, "the rows of the constrained structures are all zero");
+    }
+    c->mq = mq;
+    c->nstruct = nstruct;
+    c->ndvc = ndvc;
+    c->dvc_gamma = (float)(relax / L);
+    c->dvc_on = true;
+    return SUPPY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+suppy_status suppy_set_dvc(suppy_ctx* c, const suppy_csr* Aq, const int32_t* structure_ptr,
+                           int32_t nstruct, const suppy_dvc* dvc, int32_t ndvc, double relax) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    return set_dvc_impl(c, Aq, structure_ptr, nstruct, dvc, ndvc, relax);
+}
+
+suppy_status suppy_dvc_dose(suppy_ctx* c, float* dose, int32_t on_device) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!c->dvc_on) return fail(c, SUPPY_ESTATE, "no dose-volume constraints are set");
+    if (!dose) return fail(c, SUPPY_EINVAL, "dose is NULL");
+    CK(launch_dvc_dose(dvc_args(c, false), c->stream));
+    note_launch(c);
+    CK(cudaMemcpyAsync(dose, c->d_dose, sizeof(float) * c->mq,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) CK(cudaStreamSynchronize(c->stream));
+    return SUPPY_OK;
+}
+
+suppy_status suppy_dvc_proximity(suppy_ctx* c, double* out) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (!c->dvc_on) return fail(c, SUPPY_ESTATE, "no dose-volume constraints are set");
+    if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
+    const DvcArgs a = dvc_args(c, false);
+    CK(launch_dvc_dose(a, c->stream));
+    CK(launch_dvc_project(a, c->stream));
+    note_launch(c, 3);
+    CK(cudaMemcpyAsync(c->h_out, c->d_target, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    *out = c->h_out[0];
+    return SUPPY_OK;
+}
+
 suppy_status suppy_set_x(suppy_ctx* c, const float* x, int32_t on_device) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!x) return fail(c, SUPPY_EINVAL, "x is NULL");
@@ -2177,7 +2437,7 @@ suppy_status suppy_timing_enable(suppy_ctx* c, int32_t enable) {
     suppy_status s = flush_timing(c);
     if (s != SUPPY_OK) return s;
     c->timing = enable != 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         c->timing_ms[k] = 0.0;
         c->timing_n[k] = 0;
     }
@@ -2186,7 +2446,7 @@ suppy_status suppy_timing_enable(suppy_ctx* c, int32_t enable) {
 
 suppy_status suppy_kernel_time(suppy_ctx* c, int32_t kind, double* total_ms, int64_t* launches) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
-    if (kind < 0 || kind > 2) return fail(c, SUPPY_EINVAL, "kernel kind must be 0, 1 or 2");
+    if (kind < 0 || kind > 3) return fail(c, SUPPY_EINVAL, "kernel kind must be 0, 1, 2 or 3");
     suppy_status s = flush_timing(c);
     if (s != SUPPY_OK) return s;
     if (total_ms) *total_ms = c->timing_ms[kind];

@@ -84,6 +84,7 @@ struct EpiArgs {
     int hist_cap;
     int first_seg, last_seg;
     StopParams sp;
+    const double* p_target;  // split problems: the monitored proximity (B = 1), else null
 };
 
 struct FinalizeArgs {
@@ -301,6 +302,43 @@ cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val,
                            double* c64, float* c32, double* work, int work_ctas,
                            cudaStream_t s);
 cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s);
+
+// Split feasibility: one dose-volume constraint, in structure order.
+struct DvcDesc {
+    int kind;               // 0: upper (at most K above d_ref), 1: lower (at least K at or above)
+    int K;                  // voxel count of the constraint
+    int orig;               // position in the caller's list (proximity order)
+    int pad;
+    double w;               // weight 1 / ndvc
+    double d_ref;
+};
+
+struct DvcArgs {
+    const int* rp;          // CSR of A_q: row_ptr (m_q + 1), col, val
+    const int* col;
+    const float* val;
+    const int* cp;          // CSC of A_q: col_ptr (n + 1), row, val
+    const int* crow;
+    const float* cval;
+    const int* sptr;        // structure row ranges (nstruct + 1)
+    const int* sdvc;        // DVCs of structure s: dvc[sdvc[s] .. sdvc[s+1])
+    const DvcDesc* dvc;
+    const float* x;         // iterate read by the dose pass
+    float* xw;              // iterate updated by the correction pass
+    float* dose;            // m_q
+    float* corr;            // m_q: sum_j w_j (P_Qj(d) - d)
+    double* pd;             // per DVC: 1/2 w_j ||P_Qj(d) - d||^2 (caller order)
+    double* target;         // their sum
+    const RhsState* st;     // skip when right-hand side 0 has stopped, or null
+    float gamma;
+    int mq, n, nstruct, ndvc;
+};
+
+cudaError_t launch_dvc_dose(const DvcArgs& a, cudaStream_t s);
+cudaError_t launch_dvc_project(const DvcArgs& a, cudaStream_t s);   // + the proximity sum
+cudaError_t launch_dvc_apply(const DvcArgs& a, cudaStream_t s);
+cudaError_t launch_dvc_frob(const int* rp, const float* val, const int* sptr, int nstruct,
+                            double* out, cudaStream_t s);
 
 // Checked build (-DSUPPY_CHECKED): kernels verify indices and the alignment of
 // vector accesses before issuing them; the first violation is recorded in a

@@ -120,7 +120,7 @@ __device__ void sweep_epilogue(const EpiArgs& a) {
         if (a.first_seg) st.p_acc = 0.0;
         st.p_acc += a.scale * s;
         if (!a.last_seg) continue;
-        const double p = st.p_acc;
+        const double p = a.p_target ? a.p_target[b] : st.p_acc;
         const int k = st.k;
         if (k < a.hist_cap) {
             a.prox_hist[(size_t)b * a.hist_cap + k] = p;

@@ -394,6 +394,34 @@ def rt_problem(nx: int = 100, ny: int = 60, nz: int = 50, nbeam: int = 9, ns: in
                              voxels=(nx, ny, nz), beamlets=nbl))
 
 
+def rt_split_problem(presc: float = 60.0, oar2_cap: float = 30.0, **geo) -> Problem:
+    """The horseshoe plan as a split-feasibility problem: the constraint table
+    of the horseshoe case in the paper's radiotherapy section, with doses
+    scaled from its 2 Gy prescription to ``presc``.
+
+    Hyperslab rows (input-space sets): target voxels in [0.965, 1.135] presc
+    and OAR2 voxels below ``oar2_cap``.  Dose-volume sets (target space) on the
+    rows of ``meta["split"]["Aq"]``, structure 0 = target, 1 = core (OAR1):
+    target D95 >= presc and D5 <= 1.085 presc, core D5 <= 0.165 presc, given as
+    (kind, structure, volume, d_ref) with kind 0 = at most (upper), 1 = at
+    least (lower).  ``geo`` is passed to ``rt_problem``.
+    """
+    base = rt_problem(presc=presc, **geo)
+    nt, n1, n2 = base.meta["n_target"], base.meta["n_oar1"], base.meta["n_oar2"]
+    A = base.A
+    rows = np.concatenate([np.arange(nt), np.arange(nt + n1, nt + n1 + n2)])
+    Ac = A.rows(rows)
+    l = np.concatenate([np.full(nt, 0.965 * presc), np.full(n2, -np.inf)]).astype(np.float32)
+    u = np.concatenate([np.full(nt, 1.135 * presc), np.full(n2, oar2_cap)]).astype(np.float32)
+    blocks = np.concatenate([np.zeros(nt), np.ones(n2)]).astype(np.int32)
+    Aq = A.rows(np.arange(nt + n1))
+    dvcs = [(1, 0, 0.95, presc), (0, 0, 0.05, 1.085 * presc), (0, 1, 0.05, 0.165 * presc)]
+    meta = dict(base.meta)
+    meta["split"] = dict(Aq=Aq, sptr=np.array([0, nt, nt + n1], np.int32), dvcs=dvcs)
+    return Problem("rt_split", Ac, l, u, base.box_lo, base.box_hi, blocks=blocks,
+                   body=base.body, meta=meta)
+
+
 # ------------------------------------------------------ small test shapes --
 
 def random_csr(m: int, n: int, seed: int, mean_len: float = 20.0, max_len: int | None = None,

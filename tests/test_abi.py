@@ -63,6 +63,9 @@ def test_create_rejects_null_arguments_without_a_device(lib):
 def test_null_context_calls_fail_cleanly(lib):
     import paper_2606_27086_gb300 as pk
     assert lib.suppy_proximity(None, None) == pk.SUPPY_EINVAL
+    assert lib.suppy_set_dvc(None, None, None, 0, None, 0, 1.0) == pk.SUPPY_EINVAL
+    assert lib.suppy_dvc_dose(None, None, 0) == pk.SUPPY_EINVAL
+    assert lib.suppy_dvc_proximity(None, None) == pk.SUPPY_EINVAL
     assert lib.suppy_launch_count(None) == 0
     lib.suppy_destroy(None)
 
@@ -75,7 +78,7 @@ def test_ctypes_structs_match_the_c_layout(tmp_path):
     structs = {"suppy_csr": pk.suppy_csr, "suppy_opts": pk.suppy_opts,
                "suppy_params": pk.suppy_params, "suppy_stats": pk.suppy_stats,
                "suppy_info": pk.suppy_info, "suppy_server_opts": pk.suppy_server_opts,
-               "suppy_request_info": pk.suppy_request_info}
+               "suppy_request_info": pk.suppy_request_info, "suppy_dvc": pk.suppy_dvc}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "suppy.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
