@@ -142,6 +142,8 @@ struct suppy_ctx {
     bool dvc_on = false;
     int mq = 0, nstruct = 0, ndvc = 0;
     float dvc_gamma = 0.f;
+    size_t dvc_smem = 0;
+    long long dvc_nnz = 0;
     int* d_qrp = nullptr;
     int* d_qcol = nullptr;
     float* d_qval = nullptr;
@@ -544,6 +546,8 @@ DvcArgs dvc_args(suppy_ctx* c, bool check_stop) {
     a.n = c->n;
     a.nstruct = c->nstruct;
     a.ndvc = c->ndvc;
+    a.smem = c->dvc_smem;
+    a.nnz = c->dvc_nnz;
     return a;
 }
 
@@ -1970,6 +1974,15 @@ suppy_status suppy_update_bounds(suppy_ctx* c, const float* l, const float* u, i
 
 namespace {
 
+// Order-preserving key of a float (the device's dose keys): larger value,
+// larger key; -0 and +0 share a key.
+uint32_t float_key(float f) {
+    if (f == 0.0f) f = 0.0f;
+    uint32_t b;
+    std::memcpy(&b, &f, sizeof(b));
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
 void free_dvc(suppy_ctx* c) {
     void* bufs[] = {c->d_qrp,   c->d_qcol,  c->d_qval, c->d_qcp,  c->d_qrow,
                     c->d_qcval, c->d_qsptr, c->d_qsdvc, c->d_qdvc, c->d_dose,
@@ -1980,6 +1993,7 @@ void free_dvc(suppy_ctx* c) {
     c->d_qdvc = nullptr;
     c->d_qpd = c->d_target = nullptr;
     c->dvc_on = false;
+    c->dvc_smem = 0;
     c->mq = c->nstruct = c->ndvc = 0;
     c->dvc_gamma = 0.f;
 }
@@ -2065,8 +2079,15 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
             d.kind = q.kind;
             d.K = (int)(q.kind == SUPPY_DVC_UPPER ? std::floor(vN) : std::ceil(vN));
             d.orig = j;
-            d.pad = 0;
+            float lo_f = (float)q.d_ref, hi_f = (float)q.d_ref;
+            if ((double)lo_f > q.d_ref) lo_f = std::nextafter(lo_f, -INFINITY);
+            if ((double)hi_f < q.d_ref) hi_f = std::nextafter(hi_f, INFINITY);
+            d.key_gt = float_key(lo_f);
+            d.key_ge = float_key(hi_f);
+            d.ref_hi = (float)q.d_ref;
+            d.ref_lo = (float)(q.d_ref - (double)d.ref_hi);
             d.w = 1.0 / (double)ndvc;
+            d.wf = (float)d.w;
             d.d_ref = q.d_ref;
             desc.push_back(d);
         }
@@ -2104,19 +2125,32 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
         return s;
     }
     if ((s = dalloc(c, &c->d_dose, (size_t)mq)) != SUPPY_OK || (s = dalloc(c, &c->d_qcorr, (size_t)mq)) != SUPPY_OK ||
-        (s = dalloc(c, &c->d_qpd, (size_t)ndvc + (size_t)nstruct)) != SUPPY_OK ||
+        (s = dalloc(c, &c->d_qpd, (size_t)ndvc * kDvcCluster)) != SUPPY_OK ||
         (s = dalloc(c, &c->d_target, 1)) != SUPPY_OK) {
         free_dvc(c);
         return s;
     }
     // step size: gamma = relax / sum_j w_j ||A_j||_F^2 (per-structure norms on the device)
-    double* d_frob = c->d_qpd + ndvc;
-    CK(launch_dvc_frob(c->d_qrp, c->d_qval, c->d_qsptr, nstruct, d_frob, c->stream));
-    note_launch(c);
+    double* d_frob = nullptr;
+    if ((s = dalloc(c, &d_frob, (size_t)nstruct * 33)) != SUPPY_OK) {
+        free_dvc(c);
+        return s;
+    }
+    cudaError_t fe = launch_dvc_frob(c->d_qrp, c->d_qval, c->d_qsptr, nstruct, d_frob + nstruct,
+                                     d_frob, c->stream);
+    note_launch(c, 2);
     std::vector<double> frob(nstruct);
-    CK(cudaMemcpyAsync(frob.data(), d_frob, sizeof(double) * nstruct, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemsetAsync(c->d_target, 0, sizeof(double), c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    if (fe == cudaSuccess)
+        fe = cudaMemcpyAsync(frob.data(), d_frob, sizeof(double) * nstruct, cudaMemcpyDeviceToHost,
+                             c->stream);
+    if (fe == cudaSuccess) fe = cudaMemsetAsync(c->d_target, 0, sizeof(double), c->stream);
+    if (fe == cudaSuccess) fe = cudaStreamSynchronize(c->stream);
+    dfree(c, d_frob);
+    if (fe != cudaSuccess) {
+        free_dvc(c);
+        cudaGetLastError();
+        return fail(c, SUPPY_ECUDA, std::string("DVC norms: ") + cudaGetErrorString(fe));
+    }
     double L = 0.0;
     for (int j = 0; j < ndvc; ++j) L += (1.0 / (double)ndvc) * frob[dvc[j].structure];
     if (!(L > 0.0)) {
@@ -2127,6 +2161,10 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
     c->nstruct = nstruct;
     c->ndvc = ndvc;
     c->dvc_gamma = (float)(relax / L);
+    int max_rows = 0;
+    for (int k = 0; k < nstruct; ++k) max_rows = std::max(max_rows, st[k + 1] - st[k]);
+    c->dvc_smem = dvc_project_smem(max_rows);
+    c->dvc_nnz = A->nnz;
     c->dvc_on = true;
     return SUPPY_OK;
 }

@@ -304,11 +304,16 @@ cudaError_t launch_colmean(const int* row_ptr, const int* col, const float* val,
 cudaError_t launch_sumsq(const double* v, int n, double* out, cudaStream_t s);
 
 // Split feasibility: one dose-volume constraint, in structure order.
+// Doses are compared with d_ref through order-preserving keys of floats:
+// d > d_ref iff key(d) > key_gt (key of the largest float <= d_ref), d >= d_ref
+// iff key(d) >= key_ge (key of the smallest float >= d_ref).
 struct DvcDesc {
     int kind;               // 0: upper (at most K above d_ref), 1: lower (at least K at or above)
     int K;                  // voxel count of the constraint
     int orig;               // position in the caller's list (proximity order)
-    int pad;
+    uint32_t key_gt, key_ge;
+    float ref_hi, ref_lo;   // d_ref as float-float
+    float wf;               // w as float
     double w;               // weight 1 / ndvc
     double d_ref;
 };
@@ -327,18 +332,26 @@ struct DvcArgs {
     float* xw;              // iterate updated by the correction pass
     float* dose;            // m_q
     float* corr;            // m_q: sum_j w_j (P_Qj(d) - d)
-    double* pd;             // per DVC: 1/2 w_j ||P_Qj(d) - d||^2 (caller order)
+    double* pd;             // per DVC (caller order) x cluster rank: chunk sums of the
+                            // squared corrections
     double* target;         // their sum
     const RhsState* st;     // skip when right-hand side 0 has stopped, or null
     float gamma;
     int mq, n, nstruct, ndvc;
+    long long nnz;          // entries of A_q
+    size_t smem;            // dynamic shared memory of the projection (keys staged), or 0
 };
+
+constexpr int kDvcCluster = 8;                // CTAs (one cluster) per structure
+constexpr size_t kDvcSmemMax = 192 * 1024;   // structures up to 8 x 49152 rows stage their keys
+size_t dvc_project_smem(int max_rows);
 
 cudaError_t launch_dvc_dose(const DvcArgs& a, cudaStream_t s);
 cudaError_t launch_dvc_project(const DvcArgs& a, cudaStream_t s);   // + the proximity sum
 cudaError_t launch_dvc_apply(const DvcArgs& a, cudaStream_t s);
+// part: nstruct x 32 chunk sums (scratch), out: nstruct norms
 cudaError_t launch_dvc_frob(const int* rp, const float* val, const int* sptr, int nstruct,
-                            double* out, cudaStream_t s);
+                            double* part, double* out, cudaStream_t s);
 
 // Checked build (-DSUPPY_CHECKED): kernels verify indices and the alignment of
 // vector accesses before issuing them; the first violation is recorded in a

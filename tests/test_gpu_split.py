@@ -18,6 +18,10 @@ pk = pytest.importorskip("paper_2606_27086_gb300")
 pytestmark = pytest.mark.gpu
 
 F32 = np.float32
+# The device sums the squared corrections in float-float arithmetic (about 44
+# significant bits) over short per-thread runs and a fixed-order tree: the
+# proximity carries a relative error of a few 2^-44 at most.
+PROX_TOL = 1e-11
 
 
 def _identity_ctx(Aq, n, obj=None):
@@ -76,7 +80,23 @@ def test_cq_step_is_exact_on_integer_doses_with_ties(seed):
     assert len(np.unique(d)) < len(d) // 4            # ties are common
     xo, po = O.cq_step(SS, x.astype(np.float64))
     assert po > 0
-    assert rel(p_gpu, po) < 1e-13
+    assert rel(p_gpu, po) < PROX_TOL
+    assert rel_l2(xg, xo) < 2e-6
+
+
+def test_cq_step_on_a_structure_too_large_for_shared_memory():
+    """A structure of 60000 rows (its keys do not fit in shared memory: every
+    pass re-reads the doses) next to a small one; exact decisions as above."""
+    A, sptr, x = _integer_case(21, [60000, 40], mean_len=8)
+    d0 = A.to_scipy() @ x.astype(np.float64)
+    dvcs = [(0, 0, 0.15, float(np.quantile(d0[:60000], 0.5))),
+            (1, 0, 0.7, float(np.quantile(d0[:60000], 0.4)) + 0.5),
+            (0, 1, 0.1, float(np.quantile(d0[60000:], 0.3)))]
+    d, d_exact, p_gpu, xg, SS = _step_compare(A, sptr, dvcs, x, 1.0)
+    assert np.array_equal(d.astype(np.float64), d_exact)
+    xo, po = O.cq_step(SS, x.astype(np.float64))
+    assert po > 0
+    assert rel(p_gpu, po) < PROX_TOL
     assert rel_l2(xg, xo) < 2e-6
 
 
@@ -98,7 +118,7 @@ def test_cq_step_on_float_doses_decides_like_the_oracle(seed):
     d, d_exact, p_gpu, xg, SS = _step_compare(A, sptr, dvcs, x, 1.0)
     assert rel_l2(d, d_exact) < 1e-6
     c, po = O.dvc_corrections(SS, d.astype(np.float64))
-    assert rel(p_gpu, po) < 1e-12
+    assert rel(p_gpu, po) < PROX_TOL
     xo = x.astype(np.float64) + SS.gamma * (SS.Aq.T @ c)
     assert rel_l2(xg, xo) < 2e-6
 
@@ -113,7 +133,7 @@ def test_extreme_volumes_and_satisfied_constraints():
                  [(0, 0, 0.5, float(d0.max()) + 1.0), (1, 1, 0.5, float(d0.min()) - 1.0)]):
         d, d_exact, p_gpu, xg, SS = _step_compare(A, sptr, dvcs, x, 1.0)
         xo, po = O.cq_step(SS, x.astype(np.float64))
-        assert rel(p_gpu, po) < 1e-13 if po > 0 else p_gpu == 0.0
+        assert rel(p_gpu, po) < PROX_TOL if po > 0 else p_gpu == 0.0
         if po == 0:
             assert np.array_equal(xg, x)
         else:
