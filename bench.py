@@ -647,7 +647,9 @@ def profile_case(case: int, steps: int) -> int:
     """A short run for ncu.  Cases 1 / 2: CT 384x384 (A ~0.4 GB, above L2; the
     device holds about 1 GB) with the one- / two-pass sweep.  Case 3: the CT
     512x512 workload with the sweep and launch shapes bench.py uses (two
-    passes, shapes tuned at create); case 4: the same with the one-pass sweep.
+    passes, shapes tuned at create); case 4: the same with the one-pass sweep;
+    case 5: the horseshoe radiotherapy plan as a split problem (dose-volume
+    sets by the CQ step, slabs by EMR, mean-dose perturbations).
     The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches."""
     import torch
@@ -655,7 +657,15 @@ def profile_case(case: int, steps: int) -> int:
     from paper_2606_27086_gb300 import build as pkbuild
     pkbuild.build()
     import paper_2606_27086_gb300 as pk
-    if case in (3, 4):
+    params = SUP
+    if case == 5:
+        prob = synth.rt_split_problem()
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_LINEAR, mode=pk.SUPPY_EMR)
+        sp = prob.meta["split"]
+        Aq = sp["Aq"]
+        ctx.suppy_set_dvc(Aq.row_ptr, Aq.col, Aq.val, Aq.m, sp["sptr"], sp["dvcs"], 1.0)
+        params = dict(gamma=1.0, alpha=0.7, n_red=1, restart_every=500)
+    elif case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
                               strategy=pk.STRATEGY_TWO_PASS if case == 3 else
@@ -668,7 +678,7 @@ def profile_case(case: int, steps: int) -> int:
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx:
         nvtx.range_push("profile")
-    ctx.suppy_run(pk.suppy_params_default(max_sweeps=steps, use_graphs=0, **SUP))
+    ctx.suppy_run(pk.suppy_params_default(max_sweeps=steps, use_graphs=0, **params))
     torch.cuda.synchronize()
     if nvtx:
         nvtx.range_pop()
@@ -691,11 +701,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
                          "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
-                         "pass")
+                         "pass; 5 the horseshoe split problem (DVCs by the CQ step)")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6)
