@@ -31,7 +31,8 @@ constrained physical problems with SupPy"):
   horseshoe plan's constraints), x <- x + gamma sum_j w_j A_j^T (P_Qj(A_j x) -
   A_j x);
 * superiorization -- Algorithm 1 with the power-law step beta = gamma alpha^l
-  and the normalised subgradient direction of Sec. 2.1.2;
+  and the normalised subgradient direction of Sec. 2.1.2, or the adaptive
+  step beta = (f(x) - f_ref)/||g|| of Nikazad et al. (Sec. 2.1.2, Q29);
 * stopping -- Sec. 2.2.1 (P <= P*, relative proximity change below dP* for N
   consecutive iterations, N_max) and Sec. 2.2.3 (relative objective change);
 * objectives -- isotropic TV, Eq. (TV) with the subgradient of the Combettes /
@@ -64,7 +65,10 @@ ranked by voxel index.  Q27 split iteration: the CQ step with weights
 w_j = 1/t over the t DVCs and gamma = relax / sum_j w_j ||A_j||_F^2, then the
 feasibility sweep over the slabs (P_C), then the box.  Q28 with a split problem
 the stopping rule and the recorded proximity use the target-space proximity
-1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 (Sec. 2.2.1).
+1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 (Sec. 2.2.1).  Q29 adaptive step
+(Nikazad et al., Sec. 2.1.2): f_ref, "automatically updated", is taken as the
+lowest objective value at the start of a perturbation phase so far (or a
+value the caller fixes); one step per reduction, kept when f(z) <= f(y).
 
 Parity of the whole superiorized run against printed values is unpinned: the
 paper prints no iterates for this path.
@@ -495,6 +499,8 @@ class Params:
     obj_rel: float = 1e-6
     use_stopping: bool = False      # False: run exactly max_sweeps sweeps
     variance_tol: float = 0.0       # > 0: the variance stopping rule (Sec. 3.2, CT study)
+    adaptive: int = 0               # 1: adaptive step, f_ref automatic (Q29); 2: f_ref fixed
+    f_ref: float = 0.0              # the reference value when adaptive == 2
 
 
 @dataclass
@@ -502,6 +508,40 @@ class PertState:
     ell: int = 0
     restarts: int = 0
     last_restart_k: int = 0
+    f_best: float | None = None     # adaptive step: lowest objective at a phase start
+
+
+def adaptive_phase(obj: Objective, y: np.ndarray, st: PertState, P: Params) -> tuple:
+    """The perturbation phase with the adaptive step of Nikazad et al.
+    (Sec. 2.1.2): beta = (f(y) - f_ref)/||g|| when f(y) > f_ref, else no step,
+    i.e. the subgradient projection of y onto the level set {f <= f_ref} of
+    the linearisation of f at y.  Reading Q29: f_ref is the lowest objective
+    value seen at the start of a perturbation phase so far, this phase's
+    included (adaptive = 1), or a fixed value (adaptive = 2); each of the n_red
+    reduction steps takes this one step and keeps it when f(z) <= f(y)
+    (Algorithm 1's test), else the phase ends; l is not used."""
+    f0 = obj.f(y)
+    if P.adaptive == 2:
+        f_ref = P.f_ref
+    else:
+        st.f_best = f0 if st.f_best is None else min(st.f_best, f0)
+        f_ref = st.f_best
+    n = trials = 0
+    while n < P.n_red:
+        g = obj.g(y)
+        gn = float(np.sqrt(g @ g))
+        fy = obj.f(y)
+        if gn == 0.0 or fy <= f_ref:
+            break
+        beta = (fy - f_ref) / gn
+        z = y - beta * g / gn
+        trials += 1
+        if obj.f(z) <= fy:
+            y = z
+            n += 1
+        else:
+            break
+    return y, n, trials
 
 
 def perturbation_phase(obj: Objective, y: np.ndarray, st: PertState, P: Params) -> tuple:
@@ -512,6 +552,8 @@ def perturbation_phase(obj: Objective, y: np.ndarray, st: PertState, P: Params) 
     z = y + beta v, accept when f(z) <= f(y) (Algorithm 1); after max_trials
     rejected trials the phase ends (Q6).  Returns (y, accepted, trials).
     """
+    if P.adaptive:
+        return adaptive_phase(obj, y, st, P)
     n = 0
     trials = 0
     while n < P.n_red:

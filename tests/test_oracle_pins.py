@@ -855,3 +855,78 @@ def test_cq_step_is_the_identity_when_every_dvc_holds():
     SS = O.split_setup(sp.csr_matrix(A), sptr, dv, 1.0)
     xn, p = O.cq_step(SS, x)
     assert p == 0.0 and np.array_equal(xn, x)
+
+
+# ------------------------------------------------ adaptive step (Nikazad) --
+
+def test_adaptive_step_lands_on_the_reference_level_of_a_linear_objective():
+    """For f = c.x the linearisation is exact: one adaptive step
+    beta = (f(y) - f_ref)/||g|| along -g/||g|| reaches f(z) = f_ref."""
+    rng = np.random.default_rng(41)
+    c = rng.uniform(0.1, 1.0, 30)
+    obj = O.Objective(O.OBJ_LINEAR, c=c)
+    y = rng.uniform(0, 2, 30)
+    f_ref = 0.6 * float(c @ y)
+    P = O.Params(adaptive=2, f_ref=f_ref, n_red=1)
+    z, acc, tri = O.perturbation_phase(obj, y, O.PertState(), P)
+    assert acc == 1 and tri == 1
+    assert np.isclose(c @ z, f_ref, rtol=1e-13)
+    # below the reference level nothing moves
+    z2, acc2, tri2 = O.perturbation_phase(obj, y, O.PertState(), O.Params(adaptive=2, f_ref=2 * c @ y))
+    assert acc2 == 0 and tri2 == 0 and np.array_equal(z2, y)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_adaptive_step_is_the_projection_onto_the_linearised_level_set(seed):
+    """The step is the Euclidean projection of y onto {u : f(y) + g.(u - y) <=
+    f_ref} (SLSQP on the constrained least-distance problem), here for the
+    L1 norm with its subgradient sign(y)."""
+    rng = np.random.default_rng(60 + seed)
+    y = rng.standard_normal(6)
+    obj = O.Objective(O.OBJ_L1)
+    f_ref = 0.5 * float(np.abs(y).sum())
+    z, acc, _ = O.perturbation_phase(obj, y, O.PertState(), O.Params(adaptive=2, f_ref=f_ref))
+    g = np.sign(y)
+    fy = float(np.abs(y).sum())
+    res = so.minimize(lambda u: np.sum((u - y) ** 2), y.copy(), method="SLSQP",
+                      constraints=[{"type": "ineq", "fun": lambda u: f_ref - fy - g @ (u - y)}],
+                      options={"ftol": 1e-14, "maxiter": 500})
+    assert acc == 1
+    assert np.allclose(z, res.x, atol=1e-6)
+
+
+def test_adaptive_steps_never_move_away_from_the_level_set():
+    """Subgradient projections are Fejer monotone with respect to the level
+    set: for the convex L1 norm and f_ref >= 0 every point u with
+    ||u||_1 <= f_ref (here u = 0) gets no farther away, step after step."""
+    rng = np.random.default_rng(71)
+    y = rng.standard_normal(40) * 3
+    f0 = np.abs(y).sum()
+    obj = O.Objective(O.OBJ_L1)
+    P = O.Params(adaptive=2, f_ref=1.0, n_red=1)
+    prev = np.linalg.norm(y)
+    for _ in range(50):
+        y, acc, _ = O.perturbation_phase(obj, y, O.PertState(), P)
+        cur = np.linalg.norm(y)
+        assert cur <= prev * (1 + 1e-12)
+        prev = cur
+    assert np.abs(y).sum() < 0.1 * f0
+
+
+def test_adaptive_reference_is_the_lowest_phase_start_objective():
+    """Q29: with the automatic reference the first phase takes no step
+    (f(x^0) is the reference), and later phases pull f back towards the
+    lowest value seen at a phase start."""
+    c = np.array([1.0, 2.0, 3.0])
+    obj = O.Objective(O.OBJ_LINEAR, c=c)
+    st = O.PertState()
+    P = O.Params(adaptive=1, n_red=1)
+    y0 = np.array([1.0, 1.0, 1.0])
+    z, acc, tri = O.perturbation_phase(obj, y0, st, P)
+    assert acc == 0 and np.array_equal(z, y0) and st.f_best == 6.0
+    y1 = np.array([2.0, 2.0, 2.0])            # f = 12 after a feasibility step
+    z, acc, _ = O.perturbation_phase(obj, y1, st, P)
+    assert acc == 1 and np.isclose(c @ z, 6.0, rtol=1e-14) and st.f_best == 6.0
+    y2 = np.array([0.5, 0.5, 0.5])            # f = 3: a new lowest value, no step
+    z, acc, _ = O.perturbation_phase(obj, y2, st, P)
+    assert acc == 0 and st.f_best == 3.0
