@@ -184,6 +184,16 @@ typedef struct {
      * (since the last set_x / set_bounds / reset) is below variance_tol.  Applies
      * in suppy_run, whatever use_stopping says; 0 disables it. */
     double variance_tol;
+    /* Step size of the perturbations: 0 the power law beta = gamma alpha^l;
+     * 1 the adaptive step of Nikazad et al. (Sec. 2.1.2), beta = (f(y) -
+     * f_ref)/||g|| when f(y) > f_ref and no step otherwise, with f_ref the
+     * lowest objective value at the start of a perturbation phase so far (this
+     * phase's included; reset by set_x / set_bounds); 2 the same with f_ref
+     * fixed to the field below.  With 1 or 2 each reduction step takes this one
+     * trial and keeps it when f(z) <= f(y); l and max_trials are not used. */
+    int32_t adaptive;
+    int32_t reserved;       /* 0                                                   */
+    double f_ref;           /* the reference value when adaptive = 2 (finite)      */
 } suppy_params;
 
 typedef struct {

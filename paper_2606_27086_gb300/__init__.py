@@ -67,7 +67,8 @@ class suppy_params(ctypes.Structure):
                 ("prox_abs", ctypes.c_double), ("prox_rel", ctypes.c_double),
                 ("obj_rel", ctypes.c_double), ("patience", ctypes.c_int32),
                 ("use_stopping", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("variance_tol", ctypes.c_double)]
+                ("variance_tol", ctypes.c_double), ("adaptive", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("f_ref", ctypes.c_double)]
 
 
 class suppy_stats(ctypes.Structure):

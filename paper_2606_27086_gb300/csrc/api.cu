@@ -741,6 +741,8 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.n_red = p ? p->n_red : 0;
     a.max_trials = p ? p->max_trials : 0;
     a.restart_every = p ? p->restart_every : 0;
+    a.adaptive = p ? p->adaptive : 0;
+    a.f_ref = p ? p->f_ref : 0.0;
     a.st = c->d_st;
     a.record_only = record_only;
     a.ws = c->d_ws;
@@ -795,6 +797,10 @@ suppy_status check_params(suppy_ctx* c, const suppy_params* p) {
     if (p->n_red < 0 || p->max_trials < 0 || p->max_sweeps < 0 || p->patience < 0 ||
         p->restart_every < 0)
         return fail(c, SUPPY_EINVAL, "negative count in params");
+    if (p->adaptive < 0 || p->adaptive > 2)
+        return fail(c, SUPPY_EINVAL, "adaptive must be 0, 1 or 2");
+    if (p->adaptive == 2 && !std::isfinite(p->f_ref))
+        return fail(c, SUPPY_EINVAL, "a fixed f_ref must be finite");
     return SUPPY_OK;
 }
 
@@ -2397,7 +2403,7 @@ suppy_status suppy_get_state(suppy_ctx* c, void* buf, size_t* len) {
     }
     if (*len < need) return fail(c, SUPPY_EINVAL, "checkpoint buffer too small");
     char* q = static_cast<char*>(buf);
-    CkptHeader h{kMagic, 2, c->n, c->m, c->B};
+    CkptHeader h{kMagic, 3, c->n, c->m, c->B};
     std::memcpy(q, &h, sizeof(h));
     CK(cudaMemcpyAsync(q + sizeof(h), c->d_x, sizeof(float) * (size_t)c->n * c->B,
                        cudaMemcpyDeviceToHost, c->stream));
@@ -2416,7 +2422,7 @@ suppy_status suppy_set_state(suppy_ctx* c, const void* buf, size_t len) {
     if (len < need) return fail(c, SUPPY_EINVAL, "checkpoint too short");
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    if (h.magic != kMagic || h.version != 2 || h.n != c->n || h.m != c->m || h.B != c->B)
+    if (h.magic != kMagic || h.version != 3 || h.n != c->n || h.m != c->m || h.B != c->B)
         return fail(c, SUPPY_EINVAL, "checkpoint does not match this context");
     const char* q = static_cast<const char*>(buf);
     CK(cudaMemcpyAsync(c->d_x, q + sizeof(h), sizeof(float) * (size_t)c->n * c->B,

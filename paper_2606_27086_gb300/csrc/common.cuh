@@ -36,7 +36,8 @@ struct RhsState {
     double last_prox;
     double w_s1, w_s2;      // variance rule: sums of the relative changes and their squares
     int w_n;                // relative changes recorded
-    int pad1;
+    int has_ref;            // adaptive step: f_ref holds a phase-start objective
+    double f_ref;           // adaptive step: lowest objective at a phase start so far
 };
 
 struct StopParams {
@@ -143,6 +144,8 @@ struct PerturbArgs {
     double gamma, alpha;
     double log2_alpha;      // log2(alpha), for the trial step sizes
     int n_red, max_trials, restart_every;
+    int adaptive;           // 0 power law, 1 adaptive (automatic f_ref), 2 adaptive (fixed f_ref)
+    double f_ref;           // the fixed reference value (adaptive = 2)
     RhsState* st;
     int record_only;        // 1: compute f(x) into st->f_cur only (no step)
     WideState* ws;          // whole-GPU first step state (resume mode)

@@ -72,6 +72,20 @@ __device__ __forceinline__ float trial_scale(double gamma, double log2_alpha, lo
     return (float)gamma * ldexpf(exp2f(f), (int)k) * inv_gnorm;
 }
 
+// Adaptive step of Nikazad et al. (Sec. 2.1.2): the reference value of a
+// phase that starts at f_start -- fixed, or the lowest phase-start objective
+// so far, this one included -- and beta / ||g|| = (f - f_ref) / ||g||^2, the
+// subgradient projection onto the level set of f's linearisation.
+__device__ __forceinline__ double adaptive_ref(const PerturbArgs& a, const RhsState& st,
+                                               double f_start) {
+    if (a.adaptive == 2) return a.f_ref;
+    return st.has_ref ? fmin(st.f_ref, f_start) : f_start;
+}
+
+__device__ __forceinline__ float adaptive_scale(double fy, double f_ref, double gg) {
+    return fy > f_ref ? (float)((fy - f_ref) / gg) : 0.f;
+}
+
 // Objectives whose value is a sum of per-element terms (no stencil): the
 // linear mean dose c.x, ||x||_1 and ||x||_2^2.
 __device__ __forceinline__ bool elementwise(int obj) {
@@ -230,6 +244,10 @@ __device__ __forceinline__ void phase_end(const PerturbArgs& a, RhsState& st, co
     st.f_cur = f_start;
     st.f_valid = 1;
     if (a.record_only) return;
+    if (a.adaptive == 1) {
+        st.f_ref = adaptive_ref(a, st, f_start);
+        st.has_ref = 1;
+    }
     st.ell = ell;
     st.restarts = ps.restarts;
     st.last_restart_k = ps.last_restart_k;
@@ -280,10 +298,17 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
         }
         if (a.record_only || gg == 0.0) break;
         const float inv_gnorm = 1.0f / sqrtf((float)gg);
+        float asc = 0.f;
+        if (a.adaptive) {
+            const double f_ref = adaptive_ref(a, st, f_start);
+            if (!(fy > f_ref)) break;
+            asc = adaptive_scale(fy, f_ref, gg);
+        }
         bool ok = false;
-        for (int j = (s == ps.s0 ? ps.jt0 : 0); j < a.max_trials; ++j) {
-            const float sc = trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
-            ell += 1;
+        const int jmax = a.adaptive ? 1 : a.max_trials;
+        for (int j = (s == ps.s0 ? ps.jt0 : 0); j < jmax; ++j) {
+            const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            if (!a.adaptive) ell += 1;
             trials += 1;
             Vec yy = y;
             Vec gv = g;
@@ -483,10 +508,17 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
         }
         if (a.record_only || gg == 0.0) break;
         const float inv_gnorm = 1.0f / sqrtf((float)gg);
+        float asc = 0.f;
+        if (a.adaptive) {
+            const double f_ref = adaptive_ref(a, st, f_start);
+            if (!(fy > f_ref)) break;
+            asc = adaptive_scale(fy, f_ref, gg);
+        }
         bool ok = false;
-        for (int jt = (s == ps.s0 ? ps.jt0 : 0); jt < a.max_trials; ++jt) {
-            const float sc = trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
-            ell += 1;
+        const int jmax = a.adaptive ? 1 : a.max_trials;
+        for (int jt = (s == ps.s0 ? ps.jt0 : 0); jt < jmax; ++jt) {
+            const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            if (!a.adaptive) ell += 1;
             trials += 1;
             double fz = 0.0;
             if (lin) {
@@ -715,9 +747,21 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_grad(const PerturbArgs a)
             w.trials = 0;
             w.pending = 0;
             w.done = 0;
-            if (G2 == 0.0 || a.n_red <= 0) {
+            double f_ref = 0.0;
+            if (a.adaptive) {
+                f_ref = adaptive_ref(a, st, F);
+                if (a.adaptive == 1) {
+                    st.f_ref = f_ref;
+                    st.has_ref = 1;
+                }
+            }
+            if (G2 == 0.0 || a.n_red <= 0 || (a.adaptive && !(F > f_ref))) {
                 w.done = 1;
                 wide_bookkeeping(st, 0, 0);
+            } else if (a.adaptive) {
+                // one trial: the adaptive step (every slot holds it)
+                const float sc = adaptive_scale(F, f_ref, G2);
+                for (int jj = 0; jj < kWideTrials; ++jj) w.step[jj] = sc;
             } else {
                 ell_s[r] = ell;
                 inv_s[r] = 1.0f / sqrtf((float)G2);
@@ -786,7 +830,8 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_trials(const PerturbArgs 
         RhsState& st = a.st[r];
         WideState& w = a.ws[r];
         if (!st.stopped && !w.done) {
-            const int jmax = min(kWideTrials, a.max_trials);
+            const int tmax = a.adaptive ? 1 : a.max_trials;
+            const int jmax = min(kWideTrials, tmax);
             int hit = -1;
             for (int jj = 0; jj < jmax; ++jj)
                 if (res[r * kWideTrials + jj] <= w.fy) {
@@ -798,11 +843,11 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_trials(const PerturbArgs 
                 w.pending = 1;
                 w.acc = 1;
                 w.trials = hit + 1;
-                st.ell += hit + 1;
+                if (!a.adaptive) st.ell += hit + 1;
             } else {
                 w.trials = jmax;
-                st.ell += jmax;
-                if (jmax >= a.max_trials) {
+                if (!a.adaptive) st.ell += jmax;
+                if (jmax >= tmax) {
                     // the step ran out of trials: the phase ends
                     w.done = 1;
                     wide_bookkeeping(st, 0, jmax);
