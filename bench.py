@@ -649,7 +649,8 @@ def profile_case(case: int, steps: int) -> int:
     512x512 workload with the sweep and launch shapes bench.py uses (two
     passes, shapes tuned at create); case 4: the same with the one-pass sweep;
     case 5: the horseshoe radiotherapy plan as a split problem (dose-volume
-    sets by the CQ step, slabs by EMR, mean-dose perturbations).
+    sets by the CQ step, slabs by EMR, mean-dose perturbations); case 6: the
+    CT 512x512 workload block-iteratively (36 interleaved angle blocks, tuned).
     The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches."""
     import torch
@@ -665,6 +666,10 @@ def profile_case(case: int, steps: int) -> int:
         Aq = sp["Aq"]
         ctx.suppy_set_dvc(Aq.row_ptr, Aq.col, Aq.val, Aq.m, sp["sptr"], sp["dvcs"], 1.0)
         params = dict(gamma=1.0, alpha=0.7, n_red=1, restart_every=500)
+    elif case == 6:
+        prob = ct512()
+        prob.blocks = synth.angle_blocks(360, 725, 36)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP, tune=1)
     elif case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
@@ -701,11 +706,12 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
                          "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
-                         "pass; 5 the horseshoe split problem (DVCs by the CQ step)")
+                         "pass; 5 the horseshoe split problem (DVCs by the CQ step); 6 CT "
+                         "512x512 with 36 BIP blocks")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6)

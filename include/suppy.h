@@ -156,7 +156,7 @@ typedef struct {
      * first accepted one applied: the same choice as the sequential trial
      * loop), the rest of the phase, when there is one, by one thread-block
      * cluster per right-hand side; 1 -- the cluster kernel alone; 0 --
-     * automatic: 2 when n * nrhs >= 65536, else 1. */
+     * automatic: 2 for one right-hand side with n >= 65536, else 1. */
     int32_t perturb_path;
 } suppy_opts;
 

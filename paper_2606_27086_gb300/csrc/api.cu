@@ -1512,10 +1512,14 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     if (c->obj != SUPPY_OBJ_NONE) {
         if ((s = dalloc(c, &c->d_g, nB)) != SUPPY_OK) return s;
-        // the whole-GPU first step pays off for large images (a few fixed
-        // microseconds of launches and reductions against the cluster's
-        // per-pixel work); 2 forces it, 1 disables it
-        if (o->perturb_path == 2 || (o->perturb_path == 0 && (long long)nB >= 65536)) {
+        // the whole-GPU first step pays off for one large image (a few fixed
+        // microseconds of launches and reductions against a single cluster's
+        // per-pixel work); with two or more right-hand sides their clusters
+        // already share the GPU and the cluster path is faster (measured on
+        // GB300: 16 seismic images 0.092 against 0.150 ms a phase, 2 images
+        // 0.046 against 0.060 ms); 2 forces it, 1 disables it
+        if (o->perturb_path == 2 ||
+            (o->perturb_path == 0 && (long long)nB >= 65536 && c->B == 1)) {
             c->wide = true;
             c->wide_grid = (int)std::max<long long>(
                 1, std::min<long long>(2LL * sms, ((long long)nB + kWideThreads - 1) / kWideThreads));
