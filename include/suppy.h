@@ -300,7 +300,11 @@ suppy_status suppy_objective(suppy_ctx* ctx, double* out);
  * sweep] until the stopping rule holds for every right-hand side or
  * max_sweeps sweeps ran.  Sweeps of a stopped right-hand side are skipped
  * on the device.  out (host, B entries) may be NULL.  Synchronizes at the
- * end and every check_every sweeps when use_stopping is set. */
+ * end and every check_every sweeps when use_stopping is set.  With out NULL
+ * and use_stopping 0 the call only enqueues the iterations on the context's
+ * stream and returns; a device-side wait that gave up is then reported
+ * (SUPPY_ETIMEOUT) by the next call that synchronizes (suppy_get_x into host
+ * memory, suppy_run with out, suppy_proximity, ...). */
 suppy_status suppy_run(suppy_ctx* ctx, const suppy_params* p, suppy_stats* out);
 
 /* Copy the per-sweep history of right-hand side rhs: prox[k] (monitored

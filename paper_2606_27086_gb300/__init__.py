@@ -374,7 +374,12 @@ class Context:
         _check(self._lib.suppy_objective(self.ctx, ctypes.c_void_p(out.ctypes.data)), self.ctx)
         return out
 
-    def suppy_run(self, params: suppy_params):
+    def suppy_run(self, params: suppy_params, want_stats: bool = True):
+        """With want_stats False (and params.use_stopping 0) the call only
+        enqueues the iterations and returns None."""
+        if not want_stats:
+            _check(self._lib.suppy_run(self.ctx, ctypes.byref(params), None), self.ctx)
+            return None
         st = (suppy_stats * self.nrhs)()
         _check(self._lib.suppy_run(self.ctx, ctypes.byref(params), ctypes.cast(st, ctypes.c_void_p)),
                self.ctx)

@@ -89,6 +89,7 @@ struct suppy_ctx {
     double* d_objpart = nullptr;
     int* d_part = nullptr;          // nseg x (groups + 1)
     double* h_out = nullptr;        // pinned B doubles
+    int* h_err = nullptr;           // pinned copy of the streaming passes' error word
     int k_upper = 0;                // upper bound of the sweep counters (history sizing)
     float* d_stage_l = nullptr;     // persistent staging of host bounds (set_bounds)
     float* d_stage_u = nullptr;
@@ -776,17 +777,21 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
 
 // A streaming kernel whose bounded wait gave up leaves a nonzero error word;
 // report (and clear) it at the next synchronizing call.
-suppy_status check_device_error(suppy_ctx* c) {
-    if (!c->d_err) return SUPPY_OK;
-    int h = 0;
-    CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    if (h) {
-        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-        return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
-    }
+// The streaming passes' error word (sticky until read) travels to pinned
+// host memory with the copies of a synchronizing call: enqueue the copy,
+// synchronize once, then look.
+suppy_status enqueue_err_copy(suppy_ctx* c) {
+    if (c->d_err) CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     return SUPPY_OK;
 }
+
+suppy_status err_after_sync(suppy_ctx* c) {
+    if (!c->d_err || !*c->h_err) return SUPPY_OK;
+    *c->h_err = 0;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
+}
+
 
 suppy_status check_params(suppy_ctx* c, const suppy_params* p) {
     if (!p) return fail(c, SUPPY_EINVAL, "params is NULL");
@@ -1536,6 +1541,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     c->grid_obj = std::max(1, std::min(sms * 4, (n + 255) / 256));
     if ((s = dalloc(c, &c->d_objpart, (size_t)c->grid_obj * c->B)) != SUPPY_OK) return s;
     CK(cudaMallocHost(&c->h_out, sizeof(double) * kMaxRhs));
+    CK(cudaMallocHost(&c->h_err, sizeof(int)));
+    *c->h_err = 0;
 
     // ---- linear objective vector
     if (c->obj == SUPPY_OBJ_LINEAR) {
@@ -1872,6 +1879,7 @@ void destroy_impl(suppy_ctx* c) {
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_out) cudaFreeHost(c->h_out);
+    if (c->h_err) cudaFreeHost(c->h_err);
     delete c;
 }
 
@@ -1951,14 +1959,10 @@ suppy_status load_bounds(suppy_ctx* c, const float* l, const float* u, int32_t o
     // one synchronization reads both results
     if (!c->d_flags && (s = dalloc(c, &c->d_flags, 4)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(int), c->stream));
-    CK(launch_validate_vec(s_l, (long long)mB, 1, c->d_flags, 1, c->stream));
-    CK(launch_validate_vec(s_u, (long long)mB, 1, c->d_flags, 2, c->stream));
-    CK(launch_validate_pair(s_l, s_u, (long long)mB, c->d_flags, 4, c->stream));
-    CK(launch_zero_row_check_src(c->d_rho, s_l, s_u, c->d_perm, c->m, c->B_user, c->d_flags + 1,
-                                 c->stream));
+    CK(launch_check_bounds(c->d_rho, s_l, s_u, c->d_perm, c->m, c->B_user, c->d_flags, c->stream));
     CK(launch_permute_bounds(s_l, s_u, c->d_perm, c->m, c->B_user, c->B, c->d_l, c->d_u, c->stream,
                              c->d_flags, 2));
-    note_launch(c, 5);
+    note_launch(c, 2);
     int hf[2] = {0, 0};
     if ((s = read_flags(c, c->d_flags, hf, 2)) != SUPPY_OK) return s;
     if (hf[0]) return fail(c, SUPPY_EINVAL, "bounds need l <= u and no NaN");
@@ -2251,8 +2255,11 @@ suppy_status suppy_get_x(suppy_ctx* c, float* x, int32_t on_device) {
         if (!on_device)
             CK(cudaMemcpyAsync(x, tmp, cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
     }
-    if (!on_device) CK(cudaStreamSynchronize(c->stream));
-    return on_device ? SUPPY_OK : check_device_error(c);
+    if (on_device) return SUPPY_OK;
+    suppy_status s = enqueue_err_copy(c);
+    if (s != SUPPY_OK) return s;
+    CK(cudaStreamSynchronize(c->stream));
+    return err_after_sync(c);
 }
 
 suppy_status suppy_perturb(suppy_ctx* c, const suppy_params* p, int32_t* accepted) {
@@ -2342,18 +2349,15 @@ suppy_status suppy_run(suppy_ctx* c, const suppy_params* p, suppy_stats* out) {
         }
     }
     // the error word of the streaming passes and the statistics in one
-    // synchronization
-    int herr = 0;
-    if (c->d_err)
-        CK(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    // synchronization; without statistics or the stopping rule the call only
+    // enqueues, and the next synchronizing call reports the error word
+    if ((s = enqueue_err_copy(c)) != SUPPY_OK) return s;
+    if (!out && !p->use_stopping) return SUPPY_OK;
     if (out)
         CK(cudaMemcpyAsync(st.data(), c->d_st, sizeof(RhsState) * c->B, cudaMemcpyDeviceToHost,
                            c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (herr) {
-        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-        return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
-    }
+    if ((s = err_after_sync(c)) != SUPPY_OK) return s;
     if (out) {
         for (int b = 0; b < c->B_user; ++b) {
             out[b].sweeps = st[b].k;

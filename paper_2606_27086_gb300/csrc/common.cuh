@@ -280,9 +280,8 @@ cudaError_t launch_zero_row_check(const double* rho, const float* l, const float
 cudaError_t launch_permute_bounds(const float* l_in, const float* u_in, const int* perm, int m,
                                   int B_in, int B, float* l, float* u, cudaStream_t s,
                                   const int* skip = nullptr, int nskip = 0);
-cudaError_t launch_zero_row_check_src(const double* rho, const float* l_in, const float* u_in,
-                                      const int* perm, int m, int B_in, int* flags,
-                                      cudaStream_t s);
+cudaError_t launch_check_bounds(const double* rho, const float* l_in, const float* u_in,
+                                const int* perm, int m, int B_in, int* flags, cudaStream_t s);
 cudaError_t launch_reset_states(RhsState* st, int B, int B_user, cudaStream_t s);
 cudaError_t launch_box_init(float* x, const float* lo, const float* hi, long long nB, int B,
                             int box_len, const float* x_in, int B_in, cudaStream_t s);

@@ -136,14 +136,19 @@ __global__ void k_zero_row_check(const double* rho, const float* l, const float*
 
 // Zero rows (||a_i|| = 0, device row i) against source-order bounds: the
 // slab must contain 0.
-__global__ void k_zero_row_check_src(const double* rho, const float* l_in, const float* u_in,
-                                     const int* perm, int m, int B_in, int* flags) {
+// New slab bounds in one pass over the device rows: NaN or l > u anywhere
+// sets bit 1 of flags[0]; a zero row whose slab excludes 0 sets flags[1].
+// (Each source row is the image of exactly one device row.)
+__global__ void k_check_bounds(const double* rho, const float* l_in, const float* u_in,
+                               const int* perm, int m, int B_in, int* flags) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        if (rho[i] > 0.0) continue;
         const int src = perm ? perm[i] : i;
+        const bool zero = !(rho[i] > 0.0);
         for (int b = 0; b < B_in; ++b) {
             const size_t o = (size_t)src * B_in + b;
-            if (!(l_in[o] <= 0.f && u_in[o] >= 0.f)) atomicOr(flags, 1);
+            const float lv = l_in[o], uv = u_in[o];
+            if (isnan(lv) || isnan(uv) || !(lv <= uv)) atomicOr(flags, 1);
+            if (zero && !(lv <= 0.f && uv >= 0.f)) atomicOr(flags + 1, 1);
         }
     }
 }
@@ -346,10 +351,9 @@ cudaError_t launch_permute_bounds(const float* l_in, const float* u_in, const in
     return cudaGetLastError();
 }
 
-cudaError_t launch_zero_row_check_src(const double* rho, const float* l_in, const float* u_in,
-                                      const int* perm, int m, int B_in, int* flags,
-                                      cudaStream_t s) {
-    k_zero_row_check_src<<<grid_for(m), 256, 0, s>>>(rho, l_in, u_in, perm, m, B_in, flags);
+cudaError_t launch_check_bounds(const double* rho, const float* l_in, const float* u_in,
+                                const int* perm, int m, int B_in, int* flags, cudaStream_t s) {
+    k_check_bounds<<<grid_for(m), 256, 0, s>>>(rho, l_in, u_in, perm, m, B_in, flags);
     return cudaGetLastError();
 }
 

@@ -665,6 +665,29 @@ def test_variance_stopping_rule_stops_with_the_oracle(graphs):
             assert rel_l2(xg[:, b], r.x) <= 1e-3
 
 
+def test_run_without_statistics_enqueues_the_same_iterations():
+    """suppy_run with out = NULL (and no stopping rule) returns after
+    enqueuing; the next synchronizing call sees exactly the iterations a
+    synchronizing run leaves (two-pass sweep: the iterate bitwise)."""
+    prob = small_ct()
+    x0 = random_x(prob.A.n, 1, seed=91)
+    xs, hs = [], []
+    for want in (True, False):
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS)
+        ctx.suppy_set_x(x0)
+        for _ in range(3):
+            r = ctx.suppy_run(_params(max_sweeps=2), want_stats=want)
+            assert (r is None) == (not want)
+        xs.append(ctx.suppy_get_x())
+        hs.append(ctx.suppy_history(0)[0])
+        ctx.close()
+    assert np.array_equal(xs[0], xs[1])
+    # the streamed row pass hands items out dynamically: each thread's
+    # compensated FP32 proximity sum takes its terms in a varying order (x is
+    # bitwise equal, the history to the FP32 compensation error)
+    assert len(hs[1]) == 6 and np.allclose(hs[0], hs[1], rtol=1e-6, atol=0)
+
+
 def test_update_bounds_keeps_the_iteration_state():
     """suppy_update_bounds swaps the slabs and Algorithm 1 continues (same
     exponent l, counters and history) -- the oracle's loop with the bounds
