@@ -169,8 +169,8 @@ struct suppy_ctx {
     double timing_ms[4] = {0.0, 0.0, 0.0, 0.0};
     long long timing_n[4] = {0, 0, 0, 0};
     long long launches = 0;
-    size_t dev_bytes = 0;
-    std::vector<void*> allocs;
+    size_t dev_bytes = 0;                               // held now (allocs)
+    std::vector<std::pair<void*, size_t>> allocs;      // library-owned device buffers
 
     // CUDA graph of one superiorized iteration (perturbation + sweep)
     cudaGraphExec_t graph = nullptr;
@@ -210,7 +210,7 @@ suppy_status dalloc(suppy_ctx* c, T** p, size_t count) {
         return fail(c, e == cudaErrorMemoryAllocation ? SUPPY_ENOMEM : SUPPY_ECUDA,
                     std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
     }
-    c->allocs.push_back(q);
+    c->allocs.emplace_back(q, bytes);
     c->dev_bytes += bytes;
     *p = static_cast<T*>(q);
     return SUPPY_OK;
@@ -218,8 +218,12 @@ suppy_status dalloc(suppy_ctx* c, T** p, size_t count) {
 
 void dfree(suppy_ctx* c, void* p) {
     if (!p) return;
-    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
-    if (it != c->allocs.end()) c->allocs.erase(it);
+    auto it = std::find_if(c->allocs.begin(), c->allocs.end(),
+                           [p](const std::pair<void*, size_t>& a) { return a.first == p; });
+    if (it != c->allocs.end()) {
+        c->dev_bytes -= it->second;
+        c->allocs.erase(it);
+    }
     cudaFree(p);
 }
 
@@ -1877,7 +1881,7 @@ void destroy_impl(suppy_ctx* c) {
     }
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    for (void* p : c->allocs) cudaFree(p);
+    for (auto& a : c->allocs) cudaFree(a.first);
     if (c->h_out) cudaFreeHost(c->h_out);
     if (c->h_err) cudaFreeHost(c->h_err);
     delete c;

@@ -235,9 +235,13 @@ def test_split_validation_and_removal():
     col[5] = A.n
     with pytest.raises(pk.SuppyError):
         ctx.suppy_set_dvc(A.row_ptr, col, A.val, A.m, sptr, [(0, 0, 0.5, 1.0)], 1.0)
-    # set, then remove: sweeps are plain slab sweeps again
+    # set, then remove: sweeps are plain slab sweeps again and the device
+    # memory the sets held is given back
+    held = ctx.suppy_info_get()["device_bytes"]
     ctx.suppy_set_dvc(A.row_ptr, A.col, A.val, A.m, sptr, [(0, 0, 0.0, 0.5)], 1.0)
+    assert ctx.suppy_info_get()["device_bytes"] > held
     ctx.suppy_set_dvc(None, None, None, 0, [0], [], 1.0)
+    assert ctx.suppy_info_get()["device_bytes"] == held
     ctx.suppy_set_x(x)
     ctx.suppy_sweep(pk.suppy_params_default(), 1)
     assert np.array_equal(ctx.suppy_get_x(), x)
