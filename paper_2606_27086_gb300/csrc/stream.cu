@@ -344,6 +344,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             nxt = (nb + gw < nitems) ? a.info[I0 + nb + gw] : make_int2(0, 0);
             work.prefetch(nb + gw < nitems ? I0 + nb + gw : -1);
             const bool has = valid && inf.y > 0;
+            if (valid && inf.y == 0 && gl == 0) work.empty(i);
             const int g0 = (int)((long long)inf.x - Ea);
             int kb = BIG, ke = -1;
             if (has) {
@@ -441,6 +442,7 @@ struct RowWork {
         cm = ncm;
         pm = npm;
     }
+    __device__ void empty(int) {}   // an empty row: no coefficient, no proximity term
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
         float dot = ring_dot<VT, G>(r, g0, len, gl, a.x);
@@ -491,6 +493,12 @@ struct ColWork {
         lo = nlo;
         hi = nhi;
         z = nz;
+    }
+    // an empty column: the box step alone (the perturbation may have left x_j
+    // outside the box); in accumulate mode its sum is 0
+    __device__ void empty(int j) {
+        if (a.delta_out) a.delta_out[j] = 0.f;
+        else a.xw[j] = clampf(xj, lo, hi);
     }
     __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);

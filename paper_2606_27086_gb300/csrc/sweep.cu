@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass(const ColArgs a) {
             s += dot_batch<VT, G, 8>(vcol, rcol, base, ci.y, lane, coef, pol);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o);
-        if (lane == 0 && ci.y > 0) {
+        if (lane == 0) {   // an empty column still takes the box step
             const int bj = (a.box_len == 1) ? 0 : j;
             if (a.zc) s *= a.zc[j];
             if (a.delta_out) a.delta_out[j] = s;
@@ -436,8 +436,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
     if (!CHECKED(jb >= 0 && jb <= je && je <= a.n, 311, warp)) je = jb;
     const VT* __restrict__ val = static_cast<const VT*>(a.cval);
     for (int j = jb; j < je; ++j) {
-        const int2 ci = a.cinfo[j];
-        if (ci.y == 0) continue;
+        const int2 ci = a.cinfo[j];   // an empty column still takes the box step
         if (!CHECKED(ci.x >= 0 && (long long)ci.x + ci.y <= a.nnz, 312, j)) continue;
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
@@ -672,7 +671,8 @@ __global__ void __launch_bounds__(256) k_ext_norm(const ExtArgs a) {
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
-// x <- box(x + lambda t_b delta), delta <- 0.
+// x <- box(x + lambda t_b delta), delta <- 0 (the box also when t_b = 0: the
+// perturbation may have left x outside it).
 __global__ void __launch_bounds__(256) k_ext_apply(const ExtArgs a) {
     const long long nB = a.n * a.B;
     for (long long e = (long long)blockIdx.x * 256 + threadIdx.x; e < nB;
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) k_ext_apply(const ExtArgs a) {
         const float t = a.lam * (float)a.tstep[b];
         const long long bj = (a.box_len == 1) ? 0 : j;
         const float d = a.delta[e];
-        if (t != 0.f) a.x[e] = clampf(a.x[e] + t * d, a.lo[bj], a.hi[bj]);
+        a.x[e] = clampf(a.x[e] + t * d, a.lo[bj], a.hi[bj]);
         a.delta[e] = 0.f;
     }
 }

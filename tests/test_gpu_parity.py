@@ -665,6 +665,40 @@ def test_variance_stopping_rule_stops_with_the_oracle(graphs):
             assert rel_l2(xg[:, b], r.x) <= 1e-3
 
 
+@pytest.mark.parametrize("mode,omode", [(pk.SUPPY_CIMMINO, O.CIMMINO), (pk.SUPPY_DROP, O.DROP),
+                                        (pk.SUPPY_EL, O.EL), (pk.SUPPY_EMR, O.EMR)])
+@pytest.mark.parametrize("strategy,tma", [(pk.STRATEGY_ONE_PASS, -1), (pk.STRATEGY_TWO_PASS, -1),
+                                          (pk.STRATEGY_TWO_PASS, 0)])
+def test_box_step_covers_empty_columns_after_perturbation(mode, omode, strategy, tma):
+    """Columns without entries still take the box step: the L1 perturbation
+    lowers every positive entry by beta/sqrt(n), so entries starting on the
+    lower bound leave the box, and only the sweep's box brings those of empty
+    columns back (as in the oracle) -- in the one-pass box kernel, the
+    register-fed and streamed column passes, and the extrapolated update."""
+    prob = synth.random_problem(400, 3000, seed=61, mean_len=6, box=(0.2, 0.8))
+    A = prob.A
+    empty = np.setdiff1d(np.arange(A.n), A.col)
+    assert len(empty) > 1000
+    rng = np.random.default_rng(62)
+    x0 = rng.uniform(0.2, 0.8, A.n).astype(np.float32)
+    x0[empty[::2]] = 0.2
+    K = 3
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_L1, mode=mode, strategy=strategy, tma=tma)
+    if mode not in (pk.SUPPY_EL, pk.SUPPY_EMR):   # EL / EMR always take two passes
+        assert ctx.suppy_info_get()["strategy"] == strategy
+    ctx.suppy_set_x(x0)
+    ctx.suppy_run(_params(max_sweeps=K, use_stopping=0))
+    xg = ctx.suppy_get_x()
+    ctx.close()
+    S, l, u, lo, hi = O.from_problem(prob, omode)
+    r = O.run(S, omode, l, u, lo, hi, O.Objective(O.OBJ_L1), O.Params(max_sweeps=K),
+              x0=x0.astype(np.float64))
+    assert sum(r.accepted) == K
+    assert xg.min() >= 0.2 and xg.max() <= 0.8
+    assert np.array_equal(xg[empty[::2]], np.full(len(empty[::2]), 0.2, np.float32))
+    assert rel_l2(xg, r.x) <= 1e-5
+
+
 def test_run_without_statistics_enqueues_the_same_iterations():
     """suppy_run with out = NULL (and no stopping rule) returns after
     enqueuing; the next synchronizing call sees exactly the iterations a
