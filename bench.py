@@ -444,17 +444,15 @@ def serving_workload(pk, nreq: int, seed: int = 501):
     return mats, reqs
 
 
-def serving(pk, nreq: int):
-    """Batched BF16 continuous-batching server against one-at-a-time FP32
-    solves of the same requests (arrival times kept, queueing included)."""
+def _serve_batched(pk, mats, reqs, dtype):
+    """The requests through one continuous-batching server (A stored as dtype);
+    returns its figures and the final proximity / objective per request."""
     import torch
-    mats, reqs = serving_workload(pk, nreq)
-    # batched, mixed precision
     srv = pk.Server(slots=32, check_every=8)
     mids = []
     for prob, spec in mats:
         P = pk.suppy_params_default(**spec["sup"], **SERVE_STOP)
-        mids.append(srv.suppy_server_add_matrix(prob, P, dtype=pk.SUPPY_BF16, mode=spec["mode"],
+        mids.append(srv.suppy_server_add_matrix(prob, P, dtype=dtype, mode=spec["mode"],
                                                 obj=spec["obj"]))
     ids = [None] * len(reqs)
     t0 = srv.suppy_server_clock()
@@ -467,21 +465,33 @@ def serving(pk, nreq: int):
         r, w = srv.suppy_server_step()
         if nxt == len(reqs) and r == 0 and w == 0:
             break
-    lat, fin, prox_b, obj_b, sweeps_b = [], [], [], [], []
+    lat, fin, prox, obj, sweeps = [], [], [], [], []
     for k, rid in enumerate(ids):
         info, _ = srv.suppy_server_query(rid)
         lat.append(info["t_done"] - t0 - reqs[k][0])
         fin.append(info["t_done"] - t0)
-        prox_b.append(info["proximity"])
-        obj_b.append(info["objective"])
-        sweeps_b.append(info["sweeps"])
+        prox.append(info["proximity"])
+        obj.append(info["objective"])
+        sweeps.append(info["sweeps"])
     peak_bytes = srv.suppy_server_device_bytes()
     srv.close()
     torch.cuda.synchronize()
-    batched = {"solves_per_s": len(reqs) / max(fin), "p50_s": float(np.percentile(lat, 50)),
-               "p99_s": float(np.percentile(lat, 99)), "makespan_s": max(fin),
-               "mean_sweeps": float(np.mean(sweeps_b)), "dtype": "bf16 A, f32 x, f64 acceptance",
-               "device_bytes_end": int(peak_bytes)}
+    name = "bf16 A" if dtype == pk.SUPPY_BF16 else "f32 A"
+    figs = {"solves_per_s": len(reqs) / max(fin), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "makespan_s": max(fin),
+            "mean_sweeps": float(np.mean(sweeps)), "dtype": name + ", f32 x, f64 acceptance",
+            "device_bytes_end": int(peak_bytes)}
+    return figs, prox, obj
+
+
+def serving(pk, nreq: int):
+    """Batched continuous-batching server (BF16 A, and FP32 A for a comparison
+    at equal precision) against one-at-a-time FP32 solves of the same requests
+    (arrival times kept, queueing included)."""
+    import torch
+    mats, reqs = serving_workload(pk, nreq)
+    batched, prox_b, obj_b = _serve_batched(pk, mats, reqs, pk.SUPPY_BF16)
+    batched32, prox_b32, obj_b32 = _serve_batched(pk, mats, reqs, pk.SUPPY_F32)
     # one at a time, FP32, per-matrix context resident after first use
     ctxs = {}
     lat1, fin1, prox_1, obj_1 = [], [], [], []
@@ -507,14 +517,20 @@ def serving(pk, nreq: int):
     torch.cuda.synchronize()
     plain = {"solves_per_s": len(reqs) / max(fin1), "p50_s": float(np.percentile(lat1, 50)),
              "p99_s": float(np.percentile(lat1, 99)), "makespan_s": max(fin1), "dtype": "f32"}
-    rp = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(prox_b, prox_1)]
-    ro = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(obj_b, obj_1)]
+    def rel_diffs(pb, ob):
+        rp = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(pb, prox_1)]
+        ro = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(ob, obj_1)]
+        return ({"median": float(np.median(rp)), "max": float(np.max(rp))},
+                {"median": float(np.median(ro)), "max": float(np.max(ro))})
+    rp, ro = rel_diffs(prox_b, obj_b)
+    rp32, ro32 = rel_diffs(prox_b32, obj_b32)
+    batched32["final_proximity_rel_diff"] = rp32
+    batched32["final_objective_rel_diff"] = ro32
     return {"requests": len(reqs), "arrival_rate_per_s": 200.0,
             "mix": {spec["name"]: sum(1 for r in reqs if r[1] == i)
                     for i, (_, spec) in enumerate(mats)},
-            "batched": batched, "one_at_a_time": plain,
-            "final_proximity_rel_diff": {"median": float(np.median(rp)), "max": float(np.max(rp))},
-            "final_objective_rel_diff": {"median": float(np.median(ro)), "max": float(np.max(ro))},
+            "batched": batched, "batched_f32": batched32, "one_at_a_time": plain,
+            "final_proximity_rel_diff": rp, "final_objective_rel_diff": ro,
             "stopping": "proximity change < 1e-4 relative for 5 sweeps, P <= 1e-6, or 500 sweeps"}
 
 
