@@ -616,7 +616,7 @@ def ours(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(Ke):
-        ctx.suppy_update_bounds(l_pin, u_pin)
+        ctx.suppy_update_bounds_async(l_pin, u_pin)
         ctx.suppy_run(p1, want_stats=False)
         ctx.suppy_get_x(x_pin)
     torch.cuda.synchronize()
@@ -624,9 +624,10 @@ def ours(args):
     e2e = {"value": A.nnz * Ke * world / te, "unit": UNIT,
            "h2d_bytes_per_step": 2 * A.m * 4, "d2h_bytes_per_step": A.n * 4 + 40,
            "steps": Ke,
-           "note": "per step: suppy_update_bounds(pinned host l, u; the iteration state continues) "
-                   "+ suppy_run of one superiorized iteration (enqueued, no statistics) + "
-                   "suppy_get_x(pinned host x, one synchronization); "
+           "note": "per step: suppy_update_bounds_async(pinned host l, u; copies, checks and "
+                   "swap enqueued; the iteration state continues) + suppy_run of one "
+                   "superiorized iteration (enqueued, no statistics) + suppy_get_x(pinned host "
+                   "x: the step's one synchronization, which also reports a rejected bounds set); "
                    "suppy_set_bounds would also reset the exponent l, and the first phase after "
                    "a reset near convergence spends all 100 trials"}
 

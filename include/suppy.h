@@ -263,6 +263,16 @@ suppy_status suppy_set_bounds(suppy_ctx* ctx, const float* l, const float* u, in
  * object.  A rejected call (SUPPY_EINVAL) leaves the old bounds. */
 suppy_status suppy_update_bounds(suppy_ctx* ctx, const float* l, const float* u, int32_t on_device);
 
+/* suppy_update_bounds without its synchronization: the copies, checks and
+ * the swap are enqueued on the context's stream and the call returns.  A
+ * rejected set (NaN, l > u, a zero row whose slab excludes 0) is skipped on
+ * the device, so the old bounds stay, and it is reported (SUPPY_EINVAL) by the
+ * next call that synchronizes with the results: suppy_get_x into host memory
+ * or suppy_run with statistics.  Host arrays must stay unchanged until then
+ * (pinned host memory lets the copy overlap). */
+suppy_status suppy_update_bounds_async(suppy_ctx* ctx, const float* l, const float* u,
+                                       int32_t on_device);
+
 /* Set x (n x B) and project it onto the box.  Resets iteration counters,
  * exponents, histories and stop flags. */
 suppy_status suppy_set_x(suppy_ctx* ctx, const float* x, int32_t on_device);

@@ -30,7 +30,7 @@ SUPPY_DVC_UPPER, SUPPY_DVC_LOWER = 0, 1
 
 EXPORTED = [
     "suppy_params_default", "suppy_create", "suppy_destroy", "suppy_set_stream",
-    "suppy_set_bounds", "suppy_update_bounds", "suppy_set_x", "suppy_get_x", "suppy_perturb",
+    "suppy_set_bounds", "suppy_update_bounds", "suppy_update_bounds_async", "suppy_set_x", "suppy_get_x", "suppy_perturb",
     "suppy_sweep",
     "suppy_proximity", "suppy_objective", "suppy_run", "suppy_history", "suppy_get_state",
     "suppy_set_state", "suppy_info_get", "suppy_timing_enable", "suppy_kernel_time",
@@ -131,6 +131,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_set_stream": (ctypes.c_int, [P, P]),
         "suppy_set_bounds": (ctypes.c_int, [P, P, P, I32]),
         "suppy_update_bounds": (ctypes.c_int, [P, P, P, I32]),
+        "suppy_update_bounds_async": (ctypes.c_int, [P, P, P, I32]),
         "suppy_set_x": (ctypes.c_int, [P, P, I32]),
         "suppy_get_x": (ctypes.c_int, [P, P, I32]),
         "suppy_perturb": (ctypes.c_int, [P, ctypes.POINTER(suppy_params), P]),
@@ -314,6 +315,14 @@ class Context:
         lp, dl, k1 = _ptr(l)
         up, du, k2 = _ptr(u)
         _check(self._lib.suppy_update_bounds(self.ctx, lp, up, dl), self.ctx)
+
+    def suppy_update_bounds_async(self, l, u):
+        """Enqueue-only bounds update; keep l and u alive and unchanged until the
+        next synchronizing call (which reports a rejected set)."""
+        lp, dl, k1 = _ptr(l)
+        up, du, k2 = _ptr(u)
+        self._pending_bounds = (k1, k2)
+        _check(self._lib.suppy_update_bounds_async(self.ctx, lp, up, dl), self.ctx)
 
     def suppy_set_x(self, x):
         xp, d, k = _ptr(x)

@@ -90,6 +90,8 @@ struct suppy_ctx {
     int* d_part = nullptr;          // nseg x (groups + 1)
     double* h_out = nullptr;        // pinned B doubles
     int* h_err = nullptr;           // pinned copy of the streaming passes' error word
+    int* h_bflags = nullptr;        // pinned copy of an enqueued bounds check (2 words)
+    bool bounds_pending = false;    // h_bflags holds a check not yet reported
     int k_upper = 0;                // upper bound of the sweep counters (history sizing)
     float* d_stage_l = nullptr;     // persistent staging of host bounds (set_bounds)
     float* d_stage_u = nullptr;
@@ -790,6 +792,14 @@ suppy_status enqueue_err_copy(suppy_ctx* c) {
 }
 
 suppy_status err_after_sync(suppy_ctx* c) {
+    if (c->bounds_pending) {
+        // the checks of enqueued bounds updates (suppy_update_bounds_async)
+        c->bounds_pending = false;
+        const int f0 = c->h_bflags[0], f1 = c->h_bflags[1];
+        if (f0 || f1) CK(cudaMemsetAsync(c->d_flags + 2, 0, 2 * sizeof(int), c->stream));
+        if (f0) return fail(c, SUPPY_EINVAL, "an enqueued bounds update was rejected (l <= u and no NaN needed); the old bounds stay");
+        if (f1) return fail(c, SUPPY_EINVAL, "an enqueued bounds update was rejected (a zero row needs l <= 0 <= u); the old bounds stay");
+    }
     if (!c->d_err || !*c->h_err) return SUPPY_OK;
     *c->h_err = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
@@ -1547,6 +1557,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     CK(cudaMallocHost(&c->h_out, sizeof(double) * kMaxRhs));
     CK(cudaMallocHost(&c->h_err, sizeof(int)));
     *c->h_err = 0;
+    CK(cudaMallocHost(&c->h_bflags, 2 * sizeof(int)));
+    c->h_bflags[0] = c->h_bflags[1] = 0;
 
     // ---- linear objective vector
     if (c->obj == SUPPY_OBJ_LINEAR) {
@@ -1884,6 +1896,7 @@ void destroy_impl(suppy_ctx* c) {
     for (auto& a : c->allocs) cudaFree(a.first);
     if (c->h_out) cudaFreeHost(c->h_out);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_bflags) cudaFreeHost(c->h_bflags);
     delete c;
 }
 
@@ -1941,7 +1954,8 @@ suppy_status suppy_set_stream(suppy_ctx* c, void* stream) {
 namespace {
 
 // New slab bounds, validated; the old ones stay when the call is rejected.
-suppy_status load_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
+suppy_status load_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device,
+                         bool wait = true) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!l || !u) return fail(c, SUPPY_EINVAL, "NULL bounds");
     const size_t mB = (size_t)c->m * c->B_user;
@@ -1961,17 +1975,31 @@ suppy_status load_bounds(suppy_ctx* c, const float* l, const float* u, int32_t o
     // row order; the permutation into the device layout is skipped on the
     // device when either failed, so a rejected call leaves the old bounds;
     // one synchronization reads both results
-    if (!c->d_flags && (s = dalloc(c, &c->d_flags, 4)) != SUPPY_OK) return s;
+    if (!c->d_flags) {
+        if ((s = dalloc(c, &c->d_flags, 4)) != SUPPY_OK) return s;
+        CK(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
+    }
     CK(cudaMemsetAsync(c->d_flags, 0, 2 * sizeof(int), c->stream));
     CK(launch_check_bounds(c->d_rho, s_l, s_u, c->d_perm, c->m, c->B_user, c->d_flags, c->stream));
     CK(launch_permute_bounds(s_l, s_u, c->d_perm, c->m, c->B_user, c->B, c->d_l, c->d_u, c->stream,
                              c->d_flags, 2));
     note_launch(c, 2);
+    if (!wait) {
+        // the sticky words collect every enqueued check until it is reported
+        CK(cudaMemcpyAsync(c->h_bflags, c->d_flags + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+        c->bounds_pending = true;
+        return SUPPY_OK;
+    }
     int hf[2] = {0, 0};
     if ((s = read_flags(c, c->d_flags, hf, 2)) != SUPPY_OK) return s;
+    // earlier enqueued updates are reported first (their copy landed with
+    // this synchronization); this check's own bits leave the sticky words
+    const suppy_status pending = c->bounds_pending ? err_after_sync(c) : SUPPY_OK;
+    CK(cudaMemsetAsync(c->d_flags + 2, 0, 2 * sizeof(int), c->stream));
     if (hf[0]) return fail(c, SUPPY_EINVAL, "bounds need l <= u and no NaN");
     if (hf[1]) return fail(c, SUPPY_EINVAL, "a zero row needs l <= 0 <= u");
-    return SUPPY_OK;
+    return pending;
 }
 
 }  // namespace
@@ -1986,6 +2014,11 @@ suppy_status suppy_set_bounds(suppy_ctx* c, const float* l, const float* u, int3
 
 suppy_status suppy_update_bounds(suppy_ctx* c, const float* l, const float* u, int32_t on_device) {
     return load_bounds(c, l, u, on_device);
+}
+
+suppy_status suppy_update_bounds_async(suppy_ctx* c, const float* l, const float* u,
+                                       int32_t on_device) {
+    return load_bounds(c, l, u, on_device, false);
 }
 
 }  // extern "C"

@@ -138,7 +138,9 @@ __global__ void k_zero_row_check(const double* rho, const float* l, const float*
 // slab must contain 0.
 // New slab bounds in one pass over the device rows: NaN or l > u anywhere
 // sets bit 1 of flags[0]; a zero row whose slab excludes 0 sets flags[1].
-// (Each source row is the image of exactly one device row.)
+// flags[2] and flags[3] receive the same bits and keep them across calls
+// (the report of checks that were only enqueued).  (Each source row is the
+// image of exactly one device row.)
 __global__ void k_check_bounds(const double* rho, const float* l_in, const float* u_in,
                                const int* perm, int m, int B_in, int* flags) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -147,8 +149,14 @@ __global__ void k_check_bounds(const double* rho, const float* l_in, const float
         for (int b = 0; b < B_in; ++b) {
             const size_t o = (size_t)src * B_in + b;
             const float lv = l_in[o], uv = u_in[o];
-            if (isnan(lv) || isnan(uv) || !(lv <= uv)) atomicOr(flags, 1);
-            if (zero && !(lv <= 0.f && uv >= 0.f)) atomicOr(flags + 1, 1);
+            if (isnan(lv) || isnan(uv) || !(lv <= uv)) {
+                atomicOr(flags, 1);
+                atomicOr(flags + 2, 1);
+            }
+            if (zero && !(lv <= 0.f && uv >= 0.f)) {
+                atomicOr(flags + 1, 1);
+                atomicOr(flags + 3, 1);
+            }
         }
     }
 }

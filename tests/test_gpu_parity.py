@@ -699,6 +699,45 @@ def test_box_step_covers_empty_columns_after_perturbation(mode, omode, strategy,
     assert rel_l2(xg, r.x) <= 1e-5
 
 
+def test_enqueued_bounds_updates_and_their_rejection():
+    """suppy_update_bounds_async gives the iterations suppy_update_bounds
+    gives; a rejected set (NaN) keeps the old bounds and is reported once, by
+    the next synchronizing call, also when a valid set follows it."""
+    prob = small_ct()
+    x0 = random_x(prob.A.n, 1, seed=93)
+    l2 = (prob.l - 0.01 * np.abs(prob.l)).astype(np.float32)   # wider slabs
+    u2 = (prob.u + 0.01 * np.abs(prob.u)).astype(np.float32)
+    out = []
+    for use_async in (False, True):
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS)
+        ctx.suppy_set_x(x0)
+        for _ in range(3):
+            if use_async:
+                ctx.suppy_update_bounds_async(l2, u2)
+            else:
+                ctx.suppy_update_bounds(l2, u2)
+            ctx.suppy_run(_params(max_sweeps=1), want_stats=False)
+        out.append(ctx.suppy_get_x())
+        ctx.close()
+    assert np.array_equal(out[0], out[1])
+    bad = l2.copy()
+    bad[5] = np.nan
+    ref = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS)
+    for c in (ref, ctx):
+        c.suppy_set_x(x0)
+    ctx.suppy_update_bounds_async(bad, u2)          # rejected: the create-time bounds stay
+    ctx.suppy_update_bounds_async(prob.l, prob.u)   # valid, the same bounds
+    ctx.suppy_run(_params(max_sweeps=2), want_stats=False)
+    ref.suppy_run(_params(max_sweeps=2), want_stats=False)
+    with pytest.raises(pk.SuppyError) as e:
+        ctx.suppy_get_x()
+    assert e.value.status == pk.SUPPY_EINVAL
+    assert np.array_equal(ctx.suppy_get_x(), ref.suppy_get_x())   # reported once
+    ctx.close()
+    ref.close()
+
+
 def test_run_without_statistics_enqueues_the_same_iterations():
     """suppy_run with out = NULL (and no stopping rule) returns after
     enqueuing; the next synchronizing call sees exactly the iterations a
