@@ -660,16 +660,21 @@ def ours(args):
     return 0
 
 
-def profile_case(case: int, steps: int) -> int:
+def profile_case(case: int, steps: int, warm: int = 0) -> int:
     """A short run for ncu.  Cases 1 / 2: CT 384x384 (A ~0.4 GB, above L2; the
     device holds about 1 GB) with the one- / two-pass sweep.  Case 3: the CT
     512x512 workload with the sweep and launch shapes bench.py uses (two
     passes, shapes tuned at create); case 4: the same with the one-pass sweep;
     case 5: the horseshoe radiotherapy plan as a split problem (dose-volume
     sets by the CQ step, slabs by EMR, mean-dose perturbations); case 6: the
-    CT 512x512 workload block-iteratively (36 interleaved angle blocks, tuned).
+    CT 512x512 workload block-iteratively (36 interleaved angle blocks, tuned);
+    case 7: the seismic workload with 16 right-hand sides (batched register-fed
+    two-pass sweep, one perturbation cluster per image); case 8: CT 384x384
+    with EMR and the variance rule evaluated every iteration (extrapolation
+    and variance kernels).
     The profiled iterations run inside the NVTX range "profile", so that
-    `ncu --nvtx --nvtx-include profile/` skips the tuning launches."""
+    `ncu --nvtx --nvtx-include profile/` skips the tuning launches and the
+    `warm` iterations run before it."""
     import torch
     import synth
     from paper_2606_27086_gb300 import build as pkbuild
@@ -687,6 +692,14 @@ def profile_case(case: int, steps: int) -> int:
         prob = ct512()
         prob.blocks = synth.angle_blocks(360, 725, 36)
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP, tune=1)
+    elif case == 7:
+        prob = synth.seismic_problem(nrhs=16)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ANISO, strategy=pk.STRATEGY_TWO_PASS)
+    elif case == 8:
+        prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
+                                seed_noise=202)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EMR)
+        params = dict(SUP, variance_tol=1e-30)
     elif case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
@@ -696,6 +709,9 @@ def profile_case(case: int, steps: int) -> int:
         prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
                                 seed_noise=202)
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=case)
+    if warm:
+        # steady state first: the early phases spend many trials
+        ctx.suppy_run(pk.suppy_params_default(max_sweeps=warm, **params))
     torch.cuda.synchronize()
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx:
@@ -716,6 +732,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--profile-warmup", type=int, default=0,
+                    help="with --profile: unprofiled iterations before the profiled ones (300 "
+                         "reaches the steady state; 0 profiles the first iterations)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -723,15 +742,17 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=128,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
                          "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
                          "pass; 5 the horseshoe split problem (DVCs by the CQ step); 6 CT "
-                         "512x512 with 36 BIP blocks")
+                         "512x512 with 36 BIP blocks; 7 seismic with 16 right-hand sides; 8 "
+                         "CT 384x384 with EMR and the variance rule")
     args = ap.parse_args()
     if args.profile:
-        return profile_case(args.profile, args.steps if args.steps < 50 else 6)
+        return profile_case(args.profile, args.steps if args.steps < 50 else 6,
+                            args.profile_warmup)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -100,3 +100,26 @@ def test_adaptive_parameters_are_validated():
             ctx.suppy_perturb(_params(**kw))
         assert e.value.status == pk.SUPPY_EINVAL
     ctx.close()
+
+
+def test_checkpoint_keeps_the_adaptive_reference():
+    """The automatic reference value travels in the checkpoint: a restored
+    context continues the adaptive run exactly as the uninterrupted one (the
+    two-pass sweep and the fixed-order perturbation are bitwise
+    reproducible)."""
+    rt = synth.rt_problem(nx=30, ny=20, nz=12, ns=9, nzb=7)
+    P = _params(adaptive=1, max_sweeps=5, use_stopping=0)
+    ctx = pk.from_problem(rt, mode=pk.SUPPY_BIP, obj=pk.SUPPY_OBJ_LINEAR,
+                          strategy=pk.STRATEGY_TWO_PASS)
+    ctx.suppy_set_x(np.ones(rt.A.n, np.float32))
+    ctx.suppy_run(P)
+    blob = ctx.suppy_get_state()
+    ctx.suppy_run(P)
+    x_a = ctx.suppy_get_x().copy()
+    st_a = ctx.suppy_run(_params(adaptive=1, max_sweeps=0))[0]
+    ctx.suppy_set_state(blob)
+    ctx.suppy_run(P)
+    st_b = ctx.suppy_run(_params(adaptive=1, max_sweeps=0))[0]
+    assert np.array_equal(ctx.suppy_get_x(), x_a)
+    assert st_b["accepted"] == st_a["accepted"] and st_a["accepted"] >= 2
+    ctx.close()
