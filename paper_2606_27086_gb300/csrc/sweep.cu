@@ -441,17 +441,38 @@ __global__ void __launch_bounds__(kSweepThreads) k_colpass_batched(const ColArgs
         const VT* vcol = val + ci.x;
         const int* rcol = a.ridx + ci.x;
         float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int e = e0; e < ci.y; e += E) {
-            const float v = (float)__ldg(vcol + e);
-            int r = __ldg(rcol + e);
+        auto load_el = [&](int e, float& v, int& r) {
+            v = (float)__ldg(vcol + e);
+            r = __ldg(rcol + e);
             if (!CHECKED(r >= 0 && r < a.m && ALIGNED16(a.coef + (size_t)r * B + 4 * q), 313,
                          (long long)j * 64 + e))
                 r = 0;
-            const float4 cv = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r * B) + q);
+        };
+        auto fma4 = [&](float v, const float4& cv) {
             s.x = fmaf(v, cv.x, s.x);
             s.y = fmaf(v, cv.y, s.y);
             s.z = fmaf(v, cv.z, s.z);
             s.w = fmaf(v, cv.w, s.w);
+        };
+        int e = e0;
+        // four elements a lane in flight: their loads, then their gathers
+        for (; e + 3 * E < ci.y; e += 4 * E) {
+            float v[4];
+            int r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) load_el(e + u * E, v[u], r[u]);
+            float4 cv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                cv[u] = __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r[u] * B) + q);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) fma4(v[u], cv[u]);
+        }
+        for (; e < ci.y; e += E) {
+            float v;
+            int r;
+            load_el(e, v, r);
+            fma4(v, __ldg(reinterpret_cast<const float4*>(a.coef + (size_t)r * B) + q));
         }
 #pragma unroll
         for (int o = 16; o >= Q; o >>= 1) {
