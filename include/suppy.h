@@ -24,7 +24,13 @@
  *                          for N consecutive iterations, N_max) and Sec. 2.2.3
  *                          (relative change of f below df*)
  *   objectives             Eq. (TV) with its Combettes/Penfold subgradient
- *                          (Sec. 2.3.1); anisotropic TV; f_Mean of Sec. 2.3.3
+ *                          (Sec. 2.3.1); anisotropic TV; f_Mean of Sec. 2.3.3;
+ *                          the L1 / L2 perturbations of the seismic study
+ *   adaptive step          beta = (f - f_ref)/||g_f|| of Nikazad et al. (Sec. 2.1.2)
+ *   variance stopping      the CT study's variance of relative changes (Sec. 3.2)
+ *   DROP, EL, EMR          the appendix table of used methods, in slab form
+ *   split feasibility      Eq. (Split) and the CQ iteration after it, with the
+ *                          dose-volume constraints of Sec. 2.3.3 as the sets Q_j
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -35,8 +41,8 @@
  * - Pointers flagged "on_device" are CUDA device pointers of the current
  *   device; otherwise they are host pointers (pageable or pinned).  Inputs are
  *   always copied: the caller keeps ownership and may free them after the call
- *   returns.  Library device memory is owned by the context until
- *   suppy_destroy.
+ *   returns (suppy_update_bounds_async: after the next synchronizing call).
+ *   Library device memory is owned by the context until suppy_destroy.
  * - All GPU work is enqueued on the context's stream (suppy_create /
  *   suppy_set_stream).  Calls that return host values (proximity, objective,
  *   get_x to host, run statistics, state) synchronize that stream.  A context
@@ -291,11 +297,16 @@ suppy_status suppy_get_x(suppy_ctx* ctx, float* x, int32_t on_device);
 suppy_status suppy_perturb(suppy_ctx* ctx, const suppy_params* p, int32_t* accepted);
 
 /* Apply the feasibility-seeking operator T nsweeps times (no perturbation):
- * Cimmino -- one fused pass over A computing r = A x, the clamped corrections
- * and their scatter, then x <- box(x + delta); BIP -- the same per block.  Each
- * sweep records the monitored proximity (Cimmino: P at the sweep's input point;
- * BIP: the sum of each block's terms at that block's input point) and advances
- * the stopping rule when p->use_stopping is set.  Asynchronous. */
+ * Cimmino -- x <- box(x + lambda sum_i w_i (P_i x - x)), by the strategy
+ * chosen at create (one pass over A scattering the corrections, then the box
+ * kernel; or a row pass writing the coefficients and a column pass over the
+ * CSC copy applying the sum and the box); BIP -- the same per block, the box
+ * after each block; DROP, EL and EMR -- their steps (suppy_mode).  With
+ * dose-volume constraints (suppy_set_dvc) each sweep starts with the CQ step.
+ * Each sweep records the monitored proximity (Cimmino: P at the sweep's input
+ * point; BIP: the sum of each block's terms at that block's input point;
+ * split problems: the target-space proximity) and advances the stopping rule
+ * when p->use_stopping is set.  Asynchronous. */
 suppy_status suppy_sweep(suppy_ctx* ctx, const suppy_params* p, int32_t nsweeps);
 
 /* Eq. (WeightedProximity) at the current x, w_i = 1/m', FP64, deterministic:
