@@ -27,7 +27,7 @@
  *                          (Sec. 2.3.1); anisotropic TV; f_Mean of Sec. 2.3.3;
  *                          the L1 / L2 perturbations of the seismic study
  *   adaptive step          beta = (f - f_ref)/||g_f|| of Nikazad et al. (Sec. 2.1.2)
- *   variance stopping      the CT study's variance of relative changes (Sec. 3.2)
+ *   variance stopping      the CT study's variance of relative changes (Sec. 2.3.2)
  *   DROP, EL, EMR          the appendix table of used methods, in slab form
  *   split feasibility      Eq. (Split) and the CQ iteration after it, with the
  *                          dose-volume constraints of Sec. 2.3.3 as the sets Q_j
@@ -184,7 +184,7 @@ typedef struct {
     int32_t patience;       /* N                                                   */
     int32_t use_stopping;   /* 0: run exactly max_sweeps sweeps                    */
     int32_t use_graphs;     /* 1: suppy_run replays one captured iteration (CUDA graph) */
-    /* > 0: the variance stopping rule of the CT study (Sec. 3.2): a right-hand
+    /* > 0: the variance stopping rule of the CT study (Sec. 2.3.2): a right-hand
      * side stops after iteration k >= 2 once the sample variance of the
      * relative changes ||x^i - x^(i-1)|| / ||x^i||, i = 1..k, of its iterates
      * (since the last set_x / set_bounds / reset) is below variance_tol.  Applies

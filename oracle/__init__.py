@@ -498,7 +498,7 @@ class Params:
     patience: int = 5
     obj_rel: float = 1e-6
     use_stopping: bool = False      # False: run exactly max_sweeps sweeps
-    variance_tol: float = 0.0       # > 0: the variance stopping rule (Sec. 3.2, CT study)
+    variance_tol: float = 0.0       # > 0: the variance stopping rule (Sec. 2.3.2, CT study)
     adaptive: int = 0               # 1: adaptive step, f_ref automatic (Q29); 2: f_ref fixed
     f_ref: float = 0.0              # the reference value when adaptive == 2
 
@@ -628,7 +628,7 @@ class RunResult:
 
 
 def variance_of_changes(omega: list) -> float:
-    """Variance stopping measure of the CT study (Sec. 3.2): the sample
+    """Variance stopping measure of the CT study (Sec. 2.3.2): the sample
     variance 1/(k-1) sum_i (omega_i - mean)^2 of the relative changes
     omega_i = ||x^i - x^(i-1)|| / ||x^i|| of all iterates so far."""
     w = np.asarray(omega, np.float64)
