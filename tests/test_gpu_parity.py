@@ -353,7 +353,9 @@ def test_graph_replay_equals_direct_launches(strategy, mode):
     if strategy == pk.STRATEGY_TWO_PASS:
         np.testing.assert_array_equal(xs[0], xs[1])
     else:
-        assert rel_l2(xs[1], xs[0]) <= 1e-5
+        # the one-pass scatter adds in a varying order: FP32 rounding
+        # differences over 15 superiorized sweeps (1e-5 a sweep)
+        assert rel_l2(xs[1], xs[0]) <= 1e-4
 
 
 def test_perturbation_resident_kernel_on_large_image():
