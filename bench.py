@@ -314,6 +314,7 @@ def variants(pk, K, W):
                      "col_lanes": info["col_lanes"], "nblocks": info["nblocks"],
                      "tma": info["tma"], "tile": info["tile"], "stages": info["stages"],
                      "col_tile": info["col_tile"], "col_stages": info["col_stages"],
+                     "map": info["map"], "col_map": info["col_map"],
                      "launches_per_step": nl / Kv}
         if split:
             out[name]["nnz_split"] = nnz_q
@@ -640,7 +641,8 @@ def ours(args):
            "launch_shape": {k: info[k] for k in ("strategy", "scatter", "tma", "lanes_per_row",
                                                   "elems_in_regs", "grid", "col_lanes",
                                                   "col_grid", "perturb_cluster", "tile", "stages",
-                                                  "col_tile", "col_stages")}}
+                                                  "col_tile", "col_stages", "map",
+                                                  "col_map")}}
     ctx.close()
     if rank == 0 and not args.no_variants:
         res["variants"] = variants(pk, K, min(W, 5))

@@ -164,6 +164,12 @@ typedef struct {
      * cluster per right-hand side; 1 -- the cluster kernel alone; 0 --
      * automatic: 2 for one right-hand side with n >= 65536, else 1. */
     int32_t perturb_path;
+    /* Lane map of the streaming passes: 0 automatic (measured when tune is
+     * set), 1 four consecutive elements per lane (16-byte ring reads),
+     * 2 lane-interleaved elements (lane k of a group takes elements k, k + G,
+     * k + 2G, ...: one gather instruction reads G consecutive elements of an
+     * item).  Other values give SUPPY_EINVAL. */
+    int32_t stream_map;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -229,6 +235,7 @@ typedef struct {
     int32_t tma;                  /* 1: the sweep streams A by bulk copies   */
     int32_t tile, stages;         /* streaming row pass: ring tile length (elements), stages */
     int32_t col_tile, col_stages; /* streaming column pass: the same       */
+    int32_t map, col_map;         /* streaming lane maps (opts.stream_map: 1 or 2) */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

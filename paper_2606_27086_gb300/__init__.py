@@ -56,7 +56,8 @@ class suppy_opts(ctypes.Structure):
                 ("nrhs", ctypes.c_int32), ("box_len", ctypes.c_int64), ("tune", ctypes.c_int32),
                 ("strategy", ctypes.c_int32), ("tma", ctypes.c_int32),
                 ("stream_tile", ctypes.c_int32), ("stream_stages", ctypes.c_int32),
-                ("stream_lanes", ctypes.c_int32), ("perturb_path", ctypes.c_int32)]
+                ("stream_lanes", ctypes.c_int32), ("perturb_path", ctypes.c_int32),
+                ("stream_map", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -107,7 +108,8 @@ class suppy_info(ctypes.Structure):
                 ("col_lanes", ctypes.c_int32), ("col_grid", ctypes.c_int32),
                 ("tma", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("col_tile", ctypes.c_int32),
-                ("col_stages", ctypes.c_int32)]
+                ("col_stages", ctypes.c_int32), ("map", ctypes.c_int32),
+                ("col_map", ctypes.c_int32)]
 
 
 _lib = None
@@ -237,7 +239,7 @@ class Context:
     def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
                  c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None,
-                 stream_shape=(0, 0, 0), perturb_path=0):
+                 stream_shape=(0, 0, 0), perturb_path=0, stream_map=0):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -274,6 +276,7 @@ class Context:
         o.tma = int(tma)
         o.stream_tile, o.stream_stages, o.stream_lanes = (int(v) for v in stream_shape)
         o.perturb_path = int(perturb_path)
+        o.stream_map = int(stream_map)
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
@@ -440,7 +443,7 @@ class Context:
 
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
                  stream=None, tune=0, strategy=0, tma=0, stream_shape=(0, 0, 0),
-                 perturb_path=0) -> Context:
+                 perturb_path=0, stream_map=0) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -464,7 +467,7 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
                    block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
                    strategy=strategy, tma=tma, stream_shape=stream_shape,
-                   perturb_path=perturb_path, **kw)
+                   perturb_path=perturb_path, stream_map=stream_map, **kw)
 
 
 def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,

@@ -22,6 +22,13 @@ thread_local std::string g_err;
 // this much zeroed slack after the last item, since a pass reads whole tiles.
 constexpr int kMaxTile = 4096;
 
+// Lane maps of the streaming row and column passes when neither the caller
+// nor the tuner chose one (0 quads per lane, 1 lane-interleaved).  On the
+// CT 512x512 matrix the row pass ran faster with quads (217 against 249 us)
+// and the column pass with interleaved lanes (202 against 213 us).
+constexpr int kDefaultRowMap = 0;
+constexpr int kDefaultColMap = 1;
+
 // Stored length of an item: rows and columns start at multiples of four
 // elements and are zero-padded to a multiple of four.
 inline long long pad4(long long len) { return (len + 3) & ~3LL; }
@@ -120,6 +127,7 @@ struct suppy_ctx {
     int tile = 4096, stages = 6;    // row pass ring: tile length, stages
     int ctile = 4096, cstages = 6;  // column pass ring
     int tG = 32, tGc = 32;          // lanes per item of the streaming row / column passes
+    int tMap = 0, tMapc = 0;        // their lane maps (0 quads per lane, 1 lane-interleaved)
     int max_row = 0, max_col = 0;
     std::vector<int> seg_tgrid, seg_ctgrid;
     std::vector<size_t> seg_tpart_off, seg_ctpart_off;
@@ -486,7 +494,7 @@ suppy_status enqueue_ext_step(suppy_ctx* c, const suppy_params* p, int t, int np
             q.check_stop = 1;
             Timed tm{c, 0};
             CK(tm.begin());
-            CK(launch_rows_tma(q, c->dt, c->tG, 0, c->seg_tgrid[t], c->stream));
+            CK(launch_rows_tma(q, c->dt, c->tG, 0, c->tMap, c->seg_tgrid[t], c->stream));
             CK(tm.end());
         } else {
             SweepArgs q = row_args(c, t, 0.f);
@@ -610,7 +618,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             {
                 Timed tm{c, 0};
                 CK(tm.begin());
-                CK(launch_rows_tma(sa, c->dt, c->tG, c->strategy == 2 ? 0 : 1, c->seg_tgrid[t],
+                CK(launch_rows_tma(sa, c->dt, c->tG, c->strategy == 2 ? 0 : 1, c->tMap, c->seg_tgrid[t],
                                    c->stream));
                 CK(tm.end());
                 note_launch(c);
@@ -636,7 +644,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 {
                     Timed tm{c, 1};
                     CK(tm.begin());
-                    CK(launch_cols_tma(ca, c->dt, c->tGc, c->seg_ctgrid[t], c->stream));
+                    CK(launch_cols_tma(ca, c->dt, c->tGc, c->tMapc, c->seg_ctgrid[t], c->stream));
                     CK(tm.end());
                     note_launch(c);
                 }
@@ -1238,40 +1246,46 @@ bool tma_eligible(const suppy_ctx* c, int want) {
 
 // Measured choice of the streaming passes' shapes: every ring (tile length
 // 1024 / 2048 / 4096 elements, the full shared-memory budget of stages or
-// half of it) and group width (4 .. 32 lanes per item) whose window holds a
-// warp's round is timed on this matrix, first for the row pass, then for the
-// column pass; the fastest stays.
-suppy_status tune_tma(suppy_ctx* c) {
+// half of it), group width (4 .. 32 lanes per item) whose window holds a
+// warp's round, and lane map (both, unless the caller fixed it) is timed on
+// this matrix, first for the row pass, then for the column pass; the fastest
+// stays.
+suppy_status tune_tma(suppy_ctx* c, bool tune_map) {
     struct Shape {
-        int G, tile, stages;
+        int G, tile, stages, map;
     };
-    auto cands = [&](int max_item) {
+    auto cands = [&](int max_item, int map_now) {
         std::vector<Shape> v;
         for (int tile : {1024, 2048, 4096}) {
             const int full = stream_stages_for(c->dt, tile);
             for (int st : {full, full / 2}) {
                 if (st < 3 || stream_max_item(tile, st) < max_item) continue;
                 for (int G : {4, 8, 16, 32})
-                    if (group_fits(G, max_item, tile, st)) v.push_back({G, tile, st});
+                    if (group_fits(G, max_item, tile, st))
+                        for (int map = tune_map ? 0 : map_now; map <= (tune_map ? 1 : map_now); ++map)
+                            v.push_back({G, tile, st, map});
             }
         }
         return v;
     };
     suppy_status s;
     for (int pass = 0; pass < (c->strategy == 2 ? 2 : 1); ++pass) {
-        const std::vector<Shape> v = cands(pass == 0 ? c->max_row : c->max_col);
+        const std::vector<Shape> v =
+            cands(pass == 0 ? c->max_row : c->max_col, pass == 0 ? c->tMap : c->tMapc);
         Shape best{pass == 0 ? c->tG : c->tGc, pass == 0 ? c->tile : c->ctile,
-                   pass == 0 ? c->stages : c->cstages};
+                   pass == 0 ? c->stages : c->cstages, pass == 0 ? c->tMap : c->tMapc};
         float best_ms = 1e30f;
         for (const Shape& sh : v) {
             if (pass == 0) {
                 c->tG = sh.G;
                 c->tile = sh.tile;
                 c->stages = sh.stages;
+                c->tMap = sh.map;
             } else {
                 c->tGc = sh.G;
                 c->ctile = sh.tile;
                 c->cstages = sh.stages;
+                c->tMapc = sh.map;
             }
             if ((s = build_tma_partitions(c)) != SUPPY_OK) return s;
             float ms = 0.f;
@@ -1285,10 +1299,12 @@ suppy_status tune_tma(suppy_ctx* c) {
             c->tG = best.G;
             c->tile = best.tile;
             c->stages = best.stages;
+            c->tMap = best.map;
         } else {
             c->tGc = best.G;
             c->ctile = best.tile;
             c->cstages = best.stages;
+            c->tMapc = best.map;
         }
     }
     return build_tma_partitions(c);
@@ -1325,6 +1341,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_lanes must be 0, 4, 8, 16 or 32");
         if (st != 0 && (st < 2 || st > stream_stages_for(o->a_dtype, t ? t : kMaxTile)))
             return fail(c, SUPPY_EINVAL, "stream_stages must be 0 or 2.. the shared-memory budget");
+        if (o->stream_map < 0 || o->stream_map > 2)
+            return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
     }
     c->B = 1;
     if (c->B_user > 1) {
@@ -1668,6 +1686,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     choose_row_shape(c, mean_len, max_len);
     if ((s = build_row_partition(c)) != SUPPY_OK) return s;
     default_tma_shape(c);
+    c->tMap = o->stream_map ? o->stream_map - 1 : kDefaultRowMap;
+    c->tMapc = o->stream_map ? o->stream_map - 1 : kDefaultColMap;
     const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
     if (fixed_shape) apply_stream_shape(c, o->stream_tile, o->stream_stages, o->stream_lanes);
     c->use_tma = tma_eligible(c, o->tma);
@@ -1677,7 +1697,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         c->use_tma = false;
     if (c->use_tma) {
         if ((s = build_tma_partitions(c)) != SUPPY_OK) return s;
-        if (o->tune && !fixed_shape && (s = tune_tma(c)) != SUPPY_OK) return s;
+        if (o->tune && !fixed_shape && (s = tune_tma(c, o->stream_map == 0)) != SUPPY_OK) return s;
     }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
@@ -2509,6 +2529,8 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->stages = c->use_tma ? c->stages : 0;
     out->col_tile = (c->use_tma && c->strategy == 2) ? c->ctile : 0;
     out->col_stages = (c->use_tma && c->strategy == 2) ? c->cstages : 0;
+    out->map = c->use_tma ? c->tMap + 1 : 0;
+    out->col_map = (c->use_tma && c->strategy == 2) ? c->tMapc + 1 : 0;
     if (c->use_tma) {
         out->grid = c->seg_tgrid[0];
         out->block = kStreamThreads;

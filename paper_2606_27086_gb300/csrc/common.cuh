@@ -229,9 +229,13 @@ size_t stream_smem_bytes(suppy_dtype dt, int tile, int stages);
 int stream_stages_for(suppy_dtype dt, int tile);   // stages filling the shared-memory budget
 int stream_max_item(int tile, int stages);          // longest item a ring window holds
 int stream_blocks_per_sm(suppy_dtype dt, int tile, int stages);
-cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
+// map: how a group's G lanes split an item -- 0 four consecutive elements per
+// lane and 16-byte ring reads, 1 lane-interleaved elements (lane gl takes
+// gl, gl + G, ...) and 4-byte ring reads
+cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int map, int grid,
                             cudaStream_t s);
-cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s);
+cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int map, int grid,
+                            cudaStream_t s);
 // scat: 0 no scatter (proximity / coefficient output), 1 global reductions,
 // 2 shared-memory staged reductions (n * 4 bytes of shared memory)
 cudaError_t launch_sweep(const SweepArgs& a, suppy_dtype dt, int G, int maxe, int scat, int grid,

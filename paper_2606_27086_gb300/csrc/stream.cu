@@ -8,8 +8,9 @@
 // (cp.async.bulk, L2 evict-first) tracked by mbarriers; twenty-three consumer
 // warps, split into groups of G lanes (one group per item), take batches of
 // consecutive items in order from a shared counter and read them from the
-// ring four elements per 16-byte access, so HBM streaming runs ahead of the
-// gathers of x (or of the coefficients) instead of waiting behind them.  A
+// ring (four consecutive elements per lane and 16-byte access, or lane-
+// interleaved elements), so HBM streaming runs ahead of the gathers of x (or
+// of the coefficients) instead of waiting behind them.  A
 // stage is refilled once every item element of its tile is done.  G, T and S are launch parameters (chosen per matrix,
 // by measurement when the context is tuned).
 //
@@ -219,6 +220,87 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
     return acc0 + acc1;
 }
 
+// Lane-interleaved form of ring_dot: lane gl takes the elements gl, gl + G,
+// gl + 2G, ... of the item, U per batch, with 4-byte ring reads.  One
+// gather instruction of a group then reads G consecutive elements of the
+// item (and the group beside it the same positions of the next item), which
+// for the rows of a ray and the columns of neighbouring pixels lie in far
+// fewer cache lines than the 4G-element spread of one quad-form instruction.
+// Masked-off positions are not read; the padding is never touched.
+template <typename VT, int G, int U>
+__device__ __forceinline__ float ring_dot_il(const Ring<VT>& r, int g0, int len, int gl,
+                                             const float* __restrict__ vec) {
+    float acc0 = 0.f, acc1 = 0.f;
+    const int p0 = r.pos(g0);
+    const int n = len - gl;   // this lane's elements: gl + e with e = t G < n
+    auto fma_batch = [&](const float* av, const float* xv) {
+#pragma unroll
+        for (int t = 0; t < U; t += 2) {
+            acc0 = fmaf(av[t], xv[t], acc0);
+            acc1 = fmaf(av[t + 1], xv[t + 1], acc1);
+        }
+    };
+    if (p0 + len <= r.size) {
+        const VT* v = r.val + p0 + gl;
+        const int* ix = r.idx + p0 + gl;
+        int e = 0;
+        for (; e + (U - 1) * G < n; e += U * G) {
+            int c[U];
+            float av[U], xv[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                c[t] = ix[e + t * G];
+                av[t] = to_f(v[e + t * G]);
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
+            fma_batch(av, xv);
+        }
+        if (e < n) {
+            // fewer than U elements left for this lane: one masked batch
+            int c[U];
+            float av[U], xv[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const bool in = e + t * G < n;
+                c[t] = in ? ix[e + t * G] : 0;
+                av[t] = in ? to_f(v[e + t * G]) : 0.f;
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
+            fma_batch(av, xv);
+        }
+    } else {
+        // the item wraps around the end of the ring
+        int p = p0 + gl;
+        if (p >= r.size) p -= r.size;
+        for (int e = 0; e < n; e += U * G) {
+            int c[U];
+            float av[U], xv[U];
+#pragma unroll
+            for (int t = 0; t < U; ++t) {
+                const bool in = e + t * G < n;
+                c[t] = in ? r.idx[p] : 0;
+                av[t] = in ? to_f(r.val[p]) : 0.f;
+                r.step(p, G);
+            }
+#pragma unroll
+            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
+            fma_batch(av, xv);
+        }
+    }
+    return acc0 + acc1;
+}
+
+// U: elements a lane holds per batch of the lane-interleaved form (the row
+// pass keeps more per-item state live and takes fewer, spilling none).
+template <typename VT, int G, int MAP, int U>
+__device__ __forceinline__ float item_dot(const Ring<VT>& r, int g0, int len, int gl,
+                                          const float* __restrict__ vec) {
+    if constexpr (MAP == 1) return ring_dot_il<VT, G, U>(r, g0, len, gl, vec);
+    else return ring_dot<VT, G>(r, g0, len, gl, vec);
+}
+
 // Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes.
 // A warp takes the next 32/G consecutive items of the CTA's range from a
 // shared counter (one group per item), so all warps move through the slice
@@ -408,7 +490,7 @@ __device__ __forceinline__ void cta_sum_to(double v, double* out) {
 }
 
 // Row pass.  SCAT 0: coefficients written to a.coef (when set); 1: scatter.
-template <typename VT, int G, int SCAT>
+template <typename VT, int G, int SCAT, int MAP>
 struct RowWork {
     const StreamArgs& a;
     float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
@@ -445,7 +527,7 @@ struct RowWork {
     __device__ void empty(int) {}   // an empty row: no coefficient, no proximity term
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        float dot = ring_dot<VT, G>(r, g0, len, gl, a.x);
+        float dot = item_dot<VT, G, MAP, 12>(r, g0, len, gl, a.x);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;
@@ -465,16 +547,16 @@ struct RowWork {
     }
 };
 
-template <typename VT, int G, int SCAT>
+template <typename VT, int G, int SCAT, int MAP>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs a) {
     if (a.check_stop && a.st[0].stopped) return;
-    RowWork<VT, G, SCAT> work{a};
+    RowWork<VT, G, SCAT, MAP> work{a};
     stream_items<VT, G>(a, work);
     cta_sum_to(work.total(), a.pp + blockIdx.x);
 }
 
 // Column pass of the two-pass sweep (B = 1).
-template <typename VT, int G>
+template <typename VT, int G, int MAP>
 struct ColWork {
     const StreamArgs& a;
     float xj = 0.f, lo = 0.f, hi = 0.f, z = 1.f;
@@ -502,7 +584,7 @@ struct ColWork {
     }
     __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        float s = ring_dot<VT, G>(r, g0, len, gl, a.coef_in);
+        float s = item_dot<VT, G, MAP, sizeof(VT) == 4 ? 16 : 12>(r, g0, len, gl, a.coef_in);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
         if (a.zc) s *= z;
@@ -514,10 +596,10 @@ struct ColWork {
     }
 };
 
-template <typename VT, int G>
+template <typename VT, int G, int MAP>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs a) {
     if (a.epi.st[0].stopped) return;   // the row pass left no coefficients
-    ColWork<VT, G> work{a};
+    ColWork<VT, G, MAP> work{a};
     stream_items<VT, G>(a, work);
     __syncthreads();
     if (blockIdx.x == 0 && !a.epi.last_seg) {
@@ -539,36 +621,46 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs
 
 using StreamFn = void (*)(StreamArgs);
 
-template <typename VT>
+template <typename VT, int MAP>
 StreamFn pick_rows(int G, int scat) {
     switch (G) {
-        case 4: return scat ? k_rows_tma<VT, 4, 1> : k_rows_tma<VT, 4, 0>;
-        case 8: return scat ? k_rows_tma<VT, 8, 1> : k_rows_tma<VT, 8, 0>;
-        case 16: return scat ? k_rows_tma<VT, 16, 1> : k_rows_tma<VT, 16, 0>;
-        default: return scat ? k_rows_tma<VT, 32, 1> : k_rows_tma<VT, 32, 0>;
+        case 4: return scat ? k_rows_tma<VT, 4, 1, MAP> : k_rows_tma<VT, 4, 0, MAP>;
+        case 8: return scat ? k_rows_tma<VT, 8, 1, MAP> : k_rows_tma<VT, 8, 0, MAP>;
+        case 16: return scat ? k_rows_tma<VT, 16, 1, MAP> : k_rows_tma<VT, 16, 0, MAP>;
+        default: return scat ? k_rows_tma<VT, 32, 1, MAP> : k_rows_tma<VT, 32, 0, MAP>;
+    }
+}
+
+template <typename VT, int MAP>
+StreamFn pick_cols(int G) {
+    switch (G) {
+        case 4: return k_cols_tma<VT, 4, MAP>;
+        case 8: return k_cols_tma<VT, 8, MAP>;
+        case 16: return k_cols_tma<VT, 16, MAP>;
+        default: return k_cols_tma<VT, 32, MAP>;
     }
 }
 
 template <typename VT>
-StreamFn pick_cols(int G) {
-    switch (G) {
-        case 4: return k_cols_tma<VT, 4>;
-        case 8: return k_cols_tma<VT, 8>;
-        case 16: return k_cols_tma<VT, 16>;
-        default: return k_cols_tma<VT, 32>;
-    }
+StreamFn pick_rows_map(int G, int scat, int map) {
+    return map ? pick_rows<VT, 1>(G, scat) : pick_rows<VT, 0>(G, scat);
 }
 
-StreamFn rows_fn(suppy_dtype dt, int G, int scat) {
-    if (dt == SUPPY_F32) return pick_rows<float>(G, scat);
-    if (dt == SUPPY_BF16) return pick_rows<__nv_bfloat16>(G, scat);
-    return pick_rows<__half>(G, scat);
+template <typename VT>
+StreamFn pick_cols_map(int G, int map) {
+    return map ? pick_cols<VT, 1>(G) : pick_cols<VT, 0>(G);
 }
 
-StreamFn cols_fn(suppy_dtype dt, int G) {
-    if (dt == SUPPY_F32) return pick_cols<float>(G);
-    if (dt == SUPPY_BF16) return pick_cols<__nv_bfloat16>(G);
-    return pick_cols<__half>(G);
+StreamFn rows_fn(suppy_dtype dt, int G, int scat, int map) {
+    if (dt == SUPPY_F32) return pick_rows_map<float>(G, scat, map);
+    if (dt == SUPPY_BF16) return pick_rows_map<__nv_bfloat16>(G, scat, map);
+    return pick_rows_map<__half>(G, scat, map);
+}
+
+StreamFn cols_fn(suppy_dtype dt, int G, int map) {
+    if (dt == SUPPY_F32) return pick_cols_map<float>(G, map);
+    if (dt == SUPPY_BF16) return pick_cols_map<__nv_bfloat16>(G, map);
+    return pick_cols_map<__half>(G, map);
 }
 
 }  // namespace
@@ -608,18 +700,19 @@ static cudaError_t launch_stream(StreamFn f, const StreamArgs& a, suppy_dtype dt
     return cudaGetLastError();
 }
 
-cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int grid,
+cudaError_t launch_rows_tma(const StreamArgs& a, suppy_dtype dt, int G, int scat, int map, int grid,
                             cudaStream_t s) {
-    return launch_stream(rows_fn(dt, G, scat), a, dt, grid, s);
+    return launch_stream(rows_fn(dt, G, scat, map), a, dt, grid, s);
 }
 
-cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int grid, cudaStream_t s) {
-    return launch_stream(cols_fn(dt, G), a, dt, grid, s);
+cudaError_t launch_cols_tma(const StreamArgs& a, suppy_dtype dt, int G, int map, int grid,
+                            cudaStream_t s) {
+    return launch_stream(cols_fn(dt, G, map), a, dt, grid, s);
 }
 
 int stream_blocks_per_sm(suppy_dtype dt, int tile, int stages) {
     const size_t smem = stream_smem_bytes(dt, tile, stages);
-    StreamFn f = rows_fn(dt, 32, 1);
+    StreamFn f = rows_fn(dt, 32, 1, 0);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;

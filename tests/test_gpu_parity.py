@@ -423,21 +423,24 @@ def test_tma_block_iterative_and_long_rows():
     assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
 
 
+@pytest.mark.parametrize("stream_map", [1, 2])
 @pytest.mark.parametrize("strategy", STRATS)
 @pytest.mark.parametrize("shape", [(256, 8, 4), (512, 32, 8), (1024, 4, 16), (2048, 12, 32),
                                    (4096, 2, 32)])
-def test_tma_stream_shapes_match_oracle(shape, strategy):
+def test_tma_stream_shapes_match_oracle(shape, strategy, stream_map):
     """Every ring shape the tuner may pick (tile length, stages, lanes per
-    item) gives the oracle's sweep on ragged items: row and column lengths
-    that are not multiples of four, empty rows, several tiles per CTA."""
+    item, lane map) gives the oracle's sweep on ragged items: row and column
+    lengths that are not multiples of four, empty rows, several tiles per CTA
+    (items wrap around the ring's end)."""
     prob = synth.random_problem(4000, 30011, seed=45, feasible=False, mean_len=37,
                                 empty_frac=0.05, long_rows=5, long_len=190)
-    ctx = pk.from_problem(prob, strategy=strategy, stream_shape=shape)
+    ctx = pk.from_problem(prob, strategy=strategy, stream_shape=shape, stream_map=stream_map)
     info = ctx.suppy_info_get()
-    assert info["tma"] == 1
+    assert info["tma"] == 1 and info["map"] == stream_map
     assert (info["tile"], info["stages"], info["lanes_per_row"]) == shape
     if strategy == pk.STRATEGY_TWO_PASS:
         assert (info["col_tile"], info["col_stages"], info["col_lanes"]) == shape
+        assert info["col_map"] == stream_map
     x0 = random_x(prob.A.n, 1, seed=46)
     ctx.suppy_set_x(x0)
     ctx.suppy_sweep(_params(lam=1.3), 2)
@@ -461,6 +464,7 @@ def test_tuned_stream_shapes_match_oracle():
     assert info["tile"] in (1024, 2048, 4096) and info["col_tile"] in (1024, 2048, 4096)
     assert 3 <= info["stages"] <= 32 and 3 <= info["col_stages"] <= 32
     assert info["lanes_per_row"] in (4, 8, 16, 32) and info["col_lanes"] in (4, 8, 16, 32)
+    assert info["map"] in (1, 2) and info["col_map"] in (1, 2)
     x0 = random_x(prob.A.n, 1, seed=47)
     ctx.suppy_set_x(x0)
     ctx.suppy_sweep(_params(), 1)
@@ -473,6 +477,13 @@ def test_invalid_stream_shapes_are_rejected(shape):
     prob = small_ct()
     with pytest.raises(pk.SuppyError):
         pk.from_problem(prob, stream_shape=shape)
+
+
+@pytest.mark.parametrize("stream_map", [-1, 3])
+def test_invalid_stream_maps_are_rejected(stream_map):
+    with pytest.raises(pk.SuppyError) as e:
+        pk.from_problem(small_ct(), stream_map=stream_map)
+    assert e.value.status == pk.SUPPY_EINVAL
 
 
 @pytest.mark.parametrize("tma", [0, -1])
