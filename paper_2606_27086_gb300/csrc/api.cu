@@ -3,6 +3,7 @@
 // the Algorithm 1 driver loop, checkpoints and measurement hooks.  All compute
 // runs in the kernels of sweep.cu, perturb.cu and setup.cu.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -142,12 +143,11 @@ struct suppy_ctx {
     float* d_slot_l = nullptr;
     float* d_slot_u = nullptr;
     std::vector<unsigned char> zero_row;   // source order: ||a_i|| = 0
-    // whole-GPU first step of the perturbation phase
+    // whole-GPU perturbation phase (one cooperative launch)
     bool wide = false;
     int wide_grid = 0;
-    WideState* d_ws = nullptr;
     double* d_wpart = nullptr;
-    unsigned* d_ticket = nullptr;
+    unsigned* d_ticket = nullptr;   // grid barrier of the whole-GPU perturbation {count, generation}
     std::vector<long long> rpref;   // row-work prefix (m + 1)
     // split feasibility: dose rows A_q (CSR and CSC), structures, DVCs
     bool dvc_on = false;
@@ -760,15 +760,14 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.f_ref = p ? p->f_ref : 0.0;
     a.st = c->d_st;
     a.record_only = record_only;
-    a.ws = c->d_ws;
-    a.resume = 0;
     a.part = c->d_wpart;
     a.ticket = c->d_ticket;
+    a.err = c->d_err;
     Timed tm{c, 2};
     CK(tm.begin());
     if (c->wide && !record_only) {
-        CK(launch_perturb_wide(a, c->wide_grid, c->perturb_cluster, c->stream));
-        note_launch(c, 4);
+        CK(launch_perturb_wide(a, c->wide_grid, c->stream));
+        note_launch(c);
     } else {
         CK(launch_perturb(a, c->perturb_cluster, c->stream));
         note_launch(c);
@@ -789,8 +788,9 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     return SUPPY_OK;
 }
 
-// A streaming kernel whose bounded wait gave up leaves a nonzero error word;
-// report (and clear) it at the next synchronizing call.
+// A streaming pass or the whole-GPU perturbation kernel whose bounded wait
+// gave up leaves a nonzero error word; report (and clear) it at the next
+// synchronizing call.
 // The streaming passes' error word (sticky until read) travels to pinned
 // host memory with the copies of a synchronizing call: enqueue the copy,
 // synchronize once, then look.
@@ -811,7 +811,7 @@ suppy_status err_after_sync(suppy_ctx* c) {
     if (!c->d_err || !*c->h_err) return SUPPY_OK;
     *c->h_err = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass)");
+    return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass or whole-GPU perturbation barrier)");
 }
 
 
@@ -1549,23 +1549,26 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
     if (c->obj != SUPPY_OBJ_NONE) {
         if ((s = dalloc(c, &c->d_g, nB)) != SUPPY_OK) return s;
-        // the whole-GPU first step pays off for one large image (a few fixed
-        // microseconds of launches and reductions against a single cluster's
-        // per-pixel work); with two or more right-hand sides their clusters
-        // already share the GPU and the cluster path is faster (measured on
-        // GB300: 16 seismic images 0.092 against 0.150 ms a phase, 2 images
-        // 0.046 against 0.060 ms); 2 forces it, 1 disables it
-        if (o->perturb_path == 2 ||
-            (o->perturb_path == 0 && (long long)nB >= 65536 && c->B == 1)) {
+        // the whole-GPU phase pays off for one large image (a few fixed
+        // microseconds of grid barriers and reductions against a single
+        // cluster's per-pixel work); with two or more right-hand sides their
+        // clusters already share the GPU, while the whole-GPU kernel takes
+        // them one after the other, so the cluster path is faster; 2 forces
+        // it, 1 disables it
+        // (its pixel loops step an int index by the grid's thread count)
+        const bool wide_fits = (long long)c->n + 4LL * sms * kWideThreads < (long long)INT_MAX;
+        if (wide_fits && (o->perturb_path == 2 ||
+                          (o->perturb_path == 0 && (long long)nB >= 65536 && c->B == 1))) {
+            // a cooperative launch: every CTA must be resident at once
+            const int per_sm = std::min(2, wide_phase_blocks_per_sm());
+            if (per_sm < 1) return fail(c, SUPPY_ECUDA, "whole-GPU perturbation kernel cannot be resident");
             c->wide = true;
             c->wide_grid = (int)std::max<long long>(
-                1, std::min<long long>(2LL * sms, ((long long)nB + kWideThreads - 1) / kWideThreads));
-            if ((s = dalloc(c, &c->d_ws, (size_t)c->B)) != SUPPY_OK) return s;
-            if ((s = dalloc(c, &c->d_wpart, wide_part_doubles(c->wide_grid, c->B))) != SUPPY_OK)
-                return s;
-            if ((s = dalloc(c, &c->d_ticket, 1)) != SUPPY_OK) return s;
-            CK(cudaMemsetAsync(c->d_ws, 0, sizeof(WideState) * c->B, c->stream));
-            CK(cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream));
+                1, std::min<long long>((long long)per_sm * sms,
+                                       ((long long)c->n + kWideThreads - 1) / kWideThreads));
+            if ((s = dalloc(c, &c->d_wpart, wide_part_doubles(c->wide_grid))) != SUPPY_OK) return s;
+            if ((s = dalloc(c, &c->d_ticket, 2)) != SUPPY_OK) return s;
+            CK(cudaMemsetAsync(c->d_ticket, 0, 2 * sizeof(unsigned), c->stream));
         }
     }
     if ((s = dalloc(c, &c->d_st, (size_t)c->B)) != SUPPY_OK) return s;

@@ -123,18 +123,6 @@ struct ColArgs {
 // Per right-hand side state of the first reduction step of a perturbation
 // phase taken by the whole-GPU kernels (k_wide_*); the cluster kernel
 // resumes from it when that step did not finish the phase.
-struct WideState {
-    double gnorm;           // ||g|| at the phase's starting point
-    double fy;              // f at the phase's starting point
-    float step[8];          // beta_j / ||g|| of the trials of one launch
-    float sc;               // accepted step beta / ||g||
-    int acc;                // steps accepted so far in this phase
-    int trials;             // trials so far in this phase
-    int done;               // the phase is complete (bookkeeping written)
-    int pending;            // an accepted step waits for the update kernel
-    int pad;
-};
-
 struct PerturbArgs {
     float* x;               // n x B
     float* g;               // n x B scratch for the subgradient
@@ -148,13 +136,13 @@ struct PerturbArgs {
     double f_ref;           // the fixed reference value (adaptive = 2)
     RhsState* st;
     int record_only;        // 1: compute f(x) into st->f_cur only (no step)
-    WideState* ws;          // whole-GPU first step state (resume mode)
-    int resume;             // 1: continue the phase the k_wide_* kernels began
-    double* part;           // whole-GPU kernels: per-CTA partials
-    unsigned* ticket;       // whole-GPU kernels: CTAs finished (last one reduces)
+    double* part;           // whole-GPU kernel: per-CTA partials (two buffers)
+    unsigned* ticket;       // whole-GPU kernel: grid barrier {arrivals, generation}
+    int* err;               // whole-GPU kernel: error word (2: a barrier timed out)
 };
 
-// CTAs of the whole-GPU perturbation kernels and trial steps per launch.
+// Threads per CTA of the whole-GPU perturbation kernel and the trial points
+// one of its passes evaluates.
 constexpr int kWideThreads = 256;
 constexpr int kWideTrials = 8;
 
@@ -253,8 +241,10 @@ cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s);
 // Whole-GPU first reduction step of a perturbation phase (subgradient pass,
 // kWideTrials trial evaluations in one pass, update) followed by the cluster
 // kernel in resume mode; `grid` CTAs of kWideThreads threads.
-cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, int cluster, cudaStream_t s);
-size_t wide_part_doubles(int grid, int B);   // partials the whole-GPU kernels need
+// the whole phase on the whole GPU, one cooperative launch (grid CTAs, all resident)
+cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, cudaStream_t s);
+size_t wide_part_doubles(int grid);   // partials the whole-GPU kernel needs
+int wide_phase_blocks_per_sm();       // its resident CTAs per SM
 int choose_perturb_cluster(int n, int B);
 int fit_perturb_cluster(int want, int obj, int n, int H, int W);
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s);

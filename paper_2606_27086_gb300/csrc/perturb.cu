@@ -191,19 +191,11 @@ __device__ double2 cluster_sum2(double a, double b, double2* sw, double2* scta,
     return t;
 }
 
-// Where a perturbation phase starts: a fresh phase applies the restart rule
-// (Sec. 2.1.2: l <- r at the r-th restart); in resume mode the whole-GPU
-// kernels already took the first reduction step (or its first trials) and
-// the phase continues from their state.
+// Where a perturbation phase starts: the restart rule (Sec. 2.1.2: l <- r at
+// the r-th restart) applied to the exponent and the restart state.
 struct PhaseStart {
     long long ell;
     int restarts, last_restart_k;
-    int accepted, trials;
-    int s0;        // first reduction step to take
-    int jt0;       // trials already spent in step s0
-    double f_start;
-    bool have_f;
-    bool skip;     // nothing left to do
 };
 
 __device__ __forceinline__ PhaseStart phase_start(const PerturbArgs& a, int b) {
@@ -212,21 +204,6 @@ __device__ __forceinline__ PhaseStart phase_start(const PerturbArgs& a, int b) {
     ps.ell = st.ell;
     ps.restarts = st.restarts;
     ps.last_restart_k = st.last_restart_k;
-    ps.accepted = ps.trials = ps.s0 = ps.jt0 = 0;
-    ps.f_start = 0.0;
-    ps.have_f = false;
-    ps.skip = false;
-    if (a.resume && !a.record_only) {
-        const WideState& w = a.ws[b];
-        ps.skip = w.done != 0;
-        ps.accepted = w.acc;
-        ps.trials = w.trials;
-        ps.s0 = w.acc;
-        ps.jt0 = (w.acc == 0) ? w.trials : 0;
-        ps.f_start = w.fy;
-        ps.have_f = true;
-        return ps;
-    }
     const int k = st.k;
     if (!a.record_only && a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
         ps.last_restart_k != k) {
@@ -272,13 +249,12 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
     Vec y{a.x + b, a.B};
     Vec g{a.g + b, a.B};
 
-    PhaseStart ps = phase_start(a, b);
-    if (ps.skip) return;                        // uniform over the cluster
+    const PhaseStart ps = phase_start(a, b);
     long long ell = ps.ell;
-    int accepted = ps.accepted, trials = ps.trials;
-    double f_start = ps.f_start;
-    bool have_f = ps.have_f;
-    for (int s = ps.s0; s < (a.record_only ? 1 : a.n_red); ++s) {
+    int accepted = 0, trials = 0;
+    double f_start = 0.0;
+    bool have_f = false;
+    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
         // pass G: subgradient, ||g||^2 and f(y)
         double gg = 0.0, fy = 0.0;
         for (int p = tid; p < n; p += nthr) {
@@ -306,7 +282,7 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
         }
         bool ok = false;
         const int jmax = a.adaptive ? 1 : a.max_trials;
-        for (int j = (s == ps.s0 ? ps.jt0 : 0); j < jmax; ++j) {
+        for (int j = 0; j < jmax; ++j) {
             const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
             if (!a.adaptive) ell += 1;
             trials += 1;
@@ -434,7 +410,6 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     RhsState& st = a.st[b];
     if (st.stopped) return;
     const PhaseStart ps = phase_start(a, b);
-    if (ps.skip) return;                        // uniform over the cluster
     const int rank = (int)cluster.block_rank();
     const bool lin = (a.obj == SUPPY_OBJ_LINEAR);
     const bool elem = elementwise(a.obj);
@@ -468,10 +443,10 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     }
 
     long long ell = ps.ell;
-    int accepted = ps.accepted, trials = ps.trials;
-    double f_start = ps.f_start;
-    bool have_f = ps.have_f;
-    for (int s = ps.s0; s < (a.record_only ? 1 : a.n_red); ++s) {
+    int accepted = 0, trials = 0;
+    double f_start = 0.0;
+    bool have_f = false;
+    for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
         double gg = 0.0, fy = 0.0;
         KSum kg, kf;
         for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
@@ -516,7 +491,7 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
         }
         bool ok = false;
         const int jmax = a.adaptive ? 1 : a.max_trials;
-        for (int jt = (s == ps.s0 ? ps.jt0 : 0); jt < jmax; ++jt) {
+        for (int jt = 0; jt < jmax; ++jt) {
             const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
             if (!a.adaptive) ell += 1;
             trials += 1;
@@ -556,48 +531,19 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
     cluster.sync();
 }
 
-// ------------------------------------------------ whole-GPU first step ----
-// The first reduction step of a phase on the whole GPU, in three launches:
-//  k_wide_grad    g = subgradient at y, ||g||^2 and f(y) (restart rule and
-//                 f(x^k) recorded by the last CTA);
-//  k_wide_trials  f(y - beta_j g/||g||) for kWideTrials consecutive trial
-//                 exponents at once; the last CTA takes the first j with
-//                 f(z_j) <= f(y), exactly the trial the sequential loop of
-//                 Algorithm 1 would accept, and advances l by j + 1;
-//  k_wide_update  y <- z_j.
-// Element e of the n x B array is pixel e / B of right-hand side e % B; every
-// thread keeps one right-hand side (the grid stride is a multiple of B).
-// CTA partials are summed by the last CTA to finish in a fixed order, so the
-// decisions are deterministic.  What this step leaves undone (more reduction
-// steps, or more trials) the cluster kernel finishes in resume mode.
-
-__device__ __forceinline__ void wide_bookkeeping(RhsState& st, int acc, int trials) {
-    st.accepted_last = acc;
-    st.trials_last = trials;
-    st.accepted_total += acc;
-    st.trials_total += trials;
-}
-
-// TV term of pixel p of z = y - s g (the trial point of every term computed
-// as in the cluster kernels); y, g point at right-hand side b's element 0.
-__device__ __forceinline__ float wide_tv_term(int obj, int i, int j, int H, int W, const float* y,
-                                              const float* g, int B, float s) {
-    const size_t p = (size_t)i * W + j;
-    const float z0 = trial(__ldg(y + p * B), __ldg(g + p * B), s);
-    if (obj == SUPPY_OBJ_TV_ISO) {
-        if (i < H - 1 && j < W - 1) {
-            const size_t pd = p + W, pr = p + 1;
-            const float dx = trial(__ldg(y + pd * B), __ldg(g + pd * B), s) - z0;
-            const float dy = trial(__ldg(y + pr * B), __ldg(g + pr * B), s) - z0;
-            return sqrtf(dx * dx + dy * dy);
-        }
-        return 0.f;
-    }
-    float t = 0.f;
-    if (i < H - 1) t += fabsf(trial(__ldg(y + (p + W) * B), __ldg(g + (p + W) * B), s) - z0);
-    if (j < W - 1) t += fabsf(trial(__ldg(y + (p + 1) * B), __ldg(g + (p + 1) * B), s) - z0);
-    return t;
-}
+// ------------------------------------------------ whole-GPU phase ----
+// The perturbation phase of Algorithm 1 on the whole GPU, one right-hand side
+// after the other, in a single cooperative launch (every CTA resident).  Each
+// pass over the image -- the subgradient with ||g||^2 and f(y); f at up to
+// kWideTrials consecutive trial points y - beta_j g/||g|| at once; the update
+// y <- z_j -- takes a grid-stride share of the pixels per thread and ends in
+// a grid barrier, inside which the last CTA to arrive sums the CTA partials
+// in a fixed order; every CTA reads the same sums and takes the same
+// decisions (the first j with f(z_j) <= f(y): exactly the trial the
+// sequential loop accepts) without a further barrier.  y and g are read with plain coherent
+// loads (other CTAs rewrite them between passes; the barrier's fences make
+// those writes visible), never through the read-only path.  Element e of the
+// n x B array is pixel e / B of right-hand side e % B.
 
 // Float-float value hi + lo (about 44 significant bits): CTA-level sums of the
 // per-thread compensated FP32 sums stay in FP32 arithmetic, and FP64 is used
@@ -669,8 +615,8 @@ __device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double*
     }
 }
 
-// In the last CTA: the grid sums of the NV * B values, one warp per value,
-// into res[b * NV + v] (shared memory).
+// The grid sums of the NV * B values, one warp per value, into res[b * NV + v]
+// (shared memory).
 template <int NV>
 __device__ __forceinline__ void grid_sums(const double* part, int B, double* res) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -681,204 +627,270 @@ __device__ __forceinline__ void grid_sums(const double* part, int B, double* res
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kWideThreads) k_wide_grad(const PerturbArgs a) {
-    __shared__ FF sw[(kWideThreads / 32) * 2 * 32];
-    __shared__ double res[2 * kMaxRhs];
-    __shared__ long long ell_s[kMaxRhs];
-    __shared__ float inv_s[kMaxRhs];
-    const int B = a.B, H = a.H, W = a.W, obj = a.obj;
-    const long long nB = (long long)a.n * B;
-    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
-    const long long stride = (long long)gridDim.x * kWideThreads;
-    const int b = (int)(tid & (B - 1));
-    const bool act = !a.st[b].stopped;
-    const bool lin = (obj == SUPPY_OBJ_LINEAR);
-    KSum kg, kf;
-    double fl = 0.0;
-    if (act) {
-        const float* yb = a.x + b;
-        for (long long e = tid; e < nB; e += stride) {
-            const int p = (int)(e / B);
-            float gp;
-            if (lin) {
-                gp = a.c32[p];
-                fl += a.c64[p] * (double)a.x[e];
-            } else if (elementwise(obj)) {
-                const float y0 = a.x[e];
-                kf.add(norm_term(obj, y0));
-                gp = norm_grad(obj, y0);
-            } else {
-                const int i = p / W, j = p - i * W;
-                GlobalImage yi{yb, B, W};
-                kf.add(tv_term(obj, i, j, H, W, yi));
-                gp = tv_subgrad(obj, i, j, H, W, yi);
-            }
-            a.g[e] = gp;
-            kg.add(gp * gp);
-        }
-    }
-    FF v[2] = {ff_of(kg), lin ? ff_of(fl) : ff_of(kf)};
-    cta_partials<2>(v, B, sw, a.part);
-    if (!last_cta(a.ticket)) return;
-    grid_sums<2>(a.part, B, res);
-    if (threadIdx.x < B) {
-        const int r = threadIdx.x;
-        const double G2 = res[2 * r], F = res[2 * r + 1];
-        RhsState& st = a.st[r];
-        WideState& w = a.ws[r];
-        ell_s[r] = -1;
-        if (st.stopped) {
-            w.done = 1;
-        } else {
-            // restart rule at the phase start (Sec. 2.1.2)
-            const int k = st.k;
-            long long ell = st.ell;
-            if (a.restart_every > 0 && k > 0 && k % a.restart_every == 0 &&
-                st.last_restart_k != k) {
-                st.restarts += 1;
-                ell = st.restarts;
-                st.ell = ell;
-                st.last_restart_k = k;
-            }
-            st.f_cur = F;
-            st.f_valid = 1;
-            w.fy = F;
-            w.acc = 0;
-            w.trials = 0;
-            w.pending = 0;
-            w.done = 0;
-            double f_ref = 0.0;
-            if (a.adaptive) {
-                f_ref = adaptive_ref(a, st, F);
-                if (a.adaptive == 1) {
-                    st.f_ref = f_ref;
-                    st.has_ref = 1;
-                }
-            }
-            if (G2 == 0.0 || a.n_red <= 0 || (a.adaptive && !(F > f_ref))) {
-                w.done = 1;
-                wide_bookkeeping(st, 0, 0);
-            } else if (a.adaptive) {
-                // one trial: the adaptive step (every slot holds it)
-                const float sc = adaptive_scale(F, f_ref, G2);
-                for (int jj = 0; jj < kWideTrials; ++jj) w.step[jj] = sc;
-            } else {
-                ell_s[r] = ell;
-                inv_s[r] = 1.0f / sqrtf((float)G2);
-            }
-        }
-    }
-    __syncthreads();
-    // the trial step sizes of the next launch, one thread each
-    if (threadIdx.x < B * kWideTrials) {
-        const int r = threadIdx.x / kWideTrials, jj = threadIdx.x - r * kWideTrials;
-        if (ell_s[r] >= 0)
-            a.ws[r].step[jj] = trial_scale(a.gamma, a.log2_alpha, ell_s[r] + jj, inv_s[r]);
-    }
-    if (threadIdx.x == 0) *a.ticket = 0u;
-}
+// Grid barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is the
+// generation.  A CTA reads the generation before it arrives; the last to
+// arrive first sums the NV CTA partials of the pass (one warp per value, a
+// fixed order: the same FP64 sums whichever CTA arrives last) into gsum, then
+// resets the count and advances the generation; the others wait, then read
+// gsum into res (shared memory).  One CTA does the FP64 reduction: FP64 is
+// scarce on GB300, and every CTA summing the partials itself took longer than
+// the wait.  The wait is bounded (about two seconds of SM clock): on timeout
+// the CTA records error word 2 and every CTA leaves at its next barrier.
+// The partials need no second buffer: they are read before the release, and
+// written again only after it.
+constexpr long long kGridWaitCycles = 4000000000LL;
 
-__global__ void __launch_bounds__(kWideThreads) k_wide_trials(const PerturbArgs a) {
-    __shared__ FF sw[(kWideThreads / 32) * kWideTrials * 32];
-    __shared__ double res[kWideTrials * kMaxRhs];
-    const int B = a.B, H = a.H, W = a.W, obj = a.obj;
-    const long long nB = (long long)a.n * B;
-    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
-    const long long stride = (long long)gridDim.x * kWideThreads;
-    const int b = (int)(tid & (B - 1));
-    const bool act = !a.st[b].stopped && !a.ws[b].done;
-    const bool lin = (obj == SUPPY_OBJ_LINEAR);
-    float sj[kWideTrials];
-    KSum kz[kWideTrials];
-    double fl[kWideTrials];
-#pragma unroll
-    for (int jj = 0; jj < kWideTrials; ++jj) {
-        sj[jj] = act ? a.ws[b].step[jj] : 0.f;
-        fl[jj] = 0.0;
-    }
-    if (act) {
-        const float* yb = a.x + b;
-        const float* gb = a.g + b;
-        for (long long e = tid; e < nB; e += stride) {
-            const int p = (int)(e / B);
-            if (lin) {
-                const float y0 = a.x[e], g0 = a.g[e];
-                const double c = a.c64[p];
-#pragma unroll
-                for (int jj = 0; jj < kWideTrials; ++jj) fl[jj] += c * (double)trial(y0, g0, sj[jj]);
-            } else if (elementwise(obj)) {
-                const float y0 = a.x[e], g0 = a.g[e];
-#pragma unroll
-                for (int jj = 0; jj < kWideTrials; ++jj)
-                    kz[jj].add(norm_term(obj, trial(y0, g0, sj[jj])));
-            } else {
-                const int i = p / W, j = p - i * W;
-#pragma unroll
-                for (int jj = 0; jj < kWideTrials; ++jj)
-                    kz[jj].add(wide_tv_term(obj, i, j, H, W, yb, gb, B, sj[jj]));
-            }
-        }
-    }
-    FF v[kWideTrials];
-#pragma unroll
-    for (int jj = 0; jj < kWideTrials; ++jj) v[jj] = lin ? ff_of(fl[jj]) : ff_of(kz[jj]);
-    cta_partials<kWideTrials>(v, B, sw, a.part);
-    if (!last_cta(a.ticket)) return;
-    grid_sums<kWideTrials>(a.part, B, res);
-    if (threadIdx.x < B) {
-        const int r = threadIdx.x;
-        RhsState& st = a.st[r];
-        WideState& w = a.ws[r];
-        if (!st.stopped && !w.done) {
-            const int tmax = a.adaptive ? 1 : a.max_trials;
-            const int jmax = min(kWideTrials, tmax);
-            int hit = -1;
-            for (int jj = 0; jj < jmax; ++jj)
-                if (res[r * kWideTrials + jj] <= w.fy) {
-                    hit = jj;
+template <int NV>
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const double* part,
+                                             double* gsum, double* res) {
+    __shared__ int st_s;   // bit 0: ok, bit 1: this CTA arrived last
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        int ok = 1, last = 0;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            last = 1;
+            __threadfence();
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (*(volatile int*)err || clock64() - t0 > kGridWaitCycles) {
+                    atomicExch(err, 2);
+                    ok = 0;
                     break;
                 }
-            if (hit >= 0) {
-                w.sc = w.step[hit];
-                w.pending = 1;
-                w.acc = 1;
-                w.trials = hit + 1;
-                if (!a.adaptive) st.ell += hit + 1;
-            } else {
-                w.trials = jmax;
-                if (!a.adaptive) st.ell += jmax;
-                if (jmax >= tmax) {
-                    // the step ran out of trials: the phase ends
-                    w.done = 1;
-                    wide_bookkeeping(st, 0, jmax);
-                }
+                __nanosleep(32);
             }
+            __threadfence();
         }
+        st_s = ok | (last << 1);
     }
-    if (threadIdx.x == 0) *a.ticket = 0u;
+    __syncthreads();
+    const int st = st_s;
+    if (st & 2) {
+        if (NV > 0) {
+            grid_sums<NV>(part, 1, res);
+            if (threadIdx.x < NV) gsum[threadIdx.x] = res[threadIdx.x];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        }
+    } else if (NV > 0) {
+        if (threadIdx.x < NV) res[threadIdx.x] = __ldcg(gsum + threadIdx.x);
+    }
+    __syncthreads();
+    return (st & 1) && *(volatile int*)err == 0;
 }
 
-__global__ void __launch_bounds__(kWideThreads) k_wide_update(const PerturbArgs a) {
-    const int B = a.B;
-    const long long nB = (long long)a.n * B;
-    const long long tid = (long long)blockIdx.x * kWideThreads + threadIdx.x;
-    const long long stride = (long long)gridDim.x * kWideThreads;
-    const int b = (int)(tid & (B - 1));
-    if (!a.st[b].stopped && a.ws[b].pending) {
-        const float sc = a.ws[b].sc;
-        for (long long e = tid; e < nB; e += stride) a.x[e] = trial(a.x[e], a.g[e], sc);
+// Image of one right-hand side read with plain (coherent, L1-cached) loads:
+// other CTAs rewrite it between passes, and the grid barrier's fences make
+// their writes visible to these loads, which the read-only path (ld.global.nc)
+// would not guarantee.
+struct CohImage {
+    const float* y;   // element 0 of the right-hand side
+    int B, W;
+    __device__ __forceinline__ float operator()(int i, int j) const {
+        return y[((size_t)i * W + j) * B];
     }
-    if (!last_cta(a.ticket)) return;
-    for (int r = threadIdx.x; r < B; r += kWideThreads) {
-        WideState& w = a.ws[r];
-        if (!w.pending) continue;
-        w.pending = 0;
-        if (w.acc >= a.n_red) {
-            w.done = 1;
-            wide_bookkeeping(a.st[r], w.acc, w.trials);
+};
+
+// The values a TV term of pixel (i, j) reads at every trial point z = y - s g:
+// y and g at (i, j), (i + 1, j) and (i, j + 1), loaded once per pixel.
+struct TvNbr {
+    float y0, g0, yd, gd, yr, gr;
+    bool down, right;
+};
+
+__device__ __forceinline__ TvNbr tv_nbr(int i, int j, int H, int W, const float* y, const float* g,
+                                        int B) {
+    const size_t p = (size_t)i * W + j;
+    TvNbr t;
+    t.down = i < H - 1;
+    t.right = j < W - 1;
+    t.y0 = y[p * B];
+    t.g0 = g[p * B];
+    t.yd = t.down ? y[(p + W) * B] : 0.f;
+    t.gd = t.down ? g[(p + W) * B] : 0.f;
+    t.yr = t.right ? y[(p + 1) * B] : 0.f;
+    t.gr = t.right ? g[(p + 1) * B] : 0.f;
+    return t;
+}
+
+// TV term at the trial point with step s (computed as in the cluster kernels).
+__device__ __forceinline__ float tv_trial_term(int obj, const TvNbr& t, float s) {
+    const float z0 = trial(t.y0, t.g0, s);
+    if (obj == SUPPY_OBJ_TV_ISO) {
+        if (t.down && t.right) {
+            const float dx = trial(t.yd, t.gd, s) - z0;
+            const float dy = trial(t.yr, t.gr, s) - z0;
+            return sqrtf(dx * dx + dy * dy);
         }
+        return 0.f;
     }
-    if (threadIdx.x == 0) *a.ticket = 0u;
+    float v = 0.f;
+    if (t.down) v += fabsf(trial(t.yd, t.gd, s) - z0);
+    if (t.right) v += fabsf(trial(t.yr, t.gr, s) - z0);
+    return v;
+}
+
+__global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a) {
+    __shared__ FF sw[(kWideThreads / 32) * kWideTrials * 32];
+    __shared__ double res[kWideTrials];
+    __shared__ float sj_s[kWideTrials];
+    __shared__ int dec_s[2];     // continue the step; the accepted trial (-1: none)
+    __shared__ float dec_f[2];   // 1/||g||; the adaptive step
+    const int B = a.B, n = a.n, H = a.H, W = a.W, obj = a.obj;
+    const int tid = blockIdx.x * kWideThreads + threadIdx.x;
+    const int stride = gridDim.x * kWideThreads;
+    const bool lin = (obj == SUPPY_OBJ_LINEAR);
+    double* const part = a.part;
+    double* const gsum = a.part + (size_t)gridDim.x * kWideTrials;
+    for (int b = 0; b < B; ++b) {
+        RhsState& st = a.st[b];
+        if (st.stopped) continue;   // read by every CTA before the phase's first barrier
+        const PhaseStart ps = phase_start(a, b);
+        const bool has_ref = st.has_ref;
+        const double st_ref = st.f_ref;
+        long long ell = ps.ell;
+        int accepted = 0, trials = 0;
+        double f_start = 0.0;
+        float* X = a.x + b;
+        float* G = a.g + b;
+        for (int s = 0; s < a.n_red; ++s) {
+            // pass G: subgradient, ||g||^2 and f(y)
+            KSum kg, kf;
+            double fl = 0.0;
+            for (int p = tid; p < n; p += stride) {
+                float gp;
+                if (lin) {
+                    gp = a.c32[p];
+                    fl += a.c64[p] * (double)X[(size_t)p * B];
+                } else if (elementwise(obj)) {
+                    const float y0 = X[(size_t)p * B];
+                    kf.add(norm_term(obj, y0));
+                    gp = norm_grad(obj, y0);
+                } else {
+                    const int i = p / W, j = p - i * W;
+                    const CohImage yi{X, B, W};
+                    kf.add(tv_term(obj, i, j, H, W, yi));
+                    gp = tv_subgrad(obj, i, j, H, W, yi);
+                }
+                G[(size_t)p * B] = gp;
+                kg.add(gp * gp);
+            }
+            {
+                FF v[2] = {ff_of(kg), lin ? ff_of(fl) : ff_of(kf)};
+                cta_partials<2>(v, 1, sw, part);
+            }
+            if (!grid_barrier<2>(a.ticket, a.err, part, gsum, res)) return;
+            // the step's scalar decisions by one thread (FP64 is scarce on
+            // GB300: not by every thread of the grid), shared through smem
+            const double fy = res[1];
+            if (threadIdx.x == 0) {
+                const double gg = res[0];
+                if (s == 0) f_start = fy;
+                int go = gg != 0.0;
+                float inv_gnorm = 0.f, asc = 0.f;
+                if (go) {
+                    inv_gnorm = 1.0f / sqrtf((float)gg);
+                    if (a.adaptive) {
+                        const double f_ref =
+                            a.adaptive == 2 ? a.f_ref : (has_ref ? fmin(st_ref, f_start) : f_start);
+                        if (!(fy > f_ref)) go = 0;
+                        else asc = adaptive_scale(fy, f_ref, gg);
+                    }
+                }
+                dec_s[0] = go;
+                dec_f[0] = inv_gnorm;
+                dec_f[1] = asc;
+            }
+            __syncthreads();
+            if (!dec_s[0]) break;
+            const float inv_gnorm = dec_f[0], asc = dec_f[1];
+            const int jmax = a.adaptive ? 1 : a.max_trials;
+            bool ok = false;
+            for (int jt = 0; jt < jmax && !ok;) {
+                const int cnt = min(kWideTrials, jmax - jt);
+                // the trial step sizes, one thread each
+                if (threadIdx.x < kWideTrials)
+                    sj_s[threadIdx.x] = a.adaptive
+                                            ? asc
+                                            : trial_scale(a.gamma, a.log2_alpha, ell + threadIdx.x,
+                                                          inv_gnorm);
+                __syncthreads();
+                float sj[kWideTrials];
+#pragma unroll
+                for (int q = 0; q < kWideTrials; ++q) sj[q] = sj_s[q];
+                // pass T: f at the cnt trial points (the slots past cnt are not read)
+                KSum kz[kWideTrials];
+                double fz[kWideTrials];
+#pragma unroll
+                for (int q = 0; q < kWideTrials; ++q) fz[q] = 0.0;
+                for (int p = tid; p < n; p += stride) {
+                    if (lin) {
+                        const float y0 = X[(size_t)p * B], g0 = G[(size_t)p * B];
+                        const double c = a.c64[p];
+#pragma unroll
+                        for (int q = 0; q < kWideTrials; ++q)
+                            if (q < cnt) fz[q] += c * (double)trial(y0, g0, sj[q]);
+                    } else if (elementwise(obj)) {
+                        const float y0 = X[(size_t)p * B], g0 = G[(size_t)p * B];
+#pragma unroll
+                        for (int q = 0; q < kWideTrials; ++q)
+                            if (q < cnt) kz[q].add(norm_term(obj, trial(y0, g0, sj[q])));
+                    } else {
+                        const int i = p / W, j = p - i * W;
+                        const TvNbr t = tv_nbr(i, j, H, W, X, G, B);
+#pragma unroll
+                        for (int q = 0; q < kWideTrials; ++q)
+                            if (q < cnt) kz[q].add(tv_trial_term(obj, t, sj[q]));
+                    }
+                }
+                {
+                    FF v[kWideTrials];
+#pragma unroll
+                    for (int q = 0; q < kWideTrials; ++q) v[q] = lin ? ff_of(fz[q]) : ff_of(kz[q]);
+                    cta_partials<kWideTrials>(v, 1, sw, part);
+                }
+                if (!grid_barrier<kWideTrials>(a.ticket, a.err, part, gsum, res)) return;
+                if (threadIdx.x == 0) {
+                    int h = -1;
+                    for (int q = 0; q < cnt; ++q)
+                        if (res[q] <= fy) {
+                            h = q;
+                            break;
+                        }
+                    dec_s[1] = h;
+                }
+                __syncthreads();
+                const int hit = dec_s[1];
+                const int used = hit >= 0 ? hit + 1 : cnt;
+                if (!a.adaptive) ell += used;
+                trials += used;
+                jt += used;
+                if (hit >= 0) {
+                    // pass U: y <- z_hit
+                    const float sc = sj_s[hit];
+                    for (int p = tid; p < n; p += stride) {
+                        const size_t o = (size_t)p * B;
+                        X[o] = trial(X[o], G[o], sc);
+                    }
+                    accepted += 1;
+                    ok = true;
+                }
+            }
+            if (!ok) break;
+            // the next reduction step reads the neighbours' new y
+            if (s + 1 < a.n_red && !grid_barrier<0>(a.ticket, a.err, part, gsum, res)) return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) phase_end(a, st, ps, ell, accepted, trials, f_start);
+    }
 }
 
 // ------------------------------------------------ variance stopping rule ----
@@ -1017,7 +1029,18 @@ cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-size_t wide_part_doubles(int grid, int B) { return (size_t)grid * B * kWideTrials; }
+// kWideTrials partials per CTA, then the kWideTrials grid sums
+size_t wide_part_doubles(int grid) { return ((size_t)grid + 1) * kWideTrials; }
+
+int wide_phase_blocks_per_sm() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wide_phase, kWideThreads, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
 
 cudaError_t launch_variance(float* x, float* xprev, long long n, int B, RhsState* st,
                             double* part, unsigned* ticket, double tol, int grid, cudaStream_t s) {
@@ -1025,16 +1048,19 @@ cudaError_t launch_variance(float* x, float* xprev, long long n, int B, RhsState
     return cudaGetLastError();
 }
 
-cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, int cluster, cudaStream_t s) {
-    if (a.B != 1 && (a.B & (a.B - 1))) return cudaErrorInvalidValue;
-    k_wide_grad<<<grid, kWideThreads, 0, s>>>(a);
-    k_wide_trials<<<grid, kWideThreads, 0, s>>>(a);
-    k_wide_update<<<grid, kWideThreads, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    PerturbArgs r = a;
-    r.resume = 1;
-    return launch_perturb(r, cluster, s);
+cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, cudaStream_t s) {
+    if (!a.ticket || !a.err || !a.part || grid < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kWideThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_wide_phase, a);
 }
 
 cudaError_t launch_objective(const ObjArgs& a, int grid, double* out, cudaStream_t s) {

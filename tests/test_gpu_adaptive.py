@@ -1,7 +1,7 @@
 """GPU parity of the adaptive perturbation step (Nikazad et al., Sec. 2.1.2)
 against the FP64 oracle, on every perturbation path: the cluster kernel with
-the image in shared memory or in global memory, and the whole-GPU first step
-with the cluster kernel resuming."""
+the image in shared memory or in global memory, and the whole-GPU phase
+kernel (one cooperative launch)."""
 import numpy as np
 import pytest
 

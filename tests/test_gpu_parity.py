@@ -515,12 +515,13 @@ def test_interleaved_row_order_matches_oracle(mode, strategy, tma):
         assert rel(ctx.suppy_proximity()[0], O.proximity(S, l, u, xo)) <= 1e-3
 
 
-# ------------------------------------------- whole-GPU perturbation step ----
+# ------------------------------------------ whole-GPU perturbation phase ----
 
 PERT_CASES = [
     # (gamma, alpha, n_red, max_trials): first trial accepted; later trials only
-    # (the first eight rejected, the cluster kernel resumes); several reduction
-    # steps; fewer trials than one whole-GPU launch evaluates
+    # (the first eight rejected: further trial passes); several reduction
+    # steps (grid barrier before each next subgradient); fewer trials than one
+    # pass evaluates
     (0.05, 0.99, 1, 100),
     (40.0, 0.7, 1, 100),
     (2.0, 0.9, 3, 50),
@@ -531,9 +532,11 @@ PERT_CASES = [
 @pytest.mark.parametrize("case", PERT_CASES)
 @pytest.mark.parametrize("kind", ["tv", "atv"])
 def test_whole_gpu_perturbation_matches_oracle_and_cluster_path(kind, case):
-    """The whole-GPU first step (eight trials per pass, first acceptance kept)
-    followed by the cluster kernel's resume gives the oracle's phase: the same
-    accepted steps, trial count and exponent, and the same point."""
+    """The whole-GPU phase (one cooperative launch; eight trials per pass,
+    first acceptance kept; grid barriers between passes) gives the oracle's
+    phase and the cluster kernel's: the same accepted steps, trial count and
+    exponent, and the same point -- also when a step needs more than one
+    pass of trials (max_trials 100) or the trials run out (max_trials 3)."""
     gamma, alpha, n_red, max_trials = case
     prob = synth.ct_problem(128, 60, 181)
     obj = {"tv": pk.SUPPY_OBJ_TV_ISO, "atv": pk.SUPPY_OBJ_TV_ANISO}[kind]
@@ -557,8 +560,9 @@ def test_whole_gpu_perturbation_matches_oracle_and_cluster_path(kind, case):
 
 
 def test_whole_gpu_perturbation_batched_and_linear():
-    """Several right-hand sides in one whole-GPU launch (each its own
-    exponent and decisions), and the linear mean-dose objective."""
+    """Several right-hand sides in one whole-GPU launch (their phases one
+    after the other, each its own exponent and decisions; the padding
+    right-hand sides skipped), and the linear mean-dose objective."""
     prob = synth.ct_problem(96, 40, 137, nrhs=5)
     x0 = random_x(prob.A.n, 5, seed=52)
     P = dict(gamma=3.0, alpha=0.8, n_red=2, max_trials=40)
