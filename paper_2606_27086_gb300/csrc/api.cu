@@ -135,6 +135,7 @@ struct suppy_ctx {
     int* d_tpart = nullptr;
     int* d_ctpart = nullptr;
     int* d_err = nullptr;           // set by a kernel whose bounded wait gave up
+    unsigned* d_cticket = nullptr;  // streamed column pass: CTAs finished (fused epilogue)
     int grid_fin = 0;
     int grid_obj = 0;
     int perturb_cluster = 1;
@@ -641,6 +642,10 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.delta_out = ext ? c->d_delta : nullptr;
                 ca.box_len = c->box_len;
                 ca.epi = e2;
+                // without an extrapolated step the column pass's last CTA runs
+                // the sweep epilogue (one launch fewer per sweep)
+                const bool fuse_epi = !ext && e2.last_seg && c->d_cticket;
+                ca.ticket = fuse_epi ? c->d_cticket : nullptr;
                 {
                     Timed tm{c, 1};
                     CK(tm.begin());
@@ -649,7 +654,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                     note_launch(c);
                 }
                 if (ext && (s = enqueue_ext_step(c, p, t, e2.npp)) != SUPPY_OK) return s;
-                if (e2.last_seg) {
+                if (e2.last_seg && !fuse_epi) {
                     CK(launch_epilogue(e2, c->stream));
                     note_launch(c);
                 }
@@ -1556,16 +1561,16 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         // them one after the other, so the cluster path is faster; 2 forces
         // it, 1 disables it
         // (its pixel loops step an int index by the grid's thread count)
-        const bool wide_fits = (long long)c->n + 4LL * sms * kWideThreads < (long long)INT_MAX;
+        const bool wide_fits = (long long)c->n + 2LL * sms * kPhaseThreads < (long long)INT_MAX;
         if (wide_fits && (o->perturb_path == 2 ||
                           (o->perturb_path == 0 && (long long)nB >= 65536 && c->B == 1))) {
             // a cooperative launch: every CTA must be resident at once
-            const int per_sm = std::min(2, wide_phase_blocks_per_sm());
+            const int per_sm = std::min(1, wide_phase_blocks_per_sm());
             if (per_sm < 1) return fail(c, SUPPY_ECUDA, "whole-GPU perturbation kernel cannot be resident");
             c->wide = true;
             c->wide_grid = (int)std::max<long long>(
                 1, std::min<long long>((long long)per_sm * sms,
-                                       ((long long)c->n + kWideThreads - 1) / kWideThreads));
+                                       ((long long)c->n + kPhaseThreads - 1) / kPhaseThreads));
             if ((s = dalloc(c, &c->d_wpart, wide_part_doubles(c->wide_grid))) != SUPPY_OK) return s;
             if ((s = dalloc(c, &c->d_ticket, 2)) != SUPPY_OK) return s;
             CK(cudaMemsetAsync(c->d_ticket, 0, 2 * sizeof(unsigned), c->stream));
@@ -1634,6 +1639,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     c->max_row = max_len;
     if ((s = dalloc(c, &c->d_err, 1)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if ((s = dalloc(c, &c->d_cticket, 1)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_cticket, 0, sizeof(unsigned), c->stream));
     const bool smem_ok = (c->B == 1) && (size_t)n * sizeof(float) <= 64 * 1024;
     // EL / EMR take the two-pass sweep (the column pass accumulates A^T(.));
     // their buffers exist before any timed candidate sweep

@@ -141,9 +141,11 @@ struct PerturbArgs {
     int* err;               // whole-GPU kernel: error word (2: a barrier timed out)
 };
 
-// Threads per CTA of the whole-GPU perturbation kernel and the trial points
-// one of its passes evaluates.
+// Threads per CTA of the whole-GPU reduction kernels (variance rule), of the
+// whole-GPU perturbation kernel (one CTA per SM), and the trial points one of
+// its passes evaluates.
 constexpr int kWideThreads = 256;
+constexpr int kPhaseThreads = 512;
 constexpr int kWideTrials = 8;
 
 struct ObjArgs {
@@ -188,6 +190,8 @@ struct StreamArgs {
     float* delta_out;       // EL / EMR: the column sums go here, x untouched
     int box_len;
     EpiArgs epi;
+    unsigned* ticket;       // column pass of the last block: CTAs finished (the
+                            // last one runs the sweep epilogue), or null
 };
 
 // Extrapolated step of EL / EMR (sweep.cu): t_b from the sweep's reductions,
@@ -238,10 +242,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                              double* out, cudaStream_t s);
 cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s);
-// Whole-GPU first reduction step of a perturbation phase (subgradient pass,
-// kWideTrials trial evaluations in one pass, update) followed by the cluster
-// kernel in resume mode; `grid` CTAs of kWideThreads threads.
-// the whole phase on the whole GPU, one cooperative launch (grid CTAs, all resident)
+// The whole perturbation phase on the whole GPU: one cooperative launch of
+// `grid` CTAs of kPhaseThreads threads, all resident (subgradient pass,
+// kWideTrials trial evaluations per pass, update, grid barriers between).
 cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, cudaStream_t s);
 size_t wide_part_doubles(int grid);   // partials the whole-GPU kernel needs
 int wide_phase_blocks_per_sm();       // its resident CTAs per SM
@@ -381,6 +384,55 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) {
     return fminf(fmaxf(v, lo), hi);
+}
+
+// Sweep epilogue, run by one CTA (warp w handles right-hand sides w, w + W,
+// ... for W warps): the proximity partials of the pass summed in a fixed
+// order, the monitored proximity and objective recorded, and the stopping
+// rule of Sec. 2.2.1 / 2.2.3 applied.  The CTA that runs it must be the last
+// reader of the stop flags in its launch.
+__device__ __forceinline__ void sweep_epilogue(const EpiArgs& a) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = wid; b < a.B; b += blockDim.x / 32) {
+        double s = 0.0;
+        for (int c = lane; c < a.npp; c += 32) s += a.pp[(size_t)c * a.B + b];
+        s = warp_sum(s);
+        if (lane != 0) continue;
+        RhsState& st = a.st[b];
+        if (st.stopped) continue;
+        if (a.first_seg) st.p_acc = 0.0;
+        st.p_acc += a.scale * s;
+        if (!a.last_seg) continue;
+        const double p = a.p_target ? a.p_target[b] : st.p_acc;
+        const int k = st.k;
+        if (k < a.hist_cap) {
+            a.prox_hist[(size_t)b * a.hist_cap + k] = p;
+            a.obj_hist[(size_t)b * a.hist_cap + k] =
+                st.f_valid ? st.f_cur : __longlong_as_double(0x7ff8000000000000LL);
+        }
+        // stopping rule (Sec. 2.2.1 and 2.2.3)
+        if (st.has_prev_p && fabs(p - st.p_prev) / fmax(1.0, st.p_prev) < a.sp.prox_rel)
+            st.calm += 1;
+        else
+            st.calm = 0;
+        const bool feas = (p <= a.sp.prox_abs) || (st.calm >= a.sp.patience);
+        bool objok = true;
+        if (a.sp.has_obj && a.sp.obj_rel > 0.0 && st.f_valid) {
+            objok = st.has_prev_f &&
+                    fabs(st.f_cur - st.f_prev) / fmax(1.0, fabs(st.f_prev)) < a.sp.obj_rel;
+        }
+        st.p_prev = p;
+        st.has_prev_p = 1;
+        if (st.f_valid) {
+            st.f_prev = st.f_cur;
+            st.has_prev_f = 1;
+        }
+        st.f_valid = 0;
+        st.last_prox = p;
+        st.k = k + 1;
+        if ((a.sp.use_stopping && feas && objok) || (a.sp.max_sweeps > 0 && k + 1 >= a.sp.max_sweeps))
+            st.stopped = 1;
+    }
 }
 
 }  // namespace suppy

@@ -593,7 +593,7 @@ __device__ __forceinline__ double warp_sum_parts(const double* part, int ncta, i
 // Per-CTA sums of NV values per right-hand side, written as FP64 to
 // part[(cta * B + b) * NV + v]: float-float sums over the lanes of each
 // right-hand side, then over the warps in order.  sw holds 8 * NV * 32 values.
-template <int NV>
+template <int NV, int NT = kWideThreads>
 __device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double* part) {
 #pragma unroll
     for (int j = 0; j < NV; ++j)
@@ -607,20 +607,20 @@ __device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double*
 #pragma unroll
         for (int j = 0; j < NV; ++j) sw[(wid * NV + j) * 32 + lane] = v[j];
     __syncthreads();
-    for (int t = threadIdx.x; t < NV * B; t += kWideThreads) {
+    for (int t = threadIdx.x; t < NV * B; t += NT) {
         const int b = t / NV, j = t - b * NV;
         FF acc{0.f, 0.f};
-        for (int w = 0; w < kWideThreads / 32; ++w) acc = ff_add(acc, sw[(w * NV + j) * 32 + b]);
+        for (int w = 0; w < NT / 32; ++w) acc = ff_add(acc, sw[(w * NV + j) * 32 + b]);
         part[((size_t)blockIdx.x * B + b) * NV + j] = (double)acc.hi + (double)acc.lo;
     }
 }
 
 // The grid sums of the NV * B values, one warp per value, into res[b * NV + v]
 // (shared memory).
-template <int NV>
+template <int NV, int NT = kWideThreads>
 __device__ __forceinline__ void grid_sums(const double* part, int B, double* res) {
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int t = wid; t < NV * B; t += kWideThreads / 32) {
+    for (int t = wid; t < NV * B; t += NT / 32) {
         const double v = warp_sum_parts(part, gridDim.x, NV * B, t);
         if (lane == 0) res[t] = v;
     }
@@ -639,6 +639,7 @@ __device__ __forceinline__ void grid_sums(const double* part, int B, double* res
 // The partials need no second buffer: they are read before the release, and
 // written again only after it.
 constexpr long long kGridWaitCycles = 4000000000LL;
+constexpr int kFirstTrials = 2;
 
 template <int NV>
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const double* part,
@@ -671,7 +672,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const doub
     const int st = st_s;
     if (st & 2) {
         if (NV > 0) {
-            grid_sums<NV>(part, 1, res);
+            grid_sums<NV, kPhaseThreads>(part, 1, res);
             if (threadIdx.x < NV) gsum[threadIdx.x] = res[threadIdx.x];
             __syncthreads();
         }
@@ -739,16 +740,37 @@ __device__ __forceinline__ float tv_trial_term(int obj, const TvNbr& t, float s)
     return v;
 }
 
-__global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a) {
-    __shared__ FF sw[(kWideThreads / 32) * kWideTrials * 32];
+// Row and column of pixel p of a grid-stride loop, advanced without a
+// division per pixel: p grows by stride = si W + sj.
+struct PixelWalk {
+    int i, j, si, sj, W;
+    __device__ PixelWalk(int p0, int stride, int w) : W(w) {
+        i = p0 / w;
+        j = p0 - i * w;
+        si = stride / w;
+        sj = stride - si * w;
+    }
+    __device__ __forceinline__ void next() {
+        i += si;
+        j += sj;
+        if (j >= W) {
+            j -= W;
+            ++i;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbArgs a) {
+    __shared__ FF sw[(kPhaseThreads / 32) * kWideTrials * 32];
     __shared__ double res[kWideTrials];
     __shared__ float sj_s[kWideTrials];
     __shared__ int dec_s[2];     // continue the step; the accepted trial (-1: none)
     __shared__ float dec_f[2];   // 1/||g||; the adaptive step
     const int B = a.B, n = a.n, H = a.H, W = a.W, obj = a.obj;
-    const int tid = blockIdx.x * kWideThreads + threadIdx.x;
-    const int stride = gridDim.x * kWideThreads;
+    const int tid = blockIdx.x * kPhaseThreads + threadIdx.x;
+    const int stride = gridDim.x * kPhaseThreads;
     const bool lin = (obj == SUPPY_OBJ_LINEAR);
+    const bool tv = !elementwise(obj);
     double* const part = a.part;
     double* const gsum = a.part + (size_t)gridDim.x * kWideTrials;
     for (int b = 0; b < B; ++b) {
@@ -766,27 +788,27 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a
             // pass G: subgradient, ||g||^2 and f(y)
             KSum kg, kf;
             double fl = 0.0;
-            for (int p = tid; p < n; p += stride) {
+            PixelWalk px(tid, stride, tv ? W : 1);
+            for (int p = tid; p < n; p += stride, px.next()) {
                 float gp;
                 if (lin) {
                     gp = a.c32[p];
                     fl += a.c64[p] * (double)X[(size_t)p * B];
-                } else if (elementwise(obj)) {
+                } else if (!tv) {
                     const float y0 = X[(size_t)p * B];
                     kf.add(norm_term(obj, y0));
                     gp = norm_grad(obj, y0);
                 } else {
-                    const int i = p / W, j = p - i * W;
                     const CohImage yi{X, B, W};
-                    kf.add(tv_term(obj, i, j, H, W, yi));
-                    gp = tv_subgrad(obj, i, j, H, W, yi);
+                    kf.add(tv_term(obj, px.i, px.j, H, W, yi));
+                    gp = tv_subgrad(obj, px.i, px.j, H, W, yi);
                 }
                 G[(size_t)p * B] = gp;
                 kg.add(gp * gp);
             }
             {
                 FF v[2] = {ff_of(kg), lin ? ff_of(fl) : ff_of(kf)};
-                cta_partials<2>(v, 1, sw, part);
+                cta_partials<2, kPhaseThreads>(v, 1, sw, part);
             }
             if (!grid_barrier<2>(a.ticket, a.err, part, gsum, res)) return;
             // the step's scalar decisions by one thread (FP64 is scarce on
@@ -816,7 +838,10 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a
             const int jmax = a.adaptive ? 1 : a.max_trials;
             bool ok = false;
             for (int jt = 0; jt < jmax && !ok;) {
-                const int cnt = min(kWideTrials, jmax - jt);
+                // the first pass of a step tries kFirstTrials points (usually
+                // the first is accepted once the exponent has settled), later
+                // passes kWideTrials; the accepted trial is the same either way
+                const int cnt = min(jt == 0 ? kFirstTrials : kWideTrials, jmax - jt);
                 // the trial step sizes, one thread each
                 if (threadIdx.x < kWideTrials)
                     sj_s[threadIdx.x] = a.adaptive
@@ -832,21 +857,21 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a
                 double fz[kWideTrials];
 #pragma unroll
                 for (int q = 0; q < kWideTrials; ++q) fz[q] = 0.0;
-                for (int p = tid; p < n; p += stride) {
+                PixelWalk px(tid, stride, tv ? W : 1);
+                for (int p = tid; p < n; p += stride, px.next()) {
                     if (lin) {
                         const float y0 = X[(size_t)p * B], g0 = G[(size_t)p * B];
                         const double c = a.c64[p];
 #pragma unroll
                         for (int q = 0; q < kWideTrials; ++q)
                             if (q < cnt) fz[q] += c * (double)trial(y0, g0, sj[q]);
-                    } else if (elementwise(obj)) {
+                    } else if (!tv) {
                         const float y0 = X[(size_t)p * B], g0 = G[(size_t)p * B];
 #pragma unroll
                         for (int q = 0; q < kWideTrials; ++q)
                             if (q < cnt) kz[q].add(norm_term(obj, trial(y0, g0, sj[q])));
                     } else {
-                        const int i = p / W, j = p - i * W;
-                        const TvNbr t = tv_nbr(i, j, H, W, X, G, B);
+                        const TvNbr t = tv_nbr(px.i, px.j, H, W, X, G, B);
 #pragma unroll
                         for (int q = 0; q < kWideTrials; ++q)
                             if (q < cnt) kz[q].add(tv_trial_term(obj, t, sj[q]));
@@ -856,7 +881,7 @@ __global__ void __launch_bounds__(kWideThreads) k_wide_phase(const PerturbArgs a
                     FF v[kWideTrials];
 #pragma unroll
                     for (int q = 0; q < kWideTrials; ++q) v[q] = lin ? ff_of(fz[q]) : ff_of(kz[q]);
-                    cta_partials<kWideTrials>(v, 1, sw, part);
+                    cta_partials<kWideTrials, kPhaseThreads>(v, 1, sw, part);
                 }
                 if (!grid_barrier<kWideTrials>(a.ticket, a.err, part, gsum, res)) return;
                 if (threadIdx.x == 0) {
@@ -1034,7 +1059,7 @@ size_t wide_part_doubles(int grid) { return ((size_t)grid + 1) * kWideTrials; }
 
 int wide_phase_blocks_per_sm() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wide_phase, kWideThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_wide_phase, kPhaseThreads, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -1052,7 +1077,7 @@ cudaError_t launch_perturb_wide(const PerturbArgs& a, int grid, cudaStream_t s) 
     if (!a.ticket || !a.err || !a.part || grid < 1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(kWideThreads, 1, 1);
+    cfg.blockDim = dim3(kPhaseThreads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

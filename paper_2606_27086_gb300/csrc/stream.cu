@@ -602,10 +602,22 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_cols_tma(const StreamArgs
     ColWork<VT, G, MAP> work{a};
     stream_items<VT, G>(a, work);
     __syncthreads();
-    if (blockIdx.x == 0 && !a.epi.last_seg) {
+    if (a.epi.last_seg && a.ticket) {
+        // the last CTA to finish runs the sweep epilogue: every CTA of the
+        // launch has read the stop flag by then, so the flag it may set is
+        // seen by the next launch only
+        __shared__ bool last;
+        __threadfence();
+        if (threadIdx.x == 0) last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            sweep_epilogue(a.epi);
+            if (threadIdx.x == 0) *a.ticket = 0u;
+        }
+    } else if (blockIdx.x == 0 && !a.epi.last_seg) {
         // CTA 0 also accumulates the row pass's proximity partials of this
-        // block (never for the last block: the stop flag is set by a
-        // separate launch)
+        // block (the last block's are summed by its epilogue)
         const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int b = wid; b < a.epi.B; b += kStreamThreads / 32) {
             double s = 0.0;

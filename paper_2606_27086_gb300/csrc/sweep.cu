@@ -107,51 +107,6 @@ __device__ __forceinline__ void cta_partial(double prox, double* out) {
     }
 }
 
-// Epilogue: CTA 0, warp w handles right-hand sides w, w+8, ...
-__device__ void sweep_epilogue(const EpiArgs& a) {
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = wid; b < a.B; b += blockDim.x / 32) {
-        double s = 0.0;
-        for (int c = lane; c < a.npp; c += 32) s += a.pp[(size_t)c * a.B + b];
-        s = warp_sum(s);
-        if (lane != 0) continue;
-        RhsState& st = a.st[b];
-        if (st.stopped) continue;
-        if (a.first_seg) st.p_acc = 0.0;
-        st.p_acc += a.scale * s;
-        if (!a.last_seg) continue;
-        const double p = a.p_target ? a.p_target[b] : st.p_acc;
-        const int k = st.k;
-        if (k < a.hist_cap) {
-            a.prox_hist[(size_t)b * a.hist_cap + k] = p;
-            a.obj_hist[(size_t)b * a.hist_cap + k] =
-                st.f_valid ? st.f_cur : __longlong_as_double(0x7ff8000000000000LL);
-        }
-        // stopping rule (Sec. 2.2.1 and 2.2.3)
-        if (st.has_prev_p && fabs(p - st.p_prev) / fmax(1.0, st.p_prev) < a.sp.prox_rel)
-            st.calm += 1;
-        else
-            st.calm = 0;
-        const bool feas = (p <= a.sp.prox_abs) || (st.calm >= a.sp.patience);
-        bool objok = true;
-        if (a.sp.has_obj && a.sp.obj_rel > 0.0 && st.f_valid) {
-            objok = st.has_prev_f &&
-                    fabs(st.f_cur - st.f_prev) / fmax(1.0, fabs(st.f_prev)) < a.sp.obj_rel;
-        }
-        st.p_prev = p;
-        st.has_prev_p = 1;
-        if (st.f_valid) {
-            st.f_prev = st.f_cur;
-            st.has_prev_f = 1;
-        }
-        st.f_valid = 0;
-        st.last_prox = p;
-        st.k = k + 1;
-        if ((a.sp.use_stopping && feas && objok) || (a.sp.max_sweeps > 0 && k + 1 >= a.sp.max_sweeps))
-            st.stopped = 1;
-    }
-}
-
 // ------------------------------------------------------ row pass, B = 1 ----
 // Lane `lane` of a G-lane group owns elements lane, lane+G, lane+2G, ... of
 // the row.  Loads are issued in batches (all values and indices of a batch
