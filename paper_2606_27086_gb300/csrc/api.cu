@@ -24,11 +24,14 @@ thread_local std::string g_err;
 constexpr int kMaxTile = 4096;
 
 // Lane maps of the streaming row and column passes when neither the caller
-// nor the tuner chose one (0 quads per lane, 1 lane-interleaved).  On the
-// CT 512x512 matrix the row pass ran faster with quads (217 against 249 us)
-// and the column pass with interleaved lanes (202 against 213 us).
+// nor the tuner chose one (0 quads per lane, 1 lane-interleaved).  Which map
+// is faster depends on the matrix and the ring shape: tuned on CT 512x512,
+// the column pass ran faster interleaved (202 against 213 us, 1024-element
+// tiles) and the row pass with quads (217 against 249 us); on CT 384x384 at
+// the default 4096-element tiles the interleaved column pass was slower
+// (126 against 112 us).  Untuned contexts keep quads; the tuner tries both.
 constexpr int kDefaultRowMap = 0;
-constexpr int kDefaultColMap = 1;
+constexpr int kDefaultColMap = 0;
 
 // Stored length of an item: rows and columns start at multiples of four
 // elements and are zero-padded to a multiple of four.

@@ -593,22 +593,27 @@ __device__ __forceinline__ double warp_sum_parts(const double* part, int ncta, i
 // Per-CTA sums of NV values per right-hand side, written as FP64 to
 // part[(cta * B + b) * NV + v]: float-float sums over the lanes of each
 // right-hand side, then over the warps in order.  sw holds 8 * NV * 32 values.
+// Only the first nv values (uniform over the CTA) are reduced and written.
 template <int NV, int NT = kWideThreads>
-__device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double* part) {
+__device__ __forceinline__ void cta_partials(FF (&v)[NV], int B, FF* sw, double* part,
+                                             int nv = NV) {
 #pragma unroll
     for (int j = 0; j < NV; ++j)
-        for (int o = 16; o >= B && o > 0; o >>= 1) {
-            const FF w{__shfl_xor_sync(0xffffffffu, v[j].hi, o),
-                       __shfl_xor_sync(0xffffffffu, v[j].lo, o)};
-            v[j] = ff_add(v[j], w);
-        }
+        if (j < nv)
+            for (int o = 16; o >= B && o > 0; o >>= 1) {
+                const FF w{__shfl_xor_sync(0xffffffffu, v[j].hi, o),
+                           __shfl_xor_sync(0xffffffffu, v[j].lo, o)};
+                v[j] = ff_add(v[j], w);
+            }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane < B)
 #pragma unroll
-        for (int j = 0; j < NV; ++j) sw[(wid * NV + j) * 32 + lane] = v[j];
+        for (int j = 0; j < NV; ++j)
+            if (j < nv) sw[(wid * NV + j) * 32 + lane] = v[j];
     __syncthreads();
     for (int t = threadIdx.x; t < NV * B; t += NT) {
         const int b = t / NV, j = t - b * NV;
+        if (j >= nv) continue;
         FF acc{0.f, 0.f};
         for (int w = 0; w < NT / 32; ++w) acc = ff_add(acc, sw[(w * NV + j) * 32 + b]);
         part[((size_t)blockIdx.x * B + b) * NV + j] = (double)acc.hi + (double)acc.lo;
@@ -881,7 +886,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
                     FF v[kWideTrials];
 #pragma unroll
                     for (int q = 0; q < kWideTrials; ++q) v[q] = lin ? ff_of(fz[q]) : ff_of(kz[q]);
-                    cta_partials<kWideTrials, kPhaseThreads>(v, 1, sw, part);
+                    cta_partials<kWideTrials, kPhaseThreads>(v, 1, sw, part, cnt);
                 }
                 if (!grid_barrier<kWideTrials>(a.ticket, a.err, part, gsum, res)) return;
                 if (threadIdx.x == 0) {
