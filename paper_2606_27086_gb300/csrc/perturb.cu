@@ -163,32 +163,105 @@ __device__ __forceinline__ float subgrad(int obj, int p, int H, int W, const flo
     return g;
 }
 
-// Deterministic cluster-wide sum of two FP64 values.
-__device__ double2 cluster_sum2(double a, double b, double2* sw, double2* scta,
+// Per-thread compensated FP32 sum (Kahan); widened to FP64 for the cluster
+// reduction.  FP64 arithmetic is scarce on GB300: one FP64 add per pixel and
+// pass would cost more than the stencil itself.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        const float y = v - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Float-float value hi + lo (about 44 significant bits): CTA-level sums of the
+// per-thread compensated FP32 sums stay in FP32 arithmetic, and FP64 is used
+// only for the grid-level sum of the CTA partials.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
+    const float hi = s + e;
+    return FF{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ FF ff_of(const KSum& k) { return FF{k.s, -k.c}; }
+
+// An FP64 value as float-float (used for the FP64 per-element sums of the
+// linear objective).
+__device__ __forceinline__ FF ff_of(double v) {
+    const float hi = (float)v;
+    return FF{hi, (float)(v - (double)hi)};
+}
+
+// Deterministic cluster-wide sum of two values: float-float over the lanes
+// and then the warps of each CTA (FP32 arithmetic), then one thread per CTA
+// sums the cluster's CTA values in FP64 in rank order.  Every thread gets the
+// same result, read from shared memory.  FP64 stays with one thread per CTA:
+// it is scarce on GB300.
+__device__ double2 cluster_sum2(FF a, FF b, FF* swf, double2* scta, double2* sres,
                                 cg::cluster_group& cluster) {
-    a = warp_sum(a);
-    b = warp_sum(b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = ff_add(a, FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)});
+        b = ff_add(b, FF{__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o)});
+    }
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sw[wid] = make_double2(a, b);
+    if (lane == 0) {
+        swf[2 * wid] = a;
+        swf[2 * wid + 1] = b;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double2 s = make_double2(0.0, 0.0);
+        FF sa{0.f, 0.f}, sb{0.f, 0.f};
         for (int w = 0; w < kPerturbThreads / 32; ++w) {
-            s.x += sw[w].x;
-            s.y += sw[w].y;
+            sa = ff_add(sa, swf[2 * w]);
+            sb = ff_add(sb, swf[2 * w + 1]);
         }
-        *scta = s;
+        *scta = make_double2((double)sa.hi + (double)sa.lo, (double)sb.hi + (double)sb.lo);
     }
     cluster.sync();
-    double2 t = make_double2(0.0, 0.0);
-    const unsigned nr = cluster.num_blocks();
-    for (unsigned r = 0; r < nr; ++r) {
-        const double2 v = *cluster.map_shared_rank(scta, r);
-        t.x += v.x;
-        t.y += v.y;
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0);
+        const unsigned nr = cluster.num_blocks();
+        for (unsigned r = 0; r < nr; ++r) {
+            const double2 v = *cluster.map_shared_rank(scta, r);
+            t.x += v.x;
+            t.y += v.y;
+        }
+        *sres = t;
     }
-    cluster.sync();   // nobody overwrites scta before every CTA has read it
-    return t;
+    cluster.sync();   // every CTA has read scta; sres is visible to the CTA
+    return *sres;
+}
+
+// Scalar decisions of a reduction step, taken by one thread after the
+// subgradient pass and shared through shared memory: whether the step goes
+// on, 1/||g|| and the adaptive step.
+struct StepDecision {
+    int go;
+    float inv_gnorm, asc;
+};
+
+__device__ __forceinline__ StepDecision step_decision(const PerturbArgs& a, const RhsState& st,
+                                                      double gg, double fy, double f_start) {
+    StepDecision d{0, 0.f, 0.f};
+    if (a.record_only || gg == 0.0) return d;
+    d.inv_gnorm = 1.0f / sqrtf((float)gg);
+    if (a.adaptive) {
+        const double f_ref = adaptive_ref(a, st, f_start);
+        if (!(fy > f_ref)) return d;
+        d.asc = adaptive_scale(fy, f_ref, gg);
+    }
+    d.go = 1;
+    return d;
 }
 
 // Where a perturbation phase starts: the restart rule (Sec. 2.1.2: l <- r at
@@ -236,8 +309,10 @@ __device__ __forceinline__ void phase_end(const PerturbArgs& a, RhsState& st, co
 
 __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a) {
     cg::cluster_group cluster = cg::this_cluster();
-    __shared__ double2 sw[kPerturbThreads / 32];
-    __shared__ double2 scta;
+    __shared__ FF swf[2 * (kPerturbThreads / 32)];
+    __shared__ double2 scta, sres;
+    __shared__ StepDecision dec;
+    __shared__ float sc_s;
     const int ncl = (int)cluster.num_blocks();
     const int b = blockIdx.x / ncl;             // right-hand side of this cluster
     RhsState& st = a.st[b];
@@ -246,52 +321,64 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb(const PerturbArgs a
     const int tid = rank * kPerturbThreads + threadIdx.x;
     const int nthr = ncl * kPerturbThreads;
     const int n = a.n, H = a.H, W = a.W, obj = a.obj;
+    const bool lin = (obj == SUPPY_OBJ_LINEAR);
     Vec y{a.x + b, a.B};
     Vec g{a.g + b, a.B};
 
     const PhaseStart ps = phase_start(a, b);
     long long ell = ps.ell;
     int accepted = 0, trials = 0;
-    double f_start = 0.0;
+    double f_start = 0.0;   // thread 0 of each CTA
     bool have_f = false;
     for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
-        // pass G: subgradient, ||g||^2 and f(y)
-        double gg = 0.0, fy = 0.0;
+        // pass G: subgradient, ||g||^2 and f(y) (the linear objective's terms
+        // in FP64, the others compensated FP32)
+        KSum kg, kf;
+        double fl = 0.0;
         for (int p = tid; p < n; p += nthr) {
-            fy += obj_term(obj, p, H, W, a.c64, y);
+            const double t = obj_term(obj, p, H, W, a.c64, y);
+            if (lin) fl += t;
+            else kf.add((float)t);
             if (!a.record_only) {
                 const float gp = subgrad(obj, p, H, W, a.c32, y);
                 __stcg(g.p + (size_t)p * a.B, gp);
-                gg += (double)gp * (double)gp;
+                kg.add(gp * gp);
             }
         }
-        const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
-        gg = r.x;
-        fy = r.y;
-        if (!have_f) {
-            f_start = fy;
-            have_f = true;
+        const double2 r = cluster_sum2(ff_of(kg), lin ? ff_of(fl) : ff_of(kf), swf, &scta, &sres,
+                                       cluster);
+        const double fy = r.y;
+        if (threadIdx.x == 0) {
+            if (!have_f) {
+                f_start = fy;
+                have_f = true;
+            }
+            dec = step_decision(a, st, r.x, fy, f_start);
         }
-        if (a.record_only || gg == 0.0) break;
-        const float inv_gnorm = 1.0f / sqrtf((float)gg);
-        float asc = 0.f;
-        if (a.adaptive) {
-            const double f_ref = adaptive_ref(a, st, f_start);
-            if (!(fy > f_ref)) break;
-            asc = adaptive_scale(fy, f_ref, gg);
-        }
+        __syncthreads();
+        if (!dec.go) break;
+        const float inv_gnorm = dec.inv_gnorm, asc = dec.asc;
         bool ok = false;
         const int jmax = a.adaptive ? 1 : a.max_trials;
         for (int j = 0; j < jmax; ++j) {
-            const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            if (threadIdx.x == 0)
+                sc_s = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            __syncthreads();
+            const float sc = sc_s;
             if (!a.adaptive) ell += 1;
             trials += 1;
             Vec yy = y;
             Vec gv = g;
             auto z = [yy, gv, sc](int q) { return trial(yy(q), gv(q), sc); };
-            double fz = 0.0;
-            for (int p = tid; p < n; p += nthr) fz += obj_term(obj, p, H, W, a.c64, z);
-            fz = cluster_sum2(fz, 0.0, sw, &scta, cluster).x;
+            KSum kz;
+            double fzl = 0.0;
+            for (int p = tid; p < n; p += nthr) {
+                const double t = obj_term(obj, p, H, W, a.c64, z);
+                if (lin) fzl += t;
+                else kz.add((float)t);
+            }
+            const double fz =
+                cluster_sum2(lin ? ff_of(fzl) : ff_of(kz), FF{0.f, 0.f}, swf, &scta, &sres, cluster).x;
             if (fz <= fy) {
                 for (int p = tid; p < n; p += nthr) {
                     const size_t o = (size_t)p * a.B;
@@ -336,20 +423,6 @@ struct GlobalImage {
     __device__ __forceinline__ float operator()(int i, int j) const {
         return __ldg(y + ((size_t)i * W + j) * B);
     }
-};
-
-// Per-thread compensated FP32 sum (Kahan); widened to FP64 for the cluster
-// reduction.  FP64 arithmetic is scarce on GB300: one FP64 add per pixel and
-// pass would cost more than the stencil itself.
-struct KSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        const float y = v - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 template <class Y>
@@ -400,11 +473,34 @@ __device__ __forceinline__ float tv_subgrad(int obj, int i, int j, int H, int W,
     return g;
 }
 
+// Row and column of element q of a strided loop over a row-major image (or
+// band) of width W, advanced without a division per element: q grows by
+// stride = si W + sj.
+struct StrideWalk {
+    int i, j, si, sj, W;
+    __device__ StrideWalk(int q0, int stride, int w) : W(w) {
+        i = q0 / w;
+        j = q0 - i * w;
+        si = stride / w;
+        sj = stride - si * w;
+    }
+    __device__ __forceinline__ void next() {
+        i += si;
+        j += sj;
+        if (j >= W) {
+            j -= W;
+            ++i;
+        }
+    }
+};
+
 __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbArgs a) {
     extern __shared__ float smem[];
     cg::cluster_group cluster = cg::this_cluster();
-    __shared__ double2 sw[kPerturbThreads / 32];
-    __shared__ double2 scta;
+    __shared__ FF swf[2 * (kPerturbThreads / 32)];
+    __shared__ double2 scta, sres;
+    __shared__ StepDecision dec;
+    __shared__ float sc_s;
     const int cs = (int)cluster.num_blocks();
     const int b = blockIdx.x / cs;
     RhsState& st = a.st[b];
@@ -444,74 +540,79 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
 
     long long ell = ps.ell;
     int accepted = 0, trials = 0;
-    double f_start = 0.0;
+    double f_start = 0.0;   // thread 0 of each CTA
     bool have_f = false;
     for (int s = 0; s < (a.record_only ? 1 : a.n_red); ++s) {
-        double gg = 0.0, fy = 0.0;
         KSum kg, kf;
-        for (int q = threadIdx.x; q < band; q += kPerturbThreads) {
-            if (lin) {
-                const int p = p0 + q;
-                fy += a.c64[p] * (double)ys[q];
-                const float gp = gs[q];
-                kg.add(gp * gp);
-            } else if (elem) {
-                kf.add(norm_term(a.obj, ys[q]));
-                if (!a.record_only) {
-                    const float gp = norm_grad(a.obj, ys[q]);
-                    gs[q] = gp;
+        double fl = 0.0;
+        {
+            StrideWalk px(threadIdx.x, kPerturbThreads, W);
+            for (int q = threadIdx.x; q < band; q += kPerturbThreads, px.next()) {
+                if (lin) {
+                    const int p = p0 + q;
+                    fl += a.c64[p] * (double)ys[q];
+                    const float gp = gs[q];
                     kg.add(gp * gp);
-                }
-            } else {
-                const int i = r0 + q / W, j = q % W;
-                kf.add(tv_term(a.obj, i, j, H, W, yb));
-                if (!a.record_only) {
-                    const float gp = tv_subgrad(a.obj, i, j, H, W, yb);
-                    gs[q] = gp;
-                    kg.add(gp * gp);
+                } else if (elem) {
+                    kf.add(norm_term(a.obj, ys[q]));
+                    if (!a.record_only) {
+                        const float gp = norm_grad(a.obj, ys[q]);
+                        gs[q] = gp;
+                        kg.add(gp * gp);
+                    }
+                } else {
+                    const int i = r0 + px.i, j = px.j;
+                    kf.add(tv_term(a.obj, i, j, H, W, yb));
+                    if (!a.record_only) {
+                        const float gp = tv_subgrad(a.obj, i, j, H, W, yb);
+                        gs[q] = gp;
+                        kg.add(gp * gp);
+                    }
                 }
             }
         }
-        gg += kg.value();
-        fy += kf.value();
-        const double2 r = cluster_sum2(gg, fy, sw, &scta, cluster);
-        gg = r.x;
-        fy = r.y;
-        if (!have_f) {
-            f_start = fy;
-            have_f = true;
+        const double2 r = cluster_sum2(ff_of(kg), lin ? ff_of(fl) : ff_of(kf), swf, &scta, &sres,
+                                       cluster);
+        const double fy = r.y;
+        if (threadIdx.x == 0) {
+            if (!have_f) {
+                f_start = fy;
+                have_f = true;
+            }
+            dec = step_decision(a, st, r.x, fy, f_start);
         }
-        if (a.record_only || gg == 0.0) break;
-        const float inv_gnorm = 1.0f / sqrtf((float)gg);
-        float asc = 0.f;
-        if (a.adaptive) {
-            const double f_ref = adaptive_ref(a, st, f_start);
-            if (!(fy > f_ref)) break;
-            asc = adaptive_scale(fy, f_ref, gg);
-        }
+        __syncthreads();
+        if (!dec.go) break;
+        const float inv_gnorm = dec.inv_gnorm, asc = dec.asc;
         bool ok = false;
         const int jmax = a.adaptive ? 1 : a.max_trials;
         for (int jt = 0; jt < jmax; ++jt) {
-            const float sc = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            if (threadIdx.x == 0)
+                sc_s = a.adaptive ? asc : trial_scale(a.gamma, a.log2_alpha, ell, inv_gnorm);
+            __syncthreads();
+            const float sc = sc_s;
             if (!a.adaptive) ell += 1;
             trials += 1;
-            double fz = 0.0;
+            FF fzp;
             if (lin) {
+                double fzl = 0.0;
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
-                    fz += a.c64[p0 + q] * (double)trial(ys[q], gs[q], sc);
+                    fzl += a.c64[p0 + q] * (double)trial(ys[q], gs[q], sc);
+                fzp = ff_of(fzl);
             } else if (elem) {
                 KSum kz;
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
                     kz.add(norm_term(a.obj, trial(ys[q], gs[q], sc)));
-                fz = kz.value();
+                fzp = ff_of(kz);
             } else {
                 auto z = [&yb, &gb, sc](int i, int j) { return trial(yb(i, j), gb(i, j), sc); };
                 KSum kz;
-                for (int q = threadIdx.x; q < band; q += kPerturbThreads)
-                    kz.add(tv_term(a.obj, r0 + q / W, q % W, H, W, z));
-                fz = kz.value();
+                StrideWalk px(threadIdx.x, kPerturbThreads, W);
+                for (int q = threadIdx.x; q < band; q += kPerturbThreads, px.next())
+                    kz.add(tv_term(a.obj, r0 + px.i, px.j, H, W, z));
+                fzp = ff_of(kz);
             }
-            fz = cluster_sum2(fz, 0.0, sw, &scta, cluster).x;
+            const double fz = cluster_sum2(fzp, FF{0.f, 0.f}, swf, &scta, &sres, cluster).x;
             if (fz <= fy) {
                 for (int q = threadIdx.x; q < band; q += kPerturbThreads)
                     ys[q] = trial(ys[q], gs[q], sc);
@@ -544,30 +645,6 @@ __global__ void __launch_bounds__(kPerturbThreads) k_perturb_smem(const PerturbA
 // loads (other CTAs rewrite them between passes; the barrier's fences make
 // those writes visible), never through the read-only path.  Element e of the
 // n x B array is pixel e / B of right-hand side e % B.
-
-// Float-float value hi + lo (about 44 significant bits): CTA-level sums of the
-// per-thread compensated FP32 sums stay in FP32 arithmetic, and FP64 is used
-// only for the grid-level sum of the CTA partials.
-struct FF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b.hi - bb) + (a.lo + b.lo);
-    const float hi = s + e;
-    return FF{hi, e - (hi - s)};
-}
-
-__device__ __forceinline__ FF ff_of(const KSum& k) { return FF{k.s, -k.c}; }
-
-// An FP64 value as float-float (used for the FP64 per-element sums of the
-// linear objective).
-__device__ __forceinline__ FF ff_of(double v) {
-    const float hi = (float)v;
-    return FF{hi, (float)(v - (double)hi)};
-}
 
 // Last-CTA election: every CTA's partials are visible to the CTA that draws
 // the last ticket; it resets the ticket for the next launch.
@@ -745,26 +822,6 @@ __device__ __forceinline__ float tv_trial_term(int obj, const TvNbr& t, float s)
     return v;
 }
 
-// Row and column of pixel p of a grid-stride loop, advanced without a
-// division per pixel: p grows by stride = si W + sj.
-struct PixelWalk {
-    int i, j, si, sj, W;
-    __device__ PixelWalk(int p0, int stride, int w) : W(w) {
-        i = p0 / w;
-        j = p0 - i * w;
-        si = stride / w;
-        sj = stride - si * w;
-    }
-    __device__ __forceinline__ void next() {
-        i += si;
-        j += sj;
-        if (j >= W) {
-            j -= W;
-            ++i;
-        }
-    }
-};
-
 __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbArgs a) {
     __shared__ FF sw[(kPhaseThreads / 32) * kWideTrials * 32];
     __shared__ double res[kWideTrials];
@@ -793,7 +850,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
             // pass G: subgradient, ||g||^2 and f(y)
             KSum kg, kf;
             double fl = 0.0;
-            PixelWalk px(tid, stride, tv ? W : 1);
+            StrideWalk px(tid, stride, tv ? W : 1);
             for (int p = tid; p < n; p += stride, px.next()) {
                 float gp;
                 if (lin) {
@@ -862,7 +919,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
                 double fz[kWideTrials];
 #pragma unroll
                 for (int q = 0; q < kWideTrials; ++q) fz[q] = 0.0;
-                PixelWalk px(tid, stride, tv ? W : 1);
+                StrideWalk px(tid, stride, tv ? W : 1);
                 for (int p = tid; p < n; p += stride, px.next()) {
                     if (lin) {
                         const float y0 = X[(size_t)p * B], g0 = G[(size_t)p * B];
