@@ -161,25 +161,45 @@ __device__ __forceinline__ unsigned gmask_of(int lane) {
     else return ((1u << G) - 1u) << (lane & ~(G - 1));
 }
 
+// Hands ring space back: the padded elements [e0, e1) of the slice count
+// toward their tiles, and the thread that completes a tile's count resets it
+// and arrives on the stage's empty barrier, so the producer may refill it.
+// Called by one lane of a group, after a __syncwarp over the group has
+// ordered every lane's reads of those elements before it.
+struct RingRelease {
+    int* tile_done;
+    uint64_t* empty;
+    int S, ts, lo_r, hi_r;
+    __device__ __forceinline__ void operator()(int e0, int e1) const {
+        for (int k = e0 >> ts; k <= (e1 - 1) >> ts; ++k) {
+            const int ov = min(e1, (k + 1) << ts) - max(e0, k << ts);
+            const int s = k % S;
+            const int target = min((k + 1) << ts, hi_r) - max(k << ts, lo_r);
+            if (atomicAdd(&tile_done[s], ov) + ov == target) {
+                tile_done[s] = 0;
+                mbar_arrive(&empty[s]);
+            }
+        }
+    }
+};
+
 // sum_e a_e * vec[idx_e] over the item's elements held in the ring, by the
-// G lanes of one group reading four elements per 16-byte ring access.  Lane
-// gl takes the quads gl, gl + G, gl + 2G, ...: four at a time (sixteen gathers
-// in flight), and the last one to three together, so that an item of up to
-// 16 G entries costs a single gather latency.  (One predicated batch of up
-// to eight quads measured slower on GB300: the extra outstanding gathers only
-// lengthen the queue at L1.)
-template <typename VT, int G>
+// G lanes of one group reading four elements per 16-byte ring access.  The
+// group walks the item in batches of 4G quads (uniform over the group):
+// lane gl loads the quads qb + gl, qb + gl + G, qb + gl + 2G, qb + gl + 3G
+// that exist (a missing quad gathers vec[0] with value 0), then issues their
+// sixteen gathers together, so that a batch costs one gather latency.  With
+// EARLY the group hands the batch's ring space back as soon as it sits in
+// registers, before the gathers, so the producer can refill it while the
+// gathers are in flight; without it each lane runs its own batches (the
+// form that measured fastest for the row pass).
+template <typename VT, int G, bool EARLY>
 __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, int gl,
-                                          const float* __restrict__ vec) {
+                                          const float* __restrict__ vec, const RingRelease& rel) {
     const int nq = (len + 3) >> 2;
-    int q = gl;
-    int p = r.pos(g0 + 4 * gl);
     float acc0 = 0.f, acc1 = 0.f;
-    auto quad = [&](float4& v, int4& c) {
-        v = Quad<VT>::load(r.val + p);
-        c = *reinterpret_cast<const int4*>(r.idx + p);
-        r.step(p, 4 * G);
-    };
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 zi = make_int4(0, 0, 0, 0);
     auto gather = [&](const int4& c) {
         return make_float4(__ldg(vec + c.x), __ldg(vec + c.y), __ldg(vec + c.z), __ldg(vec + c.w));
     };
@@ -189,104 +209,129 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
         acc0 = fmaf(v.z, x.z, acc0);
         acc1 = fmaf(v.w, x.w, acc1);
     };
-    for (; q + 3 * G < nq; q += 4 * G) {
-        float4 v0, v1, v2, v3;
-        int4 c0, c1, c2, c3;
-        quad(v0, c0);
-        quad(v1, c1);
-        quad(v2, c2);
-        quad(v3, c3);
-        const float4 x0 = gather(c0), x1 = gather(c1), x2 = gather(c2), x3 = gather(c3);
-        fma4(v0, x0);
-        fma4(v1, x1);
-        fma4(v2, x2);
-        fma4(v3, x3);
+    if constexpr (!EARLY) {
+        // no hand-back per batch: each lane runs its own full batches, then
+        // one batch of the one to three quads it has left
+        int q = gl;
+        int p = r.pos(g0 + 4 * gl);
+        for (; q + 3 * G < nq; q += 4 * G) {
+            float4 v[4];
+            int4 c[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = Quad<VT>::load(r.val + p);
+                c[k] = *reinterpret_cast<const int4*>(r.idx + p);
+                r.step(p, 4 * G);
+            }
+            float4 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = gather(c[k]);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) fma4(v[k], x[k]);
+        }
+        if (q < nq) {
+            float4 v[3] = {z, z, z};
+            int4 c[3] = {zi, zi, zi};
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (q + k * G < nq) {
+                    v[k] = Quad<VT>::load(r.val + p);
+                    c[k] = *reinterpret_cast<const int4*>(r.idx + p);
+                    r.step(p, G * 4);
+                }
+            float4 x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) x[k] = gather(c[k]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) fma4(v[k], x[k]);
+        }
+        return acc0 + acc1;
     }
-    if (q < nq) {
-        // one to three quads left: one batch; a missing quad gathers vec[0]
-        // with value 0
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int4 zi = make_int4(0, 0, 0, 0);
-        float4 v0, v1 = z, v2 = z;
-        int4 c0, c1 = zi, c2 = zi;
-        quad(v0, c0);
-        if (q + G < nq) quad(v1, c1);
-        if (q + 2 * G < nq) quad(v2, c2);
-        const float4 x0 = gather(c0), x1 = gather(c1), x2 = gather(c2);
-        fma4(v0, x0);
-        fma4(v1, x1);
-        fma4(v2, x2);
+    for (int qb = 0; qb < nq; qb += 4 * G) {
+        float4 v[4];
+        int4 c[4];
+        if (qb + 4 * G <= nq) {
+            int p = r.pos(g0 + 4 * (qb + gl));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = Quad<VT>::load(r.val + p);
+                c[k] = *reinterpret_cast<const int4*>(r.idx + p);
+                r.step(p, 4 * G);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int q = qb + gl + k * G;
+                if (q < nq) {
+                    const int p = r.pos(g0 + 4 * q);
+                    v[k] = Quad<VT>::load(r.val + p);
+                    c[k] = *reinterpret_cast<const int4*>(r.idx + p);
+                } else {
+                    v[k] = z;
+                    c[k] = zi;
+                }
+            }
+        }
+        if constexpr (EARLY) {
+            __syncwarp(gmask_of<G>(threadIdx.x & 31));
+            if (gl == 0) rel(g0 + 4 * qb, g0 + 4 * min(qb + 4 * G, nq));
+        }
+        float4 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = gather(c[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fma4(v[k], x[k]);
     }
     return acc0 + acc1;
 }
 
 // Lane-interleaved form of ring_dot: lane gl takes the elements gl, gl + G,
-// gl + 2G, ... of the item, U per batch, with 4-byte ring reads.  One
-// gather instruction of a group then reads G consecutive elements of the
-// item (and the group beside it the same positions of the next item), which
-// for the rows of a ray and the columns of neighbouring pixels lie in far
-// fewer cache lines than the 4G-element spread of one quad-form instruction.
-// Masked-off positions are not read; the padding is never touched.
-template <typename VT, int G, int U>
+// gl + 2G, ... of the item, U per batch (batches of U G elements, uniform
+// over the group), with 4-byte ring reads.  One gather instruction of a group
+// then reads G consecutive elements of the item (and the group beside it the
+// same positions of the next item), which for the rows of a ray and the
+// columns of neighbouring pixels lie in far fewer cache lines than the
+// 4G-element spread of one quad-form instruction.  Masked-off positions are
+// not read.  EARLY as in ring_dot (the last batch also hands back the padding).
+template <typename VT, int G, int U, bool EARLY>
 __device__ __forceinline__ float ring_dot_il(const Ring<VT>& r, int g0, int len, int gl,
-                                             const float* __restrict__ vec) {
+                                             const float* __restrict__ vec, const RingRelease& rel) {
     float acc0 = 0.f, acc1 = 0.f;
     const int p0 = r.pos(g0);
-    const int n = len - gl;   // this lane's elements: gl + e with e = t G < n
-    auto fma_batch = [&](const float* av, const float* xv) {
-#pragma unroll
-        for (int t = 0; t < U; t += 2) {
-            acc0 = fmaf(av[t], xv[t], acc0);
-            acc1 = fmaf(av[t + 1], xv[t + 1], acc1);
-        }
-    };
-    if (p0 + len <= r.size) {
-        const VT* v = r.val + p0 + gl;
-        const int* ix = r.idx + p0 + gl;
-        int e = 0;
-        for (; e + (U - 1) * G < n; e += U * G) {
-            int c[U];
-            float av[U], xv[U];
+    const int lenp = (len + 3) & ~3;
+    const bool wraps = p0 + len > r.size;   // the item wraps around the end of the ring
+    for (int e = 0; e < len; e += U * G) {
+        int c[U];
+        float av[U], xv[U];
+        if (!wraps && e + U * G <= len) {
+            const VT* v = r.val + p0 + e + gl;
+            const int* ix = r.idx + p0 + e + gl;
 #pragma unroll
             for (int t = 0; t < U; ++t) {
-                c[t] = ix[e + t * G];
-                av[t] = to_f(v[e + t * G]);
+                c[t] = ix[t * G];
+                av[t] = to_f(v[t * G]);
             }
-#pragma unroll
-            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
-            fma_batch(av, xv);
-        }
-        if (e < n) {
-            // fewer than U elements left for this lane: one masked batch
-            int c[U];
-            float av[U], xv[U];
+        } else {
+            int p = p0 + e + gl;
+            if (p >= r.size) p -= r.size;
 #pragma unroll
             for (int t = 0; t < U; ++t) {
-                const bool in = e + t * G < n;
-                c[t] = in ? ix[e + t * G] : 0;
-                av[t] = in ? to_f(v[e + t * G]) : 0.f;
-            }
-#pragma unroll
-            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
-            fma_batch(av, xv);
-        }
-    } else {
-        // the item wraps around the end of the ring
-        int p = p0 + gl;
-        if (p >= r.size) p -= r.size;
-        for (int e = 0; e < n; e += U * G) {
-            int c[U];
-            float av[U], xv[U];
-#pragma unroll
-            for (int t = 0; t < U; ++t) {
-                const bool in = e + t * G < n;
+                const bool in = e + gl + t * G < len;
                 c[t] = in ? r.idx[p] : 0;
                 av[t] = in ? to_f(r.val[p]) : 0.f;
                 r.step(p, G);
             }
+        }
+        if constexpr (EARLY) {
+            __syncwarp(gmask_of<G>(threadIdx.x & 31));
+            if (gl == 0) rel(g0 + e, g0 + (e + U * G >= len ? lenp : e + U * G));
+        }
 #pragma unroll
-            for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
-            fma_batch(av, xv);
+        for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
+#pragma unroll
+        for (int t = 0; t < U; t += 2) {
+            acc0 = fmaf(av[t], xv[t], acc0);
+            acc1 = fmaf(av[t + 1], xv[t + 1], acc1);
         }
     }
     return acc0 + acc1;
@@ -294,11 +339,11 @@ __device__ __forceinline__ float ring_dot_il(const Ring<VT>& r, int g0, int len,
 
 // U: elements a lane holds per batch of the lane-interleaved form (the row
 // pass keeps more per-item state live and takes fewer, spilling none).
-template <typename VT, int G, int MAP, int U>
+template <typename VT, int G, int MAP, int U, bool EARLY>
 __device__ __forceinline__ float item_dot(const Ring<VT>& r, int g0, int len, int gl,
-                                          const float* __restrict__ vec) {
-    if constexpr (MAP == 1) return ring_dot_il<VT, G, U>(r, g0, len, gl, vec);
-    else return ring_dot<VT, G>(r, g0, len, gl, vec);
+                                          const float* __restrict__ vec, const RingRelease& rel) {
+    if constexpr (MAP == 1) return ring_dot_il<VT, G, U, EARLY>(r, g0, len, gl, vec, rel);
+    else return ring_dot<VT, G, EARLY>(r, g0, len, gl, vec, rel);
 }
 
 // Producer / consumer skeleton.  Consumer warps hold 32/G groups of G lanes.
@@ -404,9 +449,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             }
             return mbar_wait(&full[s], (k / S) & 1, &abort_flag);
         };
-        auto target = [&](int k) {
-            return min((k + 1) << ts, hi_r) - max(k << ts, lo_r);
-        };
+        const RingRelease rel{tile_done, empty, S, ts, lo_r, hi_r};
         auto grab = [&]() {
             int b = 0;
             if (lane == 0) b = atomicAdd(&next_grab, GPW);
@@ -440,21 +483,12 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             for (int k = kb; ok && k <= ke; ++k) ok = __all_sync(0xffffffffu, wait_tile(k));
             const long long t3 = SSTAT_CLOCK();
             if (!ok) break;
-            if (has) acc += work(i, inf.y, g0, ring, gl);
+            if (has) acc += work(i, inf.y, g0, ring, gl, rel);
             __syncwarp();
             const long long t4 = SSTAT_CLOCK();
-            // hand the group's padded elements back, tile by tile
-            if (has && gl == 0) {
-                const int e1 = g0 + ((inf.y + 3) & ~3);
-                for (int k = g0 >> ts; k <= (e1 - 1) >> ts; ++k) {
-                    const int ov = min(e1, (k + 1) << ts) - max(g0, k << ts);
-                    const int s = k % S;
-                    if (atomicAdd(&tile_done[s], ov) + ov == target(k)) {
-                        tile_done[s] = 0;
-                        mbar_arrive(&empty[s]);
-                    }
-                }
-            }
+            // hand the group's padded elements back (a work that reads the
+            // ring only once did so batch by batch)
+            if (!Work::kEarly && has && gl == 0) rel(g0, g0 + ((inf.y + 3) & ~3));
             st_full += t3 - t2;
             st_work += t4 - t3;
             st_rel += SSTAT_CLOCK() - t4;
@@ -492,6 +526,11 @@ __device__ __forceinline__ void cta_sum_to(double v, double* out) {
 // Row pass.  SCAT 0: coefficients written to a.coef (when set); 1: scatter.
 template <typename VT, int G, int SCAT, int MAP>
 struct RowWork {
+    // the ring space goes back once the item is done (the scatter reads the
+    // item's elements a second time; without it, handing space back batch by
+    // batch measured slower for this pass: 0.233 against 0.217 ms on CT
+    // 512x512, while the column pass gained)
+    static constexpr bool kEarly = false;
     const StreamArgs& a;
     float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
     float nl = 0.f, nu = 0.f, nw = 0.f;     // next round's
@@ -525,9 +564,10 @@ struct RowWork {
         pm = npm;
     }
     __device__ void empty(int) {}   // an empty row: no coefficient, no proximity term
-    __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl) {
+    __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl,
+                                 const RingRelease& rel) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        float dot = item_dot<VT, G, MAP, 12>(r, g0, len, gl, a.x);
+        float dot = item_dot<VT, G, MAP, 12, kEarly>(r, g0, len, gl, a.x, rel);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;
@@ -558,6 +598,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_rows_tma(const StreamArgs
 // Column pass of the two-pass sweep (B = 1).
 template <typename VT, int G, int MAP>
 struct ColWork {
+    static constexpr bool kEarly = true;
     const StreamArgs& a;
     float xj = 0.f, lo = 0.f, hi = 0.f, z = 1.f;
     float nx = 0.f, nlo = 0.f, nhi = 0.f, nz = 1.f;
@@ -582,9 +623,10 @@ struct ColWork {
         if (a.delta_out) a.delta_out[j] = 0.f;
         else a.xw[j] = clampf(xj, lo, hi);
     }
-    __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl) {
+    __device__ double operator()(int j, int len, int g0, const Ring<VT>& r, int gl,
+                                 const RingRelease& rel) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        float s = item_dot<VT, G, MAP, sizeof(VT) == 4 ? 16 : 12>(r, g0, len, gl, a.coef_in);
+        float s = item_dot<VT, G, MAP, sizeof(VT) == 4 ? 16 : 12, true>(r, g0, len, gl, a.coef_in, rel);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gm, s, o);
         if (a.zc) s *= z;
