@@ -1676,41 +1676,75 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (need_csc) cands.push_back({2, 0});
     Cand best = cands[0];
     if (want == 0 && !o->tune) best = smem_ok ? Cand{1, 2} : Cand{2, 0};
+    const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
+    // Launch shape of a candidate: the register-fed sweep's row shape, then
+    // (when the streamed passes serve it) their ring shapes and lane maps,
+    // fixed by the caller, defaulted, or -- when tuning -- measured.
+    struct Shapes {
+        int tG, tile, stages, tMap, tGc, ctile, cstages, tMapc;
+        bool use_tma;
+    };
+    auto set_up = [&](const Cand& cd, bool tune_streams) -> suppy_status {
+        c->strategy = cd.strategy;
+        c->scat = cd.scat;
+        choose_row_shape(c, mean_len, max_len);
+        suppy_status st;
+        if ((st = build_row_partition(c)) != SUPPY_OK) return st;
+        default_tma_shape(c);
+        c->tMap = o->stream_map ? o->stream_map - 1 : kDefaultRowMap;
+        c->tMapc = o->stream_map ? o->stream_map - 1 : kDefaultColMap;
+        if (fixed_shape) apply_stream_shape(c, o->stream_tile, o->stream_stages, o->stream_lanes);
+        c->use_tma = tma_eligible(c, o->tma);
+        if (fixed_shape && c->use_tma &&
+            (!group_fits(c->tG, c->max_row, c->tile, c->stages) ||
+             (c->strategy == 2 && !group_fits(c->tGc, c->max_col, c->ctile, c->cstages))))
+            c->use_tma = false;
+        if (c->use_tma) {
+            if ((st = build_tma_partitions(c)) != SUPPY_OK) return st;
+            if (tune_streams && !fixed_shape && (st = tune_tma(c, o->stream_map == 0)) != SUPPY_OK)
+                return st;
+        }
+        return SUPPY_OK;
+    };
+    auto save = [&]() {
+        return Shapes{c->tG, c->tile, c->stages, c->tMap, c->tGc, c->ctile, c->cstages, c->tMapc,
+                      c->use_tma};
+    };
+    Shapes best_sh{};
+    bool have_sh = false;
     if (o->tune && cands.size() > 1) {
+        // every candidate strategy with its own streamed shapes tuned, so the
+        // comparison is between the best form of each
         float best_ms = 1e30f;
         for (const Cand& cd : cands) {
-            c->strategy = cd.strategy;
-            c->scat = cd.scat;
-            choose_row_shape(c, mean_len, max_len);
-            if ((s = build_row_partition(c)) != SUPPY_OK) return s;
-            default_tma_shape(c);
-            c->use_tma = tma_eligible(c, o->tma);
-            if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
+            if ((s = set_up(cd, true)) != SUPPY_OK) return s;
             float ms = 0.f;
             if ((s = time_config(c, &ms)) != SUPPY_OK) return s;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = cd;
+                best_sh = save();
+                have_sh = true;
             }
         }
     }
-    c->strategy = best.strategy;
-    c->scat = best.scat;
-    choose_row_shape(c, mean_len, max_len);
-    if ((s = build_row_partition(c)) != SUPPY_OK) return s;
-    default_tma_shape(c);
-    c->tMap = o->stream_map ? o->stream_map - 1 : kDefaultRowMap;
-    c->tMapc = o->stream_map ? o->stream_map - 1 : kDefaultColMap;
-    const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
-    if (fixed_shape) apply_stream_shape(c, o->stream_tile, o->stream_stages, o->stream_lanes);
-    c->use_tma = tma_eligible(c, o->tma);
-    if (fixed_shape && c->use_tma && (!group_fits(c->tG, c->max_row, c->tile, c->stages) ||
-                                      (c->strategy == 2 &&
-                                       !group_fits(c->tGc, c->max_col, c->ctile, c->cstages))))
-        c->use_tma = false;
-    if (c->use_tma) {
-        if ((s = build_tma_partitions(c)) != SUPPY_OK) return s;
-        if (o->tune && !fixed_shape && (s = tune_tma(c, o->stream_map == 0)) != SUPPY_OK) return s;
+    if (have_sh) {
+        c->strategy = best.strategy;
+        c->scat = best.scat;
+        choose_row_shape(c, mean_len, max_len);
+        if ((s = build_row_partition(c)) != SUPPY_OK) return s;
+        c->tG = best_sh.tG;
+        c->tile = best_sh.tile;
+        c->stages = best_sh.stages;
+        c->tMap = best_sh.tMap;
+        c->tGc = best_sh.tGc;
+        c->ctile = best_sh.ctile;
+        c->cstages = best_sh.cstages;
+        c->tMapc = best_sh.tMapc;
+        c->use_tma = best_sh.use_tma;
+        if (c->use_tma && (s = build_tma_partitions(c)) != SUPPY_OK) return s;
+    } else if ((s = set_up(best, o->tune != 0)) != SUPPY_OK) {
+        return s;
     }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
