@@ -969,11 +969,13 @@ bool group_fits(int G, int max_item, int tile, int stages) {
 }
 
 // Lanes per item of a streaming pass.  The items all consumer warps hold in
-// one round must fill well under half of the ring, so that the rest streams
-// ahead of them; within that, narrow groups (several items per warp) keep
-// more gathers in flight per lane.
+// one round must leave part of the ring to stream ahead of them; within that,
+// narrow groups (several items per warp) keep more gathers in flight per lane.
+// The budget (items of up to 90% of the ring in a round) matches the lane
+// counts the tuner measured fastest on CT 384x384 and 512x512 (16 lanes where
+// a budget of 45% gave 32).
 int stream_group(double mean_len, int max_item, int tile, int stages) {
-    const double budget = 0.45 * (double)stages * tile / (kStreamThreads / 32 - 1);
+    const double budget = 0.9 * (double)stages * tile / (kStreamThreads / 32 - 1);
     int g = 4;
     while (g < 32 && ((32 / g) * mean_len > budget || !group_fits(g, max_item, tile, stages))) g *= 2;
     return g;

@@ -190,9 +190,9 @@ struct RingRelease {
 // that exist (a missing quad gathers vec[0] with value 0), then issues their
 // sixteen gathers together, so that a batch costs one gather latency.  With
 // EARLY the group hands the batch's ring space back as soon as it sits in
-// registers, before the gathers, so the producer can refill it while the
-// gathers are in flight; without it each lane runs its own batches (the
-// form that measured fastest for the row pass).
+// registers, while its gathers are in flight, so the producer can refill it
+// meanwhile; without it each lane runs its own batches (the form that
+// measured fastest for the row pass).
 template <typename VT, int G, bool EARLY>
 __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, int gl,
                                           const float* __restrict__ vec, const RingRelease& rel) {
@@ -272,13 +272,14 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
                 }
             }
         }
-        if constexpr (EARLY) {
-            __syncwarp(gmask_of<G>(threadIdx.x & 31));
-            if (gl == 0) rel(g0 + 4 * qb, g0 + 4 * min(qb + 4 * G, nq));
-        }
+        // every lane's ring reads of the batch are done; the hand-back goes
+        // after the gathers are issued, so its shared-memory atomics overlap
+        // their latency instead of delaying them
+        __syncwarp(gmask_of<G>(threadIdx.x & 31));
         float4 x[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) x[k] = gather(c[k]);
+        if (gl == 0) rel(g0 + 4 * qb, g0 + 4 * min(qb + 4 * G, nq));
 #pragma unroll
         for (int k = 0; k < 4; ++k) fma4(v[k], x[k]);
     }
@@ -322,12 +323,13 @@ __device__ __forceinline__ float ring_dot_il(const Ring<VT>& r, int g0, int len,
                 r.step(p, G);
             }
         }
-        if constexpr (EARLY) {
-            __syncwarp(gmask_of<G>(threadIdx.x & 31));
-            if (gl == 0) rel(g0 + e, g0 + (e + U * G >= len ? lenp : e + U * G));
-        }
+        if constexpr (EARLY) __syncwarp(gmask_of<G>(threadIdx.x & 31));
 #pragma unroll
         for (int t = 0; t < U; ++t) xv[t] = __ldg(vec + c[t]);
+        if constexpr (EARLY) {
+            // after the gathers are issued (see ring_dot)
+            if (gl == 0) rel(g0 + e, g0 + (e + U * G >= len ? lenp : e + U * G));
+        }
 #pragma unroll
         for (int t = 0; t < U; t += 2) {
             acc0 = fmaf(av[t], xv[t], acc0);
