@@ -528,15 +528,17 @@ __device__ __forceinline__ void cta_sum_to(double v, double* out) {
 // Row pass.  SCAT 0: coefficients written to a.coef (when set); 1: scatter.
 template <typename VT, int G, int SCAT, int MAP>
 struct RowWork {
-    // the ring space goes back once the item is done (the scatter reads the
-    // item's elements a second time; without it, handing space back batch by
-    // batch measured slower for this pass: 0.233 against 0.217 ms on CT
-    // 512x512, while the column pass gained)
-    static constexpr bool kEarly = false;
+    // the scatter reads the item's ring elements a second time: they go back
+    // only once the item is done; otherwise batch by batch, as they are read
+    // (FP32 values: with 16-bit values the extra state spills and the BF16
+    // row pass measured slower, 0.214 against 0.193 ms on CT 512x512)
+    static constexpr bool kEarly = (SCAT == 0 && sizeof(VT) == 4);
     const StreamArgs& a;
     float li = 0.f, ui = 0.f, w = 0.f;      // current round's bounds and weight
     float nl = 0.f, nu = 0.f, nw = 0.f;     // next round's
-    float cm = 1.f, pm = 1.f, ncm = 1.f, npm = 1.f;   // coefficient / proximity multipliers
+    // the row multiplier of the coefficient (coef_mul) or of the proximity
+    // term (prox_mul): a pass sets at most one of them
+    float m = 1.f, nm = 1.f;
     // The group leader's proximity terms are summed in FP32 with Kahan
     // compensation (error independent of the term count) and widened to FP64
     // for the CTA and grid reductions: FP64 arithmetic is scarce on GB300 and
@@ -554,16 +556,15 @@ struct RowWork {
             nl = __ldg(a.l + i);
             nu = __ldg(a.u + i);
             nw = __ldg(a.wr + i);
-            if (a.coef_mul) ncm = __ldg(a.coef_mul + i);
-            if (a.prox_mul) npm = __ldg(a.prox_mul + i);
+            const float* mp = a.coef_mul ? a.coef_mul : a.prox_mul;
+            if (mp) nm = __ldg(mp + i);
         }
     }
     __device__ void advance() {
         li = nl;
         ui = nu;
         w = nw;
-        cm = ncm;
-        pm = npm;
+        m = nm;
     }
     __device__ void empty(int) {}   // an empty row: no coefficient, no proximity term
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl,
@@ -573,7 +574,7 @@ struct RowWork {
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;
-        const float coef = a.lam * w * d * cm;
+        const float coef = a.lam * w * d * (a.coef_mul ? m : 1.f);
         if (SCAT == 0) {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
@@ -584,7 +585,7 @@ struct RowWork {
                 r.step(p, G);
             }
         }
-        if (gl == 0) kahan_add(d * d * w * pm);
+        if (gl == 0) kahan_add(d * d * w * (a.prox_mul ? m : 1.f));
         return 0.0;
     }
 };
