@@ -157,11 +157,12 @@ typedef struct {
      * (4, 8, 16 or 32).  Values outside these ranges give SUPPY_EINVAL; a shape
      * whose ring window cannot hold a warp's items leaves streaming off. */
     int32_t stream_tile, stream_stages, stream_lanes;
-    /* Perturbation phase: 2 -- the first reduction step on the whole GPU
-     * (subgradient pass, eight trial step sizes evaluated in one pass, the
-     * first accepted one applied: the same choice as the sequential trial
-     * loop), the rest of the phase, when there is one, by one thread-block
-     * cluster per right-hand side; 1 -- the cluster kernel alone; 0 --
+    /* Perturbation phase: 2 -- the whole phase on the whole GPU in one
+     * cooperative launch (subgradient pass, passes evaluating up to eight
+     * consecutive trial step sizes at once with the first accepted one
+     * applied -- the same choice as the sequential trial loop -- and grid
+     * barriers between passes; several right-hand sides one after the
+     * other); 1 -- one thread-block cluster per right-hand side; 0 --
      * automatic: 2 for one right-hand side with n >= 65536, else 1. */
     int32_t perturb_path;
     /* Lane map of the streaming passes: 0 automatic (measured when tune is

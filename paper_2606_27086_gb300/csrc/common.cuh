@@ -120,9 +120,8 @@ struct ColArgs {
     EpiArgs epi;
 };
 
-// Per right-hand side state of the first reduction step of a perturbation
-// phase taken by the whole-GPU kernels (k_wide_*); the cluster kernel
-// resumes from it when that step did not finish the phase.
+// Arguments of the perturbation-phase kernels (cluster kernels and the
+// whole-GPU cooperative kernel).
 struct PerturbArgs {
     float* x;               // n x B
     float* g;               // n x B scratch for the subgradient

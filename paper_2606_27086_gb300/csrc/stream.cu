@@ -10,9 +10,12 @@
 // consecutive items in order from a shared counter and read them from the
 // ring (four consecutive elements per lane and 16-byte access, or lane-
 // interleaved elements), so HBM streaming runs ahead of the gathers of x (or
-// of the coefficients) instead of waiting behind them.  A
-// stage is refilled once every item element of its tile is done.  G, T and S are launch parameters (chosen per matrix,
-// by measurement when the context is tuned).
+// of the coefficients) instead of waiting behind them.  A stage is refilled
+// once every item element of its tile has been read (a group hands its
+// elements back batch by batch as they reach registers, or, when it reads
+// them again later, once the item is done).  G, T, S and the lane map are
+// launch parameters (chosen per matrix, by measurement when the context is
+// tuned).
 //
 // Items start at multiples of four elements and are zero-padded to a
 // multiple of four (value 0, index 0), so a 16-byte ring access never holds

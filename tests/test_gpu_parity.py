@@ -532,8 +532,9 @@ PERT_CASES = [
 @pytest.mark.parametrize("case", PERT_CASES)
 @pytest.mark.parametrize("kind", ["tv", "atv"])
 def test_whole_gpu_perturbation_matches_oracle_and_cluster_path(kind, case):
-    """The whole-GPU phase (one cooperative launch; eight trials per pass,
-    first acceptance kept; grid barriers between passes) gives the oracle's
+    """The whole-GPU phase (one cooperative launch; two trials in a step's
+    first pass, eight in later ones, first acceptance kept; grid barriers
+    between passes) gives the oracle's
     phase and the cluster kernel's: the same accepted steps, trial count and
     exponent, and the same point -- also when a step needs more than one
     pass of trials (max_trials 100) or the trials run out (max_trials 3)."""
