@@ -163,9 +163,9 @@ __device__ __forceinline__ float subgrad(int obj, int p, int H, int W, const flo
     return g;
 }
 
-// Per-thread compensated FP32 sum (Kahan); widened to FP64 for the cluster
-// reduction.  FP64 arithmetic is scarce on GB300: one FP64 add per pixel and
-// pass would cost more than the stencil itself.
+// Per-thread compensated FP32 sum (Kahan), handed to the CTA and cluster
+// reductions as a float-float value.  FP64 arithmetic is scarce on GB300: one
+// FP64 add per pixel and pass would cost more than the stencil itself.
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v) {
@@ -174,7 +174,6 @@ struct KSum {
         c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 // Float-float value hi + lo (about 44 significant bits): CTA-level sums of the
@@ -415,15 +414,6 @@ struct Band {
 };
 
 __device__ __forceinline__ int band_start(int r, int H, int cs) { return (int)((long long)H * r / cs); }
-
-// Image of one right-hand side in global memory (read-only during a launch).
-struct GlobalImage {
-    const float* y;   // element 0 of the right-hand side
-    int B, W;
-    __device__ __forceinline__ float operator()(int i, int j) const {
-        return __ldg(y + ((size_t)i * W + j) * B);
-    }
-};
 
 template <class Y>
 __device__ __forceinline__ float tv_term(int obj, int i, int j, int H, int W, const Y& y) {
@@ -753,7 +743,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const doub
     __syncthreads();
     const int st = st_s;
     if (st & 2) {
-        if (NV > 0) {
+        if constexpr (NV > 0) {
             grid_sums<NV, kPhaseThreads>(part, 1, res);
             if (threadIdx.x < NV) gsum[threadIdx.x] = res[threadIdx.x];
             __syncthreads();
@@ -764,8 +754,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const doub
             __threadfence();
             atomicAdd(bar + 1, 1u);
         }
-    } else if (NV > 0) {
-        if (threadIdx.x < NV) res[threadIdx.x] = __ldcg(gsum + threadIdx.x);
+    } else {
+        if constexpr (NV > 0)
+            if (threadIdx.x < NV) res[threadIdx.x] = __ldcg(gsum + threadIdx.x);
     }
     __syncthreads();
     return (st & 1) && *(volatile int*)err == 0;

@@ -249,44 +249,45 @@ __device__ __forceinline__ float ring_dot(const Ring<VT>& r, int g0, int len, in
             for (int k = 0; k < 3; ++k) fma4(v[k], x[k]);
         }
         return acc0 + acc1;
-    }
-    for (int qb = 0; qb < nq; qb += 4 * G) {
-        float4 v[4];
-        int4 c[4];
-        if (qb + 4 * G <= nq) {
-            int p = r.pos(g0 + 4 * (qb + gl));
+    } else {
+        for (int qb = 0; qb < nq; qb += 4 * G) {
+            float4 v[4];
+            int4 c[4];
+            if (qb + 4 * G <= nq) {
+                int p = r.pos(g0 + 4 * (qb + gl));
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v[k] = Quad<VT>::load(r.val + p);
-                c[k] = *reinterpret_cast<const int4*>(r.idx + p);
-                r.step(p, 4 * G);
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int q = qb + gl + k * G;
-                if (q < nq) {
-                    const int p = r.pos(g0 + 4 * q);
+                for (int k = 0; k < 4; ++k) {
                     v[k] = Quad<VT>::load(r.val + p);
                     c[k] = *reinterpret_cast<const int4*>(r.idx + p);
-                } else {
-                    v[k] = z;
-                    c[k] = zi;
+                    r.step(p, 4 * G);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = qb + gl + k * G;
+                    if (q < nq) {
+                        const int p = r.pos(g0 + 4 * q);
+                        v[k] = Quad<VT>::load(r.val + p);
+                        c[k] = *reinterpret_cast<const int4*>(r.idx + p);
+                    } else {
+                        v[k] = z;
+                        c[k] = zi;
+                    }
                 }
             }
+            // every lane's ring reads of the batch are done; the hand-back goes
+            // after the gathers are issued, so its shared-memory atomics overlap
+            // their latency instead of delaying them
+            __syncwarp(gmask_of<G>(threadIdx.x & 31));
+            float4 x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = gather(c[k]);
+            if (gl == 0) rel(g0 + 4 * qb, g0 + 4 * min(qb + 4 * G, nq));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) fma4(v[k], x[k]);
         }
-        // every lane's ring reads of the batch are done; the hand-back goes
-        // after the gathers are issued, so its shared-memory atomics overlap
-        // their latency instead of delaying them
-        __syncwarp(gmask_of<G>(threadIdx.x & 31));
-        float4 x[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = gather(c[k]);
-        if (gl == 0) rel(g0 + 4 * qb, g0 + 4 * min(qb + 4 * G, nq));
-#pragma unroll
-        for (int k = 0; k < 4; ++k) fma4(v[k], x[k]);
+        return acc0 + acc1;
     }
-    return acc0 + acc1;
 }
 
 // Lane-interleaved form of ring_dot: lane gl takes the elements gl, gl + G,
@@ -409,6 +410,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             const uint32_t bytes_v = (uint32_t)(T * sizeof(VT)), bytes_i = (uint32_t)(T * 4);
             int issued = 0;
             long long st_t0 = SSTAT_CLOCK(), st_wait = 0;
+            (void)st_t0;
             for (int k = 0, s = 0, ph = 0; k < K; ++k) {
                 const long long tw = SSTAT_CLOCK();
                 if (k >= S && !mbar_wait(&empty[s], (ph - 1) & 1, &abort_flag)) {
@@ -462,6 +464,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
         };
         constexpr int BIG = 0x7fffffff;
         long long st_t0 = SSTAT_CLOCK(), st_full = 0, st_rel = 0, st_work = 0, st_rounds = 0;
+        (void)st_t0;
         int nb = grab();
         int2 nxt = (nb + gw < nitems) ? a.info[I0 + nb + gw] : make_int2(0, 0);
         work.prefetch(nb + gw < nitems ? I0 + nb + gw : -1);
