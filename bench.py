@@ -226,6 +226,24 @@ def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
 KIND = {0: "row pass", 1: "column pass / finalize", 2: "perturbation", 3: "split (CQ) step"}
 
 
+def measured_traffic(table, info, dom):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    capture (profiles/traffic.json), or None when there is none or it was
+    taken on another launch shape than the one this run's tuner picked (ring
+    tile and stages, lanes per item, lane map)."""
+    key = f"ct512_{info['strategy']}_{dom}"
+    tr, shape = table.get(key), table.get(key + "_shape")
+    if not tr or not shape:
+        return None
+    if dom == 0:
+        now = {"tile": info["tile"], "stages": info["stages"], "lanes": info["lanes_per_row"],
+               "map": info["map"]}
+    else:
+        now = {"tile": info["col_tile"], "stages": info["col_stages"], "lanes": info["col_lanes"],
+               "map": info["col_map"]}
+    return tr if now == shape else None
+
+
 def kernel_alg_bytes(strategy, kind, m, n, nnz, vb, B=1):
     """Algorithmic bytes of one sweep's kernel of the given kind (summed over
     the blocks of a block-iterative sweep).  Row pass: A's values and column
@@ -602,11 +620,12 @@ def ours(args):
     traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(traffic_path):
         try:
-            tr = json.load(open(traffic_path)).get(f"ct512_{info['strategy']}_{dom}")
-            if tr:
-                roof["traffic"] = tr
-        except Exception:
-            pass
+            table = json.load(open(traffic_path))
+        except (OSError, ValueError):
+            table = {}
+        roof["traffic"] = measured_traffic(table, info, dom)
+        if roof["traffic"] is None and f"ct512_{info['strategy']}_{dom}" in table:
+            roof["traffic_note"] = "the committed capture is of another launch shape"
 
     # end to end through the C ABI with host buffers
     Ke = max(5, min(K, 100))
