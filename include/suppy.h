@@ -133,7 +133,9 @@ typedef struct {
     const int32_t* block_of_row;
     int32_t nblocks;
     suppy_obj obj;
-    int32_t img_h, img_w;     /* TV objectives: img_h * img_w == n */
+    int32_t img_h, img_w;     /* TV objectives: img_h * img_w == n; with other
+                                 objectives optional (0, 0), the grid of the
+                                 unknowns the tiled sweep cuts into tiles */
     /* SUPPY_OBJ_LINEAR: either c_lin (n floats, host) or obj_rows, an
      * objective matrix S whose column means c = S^T 1 / rows(S) are computed
      * on the device at create (f_Mean over the structure S). */
@@ -146,7 +148,16 @@ typedef struct {
      * correction scattered by L2 reductions, or staged in shared memory when
      * n*B*4 bytes fit); 2 two passes (row pass writing the coefficients, then a
      * column pass over a CSC copy of A gathering them -- no atomics, bitwise
-     * reproducible, twice the matrix memory). */
+     * reproducible, twice the matrix memory); 3 tiled one pass (one
+     * right-hand side; Cimmino, BIP or DROP): the unknowns are split into one
+     * tile per SM (image rectangles when img_h x img_w is given, column
+     * ranges otherwise), each CTA keeps its tile's x and correction in shared
+     * memory and streams its tile's segments of A -- runs of a row's entries
+     * in the tile, with 16-bit tile-local indices -- once per sweep; the dot
+     * products of a row are combined across tiles by L2 reductions, chunk by
+     * chunk.  Strategy 3 gives SUPPY_EINVAL when the problem does not fit it
+     * (a tile above 8192 unknowns, several right-hand sides, EL / EMR); with
+     * tune set and strategy 0 it is one of the timed candidates. */
     int32_t strategy;
     /* Streaming of A through shared memory by bulk asynchronous copies (TMA)
      * for one right-hand side: 0 automatic (used when eligible), -1 off. */
@@ -171,6 +182,16 @@ typedef struct {
      * k + 2G, ...: one gather instruction reads G consecutive elements of an
      * item).  Other values give SUPPY_EINVAL. */
     int32_t stream_map;
+    /* Tiled sweep (strategy 3): lanes per segment (0 automatic = 8, else 8,
+     * 16 or 32) and warps of its dot-product phase (0 automatic = 12, else
+     * 1..30; the correction phase gets the other 31 - tile_warps1 warps of a
+     * 1024-thread CTA).  Other values give SUPPY_EINVAL. */
+    int32_t tile_lanes, tile_warps1;
+    /* Tiled sweep: stream bytes per tile and chunk aimed at (0 automatic =
+     * 16384; smaller values give more chunks) and a fixed ring (0 automatic =
+     * up to 24 copies of 8 KB in the shared memory left; else 8 copies of
+     * tile_ring_bytes / 8 bytes, a power of two in [256, 8192]). */
+    int32_t tile_chunk_bytes, tile_ring_bytes;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -229,7 +250,7 @@ typedef struct {
     int32_t block;                /* threads per CTA of the sweep launch     */
     int32_t perturb_cluster;      /* CTAs per cluster of the perturbation    */
     int64_t device_bytes;         /* device memory held by the context       */
-    int32_t strategy;             /* 1 one pass, 2 two passes                */
+    int32_t strategy;             /* 1 one pass, 2 two passes, 3 tiled one pass */
     int32_t scatter;              /* one pass: 1 L2 reductions, 2 shared-memory staged */
     int32_t col_lanes;            /* two passes: lanes per column            */
     int32_t col_grid;             /* two passes: CTAs of the column pass     */
@@ -237,6 +258,11 @@ typedef struct {
     int32_t tile, stages;         /* streaming row pass: ring tile length (elements), stages */
     int32_t col_tile, col_stages; /* streaming column pass: the same       */
     int32_t map, col_map;         /* streaming lane maps (opts.stream_map: 1 or 2) */
+    /* tiled sweep (strategy 3): tiles (= CTAs), chunks, lanes per segment,
+     * warps of the two phases, ring bytes, bytes and segments of the tile
+     * streams; zero for the other strategies */
+    int32_t tiles, chunks, tile_lanes, tile_warps1, tile_warps2, tile_ring;
+    int64_t tile_stream_bytes, tile_segments;
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */
@@ -411,11 +437,22 @@ suppy_status suppy_dvc_proximity(suppy_ctx* ctx, double* out);
  * below is bracketed by CUDA events on the context's stream.
  * suppy_kernel_time(kind) returns the summed event time (ms) and the launch
  * count since timing was enabled, and synchronizes.  kind: 0 the row pass
- * (the fused one-pass sweep, or the row pass of the two-pass sweep); 1 the
+ * (the fused one-pass sweep, the row pass of the two-pass sweep, or the whole
+ * tiled sweep); 1 the
  * box step (finalize kernel, or the column pass of the two-pass sweep); 2 the
  * perturbation phase; 3 the CQ step of a split problem (all its launches). */
 suppy_status suppy_timing_enable(suppy_ctx* ctx, int32_t enable);
 suppy_status suppy_kernel_time(suppy_ctx* ctx, int32_t kind, double* total_ms, int64_t* launches);
+
+/* Budget of every bounded device-side wait of this context's kernels (ring
+ * stages of the streamed passes, chunk counters of the tiled sweep, grid
+ * barriers of the whole-GPU perturbation phase), in SM clock cycles; 0
+ * restores the default (4e9 cycles, about two seconds).  A wait that runs out
+ * makes its kernel stop and the next synchronizing call return SUPPY_ETIMEOUT,
+ * after which the context's synchronisation words are reset and the context
+ * stays usable.  A diagnostic knob (no paper counterpart): a short budget lets
+ * a test exercise that path.  Negative values give SUPPY_EINVAL. */
+suppy_status suppy_set_wait_limit(suppy_ctx* ctx, int64_t cycles);
 
 /* One simultaneous sweep on caller-provided device buffers, allocating
  * nothing.  The paper has no counterpart: this is an integration entry point

@@ -25,7 +25,7 @@ SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2
 SUPPY_CIMMINO, SUPPY_BIP, SUPPY_DROP, SUPPY_EL, SUPPY_EMR = 0, 1, 2, 3, 4
 SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
 SUPPY_OBJ_L1, SUPPY_OBJ_L2 = 4, 5
-STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS = 0, 1, 2
+STRATEGY_AUTO, STRATEGY_ONE_PASS, STRATEGY_TWO_PASS, STRATEGY_TILED = 0, 1, 2, 3
 SUPPY_DVC_UPPER, SUPPY_DVC_LOWER = 0, 1
 
 EXPORTED = [
@@ -38,7 +38,7 @@ EXPORTED = [
     "suppy_server_create", "suppy_server_destroy", "suppy_server_add_matrix",
     "suppy_server_submit", "suppy_server_step", "suppy_server_query", "suppy_server_clock",
     "suppy_server_device_bytes", "suppy_server_last_error", "suppy_set_dvc", "suppy_dvc_dose",
-    "suppy_dvc_proximity",
+    "suppy_dvc_proximity", "suppy_set_wait_limit",
 ]
 
 
@@ -57,7 +57,9 @@ class suppy_opts(ctypes.Structure):
                 ("strategy", ctypes.c_int32), ("tma", ctypes.c_int32),
                 ("stream_tile", ctypes.c_int32), ("stream_stages", ctypes.c_int32),
                 ("stream_lanes", ctypes.c_int32), ("perturb_path", ctypes.c_int32),
-                ("stream_map", ctypes.c_int32)]
+                ("stream_map", ctypes.c_int32), ("tile_lanes", ctypes.c_int32),
+                ("tile_warps1", ctypes.c_int32), ("tile_chunk_bytes", ctypes.c_int32),
+                ("tile_ring_bytes", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -109,7 +111,11 @@ class suppy_info(ctypes.Structure):
                 ("tma", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("stages", ctypes.c_int32), ("col_tile", ctypes.c_int32),
                 ("col_stages", ctypes.c_int32), ("map", ctypes.c_int32),
-                ("col_map", ctypes.c_int32)]
+                ("col_map", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("chunks", ctypes.c_int32), ("tile_lanes", ctypes.c_int32),
+                ("tile_warps1", ctypes.c_int32), ("tile_warps2", ctypes.c_int32),
+                ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
+                ("tile_segments", ctypes.c_int64)]
 
 
 _lib = None
@@ -167,6 +173,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                          ctypes.POINTER(suppy_dvc), I32, D]),
         "suppy_dvc_dose": (ctypes.c_int, [P, P, I32]),
         "suppy_dvc_proximity": (ctypes.c_int, [P, ctypes.POINTER(D)]),
+        "suppy_set_wait_limit": (ctypes.c_int, [P, I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,7 +246,8 @@ class Context:
     def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
                  c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None,
-                 stream_shape=(0, 0, 0), perturb_path=0, stream_map=0):
+                 stream_shape=(0, 0, 0), perturb_path=0, stream_map=0, tile_lanes=0,
+                 tile_warps1=0, tile_chunk_bytes=0, tile_ring_bytes=0):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -277,6 +285,10 @@ class Context:
         o.stream_tile, o.stream_stages, o.stream_lanes = (int(v) for v in stream_shape)
         o.perturb_path = int(perturb_path)
         o.stream_map = int(stream_map)
+        o.tile_lanes = int(tile_lanes)
+        o.tile_warps1 = int(tile_warps1)
+        o.tile_chunk_bytes = int(tile_chunk_bytes)
+        o.tile_ring_bytes = int(tile_ring_bytes)
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
@@ -426,6 +438,10 @@ class Context:
         _check(self._lib.suppy_info_get(self.ctx, ctypes.byref(inf)), self.ctx)
         return {k: getattr(inf, k) for k, _ in suppy_info._fields_}
 
+    def suppy_set_wait_limit(self, cycles: int = 0):
+        """Budget of every bounded device wait in SM cycles (0: the default)."""
+        _check(self._lib.suppy_set_wait_limit(self.ctx, int(cycles)), self.ctx)
+
     def suppy_timing_enable(self, enable: bool = True):
         _check(self._lib.suppy_timing_enable(self.ctx, int(enable)), self.ctx)
 
@@ -443,7 +459,8 @@ class Context:
 
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
                  stream=None, tune=0, strategy=0, tma=0, stream_shape=(0, 0, 0),
-                 perturb_path=0, stream_map=0) -> Context:
+                 perturb_path=0, stream_map=0, tile_lanes=0, tile_warps1=0,
+                 tile_chunk_bytes=0, tile_ring_bytes=0) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -455,7 +472,9 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
         arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
     rp, col, val, l, u, lo, hi = arrs
     kw = {}
-    if obj in (SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO):
+    # the image grid: required by the TV objectives, and where the tiled
+    # sweep cuts its tiles with any objective
+    if prob.shape is not None and len(prob.shape) == 2:
         kw["shape"] = prob.shape
     if obj == SUPPY_OBJ_LINEAR:
         if prob.body is not None:
@@ -467,7 +486,9 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
                    block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
                    strategy=strategy, tma=tma, stream_shape=stream_shape,
-                   perturb_path=perturb_path, stream_map=stream_map, **kw)
+                   perturb_path=perturb_path, stream_map=stream_map, tile_lanes=tile_lanes,
+                   tile_warps1=tile_warps1, tile_chunk_bytes=tile_chunk_bytes,
+                   tile_ring_bytes=tile_ring_bytes, **kw)
 
 
 def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,

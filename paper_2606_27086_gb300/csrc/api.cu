@@ -53,6 +53,7 @@ struct suppy_ctx {
     suppy_mode mode = SUPPY_CIMMINO;
     suppy_obj obj = SUPPY_OBJ_NONE;
     int H = 0, W = 0;
+    int gH = 1, gW = 1;             // grid of the unknowns (image rows x columns, or 1 x n)
     int box_len = 1;
     int nseg = 1;
     std::vector<int> seg_start;     // device-order row ranges of the segments (blocks)
@@ -118,8 +119,27 @@ struct suppy_ctx {
     long long nnz_csc = 0;
     long long csc_len = 0;          // storage length of the CSC copy (columns padded to 4)
 
+    // tiled one-pass sweep (strategy 3): tile streams, tables, accumulators
+    unsigned char* d_tstream = nullptr;
+    long long* d_tbase = nullptr;
+    int* d_tcoff = nullptr;
+    int* d_tnseg = nullptr;
+    int4* d_trect = nullptr;
+    int* d_tcblk = nullptr;
+    double* d_tscale = nullptr;
+    float* d_tr = nullptr;          // 2 x m
+    unsigned* d_tcnt = nullptr;     // chunk counters
+    unsigned* d_tsync = nullptr;    // {CTAs finished, epoch}
+    double* d_tpp = nullptr;
+    int tiP = 0, tiK = 0, ticap = 0, timaxchunk = 0;
+    int tiG = 8, tiW1 = 12, tiW2 = 19;    // lanes per segment, warps of the two phases
+    int tipiece = 8192, tistages = 0;     // ring: bytes per copy, stages
+    size_t tismem = 0;
+    long long tibytes = 0;                // bytes of the tile streams
+    long long tisegs = 0;                 // segments
+
     // launch shapes
-    int strategy = 1;               // 1 one pass, 2 two passes
+    int strategy = 1;               // 1 one pass, 2 two passes, 3 tiled one pass
     int scat = 1;                   // one pass: 1 L2 reductions, 2 shared-memory staged
     int G = 32, maxe = 8;
     int grid_sweep = 0, groups = 0;             // largest row-pass launch
@@ -138,6 +158,7 @@ struct suppy_ctx {
     int* d_tpart = nullptr;
     int* d_ctpart = nullptr;
     int* d_err = nullptr;           // set by a kernel whose bounded wait gave up
+    long long wait_cycles = kDefaultWaitCycles;   // budget of one bounded device wait
     unsigned* d_cticket = nullptr;  // streamed column pass: CTAs finished (fused epilogue)
     int grid_fin = 0;
     int grid_obj = 0;
@@ -239,6 +260,16 @@ void dfree(suppy_ctx* c, void* p) {
         c->allocs.erase(it);
     }
     cudaFree(p);
+}
+
+// Copy a host vector into a new library-owned device buffer (enqueued).
+template <typename T>
+suppy_status upload(suppy_ctx* c, const std::vector<T>& v, T** out) {
+    suppy_status s = dalloc(c, out, v.size());
+    if (s != SUPPY_OK) return s;
+    if (!v.empty())
+        CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+    return SUPPY_OK;
 }
 
 // Copy count elements from a host or device pointer into a new device buffer
@@ -487,6 +518,7 @@ suppy_status enqueue_ext_step(suppy_ctx* c, const suppy_params* p, int t, int np
             q.tile = c->tile;
             q.stages = c->stages;
             q.err = c->d_err;
+            q.wait_cycles = c->wait_cycles;
             q.l = c->d_zero;
             q.u = c->d_zero;
             q.wr = c->d_wr;
@@ -584,10 +616,66 @@ suppy_status enqueue_cq_step(suppy_ctx* c) {
     return SUPPY_OK;
 }
 
+// The tiled one-pass sweep: every block in one cooperative launch whose last
+// CTA runs the epilogue (the proximity terms arrive scaled per block).
+suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopParams& sp) {
+    TileArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.stream = c->d_tstream;
+    a.base = c->d_tbase;
+    a.coff = c->d_tcoff;
+    a.nseg = c->d_tnseg;
+    a.rect = c->d_trect;
+    a.chunk_blk = c->d_tcblk;
+    a.blk_scale = c->d_tscale;
+    a.K = c->tiK;
+    a.W = c->gW;
+    a.piece = c->tipiece;
+    a.stages = c->tistages;
+    a.tile_cap = c->ticap;
+    a.W1 = c->tiW1;
+    a.W2 = c->tiW2;
+    a.l = c->d_l;
+    a.u = c->d_u;
+    a.wr = c->d_wr;
+    a.x = c->d_x;
+    a.lo = c->d_lo;
+    a.hi = c->d_hi;
+    a.zc = c->d_zc;
+    a.box_len = c->box_len;
+    a.m = c->m;
+    a.r = c->d_tr;
+    a.cnt = c->d_tcnt;
+    a.sync = c->d_tsync;
+    a.pp = c->d_tpp;
+    a.st = c->d_st;
+    a.err = c->d_err;
+    a.wait_cycles = c->wait_cycles;
+    a.lam = (float)p->lambda;
+    EpiArgs e = epi_args(c, c->nseg - 1, sp);
+    e.pp = c->d_tpp;
+    e.npp = c->tiP;
+    e.scale = 1.0;
+    e.first_seg = 1;
+    e.last_seg = 1;
+    a.epi = e;
+    {
+        Timed tm{c, 0};
+        CK(tm.begin());
+        CK(launch_tile_sweep(a, c->dt, c->tiG, c->tiP, c->tismem, c->stream));
+        CK(tm.end());
+        note_launch(c);
+    }
+    c->k_upper += 1;
+    if (c->evs.size() > 8192) return flush_timing(c);
+    return SUPPY_OK;
+}
+
 suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     const StopParams sp = stop_params(c, p);
     suppy_status s;
     if (c->dvc_on && (s = enqueue_cq_step(c)) != SUPPY_OK) return s;
+    if (c->strategy == 3) return enqueue_tile_sweep(c, p, sp);
     // EL / EMR: the row pass writes unrelaxed coefficients, the column pass
     // accumulates A^T(.) into delta, and the extrapolated step applies it
     const bool ext = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
@@ -606,6 +694,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             sa.tile = c->tile;
             sa.stages = c->stages;
             sa.err = c->d_err;
+            sa.wait_cycles = c->wait_cycles;
             sa.l = c->d_l;
             sa.u = c->d_u;
             sa.wr = c->d_wr;
@@ -637,6 +726,7 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 ca.tile = c->ctile;
                 ca.stages = c->cstages;
                 ca.err = c->d_err;
+                ca.wait_cycles = c->wait_cycles;
                 ca.coef_in = c->d_coef;
                 ca.xw = c->d_x;
                 ca.lo = c->d_lo;
@@ -771,6 +861,7 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.part = c->d_wpart;
     a.ticket = c->d_ticket;
     a.err = c->d_err;
+    a.wait_cycles = c->wait_cycles;
     Timed tm{c, 2};
     CK(tm.begin());
     if (c->wide && !record_only) {
@@ -807,6 +898,8 @@ suppy_status enqueue_err_copy(suppy_ctx* c) {
     return SUPPY_OK;
 }
 
+suppy_status reset_sync_words(suppy_ctx* c);
+
 suppy_status err_after_sync(suppy_ctx* c) {
     if (c->bounds_pending) {
         // the checks of enqueued bounds updates (suppy_update_bounds_async)
@@ -819,7 +912,9 @@ suppy_status err_after_sync(suppy_ctx* c) {
     if (!c->d_err || !*c->h_err) return SUPPY_OK;
     *c->h_err = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass or whole-GPU perturbation barrier)");
+    suppy_status rs = reset_sync_words(c);
+    if (rs != SUPPY_OK) return rs;
+    return fail(c, SUPPY_ETIMEOUT, "a bounded device-side wait gave up (streaming pass, tiled sweep or whole-GPU perturbation barrier)");
 }
 
 
@@ -854,7 +949,7 @@ void choose_row_shape(suppy_ctx* c, double mean_len, int max_len) {
     else if (mean_len >= 20) c->G = 8;
     else c->G = 4;
     const int need = (max_len + c->G - 1) / c->G;
-    if (c->strategy == 2 || c->G == 4) c->maxe = 8;   // no scatter: registers only buffer loads
+    if (c->strategy >= 2 || c->G == 4) c->maxe = 8;   // no scatter: registers only buffer loads
     else c->maxe = need <= 8 ? 8 : 16;
 }
 
@@ -1199,6 +1294,159 @@ void free_csc(suppy_ctx* c) {
     c->cpref.shrink_to_fit();
 }
 
+// Tiled one-pass sweep: plan the tiles and the chunked segment streams on the
+// host (entries per column give nnz-balanced tiles; one CTA per SM), upload
+// the tables, fill the streams on the device from the packed row copy, and
+// size the ring to the shared memory left beside the tile's x and Delta.
+void free_tile(suppy_ctx* c) {
+    for (void* p : {(void*)c->d_tstream, (void*)c->d_tbase, (void*)c->d_tcoff, (void*)c->d_tnseg,
+                    (void*)c->d_trect, (void*)c->d_tcblk, (void*)c->d_tscale, (void*)c->d_tr,
+                    (void*)c->d_tcnt, (void*)c->d_tsync, (void*)c->d_tpp})
+        if (p) dfree(c, p);
+    c->d_tstream = nullptr;
+    c->d_tbase = nullptr;
+    c->d_tcoff = nullptr;
+    c->d_tnseg = nullptr;
+    c->d_trect = nullptr;
+    c->d_tcblk = nullptr;
+    c->d_tscale = nullptr;
+    c->d_tr = nullptr;
+    c->d_tcnt = nullptr;
+    c->d_tsync = nullptr;
+    c->d_tpp = nullptr;
+    c->tiP = c->tiK = 0;
+}
+
+constexpr int kTileThreadsTotal = 1024;          // warps of a tiled-sweep CTA: 1 + W1 + W2
+constexpr long long kTileMaxWords = 6144;        // unknowns of one tile (x and Delta in shared memory)
+constexpr int kTileSmemMax = 227 * 1024;         // dynamic shared memory of one CTA
+constexpr int kTileStaticSmem = 2048;            // the kernel's static shared memory, rounded up
+
+// Why the tiled sweep cannot serve this context, or "" when it can.
+std::string tile_ineligible(const suppy_ctx* c) {
+    if (c->B != 1) return "the tiled sweep serves one right-hand side";
+    if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP)
+        return "the tiled sweep serves Cimmino, BIP and DROP sweeps";
+    if (c->nnz == 0) return "the tiled sweep needs a nonempty matrix";
+    return "";
+}
+
+suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hcol,
+                        const std::vector<int>& perm, const std::vector<int2>& rinfo,
+                        int ring_req, int chunk_req, bool* ok) {
+    *ok = false;
+    free_tile(c);
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    // ring: pieces of 8 KB, up to 24 of them (a caller-fixed ring is eight
+    // pieces); the largest chunk of one tile is at most half the ring less a
+    // piece, so two of them and a piece in flight fit
+    int piece = 8192, want_stages = 24;
+    if (ring_req) {
+        piece = ring_req / 8;
+        want_stages = 8;
+    }
+    const int vbytes = (c->dt == SUPPY_F32) ? 4 : 2;
+    const long long max_chunk = (long long)(want_stages - 1) * piece / 2;
+    TilePlanIn in;
+    in.m = c->m;
+    in.n = c->n;
+    in.H = c->gH;
+    in.W = c->gW;
+    in.P = sms;
+    in.vbytes = vbytes;
+    in.perm = perm.empty() ? nullptr : perm.data();
+    in.rp = rp.data();
+    in.col = hcol;
+    std::vector<int> rstart(c->m);
+    for (int i = 0; i < c->m; ++i) rstart[i] = rinfo[i].x;
+    in.row_start = rstart.data();
+    in.seg_start = c->seg_start;
+    in.max_chunk = std::min<long long>(40 * 1024, max_chunk);
+    in.chunk_target = chunk_req ? chunk_req : std::min<long long>(16 * 1024, in.max_chunk / 2);
+    in.max_chunks = kTileMaxChunks;
+    // a segment, its descriptor and padding fit well inside one chunk
+    in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 2 - 32) / (vbytes + 2)));
+    in.max_tile_words = kTileMaxWords;
+    TilePlan plan;
+    std::string why;
+    if (!plan_tiles(in, plan, why)) {
+        c->err = why;
+        return SUPPY_OK;   // not eligible: the caller keeps another strategy
+    }
+    // the ring takes the shared memory the tables and tiles leave
+    const size_t fixed = tile_smem_bytes(0, plan.tile_cap, plan.K, kTileMaxStages) + kTileStaticSmem;
+    if (fixed >= (size_t)kTileSmemMax) {
+        c->err = "tiled sweep: tiles and tables leave no room for the ring";
+        return SUPPY_OK;
+    }
+    const int stages = std::min<int>(want_stages, (int)((kTileSmemMax - fixed) / piece));
+    if (stages < 4 || (long long)(stages - 1) * piece < 2LL * plan.max_chunk) {
+        c->err = "tiled sweep: the ring cannot hold two of the largest chunks";
+        return SUPPY_OK;
+    }
+    c->tipiece = piece;
+    c->tistages = stages;
+    c->tiP = plan.P;
+    c->tiK = plan.K;
+    c->ticap = plan.tile_cap;
+    c->timaxchunk = plan.max_chunk;
+    c->tibytes = plan.bytes;
+    c->tisegs = (long long)plan.segs.size();
+    c->tismem = tile_smem_bytes(c->tistages * c->tipiece, plan.tile_cap, plan.K, c->tistages);
+    const int threads = 32 * (1 + c->tiW1 + c->tiW2);
+    if (tile_blocks_per_sm(c->dt, c->tiG, threads, c->tismem) < 1) {
+        c->err = "tiled sweep: one CTA per SM is not resident";
+        return SUPPY_OK;
+    }
+    suppy_status s;
+    const int P = plan.P, K = plan.K;
+    if ((s = dalloc(c, &c->d_tstream, (size_t)plan.bytes + 16)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_tstream, 0, (size_t)plan.bytes + 16, c->stream));
+    if ((s = upload(c, plan.base, &c->d_tbase)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.coff, &c->d_tcoff)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.nseg, &c->d_tnseg)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.rect, &c->d_trect)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.chunk_blk, &c->d_tcblk)) != SUPPY_OK) return s;
+    std::vector<double> scale(c->nseg);
+    for (int t = 0; t < c->nseg; ++t) scale[t] = seg_scale(c, t);
+    if ((s = upload(c, scale, &c->d_tscale)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_tr, (size_t)2 * c->m)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_tr, 0, sizeof(float) * 2 * (size_t)c->m, c->stream));
+    if ((s = dalloc(c, &c->d_tcnt, (size_t)K)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_tcnt, 0, sizeof(unsigned) * K, c->stream));
+    if ((s = dalloc(c, &c->d_tsync, 2)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_tsync, 0, sizeof(unsigned) * 2, c->stream));
+    if ((s = dalloc(c, &c->d_tpp, (size_t)P)) != SUPPY_OK) return s;
+    // the streams: segment records and the local column map, then the fill
+    TileSegRec* d_segs = nullptr;
+    unsigned short* d_local = nullptr;
+    if ((s = upload(c, plan.segs, &d_segs)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.local_of, &d_local)) != SUPPY_OK) return s;
+    CK(launch_tile_fill(d_segs, (long long)plan.segs.size(), c->d_val, c->dt, c->d_col, d_local,
+                        c->d_tstream, c->stream));
+    note_launch(c);
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, d_segs);
+    dfree(c, d_local);
+    *ok = true;
+    c->err.clear();
+    return SUPPY_OK;
+}
+
+// Clears the synchronisation words of the grid-wide kernels (tickets, chunk
+// counters) after a bounded wait gave up: a CTA that left early may have left
+// a count behind.
+suppy_status reset_sync_words(suppy_ctx* c) {
+    if (c->d_ticket) CK(cudaMemsetAsync(c->d_ticket, 0, 2 * sizeof(unsigned), c->stream));
+    if (c->d_cticket) CK(cudaMemsetAsync(c->d_cticket, 0, sizeof(unsigned), c->stream));
+    if (c->d_xticket) CK(cudaMemsetAsync(c->d_xticket, 0, sizeof(unsigned), c->stream));
+    if (c->d_vticket) CK(cudaMemsetAsync(c->d_vticket, 0, sizeof(unsigned), c->stream));
+    if (c->d_tcnt) CK(cudaMemsetAsync(c->d_tcnt, 0, sizeof(unsigned) * c->tiK, c->stream));
+    if (c->d_tsync) CK(cudaMemsetAsync(c->d_tsync, 0, sizeof(unsigned), c->stream));
+    return SUPPY_OK;
+}
+
 // Time a few sweeps of the current configuration on a scratch copy of the
 // iterate and state (restored afterwards).
 suppy_status time_config(suppy_ctx* c, float* ms_out) {
@@ -1248,6 +1496,7 @@ suppy_status time_config(suppy_ctx* c, float* ms_out) {
 bool tma_eligible(const suppy_ctx* c, int want) {
     if (want < 0) return false;                 // disabled by the caller
     if (c->B != 1) return false;
+    if (c->strategy == 3) return false;         // the tiled sweep streams its own layout
     if (c->strategy == 1 && c->scat != 1) return false;
     if (c->max_row > stream_max_item(c->tile, c->stages)) return false;
     if (c->strategy == 2 && c->max_col > stream_max_item(c->ctile, c->cstages)) return false;
@@ -1353,6 +1602,14 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_stages must be 0 or 2.. the shared-memory budget");
         if (o->stream_map < 0 || o->stream_map > 2)
             return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
+        if (o->tile_lanes != 0 && o->tile_lanes != 8 && o->tile_lanes != 16 && o->tile_lanes != 32)
+            return fail(c, SUPPY_EINVAL, "tile_lanes must be 0, 8, 16 or 32");
+        if (o->tile_warps1 < 0 || o->tile_warps1 > 30)
+            return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..30");
+        const int rb = o->tile_ring_bytes;
+        if (rb != 0 && (rb % 8 != 0 || (rb / 8) < 256 || (rb / 8) > 8192 || ((rb / 8) & (rb / 8 - 1))))
+            return fail(c, SUPPY_EINVAL, "tile_ring_bytes must be 0 or 8 x a power of two in [256, 8192]");
+        if (o->tile_chunk_bytes < 0) return fail(c, SUPPY_EINVAL, "tile_chunk_bytes must be >= 0");
     }
     c->B = 1;
     if (c->B_user > 1) {
@@ -1370,6 +1627,17 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     } else {
         c->H = 1;
         c->W = A->n;
+    }
+    // grid of the unknowns for the tiled sweep: the image when given (with
+    // any objective), else one row of n
+    if (o->img_h != 0 || o->img_w != 0) {
+        if (o->img_h < 1 || o->img_w < 1 || (long long)o->img_h * o->img_w != A->n)
+            return fail(c, SUPPY_EINVAL, "img_h * img_w must equal n when given");
+        c->gH = o->img_h;
+        c->gW = o->img_w;
+    } else {
+        c->gH = 1;
+        c->gW = A->n;
     }
     if (c->obj == SUPPY_OBJ_LINEAR && !o->c_lin && !o->obj_rows)
         return fail(c, SUPPY_EINVAL, "linear objective needs c_lin or obj_rows");
@@ -1651,31 +1919,55 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     // their buffers exist before any timed candidate sweep
     const bool ext_mode = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
     if (ext_mode && (s = prepare_ext(c)) != SUPPY_OK) return s;
+    if (ext_mode && o->strategy == 3)
+        return fail(c, SUPPY_EINVAL, "the tiled sweep serves Cimmino, BIP and DROP sweeps");
     const int want = ext_mode ? 2 : o->strategy;
-    if (want < 0 || want > 2) return fail(c, SUPPY_EINVAL, "unknown strategy");
+    if (want < 0 || want > 3) return fail(c, SUPPY_EINVAL, "unknown strategy");
+    const std::string tile_why = tile_ineligible(c);
+    if (want == 3 && !tile_why.empty()) return fail(c, SUPPY_EINVAL, tile_why);
     const bool need_csc = (want == 2) || (want == 0 && (o->tune || !smem_ok));
+    const bool tile_cand = tile_why.empty() && (want == 3 || (want == 0 && o->tune));
+    std::vector<int> hcol_buf;
+    const int* hcol = A->col;
+    if ((need_csc || tile_cand) && on_dev) {
+        hcol_buf.resize((size_t)std::max<long long>(A->nnz, 1));
+        if (A->nnz)
+            CK(cudaMemcpyAsync(hcol_buf.data(), A->col, sizeof(int) * A->nnz, cudaMemcpyDeviceToHost,
+                               c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        hcol = hcol_buf.data();
+    }
     if (need_csc) {
-        std::vector<int> hcol_buf;
-        const int* hcol = A->col;
-        if (on_dev) {
-            hcol_buf.resize((size_t)std::max<long long>(A->nnz, 1));
-            if (A->nnz)
-                CK(cudaMemcpyAsync(hcol_buf.data(), A->col, sizeof(int) * A->nnz,
-                                   cudaMemcpyDeviceToHost, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
-            hcol = hcol_buf.data();
-        }
         if ((s = build_csc(c, rp, hcol, perm, seg_of_row, rinfo)) != SUPPY_OK) return s;
         choose_col_shape(c, mean_col);
         if ((s = build_col_partition(c)) != SUPPY_OK) return s;
     }
+    bool tile_ok = false;
+    if (tile_cand) {
+        c->tiG = o->tile_lanes ? o->tile_lanes : 8;
+        if (o->tile_warps1) {
+            c->tiW1 = o->tile_warps1;
+            c->tiW2 = kTileThreadsTotal / 32 - 1 - c->tiW1;
+        }
+        if ((s = build_tile(c, rp, hcol, perm, rinfo, o->tile_ring_bytes, o->tile_chunk_bytes,
+                            &tile_ok)) != SUPPY_OK)
+            return s;
+        if (want == 3 && !tile_ok) return fail(c, SUPPY_EINVAL, c->err);
+    }
+    hcol_buf.clear();
+    hcol_buf.shrink_to_fit();
     struct Cand {
         int strategy, scat;
     };
     std::vector<Cand> cands;
-    if (want != 2) cands.push_back({1, smem_ok ? 2 : 1});
-    if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1});
-    if (need_csc) cands.push_back({2, 0});
+    if (want == 3) {
+        cands.push_back({3, 0});
+    } else {
+        if (want != 2) cands.push_back({1, smem_ok ? 2 : 1});
+        if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1});
+        if (need_csc) cands.push_back({2, 0});
+        if (tile_ok) cands.push_back({3, 0});
+    }
     Cand best = cands[0];
     if (want == 0 && !o->tune) best = smem_ok ? Cand{1, 2} : Cand{2, 0};
     const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
@@ -1749,6 +2041,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         return s;
     }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
+    if (c->strategy != 3 && c->d_tstream) free_tile(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
     CK(cudaStreamSynchronize(c->stream));
@@ -2125,15 +2418,6 @@ suppy_status to_host(suppy_ctx* c, const T* src, size_t count, int on_device, st
     if (!src) return fail(c, SUPPY_EINVAL, "a DVC matrix array is NULL");
     if (on_device) CK(cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost));
     else std::memcpy(out.data(), src, count * sizeof(T));
-    return SUPPY_OK;
-}
-
-template <typename T>
-suppy_status upload(suppy_ctx* c, const std::vector<T>& v, T** out) {
-    suppy_status s = dalloc(c, out, v.size());
-    if (s != SUPPY_OK) return s;
-    if (!v.empty())
-        CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     return SUPPY_OK;
 }
 
@@ -2578,6 +2862,14 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->stages = c->use_tma ? c->stages : 0;
     out->col_tile = (c->use_tma && c->strategy == 2) ? c->ctile : 0;
     out->col_stages = (c->use_tma && c->strategy == 2) ? c->cstages : 0;
+    out->tiles = c->strategy == 3 ? c->tiP : 0;
+    out->chunks = c->strategy == 3 ? c->tiK : 0;
+    out->tile_lanes = c->strategy == 3 ? c->tiG : 0;
+    out->tile_warps1 = c->strategy == 3 ? c->tiW1 : 0;
+    out->tile_warps2 = c->strategy == 3 ? c->tiW2 : 0;
+    out->tile_ring = c->strategy == 3 ? c->tistages * c->tipiece : 0;
+    out->tile_stream_bytes = c->strategy == 3 ? c->tibytes : 0;
+    out->tile_segments = c->strategy == 3 ? c->tisegs : 0;
     out->map = c->use_tma ? c->tMap + 1 : 0;
     out->col_map = (c->use_tma && c->strategy == 2) ? c->tMapc + 1 : 0;
     if (c->use_tma) {
@@ -2588,6 +2880,19 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
             out->col_grid = c->seg_ctgrid[0];
             out->col_lanes = c->tGc;
         }
+    }
+    return SUPPY_OK;
+}
+
+suppy_status suppy_set_wait_limit(suppy_ctx* c, int64_t cycles) {
+    if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
+    if (cycles < 0) return fail(c, SUPPY_EINVAL, "the wait limit must be >= 0");
+    c->wait_cycles = cycles ? (long long)cycles : kDefaultWaitCycles;
+    // a captured iteration holds the old budget in its launch arguments
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_key.clear();
     }
     return SUPPY_OK;
 }

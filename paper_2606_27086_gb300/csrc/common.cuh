@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "suppy.h"
 
@@ -17,6 +18,8 @@ constexpr int kSweepThreads = 256;     // threads per CTA of the sweep kernels
 constexpr int kFinalizeThreads = 256;
 constexpr int kPerturbThreads = 512;   // threads per CTA of the perturbation cluster
 constexpr int kMaxRhs = 32;
+// Default budget of one bounded device-side wait: about two seconds of SM clock.
+constexpr long long kDefaultWaitCycles = 4000000000LL;
 
 // Per right-hand-side iteration state, resident on the device so that the
 // perturbation, sweep and stopping logic never wait for the host.
@@ -138,6 +141,7 @@ struct PerturbArgs {
     double* part;           // whole-GPU kernel: per-CTA partials (two buffers)
     unsigned* ticket;       // whole-GPU kernel: grid barrier {arrivals, generation}
     int* err;               // whole-GPU kernel: error word (2: a barrier timed out)
+    long long wait_cycles;  // whole-GPU kernel: budget of one barrier wait (SM clock cycles)
 };
 
 // Threads per CTA of the whole-GPU reduction kernels (variance rule), of the
@@ -167,6 +171,7 @@ struct StreamArgs {
     int tile;               // ring stage length in elements (power of two)
     int stages;             // ring stages (2..32)
     int* err;               // set to 1 when a bounded wait gives up
+    long long wait_cycles;  // budget of one bounded wait (SM clock cycles)
     // row pass
     const float* l;
     const float* u;
@@ -192,6 +197,95 @@ struct StreamArgs {
     unsigned* ticket;       // column pass of the last block: CTAs finished (the
                             // last one runs the sweep epilogue), or null
 };
+
+// Tiled one-pass sweep (tile.cu): one cooperative launch of P CTAs, CTA b
+// owning tile b of the unknowns (x and the correction in shared memory) and
+// streaming tile b's segments of A once per sweep.  A CTA is one producer
+// warp, W1 warps of dot products (phase 1) and W2 warps of corrections
+// (phase 2).
+constexpr int kTileMaxWarps = 32;
+constexpr int kTileMaxStages = 64;
+constexpr int kTileMaxChunks = 2048;
+struct TileArgs {
+    const unsigned char* stream;   // every tile's byte stream
+    const long long* base;         // P: start of tile b's stream (16-byte aligned)
+    const int* coff;               // P x (K + 1): chunk byte offsets in the tile's stream
+    const int* nseg;               // P x K: segments of tile b in chunk k
+    const int4* rect;              // P: {first global column, rows, columns, local row stride}
+    const int* chunk_blk;          // K: block of chunk k (chunks of a block are consecutive)
+    const double* blk_scale;       // blocks: factor of the block's proximity terms
+    int K;                         // chunks
+    int W;                         // global column stride of a tile row (image width)
+    int piece;                     // bytes per bulk copy (power of two)
+    int stages;                    // ring stages of `piece` bytes
+    int tile_cap;                  // words of the shared-memory x and Delta tiles
+    int W1, W2;                    // phase-1 / phase-2 warps
+    const float* l;                // m bounds (device row order)
+    const float* u;
+    const float* wr;               // w_i / ||a_i||^2
+    float* x;                      // n
+    const float* lo;
+    const float* hi;
+    const float* zc;               // DROP column scaling or null
+    int box_len;
+    int m;
+    float* r;                      // 2 x m: <a_i, x> accumulators of alternate sweeps
+    unsigned* cnt;                 // K: phase-1 arrivals per chunk (zero between sweeps)
+    unsigned* sync;                // {CTAs finished, epoch}
+    double* pp;                    // P: proximity partials
+    RhsState* st;
+    int* err;                      // error word (3: a bounded wait gave up)
+    long long wait_cycles;         // budget of one bounded wait
+    float lam;
+    EpiArgs epi;
+};
+
+// One segment of the tile streams (host plan -> device fill).
+struct TileSegRec {
+    long long chunk_start;         // byte offset of the segment's chunk in the stream buffer
+    int sidx;                      // descriptor index inside the chunk
+    int off4;                      // data offset inside the chunk, in 4-byte words
+    int row_flag;                  // device row; bit 31: the row's first segment
+    int e0;                        // first entry in the packed row copy
+    int len;                       // entries
+    int pad;
+};
+
+struct TilePlanIn {
+    int m, n, H, W;                // rows, unknowns, image rows and columns (H W = n)
+    int P;                         // CTAs (tiles) wanted
+    int vbytes;                    // bytes per stored value
+    const int* perm;               // device row -> source row, or null
+    const int* rp;                 // source row pointer (host)
+    const int* col;                // source column indices (host)
+    const int* row_start;          // device row -> first entry in the packed copy
+    std::vector<int> seg_start;    // block row ranges (device order)
+    long long chunk_target;        // stream bytes per CTA and chunk aimed at
+    long long max_chunk;           // largest chunk of one tile the ring may hold
+    int max_chunks;                // chunks the kernel's tables hold
+    int max_seg;                   // longest segment (entries)
+    long long max_tile_words;      // shared-memory words of one tile
+};
+
+struct TilePlan {
+    int P = 0, K = 0, tile_cap = 0, max_chunk = 0;
+    long long bytes = 0;
+    std::vector<long long> base;
+    std::vector<int> coff, nseg, chunk_blk;
+    std::vector<int4> rect;
+    std::vector<int> tile_of;
+    std::vector<unsigned short> local_of;
+    std::vector<TileSegRec> segs;
+};
+
+bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why);
+size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages);
+int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem);
+cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid, size_t smem,
+                              cudaStream_t s);
+cudaError_t launch_tile_fill(const TileSegRec* segs, long long nsegs, const void* val,
+                             suppy_dtype dt, const int* col, const unsigned short* local_of,
+                             unsigned char* stream, cudaStream_t s);
 
 // Extrapolated step of EL / EMR (sweep.cu): t_b from the sweep's reductions,
 // then x <- box(x + lambda t_b delta), delta <- 0.

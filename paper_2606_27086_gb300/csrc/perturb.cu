@@ -706,16 +706,16 @@ __device__ __forceinline__ void grid_sums(const double* part, int B, double* res
 // resets the count and advances the generation; the others wait, then read
 // gsum into res (shared memory).  One CTA does the FP64 reduction: FP64 is
 // scarce on GB300, and every CTA summing the partials itself took longer than
-// the wait.  The wait is bounded (about two seconds of SM clock): on timeout
-// the CTA records error word 2 and every CTA leaves at its next barrier.
+// the wait.  The wait is bounded: on timeout
+// the CTA records error word 2 and every CTA leaves at its next barrier.  The
+// budget is a launch argument (about two seconds of SM clock by default).
 // The partials need no second buffer: they are read before the release, and
 // written again only after it.
-constexpr long long kGridWaitCycles = 4000000000LL;
 constexpr int kFirstTrials = 2;
 
 template <int NV>
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const double* part,
-                                             double* gsum, double* res) {
+                                             double* gsum, double* res, long long limit) {
     __shared__ int st_s;   // bit 0: ok, bit 1: this CTA arrived last
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -729,7 +729,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, const doub
         } else {
             const long long t0 = clock64();
             while (*gen == g0) {
-                if (*(volatile int*)err || clock64() - t0 > kGridWaitCycles) {
+                if (*(volatile int*)err || clock64() - t0 > limit) {
                     atomicExch(err, 2);
                     ok = 0;
                     break;
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
                 FF v[2] = {ff_of(kg), lin ? ff_of(fl) : ff_of(kf)};
                 cta_partials<2, kPhaseThreads>(v, 1, sw, part);
             }
-            if (!grid_barrier<2>(a.ticket, a.err, part, gsum, res)) return;
+            if (!grid_barrier<2>(a.ticket, a.err, part, gsum, res, a.wait_cycles)) return;
             // the step's scalar decisions by one thread (FP64 is scarce on
             // GB300: not by every thread of the grid), shared through smem
             const double fy = res[1];
@@ -936,7 +936,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
                     for (int q = 0; q < kWideTrials; ++q) v[q] = lin ? ff_of(fz[q]) : ff_of(kz[q]);
                     cta_partials<kWideTrials, kPhaseThreads>(v, 1, sw, part, cnt);
                 }
-                if (!grid_barrier<kWideTrials>(a.ticket, a.err, part, gsum, res)) return;
+                if (!grid_barrier<kWideTrials>(a.ticket, a.err, part, gsum, res, a.wait_cycles)) return;
                 if (threadIdx.x == 0) {
                     int h = -1;
                     for (int q = 0; q < cnt; ++q)
@@ -965,7 +965,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
             }
             if (!ok) break;
             // the next reduction step reads the neighbours' new y
-            if (s + 1 < a.n_red && !grid_barrier<0>(a.ticket, a.err, part, gsum, res)) return;
+            if (s + 1 < a.n_red && !grid_barrier<0>(a.ticket, a.err, part, gsum, res, a.wait_cycles)) return;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) phase_end(a, st, ps, ell, accepted, trials, f_start);
     }

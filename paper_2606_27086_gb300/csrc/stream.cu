@@ -28,12 +28,13 @@
 //    coalesced L2 reductions (one-pass);
 //  * column pass: x_j <- clamp(x_j + sum_i a_ij coef_i, lo_j, hi_j).
 //
-// Every mbarrier wait is bounded (about two seconds of SM clock); on timeout
-// the CTA records an error word, stops, lets its copies in flight land and
-// returns.
+// Every mbarrier wait is bounded (the launch's cycle budget, about two seconds
+// of SM clock by default); on timeout the CTA records an error word, stops,
+// lets its copies in flight land and returns.
 #include <algorithm>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace suppy {
 
@@ -52,65 +53,15 @@ __device__ unsigned long long g_stream_stats[16];
 namespace {
 
 constexpr int kMaxStages = 32;
-constexpr long long kWaitCycles = 4000000000LL;
-constexpr uint32_t kSuspendNs = 2000;   // a waiting thread sleeps up to this long per try
+// Copies already in flight always get this long to land before a CTA that gave
+// up leaves (the launch's own wait budget may be shortened for diagnostics).
+constexpr long long kDrainCycles = 4000000000LL;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                         uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint "
-        "[%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
-        : "memory");
-}
+using tma::bulk_g2s;
+using tma::mbar_arrive;
+using tma::mbar_arrive_expect_tx;
+using tma::mbar_init;
+using tma::policy_evict_first;
 
 template <typename VT>
 __device__ __forceinline__ float to_f(VT v) { return (float)v; }
@@ -413,7 +364,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             (void)st_t0;
             for (int k = 0, s = 0, ph = 0; k < K; ++k) {
                 const long long tw = SSTAT_CLOCK();
-                if (k >= S && !mbar_wait(&empty[s], (ph - 1) & 1, &abort_flag)) {
+                if (k >= S && !tma::mbar_wait(&empty[s], (ph - 1) & 1, &abort_flag, a.wait_cycles)) {
                     abort_flag = 1;
                     atomicExch(a.err, 1);
                     break;
@@ -435,7 +386,7 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
                 // let the copies in flight land before the CTA leaves
                 volatile int never = 0;
                 for (int k = (issued > S ? issued - S : 0); k < issued; ++k)
-                    mbar_wait(&full[k % S], (k / S) & 1, &never);
+                    tma::mbar_wait(&full[k % S], (k / S) & 1, &never, kDrainCycles);
             }
         }
     } else {
@@ -450,11 +401,11 @@ __device__ double stream_items(const StreamArgs& a, Work& work) {
             if (stage_tile[s] != k) {
                 const long long t0 = clock64();
                 while (stage_tile[s] != k) {
-                    if (abort_flag || clock64() - t0 > kWaitCycles) return false;
+                    if (abort_flag || clock64() - t0 > a.wait_cycles) return false;
                     __nanosleep(64);
                 }
             }
-            return mbar_wait(&full[s], (k / S) & 1, &abort_flag);
+            return tma::mbar_wait(&full[s], (k / S) & 1, &abort_flag, a.wait_cycles);
         };
         const RingRelease rel{tile_done, empty, S, ts, lo_r, hi_r};
         auto grab = [&]() {
