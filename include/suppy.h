@@ -183,9 +183,11 @@ typedef struct {
      * item).  Other values give SUPPY_EINVAL. */
     int32_t stream_map;
     /* Tiled sweep (strategy 3): lanes per segment (0 automatic = 8, else 8,
-     * 16 or 32) and warps of its dot-product phase (0 automatic = 12, else
-     * 1..30; the correction phase gets the other 31 - tile_warps1 warps of a
-     * 1024-thread CTA).  Other values give SUPPY_EINVAL. */
+     * 16 or 32) and warps of its dot-product phase (0 automatic = 10, else
+     * 1..26; of the 32 warps of a CTA one streams A and watches the grid
+     * counters, four compute the correction coefficients and the other
+     * 27 - tile_warps1 scatter the corrections).  Other values give
+     * SUPPY_EINVAL. */
     int32_t tile_lanes, tile_warps1;
     /* Tiled sweep: stream bytes per tile and chunk aimed at (0 automatic =
      * 16384; smaller values give more chunks) and a fixed ring (0 automatic =
@@ -259,10 +261,12 @@ typedef struct {
     int32_t col_tile, col_stages; /* streaming column pass: the same       */
     int32_t map, col_map;         /* streaming lane maps (opts.stream_map: 1 or 2) */
     /* tiled sweep (strategy 3): tiles (= CTAs), chunks, lanes per segment,
-     * warps of the two phases, ring bytes, bytes and segments of the tile
-     * streams; zero for the other strategies */
+     * warps of the dot products and of the scatter, ring bytes, bytes and
+     * segments of the tile streams, warps of the coefficients; zero for the
+     * other strategies */
     int32_t tiles, chunks, tile_lanes, tile_warps1, tile_warps2, tile_ring;
     int64_t tile_stream_bytes, tile_segments;
+    int32_t tile_coef_warps, reserved_;
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */
@@ -461,14 +465,17 @@ suppy_status suppy_set_wait_limit(suppy_ctx* ctx, int64_t cycles);
  * they own, or a loop that must not take the implicit synchronization of
  * cudaMalloc/cudaFree).  It computes, for the rows with ||a_i|| > 0,
  *   x <- clamp(x + lambda * weight * sum_i ((clamp(r_i, l_i, u_i) - r_i) / ||a_i||^2) a_i, lo, hi)
- * with r = A x, and writes 1/2 weight sum_i d_i^2 / ||a_i||^2 at the input
- * point to *proximity (a device double; NULL to skip).  weight = 1/m' gives
- * the equal-weight step of suppy_sweep.
+ * with r = A x (FP32) and ||a_i||^2 in FP64, and writes 1/2 weight sum_i
+ * d_i^2 / ||a_i||^2 at the input point to *proximity (a device double; NULL
+ * to skip).  weight = 1/m' gives the equal-weight step of suppy_sweep.
+ * Bounds with a NaN or l_i > u_i, or a row with ||a_i|| = 0 whose slab
+ * excludes 0, are found on the device (the call does not synchronize): x is
+ * then left unchanged and *proximity is set to NaN.
  *   A            CSR with on_device = 1; l, u (m), box_lo, box_hi (box_len =
  *                1 or n) and x (n, updated in place) are device pointers.
  *   stream       cudaStream_t the kernels are enqueued on; asynchronous.
- * Its scratch (correction accumulator and per-CTA partials) is a static
- * device array of 4 MiB + 16 KiB that every GPU loading the library holds
+ * Its scratch (correction accumulator, per-CTA partials, a validity word) is
+ * a static device array of 4 MiB + 16.25 KiB that every GPU loading the library holds
  * until exit; n above 1048576 is rejected with SUPPY_EINVAL.  Every call on a
  * device shares that array (each call clears what must start at zero), so
  * calls that can overlap on the GPU race.  The first call on a device looks

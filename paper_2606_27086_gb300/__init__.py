@@ -115,7 +115,8 @@ class suppy_info(ctypes.Structure):
                 ("chunks", ctypes.c_int32), ("tile_lanes", ctypes.c_int32),
                 ("tile_warps1", ctypes.c_int32), ("tile_warps2", ctypes.c_int32),
                 ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
-                ("tile_segments", ctypes.c_int64)]
+                ("tile_segments", ctypes.c_int64), ("tile_coef_warps", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 _lib = None

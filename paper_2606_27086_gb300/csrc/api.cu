@@ -132,7 +132,8 @@ struct suppy_ctx {
     unsigned* d_tsync = nullptr;    // {CTAs finished, epoch}
     double* d_tpp = nullptr;
     int tiP = 0, tiK = 0, ticap = 0, timaxchunk = 0;
-    int tiG = 8, tiW1 = 12, tiW2 = 19;    // lanes per segment, warps of the two phases
+    int tiG = 8, tiW1 = 10, tiW2 = 17;    // lanes per segment, warps of the dot products / scatter
+    int tiNC = 4, ticq = 8, timaxseg = 0; // coefficient warps, their slots, segments per slot
     int tipiece = 8192, tistages = 0;     // ring: bytes per copy, stages
     size_t tismem = 0;
     long long tibytes = 0;                // bytes of the tile streams
@@ -634,7 +635,10 @@ suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopP
     a.stages = c->tistages;
     a.tile_cap = c->ticap;
     a.W1 = c->tiW1;
+    a.NC = c->tiNC;
     a.W2 = c->tiW2;
+    a.cq = c->ticq;
+    a.maxseg = c->timaxseg;
     a.l = c->d_l;
     a.u = c->d_u;
     a.wr = c->d_wr;
@@ -1362,9 +1366,10 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     for (int i = 0; i < c->m; ++i) rstart[i] = rinfo[i].x;
     in.row_start = rstart.data();
     in.seg_start = c->seg_start;
-    in.max_chunk = std::min<long long>(40 * 1024, max_chunk);
-    in.chunk_target = chunk_req ? chunk_req : std::min<long long>(16 * 1024, in.max_chunk / 2);
+    in.max_chunk = std::min<long long>(48 * 1024, max_chunk);
+    in.chunk_target = chunk_req ? chunk_req : std::min<long long>(24 * 1024, in.max_chunk / 2);
     in.max_chunks = kTileMaxChunks;
+    in.max_nseg = 2048;
     // a segment, its descriptor and padding fit well inside one chunk
     in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 2 - 32) / (vbytes + 2)));
     in.max_tile_words = kTileMaxWords;
@@ -1375,7 +1380,8 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
         return SUPPY_OK;   // not eligible: the caller keeps another strategy
     }
     // the ring takes the shared memory the tables and tiles leave
-    const size_t fixed = tile_smem_bytes(0, plan.tile_cap, plan.K, kTileMaxStages) + kTileStaticSmem;
+    const size_t fixed = tile_smem_bytes(0, plan.tile_cap, plan.K, kTileMaxStages, c->ticq,
+                                         plan.max_nseg) + kTileStaticSmem;
     if (fixed >= (size_t)kTileSmemMax) {
         c->err = "tiled sweep: tiles and tables leave no room for the ring";
         return SUPPY_OK;
@@ -1393,8 +1399,10 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     c->timaxchunk = plan.max_chunk;
     c->tibytes = plan.bytes;
     c->tisegs = (long long)plan.segs.size();
-    c->tismem = tile_smem_bytes(c->tistages * c->tipiece, plan.tile_cap, plan.K, c->tistages);
-    const int threads = 32 * (1 + c->tiW1 + c->tiW2);
+    c->timaxseg = std::max(1, plan.max_nseg);
+    c->tismem = tile_smem_bytes(c->tistages * c->tipiece, plan.tile_cap, plan.K, c->tistages,
+                                c->ticq, c->timaxseg);
+    const int threads = 32 * (1 + c->tiW1 + c->tiNC + c->tiW2);
     if (tile_blocks_per_sm(c->dt, c->tiG, threads, c->tismem) < 1) {
         c->err = "tiled sweep: one CTA per SM is not resident";
         return SUPPY_OK;
@@ -1604,8 +1612,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
         if (o->tile_lanes != 0 && o->tile_lanes != 8 && o->tile_lanes != 16 && o->tile_lanes != 32)
             return fail(c, SUPPY_EINVAL, "tile_lanes must be 0, 8, 16 or 32");
-        if (o->tile_warps1 < 0 || o->tile_warps1 > 30)
-            return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..30");
+        if (o->tile_warps1 < 0 || o->tile_warps1 > 26)
+            return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..26");
         const int rb = o->tile_ring_bytes;
         if (rb != 0 && (rb % 8 != 0 || (rb / 8) < 256 || (rb / 8) > 8192 || ((rb / 8) & (rb / 8 - 1))))
             return fail(c, SUPPY_EINVAL, "tile_ring_bytes must be 0 or 8 x a power of two in [256, 8192]");
@@ -1947,7 +1955,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         c->tiG = o->tile_lanes ? o->tile_lanes : 8;
         if (o->tile_warps1) {
             c->tiW1 = o->tile_warps1;
-            c->tiW2 = kTileThreadsTotal / 32 - 1 - c->tiW1;
+            c->tiW2 = kTileThreadsTotal / 32 - 1 - c->tiNC - c->tiW1;
         }
         if ((s = build_tile(c, rp, hcol, perm, rinfo, o->tile_ring_bytes, o->tile_chunk_bytes,
                             &tile_ok)) != SUPPY_OK)
@@ -2867,6 +2875,7 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->tile_lanes = c->strategy == 3 ? c->tiG : 0;
     out->tile_warps1 = c->strategy == 3 ? c->tiW1 : 0;
     out->tile_warps2 = c->strategy == 3 ? c->tiW2 : 0;
+    out->tile_coef_warps = c->strategy == 3 ? c->tiNC : 0;
     out->tile_ring = c->strategy == 3 ? c->tistages * c->tipiece : 0;
     out->tile_stream_bytes = c->strategy == 3 ? c->tibytes : 0;
     out->tile_segments = c->strategy == 3 ? c->tisegs : 0;

@@ -200,12 +200,13 @@ struct StreamArgs {
 
 // Tiled one-pass sweep (tile.cu): one cooperative launch of P CTAs, CTA b
 // owning tile b of the unknowns (x and the correction in shared memory) and
-// streaming tile b's segments of A once per sweep.  A CTA is one producer
-// warp, W1 warps of dot products (phase 1) and W2 warps of corrections
-// (phase 2).
+// streaming tile b's segments of A once per sweep.  A CTA is one warp for the
+// bulk copies and the grid counters, W1 warps of dot products, NC warps of
+// correction coefficients and W2 warps of the scatter and the box step.
 constexpr int kTileMaxWarps = 32;
 constexpr int kTileMaxStages = 64;
 constexpr int kTileMaxChunks = 2048;
+constexpr int kTileMaxCQ = 16;          // coefficient slots
 struct TileArgs {
     const unsigned char* stream;   // every tile's byte stream
     const long long* base;         // P: start of tile b's stream (16-byte aligned)
@@ -219,7 +220,9 @@ struct TileArgs {
     int piece;                     // bytes per bulk copy (power of two)
     int stages;                    // ring stages of `piece` bytes
     int tile_cap;                  // words of the shared-memory x and Delta tiles
-    int W1, W2;                    // phase-1 / phase-2 warps
+    int W1, NC, W2;                // warps of the dot products / coefficients / scatter
+    int cq;                        // coefficient slots (chunks in flight between them)
+    int maxseg;                    // most segments of one tile in one chunk
     const float* l;                // m bounds (device row order)
     const float* u;
     const float* wr;               // w_i / ||a_i||^2
@@ -263,12 +266,13 @@ struct TilePlanIn {
     long long chunk_target;        // stream bytes per CTA and chunk aimed at
     long long max_chunk;           // largest chunk of one tile the ring may hold
     int max_chunks;                // chunks the kernel's tables hold
+    int max_nseg;                  // most segments of one tile in one chunk
     int max_seg;                   // longest segment (entries)
     long long max_tile_words;      // shared-memory words of one tile
 };
 
 struct TilePlan {
-    int P = 0, K = 0, tile_cap = 0, max_chunk = 0;
+    int P = 0, K = 0, tile_cap = 0, max_chunk = 0, max_nseg = 0;
     long long bytes = 0;
     std::vector<long long> base;
     std::vector<int> coff, nseg, chunk_blk;
@@ -279,7 +283,7 @@ struct TilePlan {
 };
 
 bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why);
-size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages);
+size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int maxseg);
 int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem);
 cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid, size_t smem,
                               cudaStream_t s);

@@ -6,8 +6,11 @@
 // start-up (a fixed memory budget, a real-time loop), code that owns all of
 // its device memory through its own pool, or code that must not trigger the
 // implicit synchronization a cudaMalloc/cudaFree can cause.  This entry point
-// keeps its scratch (the correction accumulator and the per-CTA proximity
-// partials) in a file-scope device array of fixed size instead.
+// keeps its scratch (the correction accumulator, the per-CTA proximity
+// partials and a validity word) in a file-scope device array of fixed size
+// instead.  Since the bounds live on the device and the call only enqueues,
+// invalid bounds are detected on the device: x is left unchanged and the
+// proximity written is NaN.
 //
 // The scratch array is process-wide: every GPU that loads the library holds
 // it until the process exits, and every call on a device shares it.  Calls
@@ -28,10 +31,10 @@ constexpr int kStaticMaxCtas = 2048;        // CTAs of the row kernel (partial s
 constexpr int kStaticThreads = 256;
 constexpr int kStaticDevices = 64;
 
-// correction accumulator (kStaticMaxN floats) followed by the CTA partials
-// (kStaticMaxCtas doubles): 4 MiB + 16 KiB
-static __device__ __align__(256) unsigned char g_static_scratch[sizeof(float) * kStaticMaxN +
-                                                                sizeof(double) * kStaticMaxCtas];
+// correction accumulator (kStaticMaxN floats), the CTA partials
+// (kStaticMaxCtas doubles) and a validity word: 4 MiB + 16 KiB + 256 B
+constexpr size_t kStaticFlagOffset = sizeof(float) * kStaticMaxN + sizeof(double) * kStaticMaxCtas;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticFlagOffset + 256];
 
 std::mutex g_static_mu;
 void* g_static_ptr[kStaticDevices] = {};
@@ -60,37 +63,52 @@ suppy_status static_scratch(int dev, void** out) {
     return SUPPY_OK;
 }
 
-__global__ void k_static_zero(float* delta, int n) {
+__global__ void k_static_zero(float* delta, int n, int* flag) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         delta[j] = 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
 }
 
-// One warp per row (grid-stride over rows): r = <a_i, x>, rho = ||a_i||^2,
-// d = clamp(r, l, u) - r; delta += lambda w d / rho * a_i; FP64 proximity
-// partial 1/2 w d^2 / rho per CTA.
+// One warp per row (grid-stride over rows): r = <a_i, x>, rho = ||a_i||^2 in
+// FP64 (the library's row norms are FP64 everywhere: a row of tiny values
+// whose squares underflow FP32 is still a constraint), d = clamp(r, l, u) - r;
+// delta += lambda w d / rho * a_i; FP64 proximity partial 1/2 w d^2 / rho per
+// CTA.  Bounds with a NaN or l > u, and a row with rho = 0 whose slab excludes
+// 0, set the validity word (the finalize then leaves x alone).
 __global__ void __launch_bounds__(kStaticThreads) k_static_rows(
     const int* rp, const int* col, const float* val, int m, const float* l, const float* u, float w,
-    float lam, const float* x, float* delta, double* partial) {
+    float lam, const float* x, float* delta, double* partial, int* flag) {
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (kStaticThreads / 32);
     double prox = 0.0;
     for (int i = (blockIdx.x * kStaticThreads + threadIdx.x) >> 5; i < m; i += warps) {
         const int a = rp[i], b = rp[i + 1];
-        float dot = 0.f, rho = 0.f;
+        const float li = l[i], ui = u[i];
+        float dot = 0.f;
+        double rho = 0.0;
         for (int e = a + lane; e < b; e += 32) {
             const float v = val[e];
             dot = fmaf(v, __ldg(x + col[e]), dot);
-            rho = fmaf(v, v, rho);
+            rho = fma((double)v, (double)v, rho);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dot += __shfl_xor_sync(0xffffffffu, dot, o);
             rho += __shfl_xor_sync(0xffffffffu, rho, o);
         }
-        if (rho == 0.f) continue;   // an empty row carries no constraint
-        const float d = clampf(dot, l[i], u[i]) - dot;
-        if (lane == 0) prox += 0.5 * (double)w * (double)d * (double)d / (double)rho;
-        const float coef = lam * w * d / rho;
+        const bool bad_bounds = isnan(li) || isnan(ui) || li > ui;
+        if (rho == 0.0) {
+            // an empty row carries no constraint, provided 0 lies in its slab
+            if (lane == 0 && (bad_bounds || !(li <= 0.f && 0.f <= ui))) atomicOr(flag, 1);
+            continue;
+        }
+        if (bad_bounds) {
+            if (lane == 0) atomicOr(flag, 1);
+            continue;
+        }
+        const float d = clampf(dot, li, ui) - dot;
+        if (lane == 0) prox += 0.5 * (double)w * (double)d * (double)d / rho;
+        const float coef = (float)((double)lam * (double)w * (double)d / rho);
         if (coef != 0.f)
             for (int e = a + lane; e < b; e += 32) atomicAdd(delta + col[e], coef * val[e]);
     }
@@ -106,9 +124,15 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_rows(
 }
 
 // x <- clamp(x + delta, lo, hi); CTA 0 sums the partials in a fixed order.
+// When the validity word is set, x stays as it was and the proximity is NaN.
 __global__ void k_static_finalize(float* x, const float* delta, int n, const float* lo,
                                   const float* hi, int box_len, const double* partial, int np,
-                                  double* prox_out) {
+                                  double* prox_out, const int* flag) {
+    if (*flag) {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && prox_out)
+            *prox_out = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const int bj = (box_len == 1) ? 0 : j;
         x[j] = clampf(x[j] + delta[j], lo[bj], hi[bj]);
@@ -162,15 +186,17 @@ extern "C" suppy_status suppy_sweep_static(const suppy_csr* A, const float* l, c
     float* delta = static_cast<float*>(base);
     double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(base) +
                                                 sizeof(float) * (size_t)kStaticMaxN);
+    int* flag = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + kStaticFlagOffset);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n = A->n, m = A->m;
     const int zgrid = std::min(1024, (n + kStaticThreads - 1) / kStaticThreads);
-    const int rgrid = std::max(1, std::min(kStaticMaxCtas, (m * 32 + kStaticThreads - 1) / kStaticThreads));
-    k_static_zero<<<zgrid, kStaticThreads, 0, st>>>(delta, n);
+    const int rgrid = (int)std::max<long long>(
+        1, std::min<long long>(kStaticMaxCtas, ((long long)m * 32 + kStaticThreads - 1) / kStaticThreads));
+    k_static_zero<<<zgrid, kStaticThreads, 0, st>>>(delta, n, flag);
     k_static_rows<<<rgrid, kStaticThreads, 0, st>>>(A->row_ptr, A->col, A->val, m, l, u, weight,
-                                                    lambda, x, delta, partial);
+                                                    lambda, x, delta, partial, flag);
     k_static_finalize<<<zgrid, kStaticThreads, 0, st>>>(x, delta, n, box_lo, box_hi, (int)box_len,
-                                                       partial, rgrid, proximity);
+                                                       partial, rgrid, proximity, flag);
     e = cudaGetLastError();
     if (e != cudaSuccess) return static_fail(SUPPY_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     return SUPPY_OK;

@@ -46,6 +46,18 @@
 
 namespace suppy {
 
+#ifdef SUPPY_TILE_STATS
+// Measurement build only: cycles per warp role, summed over the CTAs' warps
+// (0/1 phase-1 waits / total, 2/3 coefficient waits / total, 4/5 scatter
+// waits / total, 6/7 producer waits / total, 8/9 watcher idle polls / total).
+__device__ unsigned long long g_tile_stats[16];
+#define TSTAT_CLOCK() clock64()
+#define TSTAT_ADD(k, v) atomicAdd(&g_tile_stats[k], (unsigned long long)(v))
+#else
+#define TSTAT_CLOCK() 0LL
+#define TSTAT_ADD(k, v) ((void)0)
+#endif
+
 namespace {
 
 constexpr long long kTileDrainCycles = 4000000000LL;
@@ -134,14 +146,69 @@ __device__ __forceinline__ void scatter_batch(const unsigned char* ring, int RIN
     }
 }
 
+__device__ __forceinline__ void st_release_cta(volatile int* p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(tma::smem_addr((const void*)p)), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_cta(const volatile int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(tma::smem_addr((const void*)p))
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_add_u32_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded spin of every lane of a warp until cond() holds; false (for the
+// whole warp) when the CTA aborted, the error word is set or `limit` cycles
+// passed.
+template <class Cond>
+__device__ __forceinline__ bool warp_wait(Cond cond, volatile int* abort, const int* err,
+                                          long long limit) {
+    bool w = true;
+    if (!cond()) {
+        const long long t0 = clock64();
+        while (!cond()) {
+            if (*abort || *reinterpret_cast<const volatile int*>(err) || clock64() - t0 > limit) {
+                w = false;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    return __all_sync(0xffffffffu, w);
+}
+
+// Warp roles of one CTA (tile b):
+//   warp 0, lane 0   producer: streams the tile's bytes into the ring;
+//   warp 0, lane 1   watcher: raises chunk k's grid counter once every
+//                    phase-1 warp of the CTA finished it (one fence per batch
+//                    of chunks), and publishes to the CTA how many chunks are
+//                    complete on the whole grid;
+//   W1 warps         phase 1: partial dot products, one FP32 L2 reduction per
+//                    segment;
+//   NC warps         coefficients: for grid-complete chunks (chunk k by warp
+//                    k mod NC), c_i of every segment from the complete r_i,
+//                    into a shared-memory slot of CQ, and the proximity terms;
+//   W2 warps         scatter: Delta_j += c_i a_ij; the box step at the end of
+//                    each block.
+// Hand-offs inside the CTA are release / acquire operations on shared-memory
+// words; across CTAs, relaxed reductions after one fence by the watcher and
+// acquire loads of the counters.
 template <typename VT, int G>
 __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     if (a.st[0].stopped) return;   // uniform over the grid: nothing is touched
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
     __shared__ volatile int xver;                     // blocks whose box step is done
+    __shared__ volatile int gdone;                    // chunks complete on the grid
     __shared__ volatile int stage_piece[kTileMaxStages];
-    __shared__ volatile int p2done[kTileMaxWarps];    // chunks phase-2 warp w has finished
+    __shared__ volatile int p1done[kTileMaxWarps];    // chunks phase-1 warp w finished
+    __shared__ volatile int p2done[kTileMaxWarps];    // chunks scatter warp w finished
+    __shared__ volatile int ctag[kTileMaxCQ];         // k + 1: slot holds chunk k's coefficients
     __shared__ double prox_w[kTileMaxWarps];
     __shared__ int last_s;
     const int RING = a.stages * a.piece;
@@ -151,11 +218,12 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     int* scoff = reinterpret_cast<int*>(dt + a.tile_cap);   // K + 1 chunk offsets
     int* snseg = scoff + (a.K + 1);                         // K segment counts
     int* sblk = snseg + a.K;                                // K blocks
+    float* cbuf = reinterpret_cast<float*>(sblk + a.K);     // CQ x maxseg coefficients
     uint64_t* full = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(sblk + a.K) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(cbuf + (size_t)a.cq * a.maxseg) + 15) & ~uintptr_t(15));
     const int b = blockIdx.x, tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int W1 = a.W1, W2 = a.W2;
+    const int W1 = a.W1, NC = a.NC, W2 = a.W2, CQ = a.cq;
     const unsigned epoch = *reinterpret_cast<volatile unsigned*>(a.sync + 1);
     float* r_cur = a.r + (size_t)(epoch & 1u) * a.m;
     float* r_next = a.r + (size_t)((epoch + 1u) & 1u) * a.m;
@@ -182,14 +250,17 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             sblk[k] = a.chunk_blk[k];
         }
         if (tid < kTileMaxWarps) {
+            p1done[tid] = 0;
             p2done[tid] = 0;
             prox_w[tid] = 0.0;
         }
+        if (tid < kTileMaxCQ) ctag[tid] = 0;
         if (tid < kTileMaxStages) stage_piece[tid] = -1;
         if (tid == 0) {
             for (int s = 0; s < a.stages; ++s) tma::mbar_init(&full[s], 1);
             abort_flag = 0;
             xver = 0;
+            gdone = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
@@ -204,25 +275,28 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     };
 
     if (warp == 0) {
-        // ---- producer: one lane streams the tile's bytes into the ring
         if (lane == 0 && len_stream > 0) {
+            // ---- producer: one lane streams the tile's bytes into the ring
             const unsigned char* src = a.stream + a.base[b];
             const uint64_t pol = tma::policy_evict_first();
             const int npieces = (len_stream + a.piece - 1) >> ts;
             int issued = 0;
-            int rel_chunk = 0;   // chunks every phase-2 warp has finished (cached)
+            long long st_t0 = TSTAT_CLOCK(), st_w = 0;
+            (void)st_t0;
+            int rel_chunk = 0;   // chunks every scatter warp has finished (cached)
             for (int q = 0; q < npieces; ++q) {
                 const int s = q % a.stages;
                 if (q >= a.stages) {
-                    // the stage's previous piece must be read by both phases:
-                    // every chunk overlapping it finished phase 2
+                    // the stage's previous piece must be done with: every chunk
+                    // overlapping it finished its scatter
                     const int need = (q - a.stages + 1) << ts;
                     if (scoff[rel_chunk] < need) {
                         const long long t0 = clock64();
+                        st_w -= TSTAT_CLOCK();
                         bool ok = true;
                         while (true) {
                             int mn = 0x7fffffff;
-                            for (int w = 0; w < W2; ++w) mn = min(mn, p2done[w]);
+                            for (int w = 0; w < W2; ++w) mn = min(mn, ld_acquire_cta(&p2done[w]));
                             rel_chunk = mn;
                             if (scoff[rel_chunk] >= need) break;
                             if (abort_flag || *reinterpret_cast<volatile int*>(a.err) ||
@@ -230,8 +304,9 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                                 ok = false;
                                 break;
                             }
-                            __nanosleep(128);
+                            __nanosleep(64);
                         }
+                        st_w += TSTAT_CLOCK();
                         if (!ok) {
                             give_up(3);
                             break;
@@ -245,10 +320,49 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 tma::bulk_g2s(ring + ((size_t)s << ts), src + off, bytes, &full[s], pol);
                 issued = q + 1;
             }
+            TSTAT_ADD(6, st_w);
+            TSTAT_ADD(7, TSTAT_CLOCK() - st_t0);
             // copies in flight land before the CTA may leave
             volatile int never = 0;
             for (int q = (issued > a.stages ? issued - a.stages : 0); q < issued; ++q)
                 tma::mbar_wait(&full[q % a.stages], (q / a.stages) & 1, &never, kTileDrainCycles);
+        } else if (lane == 1) {
+            // ---- watcher
+            int sig = 0, done = 0;
+            long long t0 = clock64();
+            const unsigned P = gridDim.x;
+            long long st_t0 = TSTAT_CLOCK(), st_idle = 0;
+            (void)st_t0;
+            while (done < a.K) {
+                bool prog = false;
+                int m1 = a.K;
+                for (int w = 0; w < W1; ++w) m1 = min(m1, ld_acquire_cta(&p1done[w]));
+                if (m1 > sig) {
+                    // the phase-1 warps' reductions (ordered before their
+                    // release of p1done) reach the GPU before the counters
+                    __threadfence();
+                    for (int k = sig; k < m1; ++k) red_add_u32_gpu(a.cnt + k, 1u);
+                    sig = m1;
+                    prog = true;
+                }
+                while (done < sig && ld_acquire_gpu(a.cnt + done) >= P) {
+                    ++done;
+                    prog = true;
+                }
+                if (prog) {
+                    st_release_cta(&gdone, done);
+                    t0 = clock64();
+                } else {
+                    if (abort_flag || *reinterpret_cast<volatile int*>(a.err) || clock64() - t0 > limit) {
+                        give_up(3);
+                        break;
+                    }
+                    st_idle += 1;
+                    __nanosleep(32);
+                }
+            }
+            TSTAT_ADD(8, st_idle);
+            TSTAT_ADD(9, TSTAT_CLOCK() - st_t0);
         }
     } else if (warp <= W1) {
         // ---- phase 1: partial dot products of the tile's segments
@@ -257,22 +371,16 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
         const int gi = lane / G, gl = lane % G;
         bool ok = true;
         int cur_blk = 0;
+        long long st_t0 = TSTAT_CLOCK(), st_w = 0;
+        (void)st_t0;
         for (int k = 0; k < a.K; ++k) {
             const int blk = sblk[k];
+            st_w -= TSTAT_CLOCK();
             if (blk != cur_blk) {
                 // the next block's dot products use x after the block's box step
                 cur_blk = blk;
                 if (ok) {
-                    bool w = true;
-                    const long long t0 = clock64();
-                    while (xver < blk) {
-                        if (abort_flag || clock64() - t0 > limit) {
-                            w = false;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
-                    ok = __all_sync(0xffffffffu, w);
+                    ok = warp_wait([&] { return ld_acquire_cta(&xver) >= blk; }, &abort_flag, a.err, limit);
                     if (!ok && lane == 0) give_up(3);
                 }
             }
@@ -280,22 +388,13 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             if (ok && c1 > c0) {
                 for (int q = c0 >> ts; ok && q <= (c1 - 1) >> ts; ++q) {
                     const int s = q % a.stages;
-                    bool w = true;
-                    if (stage_piece[s] != q) {
-                        const long long t0 = clock64();
-                        while (stage_piece[s] != q) {
-                            if (abort_flag || clock64() - t0 > limit) {
-                                w = false;
-                                break;
-                            }
-                            __nanosleep(64);
-                        }
-                    }
-                    if (w) w = tma::mbar_wait(&full[s], (q / a.stages) & 1, &abort_flag, limit);
-                    ok = __all_sync(0xffffffffu, w);
+                    ok = warp_wait([&] { return stage_piece[s] == q; }, &abort_flag, a.err, limit);
+                    if (ok) ok = __all_sync(0xffffffffu, tma::mbar_wait(&full[s], (q / a.stages) & 1,
+                                                                        &abort_flag, limit));
                 }
                 if (!ok && lane == 0) give_up(3);
             }
+            st_w += TSTAT_CLOCK();
             if (ok && c1 > c0) {
                 const int nseg = snseg[k];
                 const int rc = c0 % RING;
@@ -332,8 +431,8 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                     }
 #pragma unroll
                     for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                    // lane 0 issues the warp's reductions: its release below
-                    // then orders all of them before the counter
+                    // lane 0 issues the warp's reductions: its release of
+                    // p1done then orders all of them
 #pragma unroll
                     for (int g2 = 0; g2 < GPW; ++g2) {
                         const float pv = __shfl_sync(0xffffffffu, dot, g2 * G);
@@ -343,75 +442,111 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 }
             }
             __syncwarp();
-            if (ok && lane == 0) red_release_add_gpu(a.cnt + k, 1u);
+            if (ok && lane == 0) st_release_cta(&p1done[w1], k + 1);
         }
-    } else {
-        // ---- phase 2: coefficients and the scatter into Delta
-        const int w2 = warp - 1 - W1;
-        constexpr int GPW = 32 / G;
-        const int gi = lane / G, gl = lane % G;
-        const unsigned target = (unsigned)gridDim.x * (unsigned)W1;
-        const int t2 = tid - 32 * (1 + W1);   // 0 .. 32 W2 - 1
+        if (lane == 0) {
+            TSTAT_ADD(0, st_w);
+            TSTAT_ADD(1, TSTAT_CLOCK() - st_t0);
+        }
+    } else if (warp <= W1 + NC) {
+        // ---- coefficients of grid-complete chunks
+        const int wc = warp - 1 - W1;
         double pacc = 0.0;
         bool ok = true;
-        for (int k = 0; k < a.K; ++k) {
-            const int blk = sblk[k];
-            if (ok) {
-                bool w = true;
-                if (ld_acquire_gpu(a.cnt + k) < target) {
-                    const long long t0 = clock64();
-                    while (ld_acquire_gpu(a.cnt + k) < target) {
-                        if (abort_flag || *reinterpret_cast<volatile int*>(a.err) ||
-                            clock64() - t0 > limit) {
-                            w = false;
-                            break;
-                        }
-                        __nanosleep(64);
+        long long st_t0 = TSTAT_CLOCK(), st_w = 0;
+        (void)st_t0;
+        for (int k = wc; k < a.K && ok; k += NC) {
+            const int slot = k % CQ;
+            st_w -= TSTAT_CLOCK();
+            if (k >= CQ)
+                ok = warp_wait([&] { return ld_acquire_cta(&p2done[lane < W2 ? lane : 0]) > k - CQ || lane >= W2; },
+                               &abort_flag, a.err, limit);
+            if (ok) ok = warp_wait([&] { return ld_acquire_cta(&gdone) > k; }, &abort_flag, a.err, limit);
+            st_w += TSTAT_CLOCK();
+            if (!ok) {
+                if (lane == 0) give_up(3);
+                break;
+            }
+            const int c0 = scoff[k], nseg = snseg[k];
+            const int rc = c0 % RING;
+            const double scale = a.blk_scale[sblk[k]];
+            float* cb = cbuf + (size_t)slot * a.maxseg;
+            for (int s0 = 0; s0 < nseg; s0 += 4 * 32) {
+                uint2 d[4];
+                float ri[4], li[4], ui[4], wi[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int sg = s0 + u * 32 + lane;
+                    if (sg < nseg) {
+                        d[u] = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
+                        const int row = (int)(d[u].x & 0x7fffffffu);
+                        ri[u] = ld_relaxed_gpu(r_cur + row);
+                        li[u] = __ldg(a.l + row);
+                        ui[u] = __ldg(a.u + row);
+                        wi[u] = __ldg(a.wr + row);
                     }
                 }
-                ok = __all_sync(0xffffffffu, w);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int sg = s0 + u * 32 + lane;
+                    if (sg < nseg) {
+                        const float dd = clampf(ri[u], li[u], ui[u]) - ri[u];
+                        cb[sg] = a.lam * wi[u] * dd;
+                        if (d[u].x & 0x80000000u) pacc += (double)dd * (double)dd * (double)wi[u] * scale;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) st_release_cta(&ctag[slot], k + 1);
+        }
+        pacc = warp_sum(pacc);
+        if (lane == 0) {
+            prox_w[wc] = pacc;
+            TSTAT_ADD(2, st_w);
+            TSTAT_ADD(3, TSTAT_CLOCK() - st_t0);
+        }
+    } else {
+        // ---- scatter into Delta, and the box step at the end of each block
+        const int w2 = warp - 1 - W1 - NC;
+        constexpr int GPW = 32 / G;
+        const int gi = lane / G, gl = lane % G;
+        const int t2 = tid - 32 * (1 + W1 + NC);   // 0 .. 32 W2 - 1
+        bool ok = true;
+        long long st_t0 = TSTAT_CLOCK(), st_w = 0;
+        (void)st_t0;
+        for (int k = 0; k < a.K; ++k) {
+            const int blk = sblk[k];
+            const int slot = k % CQ;
+            st_w -= TSTAT_CLOCK();
+            if (ok) {
+                ok = warp_wait([&] { return ld_acquire_cta(&ctag[slot]) > k; }, &abort_flag, a.err, limit);
                 if (!ok && lane == 0) give_up(3);
             }
-            const int c0 = scoff[k], c1 = scoff[k + 1];
-            if (ok && c1 > c0) {
-                const int nseg = snseg[k];
+            st_w += TSTAT_CLOCK();
+            const int c0 = scoff[k], nseg = snseg[k];
+            if (ok && nseg > 0) {
                 const int rc = c0 % RING;
-                const double scale = a.blk_scale[blk];
-                for (int base = w2 * 32; base < nseg; base += W2 * 32) {
-                    const int sg = base + lane;
-                    float c = 0.f;
-                    int off = 0, len = 0;
+                const float* cb = cbuf + (size_t)slot * a.maxseg;
+                for (int base = w2 * GPW; base < nseg; base += W2 * GPW) {
+                    const int sg = base + gi;
                     if (sg < nseg) {
-                        const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
-                        const int row = (int)(d.x & 0x7fffffffu);
-                        off = 4 * (int)(d.y & 0xffffu);
-                        len = (int)(d.y >> 16);
-                        const float ri = ld_relaxed_gpu(r_cur + row);
-                        const float li = __ldg(a.l + row), ui = __ldg(a.u + row), wi = __ldg(a.wr + row);
-                        const float dd = clampf(ri, li, ui) - ri;
-                        c = a.lam * wi * dd;
-                        if (d.x & 0x80000000u) pacc += (double)dd * (double)dd * (double)wi * scale;
-                    }
-                    const int cntb = min(32, nseg - base);
-                    for (int t0 = 0; t0 < cntb; t0 += GPW) {
-                        const int t = t0 + gi;
-                        const float ct = __shfl_sync(0xffffffffu, c, t & 31);
-                        const int ot = __shfl_sync(0xffffffffu, off, t & 31);
-                        const int lt = __shfl_sync(0xffffffffu, len, t & 31);
-                        if (t < cntb && ct != 0.f) {
-                            const int vp = wrap(rc + ot, RING);
-                            const int ip = wrap(vp + (int)sizeof(VT) * lt, RING);
-                            for (int e = gl; e < lt; e += kCasBatch * G)
-                                scatter_batch<VT, G>(ring, RING, vp, ip, e, lt, ct, dt);
+                        const float c = cb[sg];
+                        if (c != 0.f) {
+                            const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
+                            const int off = 4 * (int)(d.y & 0xffffu), len = (int)(d.y >> 16);
+                            const int vp = wrap(rc + off, RING);
+                            const int ip = wrap(vp + (int)sizeof(VT) * len, RING);
+                            for (int e = gl; e < len; e += kCasBatch * G)
+                                scatter_batch<VT, G>(ring, RING, vp, ip, e, len, c, dt);
                         }
                     }
                 }
             }
             __syncwarp();
-            if (lane == 0) p2done[w2] = k + 1;
+            if (lane == 0) st_release_cta(&p2done[w2], k + 1);
             if (k + 1 == a.K || sblk[k + 1] != blk) {
-                // end of the block: the box step on the tile (every phase-2
-                // warp has finished the block's scatter)
+                // end of the block: the box step on the tile (every scatter
+                // warp has finished the block's chunks)
                 named_sync(1, 32 * W2);
                 const bool last = (k + 1 == a.K);
                 for (int j = t2; j < ntile; j += 32 * W2) {
@@ -419,26 +554,28 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                     if (cc >= rect.z) continue;
                     const long long g = rect.x + (long long)rr * a.W + cc;
                     const int bj = (a.box_len == 1) ? 0 : (int)g;
-                    float s = dt[j];
-                    if (a.zc) s *= __ldg(a.zc + g);
-                    const float v = clampf(xt[j] + s, __ldg(a.lo + bj), __ldg(a.hi + bj));
+                    float sv = dt[j];
+                    if (a.zc) sv *= __ldg(a.zc + g);
+                    const float v = clampf(xt[j] + sv, __ldg(a.lo + bj), __ldg(a.hi + bj));
                     xt[j] = v;
                     dt[j] = 0.f;
                     if (last) a.x[g] = v;
                 }
                 named_sync(1, 32 * W2);
-                if (t2 == 0) xver = blk + 1;
+                if (t2 == 0) st_release_cta(&xver, blk + 1);
             }
         }
-        pacc = warp_sum(pacc);
-        if (lane == 0) prox_w[w2] = pacc;
+        if (lane == 0) {
+            TSTAT_ADD(4, st_w);
+            TSTAT_ADD(5, TSTAT_CLOCK() - st_t0);
+        }
     }
     __syncthreads();
 
     // ---- end: proximity partial, the last CTA runs the epilogue and resets
     if (tid == 0) {
         double sp = 0.0;
-        for (int w = 0; w < W2; ++w) sp += prox_w[w];
+        for (int w = 0; w < NC; ++w) sp += prox_w[w];
         a.pp[b] = sp;
         __threadfence();
         last_s = (atomicAdd(a.sync, 1u) == gridDim.x - 1) ? 1 : 0;
@@ -501,8 +638,9 @@ TileFn tile_fn(suppy_dtype dt, int G) {
 
 }  // namespace
 
-size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages) {
-    size_t b = (size_t)ring_bytes + 8 * (size_t)tile_cap + 4 * (3 * (size_t)K + 1);
+size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int maxseg) {
+    size_t b = (size_t)ring_bytes + 8 * (size_t)tile_cap + 4 * (3 * (size_t)K + 1) +
+               4 * (size_t)cq * maxseg;
     b = (b + 15) & ~(size_t)15;
     return b + 8 * (size_t)stages;
 }
@@ -518,7 +656,8 @@ int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem) {
 
 cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid, size_t smem,
                               cudaStream_t s) {
-    if (a.W1 < 1 || a.W2 < 1 || 1 + a.W1 + a.W2 > kTileMaxWarps || a.stages < 2 ||
+    if (a.W1 < 1 || a.W2 < 1 || a.NC < 1 || 1 + a.W1 + a.NC + a.W2 > kTileMaxWarps ||
+        a.cq < a.NC || a.cq > kTileMaxCQ || a.stages < 2 ||
         a.stages > kTileMaxStages || a.piece < 256 || (a.piece & (a.piece - 1)) || grid < 1)
         return cudaErrorInvalidValue;
     TileFn f = tile_fn(dt, G);
@@ -526,7 +665,7 @@ cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(32 * (1 + a.W1 + a.W2), 1, 1);
+    cfg.blockDim = dim3(32 * (1 + a.W1 + a.NC + a.W2), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -696,20 +835,30 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
     // ---- chunks: consecutive rows inside a block, about `target` stream
     // bytes per CTA each; halved while some tile's chunk exceeds max_chunk
     const int nblk = (int)in.seg_start.size() - 1;
+    // rows of a block in a scattered order (a stride near len / golden ratio,
+    // coprime to the block length): each chunk then holds rays of every
+    // direction and position, so every tile gets about the same share of it
+    std::vector<int> order(in.m);
+    for (int t = 0; t < nblk; ++t) {
+        const long long r0 = in.seg_start[t], len = in.seg_start[t + 1] - r0;
+        long long S = std::max<long long>(1, std::llround((double)len * 0.6180339887498949));
+        while (len > 1 && std::gcd(S, len) != 1) ++S;
+        for (long long j = 0; j < len; ++j) order[r0 + j] = (int)(r0 + (j * S) % std::max<long long>(len, 1));
+    }
     long long target = (long long)in.chunk_target * P;
     for (int attempt = 0; attempt < 12; ++attempt) {
-        std::vector<int> ck;      // row starts of the chunks
+        std::vector<int> ck;      // positions in `order` where the chunks start
         std::vector<int> cblk;
         for (int t = 0; t < nblk; ++t) {
             const int r0 = in.seg_start[t], r1 = in.seg_start[t + 1];
             long long acc = 0;
             int start = r0;
-            for (int i = r0; i < r1; ++i) {
-                acc += row_bytes[i];
+            for (int j = r0; j < r1; ++j) {
+                acc += row_bytes[order[j]];
                 if (acc >= target) {
                     ck.push_back(start);
                     cblk.push_back(t);
-                    start = i + 1;
+                    start = j + 1;
                     acc = 0;
                 }
             }
@@ -727,19 +876,24 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         std::vector<int> nseg((size_t)P * K, 0);
         std::vector<long long> dbytes((size_t)P * K, 0);
         for (int k = 0; k < K; ++k)
-            for (int r = row_run[ck[k]]; r < row_run[ck[k + 1]]; ++r) {
-                const Run& u = runs[r];
-                nseg[(size_t)u.tile * K + k] += 1;
-                dbytes[(size_t)u.tile * K + k] += ((long long)u.len * (vs + 2) + 3) & ~3LL;
+            for (int j = ck[k]; j < ck[k + 1]; ++j) {
+                const int i = order[j];
+                for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
+                    const Run& u = runs[r];
+                    nseg[(size_t)u.tile * K + k] += 1;
+                    dbytes[(size_t)u.tile * K + k] += ((long long)u.len * (vs + 2) + 3) & ~3LL;
+                }
             }
         long long worst = 0;
+        int worst_nseg = 0;
         std::vector<long long> csize((size_t)P * K);
         for (size_t q = 0; q < csize.size(); ++q) {
             const long long desc = ((long long)nseg[q] * 8 + 15) & ~15LL;
             csize[q] = (desc + dbytes[q] + 15) & ~15LL;
             worst = std::max(worst, csize[q]);
+            worst_nseg = std::max(worst_nseg, nseg[q]);
         }
-        if (worst > in.max_chunk) {
+        if (worst > in.max_chunk || worst_nseg > in.max_nseg) {
             target /= 2;
             if (target < 1024) break;
             continue;
@@ -752,6 +906,7 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         out.base.assign(P, 0);
         long long tot = 0;
         out.max_chunk = (int)worst;
+        out.max_nseg = worst_nseg;
         for (int p = 0; p < P; ++p) {
             out.base[p] = tot;
             long long o = 0;
@@ -773,7 +928,8 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         for (size_t q = 0; q < dpos.size(); ++q) dpos[q] = ((long long)nseg[q] * 8 + 15) & ~15LL;
         out.segs.resize(runs.size());
         for (int k = 0; k < K; ++k) {
-            for (int i = ck[k]; i < ck[k + 1]; ++i) {
+            for (int j = ck[k]; j < ck[k + 1]; ++j) {
+                const int i = order[j];
                 for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
                     const Run& u = runs[r];
                     const size_t q = (size_t)u.tile * K + k;
@@ -795,3 +951,12 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
 }
 
 }  // namespace suppy
+
+#ifdef SUPPY_TILE_STATS
+extern "C" int suppy_tile_stats(unsigned long long* out16, int reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out16, suppy::g_tile_stats, sizeof(unsigned long long) * 16);
+    if (e != cudaSuccess || !reset) return (int)e;
+    unsigned long long z[16] = {};
+    return (int)cudaMemcpyToSymbol(suppy::g_tile_stats, z, sizeof(z));
+}
+#endif

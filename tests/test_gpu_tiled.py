@@ -11,8 +11,9 @@ and warp split, Cimmino, BIP (box after each block) and DROP, FP32 and
 call (the alternating accumulators), and superiorized runs with CUDA graphs.
 
 Tolerance: one sweep from the same point <= 1e-5 relative L2 against the
-oracle (FP32 arithmetic; the order of the FP32 additions is not fixed),
-a superiorized run <= 1e-4 here (1e-3 is the run's bound).
+oracle (FP32 arithmetic; the order of the FP32 additions is not fixed), a
+superiorized run <= 1e-3 (the run's bound: TV subgradient directions at
+near-ties amplify FP32 rounding over the iterations).
 """
 import numpy as np
 import pytest
@@ -62,7 +63,7 @@ def test_tiled_one_sweep_ct_small_ring(lanes, warps1):
     prob = small_ct()
     ctx, info = _tiled(prob, tile_lanes=lanes, tile_warps1=warps1, **SMALL)
     assert info["tile_lanes"] == lanes and info["tile_warps1"] == warps1
-    assert info["tile_warps2"] == 31 - warps1
+    assert info["tile_warps2"] == 27 - warps1 and info["tile_coef_warps"] == 4
     assert info["chunks"] > 20 and info["tile_ring"] == 8192
     # every tile's stream is longer than the ring
     assert info["tile_stream_bytes"] > 3 * info["tiles"] * info["tile_ring"]
@@ -185,7 +186,7 @@ def test_tiled_low_precision_values(dtype):
 def test_tiled_superiorized_run_with_graphs(mode):
     """Algorithm 1 with TV perturbations over 25 iterations (one captured
     iteration replayed) against the oracle: same accepted steps and exponent,
-    iterate and histories within 1e-4."""
+    iterate and histories within 1e-3."""
     prob = synth.ct_problem(96, 120, 137)
     if mode == O.BIP:
         prob.blocks = synth.angle_blocks(120, 137, 12)
@@ -199,10 +200,10 @@ def test_tiled_superiorized_run_with_graphs(mode):
               x0=x0.astype(np.float64))
     assert st["sweeps"] == 25
     assert st["accepted"] == sum(r.accepted) and st["ell"] == r.ell
-    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-4
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3
     ph, _ = ctx.suppy_history()
     po = np.asarray(r.prox_hist)
-    assert np.max(np.abs(np.asarray(ph) - po) / np.abs(po)) <= 1e-4
+    assert np.max(np.abs(np.asarray(ph) - po) / np.abs(po)) <= 1e-3
     ctx.close()
 
 
