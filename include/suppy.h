@@ -182,13 +182,12 @@ typedef struct {
      * k + 2G, ...: one gather instruction reads G consecutive elements of an
      * item).  Other values give SUPPY_EINVAL. */
     int32_t stream_map;
-    /* Tiled sweep (strategy 3): lanes per segment (0 automatic = 8, else 8,
-     * 16 or 32) and warps of its dot-product phase (0 automatic = 10, else
-     * 1..26; of the 32 warps of a CTA one streams A and watches the grid
-     * counters, four compute the correction coefficients and the other
-     * 27 - tile_warps1 scatter the corrections).  Other values give
+    /* Tiled sweep (strategy 3): warps of its dot-product phase (0 automatic
+     * = 10, else 1..25; of the 32 warps of a CTA one streams A, one watches
+     * the grid counters, four compute the correction coefficients and the
+     * other 26 - tile_warps1 scatter the corrections).  Other values give
      * SUPPY_EINVAL. */
-    int32_t tile_lanes, tile_warps1;
+    int32_t tile_warps1;
     /* Tiled sweep: stream bytes per tile and chunk aimed at (0 automatic =
      * 16384; smaller values give more chunks) and a fixed ring (0 automatic =
      * up to 24 copies of 8 KB in the shared memory left; else 8 copies of
@@ -260,13 +259,11 @@ typedef struct {
     int32_t tile, stages;         /* streaming row pass: ring tile length (elements), stages */
     int32_t col_tile, col_stages; /* streaming column pass: the same       */
     int32_t map, col_map;         /* streaming lane maps (opts.stream_map: 1 or 2) */
-    /* tiled sweep (strategy 3): tiles (= CTAs), chunks, lanes per segment,
-     * warps of the dot products and of the scatter, ring bytes, bytes and
-     * segments of the tile streams, warps of the coefficients; zero for the
-     * other strategies */
-    int32_t tiles, chunks, tile_lanes, tile_warps1, tile_warps2, tile_ring;
+    /* tiled sweep (strategy 3): tiles (= CTAs), chunks, warps of the dot
+     * products, of the scatter and of the coefficients, ring bytes, bytes and
+     * segments of the tile streams; zero for the other strategies */
+    int32_t tiles, chunks, tile_warps1, tile_warps2, tile_coef_warps, tile_ring;
     int64_t tile_stream_bytes, tile_segments;
-    int32_t tile_coef_warps, reserved_;
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

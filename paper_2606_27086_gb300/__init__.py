@@ -57,9 +57,8 @@ class suppy_opts(ctypes.Structure):
                 ("strategy", ctypes.c_int32), ("tma", ctypes.c_int32),
                 ("stream_tile", ctypes.c_int32), ("stream_stages", ctypes.c_int32),
                 ("stream_lanes", ctypes.c_int32), ("perturb_path", ctypes.c_int32),
-                ("stream_map", ctypes.c_int32), ("tile_lanes", ctypes.c_int32),
-                ("tile_warps1", ctypes.c_int32), ("tile_chunk_bytes", ctypes.c_int32),
-                ("tile_ring_bytes", ctypes.c_int32)]
+                ("stream_map", ctypes.c_int32), ("tile_warps1", ctypes.c_int32),
+                ("tile_chunk_bytes", ctypes.c_int32), ("tile_ring_bytes", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -112,11 +111,10 @@ class suppy_info(ctypes.Structure):
                 ("stages", ctypes.c_int32), ("col_tile", ctypes.c_int32),
                 ("col_stages", ctypes.c_int32), ("map", ctypes.c_int32),
                 ("col_map", ctypes.c_int32), ("tiles", ctypes.c_int32),
-                ("chunks", ctypes.c_int32), ("tile_lanes", ctypes.c_int32),
-                ("tile_warps1", ctypes.c_int32), ("tile_warps2", ctypes.c_int32),
+                ("chunks", ctypes.c_int32), ("tile_warps1", ctypes.c_int32),
+                ("tile_warps2", ctypes.c_int32), ("tile_coef_warps", ctypes.c_int32),
                 ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
-                ("tile_segments", ctypes.c_int64), ("tile_coef_warps", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32)]
+                ("tile_segments", ctypes.c_int64)]
 
 
 _lib = None
@@ -247,8 +245,8 @@ class Context:
     def __init__(self, row_ptr, col, val, m, n, l, u, box_lo, box_hi, *, dtype=SUPPY_F32,
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
                  c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None,
-                 stream_shape=(0, 0, 0), perturb_path=0, stream_map=0, tile_lanes=0,
-                 tile_warps1=0, tile_chunk_bytes=0, tile_ring_bytes=0):
+                 stream_shape=(0, 0, 0), perturb_path=0, stream_map=0, tile_warps1=0,
+                 tile_chunk_bytes=0, tile_ring_bytes=0):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -286,7 +284,6 @@ class Context:
         o.stream_tile, o.stream_stages, o.stream_lanes = (int(v) for v in stream_shape)
         o.perturb_path = int(perturb_path)
         o.stream_map = int(stream_map)
-        o.tile_lanes = int(tile_lanes)
         o.tile_warps1 = int(tile_warps1)
         o.tile_chunk_bytes = int(tile_chunk_bytes)
         o.tile_ring_bytes = int(tile_ring_bytes)
@@ -460,8 +457,8 @@ class Context:
 
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
                  stream=None, tune=0, strategy=0, tma=0, stream_shape=(0, 0, 0),
-                 perturb_path=0, stream_map=0, tile_lanes=0, tile_warps1=0,
-                 tile_chunk_bytes=0, tile_ring_bytes=0) -> Context:
+                 perturb_path=0, stream_map=0, tile_warps1=0, tile_chunk_bytes=0,
+                 tile_ring_bytes=0) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -487,9 +484,8 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
     return Context(rp, col, val, A.m, A.n, l, u, lo, hi, dtype=dtype, mode=mode,
                    block_of_row=blocks, obj=obj, nrhs=nrhs, stream=stream, tune=tune,
                    strategy=strategy, tma=tma, stream_shape=stream_shape,
-                   perturb_path=perturb_path, stream_map=stream_map, tile_lanes=tile_lanes,
-                   tile_warps1=tile_warps1, tile_chunk_bytes=tile_chunk_bytes,
-                   tile_ring_bytes=tile_ring_bytes, **kw)
+                   perturb_path=perturb_path, stream_map=stream_map, tile_warps1=tile_warps1,
+                   tile_chunk_bytes=tile_chunk_bytes, tile_ring_bytes=tile_ring_bytes, **kw)
 
 
 def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,

@@ -123,7 +123,7 @@ struct suppy_ctx {
     unsigned char* d_tstream = nullptr;
     long long* d_tbase = nullptr;
     int* d_tcoff = nullptr;
-    int* d_tnseg = nullptr;
+    int* d_tnsl = nullptr;
     int4* d_trect = nullptr;
     int* d_tcblk = nullptr;
     double* d_tscale = nullptr;
@@ -132,8 +132,8 @@ struct suppy_ctx {
     unsigned* d_tsync = nullptr;    // {CTAs finished, epoch}
     double* d_tpp = nullptr;
     int tiP = 0, tiK = 0, ticap = 0, timaxchunk = 0;
-    int tiG = 8, tiW1 = 10, tiW2 = 17;    // lanes per segment, warps of the dot products / scatter
-    int tiNC = 4, ticq = 8, timaxseg = 0; // coefficient warps, their slots, segments per slot
+    int tiW1 = 10, tiW2 = 16;             // warps of the dot products / scatter
+    int tiNC = 4, ticq = 8, ticstride = 0; // coefficient warps, their slots, coefficients per slot
     int tipiece = 8192, tistages = 0;     // ring: bytes per copy, stages
     size_t tismem = 0;
     long long tibytes = 0;                // bytes of the tile streams
@@ -625,7 +625,7 @@ suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopP
     a.stream = c->d_tstream;
     a.base = c->d_tbase;
     a.coff = c->d_tcoff;
-    a.nseg = c->d_tnseg;
+    a.nsl = c->d_tnsl;
     a.rect = c->d_trect;
     a.chunk_blk = c->d_tcblk;
     a.blk_scale = c->d_tscale;
@@ -638,7 +638,7 @@ suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopP
     a.NC = c->tiNC;
     a.W2 = c->tiW2;
     a.cq = c->ticq;
-    a.maxseg = c->timaxseg;
+    a.cstride = c->ticstride;
     a.l = c->d_l;
     a.u = c->d_u;
     a.wr = c->d_wr;
@@ -666,7 +666,7 @@ suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopP
     {
         Timed tm{c, 0};
         CK(tm.begin());
-        CK(launch_tile_sweep(a, c->dt, c->tiG, c->tiP, c->tismem, c->stream));
+        CK(launch_tile_sweep(a, c->dt, c->tiP, c->tismem, c->stream));
         CK(tm.end());
         note_launch(c);
     }
@@ -1303,14 +1303,14 @@ void free_csc(suppy_ctx* c) {
 // the tables, fill the streams on the device from the packed row copy, and
 // size the ring to the shared memory left beside the tile's x and Delta.
 void free_tile(suppy_ctx* c) {
-    for (void* p : {(void*)c->d_tstream, (void*)c->d_tbase, (void*)c->d_tcoff, (void*)c->d_tnseg,
+    for (void* p : {(void*)c->d_tstream, (void*)c->d_tbase, (void*)c->d_tcoff, (void*)c->d_tnsl,
                     (void*)c->d_trect, (void*)c->d_tcblk, (void*)c->d_tscale, (void*)c->d_tr,
                     (void*)c->d_tcnt, (void*)c->d_tsync, (void*)c->d_tpp})
         if (p) dfree(c, p);
     c->d_tstream = nullptr;
     c->d_tbase = nullptr;
     c->d_tcoff = nullptr;
-    c->d_tnseg = nullptr;
+    c->d_tnsl = nullptr;
     c->d_trect = nullptr;
     c->d_tcblk = nullptr;
     c->d_tscale = nullptr;
@@ -1369,7 +1369,7 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     in.max_chunk = std::min<long long>(48 * 1024, max_chunk);
     in.chunk_target = chunk_req ? chunk_req : std::min<long long>(24 * 1024, in.max_chunk / 2);
     in.max_chunks = kTileMaxChunks;
-    in.max_nseg = 2048;
+    in.max_slices = 48;
     // a segment, its descriptor and padding fit well inside one chunk
     in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 2 - 32) / (vbytes + 2)));
     in.max_tile_words = kTileMaxWords;
@@ -1381,7 +1381,7 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     }
     // the ring takes the shared memory the tables and tiles leave
     const size_t fixed = tile_smem_bytes(0, plan.tile_cap, plan.K, kTileMaxStages, c->ticq,
-                                         plan.max_nseg) + kTileStaticSmem;
+                                         32 * plan.max_slices) + kTileStaticSmem;
     if (fixed >= (size_t)kTileSmemMax) {
         c->err = "tiled sweep: tiles and tables leave no room for the ring";
         return SUPPY_OK;
@@ -1398,12 +1398,12 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     c->ticap = plan.tile_cap;
     c->timaxchunk = plan.max_chunk;
     c->tibytes = plan.bytes;
-    c->tisegs = (long long)plan.segs.size();
-    c->timaxseg = std::max(1, plan.max_nseg);
+    c->tisegs = plan.segments;
+    c->ticstride = 32 * std::max(1, plan.max_slices);
     c->tismem = tile_smem_bytes(c->tistages * c->tipiece, plan.tile_cap, plan.K, c->tistages,
-                                c->ticq, c->timaxseg);
-    const int threads = 32 * (1 + c->tiW1 + c->tiNC + c->tiW2);
-    if (tile_blocks_per_sm(c->dt, c->tiG, threads, c->tismem) < 1) {
+                                c->ticq, c->ticstride);
+    const int threads = 32 * (2 + c->tiW1 + c->tiNC + c->tiW2);
+    if (tile_blocks_per_sm(c->dt, threads, c->tismem) < 1) {
         c->err = "tiled sweep: one CTA per SM is not resident";
         return SUPPY_OK;
     }
@@ -1413,7 +1413,7 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     CK(cudaMemsetAsync(c->d_tstream, 0, (size_t)plan.bytes + 16, c->stream));
     if ((s = upload(c, plan.base, &c->d_tbase)) != SUPPY_OK) return s;
     if ((s = upload(c, plan.coff, &c->d_tcoff)) != SUPPY_OK) return s;
-    if ((s = upload(c, plan.nseg, &c->d_tnseg)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.nsl, &c->d_tnsl)) != SUPPY_OK) return s;
     if ((s = upload(c, plan.rect, &c->d_trect)) != SUPPY_OK) return s;
     if ((s = upload(c, plan.chunk_blk, &c->d_tcblk)) != SUPPY_OK) return s;
     std::vector<double> scale(c->nseg);
@@ -1426,16 +1426,19 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     if ((s = dalloc(c, &c->d_tsync, 2)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_tsync, 0, sizeof(unsigned) * 2, c->stream));
     if ((s = dalloc(c, &c->d_tpp, (size_t)P)) != SUPPY_OK) return s;
-    // the streams: segment records and the local column map, then the fill
-    TileSegRec* d_segs = nullptr;
+    // the streams: slice and lane records and the local column map, then the fill
+    TileSliceRec* d_sl = nullptr;
+    TileLaneRec* d_ln = nullptr;
     unsigned short* d_local = nullptr;
-    if ((s = upload(c, plan.segs, &d_segs)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.slices, &d_sl)) != SUPPY_OK) return s;
+    if ((s = upload(c, plan.lanes, &d_ln)) != SUPPY_OK) return s;
     if ((s = upload(c, plan.local_of, &d_local)) != SUPPY_OK) return s;
-    CK(launch_tile_fill(d_segs, (long long)plan.segs.size(), c->d_val, c->dt, c->d_col, d_local,
+    CK(launch_tile_fill(d_sl, (long long)plan.slices.size(), d_ln, c->d_val, c->dt, c->d_col, d_local,
                         c->d_tstream, c->stream));
     note_launch(c);
     CK(cudaStreamSynchronize(c->stream));
-    dfree(c, d_segs);
+    dfree(c, d_sl);
+    dfree(c, d_ln);
     dfree(c, d_local);
     *ok = true;
     c->err.clear();
@@ -1610,10 +1613,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_stages must be 0 or 2.. the shared-memory budget");
         if (o->stream_map < 0 || o->stream_map > 2)
             return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
-        if (o->tile_lanes != 0 && o->tile_lanes != 8 && o->tile_lanes != 16 && o->tile_lanes != 32)
-            return fail(c, SUPPY_EINVAL, "tile_lanes must be 0, 8, 16 or 32");
-        if (o->tile_warps1 < 0 || o->tile_warps1 > 26)
-            return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..26");
+        if (o->tile_warps1 < 0 || o->tile_warps1 > 25)
+            return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..25");
         const int rb = o->tile_ring_bytes;
         if (rb != 0 && (rb % 8 != 0 || (rb / 8) < 256 || (rb / 8) > 8192 || ((rb / 8) & (rb / 8 - 1))))
             return fail(c, SUPPY_EINVAL, "tile_ring_bytes must be 0 or 8 x a power of two in [256, 8192]");
@@ -1952,10 +1953,9 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     }
     bool tile_ok = false;
     if (tile_cand) {
-        c->tiG = o->tile_lanes ? o->tile_lanes : 8;
         if (o->tile_warps1) {
             c->tiW1 = o->tile_warps1;
-            c->tiW2 = kTileThreadsTotal / 32 - 1 - c->tiNC - c->tiW1;
+            c->tiW2 = kTileThreadsTotal / 32 - 2 - c->tiNC - c->tiW1;
         }
         if ((s = build_tile(c, rp, hcol, perm, rinfo, o->tile_ring_bytes, o->tile_chunk_bytes,
                             &tile_ok)) != SUPPY_OK)
@@ -2872,7 +2872,6 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->col_stages = (c->use_tma && c->strategy == 2) ? c->cstages : 0;
     out->tiles = c->strategy == 3 ? c->tiP : 0;
     out->chunks = c->strategy == 3 ? c->tiK : 0;
-    out->tile_lanes = c->strategy == 3 ? c->tiG : 0;
     out->tile_warps1 = c->strategy == 3 ? c->tiW1 : 0;
     out->tile_warps2 = c->strategy == 3 ? c->tiW2 : 0;
     out->tile_coef_warps = c->strategy == 3 ? c->tiNC : 0;

@@ -201,17 +201,18 @@ struct StreamArgs {
 // Tiled one-pass sweep (tile.cu): one cooperative launch of P CTAs, CTA b
 // owning tile b of the unknowns (x and the correction in shared memory) and
 // streaming tile b's segments of A once per sweep.  A CTA is one warp for the
-// bulk copies and the grid counters, W1 warps of dot products, NC warps of
-// correction coefficients and W2 warps of the scatter and the box step.
+// bulk copies, one for the grid counters, W1 warps of dot products, NC warps
+// of correction coefficients and W2 warps of the scatter and the box step.
 constexpr int kTileMaxWarps = 32;
 constexpr int kTileMaxStages = 64;
 constexpr int kTileMaxChunks = 2048;
 constexpr int kTileMaxCQ = 16;          // coefficient slots
+constexpr int kTileQ = 32;              // chunks between the scatter and the newest data
 struct TileArgs {
     const unsigned char* stream;   // every tile's byte stream
     const long long* base;         // P: start of tile b's stream (16-byte aligned)
     const int* coff;               // P x (K + 1): chunk byte offsets in the tile's stream
-    const int* nseg;               // P x K: segments of tile b in chunk k
+    const int* nsl;                // P x K: slices of tile b in chunk k
     const int4* rect;              // P: {first global column, rows, columns, local row stride}
     const int* chunk_blk;          // K: block of chunk k (chunks of a block are consecutive)
     const double* blk_scale;       // blocks: factor of the block's proximity terms
@@ -222,7 +223,7 @@ struct TileArgs {
     int tile_cap;                  // words of the shared-memory x and Delta tiles
     int W1, NC, W2;                // warps of the dot products / coefficients / scatter
     int cq;                        // coefficient slots (chunks in flight between them)
-    int maxseg;                    // most segments of one tile in one chunk
+    int cstride;                   // coefficients per slot (32 x most slices of a tile's chunk)
     const float* l;                // m bounds (device row order)
     const float* u;
     const float* wr;               // w_i / ||a_i||^2
@@ -243,15 +244,21 @@ struct TileArgs {
     EpiArgs epi;
 };
 
-// One segment of the tile streams (host plan -> device fill).
-struct TileSegRec {
-    long long chunk_start;         // byte offset of the segment's chunk in the stream buffer
-    int sidx;                      // descriptor index inside the chunk
-    int off4;                      // data offset inside the chunk, in 4-byte words
+// One slice of the tile streams (host plan -> device fill): up to 32
+// segments of one tile and chunk, lanes longest first.
+struct TileSliceRec {
+    long long chunk_start;         // byte offset of the slice's chunk in the stream buffer
+    int sidx;                      // table entry inside the chunk
+    int off4;                      // slice offset inside the chunk, in 4-byte words
+    int nl;                        // segments (lanes), 1..32
+    int E;                         // entries
+    int first;                     // first lane record
+    int pad;
+};
+struct TileLaneRec {
     int row_flag;                  // device row; bit 31: the row's first segment
     int e0;                        // first entry in the packed row copy
     int len;                       // entries
-    int pad;
 };
 
 struct TilePlanIn {
@@ -266,30 +273,31 @@ struct TilePlanIn {
     long long chunk_target;        // stream bytes per CTA and chunk aimed at
     long long max_chunk;           // largest chunk of one tile the ring may hold
     int max_chunks;                // chunks the kernel's tables hold
-    int max_nseg;                  // most segments of one tile in one chunk
+    int max_slices;                // most slices of one tile in one chunk
     int max_seg;                   // longest segment (entries)
     long long max_tile_words;      // shared-memory words of one tile
 };
 
 struct TilePlan {
-    int P = 0, K = 0, tile_cap = 0, max_chunk = 0, max_nseg = 0;
-    long long bytes = 0;
+    int P = 0, K = 0, tile_cap = 0, max_chunk = 0, max_slices = 0;
+    long long bytes = 0, segments = 0;
     std::vector<long long> base;
-    std::vector<int> coff, nseg, chunk_blk;
+    std::vector<int> coff, nsl, chunk_blk;
     std::vector<int4> rect;
     std::vector<int> tile_of;
     std::vector<unsigned short> local_of;
-    std::vector<TileSegRec> segs;
+    std::vector<TileSliceRec> slices;
+    std::vector<TileLaneRec> lanes;
 };
 
 bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why);
-size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int maxseg);
-int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem);
-cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid, size_t smem,
+size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int cstride);
+int tile_blocks_per_sm(suppy_dtype dt, int threads, size_t smem);
+cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int grid, size_t smem,
                               cudaStream_t s);
-cudaError_t launch_tile_fill(const TileSegRec* segs, long long nsegs, const void* val,
-                             suppy_dtype dt, const int* col, const unsigned short* local_of,
-                             unsigned char* stream, cudaStream_t s);
+cudaError_t launch_tile_fill(const TileSliceRec* slices, long long nslices, const TileLaneRec* lanes,
+                             const void* val, suppy_dtype dt, const int* col,
+                             const unsigned short* local_of, unsigned char* stream, cudaStream_t s);
 
 // Extrapolated step of EL / EMR (sweep.cu): t_b from the sweep's reductions,
 // then x <- box(x + lambda t_b delta), delta <- 0.

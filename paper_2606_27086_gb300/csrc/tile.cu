@@ -5,26 +5,30 @@
 // problems, column ranges otherwise), one per CTA of one cooperative launch;
 // a CTA keeps its tile's x and correction Delta in shared memory for the
 // whole sweep.  Every row a_i is cut into segments, runs of its consecutive
-// entries that fall in one tile, and each tile's segments are stored as one
-// contiguous byte stream (values, then 16-bit tile-local column indices),
-// grouped into chunks of consecutive rows.  A CTA streams its tile's bytes
-// once per sweep into a shared-memory ring with bulk asynchronous copies, so
-// A crosses HBM once; the gathers of x and the scatter into Delta never leave
-// the SM.
+// entries that fall in one tile.  Each tile's segments form one contiguous
+// byte stream, grouped into chunks of consecutive rows; inside a chunk, up to
+// 32 segments (of neighbouring rows) form a slice, sorted by length, whose
+// entries are stored step by step: first entry 0 of every segment, then entry
+// 1 of those that have one, and so on (values, then 16-bit tile-local column
+// indices).  A warp then takes a slice with one lane per segment, and at
+// every step its active lanes read consecutive words.  A CTA streams its
+// tile's bytes once per sweep into a shared-memory ring with bulk
+// asynchronous copies, so A crosses HBM once; the gathers of x and the
+// scatter into Delta never leave the SM.
 //
 // Per chunk k:
 //   phase 1 (dot products): the partial <a_i, x> of every segment from the
-//     tile's x, added to r_i (one FP32 L2 reduction per segment), then the
-//     chunk's counter is raised (release);
-//   phase 2 (corrections), once the counter says every CTA finished phase 1
-//     of chunk k (acquire): c_i = lambda w_i (clamp(r_i, l_i, u_i) - r_i) / ||a_i||^2
-//     from the complete r_i, and Delta_j += c_i a_ij for the segment's entries
-//     (shared-memory compare-and-swap additions, several in flight per lane);
-//     the proximity term of row i is added by the segment that holds the
-//     row's first entry (FP64).
-// Phase 1 runs ahead of phase 2 by as many chunks as the ring holds, so the
-// cross-CTA dependency is a rolling one, not a grid barrier.  At the end of
-// a block (the whole sweep for Cimmino and DROP) x_j <- box(x_j + z_j Delta_j)
+//     tile's x, added to r_i (one FP32 L2 reduction per segment); once every
+//     phase-1 warp of the CTA is done with the chunk, its grid counter is
+//     raised;
+//   coefficients, once the counter says every CTA finished phase 1 of chunk
+//     k: c_i = lambda w_i (clamp(r_i, l_i, u_i) - r_i) / ||a_i||^2 from the
+//     complete r_i (and the proximity term of row i, added by the segment
+//     that holds the row's first entry, FP64);
+//   scatter: Delta_j += c_i a_ij (shared-memory compare-and-swap additions).
+// Phase 1 runs ahead of the scatter by as many chunks as the ring holds, so
+// the cross-CTA dependency is a rolling one, not a grid barrier.  At the end
+// of a block (the whole sweep for Cimmino and DROP) x_j <- box(x_j + z_j Delta_j)
 // on the tile, and the next block's dot products use the new x.
 //
 // r_i lives in two buffers used on alternate sweeps (an epoch word): a sweep
@@ -61,6 +65,7 @@ __device__ unsigned long long g_tile_stats[16];
 namespace {
 
 constexpr long long kTileDrainCycles = 4000000000LL;
+constexpr unsigned kFull = 0xffffffffu;
 
 template <typename VT>
 __device__ __forceinline__ float to_float(VT v);
@@ -75,8 +80,8 @@ __device__ __forceinline__ void red_add_gpu(float* p, float v) {
     asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-__device__ __forceinline__ void red_release_add_gpu(unsigned* p, unsigned v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_add_u32_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -91,124 +96,214 @@ __device__ __forceinline__ float ld_relaxed_gpu(const float* p) {
     return v;
 }
 
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void named_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// Ring position of stream byte p, given the chunk's ring position rc and an
-// offset within the chunk (both below the ring size).
+// Ring position of a stream offset that lies less than one ring beyond the
+// ring's end.
 __device__ __forceinline__ int wrap(int p, int ring) { return p >= ring ? p - ring : p; }
 
-// Entries a lane adds to Delta per batch of the scatter.
-constexpr int kCasBatch = 4;
-
-// Delta_j += c a_ij for the entries e, e + G, ..., e + (kCasBatch - 1) G of a
-// segment (those below len): FP32 additions into shared memory made atomic by
-// compare-and-swap.  A lane reads its entries' current sums, issues all of its
-// compare-and-swaps back to back, and retries only those another lane changed
-// in between (rare: entries of one segment are distinct columns).  The
-// library's float atomicAdd on shared memory is a compare-and-swap loop per
-// element, whose round trips a lane would wait out one after another.
-template <typename VT, int G>
-__device__ __forceinline__ void scatter_batch(const unsigned char* ring, int RING, int vp, int ip,
-                                              int e, int len, float c, float* dt) {
-    int j[kCasBatch];
-    float add[kCasBatch], old[kCasBatch];
-#pragma unroll
-    for (int u = 0; u < kCasBatch; ++u) {
-        const int eu = e + u * G;
-        j[u] = -1;
-        add[u] = 0.f;
-        if (eu < len) {
-            add[u] = c * to_float(*reinterpret_cast<const VT*>(ring + wrap(vp + (int)sizeof(VT) * eu, RING)));
-            j[u] = *reinterpret_cast<const unsigned short*>(ring + wrap(ip + 2 * eu, RING));
-        }
-    }
-    volatile float* vd = dt;
-#pragma unroll
-    for (int u = 0; u < kCasBatch; ++u) old[u] = j[u] >= 0 ? vd[j[u]] : 0.f;
-    unsigned pending = 0;
-#pragma unroll
-    for (int u = 0; u < kCasBatch; ++u) pending |= (j[u] >= 0 ? 1u : 0u) << u;
-    while (pending) {
-        unsigned prev[kCasBatch];
-#pragma unroll
-        for (int u = 0; u < kCasBatch; ++u)
-            if (pending & (1u << u))
-                prev[u] = atomicCAS(reinterpret_cast<unsigned*>(dt) + j[u], __float_as_uint(old[u]),
-                                    __float_as_uint(old[u] + add[u]));
-#pragma unroll
-        for (int u = 0; u < kCasBatch; ++u)
-            if (pending & (1u << u)) {
-                if (prev[u] == __float_as_uint(old[u])) pending &= ~(1u << u);
-                else old[u] = __uint_as_float(prev[u]);
-            }
-    }
+// One try_wait with a suspend-time hint: the thread sleeps in hardware until
+// the phase completes or about `ns` nanoseconds pass.
+__device__ __forceinline__ bool mbar_try_wait_ns(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(tma::smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
 }
 
-__device__ __forceinline__ void st_release_cta(volatile int* p, int v) {
-    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(tma::smem_addr((const void*)p)), "r"(v)
-                 : "memory");
-}
-
-__device__ __forceinline__ int ld_acquire_cta(const volatile int* p) {
-    int v;
-    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(tma::smem_addr((const void*)p))
-                 : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void red_add_u32_gpu(unsigned* p, unsigned v) {
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Bounded spin of every lane of a warp until cond() holds; false (for the
-// whole warp) when the CTA aborted, the error word is set or `limit` cycles
-// passed.
-template <class Cond>
-__device__ __forceinline__ bool warp_wait(Cond cond, volatile int* abort, const int* err,
-                                          long long limit) {
+// Bounded wait of a whole warp for the phase of `bar` with the given parity:
+// false for every lane when the CTA aborted, the error word is set or `limit`
+// cycles passed.  The waiting threads sleep in hardware between tries.
+__device__ __forceinline__ bool warp_bar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                              const int* err, long long limit) {
     bool w = true;
-    if (!cond()) {
+    if (!mbar_try_wait_ns(bar, parity, 1000)) {
         const long long t0 = clock64();
-        while (!cond()) {
+        while (!mbar_try_wait_ns(bar, parity, 1000)) {
             if (*abort || *reinterpret_cast<const volatile int*>(err) || clock64() - t0 > limit) {
                 w = false;
                 break;
             }
-            __nanosleep(32);
         }
     }
-    return __all_sync(0xffffffffu, w);
+    return __all_sync(kFull, w);
+}
+
+// A slice in the ring, seen by one warp (lane j = the slice's j-th longest
+// segment).  Layout from the slice start: nl rows (int32, bit 31 marks the
+// segment holding the row's first entry), nl lengths (u16), padding to 4
+// bytes, then E values and E column indices (u16), step by step.
+struct Slice {
+    int nl, E, L0;          // segments, entries, longest segment
+    int row_pos, vpos, ipos;
+    bool flat;              // the slice does not wrap around the ring end
+};
+
+template <typename VT>
+__device__ __forceinline__ Slice slice_at(const unsigned char* ring, int RING, int rc, int s,
+                                          int lane, int* row, int* len) {
+    const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * s, RING));
+    Slice sl;
+    sl.nl = (int)(d.y & 63u);
+    sl.E = (int)(d.y >> 6);
+    const int sp = wrap(rc + 4 * (int)d.x, RING);
+    sl.row_pos = sp;
+    const int lpos = wrap(sp + 4 * sl.nl, RING);
+    sl.vpos = wrap(sp + ((6 * sl.nl + 3) & ~3), RING);
+    sl.ipos = wrap(sl.vpos + (int)sizeof(VT) * sl.E, RING);
+    sl.flat = (sp + ((6 * sl.nl + 3) & ~3) + ((int)sizeof(VT) + 2) * sl.E) <= RING;
+    *row = -1;
+    *len = 0;
+    if (lane < sl.nl) {
+        *row = *reinterpret_cast<const int*>(ring + wrap(sp + 4 * lane, RING));
+        *len = *reinterpret_cast<const unsigned short*>(ring + wrap(lpos + 2 * lane, RING));
+    }
+    sl.L0 = __shfl_sync(kFull, *len, 0);
+    return sl;
+}
+
+template <typename VT>
+__device__ __forceinline__ float ring_val(const unsigned char* ring, int RING, const Slice& sl, int p) {
+    return to_float(*reinterpret_cast<const VT*>(ring + wrap(sl.vpos + (int)sizeof(VT) * p, RING)));
+}
+
+__device__ __forceinline__ int ring_idx(const unsigned char* ring, int RING, const Slice& sl, int p) {
+    return *reinterpret_cast<const unsigned short*>(ring + wrap(sl.ipos + 2 * p, RING));
+}
+
+// <a_i, x> over the lane's segment: at step e the lanes with len > e are
+// lanes 0 .. n_e - 1, and their entries sit at positions base_e + lane.
+template <typename VT>
+__device__ __forceinline__ float slice_dot(const unsigned char* ring, int RING, const Slice& sl,
+                                           int lane, int len, const float* xt) {
+    float a0 = 0.f, a1 = 0.f;
+    int base = 0;
+    if (sl.flat) {
+        const VT* vv = reinterpret_cast<const VT*>(ring + sl.vpos);
+        const unsigned short* ii = reinterpret_cast<const unsigned short*>(ring + sl.ipos);
+        int e = 0;
+        for (; e + 1 < sl.L0; e += 2) {
+            const bool c0 = e < len, c1 = e + 1 < len;
+            const int n0 = __popc(__ballot_sync(kFull, c0));
+            const int n1 = __popc(__ballot_sync(kFull, c1));
+            if (c0) a0 = fmaf(to_float(vv[base + lane]), xt[ii[base + lane]], a0);
+            if (c1) a1 = fmaf(to_float(vv[base + n0 + lane]), xt[ii[base + n0 + lane]], a1);
+            base += n0 + n1;
+        }
+        if (e < sl.L0 && e < len) a0 = fmaf(to_float(vv[base + lane]), xt[ii[base + lane]], a0);
+    } else {
+        for (int e = 0; e < sl.L0; ++e) {
+            const bool c0 = e < len;
+            const int n0 = __popc(__ballot_sync(kFull, c0));
+            if (c0) a0 = fmaf(ring_val<VT>(ring, RING, sl, base + lane), xt[ring_idx(ring, RING, sl, base + lane)], a0);
+            base += n0;
+        }
+    }
+    return a0 + a1;
+}
+
+// Delta_j += c a_ij over the lane's segment (c = 0: the lane only counts its
+// positions).  FP32 additions into shared memory made atomic by
+// compare-and-swap: a lane reads the current sum, and retries only when
+// another lane changed it in between (rare: a slice's segments are distinct
+// rays, and its lanes' positions at one step are distinct columns).  Two steps
+// are in flight per lane.
+__device__ __forceinline__ void cas_add(float* dt, int j, float v, float old) {
+    unsigned* p = reinterpret_cast<unsigned*>(dt) + j;
+    unsigned prev = atomicCAS(p, __float_as_uint(old), __float_as_uint(old + v));
+    while (prev != __float_as_uint(old)) {
+        old = __uint_as_float(prev);
+        prev = atomicCAS(p, prev, __float_as_uint(old + v));
+    }
+}
+
+template <typename VT>
+__device__ __forceinline__ void slice_scatter(const unsigned char* ring, int RING, const Slice& sl,
+                                              int lane, int len, float c, float* dt) {
+    volatile float* vd = dt;
+    const int lact = (c != 0.f) ? len : 0;   // steps this lane adds
+    int base = 0;
+    if (sl.flat) {
+        const VT* vv = reinterpret_cast<const VT*>(ring + sl.vpos);
+        const unsigned short* ii = reinterpret_cast<const unsigned short*>(ring + sl.ipos);
+        int e = 0;
+        for (; e + 1 < sl.L0; e += 2) {
+            const int n0 = __popc(__ballot_sync(kFull, e < len));
+            const int n1 = __popc(__ballot_sync(kFull, e + 1 < len));
+            const bool c0 = e < lact, c1 = e + 1 < lact;
+            float v0 = 0.f, v1 = 0.f, o0 = 0.f, o1 = 0.f;
+            int j0 = 0, j1 = 0;
+            if (c0) {
+                j0 = ii[base + lane];
+                v0 = c * to_float(vv[base + lane]);
+            }
+            if (c1) {
+                j1 = ii[base + n0 + lane];
+                v1 = c * to_float(vv[base + n0 + lane]);
+            }
+            if (c0) o0 = vd[j0];
+            if (c1) o1 = vd[j1];
+            if (c0) cas_add(dt, j0, v0, o0);
+            if (c1) cas_add(dt, j1, v1, o1);
+            base += n0 + n1;
+        }
+        if (e < sl.L0 && e < lact) {
+            const int j0 = ii[base + lane];
+            cas_add(dt, j0, c * to_float(vv[base + lane]), vd[j0]);
+        }
+    } else {
+        for (int e = 0; e < sl.L0; ++e) {
+            const int n0 = __popc(__ballot_sync(kFull, e < len));
+            if (e < lact) {
+                const int j0 = ring_idx(ring, RING, sl, base + lane);
+                cas_add(dt, j0, c * ring_val<VT>(ring, RING, sl, base + lane), vd[j0]);
+            }
+            base += n0;
+        }
+    }
 }
 
 // Warp roles of one CTA (tile b):
-//   warp 0, lane 0   producer: streams the tile's bytes into the ring;
-//   warp 0, lane 1   watcher: raises chunk k's grid counter once every
-//                    phase-1 warp of the CTA finished it (one fence per batch
-//                    of chunks), and publishes to the CTA how many chunks are
-//                    complete on the whole grid;
-//   W1 warps         phase 1: partial dot products, one FP32 L2 reduction per
-//                    segment;
+//   warp 0 (lane 0)  producer: streams the tile's bytes into the ring, at
+//                    most kTileQ chunks ahead of the scatter;
+//   warp 1           watcher: once every phase-1 warp of the CTA finished a
+//                    chunk, one fence and a relaxed increment of the chunk's
+//                    grid counter (several chunks share a fence); the lanes
+//                    poll up to 32 counters at once and pass the chunks that
+//                    are complete on the whole grid to the coefficient warps;
+//   W1 warps         phase 1: partial dot products of slices, one FP32 L2
+//                    reduction per segment;
 //   NC warps         coefficients: for grid-complete chunks (chunk k by warp
 //                    k mod NC), c_i of every segment from the complete r_i,
 //                    into a shared-memory slot of CQ, and the proximity terms;
 //   W2 warps         scatter: Delta_j += c_i a_ij; the box step at the end of
 //                    each block.
-// Hand-offs inside the CTA are release / acquire operations on shared-memory
-// words; across CTAs, relaxed reductions after one fence by the watcher and
-// acquire loads of the counters.
-template <typename VT, int G>
+// Every hand-off inside the CTA is an mbarrier of a ring of kTileQ slots
+// (chunk k uses slot k mod kTileQ, phase parity (k / kTileQ) & 1): arrive
+// releases and try_wait acquires at CTA scope, and a waiting warp sleeps in
+// hardware instead of polling.  No role can run kTileQ chunks ahead of the
+// scatter, so a slot's barrier never completes a phase its waiter has not
+// seen yet.
+template <typename VT>
 __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     if (a.st[0].stopped) return;   // uniform over the grid: nothing is touched
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ volatile int abort_flag;
-    __shared__ volatile int xver;                     // blocks whose box step is done
-    __shared__ volatile int gdone;                    // chunks complete on the grid
     __shared__ volatile int stage_piece[kTileMaxStages];
-    __shared__ volatile int p1done[kTileMaxWarps];    // chunks phase-1 warp w finished
-    __shared__ volatile int p2done[kTileMaxWarps];    // chunks scatter warp w finished
-    __shared__ volatile int ctag[kTileMaxCQ];         // k + 1: slot holds chunk k's coefficients
+    __shared__ __align__(8) uint64_t bar_p1[kTileQ];   // W1 arrivals: phase 1 of chunk k done
+    __shared__ __align__(8) uint64_t bar_g[kTileQ];    // 1 arrival: chunk k complete on the grid
+    __shared__ __align__(8) uint64_t bar_c[kTileQ];    // 1 arrival: chunk k's coefficients in their slot
+    __shared__ __align__(8) uint64_t bar_s[kTileQ];    // W2 arrivals: chunk k scattered
+    __shared__ __align__(8) uint64_t bar_x;            // 1 arrival per block: its box step done
     __shared__ double prox_w[kTileMaxWarps];
     __shared__ int last_s;
     const int RING = a.stages * a.piece;
@@ -216,11 +311,11 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     float* xt = reinterpret_cast<float*>(smraw + RING);
     float* dt = xt + a.tile_cap;
     int* scoff = reinterpret_cast<int*>(dt + a.tile_cap);   // K + 1 chunk offsets
-    int* snseg = scoff + (a.K + 1);                         // K segment counts
-    int* sblk = snseg + a.K;                                // K blocks
-    float* cbuf = reinterpret_cast<float*>(sblk + a.K);     // CQ x maxseg coefficients
+    int* snsl = scoff + (a.K + 1);                          // K slice counts
+    int* sblk = snsl + a.K;                                 // K blocks
+    float* cbuf = reinterpret_cast<float*>(sblk + a.K);     // CQ x cstride coefficients
     uint64_t* full = reinterpret_cast<uint64_t*>(
-        (reinterpret_cast<uintptr_t>(cbuf + (size_t)a.cq * a.maxseg) + 15) & ~uintptr_t(15));
+        (reinterpret_cast<uintptr_t>(cbuf + (size_t)a.cq * a.cstride) + 15) & ~uintptr_t(15));
     const int b = blockIdx.x, tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int W1 = a.W1, NC = a.NC, W2 = a.W2, CQ = a.cq;
@@ -243,24 +338,24 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             dt[j] = 0.f;
         }
         const int* gco = a.coff + (size_t)b * (a.K + 1);
-        const int* gns = a.nseg + (size_t)b * a.K;
+        const int* gns = a.nsl + (size_t)b * a.K;
         for (int k = tid; k <= a.K; k += blockDim.x) scoff[k] = gco[k];
         for (int k = tid; k < a.K; k += blockDim.x) {
-            snseg[k] = gns[k];
+            snsl[k] = gns[k];
             sblk[k] = a.chunk_blk[k];
         }
-        if (tid < kTileMaxWarps) {
-            p1done[tid] = 0;
-            p2done[tid] = 0;
-            prox_w[tid] = 0.0;
-        }
-        if (tid < kTileMaxCQ) ctag[tid] = 0;
+        if (tid < kTileMaxWarps) prox_w[tid] = 0.0;
         if (tid < kTileMaxStages) stage_piece[tid] = -1;
         if (tid == 0) {
             for (int s = 0; s < a.stages; ++s) tma::mbar_init(&full[s], 1);
+            for (int q = 0; q < kTileQ; ++q) {
+                tma::mbar_init(&bar_p1[q], W1);
+                tma::mbar_init(&bar_g[q], 1);
+                tma::mbar_init(&bar_c[q], 1);
+                tma::mbar_init(&bar_s[q], W2);
+            }
+            tma::mbar_init(&bar_x, 1);
             abort_flag = 0;
-            xver = 0;
-            gdone = 0;
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
     }
@@ -275,49 +370,38 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     };
 
     if (warp == 0) {
-        if (lane == 0 && len_stream > 0) {
-            // ---- producer: one lane streams the tile's bytes into the ring
+        if (lane == 0) {
+            // ---- producer
+            long long st_t0 = TSTAT_CLOCK(), st_w = 0;
+            (void)st_t0;
             const unsigned char* src = a.stream + a.base[b];
             const uint64_t pol = tma::policy_evict_first();
             const int npieces = (len_stream + a.piece - 1) >> ts;
             int issued = 0;
-            long long st_t0 = TSTAT_CLOCK(), st_w = 0;
-            (void)st_t0;
-            int rel_chunk = 0;   // chunks every scatter warp has finished (cached)
-            for (int q = 0; q < npieces; ++q) {
-                const int s = q % a.stages;
-                if (q >= a.stages) {
-                    // the stage's previous piece must be done with: every chunk
-                    // overlapping it finished its scatter
-                    const int need = (q - a.stages + 1) << ts;
-                    if (scoff[rel_chunk] < need) {
-                        const long long t0 = clock64();
-                        st_w -= TSTAT_CLOCK();
-                        bool ok = true;
-                        while (true) {
-                            int mn = 0x7fffffff;
-                            for (int w = 0; w < W2; ++w) mn = min(mn, ld_acquire_cta(&p2done[w]));
-                            rel_chunk = mn;
-                            if (scoff[rel_chunk] >= need) break;
-                            if (abort_flag || *reinterpret_cast<volatile int*>(a.err) ||
-                                clock64() - t0 > limit) {
-                                ok = false;
-                                break;
-                            }
-                            __nanosleep(64);
-                        }
-                        st_w += TSTAT_CLOCK();
-                        if (!ok) {
-                            give_up(3);
-                            break;
-                        }
-                    }
+            int rel = 0;   // chunks whose scatter finished
+            int jq = 0;    // chunk holding the last byte of the piece
+            bool ok = true;
+            for (int q = 0; q < npieces && ok; ++q) {
+                const int end = min((q + 1) << ts, len_stream);
+                while (jq + 1 < a.K && scoff[jq + 1] < end) ++jq;
+                // ring space (the stage's previous piece read by every role)
+                // and at most kTileQ chunks between the scatter and the newest data
+                const int need = (q >= a.stages) ? (q - a.stages + 1) << ts : 0;
+                while (ok && (scoff[rel] < need || jq >= rel + kTileQ)) {
+                    st_w -= TSTAT_CLOCK();
+                    ok = tma::mbar_wait(&bar_s[rel % kTileQ], (rel / kTileQ) & 1, &abort_flag, limit);
+                    st_w += TSTAT_CLOCK();
+                    if (ok) ++rel;
                 }
-                const int off = q << ts;
-                const uint32_t bytes = (uint32_t)min(a.piece, len_stream - off);
+                if (!ok) {
+                    give_up(3);
+                    break;
+                }
+                const int s = q % a.stages;
+                const uint32_t bytes = (uint32_t)(end - (q << ts));
                 stage_piece[s] = q;
                 tma::mbar_arrive_expect_tx(&full[s], bytes);
-                tma::bulk_g2s(ring + ((size_t)s << ts), src + off, bytes, &full[s], pol);
+                tma::bulk_g2s(ring + ((size_t)s << ts), src + (q << ts), bytes, &full[s], pol);
                 issued = q + 1;
             }
             TSTAT_ADD(6, st_w);
@@ -326,49 +410,74 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             volatile int never = 0;
             for (int q = (issued > a.stages ? issued - a.stages : 0); q < issued; ++q)
                 tma::mbar_wait(&full[q % a.stages], (q / a.stages) & 1, &never, kTileDrainCycles);
-        } else if (lane == 1) {
-            // ---- watcher
-            int sig = 0, done = 0;
-            long long t0 = clock64();
-            const unsigned P = gridDim.x;
-            long long st_t0 = TSTAT_CLOCK(), st_idle = 0;
-            (void)st_t0;
-            while (done < a.K) {
-                bool prog = false;
-                int m1 = a.K;
-                for (int w = 0; w < W1; ++w) m1 = min(m1, ld_acquire_cta(&p1done[w]));
-                if (m1 > sig) {
-                    // the phase-1 warps' reductions (ordered before their
-                    // release of p1done) reach the GPU before the counters
-                    __threadfence();
-                    for (int k = sig; k < m1; ++k) red_add_u32_gpu(a.cnt + k, 1u);
-                    sig = m1;
-                    prog = true;
-                }
-                while (done < sig && ld_acquire_gpu(a.cnt + done) >= P) {
-                    ++done;
-                    prog = true;
-                }
-                if (prog) {
-                    st_release_cta(&gdone, done);
-                    t0 = clock64();
-                } else {
-                    if (abort_flag || *reinterpret_cast<volatile int*>(a.err) || clock64() - t0 > limit) {
-                        give_up(3);
-                        break;
+        }
+    } else if (warp == 1) {
+        // ---- watcher
+        long long st_t0 = TSTAT_CLOCK(), st_idle = 0;
+        (void)st_t0;
+        const unsigned P = gridDim.x;
+        int sig = 0, done = 0;
+        long long t0 = clock64();
+        while (done < a.K) {
+            bool prog = false;
+            // local completions: the next chunks whose phase 1 is done here
+            int nsig = sig;
+            if (nsig < a.K) {
+                bool got = true;
+                if (lane == 0) got = mbar_try_wait_ns(&bar_p1[nsig % kTileQ], (nsig / kTileQ) & 1, 500);
+                got = __shfl_sync(kFull, got, 0);
+                if (got) {
+                    ++nsig;
+                    // more completed chunks share the fence
+                    while (nsig < a.K && nsig < sig + 32) {
+                        bool more = false;
+                        if (lane == 0) more = mbar_try_wait_ns(&bar_p1[nsig % kTileQ], (nsig / kTileQ) & 1, 0);
+                        if (!__shfl_sync(kFull, more, 0)) break;
+                        ++nsig;
                     }
-                    st_idle += 1;
-                    __nanosleep(32);
                 }
             }
+            if (nsig > sig) {
+                // the phase-1 warps' reductions, ordered before their
+                // arrivals, reach the GPU before the counters move
+                fence_acq_rel_gpu();
+                if (lane < nsig - sig) red_add_u32_gpu(a.cnt + sig + lane, 1u);
+                sig = nsig;
+                prog = true;
+            }
+            // grid completions: up to 32 counters at once
+            if (done < sig) {
+                const int j = done + lane;
+                bool c = false;
+                if (j < sig) c = ld_acquire_gpu(a.cnt + j) >= P;
+                const unsigned m = __ballot_sync(kFull, c);
+                const int nnew = (m == kFull) ? 32 : __ffs(~m) - 1;
+                __syncwarp();
+                if (nnew > 0) {
+                    if (lane == 0)
+                        for (int t = 0; t < nnew; ++t) tma::mbar_arrive(&bar_g[(done + t) % kTileQ]);
+                    done += nnew;
+                    prog = true;
+                }
+            }
+            if (prog) {
+                t0 = clock64();
+            } else {
+                st_idle += 1;
+                if (abort_flag || *reinterpret_cast<volatile int*>(a.err) || clock64() - t0 > limit) {
+                    if (lane == 0) give_up(3);
+                    break;
+                }
+                if (sig >= a.K) __nanosleep(200);
+            }
+        }
+        if (lane == 0) {
             TSTAT_ADD(8, st_idle);
             TSTAT_ADD(9, TSTAT_CLOCK() - st_t0);
         }
-    } else if (warp <= W1) {
-        // ---- phase 1: partial dot products of the tile's segments
-        const int w1 = warp - 1;
-        constexpr int GPW = 32 / G;
-        const int gi = lane / G, gl = lane % G;
+    } else if (warp <= 1 + W1) {
+        // ---- phase 1: partial dot products of the tile's slices
+        const int w1 = warp - 2;
         bool ok = true;
         int cur_blk = 0;
         long long st_t0 = TSTAT_CLOCK(), st_w = 0;
@@ -380,7 +489,7 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 // the next block's dot products use x after the block's box step
                 cur_blk = blk;
                 if (ok) {
-                    ok = warp_wait([&] { return ld_acquire_cta(&xver) >= blk; }, &abort_flag, a.err, limit);
+                    ok = warp_bar_wait(&bar_x, (blk - 1) & 1, &abort_flag, a.err, limit);
                     if (!ok && lane == 0) give_up(3);
                 }
             }
@@ -388,69 +497,46 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             if (ok && c1 > c0) {
                 for (int q = c0 >> ts; ok && q <= (c1 - 1) >> ts; ++q) {
                     const int s = q % a.stages;
-                    ok = warp_wait([&] { return stage_piece[s] == q; }, &abort_flag, a.err, limit);
-                    if (ok) ok = __all_sync(0xffffffffu, tma::mbar_wait(&full[s], (q / a.stages) & 1,
-                                                                        &abort_flag, limit));
+                    bool w = true;
+                    if (stage_piece[s] != q) {
+                        const long long t0 = clock64();
+                        int ns = 64;
+                        while (stage_piece[s] != q) {
+                            if (abort_flag || clock64() - t0 > limit) {
+                                w = false;
+                                break;
+                            }
+                            __nanosleep(ns);
+                            ns = min(ns * 2, 1024);
+                        }
+                    }
+                    if (w) w = tma::mbar_wait(&full[s], (q / a.stages) & 1, &abort_flag, limit);
+                    ok = __all_sync(kFull, w);
                 }
                 if (!ok && lane == 0) give_up(3);
             }
             st_w += TSTAT_CLOCK();
             if (ok && c1 > c0) {
-                const int nseg = snseg[k];
+                const int nsl = snsl[k];
                 const int rc = c0 % RING;
-                for (int base = w1 * GPW; base < nseg; base += W1 * GPW) {
-                    const int sg = base + gi;
-                    float dot = 0.f;
-                    int row = -1;
-                    if (sg < nseg) {
-                        const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
-                        row = (int)(d.x & 0x7fffffffu);
-                        const int off = 4 * (int)(d.y & 0xffffu), len = (int)(d.y >> 16);
-                        const int vp = wrap(rc + off, RING);
-                        const int ip = wrap(vp + (int)sizeof(VT) * len, RING);
-                        float d0 = 0.f, d1 = 0.f;
-                        if (ip + 2 * len <= RING && vp + (int)sizeof(VT) * len <= RING) {
-                            const VT* vv = reinterpret_cast<const VT*>(ring + vp);
-                            const unsigned short* ii = reinterpret_cast<const unsigned short*>(ring + ip);
-                            int e = gl;
-                            for (; e + G < len; e += 2 * G) {
-                                d0 = fmaf(to_float(vv[e]), xt[ii[e]], d0);
-                                d1 = fmaf(to_float(vv[e + G]), xt[ii[e + G]], d1);
-                            }
-                            if (e < len) d0 = fmaf(to_float(vv[e]), xt[ii[e]], d0);
-                        } else {
-                            for (int e = gl; e < len; e += G) {
-                                const float v = to_float(*reinterpret_cast<const VT*>(
-                                    ring + wrap(vp + (int)sizeof(VT) * e, RING)));
-                                const int j = *reinterpret_cast<const unsigned short*>(
-                                    ring + wrap(ip + 2 * e, RING));
-                                d0 = fmaf(v, xt[j], d0);
-                            }
-                        }
-                        dot = d0 + d1;
-                    }
-#pragma unroll
-                    for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                    // lane 0 issues the warp's reductions: its release of
-                    // p1done then orders all of them
-#pragma unroll
-                    for (int g2 = 0; g2 < GPW; ++g2) {
-                        const float pv = __shfl_sync(0xffffffffu, dot, g2 * G);
-                        const int pr = __shfl_sync(0xffffffffu, row, g2 * G);
-                        if (lane == 0 && pr >= 0) red_add_gpu(r_cur + pr, pv);
-                    }
+                for (int s = w1; s < nsl; s += W1) {
+                    int row, len;
+                    const Slice sl = slice_at<VT>(ring, RING, rc, s, lane, &row, &len);
+                    const float dot = slice_dot<VT>(ring, RING, sl, lane, len, xt);
+                    if (lane < sl.nl) red_add_gpu(r_cur + (row & 0x7fffffff), dot);
                 }
             }
+            // every lane's reductions precede the warp's arrival
             __syncwarp();
-            if (ok && lane == 0) st_release_cta(&p1done[w1], k + 1);
+            if (ok && lane == 0) tma::mbar_arrive(&bar_p1[k % kTileQ]);
         }
         if (lane == 0) {
             TSTAT_ADD(0, st_w);
             TSTAT_ADD(1, TSTAT_CLOCK() - st_t0);
         }
-    } else if (warp <= W1 + NC) {
+    } else if (warp <= 1 + W1 + NC) {
         // ---- coefficients of grid-complete chunks
-        const int wc = warp - 1 - W1;
+        const int wc = warp - 2 - W1;
         double pacc = 0.0;
         bool ok = true;
         long long st_t0 = TSTAT_CLOCK(), st_w = 0;
@@ -458,46 +544,56 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
         for (int k = wc; k < a.K && ok; k += NC) {
             const int slot = k % CQ;
             st_w -= TSTAT_CLOCK();
+            // the slot's previous chunk is scattered, and chunk k is complete
             if (k >= CQ)
-                ok = warp_wait([&] { return ld_acquire_cta(&p2done[lane < W2 ? lane : 0]) > k - CQ || lane >= W2; },
-                               &abort_flag, a.err, limit);
-            if (ok) ok = warp_wait([&] { return ld_acquire_cta(&gdone) > k; }, &abort_flag, a.err, limit);
+                ok = warp_bar_wait(&bar_s[(k - CQ) % kTileQ], ((k - CQ) / kTileQ) & 1, &abort_flag,
+                                   a.err, limit);
+            if (ok) ok = warp_bar_wait(&bar_g[k % kTileQ], (k / kTileQ) & 1, &abort_flag, a.err, limit);
             st_w += TSTAT_CLOCK();
             if (!ok) {
                 if (lane == 0) give_up(3);
                 break;
             }
-            const int c0 = scoff[k], nseg = snseg[k];
+            const int c0 = scoff[k], nsl = snsl[k];
             const int rc = c0 % RING;
             const double scale = a.blk_scale[sblk[k]];
-            float* cb = cbuf + (size_t)slot * a.maxseg;
-            for (int s0 = 0; s0 < nseg; s0 += 4 * 32) {
-                uint2 d[4];
+            float* cb = cbuf + (size_t)slot * a.cstride;
+            for (int s0 = 0; s0 < nsl; s0 += 4) {
+                int row[4];
+                bool has[4];
                 float ri[4], li[4], ui[4], wi[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int sg = s0 + u * 32 + lane;
-                    if (sg < nseg) {
-                        d[u] = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
-                        const int row = (int)(d[u].x & 0x7fffffffu);
-                        ri[u] = ld_relaxed_gpu(r_cur + row);
-                        li[u] = __ldg(a.l + row);
-                        ui[u] = __ldg(a.u + row);
-                        wi[u] = __ldg(a.wr + row);
+                    has[u] = false;
+                    row[u] = 0;
+                    if (s0 + u < nsl) {
+                        const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * (s0 + u), RING));
+                        const int nl = (int)(d.y & 63u);
+                        const int sp = wrap(rc + 4 * (int)d.x, RING);
+                        if (lane < nl) {
+                            has[u] = true;
+                            row[u] = *reinterpret_cast<const int*>(ring + wrap(sp + 4 * lane, RING));
+                        }
+                    }
+                    if (has[u]) {
+                        const int rw = row[u] & 0x7fffffff;
+                        ri[u] = ld_relaxed_gpu(r_cur + rw);
+                        li[u] = __ldg(a.l + rw);
+                        ui[u] = __ldg(a.u + rw);
+                        wi[u] = __ldg(a.wr + rw);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int sg = s0 + u * 32 + lane;
-                    if (sg < nseg) {
+                    if (has[u]) {
                         const float dd = clampf(ri[u], li[u], ui[u]) - ri[u];
-                        cb[sg] = a.lam * wi[u] * dd;
-                        if (d[u].x & 0x80000000u) pacc += (double)dd * (double)dd * (double)wi[u] * scale;
+                        cb[(s0 + u) * 32 + lane] = a.lam * wi[u] * dd;
+                        if (row[u] < 0) pacc += (double)dd * (double)dd * (double)wi[u] * scale;
                     }
                 }
             }
             __syncwarp();
-            if (lane == 0) st_release_cta(&ctag[slot], k + 1);
+            if (lane == 0) tma::mbar_arrive(&bar_c[k % kTileQ]);
         }
         pacc = warp_sum(pacc);
         if (lane == 0) {
@@ -507,10 +603,8 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
         }
     } else {
         // ---- scatter into Delta, and the box step at the end of each block
-        const int w2 = warp - 1 - W1 - NC;
-        constexpr int GPW = 32 / G;
-        const int gi = lane / G, gl = lane % G;
-        const int t2 = tid - 32 * (1 + W1 + NC);   // 0 .. 32 W2 - 1
+        const int w2 = warp - 2 - W1 - NC;
+        const int t2 = tid - 32 * (2 + W1 + NC);   // 0 .. 32 W2 - 1
         bool ok = true;
         long long st_t0 = TSTAT_CLOCK(), st_w = 0;
         (void)st_t0;
@@ -519,31 +613,23 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             const int slot = k % CQ;
             st_w -= TSTAT_CLOCK();
             if (ok) {
-                ok = warp_wait([&] { return ld_acquire_cta(&ctag[slot]) > k; }, &abort_flag, a.err, limit);
+                ok = warp_bar_wait(&bar_c[k % kTileQ], (k / kTileQ) & 1, &abort_flag, a.err, limit);
                 if (!ok && lane == 0) give_up(3);
             }
             st_w += TSTAT_CLOCK();
-            const int c0 = scoff[k], nseg = snseg[k];
-            if (ok && nseg > 0) {
+            const int c0 = scoff[k], nsl = snsl[k];
+            if (ok && nsl > 0) {
                 const int rc = c0 % RING;
-                const float* cb = cbuf + (size_t)slot * a.maxseg;
-                for (int base = w2 * GPW; base < nseg; base += W2 * GPW) {
-                    const int sg = base + gi;
-                    if (sg < nseg) {
-                        const float c = cb[sg];
-                        if (c != 0.f) {
-                            const uint2 d = *reinterpret_cast<const uint2*>(ring + wrap(rc + 8 * sg, RING));
-                            const int off = 4 * (int)(d.y & 0xffffu), len = (int)(d.y >> 16);
-                            const int vp = wrap(rc + off, RING);
-                            const int ip = wrap(vp + (int)sizeof(VT) * len, RING);
-                            for (int e = gl; e < len; e += kCasBatch * G)
-                                scatter_batch<VT, G>(ring, RING, vp, ip, e, len, c, dt);
-                        }
-                    }
+                const float* cb = cbuf + (size_t)slot * a.cstride;
+                for (int s = w2; s < nsl; s += W2) {
+                    int row, len;
+                    const Slice sl = slice_at<VT>(ring, RING, rc, s, lane, &row, &len);
+                    const float c = (lane < sl.nl) ? cb[s * 32 + lane] : 0.f;
+                    if (__any_sync(kFull, c != 0.f)) slice_scatter<VT>(ring, RING, sl, lane, len, c, dt);
                 }
             }
             __syncwarp();
-            if (lane == 0) st_release_cta(&p2done[w2], k + 1);
+            if (lane == 0) tma::mbar_arrive(&bar_s[k % kTileQ]);
             if (k + 1 == a.K || sblk[k + 1] != blk) {
                 // end of the block: the box step on the tile (every scatter
                 // warp has finished the block's chunks)
@@ -562,7 +648,7 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                     if (last) a.x[g] = v;
                 }
                 named_sync(1, 32 * W2);
-                if (t2 == 0) st_release_cta(&xver, blk + 1);
+                if (t2 == 0 && !last) tma::mbar_arrive(&bar_x);
             }
         }
         if (lane == 0) {
@@ -595,58 +681,65 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     }
 }
 
-// Fill of the tile streams: one warp per segment writes its descriptor and
-// copies its values and tile-local indices.
+// Fill of the tile streams: one warp per slice writes the slice's table
+// entry, its rows and lengths, and its values and tile-local indices step by
+// step (lane j = the slice's j-th segment, longest first).
 template <typename VT>
-__global__ void k_tile_fill(const TileSegRec* segs, long long nsegs, const VT* val, const int* col,
-                            const unsigned short* local_of, unsigned char* stream) {
+__global__ void k_tile_fill(const TileSliceRec* slices, long long nslices, const TileLaneRec* lanes,
+                            const VT* val, const int* col, const unsigned short* local_of,
+                            unsigned char* stream) {
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (w >= nsegs) return;
-    const TileSegRec r = segs[w];
+    if (w >= nslices) return;
+    const TileSliceRec r = slices[w];
     unsigned char* chunk = stream + r.chunk_start;
     if (lane == 0) {
         uint2 d;
-        d.x = (unsigned)r.row_flag;
-        d.y = (unsigned)r.off4 | ((unsigned)r.len << 16);
+        d.x = (unsigned)r.off4;
+        d.y = (unsigned)r.nl | ((unsigned)r.E << 6);
         *reinterpret_cast<uint2*>(chunk + 8LL * r.sidx) = d;
     }
-    VT* dv = reinterpret_cast<VT*>(chunk + 4LL * r.off4);
-    unsigned short* di = reinterpret_cast<unsigned short*>(chunk + 4LL * r.off4 + sizeof(VT) * r.len);
-    for (int e = lane; e < r.len; e += 32) {
-        dv[e] = val[r.e0 + e];
-        di[e] = local_of[col[r.e0 + e]];
+    unsigned char* sp = chunk + 4LL * r.off4;
+    TileLaneRec ln = {0, 0, 0};
+    if (lane < r.nl) {
+        ln = lanes[r.first + lane];
+        reinterpret_cast<int*>(sp)[lane] = ln.row_flag;
+        reinterpret_cast<unsigned short*>(sp + 4 * r.nl)[lane] = (unsigned short)ln.len;
+    }
+    VT* dv = reinterpret_cast<VT*>(sp + ((6 * r.nl + 3) & ~3));
+    unsigned short* di = reinterpret_cast<unsigned short*>(sp + ((6 * r.nl + 3) & ~3) + sizeof(VT) * r.E);
+    const int L0 = __shfl_sync(kFull, ln.len, 0);
+    int base = 0;
+    for (int e = 0; e < L0; ++e) {
+        const bool act = e < ln.len;
+        const int n = __popc(__ballot_sync(kFull, act));
+        if (act) {
+            dv[base + lane] = val[ln.e0 + e];
+            di[base + lane] = local_of[col[ln.e0 + e]];
+        }
+        base += n;
     }
 }
 
 using TileFn = void (*)(TileArgs);
 
-template <typename VT>
-TileFn tile_fn_g(int G) {
-    switch (G) {
-        case 8: return k_tile_sweep<VT, 8>;
-        case 16: return k_tile_sweep<VT, 16>;
-        default: return k_tile_sweep<VT, 32>;
-    }
-}
-
-TileFn tile_fn(suppy_dtype dt, int G) {
-    if (dt == SUPPY_F32) return tile_fn_g<float>(G);
-    if (dt == SUPPY_BF16) return tile_fn_g<__nv_bfloat16>(G);
-    return tile_fn_g<__half>(G);
+TileFn tile_fn(suppy_dtype dt) {
+    if (dt == SUPPY_F32) return k_tile_sweep<float>;
+    if (dt == SUPPY_BF16) return k_tile_sweep<__nv_bfloat16>;
+    return k_tile_sweep<__half>;
 }
 
 }  // namespace
 
-size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int maxseg) {
+size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int cstride) {
     size_t b = (size_t)ring_bytes + 8 * (size_t)tile_cap + 4 * (3 * (size_t)K + 1) +
-               4 * (size_t)cq * maxseg;
+               4 * (size_t)cq * cstride;
     b = (b + 15) & ~(size_t)15;
     return b + 8 * (size_t)stages;
 }
 
-int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem) {
-    TileFn f = tile_fn(dt, G);
+int tile_blocks_per_sm(suppy_dtype dt, int threads, size_t smem) {
+    TileFn f = tile_fn(dt);
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     int nb = 0;
@@ -654,18 +747,18 @@ int tile_blocks_per_sm(suppy_dtype dt, int G, int threads, size_t smem) {
     return nb;
 }
 
-cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid, size_t smem,
+cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int grid, size_t smem,
                               cudaStream_t s) {
-    if (a.W1 < 1 || a.W2 < 1 || a.NC < 1 || 1 + a.W1 + a.NC + a.W2 > kTileMaxWarps ||
-        a.cq < a.NC || a.cq > kTileMaxCQ || a.stages < 2 ||
-        a.stages > kTileMaxStages || a.piece < 256 || (a.piece & (a.piece - 1)) || grid < 1)
+    if (a.W1 < 1 || a.W2 < 1 || a.NC < 1 || 2 + a.W1 + a.NC + a.W2 > kTileMaxWarps ||
+        a.cq < a.NC || a.cq > kTileMaxCQ || a.stages < 2 || a.stages > kTileMaxStages ||
+        a.piece < 256 || (a.piece & (a.piece - 1)) || grid < 1)
         return cudaErrorInvalidValue;
-    TileFn f = tile_fn(dt, G);
+    TileFn f = tile_fn(dt);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
-    cfg.blockDim = dim3(32 * (1 + a.W1 + a.NC + a.W2), 1, 1);
+    cfg.blockDim = dim3(32 * (2 + a.W1 + a.NC + a.W2), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -676,22 +769,21 @@ cudaError_t launch_tile_sweep(const TileArgs& a, suppy_dtype dt, int G, int grid
     return cudaLaunchKernelEx(&cfg, f, a);
 }
 
-cudaError_t launch_tile_fill(const TileSegRec* segs, long long nsegs, const void* val,
-                             suppy_dtype dt, const int* col, const unsigned short* local_of,
-                             unsigned char* stream, cudaStream_t s) {
-    if (nsegs <= 0) return cudaSuccess;
-    const long long threads = nsegs * 32;
+cudaError_t launch_tile_fill(const TileSliceRec* slices, long long nslices, const TileLaneRec* lanes,
+                             const void* val, suppy_dtype dt, const int* col,
+                             const unsigned short* local_of, unsigned char* stream, cudaStream_t s) {
+    if (nslices <= 0) return cudaSuccess;
     const int block = 256;
-    const long long grid = (threads + block - 1) / block;
+    const long long grid = (nslices * 32 + block - 1) / block;
     if (dt == SUPPY_F32)
-        k_tile_fill<float><<<(unsigned)grid, block, 0, s>>>(segs, nsegs, static_cast<const float*>(val),
-                                                           col, local_of, stream);
+        k_tile_fill<float><<<(unsigned)grid, block, 0, s>>>(slices, nslices, lanes,
+                                                           static_cast<const float*>(val), col, local_of, stream);
     else if (dt == SUPPY_BF16)
         k_tile_fill<__nv_bfloat16><<<(unsigned)grid, block, 0, s>>>(
-            segs, nsegs, static_cast<const __nv_bfloat16*>(val), col, local_of, stream);
+            slices, nslices, lanes, static_cast<const __nv_bfloat16*>(val), col, local_of, stream);
     else
-        k_tile_fill<__half><<<(unsigned)grid, block, 0, s>>>(segs, nsegs, static_cast<const __half*>(val),
-                                                            col, local_of, stream);
+        k_tile_fill<__half><<<(unsigned)grid, block, 0, s>>>(slices, nslices, lanes,
+                                                            static_cast<const __half*>(val), col, local_of, stream);
     return cudaGetLastError();
 }
 
@@ -806,10 +898,12 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
     out.P = P;
     // ---- segments: runs of a row's consecutive entries in one tile
     struct Run {
-        int tile, row, e0, len;
+        int tile, e0, len;
     };
     std::vector<Run> runs;
     runs.reserve((size_t)in.m * 8);
+    std::vector<int> run_row;            // device row, bit 31 on the row's first run
+    run_row.reserve((size_t)in.m * 8);
     std::vector<long long> row_bytes(in.m, 0);
     std::vector<int> row_run(in.m + 1, 0);
     for (int i = 0; i < in.m; ++i) {
@@ -822,8 +916,9 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
             const int tb = out.tile_of[cp[t]];
             int e = t + 1;
             while (e < len && e - t < in.max_seg && out.tile_of[cp[e]] == tb) ++e;
-            runs.push_back(Run{tb, i, in.row_start[i] + t, e - t});
-            row_bytes[i] += 8 + (((long long)(e - t) * (vs + 2) + 3) & ~3LL);
+            runs.push_back(Run{tb, in.row_start[i] + t, e - t});
+            run_row.push_back(t == 0 ? (int)((unsigned)i | 0x80000000u) : i);
+            row_bytes[i] += 6 + (long long)(e - t) * (vs + 2);
             t = e;
         }
     }
@@ -832,68 +927,121 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         why = "tile plan: too many segments";
         return false;
     }
-    // ---- chunks: consecutive rows inside a block, about `target` stream
-    // bytes per CTA each; halved while some tile's chunk exceeds max_chunk
+    // ---- row groups: 32 consecutive rows of a block (neighbouring rays of
+    // one direction for a ray-ordered matrix), the groups of a block in a
+    // scattered order (a stride near ng / golden ratio, coprime to ng), so
+    // that every chunk holds rays of every direction and position and every
+    // tile gets about the same share of it
+    constexpr int kGroup = 32;
     const int nblk = (int)in.seg_start.size() - 1;
-    // rows of a block in a scattered order (a stride near len / golden ratio,
-    // coprime to the block length): each chunk then holds rays of every
-    // direction and position, so every tile gets about the same share of it
-    std::vector<int> order(in.m);
-    for (int t = 0; t < nblk; ++t) {
-        const long long r0 = in.seg_start[t], len = in.seg_start[t + 1] - r0;
-        long long S = std::max<long long>(1, std::llround((double)len * 0.6180339887498949));
-        while (len > 1 && std::gcd(S, len) != 1) ++S;
-        for (long long j = 0; j < len; ++j) order[r0 + j] = (int)(r0 + (j * S) % std::max<long long>(len, 1));
-    }
-    long long target = (long long)in.chunk_target * P;
-    for (int attempt = 0; attempt < 12; ++attempt) {
-        std::vector<int> ck;      // positions in `order` where the chunks start
-        std::vector<int> cblk;
+    std::vector<int> order(in.m);        // rows, group by group
+    std::vector<int> gstart;             // positions in `order` where the groups start
+    std::vector<int> gblk;
+    {
+        int pos = 0;
         for (int t = 0; t < nblk; ++t) {
             const int r0 = in.seg_start[t], r1 = in.seg_start[t + 1];
-            long long acc = 0;
-            int start = r0;
-            for (int j = r0; j < r1; ++j) {
-                acc += row_bytes[order[j]];
-                if (acc >= target) {
-                    ck.push_back(start);
-                    cblk.push_back(t);
-                    start = j + 1;
-                    acc = 0;
-                }
-            }
-            if (start < r1 || r0 == r1) {
-                ck.push_back(start);
-                cblk.push_back(t);
+            const long long ng = (r1 - r0 + kGroup - 1) / kGroup;
+            long long S = std::max<long long>(1, std::llround((double)ng * 0.6180339887498949));
+            while (ng > 1 && std::gcd(S, ng) != 1) ++S;
+            for (long long g = 0; g < ng; ++g) {
+                const long long q = (g * S) % std::max<long long>(ng, 1);
+                gstart.push_back(pos);
+                gblk.push_back(t);
+                for (int i = r0 + (int)q * kGroup; i < std::min(r1, r0 + (int)(q + 1) * kGroup); ++i)
+                    order[pos++] = i;
             }
         }
+        gstart.push_back(pos);
+    }
+    const int ngroups = (int)gblk.size();
+    // ---- chunks: consecutive groups inside a block, about `target` stream
+    // bytes per CTA each; halved while some tile's chunk exceeds max_chunk or
+    // max_slices
+    auto slice_bytes = [&](int nl, long long E) {
+        return (((6LL * nl + 3) & ~3LL) + E * (vs + 2) + 15) & ~15LL;
+    };
+    long long target = (long long)in.chunk_target * P;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        std::vector<int> ck;      // group indices where the chunks start
+        std::vector<int> cblk;
+        {
+            long long acc = 0;
+            for (int g = 0; g < ngroups; ++g) {
+                const bool new_blk = (g == 0) || gblk[g] != gblk[g - 1];
+                if (new_blk || acc >= target) {
+                    ck.push_back(g);
+                    cblk.push_back(gblk[g]);
+                    acc = 0;
+                }
+                for (int j = gstart[g]; j < gstart[g + 1]; ++j) acc += row_bytes[order[j]];
+            }
+            // blocks without rows still get a chunk (their box step)
+            std::vector<char> seen(nblk, 0);
+            for (int t : cblk) seen[t] = 1;
+            std::vector<int> ck2, cb2;
+            size_t p2 = 0;
+            for (int t = 0; t < nblk; ++t) {
+                if (!seen[t]) {
+                    ck2.push_back(p2 < ck.size() ? ck[p2] : ngroups);
+                    cb2.push_back(t);
+                    continue;
+                }
+                while (p2 < ck.size() && cblk[p2] == t) {
+                    ck2.push_back(ck[p2]);
+                    cb2.push_back(t);
+                    ++p2;
+                }
+            }
+            ck.swap(ck2);
+            cblk.swap(cb2);
+        }
         const int K = (int)ck.size();
-        ck.push_back(in.m);
+        ck.push_back(ngroups);
         if (K > in.max_chunks) {
             why = "tile plan: more chunks than the kernel's tables hold";
             return false;
         }
-        std::vector<int> nseg((size_t)P * K, 0);
-        std::vector<long long> dbytes((size_t)P * K, 0);
-        for (int k = 0; k < K; ++k)
-            for (int j = ck[k]; j < ck[k + 1]; ++j) {
-                const int i = order[j];
-                for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
-                    const Run& u = runs[r];
-                    nseg[(size_t)u.tile * K + k] += 1;
-                    dbytes[(size_t)u.tile * K + k] += ((long long)u.len * (vs + 2) + 3) & ~3LL;
-                }
-            }
+        // per (tile, chunk): the runs in group order, cut into slices of 32
+        std::vector<int> nsl((size_t)P * K, 0);
+        std::vector<long long> csize((size_t)P * K, 0);
         long long worst = 0;
-        int worst_nseg = 0;
-        std::vector<long long> csize((size_t)P * K);
-        for (size_t q = 0; q < csize.size(); ++q) {
-            const long long desc = ((long long)nseg[q] * 8 + 15) & ~15LL;
-            csize[q] = (desc + dbytes[q] + 15) & ~15LL;
-            worst = std::max(worst, csize[q]);
-            worst_nseg = std::max(worst_nseg, nseg[q]);
+        int worst_nsl = 0;
+        std::vector<int> cnt(P, 0);
+        std::vector<long long> ent(P, 0);
+        for (int k = 0; k < K; ++k) {
+            for (int p = 0; p < P; ++p) {
+                cnt[p] = 0;
+                ent[p] = 0;
+            }
+            std::vector<long long> body(P, 0);
+            for (int g = ck[k]; g < ck[k + 1]; ++g)
+                for (int j = gstart[g]; j < gstart[g + 1]; ++j) {
+                    const int i = order[j];
+                    for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
+                        const int p = runs[r].tile;
+                        if (cnt[p] == 32) {
+                            body[p] += slice_bytes(32, ent[p]);
+                            nsl[(size_t)p * K + k] += 1;
+                            cnt[p] = 0;
+                            ent[p] = 0;
+                        }
+                        cnt[p] += 1;
+                        ent[p] += runs[r].len;
+                    }
+                }
+            for (int p = 0; p < P; ++p) {
+                if (cnt[p]) {
+                    body[p] += slice_bytes(cnt[p], ent[p]);
+                    nsl[(size_t)p * K + k] += 1;
+                }
+                const size_t q = (size_t)p * K + k;
+                csize[q] = (((long long)nsl[q] * 8 + 15) & ~15LL) + body[p];
+                worst = std::max(worst, csize[q]);
+                worst_nsl = std::max(worst_nsl, nsl[q]);
+            }
         }
-        if (worst > in.max_chunk || worst_nseg > in.max_nseg) {
+        if (worst > in.max_chunk || worst_nsl > in.max_slices) {
             target /= 2;
             if (target < 1024) break;
             continue;
@@ -901,12 +1049,12 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         // ---- offsets
         out.K = K;
         out.chunk_blk = cblk;
-        out.nseg = nseg;
+        out.nsl = nsl;
         out.coff.assign((size_t)P * (K + 1), 0);
         out.base.assign(P, 0);
-        long long tot = 0;
         out.max_chunk = (int)worst;
-        out.max_nseg = worst_nseg;
+        out.max_slices = worst_nsl;
+        long long tot = 0;
         for (int p = 0; p < P; ++p) {
             out.base[p] = tot;
             long long o = 0;
@@ -922,27 +1070,53 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
             tot += o;
         }
         out.bytes = tot;
-        // ---- segment records in row order (descriptors first, then data)
-        std::vector<int> sidx((size_t)P * K, 0);
-        std::vector<long long> dpos((size_t)P * K);
-        for (size_t q = 0; q < dpos.size(); ++q) dpos[q] = ((long long)nseg[q] * 8 + 15) & ~15LL;
-        out.segs.resize(runs.size());
-        for (int k = 0; k < K; ++k) {
-            for (int j = ck[k]; j < ck[k + 1]; ++j) {
-                const int i = order[j];
-                for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
-                    const Run& u = runs[r];
-                    const size_t q = (size_t)u.tile * K + k;
-                    TileSegRec& s = out.segs[r];
-                    s.chunk_start = out.base[u.tile] + out.coff[(size_t)u.tile * (K + 1) + k];
-                    s.sidx = sidx[q]++;
-                    s.off4 = (int)(dpos[q] >> 2);
-                    s.row_flag = i | (r == row_run[i] ? (int)0x80000000u : 0);
-                    s.e0 = u.e0;
-                    s.len = u.len;
-                    dpos[q] += ((long long)u.len * (vs + 2) + 3) & ~3LL;
-                }
+        // ---- slice and lane records (lanes of a slice longest first)
+        out.slices.clear();
+        out.lanes.clear();
+        out.segments = (long long)runs.size();
+        std::vector<std::vector<int>> pend((size_t)P);
+        std::vector<int> sidx(P, 0);
+        std::vector<long long> dpos(P, 0);
+        auto flush = [&](int p, int k) {
+            std::vector<int>& v = pend[p];
+            if (v.empty()) return;
+            std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return runs[x].len > runs[y].len; });
+            TileSliceRec sr;
+            sr.chunk_start = out.base[p] + out.coff[(size_t)p * (K + 1) + k];
+            sr.sidx = sidx[p]++;
+            sr.off4 = (int)(dpos[p] >> 2);
+            sr.nl = (int)v.size();
+            long long E = 0;
+            for (int x : v) E += runs[x].len;
+            sr.E = (int)E;
+            sr.first = (int)out.lanes.size();
+            sr.pad = 0;
+            for (int x : v) {
+                TileLaneRec lr;
+                lr.row_flag = run_row[x];
+                lr.e0 = runs[x].e0;
+                lr.len = runs[x].len;
+                out.lanes.push_back(lr);
             }
+            dpos[p] += slice_bytes(sr.nl, E);
+            out.slices.push_back(sr);
+            v.clear();
+        };
+        for (int k = 0; k < K; ++k) {
+            for (int p = 0; p < P; ++p) {
+                sidx[p] = 0;
+                dpos[p] = ((long long)nsl[(size_t)p * K + k] * 8 + 15) & ~15LL;
+            }
+            for (int g = ck[k]; g < ck[k + 1]; ++g)
+                for (int j = gstart[g]; j < gstart[g + 1]; ++j) {
+                    const int i = order[j];
+                    for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
+                        const int p = runs[r].tile;
+                        if ((int)pend[p].size() == 32) flush(p, k);
+                        pend[p].push_back(r);
+                    }
+                }
+            for (int p = 0; p < P; ++p) flush(p, k);
         }
         return true;
     }
