@@ -1,14 +1,19 @@
 #!/usr/bin/env python
 """Throughput benchmark of the superiorized hyperslab-projection path on GB300.
 
-A step is one superiorized iteration (Algorithm 1): the TV perturbation phase
-followed by one fused Cimmino sweep over the CT 512x512 system (360 angles x
-725 bins, Siddon CSR, FP32 values, int32 indices) with the fused proximity.
-The headline value is nnz * sweeps / s with A resident in HBM; the e2e value
-is the same metric through the C ABI with host buffers (new bounds in, x and
-statistics out, copies inside the timed region).  Extra variants (block-
-iterative, BF16 values, batched seismic, radiotherapy, tiny CT) are reported
-under "variants".
+A step is one superiorized solve of the CT 512x512 configuration (360 angles x
+725 bins, Siddon CSR, FP32 values, int32 indices): the iterate reset to
+box(0), then 200 iterations of Algorithm 1 (TV perturbation phase followed by
+one Cimmino sweep with the fused proximity and stopping bookkeeping).  The
+headline value is nnz * sweeps / s with A resident in HBM (the sweep strategy
+and its launch shapes chosen by the library's tuner at create); the e2e value
+is the same metric through the C ABI with host buffers (new bounds and x0 in,
+x out, copies inside the timed region).  The roofline is that of the whole
+sweep (every launch of one application of T) against the algorithmic bytes
+of a sweep.  Extra variants (block-iterative, BF16 values, batched seismic,
+radiotherapy, tiny CT) are reported under "variants", the error of 16-bit
+values against the FP64 oracle on the original A under "precision", and the
+serving mix under "serving".
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs an independent replica (weak scaling).
@@ -34,6 +39,7 @@ METRIC = "nnz·sweeps/s"
 UNIT = "nnz*sweeps/s"
 CT512 = dict(N=512, nang=360, nbin=725, I0=5e3, delta=0.02, seed_phantom=201, seed_noise=202)
 SUP = dict(gamma=0.5, alpha=0.99, n_red=1)
+SWEEPS = 200          # iterations of one CT 512x512 solve (the configuration's count)
 
 
 def log(*a):
@@ -127,46 +133,85 @@ def peaks():
 
 # ------------------------------------------------------------ CPU baseline --
 
-def cpu_baseline(prob, seconds: float, warm: int = 0):
-    """The FP64 oracle as it stands, timed on this host on a bounded sample:
-    superiorized Cimmino iterations of the same workload until `seconds`."""
+_ORACLE = {}   # the oracle's setup of the CT 512x512 workload, shared with forked workers
+
+
+def _oracle_setup(prob):
     import oracle as O
-    S, l, u, lo, hi = O.from_problem(prob)
-    ob = O.Objective(O.OBJ_TV_ISO, prob.shape)
+    if "S" not in _ORACLE:
+        S, l, u, lo, hi = O.from_problem(prob)
+        _ORACLE.update(S=S, l=l, u=u, lo=lo, hi=hi,
+                       ob=O.Objective(O.OBJ_TV_ISO, prob.shape), n=prob.A.n)
+    return _ORACLE
+
+
+def _oracle_iterations(seconds: float, seed: int = 0):
+    """Superiorized Cimmino iterations of the oracle (as it stands) from box(0)
+    until `seconds` pass; returns (iterations, elapsed s)."""
+    import oracle as O
+    d = _ORACLE
     P = O.Params(**SUP)
     st = O.PertState()
-    x = np.zeros(prob.A.n)
-    for _ in range(warm):
-        x, _, _ = O.perturbation_phase(ob, x, st, P)
-        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+    x = np.zeros(d["n"])
     it = 0
     t0 = time.perf_counter()
     while True:
-        x, _, _ = O.perturbation_phase(ob, x, st, P)
-        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+        x, _, _ = O.perturbation_phase(d["ob"], x, st, P)
+        x, _ = O.sweep(d["S"], O.CIMMINO, d["l"], d["u"], 1.0, d["lo"], d["hi"], x)
         it += 1
         el = time.perf_counter() - t0
         if el >= seconds:
-            break
-    return it, el
+            return it, el
+
+
+def cpu_baselines(prob, seconds: float):
+    """The FP64 oracle timed on this host's cores on a bounded sample of the
+    headline workload: one process (one thread: scipy's sparse products are
+    single-threaded), then one process per core, each running the same
+    iterations (the aggregate rate of replicas; the setup is built once and
+    shared by the forked workers).  Must run before the first CUDA call (the
+    workers are forked)."""
+    import multiprocessing as mp
+    nnz = prob.A.nnz
+    _oracle_setup(prob)
+    it1, el1 = _oracle_iterations(seconds)
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("fork")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_iterations, [seconds] * cores)
+    its = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    single = {"value": nnz * it1 / el1, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"{it1} superiorized Cimmino iterations of the CT 512x512 workload from "
+                        f"box(0) ({el1:.1f} s, FP64 numpy/scipy oracle, one process)"}
+    allc = {"value": nnz * its / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes (one per host core) each running superiorized Cimmino "
+                      f"iterations of the CT 512x512 workload from box(0) for {seconds:.0f} s "
+                      f"({its} iterations in all, FP64 numpy/scipy oracle)",
+            "single_thread": single}
+    return allc
 
 
 def reference_arm(args):
+    """The reference arm: the FP64 oracle (there is no installable reference
+    implementation), on this host's cores, on a bounded sample of the same
+    workload and metric (each step a few superiorized iterations)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     prob = ct512()
     nnz = prob.A.nnz
     import oracle as O
-    S, l, u, lo, hi = O.from_problem(prob)
-    ob = O.Objective(O.OBJ_TV_ISO, prob.shape)
+    d = _oracle_setup(prob)
     P = O.Params(**SUP)
     st = O.PertState()
     x = np.zeros(prob.A.n)
+    per_step = 2   # iterations per step: a bounded sample of a 200-iteration solve
 
     def step(x):
-        x, _, _ = O.perturbation_phase(ob, x, st, P)
-        x, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x)
+        for _ in range(per_step):
+            x, _, _ = O.perturbation_phase(d["ob"], x, st, P)
+            x, _ = O.sweep(d["S"], O.CIMMINO, d["l"], d["u"], 1.0, d["lo"], d["hi"], x)
         return x
 
     for _ in range(args.warmup):
@@ -175,9 +220,9 @@ def reference_arm(args):
     for _ in range(args.steps):
         x = step(x)
     el = time.perf_counter() - t0
-    v = nnz * args.steps / el
-    sample = (f"{args.steps} superiorized Cimmino iterations (TV perturbation + sweep) of the "
-              f"CT 512x512 workload, FP64 numpy/scipy oracle, single thread")
+    v = nnz * per_step * args.steps / el
+    sample = (f"{args.steps} steps of {per_step} superiorized Cimmino iterations (TV perturbation "
+              f"+ sweep) of the CT 512x512 workload, FP64 numpy/scipy oracle, one process")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -193,6 +238,7 @@ def config_of(prob):
     return {"workload": "ct512_cimmino_tv_f32", "image": "512x512", "angles": 360, "bins": 725,
             "m": prob.A.m, "n": prob.A.n, "nnz": prob.A.nnz, "I0": 5e3, "slab_delta": 0.02,
             "perturbation": "TV, beta=0.5*0.99^l, n_red=1", "relaxation": 1.0,
+            "step": f"one solve: x <- box(0), then {SWEEPS} superiorized Cimmino iterations",
             "l2": "inputs larger than L2 (A values+indices ~0.96 GB > 126 MB L2)"}
 
 
@@ -224,52 +270,65 @@ def time_iterations(ctx, pk, K, W, params_kw, with_timing=True):
 
 
 KIND = {0: "row pass", 1: "column pass / finalize", 2: "perturbation", 3: "split (CQ) step"}
+STRATEGY = {1: "one pass (L2-reduction scatter)", 2: "two passes (CSR row pass, CSC column pass)",
+            3: "tiled one pass"}
 
 
-def measured_traffic(table, info, dom):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    capture (profiles/traffic.json), or None when there is none or it was
-    taken on another launch shape than the one this run's tuner picked (ring
-    tile and stages, lanes per item, lane map)."""
-    key = f"ct512_{info['strategy']}_{dom}"
-    tr, shape = table.get(key), table.get(key + "_shape")
-    if not tr or not shape:
-        return None
-    if dom == 0:
-        now = {"tile": info["tile"], "stages": info["stages"], "lanes": info["lanes_per_row"],
-               "map": info["map"]}
-    else:
-        now = {"tile": info["col_tile"], "stages": info["col_stages"], "lanes": info["col_lanes"],
-               "map": info["col_map"]}
-    return tr if now == shape else None
+def kind_name(strategy, k):
+    if strategy == 3 and k == 0:
+        return "tiled sweep"
+    return KIND[k]
 
 
-def kernel_alg_bytes(strategy, kind, m, n, nnz, vb, B=1):
-    """Algorithmic bytes of one sweep's kernel of the given kind (summed over
-    the blocks of a block-iterative sweep).  Row pass: A's values and column
-    indices once, per row its offset/length (8 B), weight (4 B) and l, u per
-    right-hand side, x read once; plus delta written once (one pass) or the
-    coefficients written once (two passes).  Column pass (two passes): the CSC
-    values and row indices once, per column offset/length, coefficients read
-    once, x read and written.  Finalize (one pass): x and delta read and
-    written.  Perturbation: not HBM-bound (x, g are L2-resident)."""
-    if kind == 0:
-        b = nnz * (vb + 4) + m * 12 + m * 8 * B + n * 4 * B
-        return b + (m * 4 * B if strategy == 2 else n * 4 * B)
-    if kind == 1:
-        if strategy == 2:
-            return nnz * (vb + 4) + n * 8 + m * 4 * B + n * 8 * B
-        return n * 16 * B
-    return n * 12 * B
+def sweep_traffic(info):
+    """DRAM bytes per sweep (all of the sweep's launches) from the committed
+    ncu capture (profiles/traffic.json), or None when there is none for this
+    strategy or it was taken on another launch shape than this run's."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, "no committed capture"
+    try:
+        table = json.load(open(path))
+    except (OSError, ValueError):
+        return None, "unreadable capture table"
+    ent = table.get(f"ct512_sweep_strategy{info['strategy']}")
+    if not ent:
+        return None, "no committed capture of this strategy"
+    shape = ent.get("shape", {})
+    now = {k: info.get(k) for k in shape}
+    if now != shape:
+        return None, "the committed capture is of another launch shape"
+    return float(ent["bytes_per_sweep"]), ent.get("note")
 
 
 def sweep_alg_bytes(m, n, nnz, vbytes, B=1):
-    """Algorithmic bytes of one application of T: A once, per-row data and the
-    iterate/correction vectors once."""
-    return nnz * (vbytes + 4) + m * (12 + 8 * B) + n * 16 * B
+    """Algorithmic bytes of one application of T (the per-unit figures of the
+    measurement plan): A's values and column indices once, per row its
+    offset, l, u and weight (16 B), per unknown x read and written and the
+    correction (16 B)."""
+    return nnz * (vbytes + 4) + m * 16 + n * 16 * B
 
 
-def summarize(ctx, prob, K, ms, kt, vb, B=1):
+def kernel_alg_bytes(strategy, kind, m, n, nnz, vb, B=1):
+    """Algorithmic bytes a kernel of the sweep carries (its share of one
+    sweep's): the pass that reads A carries A's bytes; a second read of A (the
+    column pass of the two-pass sweep reads the CSC copy) is traffic, not
+    algorithmic bytes.  Row pass: A, the per-row data (16 B); two passes add
+    the coefficients written (4 B a row).  Column pass: x read and written,
+    coefficients read; finalize: x and the correction read and written.  The
+    tiled sweep is the whole sweep."""
+    if strategy == 3:
+        return sweep_alg_bytes(m, n, nnz, vb, B) if kind == 0 else 0
+    if kind == 0:
+        return nnz * (vb + 4) + m * 16 * B + (m * 4 * B if strategy == 2 else 0)
+    if kind == 1:
+        return n * 8 * B + m * 4 * B if strategy == 2 else n * 16 * B
+    return 0
+
+
+def summarize(ctx, prob, K, kt, vb, B=1):
+    """Per-kernel times per sweep and the sweep time (the kernels of one
+    application of T: kinds 0 and 1)."""
     info = ctx.suppy_info_get()
     strat = info["strategy"]
     A = prob.A
@@ -277,19 +336,19 @@ def summarize(ctx, prob, K, ms, kt, vb, B=1):
     for k, (tms, nl) in kt.items():
         if nl == 0:
             continue
-        sweeps_launches = max(nl // K, 1)
         if k == 3:
-            # CQ step: A_q read as CSR (doses) and as CSC (correction), 8 B an
-            # entry each time, row and column offsets, doses written, x read
-            # and written
             Aq = prob.meta["split"]["Aq"]
             alg = 2 * Aq.nnz * 8 + (Aq.m + A.n) * 8 + Aq.m * 4 + A.n * 8
         else:
             alg = kernel_alg_bytes(strat, k, A.m, A.n, A.nnz, vb, B)
-        per[KIND[k]] = {"ms_per_sweep": tms / K, "launches_per_sweep": sweeps_launches,
-                        "alg_bytes_per_sweep": alg,
-                        "gbs_alg": alg / (tms / K * 1e-3) / 1e9 if k != 2 else None}
+        ms = tms / K
+        per[kind_name(strat, k)] = {"ms_per_sweep": ms, "launches_per_sweep": nl / K,
+                                    "alg_bytes_per_sweep": alg,
+                                    "gbs_alg": alg / (ms * 1e-3) / 1e9 if alg else None}
     t_sweep = sum(kt[k][0] for k in (0, 1) if k in kt) / K
+    tot = sum(kt[k][0] for k in kt) / K
+    for k, v in per.items():
+        v["share_of_step_kernels"] = v["ms_per_sweep"] / tot if tot else None
     return info, per, t_sweep
 
 
@@ -319,46 +378,51 @@ def variants(pk, K, W):
         ms, _, nl = time_iterations(ctx, pk, Kv, W, pkw, with_timing=False)
         _, kt, _ = time_iterations(ctx, pk, Kv, 0, pkw, with_timing=True)
         vb = 4 if dtype == pk.SUPPY_F32 else 2
-        info, per, t_sweep = summarize(ctx, prob, Kv, ms, kt, vb, B)
+        info, per, t_sweep = summarize(ctx, prob, Kv, kt, vb, B)
         nnz = prob.A.nnz
         alg = sweep_alg_bytes(prob.A.m, prob.A.n, nnz, vb, B)
+        peak, _ = peaks()
         # a split iteration also passes over the dose rows A_q: their entries count
         out[name] = {"value": (nnz + nnz_q) * B * Kv / (ms * 1e-3), "unit": metric_units,
                      "ms_per_step": ms / Kv, "sweep_ms": t_sweep,
                      "sweep_gbs_alg": alg / (t_sweep * 1e-3) / 1e9 if t_sweep else None,
+                     "sweep_frac_of_peak": alg / (t_sweep * 1e-3) / 1e9 / peak if t_sweep else None,
                      "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B, "kernels": per,
                      "create_s": t_create, "strategy": info["strategy"],
-                     "scatter": info["scatter"], "lanes_per_row": info["lanes_per_row"],
-                     "col_lanes": info["col_lanes"], "nblocks": info["nblocks"],
-                     "tma": info["tma"], "tile": info["tile"], "stages": info["stages"],
-                     "col_tile": info["col_tile"], "col_stages": info["col_stages"],
-                     "map": info["map"], "col_map": info["col_map"],
+                     "scatter": info["scatter"], "nblocks": info["nblocks"], "tma": info["tma"],
                      "launches_per_step": nl / Kv}
+        if info["strategy"] == 3:
+            out[name]["tiles"] = {k: info[k] for k in ("tiles", "chunks", "tile_warps1",
+                                                       "tile_warps2", "tile_coef_warps",
+                                                       "tile_ring", "tile_stream_bytes",
+                                                       "tile_segments")}
         if split:
             out[name]["nnz_split"] = nnz_q
         ctx.close()
         torch.cuda.synchronize()
 
     prob = ct512()
-    run_one("ct512_cimmino_tv_f32_twopass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
-            strategy=pk.STRATEGY_TWO_PASS, tune=1)
-    run_one("ct512_cimmino_tv_f32_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
-            strategy=pk.STRATEGY_ONE_PASS, tune=1)
+    for strat, tag in ((pk.STRATEGY_TILED, "tiled"), (pk.STRATEGY_TWO_PASS, "twopass"),
+                       (pk.STRATEGY_ONE_PASS, "onepass")):
+        run_one(f"ct512_cimmino_tv_f32_{tag}", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
+                strategy=strat, tune=1)
     run_one("ct512_cimmino_tv_f32_twopass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP,
             strategy=pk.STRATEGY_TWO_PASS, tma=-1)
-    run_one("ct512_cimmino_tv_f32_onepass_notma", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
-            params=SUP, strategy=pk.STRATEGY_ONE_PASS, tma=-1)
     run_one("ct512_emr_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EMR,
             params=SUP, tune=1)
     run_one("ct512_el_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EL,
             params=SUP, tune=1)
+    run_one("ct512_drop_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_DROP,
+            params=SUP, tune=1)
     run_one("ct512_cimmino_tv_bf16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_BF16,
             params=SUP, tune=1)
-    run_one("ct512_cimmino_tv_bf16_onepass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO,
-            dtype=pk.SUPPY_BF16, params=SUP, strategy=pk.STRATEGY_ONE_PASS, tune=1)
+    run_one("ct512_cimmino_tv_f16", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, dtype=pk.SUPPY_F16,
+            params=SUP, tune=1)
     prob.blocks = synth.angle_blocks(360, 725, 36)
     run_one("ct512_bip36_tv_f32", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP,
             params=SUP, tune=1)
+    run_one("ct512_bip36_tv_f32_twopass", prob, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP,
+            params=SUP, strategy=pk.STRATEGY_TWO_PASS, tune=1)
     del prob
     seis = synth.seismic_problem(nrhs=16)
     run_one("seismic_b16_atv_f32", seis, "nnz*rhs*sweeps/s", obj=pk.SUPPY_OBJ_TV_ANISO,
@@ -383,6 +447,69 @@ def variants(pk, K, W):
     del rts
     tiny = synth.ct_problem()
     run_one("ct64_cimmino_tv_f32", tiny, UNIT, obj=pk.SUPPY_OBJ_TV_ISO, params=SUP)
+    return out
+
+
+def precision(pk):
+    """Error of 16-bit storage of A's values against the FP64 oracle on the
+    original (FP32) values, and the parity gate against the oracle on the
+    rounded values.  CT 64x64 (configuration 1): the full 100-iteration
+    superiorized run from box(0).  CT 512x512: one sweep from a seeded point,
+    and three superiorized iterations from box(0)."""
+    import torch
+    import oracle as O
+    import synth
+
+    def rounded(v, dt):
+        t = torch.from_numpy(np.ascontiguousarray(v, np.float32))
+        return (t.to(torch.bfloat16) if dt == pk.SUPPY_BF16 else t.to(torch.float16)).to(
+            torch.float32).numpy()
+
+    def rel_l2(a, b):
+        a = np.asarray(a, np.float64)
+        b = np.asarray(b, np.float64)
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    def rel(a, b):
+        return float(abs(a - b) / max(abs(b), 1e-300))
+
+    out = {}
+    ob_kind = O.OBJ_TV_ISO
+    for label, prob, K in (("ct64_100_iterations", synth.ct_problem(), 100),
+                           ("ct512_3_iterations", ct512(), 3)):
+        ob = O.Objective(ob_kind, prob.shape)
+        P = O.Params(max_sweeps=K, **SUP)
+        S, l, u, lo, hi = O.from_problem(prob)
+        r64 = O.run(S, O.CIMMINO, l, u, lo, hi, ob, P)
+        sweep64 = None
+        if K == 3:
+            x0 = np.random.default_rng(7).uniform(0, 1, prob.A.n).astype(np.float32)
+            sweep64, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x0.astype(np.float64))
+        for dt, name in ((pk.SUPPY_BF16, "bf16"), (pk.SUPPY_F16, "f16"), (pk.SUPPY_F32, "f32")):
+            vals = prob.A.val if dt == pk.SUPPY_F32 else rounded(prob.A.val, dt)
+            Sr, lr, ur, lor, hir = O.from_problem(prob, values=vals)
+            rr = O.run(Sr, O.CIMMINO, lr, ur, lor, hir, ob, P) if dt != pk.SUPPY_F32 else r64
+            ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, dtype=dt, tune=1 if K == 3 else 0)
+            st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=K, **SUP))[0]
+            xg = ctx.suppy_get_x()
+            ph, fh = ctx.suppy_history()
+            e = {"x_rel_l2_vs_fp64_oracle_original_A": rel_l2(xg, r64.x),
+                 "x_rel_l2_vs_fp64_oracle_rounded_A": rel_l2(xg, rr.x),
+                 "final_proximity_rel_vs_original": rel(ph[-1], r64.prox_hist[-1]),
+                 "final_proximity_rel_vs_rounded": rel(ph[-1], rr.prox_hist[-1]),
+                 "final_objective_rel_vs_original": rel(fh[-1], r64.obj_hist[-1]),
+                 "oracle_rounded_vs_original_x_rel_l2": rel_l2(rr.x, r64.x),
+                 "sweeps": st["sweeps"]}
+            if sweep64 is not None:
+                ctx.suppy_set_x(x0)
+                ctx.suppy_sweep(pk.suppy_params_default(), 1)
+                x1 = ctx.suppy_get_x()
+                sr, _ = O.sweep(Sr, O.CIMMINO, lr, ur, 1.0, lor, hir, x0.astype(np.float64))
+                e["one_sweep_x_rel_l2_vs_original"] = rel_l2(x1, sweep64)
+                e["one_sweep_x_rel_l2_vs_rounded"] = rel_l2(x1, sr)
+            out[f"{label}_{name}"] = e
+            ctx.close()
+            torch.cuda.synchronize()
     return out
 
 
@@ -465,7 +592,8 @@ def serving_workload(pk, nreq: int, seed: int = 501):
 
 def _serve_batched(pk, mats, reqs, dtype):
     """The requests through one continuous-batching server (A stored as dtype);
-    returns its figures and the final proximity / objective per request."""
+    returns its figures and per request (final proximity, final objective,
+    sweeps)."""
     import torch
     srv = pk.Server(slots=32, check_every=8)
     mids = []
@@ -484,40 +612,51 @@ def _serve_batched(pk, mats, reqs, dtype):
         r, w = srv.suppy_server_step()
         if nxt == len(reqs) and r == 0 and w == 0:
             break
-    lat, fin, prox, obj, sweeps = [], [], [], [], []
+    lat, queue, service, fin, per = [], [], [], [], []
     for k, rid in enumerate(ids):
         info, _ = srv.suppy_server_query(rid)
         lat.append(info["t_done"] - t0 - reqs[k][0])
+        queue.append(info["t_start"] - t0 - reqs[k][0])
+        service.append(info["t_done"] - info["t_start"])
         fin.append(info["t_done"] - t0)
-        prox.append(info["proximity"])
-        obj.append(info["objective"])
-        sweeps.append(info["sweeps"])
+        per.append((info["proximity"], info["objective"], info["sweeps"]))
     peak_bytes = srv.suppy_server_device_bytes()
     srv.close()
     torch.cuda.synchronize()
     name = "bf16 A" if dtype == pk.SUPPY_BF16 else "f32 A"
+    arrivals = reqs[-1][0]
     figs = {"solves_per_s": len(reqs) / max(fin), "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "makespan_s": max(fin),
-            "mean_sweeps": float(np.mean(sweeps)), "dtype": name + ", f32 x, f64 acceptance",
-            "device_bytes_end": int(peak_bytes)}
-    return figs, prox, obj
+            "queue_p50_s": float(np.percentile(queue, 50)),
+            "queue_p99_s": float(np.percentile(queue, 99)),
+            "service_p50_s": float(np.percentile(service, 50)),
+            "service_p99_s": float(np.percentile(service, 99)),
+            "sustains_arrival_rate": bool(max(fin) <= arrivals * 1.05 + float(np.percentile(service, 99))),
+            "mean_sweeps": float(np.mean([p[2] for p in per])),
+            "dtype": name + ", f32 x, f64 acceptance", "device_bytes_end": int(peak_bytes)}
+    return figs, per
 
 
 def serving(pk, nreq: int):
     """Batched continuous-batching server (BF16 A, and FP32 A for a comparison
     at equal precision) against one-at-a-time FP32 solves of the same requests
-    (arrival times kept, queueing included)."""
+    (arrival times kept, queueing included).  Per request, the final
+    proximity and objective are compared with the one-at-a-time solve; a
+    request that stops at another sweep than its one-at-a-time solve is also
+    compared at equal sweep counts (the one-at-a-time history at the batched
+    request's last sweep)."""
     import torch
     mats, reqs = serving_workload(pk, nreq)
-    batched, prox_b, obj_b = _serve_batched(pk, mats, reqs, pk.SUPPY_BF16)
-    batched32, prox_b32, obj_b32 = _serve_batched(pk, mats, reqs, pk.SUPPY_F32)
+    batched, per_b = _serve_batched(pk, mats, reqs, pk.SUPPY_BF16)
+    batched32, per_b32 = _serve_batched(pk, mats, reqs, pk.SUPPY_F32)
     # one at a time, FP32, per-matrix context resident after first use
     ctxs = {}
-    lat1, fin1, prox_1, obj_1 = [], [], [], []
+    lat1, fin1, queue1, service1, per_1, hist_1 = [], [], [], [], [], []
     t1 = time.perf_counter()
     for k, (ta, mi, l, u) in enumerate(reqs):
         while time.perf_counter() - t1 < ta:
             time.sleep(1e-4)
+        ts = time.perf_counter() - t1
         prob, spec = mats[mi]
         if mi not in ctxs:
             q = _with_bounds(prob, l, u)
@@ -527,29 +666,48 @@ def serving(pk, nreq: int):
         ctx.suppy_set_x(np.zeros(prob.A.n, np.float32))
         st = ctx.suppy_run(pk.suppy_params_default(**spec["sup"], **SERVE_STOP))[0]
         d = time.perf_counter() - t1
+        ph, fh = ctx.suppy_history()
         lat1.append(d - ta)
+        queue1.append(ts - ta)
+        service1.append(d - ts)
         fin1.append(d)
-        prox_1.append(st["proximity"])
-        obj_1.append(st["objective"])
+        per_1.append((st["proximity"], st["objective"], st["sweeps"]))
+        hist_1.append((ph.copy(), fh.copy()))
     for c in ctxs.values():
         c.close()
     torch.cuda.synchronize()
     plain = {"solves_per_s": len(reqs) / max(fin1), "p50_s": float(np.percentile(lat1, 50)),
-             "p99_s": float(np.percentile(lat1, 99)), "makespan_s": max(fin1), "dtype": "f32"}
-    def rel_diffs(pb, ob):
-        rp = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(pb, prox_1)]
-        ro = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(ob, obj_1)]
-        return ({"median": float(np.median(rp)), "max": float(np.max(rp))},
-                {"median": float(np.median(ro)), "max": float(np.max(ro))})
-    rp, ro = rel_diffs(prox_b, obj_b)
-    rp32, ro32 = rel_diffs(prox_b32, obj_b32)
-    batched32["final_proximity_rel_diff"] = rp32
-    batched32["final_objective_rel_diff"] = ro32
+             "p99_s": float(np.percentile(lat1, 99)), "makespan_s": max(fin1),
+             "queue_p50_s": float(np.percentile(queue1, 50)),
+             "queue_p99_s": float(np.percentile(queue1, 99)),
+             "service_p50_s": float(np.percentile(service1, 50)),
+             "service_p99_s": float(np.percentile(service1, 99)), "dtype": "f32"}
+
+    def diffs(per_b):
+        rp, ro, rp_eq, other_stop = [], [], [], 0
+        for (pb, ob, sb), (p1, o1, s1), (h1, f1) in zip(per_b, per_1, hist_1):
+            rp.append(abs(pb - p1) / max(abs(p1), 1e-300))
+            ro.append(abs(ob - o1) / max(abs(o1), 1e-300))
+            if sb != s1:
+                other_stop += 1
+            k = min(sb, len(h1)) - 1
+            rp_eq.append(abs(pb - h1[k]) / max(abs(h1[k]), 1e-300) if k >= 0 else 0.0)
+        miss = [i for i, (a, b) in enumerate(zip(rp, ro)) if a > 1e-3 or b > 1e-3]
+        return {"final_proximity_rel_diff": {"median": float(np.median(rp)), "max": float(np.max(rp))},
+                "final_objective_rel_diff": {"median": float(np.median(ro)), "max": float(np.max(ro))},
+                "proximity_rel_diff_at_equal_sweeps": {"median": float(np.median(rp_eq)),
+                                                       "max": float(np.max(rp_eq))},
+                "requests_stopping_at_another_sweep": other_stop,
+                "requests_above_1e-3": len(miss),
+                "requests_above_1e-3_stopping_elsewhere": sum(1 for i in miss if per_b[i][2] != per_1[i][2])}
+
+    batched.update(diffs(per_b))
+    batched32.update(diffs(per_b32))
     return {"requests": len(reqs), "arrival_rate_per_s": 200.0,
+            "arrivals_span_s": reqs[-1][0],
             "mix": {spec["name"]: sum(1 for r in reqs if r[1] == i)
                     for i, (_, spec) in enumerate(mats)},
             "batched": batched, "batched_f32": batched32, "one_at_a_time": plain,
-            "final_proximity_rel_diff": rp, "final_objective_rel_diff": ro,
             "stopping": "proximity change < 1e-4 relative for 5 sweeps, P <= 1e-6, or 500 sweeps"}
 
 
@@ -563,6 +721,14 @@ def _with_bounds(prob, l, u):
 def ours(args):
     import torch
     rank, world, local = dist_env()
+    K, W = args.steps, args.warmup
+    prob = ct512()
+    A = prob.A
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        # before the first CUDA call: the all-cores oracle arm forks its workers
+        cpu = cpu_baselines(prob, args.cpu_seconds)
+        _ORACLE.clear()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
@@ -571,16 +737,22 @@ def ours(args):
     pkbuild.build()
     import paper_2606_27086_gb300 as pk
 
-    K, W = args.steps, args.warmup
-    prob = ct512()
-    A = prob.A
     log(f"[bench] CT 512^2: m={A.m} n={A.n} nnz={A.nnz}")
-    # two-pass sweep (no atomics: bitwise reproducible), launch shapes measured
-    # on this matrix at create (outside the timed region); the one-pass sweep
-    # is within 1% on this matrix and reported under "variants"
-    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1, strategy=pk.STRATEGY_TWO_PASS)
-    if W:
-        ctx.suppy_run(pk.suppy_params_default(max_sweeps=W, **SUP))
+    # the sweep strategy and its launch shapes are chosen by the library's
+    # tuner at create (outside the timed region): one pass with L2
+    # reductions, two passes over CSR and CSC copies, or the tiled one pass
+    t0 = time.perf_counter()
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1)
+    t_create = time.perf_counter() - t0
+    x_reset = torch.zeros(A.n, dtype=torch.float32, device="cuda")
+    p_solve = pk.suppy_params_default(max_sweeps=SWEEPS, **SUP)
+
+    def solve():
+        ctx.suppy_set_x(x_reset)                 # box(0): a new solve
+        ctx.suppy_run(p_solve, want_stats=False)  # 200 iterations, enqueued
+
+    for _ in range(W):
+        solve()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -589,91 +761,85 @@ def ours(args):
     time.sleep(0.3)
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx:
-        nvtx.range_push("timed")   # lets ncu --nvtx-include timed/ select the timed steps
-    # the timed steps run as suppy_run does by default (one captured CUDA graph
-    # per iteration); per-kernel event timing would add host work per launch
-    ms, _, nl = time_iterations(ctx, pk, K, 0, SUP, with_timing=False)
+        nvtx.range_push("timed")
+    l0 = ctx.suppy_launch_count()
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(K):
+        solve()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nl = ctx.suppy_launch_count() - l0
     if nvtx:
         nvtx.range_pop()
     clocks = sampler.stop()
-    # per-kernel times from a second run of the same workload with CUDA events
-    # around every launch (no graphs)
-    Kt = min(K, 500)
-    _, kt, _ = time_iterations(ctx, pk, Kt, 0, SUP, with_timing=True)
-    ms, value = aggregate_over_ranks(ms, A.nnz * K, world)
-    info, per, t_sweep = summarize(ctx, prob, Kt, ms, kt, 4)
-    # dominant kernel of the step
-    dom = max((k for k in (0, 1, 2) if kt.get(k, (0, 0))[1]), key=lambda k: kt[k][0])
-    dms, dn = kt[dom]
-    per_launch = dms / dn
-    alg = kernel_alg_bytes(info["strategy"], dom, A.m, A.n, A.nnz, 4) / max(dn // Kt, 1)
+    st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=0, **SUP))
+    # per-kernel times: one more solve with CUDA events around every launch
+    ctx.suppy_set_x(x_reset)
+    _, kt, _ = time_iterations(ctx, pk, SWEEPS, 0, SUP, with_timing=True)
+    ms, value = aggregate_over_ranks(ms, A.nnz * SWEEPS * K, world)
+    info, per, t_sweep = summarize(ctx, prob, SWEEPS, kt, 4)
     peak, peak_kind = peaks()
-    achieved = alg / (per_launch * 1e-3) / 1e9
+    alg = sweep_alg_bytes(A.m, A.n, A.nnz, 4)
+    achieved = alg / (t_sweep * 1e-3) / 1e9
+    traffic, tnote = sweep_traffic(info)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": KIND[dom],
-            "alg_bytes_per_launch": alg, "launch_ms": per_launch,
-            "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)"}
-    sweep_alg = sweep_alg_bytes(A.m, A.n, A.nnz, 4)
-    sweep_roof = {"alg_bytes": sweep_alg, "sweep_ms": t_sweep,
-                  "achieved": sweep_alg / (t_sweep * 1e-3) / 1e9,
-                  "frac": sweep_alg / (t_sweep * 1e-3) / 1e9 / peak}
-    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(traffic_path):
-        try:
-            table = json.load(open(traffic_path))
-        except (OSError, ValueError):
-            table = {}
-        roof["traffic"] = measured_traffic(table, info, dom)
-        if roof["traffic"] is None and f"ct512_{info['strategy']}_{dom}" in table:
-            roof["traffic_note"] = "the committed capture is of another launch shape"
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "sweep (every launch of one application of T: " + STRATEGY[info["strategy"]] + ")",
+            "alg_bytes_per_launch": alg, "launch_ms": t_sweep,
+            "alg_bytes_formula": "nnz*(4+4) + m*16 + n*16 per sweep",
+            "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs, a burst copy)"}
+    if tnote:
+        roof["traffic_note"] = tnote
 
-    # end to end through the C ABI with host buffers
-    Ke = max(5, min(K, 100))
+    # end to end through the C ABI with host buffers: per step new slab bounds
+    # and x0 from pinned host memory, one solve, x back to pinned host memory
+    Ke = max(3, min(K, 10))
     l_pin = torch.from_numpy(np.ascontiguousarray(prob.l)).pin_memory()
     u_pin = torch.from_numpy(np.ascontiguousarray(prob.u)).pin_memory()
+    x0_pin = torch.zeros(A.n, dtype=torch.float32).pin_memory()
     x_pin = torch.empty(A.n, dtype=torch.float32).pin_memory()
-    p1 = pk.suppy_params_default(max_sweeps=1, **SUP)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(Ke):
         ctx.suppy_update_bounds_async(l_pin, u_pin)
-        ctx.suppy_run(p1, want_stats=False)
+        ctx.suppy_set_x(x0_pin)
+        ctx.suppy_run(p_solve, want_stats=False)
         ctx.suppy_get_x(x_pin)
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    e2e = {"value": A.nnz * Ke * world / te, "unit": UNIT,
-           "h2d_bytes_per_step": 2 * A.m * 4, "d2h_bytes_per_step": A.n * 4 + 40,
+    e2e = {"value": A.nnz * SWEEPS * Ke * world / te, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * A.m * 4 + A.n * 4, "d2h_bytes_per_step": A.n * 4 + 40,
            "steps": Ke,
-           "note": "per step: suppy_update_bounds_async(pinned host l, u; copies, checks and "
-                   "swap enqueued; the iteration state continues) + suppy_run of one "
-                   "superiorized iteration (enqueued, no statistics) + suppy_get_x(pinned host "
-                   "x: the step's one synchronization, which also reports a rejected bounds set); "
-                   "suppy_set_bounds would also reset the exponent l, and the first phase after "
-                   "a reset near convergence spends all 100 trials"}
+           "note": "per step (one solve): suppy_update_bounds_async (pinned host l, u), "
+                   "suppy_set_x (pinned host x0; the solve starts at box(0)), suppy_run of "
+                   f"{SWEEPS} superiorized iterations (enqueued), suppy_get_x (pinned host x: "
+                   "the step's one synchronization)"}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_of(prob),
-           "roofline": roof, "sweep_roofline": sweep_roof, "kernels": per,
-           "kernel_timing_steps": Kt, "e2e": e2e,
-           "gpu_launches": int(nl), "clocks": clocks,
-           "launch_shape": {k: info[k] for k in ("strategy", "scatter", "tma", "lanes_per_row",
-                                                  "elems_in_regs", "grid", "col_lanes",
-                                                  "col_grid", "perturb_cluster", "tile", "stages",
-                                                  "col_tile", "col_stages", "map",
-                                                  "col_map")}}
+           "roofline": roof, "kernels": per, "e2e": e2e,
+           "gpu_launches": int(nl), "clocks": clocks, "create_s": t_create,
+           "sweeps_per_step": SWEEPS,
+           "launch_shape": {k: info[k] for k in ("strategy", "scatter", "tma", "tiles", "chunks",
+                                                  "tile_warps1", "tile_warps2", "tile_coef_warps",
+                                                  "tile_ring", "tile_stream_bytes",
+                                                  "tile_segments", "tile", "stages", "col_tile",
+                                                  "col_stages", "map", "col_map",
+                                                  "perturb_cluster")}}
     ctx.close()
     if rank == 0 and not args.no_variants:
         res["variants"] = variants(pk, K, min(W, 5))
+        res["precision"] = precision(pk)
     if rank == 0 and args.serve_requests > 0:
         res["serving"] = serving(pk, args.serve_requests)
-    if rank == 0 and not args.no_cpu:
-        it, el = cpu_baseline(prob, args.cpu_seconds)
-        res["cpu_baseline"] = {"value": A.nnz * it / el, "unit": UNIT, "cores": 1,
-                               "kind": "oracle",
-                               "sample": f"{it} superiorized Cimmino iterations of the CT "
-                                         f"512x512 workload ({el:.1f} s, FP64 numpy/scipy oracle, "
-                                         f"single thread)"}
+    if cpu is not None:
+        res["cpu_baseline"] = cpu
     if world > 1:
         torch.distributed.barrier()
     if rank == 0:
@@ -751,8 +917,9 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10,
+                    help="timed solves (each 200 superiorized iterations from box(0))")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--profile-warmup", type=int, default=0,
                     help="with --profile: unprofiled iterations before the profiled ones (300 "
                          "reaches the steady state; 0 profiles the first iterations)")
@@ -760,9 +927,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=128,
+    ap.add_argument("--serve-requests", type=int, default=512,
                     help="also run the serving mix with this many requests (512: the full "
-                         "trace) and report it under 'serving'")
+                         "trace; 0 skips it) and report it under 'serving'")
     ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
@@ -777,7 +944,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        # each oracle step is about a second of CPU work: bound the sample
+        # each oracle step is about two seconds of CPU work: bound the sample
         args.steps = min(args.steps, 20)
         args.warmup = min(args.warmup, 3)
         return reference_arm(args)

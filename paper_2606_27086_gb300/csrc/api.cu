@@ -1351,7 +1351,7 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
         want_stages = 8;
     }
     const int vbytes = (c->dt == SUPPY_F32) ? 4 : 2;
-    const long long max_chunk = (long long)(want_stages - 1) * piece / 2;
+    const long long max_chunk = (long long)(want_stages - 3) * piece / 2;
     TilePlanIn in;
     in.m = c->m;
     in.n = c->n;
@@ -1366,12 +1366,12 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     for (int i = 0; i < c->m; ++i) rstart[i] = rinfo[i].x;
     in.row_start = rstart.data();
     in.seg_start = c->seg_start;
-    in.max_chunk = std::min<long long>(48 * 1024, max_chunk);
-    in.chunk_target = chunk_req ? chunk_req : std::min<long long>(24 * 1024, in.max_chunk / 2);
+    in.max_chunk = max_chunk;
+    in.chunk_target = chunk_req ? chunk_req : std::min<long long>(24 * 1024, in.max_chunk / 3);
     in.max_chunks = kTileMaxChunks;
-    in.max_slices = 48;
+    in.max_slices = 32;
     // a segment, its descriptor and padding fit well inside one chunk
-    in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 2 - 32) / (vbytes + 2)));
+    in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 4 - 32) / (vbytes + 2)));
     in.max_tile_words = kTileMaxWords;
     TilePlan plan;
     std::string why;

@@ -53,13 +53,25 @@ namespace suppy {
 #ifdef SUPPY_TILE_STATS
 // Measurement build only: cycles per warp role, summed over the CTAs' warps
 // (0/1 phase-1 waits / total, 2/3 coefficient waits / total, 4/5 scatter
-// waits / total, 6/7 producer waits / total, 8/9 watcher idle polls / total).
+// waits / total, 6/7 producer waits / total, 8/9 watcher idle polls / total),
+// and per chunk of CTAs 0 and 1 the global time (ns) of six events: its last
+// piece issued, phase 1 done, its counter raised, grid-complete seen,
+// coefficients done, scatter done.
 __device__ unsigned long long g_tile_stats[16];
+__device__ unsigned long long g_tile_trace[2][kTileMaxChunks][6];
 #define TSTAT_CLOCK() clock64()
 #define TSTAT_ADD(k, v) atomicAdd(&g_tile_stats[k], (unsigned long long)(v))
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+#define TTRACE(k, ev) \
+    do { if (blockIdx.x < 2 && (k) < kTileMaxChunks) g_tile_trace[blockIdx.x][k][ev] = gtime(); } while (0)
 #else
 #define TSTAT_CLOCK() 0LL
 #define TSTAT_ADD(k, v) ((void)0)
+#define TTRACE(k, ev) ((void)0)
 #endif
 
 namespace {
@@ -191,15 +203,31 @@ __device__ __forceinline__ float slice_dot(const unsigned char* ring, int RING, 
         const VT* vv = reinterpret_cast<const VT*>(ring + sl.vpos);
         const unsigned short* ii = reinterpret_cast<const unsigned short*>(ring + sl.ipos);
         int e = 0;
-        for (; e + 1 < sl.L0; e += 2) {
-            const bool c0 = e < len, c1 = e + 1 < len;
-            const int n0 = __popc(__ballot_sync(kFull, c0));
-            const int n1 = __popc(__ballot_sync(kFull, c1));
-            if (c0) a0 = fmaf(to_float(vv[base + lane]), xt[ii[base + lane]], a0);
-            if (c1) a1 = fmaf(to_float(vv[base + n0 + lane]), xt[ii[base + n0 + lane]], a1);
-            base += n0 + n1;
+        for (; e + 3 < sl.L0; e += 4) {
+            // four steps' loads in flight: positions from the counts of lanes
+            // still active at each step
+            const int n0 = __popc(__ballot_sync(kFull, e < len));
+            const int n1 = __popc(__ballot_sync(kFull, e + 1 < len));
+            const int n2 = __popc(__ballot_sync(kFull, e + 2 < len));
+            const int n3 = __popc(__ballot_sync(kFull, e + 3 < len));
+            const int p0 = base + lane, p1 = p0 + n0, p2 = p1 + n1, p3 = p2 + n2;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            int j[4] = {0, 0, 0, 0};
+            if (e < len) { v[0] = to_float(vv[p0]); j[0] = ii[p0]; }
+            if (e + 1 < len) { v[1] = to_float(vv[p1]); j[1] = ii[p1]; }
+            if (e + 2 < len) { v[2] = to_float(vv[p2]); j[2] = ii[p2]; }
+            if (e + 3 < len) { v[3] = to_float(vv[p3]); j[3] = ii[p3]; }
+            a0 = fmaf(v[0], xt[j[0]], a0);
+            a1 = fmaf(v[1], xt[j[1]], a1);
+            a0 = fmaf(v[2], xt[j[2]], a0);
+            a1 = fmaf(v[3], xt[j[3]], a1);
+            base += n0 + n1 + n2 + n3;
         }
-        if (e < sl.L0 && e < len) a0 = fmaf(to_float(vv[base + lane]), xt[ii[base + lane]], a0);
+        for (; e < sl.L0; ++e) {
+            const int n0 = __popc(__ballot_sync(kFull, e < len));
+            if (e < len) a0 = fmaf(to_float(vv[base + lane]), xt[ii[base + lane]], a0);
+            base += n0;
+        }
     } else {
         for (int e = 0; e < sl.L0; ++e) {
             const bool c0 = e < len;
@@ -236,29 +264,47 @@ __device__ __forceinline__ void slice_scatter(const unsigned char* ring, int RIN
         const VT* vv = reinterpret_cast<const VT*>(ring + sl.vpos);
         const unsigned short* ii = reinterpret_cast<const unsigned short*>(ring + sl.ipos);
         int e = 0;
-        for (; e + 1 < sl.L0; e += 2) {
+        for (; e + 3 < sl.L0; e += 4) {
             const int n0 = __popc(__ballot_sync(kFull, e < len));
             const int n1 = __popc(__ballot_sync(kFull, e + 1 < len));
-            const bool c0 = e < lact, c1 = e + 1 < lact;
-            float v0 = 0.f, v1 = 0.f, o0 = 0.f, o1 = 0.f;
-            int j0 = 0, j1 = 0;
-            if (c0) {
-                j0 = ii[base + lane];
-                v0 = c * to_float(vv[base + lane]);
+            const int n2 = __popc(__ballot_sync(kFull, e + 2 < len));
+            const int n3 = __popc(__ballot_sync(kFull, e + 3 < len));
+            const int p[4] = {base + lane, base + n0 + lane, base + n0 + n1 + lane,
+                              base + n0 + n1 + n2 + lane};
+            float v[4], o[4];
+            int j[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                j[u] = 0;
+                v[u] = 0.f;
+                if (e + u < lact) {
+                    j[u] = ii[p[u]];
+                    v[u] = c * to_float(vv[p[u]]);
+                }
             }
-            if (c1) {
-                j1 = ii[base + n0 + lane];
-                v1 = c * to_float(vv[base + n0 + lane]);
-            }
-            if (c0) o0 = vd[j0];
-            if (c1) o1 = vd[j1];
-            if (c0) cas_add(dt, j0, v0, o0);
-            if (c1) cas_add(dt, j1, v1, o1);
-            base += n0 + n1;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[u] = (e + u < lact) ? vd[j[u]] : 0.f;
+            // the four compare-and-swaps issued back to back; a lost race
+            // retries with the value it found
+            unsigned prev[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u < lact)
+                    prev[u] = atomicCAS(reinterpret_cast<unsigned*>(dt) + j[u], __float_as_uint(o[u]),
+                                        __float_as_uint(o[u] + v[u]));
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (e + u < lact && prev[u] != __float_as_uint(o[u]))
+                    cas_add(dt, j[u], v[u], __uint_as_float(prev[u]));
+            base += n0 + n1 + n2 + n3;
         }
-        if (e < sl.L0 && e < lact) {
-            const int j0 = ii[base + lane];
-            cas_add(dt, j0, c * to_float(vv[base + lane]), vd[j0]);
+        for (; e < sl.L0; ++e) {
+            const int n0 = __popc(__ballot_sync(kFull, e < len));
+            if (e < lact) {
+                const int j0 = ii[base + lane];
+                cas_add(dt, j0, c * to_float(vv[base + lane]), vd[j0]);
+            }
+            base += n0;
         }
     } else {
         for (int e = 0; e < sl.L0; ++e) {
@@ -313,7 +359,8 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
     int* scoff = reinterpret_cast<int*>(dt + a.tile_cap);   // K + 1 chunk offsets
     int* snsl = scoff + (a.K + 1);                          // K slice counts
     int* sblk = snsl + a.K;                                 // K blocks
-    float* cbuf = reinterpret_cast<float*>(sblk + a.K);     // CQ x cstride coefficients
+    int* spref = sblk + a.K;                                // K + 1: slices before chunk k
+    float* cbuf = reinterpret_cast<float*>(spref + a.K + 1);   // CQ x cstride coefficients
     uint64_t* full = reinterpret_cast<uint64_t*>(
         (reinterpret_cast<uintptr_t>(cbuf + (size_t)a.cq * a.cstride) + 15) & ~uintptr_t(15));
     const int b = blockIdx.x, tid = threadIdx.x;
@@ -343,6 +390,17 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
         for (int k = tid; k < a.K; k += blockDim.x) {
             snsl[k] = gns[k];
             sblk[k] = a.chunk_blk[k];
+        }
+        if (tid == 0) {
+            // a running slice index across the chunks: slice s of chunk k goes
+            // to warp (spref[k] + s) mod W of a role, so every warp gets its
+            // share of the slices however few a chunk holds
+            int acc = 0;
+            for (int k = 0; k < a.K; ++k) {
+                spref[k] = acc;
+                acc += gns[k];
+            }
+            spref[a.K] = acc;
         }
         if (tid < kTileMaxWarps) prox_w[tid] = 0.0;
         if (tid < kTileMaxStages) stage_piece[tid] = -1;
@@ -380,6 +438,9 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             int issued = 0;
             int rel = 0;   // chunks whose scatter finished
             int jq = 0;    // chunk holding the last byte of the piece
+#ifdef SUPPY_TILE_STATS
+            int tr_k = 0;  // next chunk whose data is still to be issued
+#endif
             bool ok = true;
             for (int q = 0; q < npieces && ok; ++q) {
                 const int end = min((q + 1) << ts, len_stream);
@@ -399,6 +460,12 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 }
                 const int s = q % a.stages;
                 const uint32_t bytes = (uint32_t)(end - (q << ts));
+#ifdef SUPPY_TILE_STATS
+                while (tr_k < a.K && scoff[tr_k + 1] <= end) {
+                    TTRACE(tr_k, 0);
+                    ++tr_k;
+                }
+#endif
                 stage_piece[s] = q;
                 tma::mbar_arrive_expect_tx(&full[s], bytes);
                 tma::bulk_g2s(ring + ((size_t)s << ts), src + (q << ts), bytes, &full[s], pol);
@@ -438,10 +505,12 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 }
             }
             if (nsig > sig) {
+                if (lane < nsig - sig) TTRACE(sig + lane, 1);
                 // the phase-1 warps' reductions, ordered before their
                 // arrivals, reach the GPU before the counters move
                 fence_acq_rel_gpu();
                 if (lane < nsig - sig) red_add_u32_gpu(a.cnt + sig + lane, 1u);
+                if (lane < nsig - sig) TTRACE(sig + lane, 2);
                 sig = nsig;
                 prog = true;
             }
@@ -454,6 +523,7 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 const int nnew = (m == kFull) ? 32 : __ffs(~m) - 1;
                 __syncwarp();
                 if (nnew > 0) {
+                    if (lane < nnew) TTRACE(done + lane, 3);
                     if (lane == 0)
                         for (int t = 0; t < nnew; ++t) tma::mbar_arrive(&bar_g[(done + t) % kTileQ]);
                     done += nnew;
@@ -519,7 +589,7 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             if (ok && c1 > c0) {
                 const int nsl = snsl[k];
                 const int rc = c0 % RING;
-                for (int s = w1; s < nsl; s += W1) {
+                for (int s = (w1 - spref[k] % W1 + W1) % W1; s < nsl; s += W1) {
                     int row, len;
                     const Slice sl = slice_at<VT>(ring, RING, rc, s, lane, &row, &len);
                     const float dot = slice_dot<VT>(ring, RING, sl, lane, len, xt);
@@ -593,7 +663,10 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 }
             }
             __syncwarp();
-            if (lane == 0) tma::mbar_arrive(&bar_c[k % kTileQ]);
+            if (lane == 0) {
+                TTRACE(k, 4);
+                tma::mbar_arrive(&bar_c[k % kTileQ]);
+            }
         }
         pacc = warp_sum(pacc);
         if (lane == 0) {
@@ -621,7 +694,7 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
             if (ok && nsl > 0) {
                 const int rc = c0 % RING;
                 const float* cb = cbuf + (size_t)slot * a.cstride;
-                for (int s = w2; s < nsl; s += W2) {
+                for (int s = (w2 - spref[k] % W2 + W2) % W2; s < nsl; s += W2) {
                     int row, len;
                     const Slice sl = slice_at<VT>(ring, RING, rc, s, lane, &row, &len);
                     const float c = (lane < sl.nl) ? cb[s * 32 + lane] : 0.f;
@@ -629,7 +702,10 @@ __global__ void __launch_bounds__(1024, 1) k_tile_sweep(const TileArgs a) {
                 }
             }
             __syncwarp();
-            if (lane == 0) tma::mbar_arrive(&bar_s[k % kTileQ]);
+            if (lane == 0) {
+                if (w2 == 0) TTRACE(k, 5);
+                tma::mbar_arrive(&bar_s[k % kTileQ]);
+            }
             if (k + 1 == a.K || sblk[k + 1] != blk) {
                 // end of the block: the box step on the tile (every scatter
                 // warp has finished the block's chunks)
@@ -732,7 +808,7 @@ TileFn tile_fn(suppy_dtype dt) {
 }  // namespace
 
 size_t tile_smem_bytes(int ring_bytes, int tile_cap, int K, int stages, int cq, int cstride) {
-    size_t b = (size_t)ring_bytes + 8 * (size_t)tile_cap + 4 * (3 * (size_t)K + 1) +
+    size_t b = (size_t)ring_bytes + 8 * (size_t)tile_cap + 4 * (4 * (size_t)K + 2) +
                4 * (size_t)cq * cstride;
     b = (b + 15) & ~(size_t)15;
     return b + 8 * (size_t)stages;
@@ -961,6 +1037,9 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
     auto slice_bytes = [&](int nl, long long E) {
         return (((6LL * nl + 3) & ~3LL) + E * (vs + 2) + 15) & ~15LL;
     };
+    // a slice stays well inside a chunk: at most a quarter of the largest
+    // chunk (a slice of one segment may reach max_seg entries)
+    const long long slice_cap = std::max<long long>(in.max_chunk / 4, slice_bytes(1, in.max_seg));
     long long target = (long long)in.chunk_target * P;
     for (int attempt = 0; attempt < 12; ++attempt) {
         std::vector<int> ck;      // group indices where the chunks start
@@ -1020,8 +1099,9 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
                     const int i = order[j];
                     for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
                         const int p = runs[r].tile;
-                        if (cnt[p] == 32) {
-                            body[p] += slice_bytes(32, ent[p]);
+                        if (cnt[p] == 32 ||
+                            (cnt[p] > 0 && slice_bytes(cnt[p] + 1, ent[p] + runs[r].len) > slice_cap)) {
+                            body[p] += slice_bytes(cnt[p], ent[p]);
                             nsl[(size_t)p * K + k] += 1;
                             cnt[p] = 0;
                             ent[p] = 0;
@@ -1075,6 +1155,7 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         out.lanes.clear();
         out.segments = (long long)runs.size();
         std::vector<std::vector<int>> pend((size_t)P);
+        std::vector<long long> pend_ent(P, 0);
         std::vector<int> sidx(P, 0);
         std::vector<long long> dpos(P, 0);
         auto flush = [&](int p, int k) {
@@ -1101,6 +1182,7 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
             dpos[p] += slice_bytes(sr.nl, E);
             out.slices.push_back(sr);
             v.clear();
+            pend_ent[p] = 0;
         };
         for (int k = 0; k < K; ++k) {
             for (int p = 0; p < P; ++p) {
@@ -1112,8 +1194,12 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
                     const int i = order[j];
                     for (int r = row_run[i]; r < row_run[i + 1]; ++r) {
                         const int p = runs[r].tile;
-                        if ((int)pend[p].size() == 32) flush(p, k);
+                        const int cntp = (int)pend[p].size();
+                        if (cntp == 32 ||
+                            (cntp > 0 && slice_bytes(cntp + 1, pend_ent[p] + runs[r].len) > slice_cap))
+                            flush(p, k);
                         pend[p].push_back(r);
+                        pend_ent[p] += runs[r].len;
                     }
                 }
             for (int p = 0; p < P; ++p) flush(p, k);
@@ -1127,6 +1213,11 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
 }  // namespace suppy
 
 #ifdef SUPPY_TILE_STATS
+extern "C" int suppy_tile_trace(unsigned long long* out) {
+    return (int)cudaMemcpyFromSymbol(out, suppy::g_tile_trace, sizeof(unsigned long long) * 2 *
+                                                                   suppy::kTileMaxChunks * 6);
+}
+
 extern "C" int suppy_tile_stats(unsigned long long* out16, int reset) {
     cudaError_t e = cudaMemcpyFromSymbol(out16, suppy::g_tile_stats, sizeof(unsigned long long) * 16);
     if (e != cudaSuccess || !reset) return (int)e;
