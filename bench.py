@@ -280,17 +280,9 @@ def kind_name(strategy, k):
     return KIND[k]
 
 
-def sweep_traffic(info):
-    """DRAM bytes per sweep (all of the sweep's launches) from the committed
-    ncu capture (profiles/traffic.json), or None when there is none for this
-    strategy or it was taken on another launch shape than this run's."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None, "no committed capture"
-    try:
-        table = json.load(open(path))
-    except (OSError, ValueError):
-        return None, "unreadable capture table"
+def sweep_traffic_from(table, info):
+    """DRAM bytes per sweep (all of the sweep's launches) of a capture table
+    for this run's strategy and launch shape, or None with the reason."""
     ent = table.get(f"ct512_sweep_strategy{info['strategy']}")
     if not ent:
         return None, "no committed capture of this strategy"
@@ -299,6 +291,19 @@ def sweep_traffic(info):
     if now != shape:
         return None, "the committed capture is of another launch shape"
     return float(ent["bytes_per_sweep"]), ent.get("note")
+
+
+def sweep_traffic(info):
+    """The committed ncu capture's DRAM bytes per sweep (profiles/traffic.json)
+    when it was taken on this run's strategy and launch shape."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None, "no committed capture"
+    try:
+        table = json.load(open(path))
+    except (OSError, ValueError):
+        return None, "unreadable capture table"
+    return sweep_traffic_from(table, info)
 
 
 def sweep_alg_bytes(m, n, nnz, vbytes, B=1):

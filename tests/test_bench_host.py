@@ -1,21 +1,41 @@
-"""Host logic of bench.py's roofline line: the committed DRAM traffic of the
-dominant kernel is reported only for the launch shape it was captured on."""
+"""Host logic of bench.py's roofline line: the algorithmic bytes of a sweep
+follow the measurement plan (A's values and indices once, 16 B per row and
+per unknown), a second read of A is traffic and never algorithmic, and the
+committed DRAM traffic of the sweep is reported only for the strategy and
+launch shape it was captured on."""
 import bench
 
-TABLE = {"ct512_2_0": 974000000, "ct512_2_0_shape": {"tile": 4096, "stages": 6, "lanes": 16, "map": 1},
-         "ct512_2_1": 971000000, "ct512_2_1_shape": {"tile": 1024, "stages": 13, "lanes": 32, "map": 2}}
-INFO = {"strategy": 2, "tile": 4096, "stages": 6, "lanes_per_row": 16, "map": 1,
-        "col_tile": 1024, "col_stages": 13, "col_lanes": 32, "col_map": 2}
+TABLE = {"ct512_sweep_strategy2": {"bytes_per_sweep": 1945000000.0,
+                                   "shape": {"tile": 4096, "stages": 6, "map": 1}},
+         "ct512_sweep_strategy3": {"bytes_per_sweep": 780000000.0,
+                                   "shape": {"tiles": 152, "chunks": 250, "tile_ring": 172032}}}
+INFO2 = {"strategy": 2, "tile": 4096, "stages": 6, "map": 1}
+INFO3 = {"strategy": 3, "tiles": 152, "chunks": 250, "tile_ring": 172032}
+
+
+def test_sweep_alg_bytes_is_the_plans_formula():
+    m, n, nnz = 261000, 262144, 120309216
+    assert bench.sweep_alg_bytes(m, n, nnz, 4) == nnz * 8 + m * 16 + n * 16
+    assert bench.sweep_alg_bytes(m, n, nnz, 2) == nnz * 6 + m * 16 + n * 16
+
+
+def test_second_read_of_A_is_not_algorithmic():
+    m, n, nnz = 1000, 2000, 50000
+    row = bench.kernel_alg_bytes(2, 0, m, n, nnz, 4)
+    col = bench.kernel_alg_bytes(2, 1, m, n, nnz, 4)
+    assert col < nnz       # the column pass carries no bytes of A
+    assert row >= nnz * 8  # the row pass carries A once
+    assert bench.kernel_alg_bytes(3, 0, m, n, nnz, 4) == bench.sweep_alg_bytes(m, n, nnz, 4)
+    assert bench.kernel_alg_bytes(3, 1, m, n, nnz, 4) == 0
 
 
 def test_matching_shape_reports_the_capture():
-    assert bench.measured_traffic(TABLE, INFO, 0) == 974000000
-    assert bench.measured_traffic(TABLE, INFO, 1) == 971000000
+    assert bench.sweep_traffic_from(TABLE, INFO2)[0] == 1945000000.0
+    assert bench.sweep_traffic_from(TABLE, INFO3)[0] == 780000000.0
 
 
 def test_another_shape_or_strategy_reports_none():
-    for k, v in (("lanes_per_row", 32), ("map", 2), ("tile", 2048), ("stages", 3)):
-        assert bench.measured_traffic(TABLE, dict(INFO, **{k: v}), 0) is None
-    assert bench.measured_traffic(TABLE, dict(INFO, col_map=1), 1) is None
-    assert bench.measured_traffic(TABLE, dict(INFO, strategy=1), 0) is None
-    assert bench.measured_traffic({"ct512_2_0": 1}, INFO, 0) is None
+    for k, v in (("tile", 2048), ("stages", 3), ("map", 2)):
+        assert bench.sweep_traffic_from(TABLE, dict(INFO2, **{k: v}))[0] is None
+    assert bench.sweep_traffic_from(TABLE, dict(INFO3, chunks=300))[0] is None
+    assert bench.sweep_traffic_from(TABLE, dict(INFO2, strategy=1))[0] is None
