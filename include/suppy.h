@@ -193,6 +193,11 @@ typedef struct {
      * up to 24 copies of 8 KB in the shared memory left; else 8 copies of
      * tile_ring_bytes / 8 bytes, a power of two in [256, 8192]). */
     int32_t tile_chunk_bytes, tile_ring_bytes;
+    /* Tiled sweep: consecutive rows kept together when rows are dealt to
+     * chunks (0 automatic = 1, else 1..1024): neighbouring rays share a slice
+     * and read neighbouring columns at each step, while fewer rows per group
+     * even out the tiles' shares of a chunk. */
+    int32_t tile_group_rows;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default

@@ -41,7 +41,7 @@ constrained physical problems with SupPy"):
   of the seismic study (Sec. 2.3.1): ||x||_1 with subgradient sign(x), and
   ||x||_2^2 with gradient 2x (Q23).
 
-Readings where the paper is silent or garbled (numbered as in the design notes):
+Readings where the paper is silent or garbled (each with its number Q1..Q29):
 Q1 two-sided slab; Q2 w_i = 1/m' (Cimmino) and 1/|B_t| (BIP); Q3 descent
 direction v = -g/||g||; Q4 the exponent l is one counter advanced at every
 trial; Q5 g recomputed after each accepted step; Q6 at most J trials per

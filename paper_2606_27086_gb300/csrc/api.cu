@@ -1325,6 +1325,7 @@ constexpr int kTileThreadsTotal = 1024;          // warps of a tiled-sweep CTA: 
 constexpr long long kTileMaxWords = 6144;        // unknowns of one tile (x and Delta in shared memory)
 constexpr int kTileSmemMax = 227 * 1024;         // dynamic shared memory of one CTA
 constexpr int kTileStaticSmem = 2048;            // the kernel's static shared memory, rounded up
+constexpr int kTileGroupRows = 1;                // consecutive rows a chunk keeps together
 
 // Why the tiled sweep cannot serve this context, or "" when it can.
 std::string tile_ineligible(const suppy_ctx* c) {
@@ -1337,7 +1338,7 @@ std::string tile_ineligible(const suppy_ctx* c) {
 
 suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hcol,
                         const std::vector<int>& perm, const std::vector<int2>& rinfo,
-                        int ring_req, int chunk_req, bool* ok) {
+                        int ring_req, int chunk_req, int group_req, bool* ok) {
     *ok = false;
     free_tile(c);
     int sms = 0;
@@ -1373,6 +1374,7 @@ suppy_status build_tile(suppy_ctx* c, const std::vector<int>& rp, const int* hco
     // a segment, its descriptor and padding fit well inside one chunk
     in.max_seg = (int)std::max<long long>(8, std::min<long long>(4096, (in.max_chunk / 4 - 32) / (vbytes + 2)));
     in.max_tile_words = kTileMaxWords;
+    in.group_rows = group_req ? group_req : kTileGroupRows;
     TilePlan plan;
     std::string why;
     if (!plan_tiles(in, plan, why)) {
@@ -1619,6 +1621,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         if (rb != 0 && (rb % 8 != 0 || (rb / 8) < 256 || (rb / 8) > 8192 || ((rb / 8) & (rb / 8 - 1))))
             return fail(c, SUPPY_EINVAL, "tile_ring_bytes must be 0 or 8 x a power of two in [256, 8192]");
         if (o->tile_chunk_bytes < 0) return fail(c, SUPPY_EINVAL, "tile_chunk_bytes must be >= 0");
+        if (o->tile_group_rows < 0 || o->tile_group_rows > 1024)
+            return fail(c, SUPPY_EINVAL, "tile_group_rows must lie in 0..1024");
     }
     c->B = 1;
     if (c->B_user > 1) {
@@ -1958,7 +1962,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             c->tiW2 = kTileThreadsTotal / 32 - 2 - c->tiNC - c->tiW1;
         }
         if ((s = build_tile(c, rp, hcol, perm, rinfo, o->tile_ring_bytes, o->tile_chunk_bytes,
-                            &tile_ok)) != SUPPY_OK)
+                            o->tile_group_rows, &tile_ok)) != SUPPY_OK)
             return s;
         if (want == 3 && !tile_ok) return fail(c, SUPPY_EINVAL, c->err);
     }

@@ -275,6 +275,7 @@ struct TilePlanIn {
     int max_chunks;                // chunks the kernel's tables hold
     int max_slices;                // most slices of one tile in one chunk
     int max_seg;                   // longest segment (entries)
+    int group_rows;                // consecutive rows kept together (slice neighbours)
     long long max_tile_words;      // shared-memory words of one tile
 };
 

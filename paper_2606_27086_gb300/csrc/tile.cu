@@ -1003,12 +1003,12 @@ bool plan_tiles(const TilePlanIn& in, TilePlan& out, std::string& why) {
         why = "tile plan: too many segments";
         return false;
     }
-    // ---- row groups: 32 consecutive rows of a block (neighbouring rays of
-    // one direction for a ray-ordered matrix), the groups of a block in a
+    // ---- row groups: group_rows consecutive rows of a block (neighbouring
+    // rays of one direction for a ray-ordered matrix), the groups of a block in a
     // scattered order (a stride near ng / golden ratio, coprime to ng), so
     // that every chunk holds rays of every direction and position and every
     // tile gets about the same share of it
-    constexpr int kGroup = 32;
+    const int kGroup = std::max(1, in.group_rows);
     const int nblk = (int)in.seg_start.size() - 1;
     std::vector<int> order(in.m);        // rows, group by group
     std::vector<int> gstart;             // positions in `order` where the groups start
