@@ -56,8 +56,9 @@ def test_one_sweep_tiny_ct(mode, strategy):
 @pytest.mark.parametrize("strategy", STRATS)
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 def test_one_sweep_low_precision_values(dtype, strategy):
-    """BF16/FP16 storage: parity against the oracle run on the rounded values;
-    the error against the FP32-valued oracle is reported by the bench."""
+    """BF16/FP16 storage: parity against the oracle run on the rounded values
+    (the kernel gate); the error against the FP64 oracle on the original
+    values is checked and stated in test_gpu_precision.py."""
     prob = small_ct()
     ctx = pk.from_problem(prob, dtype=DT[dtype], strategy=strategy)
     x0 = random_x(prob.A.n, 1, seed=2)
