@@ -636,7 +636,10 @@ def _serve_batched(pk, mats, reqs, dtype):
             "queue_p99_s": float(np.percentile(queue, 99)),
             "service_p50_s": float(np.percentile(service, 50)),
             "service_p99_s": float(np.percentile(service, 99)),
-            "sustains_arrival_rate": bool(max(fin) <= arrivals * 1.05 + float(np.percentile(service, 99))),
+            # the offered load is sustained when completions keep pace with
+            # arrivals (throughput at least 95% of the arrival rate)
+            "offered_rate_per_s": len(reqs) / max(arrivals, 1e-9),
+            "sustains_arrival_rate": bool(len(reqs) / max(fin) >= 0.95 * len(reqs) / max(arrivals, 1e-9)),
             "mean_sweeps": float(np.mean([p[2] for p in per])),
             "dtype": name + ", f32 x, f64 acceptance", "device_bytes_end": int(peak_bytes)}
     return figs, per
@@ -704,7 +707,16 @@ def serving(pk, nreq: int):
                                                        "max": float(np.max(rp_eq))},
                 "requests_stopping_at_another_sweep": other_stop,
                 "requests_above_1e-3": len(miss),
-                "requests_above_1e-3_stopping_elsewhere": sum(1 for i in miss if per_b[i][2] != per_1[i][2])}
+                "requests_above_1e-3_stopping_elsewhere": sum(1 for i in miss if per_b[i][2] != per_1[i][2]),
+                "requests_above_1e-3_by_matrix": by_matrix(miss),
+                "proximity_above_1e-3": sum(1 for a in rp if a > 1e-3)}
+
+    def by_matrix(idx):
+        out = {}
+        for i in idx:
+            nm = mats[reqs[i][1]][1]["name"]
+            out[nm] = out.get(nm, 0) + 1
+        return out
 
     batched.update(diffs(per_b))
     batched32.update(diffs(per_b32))
@@ -747,7 +759,15 @@ def ours(args):
     # tuner at create (outside the timed region): one pass with L2
     # reductions, two passes over CSR and CSC copies, or the tiled one pass
     t0 = time.perf_counter()
-    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1)
+    if args.pin:
+        # a configuration the tuner chose in a plain run, rebuilt without
+        # timing (under a profiler the tuner's timings are not the plain ones)
+        st_, tile, stages, lanes, mp, cmp_ = (int(v) for v in args.pin.split(","))
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=st_,
+                              stream_shape=(tile, stages, lanes), stream_map=mp,
+                              stream_col_map=cmp_)
+    else:
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1)
     t_create = time.perf_counter() - t0
     x_reset = torch.zeros(A.n, dtype=torch.float32, device="cuda")
     p_solve = pk.suppy_params_default(max_sweeps=SWEEPS, **SUP)
@@ -836,7 +856,10 @@ def ours(args):
                                                   "tile_ring", "tile_stream_bytes",
                                                   "tile_segments", "tile", "stages", "col_tile",
                                                   "col_stages", "map", "col_map",
+                                                  "lanes_per_row", "col_lanes",
                                                   "perturb_cluster")}}
+    if args.pin:
+        res["launch_shape"]["pinned"] = args.pin
     ctx.close()
     if rank == 0 and not args.no_variants:
         res["variants"] = variants(pk, K, min(W, 5))
@@ -863,7 +886,13 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
     case 7: the seismic workload with 16 right-hand sides (batched register-fed
     two-pass sweep, one perturbation cluster per image); case 8: CT 384x384
     with EMR and the variance rule evaluated every iteration (extrapolation
-    and variance kernels).
+    and variance kernels); case 9: CT 384x384 with the register-fed two-pass
+    sweep (no bulk copies), the cluster perturbation with the image bands in
+    shared memory, and the standalone proximity and objective evaluations
+    (two each, after the iterations); case 10: a 2048x2048 image over a
+    random slab system (20000 rows) with TV, whose image bands exceed a
+    cluster's shared memory, so the cluster perturbation reads them from
+    global memory.
     The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches and the
     `warm` iterations run before it."""
@@ -892,6 +921,16 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
                                 seed_noise=202)
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_EMR)
         params = dict(SUP, variance_tol=1e-30)
+    elif case == 9:
+        prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
+                                seed_noise=202)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS, tma=-1,
+                              perturb_path=1)
+    elif case == 10:
+        prob = synth.random_problem(20000, 2048 * 2048, seed=11, feasible=False, mean_len=200)
+        prob.shape = (2048, 2048)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS,
+                              perturb_path=1)
     elif case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
@@ -908,13 +947,17 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
     nvtx = getattr(torch.cuda, "nvtx", None)
     if nvtx:
         nvtx.range_push("profile")
-    ctx.suppy_run(pk.suppy_params_default(max_sweeps=steps, use_graphs=0, **params))
+    st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=steps, use_graphs=0, **params))
+    if case == 9:
+        for _ in range(2):
+            ctx.suppy_proximity()
+            ctx.suppy_objective()
     torch.cuda.synchronize()
     if nvtx:
         nvtx.range_pop()
     info = ctx.suppy_info_get()
     log(f"[profile] case {case}: m={prob.A.m} n={prob.A.n} nnz={prob.A.nnz} "
-        f"shape={info}")
+        f"shape={info} state={st[0]} launches={ctx.suppy_launch_count()}")
     ctx.close()
     return 0
 
@@ -930,18 +973,26 @@ def main():
                          "reaches the steady state; 0 profiles the first iterations)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--pin", default="",
+                    help="build the headline context with this launch configuration instead of "
+                         "tuning it: strategy,tile,stages,lanes,map,col_map as a plain run's "
+                         "launch_shape reports it (e.g. 2,4096,6,16,1,2), for runs under a "
+                         "profiler, whose serialised launches distort the tuner's timings")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=512,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace; 0 skips it) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=[0, 1, 2, 3, 4, 5, 6, 7, 8],
+    ap.add_argument("--profile", type=int, default=0, choices=list(range(11)),
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
                          "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
                          "pass; 5 the horseshoe split problem (DVCs by the CQ step); 6 CT "
                          "512x512 with 36 BIP blocks; 7 seismic with 16 right-hand sides; 8 "
-                         "CT 384x384 with EMR and the variance rule")
+                         "CT 384x384 with EMR and the variance rule; 9 CT 384x384, "
+                         "register-fed sweep, cluster perturbation, standalone proximity and "
+                         "objective; 10 a 2048x2048 TV image, cluster perturbation from "
+                         "global memory")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6,

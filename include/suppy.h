@@ -198,6 +198,11 @@ typedef struct {
      * and read neighbouring columns at each step, while fewer rows per group
      * even out the tiles' shares of a chunk. */
     int32_t tile_group_rows;
+    /* Lane map of the column pass of the two-pass sweep alone: 0 the same
+     * as stream_map, else 1 or 2 as there (with stream_map and a fixed
+     * stream shape, a configuration the tuner chose can be rebuilt without
+     * timing, e.g. under a profiler).  Other values give SUPPY_EINVAL. */
+    int32_t stream_col_map;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default

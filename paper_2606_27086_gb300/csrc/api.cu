@@ -1615,6 +1615,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_stages must be 0 or 2.. the shared-memory budget");
         if (o->stream_map < 0 || o->stream_map > 2)
             return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
+        if (o->stream_col_map < 0 || o->stream_col_map > 2)
+            return fail(c, SUPPY_EINVAL, "stream_col_map must be 0, 1 or 2");
         if (o->tile_warps1 < 0 || o->tile_warps1 > 25)
             return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..25");
         const int rb = o->tile_ring_bytes;
@@ -1998,7 +2000,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         if ((st = build_row_partition(c)) != SUPPY_OK) return st;
         default_tma_shape(c);
         c->tMap = o->stream_map ? o->stream_map - 1 : kDefaultRowMap;
-        c->tMapc = o->stream_map ? o->stream_map - 1 : kDefaultColMap;
+        c->tMapc = o->stream_col_map ? o->stream_col_map - 1
+                                     : (o->stream_map ? o->stream_map - 1 : kDefaultColMap);
         if (fixed_shape) apply_stream_shape(c, o->stream_tile, o->stream_stages, o->stream_lanes);
         c->use_tma = tma_eligible(c, o->tma);
         if (fixed_shape && c->use_tma &&
@@ -2007,7 +2010,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             c->use_tma = false;
         if (c->use_tma) {
             if ((st = build_tma_partitions(c)) != SUPPY_OK) return st;
-            if (tune_streams && !fixed_shape && (st = tune_tma(c, o->stream_map == 0)) != SUPPY_OK)
+            if (tune_streams && !fixed_shape &&
+                (st = tune_tma(c, o->stream_map == 0 && o->stream_col_map == 0)) != SUPPY_OK)
                 return st;
         }
         return SUPPY_OK;

@@ -473,6 +473,32 @@ def test_tuned_stream_shapes_match_oracle():
     assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
 
 
+def test_tuned_configuration_rebuilt_without_timing():
+    """A tuned configuration (strategy, ring shape, lane maps per pass, as
+    suppy_info reports it) passed back as fixed options gives the same launch
+    configuration and the same sweep."""
+    prob = synth.ct_problem(128, 90, 181)
+    x0 = random_x(prob.A.n, 1, seed=48)
+    tuned = pk.from_problem(prob, tune=1, strategy=pk.STRATEGY_TWO_PASS)
+    ti = tuned.suppy_info_get()
+    for col_map in (1, 2):
+        ctx = pk.from_problem(prob, strategy=pk.STRATEGY_TWO_PASS,
+                              stream_shape=(ti["tile"], ti["stages"], ti["lanes_per_row"]),
+                              stream_map=ti["map"], stream_col_map=col_map)
+        info = ctx.suppy_info_get()
+        assert (info["tile"], info["stages"], info["lanes_per_row"], info["map"]) == \
+            (ti["tile"], ti["stages"], ti["lanes_per_row"], ti["map"])
+        assert info["col_map"] == col_map
+        ctx.suppy_set_x(x0)
+        ctx.suppy_sweep(_params(), 1)
+        xo, _ = _oracle_sweep(prob, x0)
+        assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+        ctx.close()
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(prob, stream_col_map=3)
+    tuned.close()
+
+
 @pytest.mark.parametrize("shape", [(300, 0, 0), (8192, 0, 0), (0, 1, 0), (0, 40, 0), (0, 0, 5)])
 def test_invalid_stream_shapes_are_rejected(shape):
     prob = small_ct()
