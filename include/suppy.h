@@ -203,6 +203,15 @@ typedef struct {
      * stream shape, a configuration the tuner chose can be rebuilt without
      * timing, e.g. under a profiler).  Other values give SUPPY_EINVAL. */
     int32_t stream_col_map;
+    /* One-pass sweep with L2-reduction scatter on an image grid (img_h x
+     * img_w = n, one right-hand side): a row whose entries run down the image
+     * (it spans more image rows than columns) adds its corrections into a
+     * second accumulator indexed column-major, where its consecutive entries
+     * are neighbours and share 32-byte sectors; the box step adds the two.
+     * The same sums, fewer reduction requests.  0 automatic (on when
+     * eligible), 1 on (SUPPY_EINVAL when there is no image grid or several
+     * right-hand sides), -1 off.  Other values give SUPPY_EINVAL. */
+    int32_t scatter_transpose;
 } suppy_opts;
 
 /* Parameters of Algorithm 1 and of the stopping rule.  suppy_params_default
@@ -274,6 +283,9 @@ typedef struct {
      * segments of the tile streams; zero for the other strategies */
     int32_t tiles, chunks, tile_warps1, tile_warps2, tile_coef_warps, tile_ring;
     int64_t tile_stream_bytes, tile_segments;
+    /* one pass with L2 reductions (opts.scatter_transpose): rows scattered
+     * column-major; 0 when the sweep does not use it */
+    int64_t transposed_rows;
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

@@ -59,7 +59,8 @@ class suppy_opts(ctypes.Structure):
                 ("stream_lanes", ctypes.c_int32), ("perturb_path", ctypes.c_int32),
                 ("stream_map", ctypes.c_int32), ("tile_warps1", ctypes.c_int32),
                 ("tile_chunk_bytes", ctypes.c_int32), ("tile_ring_bytes", ctypes.c_int32),
-                ("tile_group_rows", ctypes.c_int32), ("stream_col_map", ctypes.c_int32)]
+                ("tile_group_rows", ctypes.c_int32), ("stream_col_map", ctypes.c_int32),
+                ("scatter_transpose", ctypes.c_int32)]
 
 
 class suppy_params(ctypes.Structure):
@@ -115,7 +116,7 @@ class suppy_info(ctypes.Structure):
                 ("chunks", ctypes.c_int32), ("tile_warps1", ctypes.c_int32),
                 ("tile_warps2", ctypes.c_int32), ("tile_coef_warps", ctypes.c_int32),
                 ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
-                ("tile_segments", ctypes.c_int64)]
+                ("tile_segments", ctypes.c_int64), ("transposed_rows", ctypes.c_int64)]
 
 
 _lib = None
@@ -247,7 +248,8 @@ class Context:
                  mode=SUPPY_CIMMINO, block_of_row=None, obj=SUPPY_OBJ_NONE, shape=None,
                  c_lin=None, obj_rows=None, nrhs=1, tune=0, strategy=0, tma=0, stream=None,
                  stream_shape=(0, 0, 0), perturb_path=0, stream_map=0, tile_warps1=0,
-                 tile_chunk_bytes=0, tile_ring_bytes=0, tile_group_rows=0, stream_col_map=0):
+                 tile_chunk_bytes=0, tile_ring_bytes=0, tile_group_rows=0, stream_col_map=0,
+                 scatter_transpose=0):
         lib = load_library()
         self._lib = lib
         keep = []
@@ -290,6 +292,7 @@ class Context:
         o.tile_ring_bytes = int(tile_ring_bytes)
         o.tile_group_rows = int(tile_group_rows)
         o.stream_col_map = int(stream_col_map)
+        o.scatter_transpose = int(scatter_transpose)
         ctx = ctypes.c_void_p()
         self._keep = keep
         self.m, self.n, self.nrhs = int(m), int(n), int(nrhs)
@@ -461,7 +464,8 @@ class Context:
 def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NONE, device=False,
                  stream=None, tune=0, strategy=0, tma=0, stream_shape=(0, 0, 0),
                  perturb_path=0, stream_map=0, tile_warps1=0, tile_chunk_bytes=0,
-                 tile_ring_bytes=0, tile_group_rows=0, stream_col_map=0) -> Context:
+                 tile_ring_bytes=0, tile_group_rows=0, stream_col_map=0,
+                 scatter_transpose=0) -> Context:
     """Create a context from a ``synth.Problem`` (host arrays, or copied to the
     current CUDA device first when ``device`` is True)."""
     A = prob.A
@@ -489,7 +493,8 @@ def from_problem(prob, *, dtype=SUPPY_F32, mode=SUPPY_CIMMINO, obj=SUPPY_OBJ_NON
                    strategy=strategy, tma=tma, stream_shape=stream_shape,
                    perturb_path=perturb_path, stream_map=stream_map, tile_warps1=tile_warps1,
                    tile_chunk_bytes=tile_chunk_bytes, tile_ring_bytes=tile_ring_bytes,
-                   tile_group_rows=tile_group_rows, stream_col_map=stream_col_map, **kw)
+                   tile_group_rows=tile_group_rows, stream_col_map=stream_col_map,
+                   scatter_transpose=scatter_transpose, **kw)
 
 
 def suppy_sweep_static(row_ptr, col, val, m, n, l, u, weight, lam, box_lo, box_hi, x,

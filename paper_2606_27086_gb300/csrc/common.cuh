@@ -101,6 +101,9 @@ struct FinalizeArgs {
     int B;
     int box_len;            // 1 or n
     EpiArgs epi;
+    // column-major second accumulator of the one-pass scatter (B = 1) or null
+    float* deltaT;
+    int imgW, imgH;
 };
 
 // Column pass of the two-pass sweep: x_j <- box(x_j + sum_i a_ij coef_i)
@@ -196,6 +199,13 @@ struct StreamArgs {
     EpiArgs epi;
     unsigned* ticket;       // column pass of the last block: CTAs finished (the
                             // last one runs the sweep epilogue), or null
+    // one-pass scatter on an H x W image: rows with rowT[i] set add into
+    // deltaT at the column-major index (j mod W) * H + j / W (j / W by a
+    // multiply-high with recipW = floor((2^64 - 1) / W) + 1).
+    const unsigned char* rowT;
+    float* deltaT;
+    unsigned long long recipW;
+    int imgW, imgH;
 };
 
 // Tiled one-pass sweep (tile.cu): one cooperative launch of P CTAs, CTA b
@@ -486,6 +496,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// Column-major index (j mod W) * H + j / W of the row-major pixel j of an
+// H x W image.  j / W is the high word of j * recipW with recipW =
+// floor((2^64 - 1) / W) + 1 = 2^64 / W + e, 0 <= e <= 1: the product over 2^64
+// is j / W + j e / 2^64, and j e / 2^64 < 2^-32 <= 1/W never carries past the
+// next integer because the fractional part of j / W is at most 1 - 1/W
+// (j < 2^32, 2 <= W <= 2^32).
+__device__ __forceinline__ int transposed_index(int j, unsigned long long recipW, int W, int H) {
+    const int q = (int)__umul64hi((unsigned long long)(unsigned)j, recipW);
+    return (j - q * W) * H + q;
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) {

@@ -496,6 +496,8 @@ struct RowWork {
     // the row multiplier of the coefficient (coef_mul) or of the proximity
     // term (prox_mul): a pass sets at most one of them
     float m = 1.f, nm = 1.f;
+    // the row scatters into the column-major accumulator (a.rowT)
+    bool tr = false, ntr = false;
     // The group leader's proximity terms are summed in FP32 with Kahan
     // compensation (error independent of the term count) and widened to FP64
     // for the CTA and grid reductions: FP64 arithmetic is scarce on GB300 and
@@ -515,6 +517,7 @@ struct RowWork {
             nw = __ldg(a.wr + i);
             const float* mp = a.coef_mul ? a.coef_mul : a.prox_mul;
             if (mp) nm = __ldg(mp + i);
+            if (SCAT == 1 && a.rowT) ntr = __ldg(a.rowT + i) != 0;
         }
     }
     __device__ void advance() {
@@ -522,6 +525,7 @@ struct RowWork {
         ui = nu;
         w = nw;
         m = nm;
+        tr = ntr;
     }
     __device__ void empty(int) {}   // an empty row: no coefficient, no proximity term
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl,
@@ -535,10 +539,14 @@ struct RowWork {
         if (SCAT == 0) {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
-            // lane-strided over the elements: consecutive lanes, consecutive columns
+            // lane-strided over the elements: consecutive lanes, consecutive
+            // columns (column-major ones for a row running down the image)
             int p = r.pos(g0 + gl);
+            float* dst = tr ? a.deltaT : a.delta;
             for (int t = gl; t < len; t += G) {
-                atomicAdd(a.delta + r.idx[p], coef * to_f(r.val[p]));
+                const int j = r.idx[p];
+                const int jt = (SCAT == 1 && a.rowT) ? transposed_index(j, a.recipW, a.imgW, a.imgH) : j;
+                atomicAdd(dst + (tr ? jt : j), coef * to_f(r.val[p]));
                 r.step(p, G);
             }
         }

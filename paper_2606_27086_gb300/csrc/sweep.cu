@@ -13,6 +13,8 @@
 //  * two-pass: the row pass writes coef_i only; a column pass streams the CSC
 //    copy of A and computes x_j <- box(x_j + sum_i a_ij coef_i) with gathers
 //    of coef from L2, no atomics at all (bitwise deterministic).
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace suppy {
@@ -513,6 +515,48 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
     }
 }
 
+// The same box step with the one-pass scatter's column-major second
+// accumulator (one right-hand side on an H x W image): x_j <- clamp(x_j +
+// delta_j + deltaT_(c,r), lo, hi) for pixel j = (r, c), both accumulators
+// cleared.  32 x 32 pixel tiles: deltaT is read and cleared along its
+// columns and transposed through shared memory, so both sides stay coalesced.
+constexpr int kTrTile = 32;
+__global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
+    __shared__ float t[kTrTile][kTrTile + 1];
+    const int H = a.imgH, W = a.imgW;
+    const int tw = (W + kTrTile - 1) / kTrTile;
+    const long long ntiles = (long long)tw * ((H + kTrTile - 1) / kTrTile);
+    const int tx = threadIdx.x % kTrTile, ty = threadIdx.x / kTrTile;
+    const int rows = blockDim.x / kTrTile;
+    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int r0 = (int)(ti / tw) * kTrTile, c0 = (int)(ti % tw) * kTrTile;
+        for (int k = ty; k < kTrTile; k += rows) {
+            const int c = c0 + k, r = r0 + tx;
+            float v = 0.f;
+            if (c < W && r < H) {
+                float* q = a.deltaT + (long long)c * H + r;
+                v = *q;
+                *q = 0.f;
+            }
+            t[k][tx] = v;
+        }
+        __syncthreads();
+        for (int k = ty; k < kTrTile; k += rows) {
+            const int r = r0 + k, c = c0 + tx;
+            if (r < H && c < W) {
+                const long long j = (long long)r * W + c;
+                float d = a.delta[j] + t[tx][k];
+                if (a.zc) d *= a.zc[j];
+                const long long bj = (a.box_len == 1) ? 0 : j;
+                a.x[j] = clampf(a.x[j] + d, a.lo[bj], a.hi[bj]);
+                a.delta[j] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) sweep_epilogue(a.epi);
+}
+
 // Sum partials pp[c*B + b] over c in a fixed order: out[b] (+)= scale * sum.
 __global__ void k_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                             double* out) {
@@ -728,6 +772,14 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
+    if (a.deltaT) {
+        if (a.B != 1 || a.imgW < 1 || a.imgH < 1 || (long long)a.imgW * a.imgH != a.nB)
+            return cudaErrorInvalidValue;
+        const long long tiles = (long long)((a.imgW + kTrTile - 1) / kTrTile) *
+                                ((a.imgH + kTrTile - 1) / kTrTile);
+        k_finalize_tr<<<(int)std::min<long long>(tiles, 2048), 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     k_finalize<<<grid, kFinalizeThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

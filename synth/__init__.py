@@ -473,5 +473,35 @@ def random_problem(m: int, n: int, seed: int, feasible: bool = True, delta: floa
                    np.full(1, box[1], np.float32), x_true=xt.astype(np.float32))
 
 
+def line_problem(H: int, W: int, m: int, seed: int, delta: float = 0.03) -> Problem:
+    """Rows along random straight segments of an H x W pixel grid (uniform
+    direction, 20-80 unit steps from a random start, the pixels visited,
+    weights U(0.2, 1)): ray-like rows on a grid that need not be square.
+    Slabs b(1 -/+ delta) around b = A x_T perturbed by 20% noise."""
+    rng = np.random.default_rng(seed)
+    cols, lens = [], []
+    for _ in range(m):
+        th = rng.uniform(0.0, np.pi)
+        r0, c0 = rng.uniform(0, H), rng.uniform(0, W)
+        t = np.arange(int(rng.integers(20, 81)))
+        rr = np.floor(r0 + t * np.sin(th)).astype(np.int64)
+        cc = np.floor(c0 + t * np.cos(th)).astype(np.int64)
+        ok = (rr >= 0) & (rr < H) & (cc >= 0) & (cc < W)
+        j = np.unique(rr[ok] * W + cc[ok])
+        cols.append(j)
+        lens.append(len(j))
+    rp = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    col = np.concatenate(cols).astype(np.int32) if m else np.zeros(0, np.int32)
+    val = rng.uniform(0.2, 1.0, size=len(col)).astype(np.float32)
+    A = CSR(m, H * W, rp.astype(np.int32), col, val)
+    xt = rng.uniform(0.0, 1.0, size=H * W)
+    b = A.to_scipy() @ xt
+    b = b * (1.0 + 0.2 * rng.standard_normal(m))
+    l, u = slab_bounds(b, delta)
+    return Problem(f"lines{H}x{W}", A, l, u, np.zeros(1, np.float32), np.ones(1, np.float32),
+                   shape=(H, W), x_true=xt.astype(np.float32))
+
+
 def num_threads() -> int:
     return int(_load().synth_num_threads())

@@ -1,0 +1,104 @@
+"""One-pass sweep whose rows running down the image scatter into a
+column-major accumulator (opts.scatter_transpose), against the FP64 oracle.
+
+The sweep computes the same Eq. (3) step either way (Sec. 2.1.1): only the
+order of the FP32 additions changes, so the per-sweep bound stays 1e-5
+relative L2.  Sizes keep n * 4 bytes above 64 KB, where the one-pass sweep
+scatters by L2 reductions (the transposed accumulator serves only that
+form).  Covered: square and non-square grids (the index map divides by the
+width), Cimmino, BIP with angle blocks (a box step per block), DROP (the
+column scaling applies to the sum of both accumulators), a superiorized run
+with graphs, and the rejections.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_27086_gb300 as pk
+import synth
+from tests.helpers import oracle_objective, random_x, rel, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def _one_sweep(prob, mode=O.CIMMINO, lam=1.0, **kw):
+    ctx = pk.from_problem(prob, mode=mode, strategy=pk.STRATEGY_ONE_PASS, **kw)
+    info = ctx.suppy_info_get()
+    x0 = random_x(prob.A.n, 1, seed=91)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(pk.suppy_params_default(lam=lam), 1)
+    xg = ctx.suppy_get_x()
+    ph, _ = ctx.suppy_history()
+    S, l, u, lo, hi = O.from_problem(prob, mode)
+    xo, po = O.sweep(S, mode, l, u, lam, lo, hi, x0.astype(np.float64))
+    ctx.close()
+    return info, xg, ph, xo, po
+
+
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+@pytest.mark.parametrize("tr", [1, -1])
+def test_ct_one_sweep(mode, tr):
+    prob = synth.ct_problem(160, 120, 227)
+    if mode == O.BIP:
+        prob.blocks = synth.angle_blocks(120, 227, 12)
+    info, xg, ph, xo, po = _one_sweep(prob, mode, scatter_transpose=tr)
+    assert info["strategy"] == pk.STRATEGY_ONE_PASS and info["scatter"] == 1
+    if tr == 1:
+        # about half of the rays are steeper than 45 degrees
+        assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
+    else:
+        assert info["transposed_rows"] == 0
+    assert rel_l2(xg, xo) <= 1e-5
+    assert rel(ph[0], po) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", [(96, 211), (211, 96)])
+def test_non_square_grid(shape):
+    H, W = shape
+    prob = synth.line_problem(H, W, 1500, seed=H)
+    info, xg, ph, xo, po = _one_sweep(prob, lam=1.3, scatter_transpose=1)
+    # segments in uniform directions: about half run down the image
+    assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
+    assert rel_l2(xg, xo) <= 1e-5
+    assert rel(ph[0], po) <= 1e-5
+
+
+def test_drop_scales_both_accumulators():
+    prob = synth.ct_problem(160, 120, 227)
+    info, xg, ph, xo, po = _one_sweep(prob, O.DROP, scatter_transpose=1)
+    assert info["transposed_rows"] > 0
+    assert rel_l2(xg, xo) <= 1e-5
+
+
+def test_superiorized_run_with_graphs():
+    prob = synth.ct_problem(160, 120, 227)
+    K = 30
+    sup = dict(gamma=0.5, alpha=0.99, n_red=1)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_ONE_PASS,
+                          scatter_transpose=1)
+    assert ctx.suppy_info_get()["transposed_rows"] > 0
+    st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=K, use_graphs=1, **sup))[0]
+    S, l, u, lo, hi = O.from_problem(prob)
+    r = O.run(S, O.CIMMINO, l, u, lo, hi, oracle_objective(prob, O.OBJ_TV_ISO),
+              O.Params(max_sweeps=K, **sup))
+    assert st["sweeps"] == K and abs(st["accepted"] - sum(r.accepted)) <= 2
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3
+    ph, fh = ctx.suppy_history()
+    assert np.max(np.abs(np.asarray(ph) - r.prox_hist) / np.abs(r.prox_hist)) <= 1e-3
+    assert rel(fh[-1], r.obj_hist[-1]) <= 1e-3
+    ctx.close()
+
+
+def test_rejections():
+    prob = synth.random_problem(300, 30000, seed=3, mean_len=40)   # no image grid
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(prob, scatter_transpose=1)
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(synth.ct_problem(160, 120, 227), scatter_transpose=2)
+    two = synth.ct_problem(160, 120, 227, nrhs=2)
+    with pytest.raises(pk.SuppyError):
+        pk.from_problem(two, scatter_transpose=1)

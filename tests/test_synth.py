@@ -84,3 +84,18 @@ def test_random_problem_row_mix():
                          long_len=290)
     lens = np.diff(A.row_ptr)
     assert (lens == 0).sum() > 20 and (lens == 290).sum() == 3
+
+
+def test_line_problem_rows_are_segments_on_the_grid():
+    H, W = 96, 211
+    p = synth.line_problem(H, W, 400, seed=5)
+    A = p.A
+    assert p.shape == (H, W) and A.n == H * W and A.m == 400
+    assert A.col.min() >= 0 and A.col.max() < H * W
+    for i in range(0, A.m, 37):
+        j = A.col[A.row_ptr[i]:A.row_ptr[i + 1]]
+        assert np.all(np.diff(j) > 0)            # sorted, no repeats
+        assert 1 <= len(j) <= 80
+    q = synth.line_problem(H, W, 400, seed=5)
+    assert np.array_equal(q.A.col, A.col) and np.array_equal(q.l, p.l)
+    assert np.all(p.l <= p.u)
