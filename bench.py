@@ -21,6 +21,7 @@ Under torchrun each rank runs an independent replica (weak scaling).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -628,7 +629,8 @@ def _serve_batched(pk, mats, reqs, dtype):
     peak_bytes = srv.suppy_server_device_bytes()
     srv.close()
     torch.cuda.synchronize()
-    name = "bf16 A" if dtype == pk.SUPPY_BF16 else "f32 A"
+    name = {pk.SUPPY_BF16: "bf16 A", pk.SUPPY_F16: "f16 A", pk.SUPPY_F32: "f32 A"}.get(
+        dtype, "16-bit A (FP16 or BF16 per matrix, the smaller rounding error)")
     arrivals = reqs[-1][0]
     figs = {"solves_per_s": len(reqs) / max(fin), "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "makespan_s": max(fin),
@@ -646,7 +648,8 @@ def _serve_batched(pk, mats, reqs, dtype):
 
 
 def serving(pk, nreq: int):
-    """Batched continuous-batching server (BF16 A, and FP32 A for a comparison
+    """Batched continuous-batching server (16-bit A: FP16 or BF16 per matrix,
+    whichever rounds it with the smaller error; and FP32 A for a comparison
     at equal precision) against one-at-a-time FP32 solves of the same requests
     (arrival times kept, queueing included).  Per request, the final
     proximity and objective are compared with the one-at-a-time solve; a
@@ -655,7 +658,16 @@ def serving(pk, nreq: int):
     request's last sweep)."""
     import torch
     mats, reqs = serving_workload(pk, nreq)
-    batched, per_b = _serve_batched(pk, mats, reqs, pk.SUPPY_BF16)
+    batched, per_b = _serve_batched(pk, mats, reqs, pk.SUPPY_HALF_AUTO)
+    # the 16-bit format the library takes for each matrix
+    fmt = {}
+    for prob, spec in mats:
+        one = dataclasses.replace(prob, l=prob.l if prob.l.ndim == 1 else prob.l[:, 0].copy(),
+                                  u=prob.u if prob.u.ndim == 1 else prob.u[:, 0].copy())
+        c = pk.from_problem(one, dtype=pk.SUPPY_HALF_AUTO)
+        fmt[spec["name"]] = "f16" if c.suppy_info_get()["a_dtype"] == pk.SUPPY_F16 else "bf16"
+        c.close()
+    batched["formats"] = fmt
     batched32, per_b32 = _serve_batched(pk, mats, reqs, pk.SUPPY_F32)
     # one at a time, FP32, per-matrix context resident after first use
     ctxs = {}

@@ -77,8 +77,14 @@ typedef enum {
 
 /* Storage type of A's values on the device.  BF16/FP16 are rounded to nearest
  * even from the FP32 input; every accumulation stays FP32 (dot products,
- * corrections) or FP64 (row norms, proximity, objective, acceptance). */
-typedef enum { SUPPY_F32 = 0, SUPPY_BF16 = 1, SUPPY_F16 = 2 } suppy_dtype;
+ * corrections) or FP64 (row norms, proximity, objective, acceptance).
+ * SUPPY_HALF_AUTO stores 16 bits in the format with the smaller rounding
+ * error on this matrix: per entry the error bound is max(2^-11 |v|, 2^-25)
+ * for FP16 (its unit roundoff, and half its subnormal spacing) and 2^-8 |v|
+ * for BF16; FP16 is taken when no magnitude exceeds 65504 and its bounds,
+ * summed in squares over the entries, are at most BF16's, else BF16.
+ * suppy_info reports the choice. */
+typedef enum { SUPPY_F32 = 0, SUPPY_BF16 = 1, SUPPY_F16 = 2, SUPPY_HALF_AUTO = 3 } suppy_dtype;
 
 /* Feasibility-seeking operator T (Sec. 2.1.1). */
 /* SUPPY_CIMMINO: simultaneous projections, w_i = 1/m' (Sec. 2.1.1).
@@ -286,6 +292,7 @@ typedef struct {
     /* one pass with L2 reductions (opts.scatter_transpose): rows scattered
      * column-major; 0 when the sweep does not use it */
     int64_t transposed_rows;
+    int32_t a_dtype;              /* storage type of A's values (HALF_AUTO resolved) */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("SUPPY_LIBRARY") or os.path.join(_HERE, "libsuppy_gb300.so")
 
 SUPPY_OK, SUPPY_EINVAL, SUPPY_ENOMEM, SUPPY_ECUDA, SUPPY_ETIMEOUT, SUPPY_ESTATE = 0, -1, -2, -3, -4, -5
-SUPPY_F32, SUPPY_BF16, SUPPY_F16 = 0, 1, 2
+SUPPY_F32, SUPPY_BF16, SUPPY_F16, SUPPY_HALF_AUTO = 0, 1, 2, 3
 SUPPY_CIMMINO, SUPPY_BIP, SUPPY_DROP, SUPPY_EL, SUPPY_EMR = 0, 1, 2, 3, 4
 SUPPY_OBJ_NONE, SUPPY_OBJ_TV_ISO, SUPPY_OBJ_TV_ANISO, SUPPY_OBJ_LINEAR = 0, 1, 2, 3
 SUPPY_OBJ_L1, SUPPY_OBJ_L2 = 4, 5
@@ -116,7 +116,8 @@ class suppy_info(ctypes.Structure):
                 ("chunks", ctypes.c_int32), ("tile_warps1", ctypes.c_int32),
                 ("tile_warps2", ctypes.c_int32), ("tile_coef_warps", ctypes.c_int32),
                 ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
-                ("tile_segments", ctypes.c_int64), ("transposed_rows", ctypes.c_int64)]
+                ("tile_segments", ctypes.c_int64), ("transposed_rows", ctypes.c_int64),
+                ("a_dtype", ctypes.c_int32)]
 
 
 _lib = None

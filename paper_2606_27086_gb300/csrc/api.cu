@@ -1677,7 +1677,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     c->n = A->n;
     c->nnz = A->nnz;
     c->dt = o->a_dtype;
-    if (c->dt != SUPPY_F32 && c->dt != SUPPY_BF16 && c->dt != SUPPY_F16)
+    if (c->dt != SUPPY_F32 && c->dt != SUPPY_BF16 && c->dt != SUPPY_F16 && c->dt != SUPPY_HALF_AUTO)
         return fail(c, SUPPY_EINVAL, "unknown a_dtype");
     c->mode = o->mode;
     if (c->mode != SUPPY_CIMMINO && c->mode != SUPPY_BIP && c->mode != SUPPY_DROP &&
@@ -1825,7 +1825,13 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     int* d_flags = nullptr;
     if ((s = dalloc(c, &d_flags, 8)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(d_flags, 0, 8 * sizeof(int), c->stream));
-    CK(launch_validate_csr(s_rp, s_col, s_val, m, n, A->nnz, d_flags, c->stream));
+    // HALF_AUTO: the summed squared rounding-error bounds of FP16 and BF16
+    double* d_err2 = nullptr;
+    if (c->dt == SUPPY_HALF_AUTO) {
+        if ((s = dalloc(c, &d_err2, 2)) != SUPPY_OK) return s;
+        CK(cudaMemsetAsync(d_err2, 0, 2 * sizeof(double), c->stream));
+    }
+    CK(launch_validate_csr(s_rp, s_col, s_val, m, n, A->nnz, d_flags, c->stream, d_err2));
     CK(launch_validate_vec(s_l, (long long)mB, 1, d_flags + 1, 1, c->stream));
     CK(launch_validate_vec(s_u, (long long)mB, 1, d_flags + 1, 2, c->stream));
     CK(launch_validate_pair(s_l, s_u, (long long)mB, d_flags + 1, 4, c->stream));
@@ -1838,6 +1844,15 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (hf[0] & 1) return fail(c, SUPPY_EINVAL, "row_ptr is not a valid CSR row pointer");
     if (hf[0] & 2) return fail(c, SUPPY_EINVAL, "column index outside [0, n)");
     if (hf[0] & 4) return fail(c, SUPPY_EINVAL, "matrix value is NaN or infinite");
+    // 16 bits in the format whose rounding errors, summed in squares, are the
+    // smaller one (FP16 only when no value overflows it)
+    if (c->dt == SUPPY_HALF_AUTO) {
+        double e2[2] = {0.0, 0.0};
+        CK(cudaMemcpyAsync(e2, d_err2, sizeof(e2), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        dfree(c, d_err2);
+        c->dt = (!(hf[0] & 8) && e2[0] <= e2[1]) ? SUPPY_F16 : SUPPY_BF16;
+    }
     if (hf[1] & 3) return fail(c, SUPPY_EINVAL, "NaN in the slab bounds l or u");
     if (hf[1] & 4) return fail(c, SUPPY_EINVAL, "slab bounds need l <= u");
     if (hf[2] & 3) return fail(c, SUPPY_EINVAL, "NaN in the box bounds");
@@ -2991,6 +3006,7 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->tile_ring = c->strategy == 3 ? c->tistages * c->tipiece : 0;
     out->tile_stream_bytes = c->strategy == 3 ? c->tibytes : 0;
     out->tile_segments = c->strategy == 3 ? c->tisegs : 0;
+    out->a_dtype = (int32_t)c->dt;
     out->transposed_rows =
         (c->strategy == 1 && c->scat == 1 && c->use_tma && c->d_rowT && c->tr_on) ? c->trows : 0;
     out->map = c->use_tma ? c->tMap + 1 : 0;

@@ -374,7 +374,8 @@ cudaError_t launch_variance(float* x, float* xprev, long long n, int B, RhsState
                             double* part, unsigned* ticket, double tol, int grid, cudaStream_t s);
 
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,
-                                int n, long long nnz, int* flags, cudaStream_t s);
+                                int n, long long nnz, int* flags, cudaStream_t s,
+                                double* err2 = nullptr);
 cudaError_t launch_validate_vec(const float* v, long long len, int allow_inf, int* flags,
                                 int bit, cudaStream_t s);
 cudaError_t launch_validate_pair(const float* lo, const float* hi, long long len, int* flags,

@@ -9,11 +9,15 @@
 namespace suppy {
 namespace {
 
-// flags bits
-constexpr int kBadRowPtr = 1, kBadCol = 2, kBadVal = 4;
+// flags bits (kF16Over: a magnitude above FP16's largest finite value)
+constexpr int kBadRowPtr = 1, kBadCol = 2, kBadVal = 4, kF16Over = 8;
 
+// With err2 set, also the squared rounding-error bounds of storing the values
+// in FP16 and in BF16, summed over the entries: err2[0] += max(2^-11 |v|,
+// 2^-25)^2 (unit roundoff 2^-11 in the normal range, half the subnormal
+// spacing below it), err2[1] += (2^-8 v)^2 (BF16 keeps FP32's range).
 __global__ void k_validate_csr(const int* rp, const int* col, const float* val, int m, int n,
-                               long long nnz, int* flags) {
+                               long long nnz, int* flags, double* err2) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (long long i = t0; i < m; i += stride) {
@@ -21,10 +25,40 @@ __global__ void k_validate_csr(const int* rp, const int* col, const float* val, 
         if (a > b || a < 0 || (long long)b > nnz) atomicOr(flags, kBadRowPtr);
     }
     if (t0 == 0 && (rp[0] != 0 || (long long)rp[m] != nnz)) atomicOr(flags, kBadRowPtr);
+    double e16 = 0.0, ebf = 0.0;
     for (long long e = t0; e < nnz; e += stride) {
         const int c = col[e];
         if (c < 0 || c >= n) atomicOr(flags, kBadCol);
-        if (!isfinite(val[e])) atomicOr(flags, kBadVal);
+        const float v = fabsf(val[e]);
+        if (!isfinite(v)) {
+            atomicOr(flags, kBadVal);
+        } else if (err2) {
+            if (v > 65504.f) atomicOr(flags, kF16Over);
+            const double a = fmax(0x1p-11 * (double)v, v != 0.f ? 0x1p-25 : 0.0);
+            const double b = 0x1p-8 * (double)v;
+            e16 += a * a;
+            ebf += b * b;
+        }
+    }
+    if (err2) {
+        __shared__ double s16[8], sbf[8];
+        e16 = warp_sum(e16);
+        ebf = warp_sum(ebf);
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) {
+            s16[w] = e16;
+            sbf[w] = ebf;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+                a += s16[k];
+                b += sbf[k];
+            }
+            atomicAdd(err2, a);
+            atomicAdd(err2 + 1, b);
+        }
     }
 }
 
@@ -283,9 +317,9 @@ inline int grid_for(long long work, int threads = 256) {
 }  // namespace
 
 cudaError_t launch_validate_csr(const int* row_ptr, const int* col, const float* val, int m,
-                                int n, long long nnz, int* flags, cudaStream_t s) {
+                                int n, long long nnz, int* flags, cudaStream_t s, double* err2) {
     k_validate_csr<<<grid_for(nnz > m ? nnz : m), 256, 0, s>>>(row_ptr, col, val, m, n, nnz,
-                                                               flags);
+                                                               flags, err2);
     return cudaGetLastError();
 }
 

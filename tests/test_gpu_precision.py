@@ -89,3 +89,33 @@ def test_ct512_error_vs_fp64_oracle(dtype):
     print(f"ct512 one sweep {dtype}: {rel_l2(x1, s64):.3e}; 3 iterations: {err:.3e} "
           f"(rounding alone {rounding:.3e})")
     ctx.close()
+
+
+def _scaled(prob, s):
+    import copy
+    q = copy.deepcopy(prob)
+    q.A.val = (prob.A.val.astype(np.float64) * s).astype(np.float32)
+    q.l = (prob.l.astype(np.float64) * s).astype(np.float32)
+    q.u = (prob.u.astype(np.float64) * s).astype(np.float32)
+    return q
+
+
+@pytest.mark.parametrize("scale,want", [(1.0, "f16"), (1e7, "bf16"), (1e-6, "bf16")])
+def test_half_auto_takes_the_format_with_the_smaller_error(scale, want):
+    """SUPPY_HALF_AUTO: FP16 for the CT values (in FP16's range: unit
+    roundoff 2^-11 against BF16's 2^-8); BF16 when values exceed 65504, or
+    when they sit so far below FP16's normal range that its absolute error
+    (2^-25) exceeds BF16's relative one.  The sweep then matches the oracle
+    on the values rounded to the chosen format (scaling A and the slabs by
+    the same factor leaves the projections unchanged)."""
+    prob = _scaled(synth.ct_problem(), scale)
+    ctx = pk.from_problem(prob, dtype=pk.SUPPY_HALF_AUTO)
+    got = ctx.suppy_info_get()["a_dtype"]
+    assert got == {"f16": pk.SUPPY_F16, "bf16": pk.SUPPY_BF16}[want]
+    x0 = np.random.default_rng(4).uniform(0, 1, prob.A.n).astype(np.float32)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(pk.suppy_params_default(), 1)
+    S, l, u, lo, hi = O.from_problem(prob, values=rounded_values(prob.A.val, want))
+    xo, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x0.astype(np.float64))
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+    ctx.close()
