@@ -396,6 +396,7 @@ def variants(pk, K, W):
                      "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B, "kernels": per,
                      "create_s": t_create, "strategy": info["strategy"],
                      "scatter": info["scatter"], "nblocks": info["nblocks"], "tma": info["tma"],
+                     "transposed_rows": info["transposed_rows"], "a_dtype": info["a_dtype"],
                      "launches_per_step": nl / Kv}
         if info["strategy"] == 3:
             out[name]["tiles"] = {k: info[k] for k in ("tiles", "chunks", "tile_warps1",
@@ -869,7 +870,7 @@ def ours(args):
                                                   "tile_segments", "tile", "stages", "col_tile",
                                                   "col_stages", "map", "col_map",
                                                   "lanes_per_row", "col_lanes",
-                                                  "perturb_cluster")}}
+                                                  "transposed_rows", "perturb_cluster")}}
     if args.pin:
         res["launch_shape"]["pinned"] = args.pin
     ctx.close()
