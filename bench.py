@@ -905,7 +905,7 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
     (two each, after the iterations); case 10: a 2048x2048 image over a
     random slab system (20000 rows) with TV, whose image bands exceed a
     cluster's shared memory, so the cluster perturbation reads them from
-    global memory.
+    global memory; case 11: CT 384x384 with the tiled one-pass sweep.
     The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches and the
     `warm` iterations run before it."""
@@ -944,6 +944,10 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
         prob.shape = (2048, 2048)
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TWO_PASS,
                               perturb_path=1)
+    elif case == 11:
+        prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
+                                seed_noise=202)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TILED)
     elif case in (3, 4):
         prob = ct512()
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
@@ -996,7 +1000,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512,
                     help="also run the serving mix with this many requests (512: the full "
                          "trace; 0 skips it) and report it under 'serving'")
-    ap.add_argument("--profile", type=int, default=0, choices=list(range(11)),
+    ap.add_argument("--profile", type=int, default=0, choices=list(range(12)),
                     help="run a short profiling case and exit: CT 384x384 (270 angles x 545 "
                          "bins) with sweep strategy 1 (one pass) or 2 (two passes), or the "
                          "CT 512x512 workload with tuned launch shapes: 3 two passes, 4 one "
@@ -1005,7 +1009,7 @@ def main():
                          "CT 384x384 with EMR and the variance rule; 9 CT 384x384, "
                          "register-fed sweep, cluster perturbation, standalone proximity and "
                          "objective; 10 a 2048x2048 TV image, cluster perturbation from "
-                         "global memory")
+                         "global memory; 11 CT 384x384 with the tiled sweep")
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6,
