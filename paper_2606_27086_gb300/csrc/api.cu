@@ -2081,14 +2081,13 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     hcol_buf.shrink_to_fit();
     // tr: the one pass with L2 reductions scatters the rows running down the
     // image column-major (opts.scatter_transpose); untuned, it does so when
-    // the grid allows it, except that several blocks leave it to the tuner
-    // (each block's box step then also transposes the image)
+    // the grid allows it, and the tuner times both forms
     struct Cand {
         int strategy, scat;
         bool tr;
     };
     const bool have_tr = c->d_rowT != nullptr;
-    const bool tr_default = have_tr && (o->scatter_transpose == 1 || c->nseg == 1);
+    const bool tr_default = have_tr;
     std::vector<Cand> cands;
     if (want == 3) {
         cands.push_back({3, 0, false});

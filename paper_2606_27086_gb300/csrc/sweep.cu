@@ -522,34 +522,54 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
 // columns and transposed through shared memory, so both sides stay coalesced.
 constexpr int kTrTile = 32;
 __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
+    constexpr int kPer = kTrTile * kTrTile / 256;   // pixels a thread takes per tile
     __shared__ float t[kTrTile][kTrTile + 1];
     const int H = a.imgH, W = a.imgW;
     const int tw = (W + kTrTile - 1) / kTrTile;
     const long long ntiles = (long long)tw * ((H + kTrTile - 1) / kTrTile);
     const int tx = threadIdx.x % kTrTile, ty = threadIdx.x / kTrTile;
-    const int rows = blockDim.x / kTrTile;
     for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const int r0 = (int)(ti / tw) * kTrTile, c0 = (int)(ti % tw) * kTrTile;
-        for (int k = ty; k < kTrTile; k += rows) {
-            const int c = c0 + k, r = r0 + tx;
-            float v = 0.f;
-            if (c < W && r < H) {
-                float* q = a.deltaT + (long long)c * H + r;
-                v = *q;
-                *q = 0.f;
+        // every load of the tile first (one round trip), the clearing
+        // stores right behind them
+        float tv[kPer], dv[kPer], xv[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int k = ty + q * (256 / kTrTile);
+            int c = c0 + k, r = r0 + tx;
+            tv[q] = 0.f;
+            if (c < W && r < H) tv[q] = a.deltaT[(long long)c * H + r];
+            r = r0 + k;
+            c = c0 + tx;
+            dv[q] = 0.f;
+            xv[q] = 0.f;
+            if (r < H && c < W) {
+                const long long j = (long long)r * W + c;
+                dv[q] = a.delta[j];
+                xv[q] = a.x[j];
             }
-            t[k][tx] = v;
+        }
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int k = ty + q * (256 / kTrTile);
+            int c = c0 + k, r = r0 + tx;
+            if (c < W && r < H) a.deltaT[(long long)c * H + r] = 0.f;
+            r = r0 + k;
+            c = c0 + tx;
+            if (r < H && c < W) a.delta[(long long)r * W + c] = 0.f;
+            t[k][tx] = tv[q];
         }
         __syncthreads();
-        for (int k = ty; k < kTrTile; k += rows) {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int k = ty + q * (256 / kTrTile);
             const int r = r0 + k, c = c0 + tx;
             if (r < H && c < W) {
                 const long long j = (long long)r * W + c;
-                float d = a.delta[j] + t[tx][k];
+                float d = dv[q] + t[tx][k];
                 if (a.zc) d *= a.zc[j];
                 const long long bj = (a.box_len == 1) ? 0 : j;
-                a.x[j] = clampf(a.x[j] + d, a.lo[bj], a.hi[bj]);
-                a.delta[j] = 0.f;
+                a.x[j] = clampf(xv[q] + d, a.lo[bj], a.hi[bj]);
             }
         }
         __syncthreads();
