@@ -75,6 +75,8 @@ struct suppy_ctx {
     // order flags), their accumulator, and 2^64 / gW rounded up
     unsigned char* d_rowT = nullptr;
     float* d_deltaT = nullptr;
+    int* d_colT = nullptr;          // the packed indices, those rows' column-major
+    float* d_xT = nullptr;          // x column-major (the two-pass row pass gathers)
     unsigned long long recipW = 0;
     long long trows = 0;
     bool tr_on = false;             // the sweep uses them (chosen at create)
@@ -691,8 +693,11 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     // accumulates A^T(.) into delta, and the extrapolated step applies it
     const bool ext = (c->mode == SUPPY_EL || c->mode == SUPPY_EMR);
     const float lam_row = ext ? 1.f : (float)p->lambda;
-    // one pass with the column-major accumulator (rows running down the image)
+    // one pass with the column-major accumulator (rows running down the image);
+    // two passes with those rows read column-major (their indices and a copy
+    // of x made before each block's row pass: x changes after every block)
     const bool tr_scatter = c->use_tma && c->strategy == 1 && c->scat == 1 && c->d_rowT && c->tr_on;
+    const bool tr_gather = c->use_tma && c->strategy == 2 && c->d_colT && c->tr_on;
     for (int t = 0; t < c->nseg; ++t) {
         SweepArgs a = row_args(c, t, lam_row);
         if (c->mode == SUPPY_EMR) a.coef_mul = c->d_rhof;
@@ -719,6 +724,16 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             sa.lam = lam_row;
             sa.coef_mul = (c->mode == SUPPY_EMR) ? c->d_rhof : nullptr;
             sa.check_stop = 1;
+            if (tr_gather) {
+                Timed tm{c, 0};
+                CK(tm.begin());
+                CK(launch_transpose_image(c->d_x, c->d_xT, c->gH, c->gW, c->stream));
+                CK(tm.end());
+                note_launch(c);
+                sa.idx = c->d_colT;
+                sa.rowT = c->d_rowT;
+                sa.xT = c->d_xT;
+            }
             if (tr_scatter) {
                 sa.rowT = c->d_rowT;
                 sa.deltaT = c->d_deltaT;
@@ -1352,6 +1367,30 @@ suppy_status build_row_orientation(suppy_ctx* c, const std::vector<int>& rp, con
     c->trows = nt;
     CK(cudaStreamSynchronize(c->stream));   // the flags' host copy goes out of scope
     return SUPPY_OK;
+}
+
+// The two-pass row pass with the rows running down the image in the
+// column-major numbering: a copy of the packed column indices with those
+// rows' entries rewritten, and a column-major copy of x made before each row
+// pass.
+suppy_status build_col_transposed(suppy_ctx* c) {
+    if (c->d_colT || !c->d_rowT) return SUPPY_OK;
+    suppy_status s;
+    const size_t rlen = (size_t)c->nnz_pad + kMaxTile + 16;
+    if ((s = dalloc(c, &c->d_colT, rlen)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_xT, (size_t)c->n)) != SUPPY_OK) return s;
+    CK(cudaMemcpyAsync(c->d_colT, c->d_col, sizeof(int) * rlen, cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_transposed_cols(c->d_rinfo, c->d_rowT, c->m, c->recipW, c->gW, c->gH, c->d_colT,
+                              c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+void free_col_transposed(suppy_ctx* c) {
+    dfree(c, c->d_colT);
+    dfree(c, c->d_xT);
+    c->d_colT = nullptr;
+    c->d_xT = nullptr;
 }
 
 // Tiled one-pass sweep: plan the tiles and the chunked segment streams on the
@@ -2048,7 +2087,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     const bool tr_grid = c->B == 1 && c->gH >= 2 && c->gW >= 2;
     if (o->scatter_transpose == 1 && !tr_grid)
         return fail(c, SUPPY_EINVAL, "scatter_transpose needs an image grid and one right-hand side");
-    const bool tr_cand = tr_grid && o->scatter_transpose != -1 && (want == 0 || want == 1) &&
+    const bool tr_cand = tr_grid && o->scatter_transpose != -1 && !ext_mode && want != 3 &&
                          A->nnz > 0;
     std::vector<int> hcol_buf;
     const int* hcol = A->col;
@@ -2096,7 +2135,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         if (want != 2 && !smem_ok && have_tr && o->tune && o->scatter_transpose == 0)
             cands.push_back({1, 1, !tr_default});
         if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1, tr_default});
-        if (need_csc) cands.push_back({2, 0, false});
+        if (need_csc) cands.push_back({2, 0, o->scatter_transpose == 1 && have_tr});
+        if (need_csc && have_tr && o->tune && o->scatter_transpose == 0) cands.push_back({2, 0, true});
         if (tile_ok) cands.push_back({3, 0, false});
     }
     Cand best = cands[0];
@@ -2113,6 +2153,10 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         c->strategy = cd.strategy;
         c->scat = cd.scat;
         c->tr_on = cd.tr;
+        if (cd.strategy == 2 && cd.tr) {
+            suppy_status st2 = build_col_transposed(c);
+            if (st2 != SUPPY_OK) return st2;
+        }
         choose_row_shape(c, mean_len, max_len);
         suppy_status st;
         if ((st = build_row_partition(c)) != SUPPY_OK) return st;
@@ -2176,6 +2220,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
         return s;
     }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
+    if (!(c->strategy == 2 && c->tr_on) && c->d_colT) free_col_transposed(c);
     if (c->strategy != 3 && c->d_tstream) free_tile(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
@@ -3006,8 +3051,8 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->tile_stream_bytes = c->strategy == 3 ? c->tibytes : 0;
     out->tile_segments = c->strategy == 3 ? c->tisegs : 0;
     out->a_dtype = (int32_t)c->dt;
-    out->transposed_rows =
-        (c->strategy == 1 && c->scat == 1 && c->use_tma && c->d_rowT && c->tr_on) ? c->trows : 0;
+    out->transposed_rows = (((c->strategy == 1 && c->scat == 1 && c->d_rowT) ||
+                             (c->strategy == 2 && c->d_colT)) && c->use_tma && c->tr_on) ? c->trows : 0;
     out->map = c->use_tma ? c->tMap + 1 : 0;
     out->col_map = (c->use_tma && c->strategy == 2) ? c->tMapc + 1 : 0;
     if (c->use_tma) {

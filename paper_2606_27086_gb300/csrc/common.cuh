@@ -202,8 +202,12 @@ struct StreamArgs {
     // one-pass scatter on an H x W image: rows with rowT[i] set add into
     // deltaT at the column-major index (j mod W) * H + j / W (j / W by a
     // multiply-high with recipW = floor((2^64 - 1) / W) + 1).
+    // In the two-pass row pass (SCAT 0) such rows' indices in idx are
+    // column-major already, and their gathers read xT, the column-major copy
+    // of x.
     const unsigned char* rowT;
     float* deltaT;
+    const float* xT;
     unsigned long long recipW;
     int imgW, imgH;
 };
@@ -355,6 +359,9 @@ cudaError_t launch_colpass(const ColArgs& a, suppy_dtype dt, int G, int grid, cu
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 int colpass_blocks_per_sm(suppy_dtype dt, int G, int B);
 cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_transpose_image(const float* x, float* xT, int H, int W, cudaStream_t s);
+cudaError_t launch_transposed_cols(const int2* rinfo, const unsigned char* rowT, int m,
+                                   unsigned long long recipW, int W, int H, int* col, cudaStream_t s);
 cudaError_t launch_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                              double* out, cudaStream_t s);
 cudaError_t launch_perturb(const PerturbArgs& a, int cluster, cudaStream_t s);

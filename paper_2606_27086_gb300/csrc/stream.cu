@@ -517,7 +517,7 @@ struct RowWork {
             nw = __ldg(a.wr + i);
             const float* mp = a.coef_mul ? a.coef_mul : a.prox_mul;
             if (mp) nm = __ldg(mp + i);
-            if (SCAT == 1 && a.rowT) ntr = __ldg(a.rowT + i) != 0;
+            if (a.rowT) ntr = __ldg(a.rowT + i) != 0;
         }
     }
     __device__ void advance() {
@@ -531,7 +531,10 @@ struct RowWork {
     __device__ double operator()(int i, int len, int g0, const Ring<VT>& r, int gl,
                                  const RingRelease& rel) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
-        float dot = item_dot<VT, G, MAP, 12, kEarly>(r, g0, len, gl, a.x, rel);
+        // a row running down the image reads the column-major copy of x (its
+        // stored indices are column-major then) in the two-pass row pass
+        const float* xs = (SCAT == 0 && a.xT && tr) ? a.xT : a.x;
+        float dot = item_dot<VT, G, MAP, 12, kEarly>(r, g0, len, gl, xs, rel);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
         const float d = clampf(dot, li, ui) - dot;

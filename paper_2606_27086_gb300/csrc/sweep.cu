@@ -577,6 +577,43 @@ __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
     if (blockIdx.x == 0) sweep_epilogue(a.epi);
 }
 
+// xT <- x column-major (H x W image, one right-hand side), 32 x 32 tiles
+// through shared memory: the copy that the two-pass row pass gathers from for
+// the rows running down the image.
+__global__ void __launch_bounds__(256) k_transpose_image(const float* x, float* xT, int H, int W) {
+    __shared__ float t[kTrTile][kTrTile + 1];
+    const int tw = (W + kTrTile - 1) / kTrTile;
+    const long long ntiles = (long long)tw * ((H + kTrTile - 1) / kTrTile);
+    const int tx = threadIdx.x % kTrTile, ty = threadIdx.x / kTrTile;
+    const int rows = blockDim.x / kTrTile;
+    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int r0 = (int)(ti / tw) * kTrTile, c0 = (int)(ti % tw) * kTrTile;
+        for (int k = ty; k < kTrTile; k += rows) {
+            const int r = r0 + k, c = c0 + tx;
+            t[tx][k] = (r < H && c < W) ? x[(long long)r * W + c] : 0.f;
+        }
+        __syncthreads();
+        for (int k = ty; k < kTrTile; k += rows) {
+            const int c = c0 + k, r = r0 + tx;
+            if (c < W && r < H) xT[(long long)c * H + r] = t[k][tx];
+        }
+        __syncthreads();
+    }
+}
+
+// The column indices of the rows marked in rowT rewritten to column-major
+// pixel indices, in place (one warp per packed row; the rest untouched).
+__global__ void k_transposed_cols(const int2* rinfo, const unsigned char* rowT, int m,
+                                  unsigned long long recipW, int W, int H, int* col) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+        if (!rowT[i]) continue;
+        const int2 ri = rinfo[i];
+        for (int e = lane; e < ri.y; e += 32) col[ri.x + e] = transposed_index(col[ri.x + e], recipW, W, H);
+    }
+}
+
 // Sum partials pp[c*B + b] over c in a fixed order: out[b] (+)= scale * sum.
 __global__ void k_reduce_pp(const double* pp, int npp, int B, double scale, int accumulate,
                             double* out) {
@@ -801,6 +838,21 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
         return cudaGetLastError();
     }
     k_finalize<<<grid, kFinalizeThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_image(const float* x, float* xT, int H, int W, cudaStream_t s) {
+    if (H < 1 || W < 1) return cudaErrorInvalidValue;
+    const long long tiles = (long long)((W + kTrTile - 1) / kTrTile) * ((H + kTrTile - 1) / kTrTile);
+    k_transpose_image<<<(int)std::min<long long>(tiles, 2048), 256, 0, s>>>(x, xT, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transposed_cols(const int2* rinfo, const unsigned char* rowT, int m,
+                                   unsigned long long recipW, int W, int H, int* col, cudaStream_t s) {
+    if (m < 1) return cudaSuccess;
+    const int grid = (int)std::min<long long>(((long long)m * 32 + 255) / 256, 152 * 16);
+    k_transposed_cols<<<grid, 256, 0, s>>>(rinfo, rowT, m, recipW, W, H, col);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,7 @@
-"""One-pass sweep whose rows running down the image scatter into a
-column-major accumulator (opts.scatter_transpose), against the FP64 oracle.
+"""Rows running down the image handled in the column-major pixel numbering
+(opts.scatter_transpose), against the FP64 oracle: in the one-pass sweep
+they scatter into a column-major accumulator, in the two-pass sweep their
+indices are column-major and they gather from a column-major copy of x.
 
 The sweep computes the same Eq. (3) step either way (Sec. 2.1.1): only the
 order of the FP32 additions changes, so the per-sweep bound stays 1e-5
@@ -65,6 +67,46 @@ def test_non_square_grid(shape):
     assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
     assert rel_l2(xg, xo) <= 1e-5
     assert rel(ph[0], po) <= 1e-5
+
+
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+def test_two_pass_reads_those_rows_column_major(mode):
+    """Two passes: the rows running down the image keep column-major indices
+    and gather x from its column-major copy (made before each block's row
+    pass)."""
+    prob = synth.ct_problem(160, 120, 227)
+    if mode == O.BIP:
+        prob.blocks = synth.angle_blocks(120, 227, 12)
+    ctx = pk.from_problem(prob, mode=mode, strategy=pk.STRATEGY_TWO_PASS, scatter_transpose=1)
+    info = ctx.suppy_info_get()
+    assert info["strategy"] == pk.STRATEGY_TWO_PASS and info["tma"] == 1
+    assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
+    x0 = random_x(prob.A.n, 1, seed=92)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(pk.suppy_params_default(lam=1.1), 2)
+    S, l, u, lo, hi = O.from_problem(prob, mode)
+    x = x0.astype(np.float64)
+    for _ in range(2):
+        x, po = O.sweep(S, mode, l, u, 1.1, lo, hi, x)
+    assert rel_l2(ctx.suppy_get_x(), x) <= 1e-5
+    ph, _ = ctx.suppy_history()
+    assert rel(ph[-1], po) <= 1e-5
+    ctx.close()
+
+
+def test_two_pass_non_square_grid_and_proximity():
+    prob = synth.line_problem(211, 96, 1500, seed=7)
+    ctx = pk.from_problem(prob, strategy=pk.STRATEGY_TWO_PASS, scatter_transpose=1)
+    assert ctx.suppy_info_get()["transposed_rows"] > 0
+    x0 = random_x(prob.A.n, 1, seed=93)
+    ctx.suppy_set_x(x0)
+    S, l, u, lo, hi = O.from_problem(prob)
+    # the standalone proximity keeps reading the row-major indices
+    assert rel(float(ctx.suppy_proximity()[0]), O.proximity(S, l, u, x0.astype(np.float64))) <= 1e-5
+    ctx.suppy_sweep(pk.suppy_params_default(), 1)
+    xo, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x0.astype(np.float64))
+    assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
+    ctx.close()
 
 
 def test_drop_scales_both_accumulators():
