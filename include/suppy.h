@@ -209,14 +209,19 @@ typedef struct {
      * stream shape, a configuration the tuner chose can be rebuilt without
      * timing, e.g. under a profiler).  Other values give SUPPY_EINVAL. */
     int32_t stream_col_map;
-    /* One-pass sweep with L2-reduction scatter on an image grid (img_h x
-     * img_w = n, one right-hand side): a row whose entries run down the image
-     * (it spans more image rows than columns) adds its corrections into a
-     * second accumulator indexed column-major, where its consecutive entries
-     * are neighbours and share 32-byte sectors; the box step adds the two.
-     * The same sums, fewer reduction requests.  0 automatic (on when
-     * eligible), 1 on (SUPPY_EINVAL when there is no image grid or several
-     * right-hand sides), -1 off.  Other values give SUPPY_EINVAL. */
+    /* Rows of A that run down the image (on an image grid img_h x img_w = n,
+     * one right-hand side; a row that spans more image rows than columns)
+     * handled in the column-major pixel numbering, where their consecutive
+     * entries are neighbours.  One-pass sweep with L2-reduction scatter:
+     * they add their corrections into a second, column-major accumulator
+     * (fewer reduction requests), which the box step adds.  Two-pass sweep:
+     * their stored indices are column-major (a second copy of the packed
+     * indices, 4 bytes per stored entry) and their gathers read a
+     * column-major copy of x made before each row pass.  The same sums in
+     * another addition order.  0 automatic (on for the one-pass sweep when
+     * eligible; both forms timed when tune is set), 1 on (SUPPY_EINVAL when
+     * there is no image grid or several right-hand sides), -1 off.  Other
+     * values give SUPPY_EINVAL. */
     int32_t scatter_transpose;
 } suppy_opts;
 
@@ -289,8 +294,8 @@ typedef struct {
      * segments of the tile streams; zero for the other strategies */
     int32_t tiles, chunks, tile_warps1, tile_warps2, tile_coef_warps, tile_ring;
     int64_t tile_stream_bytes, tile_segments;
-    /* one pass with L2 reductions (opts.scatter_transpose): rows scattered
-     * column-major; 0 when the sweep does not use it */
+    /* rows handled column-major (opts.scatter_transpose); 0 when the sweep
+     * does not use that form */
     int64_t transposed_rows;
     int32_t a_dtype;              /* storage type of A's values (HALF_AUTO resolved) */
 } suppy_info;
