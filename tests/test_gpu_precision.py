@@ -119,3 +119,21 @@ def test_half_auto_takes_the_format_with_the_smaller_error(scale, want):
     xo, _ = O.sweep(S, O.CIMMINO, l, u, 1.0, lo, hi, x0.astype(np.float64))
     assert rel_l2(ctx.suppy_get_x(), xo) <= 1e-5
     ctx.close()
+
+
+def test_half_auto_batched_context():
+    """SUPPY_HALF_AUTO in a batched context (three right-hand sides sharing A):
+    each right-hand side's sweep matches the oracle on the FP16 values."""
+    prob = synth.ct_problem(nrhs=3)
+    ctx = pk.from_problem(prob, dtype=pk.SUPPY_HALF_AUTO)
+    assert ctx.suppy_info_get()["a_dtype"] == pk.SUPPY_F16
+    x0 = np.random.default_rng(5).uniform(0, 1, (prob.A.n, 3)).astype(np.float32)
+    ctx.suppy_set_x(x0)
+    ctx.suppy_sweep(pk.suppy_params_default(), 1)
+    xg = ctx.suppy_get_x()
+    S, l, u, lo, hi = O.from_problem(prob, values=rounded_values(prob.A.val, "f16"))
+    for b in range(3):
+        xo, _ = O.sweep(S, O.CIMMINO, O.rhs(l, b), O.rhs(u, b), 1.0, lo, hi,
+                        x0[:, b].astype(np.float64))
+        assert rel_l2(xg[:, b], xo) <= 1e-5
+    ctx.close()

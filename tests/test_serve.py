@@ -162,3 +162,24 @@ def test_server_rejects_bad_requests():
     with pytest.raises(pk.SuppyError):
         srv.suppy_server_query(12345)
     srv.close()
+
+
+def test_served_16_bit_storage_matches_the_oracle_on_rounded_values():
+    """A server storing A by SUPPY_HALF_AUTO (FP16 for these CT values)
+    serves each request as the oracle runs it on the FP16-rounded values."""
+    from tests.helpers import rounded_values
+    ct, _ = _problems()
+    P = pk.suppy_params_default(**PARAMS)
+    srv = pk.Server(slots=4, check_every=3)
+    m0 = srv.suppy_server_add_matrix(ct, P, dtype=pk.SUPPY_HALF_AUTO, obj=pk.SUPPY_OBJ_TV_ISO)
+    sched = [(2 * b, m0, ct.l[:, b], ct.u[:, b]) for b in range(3)]
+    res = _run_all(srv, sched, {m0: ct.A.n})
+    srv.close()
+    S, _, _, lo, hi = O.from_problem(ct, values=rounded_values(ct.A.val, "f16"))
+    for (t, mid, l, u), (info, x) in zip(sched, res):
+        assert info["state"] == 2
+        op = O.Params(gamma=0.5, alpha=0.99, n_red=1, max_sweeps=info["sweeps"])
+        r = O.run(S, O.CIMMINO, np.asarray(l, np.float64), np.asarray(u, np.float64), lo, hi,
+                  oracle_objective(ct, O.OBJ_TV_ISO), op)
+        assert rel_l2(x, r.x) <= 1e-3
+        assert rel(info["proximity"], r.prox_hist[-1]) <= 1e-3
