@@ -518,64 +518,44 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const FinalizeArg
 // The same box step with the one-pass scatter's column-major second
 // accumulator (one right-hand side on an H x W image): x_j <- clamp(x_j +
 // delta_j + deltaT_(c,r), lo, hi) for pixel j = (r, c), both accumulators
-// cleared.  32 x 32 pixel tiles: deltaT is read and cleared along its
-// columns and transposed through shared memory, so both sides stay coalesced.
-constexpr int kTrTile = 32;
+// cleared.  Tiles of 32 image rows x 8 columns, one pixel per thread: deltaT
+// is read along its columns (32 consecutive floats), x and delta along the
+// image rows (8), every load issued before any is used, and the transposed
+// values pass through shared memory.
+constexpr int kTrRows = 32, kTrCols = 8;
 __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
-    constexpr int kPer = kTrTile * kTrTile / 256;   // pixels a thread takes per tile
-    __shared__ float t[kTrTile][kTrTile + 1];
+    __shared__ float t[kTrCols][kTrRows + 1];
     const int H = a.imgH, W = a.imgW;
-    const int tw = (W + kTrTile - 1) / kTrTile;
-    const long long ntiles = (long long)tw * ((H + kTrTile - 1) / kTrTile);
-    const int tx = threadIdx.x % kTrTile, ty = threadIdx.x / kTrTile;
+    const int tw = (W + kTrCols - 1) / kTrCols;
+    const long long ntiles = (long long)tw * ((H + kTrRows - 1) / kTrRows);
+    // deltaT side: column c0 + ty, row r0 + tx; image side: row r0 + iy, column c0 + ix
+    const int tx = threadIdx.x % kTrRows, ty = threadIdx.x / kTrRows;
+    const int ix = threadIdx.x % kTrCols, iy = threadIdx.x / kTrCols;
     for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        const int r0 = (int)(ti / tw) * kTrTile, c0 = (int)(ti % tw) * kTrTile;
-        // every load of the tile first (one round trip), the clearing
-        // stores right behind them
-        float tv[kPer], dv[kPer], xv[kPer];
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int k = ty + q * (256 / kTrTile);
-            int c = c0 + k, r = r0 + tx;
-            tv[q] = 0.f;
-            if (c < W && r < H) tv[q] = a.deltaT[(long long)c * H + r];
-            r = r0 + k;
-            c = c0 + tx;
-            dv[q] = 0.f;
-            xv[q] = 0.f;
-            if (r < H && c < W) {
-                const long long j = (long long)r * W + c;
-                dv[q] = a.delta[j];
-                xv[q] = a.x[j];
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int k = ty + q * (256 / kTrTile);
-            int c = c0 + k, r = r0 + tx;
-            if (c < W && r < H) a.deltaT[(long long)c * H + r] = 0.f;
-            r = r0 + k;
-            c = c0 + tx;
-            if (r < H && c < W) a.delta[(long long)r * W + c] = 0.f;
-            t[k][tx] = tv[q];
-        }
+        const int r0 = (int)(ti / tw) * kTrRows, c0 = (int)(ti % tw) * kTrCols;
+        const int cT = c0 + ty, rT = r0 + tx;
+        const int r = r0 + iy, c = c0 + ix;
+        const bool inT = cT < W && rT < H, in = r < H && c < W;
+        const long long jT = (long long)cT * H + rT, j = (long long)r * W + c;
+        const float tv = inT ? a.deltaT[jT] : 0.f;
+        const float dv = in ? a.delta[j] : 0.f;
+        const float xv = in ? a.x[j] : 0.f;
+        if (inT) a.deltaT[jT] = 0.f;
+        if (in) a.delta[j] = 0.f;
+        t[ty][tx] = tv;
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < kPer; ++q) {
-            const int k = ty + q * (256 / kTrTile);
-            const int r = r0 + k, c = c0 + tx;
-            if (r < H && c < W) {
-                const long long j = (long long)r * W + c;
-                float d = dv[q] + t[tx][k];
-                if (a.zc) d *= a.zc[j];
-                const long long bj = (a.box_len == 1) ? 0 : j;
-                a.x[j] = clampf(xv[q] + d, a.lo[bj], a.hi[bj]);
-            }
+        if (in) {
+            float d = dv + t[ix][iy];
+            if (a.zc) d *= a.zc[j];
+            const long long bj = (a.box_len == 1) ? 0 : j;
+            a.x[j] = clampf(xv + d, a.lo[bj], a.hi[bj]);
         }
         __syncthreads();
     }
     if (blockIdx.x == 0) sweep_epilogue(a.epi);
 }
+
+constexpr int kTrTile = 32;
 
 // xT <- x column-major (H x W image, one right-hand side), 32 x 32 tiles
 // through shared memory: the copy that the two-pass row pass gathers from for
@@ -832,9 +812,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
     if (a.deltaT) {
         if (a.B != 1 || a.imgW < 1 || a.imgH < 1 || (long long)a.imgW * a.imgH != a.nB)
             return cudaErrorInvalidValue;
-        const long long tiles = (long long)((a.imgW + kTrTile - 1) / kTrTile) *
-                                ((a.imgH + kTrTile - 1) / kTrTile);
-        k_finalize_tr<<<(int)std::min<long long>(tiles, 2048), 256, 0, s>>>(a);
+        const long long tiles = (long long)((a.imgW + kTrCols - 1) / kTrCols) *
+                                ((a.imgH + kTrRows - 1) / kTrRows);
+        k_finalize_tr<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(a);
         return cudaGetLastError();
     }
     k_finalize<<<grid, kFinalizeThreads, 0, s>>>(a);
