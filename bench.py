@@ -283,15 +283,16 @@ def kind_name(strategy, k):
 
 def sweep_traffic_from(table, info):
     """DRAM bytes per sweep (all of the sweep's launches) of a capture table
-    for this run's strategy and launch shape, or None with the reason."""
+    for this run's strategy and launch shape, or None with the reason.  A
+    strategy's entry is one capture or a list of captures of several shapes."""
     ent = table.get(f"ct512_sweep_strategy{info['strategy']}")
     if not ent:
         return None, "no committed capture of this strategy"
-    shape = ent.get("shape", {})
-    now = {k: info.get(k) for k in shape}
-    if now != shape:
-        return None, "the committed capture is of another launch shape"
-    return float(ent["bytes_per_sweep"]), ent.get("note")
+    for e in (ent if isinstance(ent, list) else [ent]):
+        shape = e.get("shape", {})
+        if {k: info.get(k) for k in shape} == shape:
+            return float(e["bytes_per_sweep"]), e.get("note")
+    return None, "the committed capture is of another launch shape"
 
 
 def sweep_traffic(info):

@@ -39,3 +39,15 @@ def test_another_shape_or_strategy_reports_none():
         assert bench.sweep_traffic_from(TABLE, dict(INFO2, **{k: v}))[0] is None
     assert bench.sweep_traffic_from(TABLE, dict(INFO3, chunks=300))[0] is None
     assert bench.sweep_traffic_from(TABLE, dict(INFO2, strategy=1))[0] is None
+
+
+def test_a_list_of_captures_is_matched_by_shape():
+    table = {"ct512_sweep_strategy2": [dict(TABLE["ct512_sweep_strategy2"]),
+                                       {"bytes_per_sweep": 1947000000,
+                                        "shape": dict(TABLE["ct512_sweep_strategy2"]["shape"],
+                                                      transposed_rows=5)}]}
+    table["ct512_sweep_strategy2"][0]["shape"] = dict(TABLE["ct512_sweep_strategy2"]["shape"],
+                                                      transposed_rows=0)
+    assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=0))[0] == 1945000000.0
+    assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=5))[0] == 1947000000.0
+    assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=7))[0] is None
