@@ -555,28 +555,22 @@ __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
     if (blockIdx.x == 0) sweep_epilogue(a.epi);
 }
 
-constexpr int kTrTile = 32;
-
-// xT <- x column-major (H x W image, one right-hand side), 32 x 32 tiles
-// through shared memory: the copy that the two-pass row pass gathers from for
-// the rows running down the image.
+// xT <- x column-major (H x W image, one right-hand side): the copy that the
+// two-pass row pass gathers from for the rows running down the image.  Tiles
+// of 32 image rows x 8 columns as in k_finalize_tr, one pixel per thread.
 __global__ void __launch_bounds__(256) k_transpose_image(const float* x, float* xT, int H, int W) {
-    __shared__ float t[kTrTile][kTrTile + 1];
-    const int tw = (W + kTrTile - 1) / kTrTile;
-    const long long ntiles = (long long)tw * ((H + kTrTile - 1) / kTrTile);
-    const int tx = threadIdx.x % kTrTile, ty = threadIdx.x / kTrTile;
-    const int rows = blockDim.x / kTrTile;
+    __shared__ float t[kTrCols][kTrRows + 1];
+    const int tw = (W + kTrCols - 1) / kTrCols;
+    const long long ntiles = (long long)tw * ((H + kTrRows - 1) / kTrRows);
+    const int tx = threadIdx.x % kTrRows, ty = threadIdx.x / kTrRows;
+    const int ix = threadIdx.x % kTrCols, iy = threadIdx.x / kTrCols;
     for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        const int r0 = (int)(ti / tw) * kTrTile, c0 = (int)(ti % tw) * kTrTile;
-        for (int k = ty; k < kTrTile; k += rows) {
-            const int r = r0 + k, c = c0 + tx;
-            t[tx][k] = (r < H && c < W) ? x[(long long)r * W + c] : 0.f;
-        }
+        const int r0 = (int)(ti / tw) * kTrRows, c0 = (int)(ti % tw) * kTrCols;
+        const int r = r0 + iy, c = c0 + ix;
+        t[ix][iy] = (r < H && c < W) ? x[(long long)r * W + c] : 0.f;
         __syncthreads();
-        for (int k = ty; k < kTrTile; k += rows) {
-            const int c = c0 + k, r = r0 + tx;
-            if (c < W && r < H) xT[(long long)c * H + r] = t[k][tx];
-        }
+        const int cT = c0 + ty, rT = r0 + tx;
+        if (cT < W && rT < H) xT[(long long)cT * H + rT] = t[ty][tx];
         __syncthreads();
     }
 }
@@ -823,8 +817,8 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_transpose_image(const float* x, float* xT, int H, int W, cudaStream_t s) {
     if (H < 1 || W < 1) return cudaErrorInvalidValue;
-    const long long tiles = (long long)((W + kTrTile - 1) / kTrTile) * ((H + kTrTile - 1) / kTrTile);
-    k_transpose_image<<<(int)std::min<long long>(tiles, 2048), 256, 0, s>>>(x, xT, H, W);
+    const long long tiles = (long long)((W + kTrCols - 1) / kTrCols) * ((H + kTrRows - 1) / kTrRows);
+    k_transpose_image<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(x, xT, H, W);
     return cudaGetLastError();
 }
 
