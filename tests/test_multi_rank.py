@@ -48,3 +48,17 @@ def test_single_rank_is_unchanged():
     import bench
     ms, value = bench.aggregate_over_ranks(4.0, 500.0, 1)
     assert ms == 4.0 and value == pytest.approx(500.0 / 0.004)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under torchrun the reference arm (the oracle on the host cores) runs
+    and prints on rank 0 alone; every other rank exits 0 without work."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                        "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                       env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
