@@ -137,3 +137,10 @@ def test_half_auto_batched_context():
                         x0[:, b].astype(np.float64))
         assert rel_l2(xg[:, b], xo) <= 1e-5
     ctx.close()
+
+
+def test_half_auto_with_device_resident_values():
+    prob = synth.ct_problem()
+    ctx = pk.from_problem(prob, dtype=pk.SUPPY_HALF_AUTO, device=True)
+    assert ctx.suppy_info_get()["a_dtype"] == pk.SUPPY_F16
+    ctx.close()

@@ -144,3 +144,12 @@ def test_rejections():
     two = synth.ct_problem(160, 120, 227, nrhs=2)
     with pytest.raises(pk.SuppyError):
         pk.from_problem(two, scatter_transpose=1)
+
+
+def test_device_resident_inputs():
+    """A, l, u and the box given as device tensors: the row orientation is
+    taken from a host copy of the column indices, the sweep is the same."""
+    prob = synth.ct_problem(160, 120, 227)
+    info, xg, ph, xo, po = _one_sweep(prob, scatter_transpose=1, device=True)
+    assert info["transposed_rows"] > 0
+    assert rel_l2(xg, xo) <= 1e-5
