@@ -452,20 +452,25 @@ typedef struct {
  * becomes the target-space proximity 1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2
  * at the CQ step's input point (Sec. 2.2.1: stopping on the target space).
  *
- * Needs nrhs = 1.  Copies its inputs (device inputs when Aq->on_device);
+ * With several right-hand sides every one gets the same sets and its own CQ
+ * step (each its own doses, projections and target-space proximity).
+ * Copies its inputs (device inputs when Aq->on_device);
  * synchronizes; replaces an earlier set; ndvc = 0 removes the sets.
- * SUPPY_EINVAL for nrhs > 1, a malformed matrix (row_ptr, col range, NaN or
+ * SUPPY_EINVAL for a malformed matrix (row_ptr, col range, NaN or
  * infinite values), bad structure ranges, kinds, structures, volumes or d_ref,
  * relax outside (0, 2), or zero rows in every constrained structure. */
 suppy_status suppy_set_dvc(suppy_ctx* ctx, const suppy_csr* Aq, const int32_t* structure_ptr,
                            int32_t nstruct, const suppy_dvc* dvc, int32_t ndvc, double relax);
 
-/* Doses d = A_q x at the current x (m_q floats, FP32 accumulation) into host
- * or device memory.  A host copy synchronizes.  SUPPY_ESTATE without DVCs. */
+/* Doses d = A_q x at the current x (m_q x B floats, row-major like x: right-
+ * hand side b's dose of row i at dose[i * B + b]; FP32 accumulation) into
+ * host or device memory.  A host copy synchronizes.  SUPPY_ESTATE without
+ * DVCs. */
 suppy_status suppy_dvc_dose(suppy_ctx* ctx, float* dose, int32_t on_device);
 
 /* Target-space proximity 1/2 sum_j w_j ||P_Qj(A_j x) - A_j x||^2 at the current
- * x (FP64, host).  Synchronizes.  SUPPY_ESTATE without DVCs. */
+ * x (FP64, host; out receives B values, one per right-hand side).
+ * Synchronizes.  SUPPY_ESTATE without DVCs. */
 suppy_status suppy_dvc_proximity(suppy_ctx* ctx, double* out);
 
 /* Kernel timing for measurement: when enabled, every launch of the kernels

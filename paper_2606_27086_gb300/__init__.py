@@ -174,7 +174,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "suppy_set_dvc": (ctypes.c_int, [P, ctypes.POINTER(suppy_csr), P, I32,
                                          ctypes.POINTER(suppy_dvc), I32, D]),
         "suppy_dvc_dose": (ctypes.c_int, [P, P, I32]),
-        "suppy_dvc_proximity": (ctypes.c_int, [P, ctypes.POINTER(D)]),
+        "suppy_dvc_proximity": (ctypes.c_int, [P, P]),
         "suppy_set_wait_limit": (ctypes.c_int, [P, I64]),
     }
     for name, (res, args) in sig.items():
@@ -387,16 +387,19 @@ class Context:
         self.mq = int(m) if len(dvcs) else 0
 
     def suppy_dvc_dose(self, out=None):
+        """Doses A_q x: m_q values, or m_q x B for several right-hand sides."""
         if out is None:
-            out = np.empty(self.mq, dtype=np.float32)
+            shape = (self.mq,) if self.nrhs == 1 else (self.mq, self.nrhs)
+            out = np.empty(shape, dtype=np.float32)
         op, d, k = _ptr(out)
         _check(self._lib.suppy_dvc_dose(self.ctx, op, d), self.ctx)
         return out
 
-    def suppy_dvc_proximity(self) -> float:
-        v = ctypes.c_double(0.0)
-        _check(self._lib.suppy_dvc_proximity(self.ctx, ctypes.byref(v)), self.ctx)
-        return v.value
+    def suppy_dvc_proximity(self):
+        """Target-space proximity: a float, or B values for several right-hand sides."""
+        v = np.zeros(max(1, self.nrhs), dtype=np.float64)
+        _check(self._lib.suppy_dvc_proximity(self.ctx, ctypes.c_void_p(v.ctypes.data)), self.ctx)
+        return float(v[0]) if self.nrhs == 1 else v
 
     def suppy_objective(self):
         out = np.zeros(self.nrhs, dtype=np.float64)

@@ -583,8 +583,10 @@ suppy_status enqueue_ext_step(suppy_ctx* c, const suppy_params* p, int t, int np
     return SUPPY_OK;
 }
 
-// One application of T.
-DvcArgs dvc_args(suppy_ctx* c, bool check_stop) {
+// The CQ step's arguments for right-hand side b (x is n x B, one state, one
+// set of projection partials and one target-space proximity per right-hand
+// side).
+DvcArgs dvc_args(suppy_ctx* c, bool check_stop, int b = 0) {
     DvcArgs a;
     a.rp = c->d_qrp;
     a.col = c->d_qcol;
@@ -595,13 +597,14 @@ DvcArgs dvc_args(suppy_ctx* c, bool check_stop) {
     a.sptr = c->d_qsptr;
     a.sdvc = c->d_qsdvc;
     a.dvc = c->d_qdvc;
-    a.x = c->d_x;
-    a.xw = c->d_x;
+    a.x = c->d_x + b;
+    a.xw = c->d_x + b;
+    a.B = c->B;
     a.dose = c->d_dose;
     a.corr = c->d_qcorr;
-    a.pd = c->d_qpd;
-    a.target = c->d_target;
-    a.st = check_stop ? c->d_st : nullptr;
+    a.pd = c->d_qpd + (size_t)b * c->ndvc * kDvcCluster;
+    a.target = c->d_target + b;
+    a.st = check_stop ? c->d_st + b : nullptr;
     a.gamma = c->dvc_gamma;
     a.mq = c->mq;
     a.n = c->n;
@@ -615,14 +618,18 @@ DvcArgs dvc_args(suppy_ctx* c, bool check_stop) {
 // The CQ step of a split problem: doses, projections onto the DVC sets and
 // the target-space proximity, the correction x += gamma A_q^T corr.
 suppy_status enqueue_cq_step(suppy_ctx* c) {
-    const DvcArgs a = dvc_args(c, true);
     Timed tm{c, 3};
     CK(tm.begin());
-    CK(launch_dvc_dose(a, c->stream));
-    CK(launch_dvc_project(a, c->stream));
-    CK(launch_dvc_apply(a, c->stream));
+    // one right-hand side after the other: the dose and correction buffers
+    // are shared, the stream orders the launches
+    for (int b = 0; b < c->B_user; ++b) {
+        const DvcArgs a = dvc_args(c, true, b);
+        CK(launch_dvc_dose(a, c->stream));
+        CK(launch_dvc_project(a, c->stream));
+        CK(launch_dvc_apply(a, c->stream));
+        note_launch(c, 4);
+    }
     CK(tm.end());
-    note_launch(c, 4);
     return SUPPY_OK;
 }
 
@@ -2605,8 +2612,6 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
                           const suppy_dvc* dvc, int32_t ndvc, double relax) {
     if (ndvc < 0) return fail(c, SUPPY_EINVAL, "ndvc must be >= 0");
     if (ndvc > 0) {
-        if (c->B_user != 1 || c->B != 1)
-            return fail(c, SUPPY_EINVAL, "split feasibility needs a context with one right-hand side");
         if (!A || !sptr || !dvc) return fail(c, SUPPY_EINVAL, "Aq, structure_ptr and dvc must be given");
         if (A->n != c->n) return fail(c, SUPPY_EINVAL, "Aq must have the context's n columns");
         if (A->m < 1 || A->nnz < 0 || A->nnz >= (1LL << 31))
@@ -2709,8 +2714,8 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
         return s;
     }
     if ((s = dalloc(c, &c->d_dose, (size_t)mq)) != SUPPY_OK || (s = dalloc(c, &c->d_qcorr, (size_t)mq)) != SUPPY_OK ||
-        (s = dalloc(c, &c->d_qpd, (size_t)ndvc * kDvcCluster)) != SUPPY_OK ||
-        (s = dalloc(c, &c->d_target, 1)) != SUPPY_OK) {
+        (s = dalloc(c, &c->d_qpd, (size_t)ndvc * kDvcCluster * c->B)) != SUPPY_OK ||
+        (s = dalloc(c, &c->d_target, (size_t)c->B)) != SUPPY_OK) {
         free_dvc(c);
         return s;
     }
@@ -2727,7 +2732,7 @@ suppy_status set_dvc_impl(suppy_ctx* c, const suppy_csr* A, const int32_t* sptr,
     if (fe == cudaSuccess)
         fe = cudaMemcpyAsync(frob.data(), d_frob, sizeof(double) * nstruct, cudaMemcpyDeviceToHost,
                              c->stream);
-    if (fe == cudaSuccess) fe = cudaMemsetAsync(c->d_target, 0, sizeof(double), c->stream);
+    if (fe == cudaSuccess) fe = cudaMemsetAsync(c->d_target, 0, sizeof(double) * c->B, c->stream);
     if (fe == cudaSuccess) fe = cudaStreamSynchronize(c->stream);
     dfree(c, d_frob);
     if (fe != cudaSuccess) {
@@ -2767,10 +2772,16 @@ suppy_status suppy_dvc_dose(suppy_ctx* c, float* dose, int32_t on_device) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!c->dvc_on) return fail(c, SUPPY_ESTATE, "no dose-volume constraints are set");
     if (!dose) return fail(c, SUPPY_EINVAL, "dose is NULL");
-    CK(launch_dvc_dose(dvc_args(c, false), c->stream));
-    note_launch(c);
-    CK(cudaMemcpyAsync(dose, c->d_dose, sizeof(float) * c->mq,
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    // m_q x B, row-major like x: right-hand side b's doses at dose[i * B + b]
+    const int Bu = c->B_user;
+    for (int b = 0; b < Bu; ++b) {
+        CK(launch_dvc_dose(dvc_args(c, false, b), c->stream));
+        note_launch(c);
+        CK(cudaMemcpy2DAsync(dose + b, sizeof(float) * Bu, c->d_dose, sizeof(float), sizeof(float),
+                             (size_t)c->mq,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    }
     if (!on_device) CK(cudaStreamSynchronize(c->stream));
     return SUPPY_OK;
 }
@@ -2779,13 +2790,16 @@ suppy_status suppy_dvc_proximity(suppy_ctx* c, double* out) {
     if (!c) return fail(nullptr, SUPPY_EINVAL, "ctx is NULL");
     if (!c->dvc_on) return fail(c, SUPPY_ESTATE, "no dose-volume constraints are set");
     if (!out) return fail(c, SUPPY_EINVAL, "out is NULL");
-    const DvcArgs a = dvc_args(c, false);
-    CK(launch_dvc_dose(a, c->stream));
-    CK(launch_dvc_project(a, c->stream));
-    note_launch(c, 3);
-    CK(cudaMemcpyAsync(c->h_out, c->d_target, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    const int Bu = c->B_user;
+    for (int b = 0; b < Bu; ++b) {
+        const DvcArgs a = dvc_args(c, false, b);
+        CK(launch_dvc_dose(a, c->stream));
+        CK(launch_dvc_project(a, c->stream));
+        note_launch(c, 3);
+    }
+    CK(cudaMemcpyAsync(c->h_out, c->d_target, sizeof(double) * Bu, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    *out = c->h_out[0];
+    for (int b = 0; b < Bu; ++b) out[b] = c->h_out[b];
     return SUPPY_OK;
 }
 

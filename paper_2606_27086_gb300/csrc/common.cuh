@@ -451,8 +451,8 @@ struct DvcArgs {
     const int* sptr;        // structure row ranges (nstruct + 1)
     const int* sdvc;        // DVCs of structure s: dvc[sdvc[s] .. sdvc[s+1])
     const DvcDesc* dvc;
-    const float* x;         // iterate read by the dose pass
-    float* xw;              // iterate updated by the correction pass
+    const float* x;         // iterate read by the dose pass (element j at x[j * B])
+    float* xw;              // iterate updated by the correction pass (the same layout)
     float* dose;            // m_q
     float* corr;            // m_q: sum_j w_j (P_Qj(d) - d)
     double* pd;             // per DVC (caller order) x cluster rank: chunk sums of the
@@ -461,6 +461,8 @@ struct DvcArgs {
     const RhsState* st;     // skip when right-hand side 0 has stopped, or null
     float gamma;
     int mq, n, nstruct, ndvc;
+    int B;                  // stride of x: the context's right-hand sides (x is n x B);
+                            // x, xw, st, pd and target point at the one being stepped
     long long nnz;          // entries of A_q
     size_t smem;            // dynamic shared memory of the projection (keys staged), or 0
 };

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kDoseThreads) k_dvc_dose(DvcArgs a) {
                 v[u] = ok ? __ldg(a.val + e) : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s = fmaf(v[u], __ldg(a.x + c[u]), s);
+            for (int u = 0; u < 8; ++u) s = fmaf(v[u], __ldg(a.x + (size_t)c[u] * a.B), s);
         }
         s = warp_sum_f(s);
         if (lane == 0) a.dose[i] = s;
@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kApplyThreads) k_dvc_apply(DvcArgs a) {
             float t = 0.f;
 #pragma unroll
             for (int w = 0; w < W; ++w) t += part[g * W + w];
-            a.xw[j] = a.xw[j] + a.gamma * t;
+            float* xj = a.xw + (size_t)j * a.B;
+            *xj = *xj + a.gamma * t;
         }
         __syncthreads();
     }

@@ -246,14 +246,78 @@ def test_split_validation_and_removal():
     ctx.suppy_sweep(pk.suppy_params_default(), 1)
     assert np.array_equal(ctx.suppy_get_x(), x)
     ctx.close()
-    # several right-hand sides: refused
+    # several right-hand sides: accepted, the same checks apply
     l = np.full((A.m, 2), -np.inf, F32)
     ctx2 = pk.Context(A.row_ptr, A.col, A.val, A.m, A.n, l, -l, np.zeros(1, F32),
                       np.ones(1, F32), nrhs=2)
     with pytest.raises(pk.SuppyError) as e:
-        ctx2.suppy_set_dvc(A.row_ptr, A.col, A.val, A.m, sptr, [(0, 0, 0.5, 1.0)], 1.0)
+        ctx2.suppy_set_dvc(A.row_ptr, A.col, A.val, A.m, sptr, [(0, 0, 1.5, 1.0)], 1.0)
     assert e.value.status == pk.SUPPY_EINVAL
+    ctx2.suppy_set_dvc(A.row_ptr, A.col, A.val, A.m, sptr, [(0, 0, 0.5, 1.0)], 1.0)
+    assert ctx2.suppy_dvc_dose().shape == (A.m, 2) and ctx2.suppy_dvc_proximity().shape == (2,)
     ctx2.close()
+
+
+def test_batched_cq_step_equals_the_single_right_hand_side_steps():
+    """Three right-hand sides sharing A_q and the sets, each with its own
+    integer iterate: every column's doses, target-space proximity and CQ
+    step equal (bitwise) those of a one-right-hand-side context on that
+    column, and the step matches the oracle's."""
+    A, sptr, _ = _integer_case(3, [3000, 2500, 40])
+    rng = np.random.default_rng(33)
+    X = rng.integers(0, 4, size=(A.n, 3)).astype(F32)
+    d0 = A.to_scipy() @ X[:, 0].astype(np.float64)
+    q = lambda s, f: float(np.quantile(d0[sptr[s]:sptr[s + 1]], f))
+    dvcs = [(1, 0, 0.9, q(0, 0.5) + 0.5), (0, 0, 0.1, q(0, 0.6)), (0, 1, 0.05, q(1, 0.5)),
+            (1, 2, 0.8, q(2, 0.9))]
+    l = np.full((A.m, 3), -np.inf, F32)
+    ctx = pk.Context(A.row_ptr, A.col, A.val, A.m, A.n, l, -l, np.full(1, -np.inf, F32),
+                     np.full(1, np.inf, F32), nrhs=3)
+    ctx.suppy_set_dvc(A.row_ptr, A.col, A.val, A.m, sptr, dvcs, 1.3)
+    ctx.suppy_set_x(X)
+    D = ctx.suppy_dvc_dose()
+    Pq = ctx.suppy_dvc_proximity()
+    ctx.suppy_sweep(pk.suppy_params_default(use_graphs=0), 1)
+    XG = ctx.suppy_get_x()
+    ctx.close()
+    SS = _oracle_split(A, sptr, dvcs, 1.3)
+    for b in range(3):
+        d, d_ref, p_gpu, xg, _ = _step_compare(A, sptr, dvcs, X[:, b].copy(), 1.3)
+        assert np.array_equal(D[:, b], d)
+        assert Pq[b] == p_gpu
+        assert np.array_equal(XG[:, b], xg)
+        xo, _ = O.cq_step(SS, X[:, b].astype(np.float64))
+        assert rel_l2(xg, xo) <= 2e-6
+
+
+def test_batched_superiorized_split_run_matches_the_oracle():
+    """Two plans of the horseshoe split problem in one context (OAR2 caps 30
+    and 24 Gy), 12 iterations of [perturbation, CQ step, slab sweep, box]:
+    each right-hand side against its own oracle run."""
+    prob = synth.rt_split_problem(nx=24, ny=20, nz=12, ns=8, nzb=6)
+    sp = prob.meta["split"]
+    u2 = prob.u.copy()
+    u2[prob.blocks == 1] = 24.0
+    prob.l = np.stack([prob.l, prob.l], axis=1)
+    prob.u = np.stack([prob.u, u2], axis=1)
+    K = 12
+    ctx = _split_ctx(prob, pk.SUPPY_CIMMINO, pk.SUPPY_OBJ_LINEAR)
+    ctx.suppy_set_x(np.full((prob.A.n, 2), 1.0, F32))
+    st = ctx.suppy_run(pk.suppy_params_default(gamma=1.0, alpha=0.7, n_red=1, max_sweeps=K,
+                                               use_stopping=0))
+    XG = ctx.suppy_get_x()
+    SS = _oracle_split(sp["Aq"], sp["sptr"], sp["dvcs"], 1.0)
+    obj = oracle_objective(prob, O.OBJ_LINEAR)
+    P = O.Params(gamma=1.0, alpha=0.7, n_red=1, max_sweeps=K)
+    S, l, u, lo, hi = O.from_problem(prob, O.CIMMINO)
+    for b in range(2):
+        ph, _ = ctx.suppy_history(b)
+        r = O.run(S, O.CIMMINO, O.rhs(l, b), O.rhs(u, b), lo, hi, obj, P,
+                  x0=np.full(prob.A.n, 1.0), split=SS)
+        assert st[b]["sweeps"] == K
+        assert rel_l2(XG[:, b], r.x) < 1e-4
+        assert np.allclose(ph[:K], r.prox_hist, rtol=1e-4, atol=0)
+    ctx.close()
 
 
 def test_device_inputs_give_the_same_step():
