@@ -776,10 +776,12 @@ def ours(args):
     if args.pin:
         # a configuration the tuner chose in a plain run, rebuilt without
         # timing (under a profiler the tuner's timings are not the plain ones)
-        st_, tile, stages, lanes, mp, cmp_ = (int(v) for v in args.pin.split(","))
+        vals = [int(v) for v in args.pin.split(",")]
+        st_, tile, stages, lanes, mp, cmp_ = vals[:6]
+        tr = vals[6] if len(vals) > 6 else -1
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=st_,
                               stream_shape=(tile, stages, lanes), stream_map=mp,
-                              stream_col_map=cmp_)
+                              stream_col_map=cmp_, scatter_transpose=tr)
     else:
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1)
     t_create = time.perf_counter() - t0
@@ -993,9 +995,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--pin", default="",
                     help="build the headline context with this launch configuration instead of "
-                         "tuning it: strategy,tile,stages,lanes,map,col_map as a plain run's "
-                         "launch_shape reports it (e.g. 2,4096,6,16,1,2), for runs under a "
-                         "profiler, whose serialised launches distort the tuner's timings")
+                         "tuning it: strategy,tile,stages,lanes,map,col_map[,column-major rows "
+                         "1 or -1] as a plain run's launch_shape reports it (e.g. "
+                         "2,4096,6,16,1,2,1), for runs under a profiler, whose serialised "
+                         "launches distort the tuner's timings")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=512,
