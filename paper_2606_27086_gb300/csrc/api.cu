@@ -732,11 +732,6 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             sa.coef_mul = (c->mode == SUPPY_EMR) ? c->d_rhof : nullptr;
             sa.check_stop = 1;
             if (tr_gather) {
-                Timed tm{c, 0};
-                CK(tm.begin());
-                CK(launch_transpose_image(c->d_x, c->d_xT, c->gH, c->gW, c->stream));
-                CK(tm.end());
-                note_launch(c);
                 sa.idx = c->d_colT;
                 sa.rowT = c->d_rowT;
                 sa.xT = c->d_xT;
@@ -751,8 +746,14 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
             EpiArgs e2 = epi;
             e2.npp = c->seg_tgrid[t];
             {
+                // the row pass, after the column-major copy of x its steep
+                // rows read (one timed bracket for both)
                 Timed tm{c, 0};
                 CK(tm.begin());
+                if (tr_gather) {
+                    CK(launch_transpose_image(c->d_x, c->d_xT, c->gH, c->gW, c->stream));
+                    note_launch(c);
+                }
                 CK(launch_rows_tma(sa, c->dt, c->tG, c->strategy == 2 ? 0 : 1, c->tMap, c->seg_tgrid[t],
                                    c->stream));
                 CK(tm.end());
