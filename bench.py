@@ -397,7 +397,8 @@ def variants(pk, K, W):
                      "m": prob.A.m, "n": prob.A.n, "nnz": nnz, "nrhs": B, "kernels": per,
                      "create_s": t_create, "strategy": info["strategy"],
                      "scatter": info["scatter"], "nblocks": info["nblocks"], "tma": info["tma"],
-                     "transposed_rows": info["transposed_rows"], "a_dtype": info["a_dtype"],
+                     "transposed_rows": info["transposed_rows"],
+                     "scatter_patch": info["scatter_patch"], "a_dtype": info["a_dtype"],
                      "launches_per_step": nl / Kv}
         if info["strategy"] == 3:
             out[name]["tiles"] = {k: info[k] for k in ("tiles", "chunks", "tile_warps1",
@@ -873,7 +874,8 @@ def ours(args):
                                                   "tile_segments", "tile", "stages", "col_tile",
                                                   "col_stages", "map", "col_map",
                                                   "lanes_per_row", "col_lanes",
-                                                  "transposed_rows", "perturb_cluster")}}
+                                                  "transposed_rows", "scatter_patch",
+                                                  "perturb_cluster")}}
     if args.pin:
         res["launch_shape"]["pinned"] = args.pin
     ctx.close()
@@ -995,10 +997,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--pin", default="",
                     help="build the headline context with this launch configuration instead of "
-                         "tuning it: strategy,tile,stages,lanes,map,col_map[,column-major rows "
-                         "1 or -1] as a plain run's launch_shape reports it (e.g. "
-                         "2,4096,6,16,1,2,1), for runs under a profiler, whose serialised "
-                         "launches distort the tuner's timings")
+                         "tuning it: strategy,tile,stages,lanes,map,col_map[,pixel numbering: "
+                         "1 column-major rows, 2 patches (one pass), -1 off] as a plain run's "
+                         "launch_shape reports it (e.g. 1,4096,6,32,2,2,2), for runs under a "
+                         "profiler, whose serialised launches distort the tuner's timings")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serve-requests", type=int, default=512,

@@ -218,8 +218,19 @@ typedef struct {
      * their stored indices are column-major (a second copy of the packed
      * indices, 4 bytes per stored entry) and their gathers read a
      * column-major copy of x made before each row pass.  The same sums in
-     * another addition order.  0 automatic (on for the one-pass sweep when
-     * eligible; both forms timed when tune is set), 1 on (SUPPY_EINVAL when
+     * another addition order.  2: the patch numbering for the one-pass
+     * sweep.  The image, zero-padded to multiples of 8, is laid out in
+     * patches: the rows closer to the horizontal use wide patches (128-byte
+     * lines of 8 x 4 pixels made of 32-byte sectors of 4 x 2), the others
+     * tall ones (lines of 4 x 8, sectors of 2 x 4).  Every row's indices are
+     * stored as patch positions (a second copy of the packed indices, 4 bytes
+     * per stored entry), its gathers read x from a copy in its layout (both
+     * copies made at each sweep start and written by each block's box step),
+     * and its corrections go into an accumulator in the same layout, so that
+     * a warp's gathers and reductions along a slanted ray touch fewer
+     * sectors; the two-pass sweep takes 2 as 1.  0 automatic (the patch
+     * numbering for the one-pass sweep when eligible, none for the two-pass
+     * sweep; every form timed when tune is set), 1 on (SUPPY_EINVAL when
      * there is no image grid or several right-hand sides), -1 off.  Other
      * values give SUPPY_EINVAL. */
     int32_t scatter_transpose;
@@ -298,6 +309,7 @@ typedef struct {
      * does not use that form */
     int64_t transposed_rows;
     int32_t a_dtype;              /* storage type of A's values (HALF_AUTO resolved) */
+    int32_t scatter_patch;        /* 1: the one-pass sweep uses the patch numbering */
 } suppy_info;
 
 /* Fill *p with the defaults listed above. */

@@ -117,7 +117,7 @@ class suppy_info(ctypes.Structure):
                 ("tile_warps2", ctypes.c_int32), ("tile_coef_warps", ctypes.c_int32),
                 ("tile_ring", ctypes.c_int32), ("tile_stream_bytes", ctypes.c_int64),
                 ("tile_segments", ctypes.c_int64), ("transposed_rows", ctypes.c_int64),
-                ("a_dtype", ctypes.c_int32)]
+                ("a_dtype", ctypes.c_int32), ("scatter_patch", ctypes.c_int32)]
 
 
 _lib = None

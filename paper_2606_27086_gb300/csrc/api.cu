@@ -80,6 +80,12 @@ struct suppy_ctx {
     unsigned long long recipW = 0;
     long long trows = 0;
     bool tr_on = false;             // the sweep uses them (chosen at create)
+    bool tr_patch = false;          // the one-pass sweep numbers pixels by patches
+    int* d_colP = nullptr;          // the packed indices, every row's in its patch layout
+    float* d_xA = nullptr;          // x in the wide / tall patch layouts (the gathers)
+    float* d_xB = nullptr;
+    int gWp = 0;                    // image width rounded up to a multiple of 8
+    size_t acc_len = 0;             // floats of d_delta and d_deltaT (padded grid when a grid is set)
     float* d_g = nullptr;
     float* d_lo = nullptr;
     float* d_hi = nullptr;
@@ -705,6 +711,9 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     // of x made before each block's row pass: x changes after every block)
     const bool tr_scatter = c->use_tma && c->strategy == 1 && c->scat == 1 && c->d_rowT && c->tr_on;
     const bool tr_gather = c->use_tma && c->strategy == 2 && c->d_colT && c->tr_on;
+    // one pass in the patch numbering: patch indices, gathers from the patch
+    // copies of x, both accumulators in patch layouts
+    const bool patch = tr_scatter && c->tr_patch && c->d_colP;
     for (int t = 0; t < c->nseg; ++t) {
         SweepArgs a = row_args(c, t, lam_row);
         if (c->mode == SUPPY_EMR) a.coef_mul = c->d_rhof;
@@ -743,6 +752,13 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 sa.imgW = c->gW;
                 sa.imgH = c->gH;
             }
+            if (patch) {
+                sa.idx = c->d_colP;
+                sa.xW = c->d_xA;
+                sa.xT = c->d_xB;
+                sa.patch = 1;
+                sa.imgWp = c->gWp;
+            }
             EpiArgs e2 = epi;
             e2.npp = c->seg_tgrid[t];
             {
@@ -752,6 +768,12 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 CK(tm.begin());
                 if (tr_gather) {
                     CK(launch_transpose_image(c->d_x, c->d_xT, c->gH, c->gW, c->stream));
+                    note_launch(c);
+                }
+                // the patch copies of x: at the sweep start (later blocks
+                // find them written by the previous block's box step)
+                if (patch && t == 0) {
+                    CK(launch_patch_image(c->d_x, c->d_xA, c->d_xB, c->gH, c->gW, c->gWp, c->stream));
                     note_launch(c);
                 }
                 CK(launch_rows_tma(sa, c->dt, c->tG, c->strategy == 2 ? 0 : 1, c->tMap, c->seg_tgrid[t],
@@ -802,6 +824,14 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                     f.deltaT = c->d_deltaT;
                     f.imgW = c->gW;
                     f.imgH = c->gH;
+                }
+                if (patch) {
+                    f.patch = 1;
+                    f.imgWp = c->gWp;
+                    if (t + 1 < c->nseg) {
+                        f.xA = c->d_xA;
+                        f.xB = c->d_xB;
+                    }
                 }
                 f.zc = c->d_zc;
                 f.lo = c->d_lo;
@@ -1349,6 +1379,7 @@ void free_csc(suppy_ctx* c) {
 suppy_status build_row_orientation(suppy_ctx* c, const std::vector<int>& rp, const int* hcol,
                                    const std::vector<int>& perm) {
     const int m = c->m, W = c->gW;
+    c->recipW = ~0ULL / (unsigned long long)W + 1ULL;
     std::vector<unsigned char> flag(m, 0);
     long long nt = 0;
     for (int i = 0; i < m; ++i) {
@@ -1369,9 +1400,19 @@ suppy_status build_row_orientation(suppy_ctx* c, const std::vector<int>& rp, con
     if (nt == 0) return SUPPY_OK;
     suppy_status s;
     if ((s = upload(c, flag, &c->d_rowT)) != SUPPY_OK) return s;
-    if ((s = dalloc(c, &c->d_deltaT, (size_t)c->n)) != SUPPY_OK) return s;
-    CK(cudaMemsetAsync(c->d_deltaT, 0, sizeof(float) * c->n, c->stream));
-    c->recipW = ~0ULL / (unsigned long long)W + 1ULL;
+    // both accumulators cover the grid padded to multiples of 8 (the patch
+    // numbering's lines); the padding is never added into
+    c->gWp = (W + 7) & ~7;
+    const size_t acc = std::max((size_t)c->n, (size_t)((c->gH + 7) & ~7) * (size_t)c->gWp);
+    if (acc > c->acc_len) {
+        dfree(c, c->d_delta);
+        c->d_delta = nullptr;
+        if ((s = dalloc(c, &c->d_delta, acc)) != SUPPY_OK) return s;
+        CK(cudaMemsetAsync(c->d_delta, 0, sizeof(float) * acc, c->stream));
+    }
+    c->acc_len = acc;
+    if ((s = dalloc(c, &c->d_deltaT, acc)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_deltaT, 0, sizeof(float) * acc, c->stream));
     c->trows = nt;
     CK(cudaStreamSynchronize(c->stream));   // the flags' host copy goes out of scope
     return SUPPY_OK;
@@ -1392,6 +1433,34 @@ suppy_status build_col_transposed(suppy_ctx* c) {
                               c->stream));
     note_launch(c);
     return SUPPY_OK;
+}
+
+// The one-pass sweep in the patch numbering: a copy of the packed column
+// indices with every row's entries rewritten to its patch position (tall
+// patches for the rows running down the image), and the two patch-layout
+// copies of x its gathers read.
+suppy_status build_col_patch(suppy_ctx* c) {
+    if (c->d_colP || !c->d_rowT) return SUPPY_OK;
+    suppy_status s;
+    const size_t rlen = (size_t)c->nnz_pad + kMaxTile + 16;
+    if ((s = dalloc(c, &c->d_colP, rlen)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_xA, c->acc_len)) != SUPPY_OK) return s;
+    if ((s = dalloc(c, &c->d_xB, c->acc_len)) != SUPPY_OK) return s;
+    CK(cudaMemsetAsync(c->d_xA, 0, sizeof(float) * c->acc_len, c->stream));
+    CK(cudaMemsetAsync(c->d_xB, 0, sizeof(float) * c->acc_len, c->stream));
+    CK(cudaMemcpyAsync(c->d_colP, c->d_col, sizeof(int) * rlen, cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_patch_cols(c->d_rinfo, c->d_rowT, c->m, c->recipW, c->gW, c->gWp, c->d_colP, c->stream));
+    note_launch(c);
+    return SUPPY_OK;
+}
+
+void free_col_patch(suppy_ctx* c) {
+    dfree(c, c->d_colP);
+    dfree(c, c->d_xA);
+    dfree(c, c->d_xB);
+    c->d_colP = nullptr;
+    c->d_xA = nullptr;
+    c->d_xB = nullptr;
 }
 
 void free_col_transposed(suppy_ctx* c) {
@@ -1594,9 +1663,9 @@ suppy_status time_config(suppy_ctx* c, float* ms_out, int nsweeps) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_st, st.data(), sizeof(RhsState) * c->B, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && c->d_delta)
-        e = cudaMemsetAsync(c->d_delta, 0, sizeof(float) * nB, c->stream);
+        e = cudaMemsetAsync(c->d_delta, 0, sizeof(float) * std::max(nB, c->acc_len), c->stream);
     if (e == cudaSuccess && c->d_deltaT)
-        e = cudaMemsetAsync(c->d_deltaT, 0, sizeof(float) * c->n, c->stream);
+        e = cudaMemsetAsync(c->d_deltaT, 0, sizeof(float) * c->acc_len, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->timing = was_timing;
     c->k_upper = k_up;
@@ -1748,8 +1817,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
             return fail(c, SUPPY_EINVAL, "stream_map must be 0, 1 or 2");
         if (o->stream_col_map < 0 || o->stream_col_map > 2)
             return fail(c, SUPPY_EINVAL, "stream_col_map must be 0, 1 or 2");
-        if (o->scatter_transpose < -1 || o->scatter_transpose > 1)
-            return fail(c, SUPPY_EINVAL, "scatter_transpose must be -1, 0 or 1");
+        if (o->scatter_transpose < -1 || o->scatter_transpose > 2)
+            return fail(c, SUPPY_EINVAL, "scatter_transpose must be -1, 0, 1 or 2");
         if (o->tile_warps1 < 0 || o->tile_warps1 > 25)
             return fail(c, SUPPY_EINVAL, "tile_warps1 must lie in 0..25");
         const int rb = o->tile_ring_bytes;
@@ -1983,6 +2052,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if ((s = dalloc(c, &c->d_x, nB)) != SUPPY_OK) return s;
     if ((s = dalloc(c, &c->d_delta, nB)) != SUPPY_OK) return s;
     CK(cudaMemsetAsync(c->d_delta, 0, nB * sizeof(float), c->stream));
+    c->acc_len = nB;
     CK(launch_box_init(c->d_x, c->d_lo, c->d_hi, (long long)nB, c->B, c->box_len, nullptr, 0,
                        c->stream));
     note_launch(c);
@@ -2093,8 +2163,10 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     // the one-pass scatter's column-major accumulator: one right-hand side
     // on an image grid, a strategy that may take the one-pass sweep
     const bool tr_grid = c->B == 1 && c->gH >= 2 && c->gW >= 2;
-    if (o->scatter_transpose == 1 && !tr_grid)
+    if (o->scatter_transpose >= 1 && !tr_grid)
         return fail(c, SUPPY_EINVAL, "scatter_transpose needs an image grid and one right-hand side");
+    if (o->scatter_transpose >= 1 && (long long)((c->gH + 7) & ~7) * ((c->gW + 7) & ~7) >= (1LL << 31))
+        return fail(c, SUPPY_EINVAL, "scatter_transpose needs an image of fewer than 2^31 padded pixels");
     const bool tr_cand = tr_grid && o->scatter_transpose != -1 && !ext_mode && want != 3 &&
                          A->nnz > 0;
     std::vector<int> hcol_buf;
@@ -2126,29 +2198,33 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (tr_cand && (s = build_row_orientation(c, rp, hcol, perm)) != SUPPY_OK) return s;
     hcol_buf.clear();
     hcol_buf.shrink_to_fit();
-    // tr: the one pass with L2 reductions scatters the rows running down the
-    // image column-major (opts.scatter_transpose); untuned, it does so when
-    // the grid allows it, and the tuner times both forms
+    // tr: the one pass with L2 reductions takes the rows running down the
+    // image column-major (1) or every row in the patch numbering (2)
+    // (opts.scatter_transpose); untuned, it takes the patch numbering when
+    // the grid allows it (on CT 512x512 its sweep measured 0.30 ms against
+    // 0.42 ms column-major), and the tuner times every form
     struct Cand {
         int strategy, scat;
-        bool tr;
+        int tr;   // 0 none, 1 column-major rows, 2 patch numbering (one pass)
     };
     const bool have_tr = c->d_rowT != nullptr;
-    const bool tr_default = have_tr;
+    const int tr_one = !have_tr ? 0 : (o->scatter_transpose == 1 ? 1 : 2);
     std::vector<Cand> cands;
     if (want == 3) {
-        cands.push_back({3, 0, false});
+        cands.push_back({3, 0, 0});
     } else {
-        if (want != 2) cands.push_back({1, smem_ok ? 2 : 1, !smem_ok && tr_default});
-        if (want != 2 && !smem_ok && have_tr && o->tune && o->scatter_transpose == 0)
-            cands.push_back({1, 1, !tr_default});
-        if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1, tr_default});
-        if (need_csc) cands.push_back({2, 0, o->scatter_transpose == 1 && have_tr});
-        if (need_csc && have_tr && o->tune && o->scatter_transpose == 0) cands.push_back({2, 0, true});
-        if (tile_ok) cands.push_back({3, 0, false});
+        if (want != 2) cands.push_back({1, smem_ok ? 2 : 1, smem_ok ? 0 : tr_one});
+        if (want != 2 && !smem_ok && have_tr && o->tune && o->scatter_transpose == 0) {
+            cands.push_back({1, 1, 0});
+            cands.push_back({1, 1, 1});
+        }
+        if (want != 2 && smem_ok && o->tune) cands.push_back({1, 1, tr_one});
+        if (need_csc) cands.push_back({2, 0, (o->scatter_transpose >= 1 && have_tr) ? 1 : 0});
+        if (need_csc && have_tr && o->tune && o->scatter_transpose == 0) cands.push_back({2, 0, 1});
+        if (tile_ok) cands.push_back({3, 0, 0});
     }
     Cand best = cands[0];
-    if (want == 0 && !o->tune) best = smem_ok ? Cand{1, 2, false} : Cand{2, 0, false};
+    if (want == 0 && !o->tune) best = smem_ok ? Cand{1, 2, 0} : Cand{2, 0, 0};
     const bool fixed_shape = o->stream_tile || o->stream_stages || o->stream_lanes;
     // Launch shape of a candidate: the register-fed sweep's row shape, then
     // (when the streamed passes serve it) their ring shapes and lane maps,
@@ -2160,7 +2236,12 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     auto set_up = [&](const Cand& cd, bool tune_streams) -> suppy_status {
         c->strategy = cd.strategy;
         c->scat = cd.scat;
-        c->tr_on = cd.tr;
+        c->tr_on = cd.tr != 0;
+        c->tr_patch = cd.tr == 2 && cd.strategy == 1;
+        if (c->tr_patch) {
+            suppy_status st2 = build_col_patch(c);
+            if (st2 != SUPPY_OK) return st2;
+        }
         if (cd.strategy == 2 && cd.tr) {
             suppy_status st2 = build_col_transposed(c);
             if (st2 != SUPPY_OK) return st2;
@@ -2211,7 +2292,8 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     if (have_sh) {
         c->strategy = best.strategy;
         c->scat = best.scat;
-        c->tr_on = best.tr;
+        c->tr_on = best.tr != 0;
+        c->tr_patch = best.tr == 2 && best.strategy == 1;
         choose_row_shape(c, mean_len, max_len);
         if ((s = build_row_partition(c)) != SUPPY_OK) return s;
         c->tG = best_sh.tG;
@@ -2229,6 +2311,7 @@ suppy_status create_impl(const suppy_csr* A, const float* l, const float* u, con
     }
     if (c->strategy != 2 && c->d_cinfo) free_csc(c);
     if (!(c->strategy == 2 && c->tr_on) && c->d_colT) free_col_transposed(c);
+    if (!(c->strategy == 1 && c->tr_patch) && c->d_colP) free_col_patch(c);
     if (c->strategy != 3 && c->d_tstream) free_tile(c);
     if ((s = reset_state(c)) != SUPPY_OK) return s;
     dfree(c, d_flags);
@@ -3068,6 +3151,7 @@ suppy_status suppy_info_get(const suppy_ctx* cc, suppy_info* out) {
     out->a_dtype = (int32_t)c->dt;
     out->transposed_rows = (((c->strategy == 1 && c->scat == 1 && c->d_rowT) ||
                              (c->strategy == 2 && c->d_colT)) && c->use_tma && c->tr_on) ? c->trows : 0;
+    out->scatter_patch = (out->transposed_rows > 0 && c->strategy == 1 && c->tr_patch) ? 1 : 0;
     out->map = c->use_tma ? c->tMap + 1 : 0;
     out->col_map = (c->use_tma && c->strategy == 2) ? c->tMapc + 1 : 0;
     if (c->use_tma) {

@@ -104,6 +104,12 @@ struct FinalizeArgs {
     // column-major second accumulator of the one-pass scatter (B = 1) or null
     float* deltaT;
     int imgW, imgH;
+    // both accumulators in the patch numbering (patch_index) instead; when
+    // xA / xB are set the new x is also written in the wide / tall patch
+    // layout (the gathers of the next block's row pass)
+    int patch, imgWp;
+    float* xA;
+    float* xB;
 };
 
 // Column pass of the two-pass sweep: x_j <- box(x_j + sum_i a_ij coef_i)
@@ -210,6 +216,14 @@ struct StreamArgs {
     const float* xT;
     unsigned long long recipW;
     int imgW, imgH;
+    // patch numbering of the one-pass sweep (instead of row- and
+    // column-major): idx holds every row's indices as patch_index(.., wide)
+    // for rows without rowT and patch_index(.., tall) for rows with it; those
+    // rows gather from xW (wide) and xT (tall), copies of x in the two patch
+    // layouts, and add into delta and deltaT with the same indices.  imgWp =
+    // W rounded up to a multiple of 8 (each layout holds ceil8(H) x imgWp).
+    const float* xW;
+    int patch, imgWp;
 };
 
 // Tiled one-pass sweep (tile.cu): one cooperative launch of P CTAs, CTA b
@@ -359,6 +373,9 @@ cudaError_t launch_colpass(const ColArgs& a, suppy_dtype dt, int G, int grid, cu
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s);
 int colpass_blocks_per_sm(suppy_dtype dt, int G, int B);
 cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_patch_image(const float* x, float* xA, float* xB, int H, int W, int Wp, cudaStream_t s);
+cudaError_t launch_patch_cols(const int2* rinfo, const unsigned char* rowT, int m, unsigned long long recipW,
+                              int W, int Wp, int* col, cudaStream_t s);
 cudaError_t launch_transpose_image(const float* x, float* xT, int H, int W, cudaStream_t s);
 cudaError_t launch_transposed_cols(const int2* rinfo, const unsigned char* rowT, int m,
                                    unsigned long long recipW, int W, int H, int* col, cudaStream_t s);
@@ -517,6 +534,25 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ int transposed_index(int j, unsigned long long recipW, int W, int H) {
     const int q = (int)__umul64hi((unsigned long long)(unsigned)j, recipW);
     return (j - q * W) * H + q;
+}
+
+// Patch numbering of pixel j = (y, x) of an H x W image for the one-pass
+// scatter, over a zero-padded ceil8(H) x Wp grid (Wp = ceil8(W)).  Wide
+// patches: 128-byte lines of 8 x 4 pixels (x by y), each made of four 32-byte
+// sectors of 4 x 2 pixels; tall patches: lines of 4 x 8 pixels made of
+// sectors of 2 x 4.  Lines and sectors are numbered row by row, pixels inside
+// a sector row-major.  A ray's run of consecutive entries crosses fewer lines
+// and sectors here than in a row- or column-major image whenever it is not
+// axis-aligned: rays closer to the horizontal take the wide patches, the
+// others the tall ones.  y = j / W as in transposed_index.
+__device__ __forceinline__ int patch_index(int j, unsigned long long recipW, int W, int Wp, bool tall) {
+    const int y = (int)__umul64hi((unsigned long long)(unsigned)j, recipW);
+    const int x = j - y * W;
+    if (!tall)
+        return (((y >> 2) * (Wp >> 3) + (x >> 3)) << 5) | (((y >> 1) & 1) << 4) | (((x >> 2) & 1) << 3) |
+               ((y & 1) << 2) | (x & 3);
+    return (((y >> 3) * (Wp >> 2) + (x >> 2)) << 5) | (((y >> 2) & 1) << 4) | (((x >> 1) & 1) << 3) |
+           ((y & 3) << 1) | (x & 1);
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) {

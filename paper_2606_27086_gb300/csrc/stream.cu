@@ -268,15 +268,32 @@ __device__ __forceinline__ float ring_dot_il(const Ring<VT>& r, int g0, int len,
                 av[t] = to_f(v[t * G]);
             }
         } else {
+            // the item's last batch (or one that wraps around the ring's
+            // end): slots four at a time, only while they hold elements
             int p = p0 + e + gl;
             if (p >= r.size) p -= r.size;
+            for (int t0 = 0; t0 < U && e + t0 * G < len; t0 += 4) {   // uniform over the group
+                int cc[4];
+                float aa[4], xx[4];
 #pragma unroll
-            for (int t = 0; t < U; ++t) {
-                const bool in = e + gl + t * G < len;
-                c[t] = in ? r.idx[p] : 0;
-                av[t] = in ? to_f(r.val[p]) : 0.f;
-                r.step(p, G);
+                for (int t = 0; t < 4; ++t) {
+                    const bool in = e + gl + (t0 + t) * G < len;
+                    cc[t] = in ? r.idx[p] : 0;
+                    aa[t] = in ? to_f(r.val[p]) : 0.f;
+                    r.step(p, G);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) xx[t] = __ldg(vec + cc[t]);
+                acc0 = fmaf(aa[0], xx[0], acc0);
+                acc1 = fmaf(aa[1], xx[1], acc1);
+                acc0 = fmaf(aa[2], xx[2], acc0);
+                acc1 = fmaf(aa[3], xx[3], acc1);
             }
+            if constexpr (EARLY) {
+                __syncwarp(gmask_of<G>(threadIdx.x & 31));
+                if (gl == 0) rel(g0 + e, g0 + (e + U * G >= len ? lenp : e + U * G));
+            }
+            continue;
         }
         if constexpr (EARLY) __syncwarp(gmask_of<G>(threadIdx.x & 31));
 #pragma unroll
@@ -532,8 +549,9 @@ struct RowWork {
                                  const RingRelease& rel) {
         const unsigned gm = gmask_of<G>(threadIdx.x & 31);
         // a row running down the image reads the column-major copy of x (its
-        // stored indices are column-major then) in the two-pass row pass
-        const float* xs = (SCAT == 0 && a.xT && tr) ? a.xT : a.x;
+        // stored indices are column-major then) in the two-pass row pass; in
+        // the patch numbering every row reads the copy in its own layout
+        const float* xs = (a.xT && tr) ? a.xT : (a.xW ? a.xW : a.x);
         float dot = item_dot<VT, G, MAP, 12, kEarly>(r, g0, len, gl, xs, rel);
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) dot += __shfl_xor_sync(gm, dot, o);
@@ -543,14 +561,41 @@ struct RowWork {
             if (a.coef && gl == 0) a.coef[i] = coef;
         } else if (coef != 0.f) {
             // lane-strided over the elements: consecutive lanes, consecutive
-            // columns (column-major ones for a row running down the image)
-            int p = r.pos(g0 + gl);
+            // columns (column-major ones for a row running down the image, or
+            // neighbouring pixels of one patch in the patch numbering)
             float* dst = tr ? a.deltaT : a.delta;
-            for (int t = gl; t < len; t += G) {
-                const int j = r.idx[p];
-                const int jt = (SCAT == 1 && a.rowT) ? transposed_index(j, a.recipW, a.imgW, a.imgH) : j;
-                atomicAdd(dst + (tr ? jt : j), coef * to_f(r.val[p]));
-                r.step(p, G);
+            // the accumulator position of column j: the stored index itself
+            // (row-major, or a patch position in the patch numbering), or
+            // the column-major position for a row running down the image
+            const bool cm = SCAT == 1 && tr && !a.patch;
+            auto at = [&](int j) {
+                return dst + (cm ? transposed_index(j, a.recipW, a.imgW, a.imgH) : j);
+            };
+            const int p0 = r.pos(g0);
+            if (p0 + len <= r.size) {
+                // the item does not wrap around the ring's end: four
+                // elements per lane at a time, plain offsets
+                const VT* v = r.val + p0;
+                const int* ix = r.idx + p0;
+                int t = gl;
+                for (; t + 3 * G < len; t += 4 * G) {
+                    int c[4];
+                    float w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        c[u] = ix[t + u * G];
+                        w[u] = to_f(v[t + u * G]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) atomicAdd(at(c[u]), coef * w[u]);
+                }
+                for (; t < len; t += G) atomicAdd(at(ix[t]), coef * to_f(v[t]));
+            } else {
+                int p = r.pos(g0 + gl);
+                for (int t = gl; t < len; t += G) {
+                    atomicAdd(at(r.idx[p]), coef * to_f(r.val[p]));
+                    r.step(p, G);
+                }
             }
         }
         if (gl == 0) kahan_add(d * d * w * (a.prox_mul ? m : 1.f));

@@ -555,6 +555,111 @@ __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
     if (blockIdx.x == 0) sweep_epilogue(a.epi);
 }
 
+// Patch tiles: 8 image rows x 32 columns, one pixel per thread.  The tile's
+// wide patches are two runs of four 128-byte lines (line rows y0/4 and
+// y0/4 + 1, lines x0/8 .. x0/8 + 3 of each), its tall patches one run of
+// eight lines (line row y0/8, lines x0/4 .. x0/4 + 7); thread t reads or
+// writes position t of each run (coalesced), and the pixel (iy, ix) of
+// thread t sits at qa(t) / qb(t) of the runs.  Lines past the padded width
+// are not touched.
+constexpr int kPtRows = 8, kPtCols = 32;
+struct PatchTile {
+    int qa, qb;          // this thread's pixel in the wide / tall runs
+    bool ina, inb;       // run position t lies inside the padded grid
+    long long pa, pb;    // run position t in the wide / tall layouts
+    __device__ PatchTile(int t, int y0, int x0, int Wp) {
+        const int iy = t >> 5, ix = t & 31;
+        qa = ((iy >> 2) << 7) | ((ix >> 3) << 5) | (((iy >> 1) & 1) << 4) | (((ix >> 2) & 1) << 3) |
+             ((iy & 1) << 2) | (ix & 3);
+        qb = ((ix >> 2) << 5) | (((iy >> 2) & 1) << 4) | (((ix >> 1) & 1) << 3) | ((iy & 3) << 1) | (ix & 1);
+        const int lw8 = Wp >> 3, lw4 = Wp >> 2;   // lines per line row: wide, tall
+        ina = (x0 >> 3) + ((t >> 5) & 3) < lw8;
+        pa = ((long long)((y0 >> 2) + (t >> 7)) * lw8 + (x0 >> 3)) * 32 + (t & 127);
+        inb = (x0 >> 2) + (t >> 5) < lw4;
+        pb = ((long long)(y0 >> 3) * lw4 + (x0 >> 2)) * 32 + t;
+    }
+};
+
+// The same box step with both accumulators in the patch numbering
+// (patch_index), both read and cleared coalesced per patch tile; with xA / xB
+// set, the new x is also written in both patch layouts.
+__global__ void __launch_bounds__(256) k_finalize_patch(const FinalizeArgs a) {
+    __shared__ float sa[kPtRows * kPtCols], sb[kPtRows * kPtCols];
+    const int H = a.imgH, W = a.imgW;
+    const int tw = (W + kPtCols - 1) / kPtCols;
+    const long long ntiles = (long long)tw * ((H + kPtRows - 1) / kPtRows);
+    const int t = threadIdx.x;
+    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int y0 = (int)(ti / tw) * kPtRows, x0 = (int)(ti % tw) * kPtCols;
+        const PatchTile pt(t, y0, x0, a.imgWp);
+        const int y = y0 + (t >> 5), x = x0 + (t & 31);
+        const bool in = y < H && x < W;
+        const long long j = (long long)y * W + x;
+        const float va = pt.ina ? a.delta[pt.pa] : 0.f;
+        const float vb = pt.inb ? a.deltaT[pt.pb] : 0.f;
+        const float xv = in ? a.x[j] : 0.f;
+        if (pt.ina) a.delta[pt.pa] = 0.f;
+        if (pt.inb) a.deltaT[pt.pb] = 0.f;
+        sa[t] = va;
+        sb[t] = vb;
+        __syncthreads();
+        float xn = 0.f;
+        if (in) {
+            float d = sa[pt.qa] + sb[pt.qb];
+            if (a.zc) d *= a.zc[j];
+            const long long bj = (a.box_len == 1) ? 0 : j;
+            xn = clampf(xv + d, a.lo[bj], a.hi[bj]);
+            a.x[j] = xn;
+        }
+        if (a.xA) {
+            __syncthreads();
+            sa[pt.qa] = xn;
+            sb[pt.qb] = xn;
+            __syncthreads();
+            if (pt.ina) a.xA[pt.pa] = sa[t];
+            if (pt.inb) a.xB[pt.pb] = sb[t];
+        }
+        __syncthreads();
+    }
+    if (blockIdx.x == 0) sweep_epilogue(a.epi);
+}
+
+// x (row-major H x W) copied into the wide and the tall patch layouts: the
+// gathers of the one-pass row pass in the patch numbering.  Padding reads 0.
+__global__ void __launch_bounds__(256) k_patch_image(const float* x, float* xA, float* xB, int H, int W,
+                                                     int Wp) {
+    __shared__ float sa[kPtRows * kPtCols], sb[kPtRows * kPtCols];
+    const int tw = (W + kPtCols - 1) / kPtCols;
+    const long long ntiles = (long long)tw * ((H + kPtRows - 1) / kPtRows);
+    const int t = threadIdx.x;
+    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int y0 = (int)(ti / tw) * kPtRows, x0 = (int)(ti % tw) * kPtCols;
+        const PatchTile pt(t, y0, x0, Wp);
+        const int y = y0 + (t >> 5), xc = x0 + (t & 31);
+        const float v = (y < H && xc < W) ? x[(long long)y * W + xc] : 0.f;
+        sa[pt.qa] = v;
+        sb[pt.qb] = v;
+        __syncthreads();
+        if (pt.ina) xA[pt.pa] = sa[t];
+        if (pt.inb) xB[pt.pb] = sb[t];
+        __syncthreads();
+    }
+}
+
+// The packed column indices of every row rewritten to its patch position,
+// in place: tall patches for the rows marked in rowT, wide ones for the
+// others (one warp per packed row; padding entries untouched).
+__global__ void k_patch_cols(const int2* rinfo, const unsigned char* rowT, int m, unsigned long long recipW,
+                             int W, int Wp, int* col) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += nw) {
+        const int2 ri = rinfo[i];
+        const bool tall = rowT[i] != 0;
+        for (int e = lane; e < ri.y; e += 32) col[ri.x + e] = patch_index(col[ri.x + e], recipW, W, Wp, tall);
+    }
+}
+
 // xT <- x column-major (H x W image, one right-hand side): the copy that the
 // two-pass row pass gathers from for the rows running down the image.  Tiles
 // of 32 image rows x 8 columns as in k_finalize_tr, one pixel per thread.
@@ -803,6 +908,15 @@ cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
+    if (a.deltaT && a.patch) {
+        if (a.B != 1 || a.imgW < 1 || a.imgH < 1 || (long long)a.imgW * a.imgH != a.nB ||
+            a.imgWp < a.imgW || (a.imgWp & 7) != 0)
+            return cudaErrorInvalidValue;
+        const long long tiles = (long long)((a.imgW + kPtCols - 1) / kPtCols) *
+                                ((a.imgH + kPtRows - 1) / kPtRows);
+        k_finalize_patch<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.deltaT) {
         if (a.B != 1 || a.imgW < 1 || a.imgH < 1 || (long long)a.imgW * a.imgH != a.nB)
             return cudaErrorInvalidValue;
@@ -812,6 +926,22 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
         return cudaGetLastError();
     }
     k_finalize<<<grid, kFinalizeThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_image(const float* x, float* xA, float* xB, int H, int W, int Wp, cudaStream_t s) {
+    if (H < 1 || W < 1 || Wp < W || (Wp & 7) != 0) return cudaErrorInvalidValue;
+    const long long tiles = (long long)((W + kPtCols - 1) / kPtCols) * ((H + kPtRows - 1) / kPtRows);
+    k_patch_image<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(x, xA, xB, H, W, Wp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_patch_cols(const int2* rinfo, const unsigned char* rowT, int m, unsigned long long recipW,
+                              int W, int Wp, int* col, cudaStream_t s) {
+    if (m < 1) return cudaSuccess;
+    if (W < 1 || Wp < W || (Wp & 7) != 0) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(((long long)m * 32 + 255) / 256, 152 * 16);
+    k_patch_cols<<<grid, 256, 0, s>>>(rinfo, rowT, m, recipW, W, Wp, col);
     return cudaGetLastError();
 }
 

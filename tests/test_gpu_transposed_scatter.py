@@ -10,7 +10,10 @@ scatters by L2 reductions (the transposed accumulator serves only that
 form).  Covered: square and non-square grids (the index map divides by the
 width), Cimmino, BIP with angle blocks (a box step per block), DROP (the
 column scaling applies to the sum of both accumulators), a superiorized run
-with graphs, and the rejections.
+with graphs, and the rejections.  The one-pass cases run in both numberings
+of the accumulators: row- and column-major (scatter_transpose 1) and the
+patch numbering (2), whose grid is padded to multiples of 8 (the non-square
+grids have widths and heights that are not).
 """
 import numpy as np
 import pytest
@@ -42,29 +45,32 @@ def _one_sweep(prob, mode=O.CIMMINO, lam=1.0, **kw):
 
 
 @pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
-@pytest.mark.parametrize("tr", [1, -1])
+@pytest.mark.parametrize("tr", [1, 2, -1])
 def test_ct_one_sweep(mode, tr):
     prob = synth.ct_problem(160, 120, 227)
     if mode == O.BIP:
         prob.blocks = synth.angle_blocks(120, 227, 12)
     info, xg, ph, xo, po = _one_sweep(prob, mode, scatter_transpose=tr)
     assert info["strategy"] == pk.STRATEGY_ONE_PASS and info["scatter"] == 1
-    if tr == 1:
+    if tr >= 1:
         # about half of the rays are steeper than 45 degrees
         assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
     else:
         assert info["transposed_rows"] == 0
+    assert info["scatter_patch"] == (1 if tr == 2 else 0)
     assert rel_l2(xg, xo) <= 1e-5
     assert rel(ph[0], po) <= 1e-5
 
 
-@pytest.mark.parametrize("shape", [(96, 211), (211, 96)])
-def test_non_square_grid(shape):
+@pytest.mark.parametrize("tr", [1, 2])
+@pytest.mark.parametrize("shape", [(96, 211), (211, 96), (131, 157)])
+def test_non_square_grid(shape, tr):
     H, W = shape
     prob = synth.line_problem(H, W, 1500, seed=H)
-    info, xg, ph, xo, po = _one_sweep(prob, lam=1.3, scatter_transpose=1)
+    info, xg, ph, xo, po = _one_sweep(prob, lam=1.3, scatter_transpose=tr)
     # segments in uniform directions: about half run down the image
     assert 0.3 * prob.A.m < info["transposed_rows"] < 0.7 * prob.A.m
+    assert info["scatter_patch"] == (1 if tr == 2 else 0)
     assert rel_l2(xg, xo) <= 1e-5
     assert rel(ph[0], po) <= 1e-5
 
@@ -109,19 +115,21 @@ def test_two_pass_non_square_grid_and_proximity():
     ctx.close()
 
 
-def test_drop_scales_both_accumulators():
+@pytest.mark.parametrize("tr", [1, 2])
+def test_drop_scales_both_accumulators(tr):
     prob = synth.ct_problem(160, 120, 227)
-    info, xg, ph, xo, po = _one_sweep(prob, O.DROP, scatter_transpose=1)
+    info, xg, ph, xo, po = _one_sweep(prob, O.DROP, scatter_transpose=tr)
     assert info["transposed_rows"] > 0
     assert rel_l2(xg, xo) <= 1e-5
 
 
-def test_superiorized_run_with_graphs():
+@pytest.mark.parametrize("tr", [1, 2])
+def test_superiorized_run_with_graphs(tr):
     prob = synth.ct_problem(160, 120, 227)
     K = 30
     sup = dict(gamma=0.5, alpha=0.99, n_red=1)
     ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_ONE_PASS,
-                          scatter_transpose=1)
+                          scatter_transpose=tr)
     assert ctx.suppy_info_get()["transposed_rows"] > 0
     st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=K, use_graphs=1, **sup))[0]
     S, l, u, lo, hi = O.from_problem(prob)
@@ -140,10 +148,11 @@ def test_rejections():
     with pytest.raises(pk.SuppyError):
         pk.from_problem(prob, scatter_transpose=1)
     with pytest.raises(pk.SuppyError):
-        pk.from_problem(synth.ct_problem(160, 120, 227), scatter_transpose=2)
+        pk.from_problem(synth.ct_problem(160, 120, 227), scatter_transpose=3)
     two = synth.ct_problem(160, 120, 227, nrhs=2)
-    with pytest.raises(pk.SuppyError):
-        pk.from_problem(two, scatter_transpose=1)
+    for tr in (1, 2):
+        with pytest.raises(pk.SuppyError):
+            pk.from_problem(two, scatter_transpose=tr)
 
 
 def test_device_resident_inputs():
