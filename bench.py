@@ -777,12 +777,7 @@ def ours(args):
     if args.pin:
         # a configuration the tuner chose in a plain run, rebuilt without
         # timing (under a profiler the tuner's timings are not the plain ones)
-        vals = [int(v) for v in args.pin.split(",")]
-        st_, tile, stages, lanes, mp, cmp_ = vals[:6]
-        tr = vals[6] if len(vals) > 6 else -1
-        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=st_,
-                              stream_shape=(tile, stages, lanes), stream_map=mp,
-                              stream_col_map=cmp_, scatter_transpose=tr)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, **pinned_opts(pk, args.pin))
     else:
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1)
     t_create = time.perf_counter() - t0
@@ -893,7 +888,17 @@ def ours(args):
     return 0
 
 
-def profile_case(case: int, steps: int, warm: int = 0) -> int:
+def pinned_opts(pk, pin: str) -> dict:
+    """from_problem options of a --pin launch configuration
+    (strategy,tile,stages,lanes,map,col_map[,pixel numbering])."""
+    vals = [int(v) for v in pin.split(",")]
+    st_, tile, stages, lanes, mp, cmp_ = vals[:6]
+    tr = vals[6] if len(vals) > 6 else -1
+    return dict(strategy=st_, stream_shape=(tile, stages, lanes), stream_map=mp,
+                stream_col_map=cmp_, scatter_transpose=tr)
+
+
+def profile_case(case: int, steps: int, warm: int = 0, pin: str = "") -> int:
     """A short run for ncu.  Cases 1 / 2: CT 384x384 (A ~0.4 GB, above L2; the
     device holds about 1 GB) with the one- / two-pass sweep.  Case 3: the CT
     512x512 workload with the sweep and launch shapes bench.py uses (two
@@ -913,7 +918,9 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
     global memory; case 11: CT 384x384 with the tiled one-pass sweep.
     The profiled iterations run inside the NVTX range "profile", so that
     `ncu --nvtx --nvtx-include profile/` skips the tuning launches and the
-    `warm` iterations run before it."""
+    `warm` iterations run before it.  Cases 3, 4 and 6 take a --pin launch
+    configuration instead of tuning (under ncu the serialised launches
+    distort the tuner's timings)."""
     import torch
     import synth
     from paper_2606_27086_gb300 import build as pkbuild
@@ -930,7 +937,8 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
     elif case == 6:
         prob = ct512()
         prob.blocks = synth.angle_blocks(360, 725, 36)
-        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP, tune=1)
+        kw = pinned_opts(pk, pin) if pin else dict(tune=1)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, mode=pk.SUPPY_BIP, **kw)
     elif case == 7:
         prob = synth.seismic_problem(nrhs=16)
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ANISO, strategy=pk.STRATEGY_TWO_PASS)
@@ -955,9 +963,9 @@ def profile_case(case: int, steps: int, warm: int = 0) -> int:
         ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_TILED)
     elif case in (3, 4):
         prob = ct512()
-        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, tune=1,
-                              strategy=pk.STRATEGY_TWO_PASS if case == 3 else
-                              pk.STRATEGY_ONE_PASS)
+        kw = pinned_opts(pk, pin) if pin else dict(
+            tune=1, strategy=pk.STRATEGY_TWO_PASS if case == 3 else pk.STRATEGY_ONE_PASS)
+        ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, **kw)
     else:
         prob = synth.ct_problem(384, 270, 545, I0=5e3, delta=0.02, seed_phantom=201,
                                 seed_noise=202)
@@ -1019,7 +1027,7 @@ def main():
     args = ap.parse_args()
     if args.profile:
         return profile_case(args.profile, args.steps if args.steps < 50 else 6,
-                            args.profile_warmup)
+                            args.profile_warmup, args.pin)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

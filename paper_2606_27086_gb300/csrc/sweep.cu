@@ -555,94 +555,144 @@ __global__ void __launch_bounds__(256) k_finalize_tr(const FinalizeArgs a) {
     if (blockIdx.x == 0) sweep_epilogue(a.epi);
 }
 
-// Patch tiles: 8 image rows x 32 columns, one pixel per thread.  The tile's
-// wide patches are two runs of four 128-byte lines (line rows y0/4 and
-// y0/4 + 1, lines x0/8 .. x0/8 + 3 of each), its tall patches one run of
-// eight lines (line row y0/8, lines x0/4 .. x0/4 + 7); thread t reads or
-// writes position t of each run (coalesced), and the pixel (iy, ix) of
-// thread t sits at qa(t) / qb(t) of the runs.  Lines past the padded width
-// are not touched.
-constexpr int kPtRows = 8, kPtCols = 32;
-struct PatchTile {
-    int qa, qb;          // this thread's pixel in the wide / tall runs
-    bool ina, inb;       // run position t lies inside the padded grid
-    long long pa, pb;    // run position t in the wide / tall layouts
-    __device__ PatchTile(int t, int y0, int x0, int Wp) {
-        const int iy = t >> 5, ix = t & 31;
-        qa = ((iy >> 2) << 7) | ((ix >> 3) << 5) | (((iy >> 1) & 1) << 4) | (((ix >> 2) & 1) << 3) |
-             ((iy & 1) << 2) | (ix & 3);
-        qb = ((ix >> 2) << 5) | (((iy >> 2) & 1) << 4) | (((ix >> 1) & 1) << 3) | ((iy & 3) << 1) | (ix & 1);
-        const int lw8 = Wp >> 3, lw4 = Wp >> 2;   // lines per line row: wide, tall
-        ina = (x0 >> 3) + ((t >> 5) & 3) < lw8;
-        pa = ((long long)((y0 >> 2) + (t >> 7)) * lw8 + (x0 >> 3)) * 32 + (t & 127);
-        inb = (x0 >> 2) + (t >> 5) < lw4;
-        pb = ((long long)(y0 >> 3) * lw4 + (x0 >> 2)) * 32 + t;
+// Patch blocks: one thread per 4 x 4 pixel block (x0 = 4 bx, y0 = 4 by) of
+// the padded grid.  Such a block is exactly two 32-byte sectors of each patch
+// layout: in the wide layout the sectors of rows y0, y0 + 1 and y0 + 2, y0 + 3
+// (4 floats per row, at wa, wa + 4, wa + 16, wa + 20), in the tall layout
+// those of columns x0, x0 + 1 and x0 + 2, x0 + 3 (2 floats per row, at tb and
+// tb + 8), and four 16-byte rows of the row-major image when W is a multiple
+// of 4.  Every access is a 16-byte vector and a warp's 32 blocks fill whole
+// sectors; no shared memory, no barriers.  Positions as in patch_index.
+struct PatchBlock {
+    int x0, y0, wa, tb;
+    __device__ PatchBlock(int blk, int Wp) {
+        const int nbx = Wp >> 2;
+        const int by = blk / nbx, bx = blk - by * nbx;
+        x0 = bx << 2;
+        y0 = by << 2;
+        wa = ((by * (Wp >> 3) + (bx >> 1)) << 5) + ((bx & 1) << 3);
+        tb = (((by >> 1) * (Wp >> 2) + bx) << 5) + ((by & 1) << 4);
     }
+    // the block's rows r = 0..3 in the wide layout, and the tall layout's
+    // float4 k = 0..3 (columns x0, x0 + 1 of rows 2k', 2k' + 1 for k = k',
+    // columns x0 + 2, x0 + 3 for k = 2 + k')
+    __device__ int wide(int r) const { return wa + ((r >> 1) << 4) + ((r & 1) << 2); }
+    __device__ int tall(int k) const { return tb + (k << 2); }
 };
 
-// The same box step with both accumulators in the patch numbering
-// (patch_index), both read and cleared coalesced per patch tile; with xA / xB
-// set, the new x is also written in both patch layouts.
-__global__ void __launch_bounds__(256) k_finalize_patch(const FinalizeArgs a) {
-    __shared__ float sa[kPtRows * kPtCols], sb[kPtRows * kPtCols];
-    const int H = a.imgH, W = a.imgW;
-    const int tw = (W + kPtCols - 1) / kPtCols;
-    const long long ntiles = (long long)tw * ((H + kPtRows - 1) / kPtRows);
-    const int t = threadIdx.x;
-    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        const int y0 = (int)(ti / tw) * kPtRows, x0 = (int)(ti % tw) * kPtCols;
-        const PatchTile pt(t, y0, x0, a.imgWp);
-        const int y = y0 + (t >> 5), x = x0 + (t & 31);
-        const bool in = y < H && x < W;
-        const long long j = (long long)y * W + x;
-        const float va = pt.ina ? a.delta[pt.pa] : 0.f;
-        const float vb = pt.inb ? a.deltaT[pt.pb] : 0.f;
-        const float xv = in ? a.x[j] : 0.f;
-        if (pt.ina) a.delta[pt.pa] = 0.f;
-        if (pt.inb) a.deltaT[pt.pb] = 0.f;
-        sa[t] = va;
-        sb[t] = vb;
-        __syncthreads();
-        float xn = 0.f;
-        if (in) {
-            float d = sa[pt.qa] + sb[pt.qb];
-            if (a.zc) d *= a.zc[j];
-            const long long bj = (a.box_len == 1) ? 0 : j;
-            xn = clampf(xv + d, a.lo[bj], a.hi[bj]);
-            a.x[j] = xn;
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float comp(const float4& v, int i) {
+    return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Row r of a 4 x 4 block from its two tall sectors (float4 t[0..3] as loaded
+// at tall(0..3)): columns 0, 1 from t[r >> 1], columns 2, 3 from t[2 + (r >> 1)].
+__device__ __forceinline__ float4 tall_row(const float4* t, int r) {
+    const float4& a = t[r >> 1];
+    const float4& b = t[2 + (r >> 1)];
+    return (r & 1) ? make_float4(a.z, a.w, b.z, b.w) : make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Rows r of a 4 x 4 block of the row-major H x W image (0 outside it):
+// 16-byte loads when the block lies inside and W is a multiple of 4.
+__device__ __forceinline__ void load_rows(const float* img, int H, int W, const PatchBlock& pb, bool vec,
+                                          float4* row) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = pb.y0 + r;
+        if (vec) {
+            row[r] = ld4(img + (size_t)y * W + pb.x0);
+        } else {
+            float v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int x = pb.x0 + c;
+                v[c] = (y < H && x < W) ? img[(size_t)y * W + x] : 0.f;
+            }
+            row[r] = make_float4(v[0], v[1], v[2], v[3]);
         }
-        if (a.xA) {
-            __syncthreads();
-            sa[pt.qa] = xn;
-            sb[pt.qb] = xn;
-            __syncthreads();
-            if (pt.ina) a.xA[pt.pa] = sa[t];
-            if (pt.inb) a.xB[pt.pb] = sb[t];
-        }
-        __syncthreads();
     }
-    if (blockIdx.x == 0) sweep_epilogue(a.epi);
+}
+
+// Writes rows of the block to both patch layouts.
+__device__ __forceinline__ void store_patches(float* xA, float* xB, const PatchBlock& pb, const float4* row) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) st4(xA + pb.wide(r), row[r]);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float4& a = row[2 * k];
+        const float4& b = row[2 * k + 1];
+        st4(xB + pb.tall(k), make_float4(a.x, a.y, b.x, b.y));       // columns 0, 1
+        st4(xB + pb.tall(2 + k), make_float4(a.z, a.w, b.z, b.w));   // columns 2, 3
+    }
+}
+
+// The same box step with both accumulators in the patch numbering
+// (patch_index), both read and cleared per 4 x 4 block; with xA / xB set,
+// the new x is also written in both patch layouts.  The sweep epilogue needs
+// only the row pass's proximity partials and the right-hand-side state, which
+// this kernel does not touch, so the last CTA runs it beside the others.
+__global__ void __launch_bounds__(128) k_finalize_patch(const FinalizeArgs a) {
+    if (blockIdx.x == gridDim.x - 1) {
+        sweep_epilogue(a.epi);
+        return;
+    }
+    const int H = a.imgH, W = a.imgW, Wp = a.imgWp;
+    const int nblk = (Wp >> 2) * (((H + 7) & ~7) >> 2);
+    const bool wvec = (W & 3) == 0;
+    const int stride = (gridDim.x - 1) * blockDim.x;
+    for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < nblk; blk += stride) {
+        const PatchBlock pb(blk, Wp);
+        const bool vec = wvec && pb.x0 + 3 < W && pb.y0 + 3 < H;
+        float4 dA[4], dB[4], xr[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) dA[r] = ld4(a.delta + pb.wide(r));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dB[k] = ld4(a.deltaT + pb.tall(k));
+        load_rows(a.x, H, W, pb, vec, xr);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(a.delta + pb.wide(r), z4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) st4(a.deltaT + pb.tall(k), z4);
+        float4 xn[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int y = pb.y0 + r;
+            const float4 t = tall_row(dB, r);
+            float o[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int x = pb.x0 + c;
+                o[c] = 0.f;
+                if (y < H && x < W) {
+                    const size_t j = (size_t)y * W + x;
+                    float d = comp(dA[r], c) + comp(t, c);
+                    if (a.zc) d *= a.zc[j];
+                    const size_t bj = (a.box_len == 1) ? 0 : j;
+                    o[c] = clampf(comp(xr[r], c) + d, a.lo[bj], a.hi[bj]);
+                    if (!vec) a.x[j] = o[c];
+                }
+            }
+            xn[r] = make_float4(o[0], o[1], o[2], o[3]);
+            if (vec) st4(a.x + (size_t)y * W + pb.x0, xn[r]);
+        }
+        if (a.xA) store_patches(a.xA, a.xB, pb, xn);
+    }
 }
 
 // x (row-major H x W) copied into the wide and the tall patch layouts: the
 // gathers of the one-pass row pass in the patch numbering.  Padding reads 0.
-__global__ void __launch_bounds__(256) k_patch_image(const float* x, float* xA, float* xB, int H, int W,
+__global__ void __launch_bounds__(128) k_patch_image(const float* x, float* xA, float* xB, int H, int W,
                                                      int Wp) {
-    __shared__ float sa[kPtRows * kPtCols], sb[kPtRows * kPtCols];
-    const int tw = (W + kPtCols - 1) / kPtCols;
-    const long long ntiles = (long long)tw * ((H + kPtRows - 1) / kPtRows);
-    const int t = threadIdx.x;
-    for (long long ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        const int y0 = (int)(ti / tw) * kPtRows, x0 = (int)(ti % tw) * kPtCols;
-        const PatchTile pt(t, y0, x0, Wp);
-        const int y = y0 + (t >> 5), xc = x0 + (t & 31);
-        const float v = (y < H && xc < W) ? x[(long long)y * W + xc] : 0.f;
-        sa[pt.qa] = v;
-        sb[pt.qb] = v;
-        __syncthreads();
-        if (pt.ina) xA[pt.pa] = sa[t];
-        if (pt.inb) xB[pt.pb] = sb[t];
-        __syncthreads();
+    const int nblk = (Wp >> 2) * (((H + 7) & ~7) >> 2);
+    const bool wvec = (W & 3) == 0;
+    for (int blk = blockIdx.x * blockDim.x + threadIdx.x; blk < nblk; blk += gridDim.x * blockDim.x) {
+        const PatchBlock pb(blk, Wp);
+        float4 xr[4];
+        load_rows(x, H, W, pb, wvec && pb.x0 + 3 < W && pb.y0 + 3 < H, xr);
+        store_patches(xA, xB, pb, xr);
     }
 }
 
@@ -912,9 +962,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
         if (a.B != 1 || a.imgW < 1 || a.imgH < 1 || (long long)a.imgW * a.imgH != a.nB ||
             a.imgWp < a.imgW || (a.imgWp & 7) != 0)
             return cudaErrorInvalidValue;
-        const long long tiles = (long long)((a.imgW + kPtCols - 1) / kPtCols) *
-                                ((a.imgH + kPtRows - 1) / kPtRows);
-        k_finalize_patch<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(a);
+        const long long blocks = (long long)(a.imgWp >> 2) * (((a.imgH + 7) & ~7) >> 2);
+        // the pixel blocks' CTAs, then one for the epilogue
+        k_finalize_patch<<<(int)std::min<long long>((blocks + 127) / 128, 152 * 16) + 1, 128, 0, s>>>(a);
         return cudaGetLastError();
     }
     if (a.deltaT) {
@@ -931,8 +981,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a, int grid, cudaStream_t s) {
 
 cudaError_t launch_patch_image(const float* x, float* xA, float* xB, int H, int W, int Wp, cudaStream_t s) {
     if (H < 1 || W < 1 || Wp < W || (Wp & 7) != 0) return cudaErrorInvalidValue;
-    const long long tiles = (long long)((W + kPtCols - 1) / kPtCols) * ((H + kPtRows - 1) / kPtRows);
-    k_patch_image<<<(int)std::min<long long>(tiles, 4096), 256, 0, s>>>(x, xA, xB, H, W, Wp);
+    const long long blocks = (long long)(Wp >> 2) * (((H + 7) & ~7) >> 2);
+    k_patch_image<<<(int)std::min<long long>((blocks + 127) / 128, 152 * 16), 128, 0, s>>>(x, xA, xB, H, W,
+                                                                                          Wp);
     return cudaGetLastError();
 }
 
