@@ -155,6 +155,43 @@ def test_rejections():
             pk.from_problem(two, scatter_transpose=tr)
 
 
+@pytest.mark.parametrize("case", ["ct_cimmino", "ct_bip", "lines"])
+def test_patch_numbering_vector_box_and_infinite_bounds(case):
+    """The patch numbering's box step with a box per pixel and infinite slab
+    bounds: on the CT grid (widths a multiple of 4: the box step's 16-byte
+    path; BIP writes the next block's patch copies of x), and on a 131 x 157
+    grid (the element-wise path and a padded patch grid)."""
+    if case == "lines":
+        prob = synth.line_problem(131, 157, 2500, seed=31)
+    else:
+        prob = synth.ct_problem(160, 120, 227)
+    mode = O.BIP if case == "ct_bip" else O.CIMMINO
+    if mode == O.BIP:
+        prob.blocks = synth.angle_blocks(120, 227, 12)
+    n = prob.A.n
+    rng = np.random.default_rng(32)
+    prob.box_lo = rng.uniform(-0.2, 0.3, size=n).astype(np.float32)
+    prob.box_hi = (prob.box_lo + rng.uniform(0.1, 1.0, size=n)).astype(np.float32)
+    prob.l = prob.l.copy()
+    prob.u = prob.u.copy()
+    prob.l[::3] = -np.inf
+    prob.u[1::3] = np.inf
+    ctx = pk.from_problem(prob, mode=mode, strategy=pk.STRATEGY_ONE_PASS, scatter_transpose=2)
+    assert ctx.suppy_info_get()["scatter_patch"] == 1
+    x0 = random_x(n, 1, seed=33)
+    ctx.suppy_set_x(x0)   # projected onto the box
+    ctx.suppy_sweep(pk.suppy_params_default(lam=1.2), 1)
+    xg = ctx.suppy_get_x()
+    ph, _ = ctx.suppy_history()
+    ctx.close()
+    S, l, u, lo, hi = O.from_problem(prob, mode)
+    x0c = np.clip(x0.astype(np.float64), lo, hi)
+    xo, po = O.sweep(S, mode, l, u, 1.2, lo, hi, x0c)
+    assert rel_l2(xg, xo) <= 1e-5
+    assert np.all(xg >= prob.box_lo) and np.all(xg <= prob.box_hi)
+    assert rel(ph[0], po) <= 1e-5
+
+
 def test_device_resident_inputs():
     """A, l, u and the box given as device tensors: the row orientation is
     taken from a host copy of the column indices, the sweep is the same."""
