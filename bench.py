@@ -826,7 +826,8 @@ def ours(args):
     traffic, tnote = sweep_traffic(info)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "sweep (every launch of one application of T: " + STRATEGY[info["strategy"]] + ")",
+            "kernel": "sweep (every launch of one application of T: " + STRATEGY[info["strategy"]] +
+                      (", patch numbering" if info.get("scatter_patch") else "") + ")",
             "alg_bytes_per_launch": alg, "launch_ms": t_sweep,
             "alg_bytes_formula": "nnz*(4+4) + m*16 + n*16 per sweep",
             "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs, a burst copy)"}
