@@ -51,3 +51,28 @@ def test_a_list_of_captures_is_matched_by_shape():
     assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=0))[0] == 1945000000.0
     assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=5))[0] == 1947000000.0
     assert bench.sweep_traffic_from(table, dict(INFO2, transposed_rows=7))[0] is None
+
+
+def test_pinned_configuration_parses_into_create_options():
+    """--pin strategy,tile,stages,lanes,map,col_map[,numbering] becomes the
+    from_problem options that rebuild a tuned configuration without timing."""
+    o = bench.pinned_opts(None, "1,4096,6,32,2,2,2")
+    assert o == dict(strategy=1, stream_shape=(4096, 6, 32), stream_map=2, stream_col_map=2,
+                     scatter_transpose=2)
+    # without the seventh field the pixel numbering is off
+    assert bench.pinned_opts(None, "2,2048,13,16,1,2")["scatter_transpose"] == -1
+
+
+def test_committed_traffic_table_keys_the_patch_numbering():
+    """The committed captures are told apart by the numbering flag: the patch
+    form's DRAM bytes are not reported for the row-/column-major form of the
+    same ring shape, and the reverse."""
+    import json
+    import os
+    table = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    base = dict(strategy=1, tile=4096, stages=6, lanes_per_row=32, map=2, transposed_rows=116363)
+    patch, _ = bench.sweep_traffic_from(table, dict(base, scatter_patch=1))
+    plain, _ = bench.sweep_traffic_from(table, dict(base, scatter_patch=0))
+    assert patch is not None and plain is not None and patch != plain
+    # both read A once: about its 0.96 GB plus the vectors
+    assert 0.95e9 < patch < 1.0e9 and 0.95e9 < plain < 1.0e9
