@@ -192,6 +192,22 @@ def test_patch_numbering_vector_box_and_infinite_bounds(case):
     assert rel(ph[0], po) <= 1e-5
 
 
+@pytest.mark.parametrize("mode", [O.CIMMINO, O.BIP])
+def test_patch_numbering_on_scattered_rows(mode):
+    """Rows that are not rays (random columns, 32-88 entries) on a 150 x 170
+    grid: any index pattern goes through the stored patch positions, the
+    copies and the accumulators, and the box step's element-wise path (170
+    is not a multiple of 4)."""
+    prob = synth.random_problem(6000, 150 * 170, seed=41, feasible=False, mean_len=60)
+    prob.shape = (150, 170)
+    if mode == O.BIP:
+        prob.blocks = np.arange(prob.A.m) % 5
+    info, xg, ph, xo, po = _one_sweep(prob, mode, lam=0.9, scatter_transpose=2)
+    assert info["scatter_patch"] == 1
+    assert rel_l2(xg, xo) <= 1e-5
+    assert rel(ph[0], po) <= 1e-5
+
+
 def test_device_resident_inputs():
     """A, l, u and the box given as device tensors: the row orientation is
     taken from a host copy of the column indices, the sweep is the same."""
