@@ -580,14 +580,14 @@ struct RowWork {
                 int t = gl;
                 for (; t + 3 * G < len; t += 4 * G) {
                     int c[4];
-                    float w[4];
+                    float av[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         c[u] = ix[t + u * G];
-                        w[u] = to_f(v[t + u * G]);
+                        av[u] = to_f(v[t + u * G]);
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) atomicAdd(at(c[u]), coef * w[u]);
+                    for (int u = 0; u < 4; ++u) atomicAdd(at(c[u]), coef * av[u]);
                 }
                 for (; t < len; t += G) atomicAdd(at(ix[t]), coef * to_f(v[t]));
             } else {
