@@ -697,7 +697,10 @@ suppy_status enqueue_tile_sweep(suppy_ctx* c, const suppy_params* p, const StopP
     return SUPPY_OK;
 }
 
-suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
+// copies_fresh: the whole-GPU perturbation phase enqueued just before left
+// the patch copies of x (a superiorized iteration), so the sweep need not
+// make them.
+suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p, bool copies_fresh = false) {
     const StopParams sp = stop_params(c, p);
     suppy_status s;
     if (c->dvc_on && (s = enqueue_cq_step(c)) != SUPPY_OK) return s;
@@ -772,7 +775,8 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
                 }
                 // the patch copies of x: at the sweep start (later blocks
                 // find them written by the previous block's box step)
-                if (patch && t == 0) {
+                // (a dose-volume CQ step before the row pass changes x)
+                if (patch && t == 0 && !(copies_fresh && !c->dvc_on)) {
                     CK(launch_patch_image(c->d_x, c->d_xA, c->d_xB, c->gH, c->gW, c->gWp, c->stream));
                     note_launch(c);
                 }
@@ -915,7 +919,10 @@ suppy_status enqueue_sweep(suppy_ctx* c, const suppy_params* p) {
     return SUPPY_OK;
 }
 
-suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_only) {
+// copies: when not null, the phase also leaves x in the patch layouts of the
+// one-pass sweep that follows it (whole-GPU phase, patch numbering), and
+// *copies says whether it does.
+suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_only, bool* copies = nullptr) {
     PerturbArgs a;
     a.x = c->d_x;
     a.g = c->d_g;
@@ -940,6 +947,18 @@ suppy_status enqueue_perturb(suppy_ctx* c, const suppy_params* p, int record_onl
     a.ticket = c->d_ticket;
     a.err = c->d_err;
     a.wait_cycles = c->wait_cycles;
+    a.pA = nullptr;
+    a.pB = nullptr;
+    a.pWp = 0;
+    const bool patch_next = c->use_tma && c->strategy == 1 && c->scat == 1 && c->d_rowT && c->tr_on &&
+                            c->tr_patch && c->d_colP && c->B == 1;
+    if (copies) *copies = false;
+    if (copies && patch_next && c->wide && !record_only) {
+        a.pA = c->d_xA;
+        a.pB = c->d_xB;
+        a.pWp = c->gWp;
+        *copies = true;
+    }
     Timed tm{c, 2};
     CK(tm.begin());
     if (c->wide && !record_only) {
@@ -2362,8 +2381,9 @@ suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) 
     if (p->variance_tol > 0.0 && (s = ensure_variance(c)) != SUPPY_OK) return s;
     if (!use_graph) {
         for (int k = 0; k < iters; ++k) {
-            if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0)) != SUPPY_OK) return s;
-            if ((s = enqueue_sweep(c, p)) != SUPPY_OK) return s;
+            bool fresh = false;
+            if (c->obj != SUPPY_OBJ_NONE && (s = enqueue_perturb(c, p, 0, &fresh)) != SUPPY_OK) return s;
+            if ((s = enqueue_sweep(c, p, fresh)) != SUPPY_OK) return s;
             if ((s = enqueue_variance(c, p)) != SUPPY_OK) return s;
         }
         return SUPPY_OK;
@@ -2395,8 +2415,9 @@ suppy_status enqueue_iterations(suppy_ctx* c, const suppy_params* p, int iters) 
             return fail(c, SUPPY_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         }
         s = SUPPY_OK;
-        if (c->obj != SUPPY_OBJ_NONE) s = enqueue_perturb(c, p, 0);
-        if (s == SUPPY_OK) s = enqueue_sweep(c, p);
+        bool fresh = false;
+        if (c->obj != SUPPY_OBJ_NONE) s = enqueue_perturb(c, p, 0, &fresh);
+        if (s == SUPPY_OK) s = enqueue_sweep(c, p, fresh);
         if (s == SUPPY_OK) s = enqueue_variance(c, p);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(c->stream, &g);

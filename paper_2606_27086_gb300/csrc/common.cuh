@@ -151,6 +151,12 @@ struct PerturbArgs {
     unsigned* ticket;       // whole-GPU kernel: grid barrier {arrivals, generation}
     int* err;               // whole-GPU kernel: error word (2: a barrier timed out)
     long long wait_cycles;  // whole-GPU kernel: budget of one barrier wait (SM clock cycles)
+    // whole-GPU kernel, one right-hand side: when set, the phase also leaves
+    // x in the wide / tall patch layouts (padded width pWp) for the one-pass
+    // sweep that follows it
+    float* pA;
+    float* pB;
+    int pWp;
 };
 
 // Threads per CTA of the whole-GPU reduction kernels (variance rule), of the
@@ -545,14 +551,16 @@ __device__ __forceinline__ int transposed_index(int j, unsigned long long recipW
 // and sectors here than in a row- or column-major image whenever it is not
 // axis-aligned: rays closer to the horizontal take the wide patches, the
 // others the tall ones.  y = j / W as in transposed_index.
-__device__ __forceinline__ int patch_index(int j, unsigned long long recipW, int W, int Wp, bool tall) {
-    const int y = (int)__umul64hi((unsigned long long)(unsigned)j, recipW);
-    const int x = j - y * W;
+__device__ __forceinline__ int patch_pos(int y, int x, int Wp, bool tall) {
     if (!tall)
         return (((y >> 2) * (Wp >> 3) + (x >> 3)) << 5) | (((y >> 1) & 1) << 4) | (((x >> 2) & 1) << 3) |
                ((y & 1) << 2) | (x & 3);
     return (((y >> 3) * (Wp >> 2) + (x >> 2)) << 5) | (((y >> 2) & 1) << 4) | (((x >> 1) & 1) << 3) |
            ((y & 3) << 1) | (x & 1);
+}
+__device__ __forceinline__ int patch_index(int j, unsigned long long recipW, int W, int Wp, bool tall) {
+    const int y = (int)__umul64hi((unsigned long long)(unsigned)j, recipW);
+    return patch_pos(y, j - y * W, Wp, tall);
 }
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) {

@@ -837,6 +837,7 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
         double f_start = 0.0;
         float* X = a.x + b;
         float* G = a.g + b;
+        bool copied = false;   // the patch copies were written with the last update
         for (int s = 0; s < a.n_red; ++s) {
             // pass G: subgradient, ||g||^2 and f(y)
             KSum kg, kf;
@@ -953,11 +954,22 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
                 trials += used;
                 jt += used;
                 if (hit >= 0) {
-                    // pass U: y <- z_hit
+                    // pass U: y <- z_hit (and its patch copies, pixel by pixel)
                     const float sc = sj_s[hit];
-                    for (int p = tid; p < n; p += stride) {
-                        const size_t o = (size_t)p * B;
-                        X[o] = trial(X[o], G[o], sc);
+                    if (a.pA) {
+                        StrideWalk pw(tid, stride, W);
+                        for (int p = tid; p < n; p += stride, pw.next()) {
+                            const float v = trial(X[p], G[p], sc);
+                            X[p] = v;
+                            a.pA[patch_pos(pw.i, pw.j, a.pWp, false)] = v;
+                            a.pB[patch_pos(pw.i, pw.j, a.pWp, true)] = v;
+                        }
+                        copied = true;
+                    } else {
+                        for (int p = tid; p < n; p += stride) {
+                            const size_t o = (size_t)p * B;
+                            X[o] = trial(X[o], G[o], sc);
+                        }
                     }
                     accepted += 1;
                     ok = true;
@@ -966,6 +978,16 @@ __global__ void __launch_bounds__(kPhaseThreads, 1) k_wide_phase(const PerturbAr
             if (!ok) break;
             // the next reduction step reads the neighbours' new y
             if (s + 1 < a.n_red && !grid_barrier<0>(a.ticket, a.err, part, gsum, res, a.wait_cycles)) return;
+        }
+        if (a.pA && !copied) {
+            // no step was taken: the copies of y as it stands (each thread its
+            // own pixels, which no other thread writes in this launch)
+            StrideWalk pw(tid, stride, W);
+            for (int p = tid; p < n; p += stride, pw.next()) {
+                const float v = X[p];
+                a.pA[patch_pos(pw.i, pw.j, a.pWp, false)] = v;
+                a.pB[patch_pos(pw.i, pw.j, a.pWp, true)] = v;
+            }
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) phase_end(a, st, ps, ell, accepted, trials, f_start);
     }

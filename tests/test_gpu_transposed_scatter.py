@@ -143,6 +143,33 @@ def test_superiorized_run_with_graphs(tr):
     ctx.close()
 
 
+@pytest.mark.parametrize("start", ["box0", "constant"])
+def test_patch_copies_from_the_whole_gpu_phase(start):
+    """Superiorized iterations with the whole-GPU perturbation phase before
+    each patch-numbered sweep: the phase leaves x in the patch layouts
+    (written with each accepted step, or copied when no step is taken) and
+    the sweep reads those copies.  Three reduction steps per phase; from a
+    constant image the TV subgradient is zero, so the phases take no step
+    until the sweeps make the image uneven."""
+    prob = synth.ct_problem(160, 120, 227)
+    K = 12
+    sup = dict(gamma=0.5, alpha=0.99, n_red=3)
+    ctx = pk.from_problem(prob, obj=pk.SUPPY_OBJ_TV_ISO, strategy=pk.STRATEGY_ONE_PASS,
+                          scatter_transpose=2, perturb_path=2)
+    assert ctx.suppy_info_get()["scatter_patch"] == 1
+    x0 = np.zeros(prob.A.n, np.float32) if start == "box0" else np.full(prob.A.n, 0.3, np.float32)
+    ctx.suppy_set_x(x0)
+    st = ctx.suppy_run(pk.suppy_params_default(max_sweeps=K, use_graphs=1, use_stopping=0, **sup))[0]
+    S, l, u, lo, hi = O.from_problem(prob)
+    r = O.run(S, O.CIMMINO, l, u, lo, hi, oracle_objective(prob, O.OBJ_TV_ISO),
+              O.Params(max_sweeps=K, **sup), x0=x0.astype(np.float64))
+    assert st["sweeps"] == K and abs(st["accepted"] - sum(r.accepted)) <= 2
+    assert rel_l2(ctx.suppy_get_x(), r.x) <= 1e-3
+    ph, _ = ctx.suppy_history()
+    assert np.max(np.abs(np.asarray(ph[:K]) - r.prox_hist[:K]) / np.abs(r.prox_hist[:K])) <= 1e-3
+    ctx.close()
+
+
 def test_rejections():
     prob = synth.random_problem(300, 30000, seed=3, mean_len=40)   # no image grid
     with pytest.raises(pk.SuppyError):
