@@ -225,7 +225,9 @@ typedef struct {
      * tall ones (lines of 4 x 8, sectors of 2 x 4).  Every row's indices are
      * stored as patch positions (a second copy of the packed indices, 4 bytes
      * per stored entry), its gathers read x from a copy in its layout (both
-     * copies made at each sweep start and written by each block's box step),
+     * copies made at each sweep start -- in suppy_run by the whole-GPU
+     * perturbation phase before the sweep -- and written by each block's box
+     * step),
      * and its corrections go into an accumulator in the same layout, so that
      * a warp's gathers and reductions along a slanted ray touch fewer
      * sectors; the two-pass sweep takes 2 as 1.  0 automatic (the patch
